@@ -1,0 +1,23 @@
+"""FP64 CPU oracle of the MOFF imaging path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The CUDA library never calls it and shares no
+code with it; the two meet only on the seeded inputs drawn by ``synth``.
+
+Parity status per function (what pins it other than itself):
+
+* ``unpack_4bit``      -- hand-decoded byte fixtures and the pack/unpack bijection.
+* ``anchors``          -- hand-computed fixtures (half-cell ties round up).
+* ``grid_matrix`` / ``grid`` -- brute-force FX identity (Eqs. m1-m6, Bdef),
+                          Parseval with non-overlapping footprints, shift invariance.
+* ``sky_transform``    -- naive DFT on tiny grids, point-source closed form (sign).
+* ``integrate``        -- FX identity (conjugation order of XY), Cauchy-Schwarz,
+                          polarisation-scaled inputs.
+* ``moff_image``       -- all of the above composed.
+* ``fx_image``         -- agreement with ``moff_image`` (independent formulation),
+                          single-antenna flat image.
+* ``pfb_window`` / ``pfb_spectra`` -- 1-tap rectangular case equals a library FFT,
+                          a hand-summed 2-tap case, tone-in-bin power.
+* ``quantise_4bit``    -- hand fixtures including half-to-even ties and clipping.
+"""
+from .moff_oracle import *  # noqa: F401,F403

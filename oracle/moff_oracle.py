@@ -1,0 +1,334 @@
+"""Plain FP64 statement of the MOFF imaging path (Morales, arXiv 0812.3669).
+
+TEST INFRASTRUCTURE ONLY -- see the package docstring.  Slow and literal by
+design: each function follows one step of the paper's final algorithm
+(Sec. 4, Eq. m6) in the paper's order,
+
+    I'(theta) = < | F^T(theta, r) W^T(r, a) N~(a, a) E'(a) |^2 >_t ,
+
+  step 1  N~   per-antenna complex weight (noise weighting with the
+               calibration folded in)                          -> ``calibrate``
+  step 2  W^T  grid each antenna through its holographic kernel -> ``grid``
+  step 3  F^T  spatial Fourier transform to the sky             -> ``sky_transform``
+  step 4  <|.|^2>_t square and time-sum, plus the cross-pol
+               products of a dual-pol array                    -> ``integrate``
+
+preceded by the F-stage channeliser (Sec. 2, Eq. FFTofE, "often implemented
+as polyphase filters") and the 4-bit voltage format.  ``fx_image`` computes
+the same image the other way round -- visibilities first (Eq. visDef), then
+gridding with the cross-correlated kernels (Eq. Bdef) and a transform
+(Eq. RBeamEq / m1) -- which is the identity the paper derives in Eqs. m1-m6.
+
+Readings taken where the paper is silent (all library-visible):
+  * the imaging transform uses exp(+2 pi i k.r/N), unnormalised (F^T read as
+    the adjoint of the exp(-2 pi i r.theta) in Eq. Ea), so a source injected
+    with phase exp(-2 pi i p.theta/N) images at +theta;
+  * kernels are applied exactly as supplied (no conjugation);
+  * a kernel is centred on the antenna's anchor cell floor(p + 0.5) and the
+    grid wraps circularly mod N;
+  * images are sums over time (the paper's average is sum / n_samples) and
+    include the autocorrelation terms;
+  * dual-pol products are XX = |Ex|^2, YY = |Ey|^2, XY = Ex conj(Ey) stored
+    as (Re XY, Im XY).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+__all__ = [
+    "unpack_4bit", "anchors", "calibrate", "grid_matrix", "grid", "sky_transform",
+    "integrate", "moff_image", "fx_image", "footprint", "pfb_window", "pfb_spectra",
+    "quantise_4bit", "ambiguous_codes", "channelise", "max_norm_err",
+]
+
+
+# ----------------------------------------------------------------------------- input
+
+def unpack_4bit(codes) -> np.ndarray:
+    """Decode 4-bit complex voltage bytes (the digitised E'(a) of Eq. m6).
+
+    High nibble = real part, low nibble = imaginary part, each a 4-bit two's
+    complement integer in [-8, 7].  Returns complex128 of the same shape.
+    """
+    c = np.asarray(codes, dtype=np.uint8).astype(np.int64)
+    hi = c // 16
+    lo = c % 16
+    re = np.where(hi >= 8, hi - 16, hi)
+    im = np.where(lo >= 8, lo - 16, lo)
+    return re.astype(np.float64) + 1j * im.astype(np.float64)
+
+
+def anchors(pos) -> np.ndarray:
+    """Anchor cell of each antenna: the nearest grid cell, ties rounding up.
+
+    ``pos`` is (x, y) in cell units; returns int64 [A][2].  The paper leaves
+    sub-cell placement to the kernel (Sec. 3: the kernel is the antenna's
+    aperture map), so taps are given on the cells around this anchor.
+    """
+    return np.floor(np.asarray(pos, dtype=np.float64) + 0.5).astype(np.int64)
+
+
+def calibrate(x, gains) -> np.ndarray:
+    """Eq. m6 step 1: y = N~ E' with a diagonal complex N~ per (channel, antenna, pol).
+
+    ``x`` complex [..., C, A, P]; ``gains`` complex [C, A, P] (broadcast over time).
+    """
+    return np.asarray(x, dtype=np.complex128) * np.asarray(gains, dtype=np.complex128)
+
+
+# ----------------------------------------------------------------------------- gridding
+
+def _full_taps(taps, n_pol, jones):
+    """Return taps as [A][P_out][P_in][K][K]; a per-pol kernel is a diagonal Jones matrix."""
+    t = np.asarray(taps, dtype=np.complex128)
+    if jones:
+        return t
+    A, P, K, _ = t.shape
+    out = np.zeros((A, P, P, K, K), dtype=np.complex128)
+    for p in range(P):
+        out[:, p, p] = t[:, p]
+    return out
+
+
+def grid_matrix(pos, taps, grid_n: int, n_pol: int, jones: bool = False):
+    """The gridding operator W^T(r, a) of Eq. m6 step 2 as a sparse matrix.
+
+    Row index = p_out * N^2 + ry * N + rx, column index = a * P_in + p_in,
+    entry = taps[a][p_out][p_in][dy][dx] at cell
+    (anchor_y + dy - K//2, anchor_x + dx - K//2) mod N.  Entries landing on
+    the same cell are summed.
+    """
+    T = _full_taps(taps, n_pol, jones)
+    A, Po, Pi, K, _ = T.shape
+    N = grid_n
+    anc = anchors(pos)
+    h = K // 2
+    rows, cols, vals = [], [], []
+    for a in range(A):
+        for po in range(Po):
+            for pi in range(Pi):
+                for iy in range(K):
+                    ry = (anc[a, 1] + iy - h) % N
+                    for ix in range(K):
+                        v = T[a, po, pi, iy, ix]
+                        if v == 0:
+                            continue
+                        rx = (anc[a, 0] + ix - h) % N
+                        rows.append(po * N * N + ry * N + rx)
+                        cols.append(a * Pi + pi)
+                        vals.append(v)
+    return sp.coo_matrix((np.asarray(vals, dtype=np.complex128), (rows, cols)),
+                         shape=(Po * N * N, A * Pi)).tocsr()
+
+
+def grid(y, W, grid_n: int, n_pol: int) -> np.ndarray:
+    """Eq. m6 step 2: G = W^T y for every snapshot.
+
+    ``y`` complex [S, A, P_in] (S snapshots); returns complex [S, P_out, N, N].
+    """
+    y = np.asarray(y, dtype=np.complex128)
+    S = y.shape[0]
+    Y = y.reshape(S, -1).T                        # [A*P_in, S]
+    G = (W @ Y).T                                 # [S, P_out*N*N]
+    return np.asarray(G).reshape(S, n_pol, grid_n, grid_n)
+
+
+def sky_transform(G) -> np.ndarray:
+    """Eq. m6 step 3: E(k) = sum_r G(r) exp(+2 pi i (ky ry + kx rx) / N), unnormalised.
+
+    Acts on the last two axes (ry, rx) -> (ky, kx), natural DFT order.
+    """
+    G = np.asarray(G, dtype=np.complex128)
+    N = G.shape[-1]
+    return np.fft.ifft2(G, axes=(-2, -1)) * (N * N)
+
+
+def integrate(E) -> np.ndarray:
+    """Eq. m6 step 4: sum over time of |E|^2, plus the cross-pol products.
+
+    ``E`` complex [T, P, N, N].  P == 1 -> [1, N, N] = sum_t |E|^2.  P == 2 ->
+    [4, N, N] = (sum |Ex|^2, sum |Ey|^2, Re sum Ex Ey*, Im sum Ex Ey*).
+    """
+    E = np.asarray(E, dtype=np.complex128)
+    if E.shape[1] == 1:
+        return np.sum(np.abs(E[:, 0]) ** 2, axis=0)[None]
+    ex, ey = E[:, 0], E[:, 1]
+    xy = np.sum(ex * np.conj(ey), axis=0)
+    return np.stack([np.sum(np.abs(ex) ** 2, axis=0), np.sum(np.abs(ey) ** 2, axis=0),
+                     xy.real, xy.imag])
+
+
+def moff_image(codes, gains, pos, taps, grid_n: int, n_pol: int, jones: bool = False,
+               channels=None, time_chunk: int = 256) -> np.ndarray:
+    """The whole of Eq. m6 for a block of 4-bit voltages.
+
+    ``codes`` uint8 [T, C, A, P_in]; ``gains`` complex [C, A, P_in]; returns
+    float64 [len(channels), n_prod, N, N] (sums over T).  ``channels`` selects
+    a subset of channel indices (default: all).
+    """
+    codes = np.asarray(codes)
+    Tn, C, A, Pi = codes.shape
+    chans = range(C) if channels is None else list(channels)
+    W = grid_matrix(pos, taps, grid_n, n_pol, jones)
+    n_prod = 1 if n_pol == 1 else 4
+    out = np.zeros((len(chans), n_prod, grid_n, grid_n))
+    for ci, c in enumerate(chans):
+        for t0 in range(0, Tn, time_chunk):
+            x = unpack_4bit(codes[t0:t0 + time_chunk, c])            # [t, A, P]
+            y = calibrate(x, np.asarray(gains)[c])
+            G = grid(y, W, grid_n, n_pol)
+            E = sky_transform(G)
+            out[ci] += integrate(E)
+    return out
+
+
+# ----------------------------------------------------------------------------- FX form
+
+def footprint(pos, taps, grid_n: int, n_pol: int, jones: bool = False) -> np.ndarray:
+    """Each antenna's kernel placed on the grid: complex [A, P_out, P_in, N, N]."""
+    T = _full_taps(taps, n_pol, jones)
+    A, Po, Pi, K, _ = T.shape
+    N = grid_n
+    anc = anchors(pos)
+    h = K // 2
+    F = np.zeros((A, Po, Pi, N, N), dtype=np.complex128)
+    for a in range(A):
+        for iy in range(K):
+            for ix in range(K):
+                F[a, :, :, (anc[a, 1] + iy - h) % N, (anc[a, 0] + ix - h) % N] += T[a, :, :, iy, ix]
+    return F
+
+
+def fx_image(codes, gains, pos, taps, grid_n: int, n_pol: int, jones: bool = False,
+             channel: int = 0) -> np.ndarray:
+    """Brute-force FX route to the same image (Eqs. visDef, Bdef, RBeamEq / m1).
+
+    1. visibilities v_ab^{qq'} = sum_t y_aq conj(y_bq') for every antenna pair,
+       autocorrelations included (Eq. visDef);
+    2. the uv response of a pair is the correlation of the two antennas'
+       kernels (Eq. Bdef): with kernel a placed at anchor_a and kernel b at
+       anchor_b, B_ab(u) = sum_{d,d'} T_a[d] conj(T_b[d']) at the baseline
+       u = anchor_a + d - anchor_b - d' (mod N);
+    3. V_pp'(u) = sum_{a,b,q,q'} v_ab^{qq'} B_{a p q, b p' q'}(u)  (gridding, Eq. RBeamEq step 2);
+    4. I_pp'(k) = sum_u V_pp'(u) exp(+2 pi i k.u / N) as an explicit DFT-matrix
+       product (Eq. RBeamEq step 3).
+    Returns float64 [n_prod, N, N].  Cost O(A^2 K^4 P^4): small arrays only.
+    """
+    codes = np.asarray(codes)
+    y = calibrate(unpack_4bit(codes[:, channel]), np.asarray(gains)[channel])   # [T, A, Pi]
+    Tn, A, Pi = y.shape
+    N = grid_n
+    Tf = _full_taps(taps, n_pol, jones)                                          # [A, Po, Pi, K, K]
+    Po, K = Tf.shape[1], Tf.shape[3]
+    anc = anchors(pos)
+    vis = np.einsum("taq,tbs->aqbs", y, np.conj(y))                              # [A, Pi, A, Pi]
+    # w[a, b, p, p'] for one kernel-cell pair (d, d'):
+    #   sum_{q,q'} v_ab^{qq'} T_a[p, q, d] conj(T_b[p', q', d'])
+    dA = (anc[:, None, :] - anc[None, :, :])                                     # [A, A, 2] (x, y)
+    V = np.zeros((Po, Po, N * N), dtype=np.complex128)
+    for dy in range(K):
+        for dx in range(K):
+            Ta = Tf[:, :, :, dy, dx]                                              # [A, Po, Pi]
+            for ey in range(K):
+                for ex in range(K):
+                    Tb = np.conj(Tf[:, :, :, ey, ex])                             # [A, Po, Pi]
+                    w = np.einsum("aqbs,apq,brs->prab", vis, Ta, Tb)              # [Po, Po, A, A]
+                    uy = (dA[:, :, 1] + dy - ey) % N
+                    ux = (dA[:, :, 0] + dx - ex) % N
+                    idx = (uy * N + ux).ravel()
+                    for p in range(Po):
+                        for r in range(Po):
+                            np.add.at(V[p, r], idx, w[p, r].ravel())
+    V = V.reshape(Po, Po, N, N)
+    k = np.arange(N)
+    D = np.exp(2j * np.pi * np.outer(k, k) / N)                                  # D[k, u]
+    I = np.einsum("ky,pqyx,jx->pqkj", D, V, D)
+    if Po == 1:
+        return I[0, 0].real[None]
+    return np.stack([I[0, 0].real, I[1, 1].real, I[0, 1].real, I[0, 1].imag])
+
+
+# ----------------------------------------------------------------------------- F-stage
+
+def pfb_window(n_taps: int, frame: int) -> np.ndarray:
+    """Polyphase prototype filter h[n], n in [0, n_taps*M): a sinc one channel wide
+    times a Hann window over the whole filter (the paper names polyphase filters
+    for the Eq. FFTofE channeliser but gives no design; this is the reading).
+
+        h[n] = sinc((n - (P M - 1)/2) / M) * (0.5 - 0.5 cos(2 pi n / (P M - 1)))
+    """
+    L = n_taps * frame
+    n = np.arange(L, dtype=np.float64)
+    return np.sinc((n - (L - 1) / 2.0) / frame) * (0.5 - 0.5 * np.cos(2 * np.pi * n / (L - 1)))
+
+
+def pfb_spectra(adc, h, n_taps: int, frame: int) -> np.ndarray:
+    """Eq. FFTofE via a polyphase filter bank, per antenna-pol stream.
+
+    ``adc`` real [..., S]; frame count F = S // M - n_taps + 1.  For frame m
+    and phase j in [0, M):  s_m[j] = sum_{p<n_taps} h[p M + j] adc[(m + p) M + j];
+    then X_m[k] = sum_j s_m[j] exp(-2 pi i j k / M) for k in [0, M/2)
+    (the Nyquist bin is dropped).  Returns complex [..., F, M/2].
+    """
+    x = np.asarray(adc, dtype=np.float64)
+    M = frame
+    S = x.shape[-1]
+    F = S // M - n_taps + 1
+    if F <= 0:
+        raise ValueError("stream shorter than one filter length")
+    hh = np.asarray(h, dtype=np.float64).reshape(n_taps, M)
+    blocks = x[..., : (F + n_taps - 1) * M].reshape(x.shape[:-1] + (F + n_taps - 1, M))
+    s = np.zeros(x.shape[:-1] + (F, M))
+    for p in range(n_taps):
+        s += hh[p] * blocks[..., p:p + F, :]
+    X = np.fft.fft(s, axis=-1)
+    return X[..., : M // 2]
+
+
+def quantise_4bit(X, scale: float):
+    """Requantise channelised voltages to 4+4 bits: clamp(rint(X * scale), -7, 7)
+    per component, rounding half to even.  Returns (re, im) int64 arrays."""
+    z = np.asarray(X, dtype=np.complex128) * scale
+    re = np.clip(np.rint(z.real), -7, 7).astype(np.int64)
+    im = np.clip(np.rint(z.imag), -7, 7).astype(np.int64)
+    return re, im
+
+
+def ambiguous_codes(X, scale: float, delta: float) -> np.ndarray:
+    """Mask of components whose scaled value lies within ``delta`` of a rounding
+    boundary n + 1/2 that changes the clipped code (n + 1/2 in [-6.5, 6.5]).
+    There an FP32 and an FP64 evaluation may legitimately round apart."""
+    z = np.asarray(X, dtype=np.complex128) * scale
+
+    def near(v):
+        b = np.floor(v) + 0.5
+        return (np.abs(v - b) < delta) & (np.abs(b) <= 6.5)
+    return near(z.real) | near(z.imag)
+
+
+def channelise(adc, h, n_taps: int, frame: int, scale: float):
+    """F-stage as the correlator sees it: ADC ``int8 [A, P, S]`` -> 4-bit codes
+    ``uint8 [F, C, A, P]`` with C = M/2, plus the unquantised spectra."""
+    X = pfb_spectra(adc, h, n_taps, frame)                    # [A, P, F, C]
+    re, im = quantise_4bit(X, scale)
+    codes = (((re & 0xF) << 4) | (im & 0xF)).astype(np.uint8)
+    return np.transpose(codes, (2, 3, 0, 1)).copy(), np.transpose(X, (2, 3, 0, 1)).copy()
+
+
+# ----------------------------------------------------------------------------- metric
+
+def max_norm_err(img, ref) -> np.ndarray:
+    """Max-normalised error per (channel, product): max|img - ref| / max|ref|.
+
+    For the cross products (Re XY, Im XY) the denominator is max(max XX, max YY).
+    ``img``/``ref`` are [C, n_prod, N, N].
+    """
+    img = np.asarray(img, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    err = np.abs(img - ref).reshape(img.shape[0], img.shape[1], -1).max(axis=-1)
+    den = np.abs(ref).reshape(ref.shape[0], ref.shape[1], -1).max(axis=-1)
+    if ref.shape[1] == 4:
+        d = np.maximum(den[:, 0], den[:, 1])
+        den = np.stack([den[:, 0], den[:, 1], d, d], axis=1)
+    return err / np.maximum(den, 1e-300)
