@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Throughput of the MOFF imaging hot path on one GB300 (or N replicas).
+
+Workload (one step = one integration): 1024 dual-pol antennas hex-packed at
+1.5 lambda with 5 % jitter; real 8-bit ADC streams (noise sigma 20 plus three
+narrow-band sky sources) channelised by an 8-tap, 2048-sample polyphase
+filter bank into 1024 channels and requantised to 4+4 bits; each channel
+gridded on a 128x128 grid through 7x7 complex per-antenna kernels,
+transformed, squared and summed over 1000 samples into XX, YY, Re XY, Im XY.
+All arithmetic FP32 (FP64 cross-chunk sums).  A step processes
+1000 x 1024 = 1,024,000 channel-snapshots; its 4.2 GB of ADC input is far
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WL = dict(n_ant=1024, n_pol=2, n_chan=1024, grid_n=128, ksize=7, ntaps=8, frames=1000)
+SEED = 8123669 + 1
+METRIC = "MOFF channel-snapshots/s"
+UNIT = "channel-snapshots/s"
+WORKLOAD_NAME = ("dual-pol 1024-antenna hex core (1.5 lambda, 5% jitter), 8-bit ADC -> 8-tap x 2048 PFB "
+                 "-> 1024 channels 4+4-bit, 128x128 grid, 7x7 complex kernels, XX/YY/XY, 1000 samples per step")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--frames", type=int, default=WL["frames"], help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- algorithmic work
+
+def flops_per_snapshot(kind, A=WL["n_ant"], P=WL["n_pol"], N=WL["grid_n"], K=WL["ksize"]):
+    """Algorithmic FP32 flops per channel-snapshot of each kernel (5 N log2 N per
+    N-point transform, 8 per complex multiply-add, 6 per complex multiply)."""
+    fft_axis = P * N * 5 * N * math.log2(N)
+    if kind == 1:      # calibrate + grid + row transforms
+        return 6 * A * P + 8 * A * P * K * K + fft_axis
+    if kind == 2:      # column transforms + square-and-integrate
+        return fft_axis + (16 if P == 2 else 4) * N * N
+    raise ValueError(kind)
+
+
+def pfb_flops_per_stream_frame(C=WL["n_chan"], ntaps=WL["ntaps"]):
+    M = 2 * C
+    return 2 * ntaps * M + 5 * C * math.log2(C) + 10 * C
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2])); power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) sample
+
+def oracle_step(n_frames=2, seed=SEED):
+    """The FP64 oracle on a bounded sample of the workload: the whole array's
+    F-stage for ``n_frames`` frames, then every channel imaged for those frames.
+    Returns (channel-snapshots, seconds)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    cfg = synth.config_dualpol()
+    A, P, C, N, ntaps = WL["n_ant"], WL["n_pol"], WL["n_chan"], WL["grid_n"], WL["ntaps"]
+    M = 2 * C
+    rng = np.random.default_rng(seed)
+    adc = synth.adc_stream(rng, A, P, (n_frames + ntaps - 1) * M, sigma=20.0,
+                           tones=[(100.0 / M, 12.0), (600.0 / M, 8.0)])
+    gains = cfg["gains"]
+    W = oracle.grid_matrix(cfg["pos"], cfg["taps"], N, P)      # plan set-up, not timed
+    t0 = time.perf_counter()
+    h = oracle.pfb_window(ntaps, M)
+    X = oracle.pfb_spectra(adc, h, ntaps, M)
+    scale = 2.0 / np.std(np.concatenate([X.real.ravel(), X.imag.ravel()]))
+    codes, _ = oracle.channelise(adc, h, ntaps, M, scale)
+    img = np.zeros((4, N, N))
+    for c in range(C):
+        y = oracle.calibrate(oracle.unpack_4bit(codes[:, c]), gains[c])
+        img += oracle.integrate(oracle.sky_transform(oracle.grid(y, W, N, P)))
+    dt = time.perf_counter() - t0
+    return n_frames * C, dt
+
+
+def cpu_baseline_subprocess():
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"], env=env, capture_output=True,
+                       text=True, timeout=900)
+    for line in r.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    return {"error": (r.stderr or r.stdout)[-300:]}
+
+
+def run_cpu_sample():
+    units, dt = oracle_step(n_frames=6)
+    print(json.dumps({"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
+                      "sample": f"whole-array F-stage for 6 frames + all {WL['n_chan']} channels imaged "
+                                f"({units} channel-snapshots), FP64 numpy/scipy, 1 thread"}))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    for _ in range(args.warmup):
+        oracle_step(n_frames=1)
+    units = 0
+    secs = 0.0
+    for _ in range(args.steps):
+        u, dt = oracle_step()
+        units += u
+        secs += dt
+    v = units / secs
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "sample_frames_per_step": 2, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step: whole-array F-stage for 2 frames + all 1024 channels imaged"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def traffic_for(kernel_key, src_files):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    h = hashlib.sha1()
+    for f in src_files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if rec.get("source_sha1") != h.hexdigest():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_0812_3669_gb300 as moff
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    if rank == 0 or world > 1:
+        moff.build()
+    barrier()
+
+    A, P, C, N, K, ntaps, F = (WL["n_ant"], WL["n_pol"], WL["n_chan"], WL["grid_n"], WL["ksize"], WL["ntaps"],
+                               args.frames)
+    M = 2 * C
+    S = (F + ntaps - 1) * M
+    cfg = synth.config_dualpol()
+    pos, taps, gains = cfg["pos"], cfg["taps"], cfg["gains"]
+    adc = synth.device_adc(SEED + 1000 * rank, pos, P, S, M, N)
+
+    plan = moff.Plan(pos, taps, N, C, P, fstage=True)
+    plan.set_gains(gains)
+    # requantisation gain from a short calibration block: noise sigma ~ 2 codes per component
+    calib = adc[:, :, : (ntaps + 3) * M].contiguous()
+    plan.set_fstage(ntaps, None, 1.0)
+    spec = plan.channelise(calib, kind=1)
+    scale = float(2.0 / np.std(np.concatenate([spec.real.ravel(), spec.imag.ravel()])))
+    plan.set_fstage(ntaps, None, scale)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.submit_adc(adc)
+    plan.sync()
+    plan.reset()
+    plan.set_timing(True)
+
+    gpu_idx = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis and vis.split(",")[local].strip().isdigit():
+        gpu_idx = int(vis.split(",")[local])
+    clocks = ClockSampler(gpu_idx)
+
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.submit_adc(adc)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+
+    kern = {}
+    for kind, name in moff.KERNEL_KINDS.items():
+        tot, n = plan.timing(kind)
+        kern[name] = {"ms_total": tot, "launches": n}
+    plan.set_timing(False)
+    img, nsamp = plan.read_image(reset=True)
+    assert nsamp == args.steps * F and np.isfinite(img).all()
+
+    units = args.steps * F * C * world
+    value = units / (ms_max / 1000.0)
+    snaps = args.steps * F * C
+    total_kernel_ms = sum(v["ms_total"] for v in kern.values())
+    flops = {
+        "grid_rows": snaps * flops_per_snapshot(1),
+        "cols_integrate": snaps * flops_per_snapshot(2),
+        "pfb_fstage": args.steps * F * A * P * pfb_flops_per_stream_frame(),
+    }
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # FP32 FMA TFLOP/s at max SM clock
+    for name, v in kern.items():
+        v["share"] = v["ms_total"] / total_kernel_ms if total_kernel_ms else None
+        v["tflops"] = flops[name] / (v["ms_total"] / 1e3) / 1e12 if v["ms_total"] else None
+    dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    src = {"grid_rows": ["paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
+           "cols_integrate": ["paper_0812_3669_gb300/csrc/moff_image_kernels.cuh",
+                              "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
+           "pfb_fstage": ["paper_0812_3669_gb300/csrc/moff_fstage.cu", "paper_0812_3669_gb300/csrc/moff_fft.cuh"]}[dom]
+    launches = kern[dom]["launches"]
+    achieved = kern[dom]["tflops"]
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak if achieved else None,
+                "peak_basis": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (of derived peak)",
+                "flops_per_launch": flops[dom] / max(launches, 1),
+                "ms_per_launch": kern[dom]["ms_total"] / max(launches, 1),
+                "traffic": traffic_for(dom + "@dualpol1024", src)}
+    gpu_launches = sum(v["launches"] for v in kern.values())
+
+    # ---------------------------------------------------------------- end to end through host buffers
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        adc_h = torch.empty(adc.shape, dtype=torch.int8, pin_memory=True)
+        adc_h.copy_(adc)
+        del adc
+        torch.cuda.empty_cache()
+        out_h = torch.empty((C, 4, N, N), dtype=torch.float32, pin_memory=True)
+        plan.submit_adc(adc_h)                 # warm the staging buffers
+        plan.read_image(out=out_h, reset=True)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.submit_adc(adc_h)
+            plan.read_image(out=out_h, reset=True)
+        dt = time.perf_counter() - t0
+        dt_t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
+        dt = float(dt_t.item())
+        e2e = {"value": args.e2e_steps * F * C * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(adc_h.numel()), "d2h_bytes_per_step": int(out_h.numel() * 4),
+               "steps": args.e2e_steps, "api": "moff_submit_adc(host pinned ADC) + moff_read_image(host)"}
+    plan.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_subprocess()
+
+    if rank == 0:
+        fx_eq = value * A * (A - 1) / 2 * 4
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "antennas": A, "pols": P, "channels": C, "grid_n": N,
+                       "kernel": K, "pfb_taps": ntaps, "samples_per_step": F, "channel_snapshots_per_step": F * C,
+                       "l2": "inputs larger than L2 (4.2 GB of ADC per step), no flush",
+                       "parallelism": f"{world} independent replica(s), one integration each"},
+            "fx_equiv_tcmac_per_s": fx_eq / 1e12,
+            "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches, "clocks": clk,
+            "e2e": e2e, "cpu_baseline": cpu,
+        }), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.cpu_sample:
+        run_cpu_sample()
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

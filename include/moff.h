@@ -1,0 +1,210 @@
+/*
+ * moff.h -- C ABI of the GB300 MOFF imaging library (libmoff.so).
+ *
+ * The library computes, per frequency channel and time sample, the MOFF
+ * correlator image of Morales (arXiv 0812.3669), Sec. 4, Eq. m6:
+ *
+ *     I'(theta) = < | F^T(theta, r) W^T(r, a) N~(a, a) E'(a) |^2 >_t
+ *
+ * step 1 (N~):  every 4-bit complex antenna voltage E'(a) is multiplied by a
+ *               per (channel, antenna, pol) complex weight -- the noise
+ *               weighting of Eq. m4 with the gain calibration folded in;
+ * step 2 (W^T): each weighted voltage is scattered onto a regular N x N
+ *               aperture grid through that antenna's kernel (its holographic
+ *               aperture map, Sec. 3);
+ * step 3 (F^T): the gridded field is transformed to the sky with the
+ *               unnormalised 2D transform E(k) = sum_r G(r) exp(+2 pi i k.r/N);
+ * step 4:       |E|^2 (and, for two pols, the cross products) is summed over
+ *               time.
+ * An optional F-stage (Sec. 2, Eq. FFTofE; "often implemented as polyphase
+ * filters") turns real 8-bit ADC streams into the 4-bit channelised voltages.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Antenna positions are (x, y) in grid-cell units.  A kernel is centred on
+ *    the antenna's anchor cell (floor(x + 0.5), floor(y + 0.5)) and the grid
+ *    wraps circularly modulo N.
+ *  - Complex numbers are interleaved (re, im) float32 pairs.
+ *  - Voltage bytes hold a 4-bit two's-complement real part in the high nibble
+ *    and the imaginary part in the low nibble.  Layout [T][C][A][P].
+ *  - Images are SUMS over time (the paper's average = sum / n_samples) in
+ *    natural DFT order, row-major (ky, kx), not shifted.  Single pol: one
+ *    product |E|^2.  Two pols: four products XX = |Ex|^2, YY = |Ey|^2,
+ *    Re(Ex Ey*), Im(Ex Ey*).  Autocorrelation terms are included.
+ *  - All pointer arguments flagged "on_device" are device pointers of the
+ *    current CUDA device when the flag is 1, host pointers otherwise.
+ *  - Every call returns a moff_status.  On error nothing aborts, the plan is
+ *    left as it was, and moff_last_error() returns a message (thread-local).
+ *  - A plan is not thread-safe: one host thread at a time may use it.
+ *  - All work is enqueued on the plan's CUDA stream; host-pointer inputs are
+ *    fully copied before the call returns, so the caller may reuse them.
+ */
+#ifndef MOFF_H
+#define MOFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct moff_plan moff_plan; /* opaque, owned by the library */
+
+typedef enum {
+    MOFF_OK = 0,
+    MOFF_EINVAL = -1,    /* bad argument (null pointer, size out of range, wrong state of flags) */
+    MOFF_ENOMEM = -2,    /* a device or pinned-host allocation failed */
+    MOFF_ECUDA = -3,     /* a CUDA call or kernel launch failed */
+    MOFF_ESTATE = -4,    /* call not valid in the plan's current state */
+    MOFF_ETIMEDOUT = -5, /* a bounded wait ran out before the GPU finished */
+    MOFF_EBUSY = -6      /* resource temporarily unavailable */
+} moff_status;
+
+/* Plan flags. */
+enum {
+    MOFF_PREC_FP32 = 0u,   /* all arithmetic in FP32, cross-block sums in FP64 */
+    MOFF_FSTAGE = 1u << 1, /* enable the polyphase F-stage (moff_submit_adc, moff_channelise) */
+    MOFF_JONES = 1u << 2   /* kernels are full 2x2 Jones matrices (n_pol must be 2) */
+};
+
+/*
+ * moff_plan_create -- build a plan for one array (Sec. 4: the antenna layout,
+ * the kernels W and the grid of Eq. m6 step 2 are fixed for an observation).
+ *
+ *   out       receives the new plan (set to NULL on error).
+ *   n_ant     number of antennas A, 1 <= A <= 65536.
+ *   pos       host float64 [A][2], (x, y) in grid-cell units.
+ *   ksize     kernel side K, odd, 1 <= K <= min(N, 15).
+ *   taps      host float32 complex kernels, copied:
+ *               without MOFF_JONES: [A][P][K][K][2]       (one kernel per pol)
+ *               with    MOFF_JONES: [A][2][2][K][K][2]    ([a][p_out][p_in][dy][dx])
+ *   grid_n    grid side N: 32, 64, 128, 256 or 512.
+ *   n_chan    number of channels C >= 1 (with MOFF_FSTAGE: a power of two,
+ *             32 <= C <= 2048; the F-stage frame is M = 2C real samples).
+ *   n_pol     P = 1 or 2 (input pols = output pols).
+ *   flags     MOFF_* bits above.
+ *   cuda_stream  cudaStream_t to run on (cudaStreamLegacy, 0x1, selects the
+ *             legacy default stream), or NULL for a stream the plan creates.
+ * The plan owns device memory for kernels, gains (initialised to 1), FP64
+ * accumulators [C][n_prod][N][N] and scratch.  Errors: MOFF_EINVAL for any
+ * argument out of range, MOFF_ENOMEM, MOFF_ECUDA.
+ */
+moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int ksize,
+                             const float *taps, int grid_n, int n_chan, int n_pol,
+                             unsigned flags, void *cuda_stream);
+
+/*
+ * moff_set_gains -- the complex weights N~ of Eq. m6 step 1 (Sec. 4: one over
+ * the antenna noise, with any calibration folded in; Sec. 6 feeds
+ * calibration back through here).  gains: float32 complex [C][A][P][2],
+ * copied (host, or device when on_device = 1).  Takes effect for blocks
+ * submitted afterwards.
+ */
+moff_status moff_set_gains(moff_plan *plan, const float *gains, int on_device);
+
+/*
+ * moff_set_fstage -- configure the polyphase F-stage (Sec. 2, Eq. FFTofE).
+ *   n_taps  filter length in frames, 1 <= n_taps <= 16.
+ *   coeffs  host float32 [n_taps * M] prototype filter h[n], or NULL for the
+ *           default sinc(x / M) * Hann window over n_taps * M samples.
+ *   scale   requantisation scale: code = clamp(rint(X * scale), -7, 7) per
+ *           component, round half to even.
+ * Requires MOFF_FSTAGE.  Default after plan creation: 8 taps, default
+ * window, scale 1.
+ */
+moff_status moff_set_fstage(moff_plan *plan, int n_taps, const float *coeffs, float scale);
+
+/*
+ * moff_submit -- add a block of 4-bit voltages to the integration (Eq. m6,
+ * steps 1-4, summed over the block's samples).
+ *   volt    uint8 [n_time][C][A][P].
+ *   n_time  samples in the block, >= 1.
+ * With on_device = 0 the block is copied to the device before the call
+ * returns.  With on_device = 1 the caller keeps the buffer alive and
+ * unmodified until moff_sync or moff_read_image returns.
+ */
+moff_status moff_submit(moff_plan *plan, const uint8_t *volt, int n_time, int on_device);
+
+/*
+ * moff_submit_adc -- F-stage then imaging for a block of real ADC samples.
+ *   adc     int8 [A][P][n_samp], n_samp a multiple of M = 2C with
+ *           n_samp / M >= n_taps.  The block yields F = n_samp/M - n_taps + 1
+ *           frames (time samples); blocks are independent (no history is
+ *           carried between calls).
+ * Requires MOFF_FSTAGE.  Buffer ownership as for moff_submit.
+ */
+moff_status moff_submit_adc(moff_plan *plan, const int8_t *adc, long long n_samp, int on_device);
+
+/*
+ * moff_channelise -- run only the F-stage (Sec. 2, Eq. FFTofE) on one block.
+ *   out_kind 0: out = uint8 [F][C][A][P] requantised 4-bit codes.
+ *   out_kind 1: out = float32 complex [F][C][A][P][2] unquantised spectra
+ *               X_m[k] = sum_j s_m[j] exp(-2 pi i j k / M).
+ * Output goes to host memory (out_on_device = 0) or device memory (1).
+ * Synchronous: returns when out is written.  Requires MOFF_FSTAGE.
+ */
+moff_status moff_channelise(moff_plan *plan, const int8_t *adc, long long n_samp, int in_on_device,
+                            void *out, int out_kind, int out_on_device);
+
+/*
+ * moff_grid_snapshot -- gridded field of one time sample (Eq. m6 steps 1-2),
+ * for inspection and testing.
+ *   volt  uint8 [C][A][P] of a single sample (host or device per on_device).
+ *   chan  channel index whose gains apply.
+ *   out   host float32 complex [P][N][N][2].
+ * Synchronous.  Does not touch the accumulators.
+ */
+moff_status moff_grid_snapshot(moff_plan *plan, const uint8_t *volt, int on_device, int chan,
+                               float *out);
+
+/*
+ * moff_read_image -- the integrated image (Eq. m6, step 4).
+ *   out        float32 [C][n_prod][N][N]; host (out_on_device = 0) or device.
+ *   n_samples  if not NULL, receives the number of time samples summed.
+ *   reset      1: zero the accumulators after reading.
+ *   timeout_ms bounded wait for outstanding work (< 0: wait without limit);
+ *              on expiry MOFF_ETIMEDOUT and nothing is read or reset.
+ */
+moff_status moff_read_image(moff_plan *plan, float *out, long long *n_samples, int reset,
+                            int timeout_ms, int out_on_device);
+
+/* moff_sync -- bounded wait for all work enqueued on the plan (MOFF_ETIMEDOUT on expiry). */
+moff_status moff_sync(moff_plan *plan, int timeout_ms);
+
+/* moff_reset -- zero the accumulators and the sample count (enqueued on the plan's stream). */
+moff_status moff_reset(moff_plan *plan);
+
+/* moff_plan_info -- sizes chosen at plan creation (any pointer may be NULL). */
+moff_status moff_plan_info(const moff_plan *plan, int *n_prod, int *rows_per_stripe,
+                           int *time_chunk, int *chan_chunk, long long *device_bytes);
+
+/*
+ * moff_set_timing -- when on (1), every kernel the plan launches is bracketed
+ * by a pair of CUDA events on the plan's stream, so its device time can be
+ * read with moff_timing.  Off (0) by default; switching on clears old records.
+ */
+moff_status moff_set_timing(moff_plan *plan, int on);
+
+/*
+ * moff_timing -- device time of the plan's kernels since timing was switched
+ * on (or last reset), for one kernel kind:
+ *   0  F-stage polyphase filter bank,
+ *   1  calibrate + grid + row transform (Eq. m6 steps 1-2, step 3 first axis),
+ *   2  column transform + square-and-integrate (step 3 second axis, step 4).
+ * Waits for the recorded work.  total_ms / launches may be NULL.  reset = 1
+ * drops the records of every kind after reading.
+ */
+moff_status moff_timing(moff_plan *plan, int kind, double *total_ms, long long *launches, int reset);
+
+/* moff_plan_destroy -- wait for the plan's work, free everything.  NULL is a no-op. */
+moff_status moff_plan_destroy(moff_plan *plan);
+
+/* moff_last_error -- message of the last failed call on this host thread ("" if none). */
+const char *moff_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOFF_H */

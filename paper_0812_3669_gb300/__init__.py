@@ -1,0 +1,320 @@
+"""GB300-native MOFF imaging library -- Python binding of ``libmoff.so``.
+
+Morales (arXiv 0812.3669), Sec. 4, Eq. m6: per channel and time sample,
+weight the 4-bit antenna voltages, grid them through each antenna's kernel,
+transform the grid to the sky and sum |E|^2 (and the cross-pol products).
+All of it runs in the CUDA kernels of ``libmoff.so`` (csrc/); this module
+only marshals arguments through ctypes.  Functions carry the C names of
+``include/moff.h``; :class:`Plan` wraps them for convenience.
+
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory, passed with ``on_device = 1``).  Complex inputs are converted to
+interleaved float32 pairs, the ABI's format.  If the library is not built,
+every call raises :class:`MoffError` -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+__all__ = [
+    "MoffError", "lib", "build", "LIB_PATH", "MOFF_FSTAGE", "MOFF_JONES", "MOFF_PREC_FP32",
+    "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
+    "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
+    "moff_plan_info", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
+    "Plan", "header_symbols", "KERNEL_KINDS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmoff.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "moff.h")
+
+MOFF_PREC_FP32 = 0
+MOFF_FSTAGE = 1 << 1
+MOFF_JONES = 1 << 2
+
+KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate"}
+
+STATUS = {0: "MOFF_OK", -1: "MOFF_EINVAL", -2: "MOFF_ENOMEM", -3: "MOFF_ECUDA",
+          -4: "MOFF_ESTATE", -5: "MOFF_ETIMEDOUT", -6: "MOFF_EBUSY"}
+
+
+class MoffError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp, _i, _u, _ll, _f = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_longlong, ctypes.c_float
+_SIGS = {
+    "moff_plan_create": [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _i, _i, _i, _u, _vp],
+    "moff_set_gains": [_vp, _vp, _i],
+    "moff_set_fstage": [_vp, _i, _vp, _f],
+    "moff_submit": [_vp, _vp, _i, _i],
+    "moff_submit_adc": [_vp, _vp, _ll, _i],
+    "moff_channelise": [_vp, _vp, _ll, _i, _vp, _i, _i],
+    "moff_grid_snapshot": [_vp, _vp, _i, _i, _vp],
+    "moff_read_image": [_vp, _vp, ctypes.POINTER(_ll), _i, _i, _i],
+    "moff_sync": [_vp, _i],
+    "moff_reset": [_vp],
+    "moff_plan_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                       ctypes.POINTER(_ll)],
+    "moff_plan_destroy": [_vp],
+    "moff_set_timing": [_vp, _i],
+    "moff_timing": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
+}
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    """Compile libmoff.so in-tree (nvcc, sm_103a)."""
+    from . import buildlib as _b
+    return _b.build(verbose=verbose, force=force)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libmoff.so (raises MoffError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MoffError(-4, f"{LIB_PATH} is not built; call paper_0812_3669_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.moff_last_error.argtypes = []
+        L.moff_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions declared in include/moff.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:moff_status|const char \*)\s*\n?\s*(moff_\w+)\s*\(", txt, re.M)))
+
+
+def moff_last_error() -> str:
+    return lib().moff_last_error().decode()
+
+
+def _check(status):
+    if status != 0:
+        raise MoffError(status, moff_last_error())
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _addr(x):
+    """(address, on_device) of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda)
+    if not (isinstance(x, np.ndarray) and x.flags.c_contiguous):
+        raise ValueError("array must be a C-contiguous numpy array")
+    return ctypes.c_void_p(x.ctypes.data), 0
+
+
+def _f32_interleaved(z):
+    """complex host array -> contiguous float32 (re, im) pairs."""
+    z = np.ascontiguousarray(np.asarray(z), dtype=np.complex64)
+    return z.view(np.float32)
+
+
+def _torch_f32_interleaved(t):
+    import torch
+    if t.is_complex():
+        t = torch.view_as_real(t.to(torch.complex64).contiguous())
+    return t.contiguous()
+
+
+# ----------------------------------------------------------------- C-named functions
+
+def moff_plan_create(pos, taps, grid_n, n_chan, n_pol, flags=0, cuda_stream=None):
+    """Create a plan; ``pos`` float64 [A][2], ``taps`` complex kernels (see moff.h)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    taps = np.asarray(taps)
+    ksize = int(taps.shape[-1])
+    t32 = _f32_interleaved(taps)
+    out = ctypes.c_void_p()
+    st = ctypes.c_void_p(int(cuda_stream)) if cuda_stream else None
+    _check(lib().moff_plan_create(ctypes.byref(out), int(pos.shape[0]), pos.ctypes.data, ksize, t32.ctypes.data,
+                                  int(grid_n), int(n_chan), int(n_pol), int(flags), st))
+    return out
+
+
+def moff_set_gains(plan, gains):
+    if _is_torch(gains):
+        g = _torch_f32_interleaved(gains)
+        _check(lib().moff_set_gains(plan, ctypes.c_void_p(g.data_ptr()), int(g.is_cuda)))
+    else:
+        g = _f32_interleaved(gains)
+        _check(lib().moff_set_gains(plan, g.ctypes.data, 0))
+
+
+def moff_set_fstage(plan, n_taps, coeffs=None, scale=1.0):
+    c = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float32)
+    _check(lib().moff_set_fstage(plan, int(n_taps), None if c is None else c.ctypes.data, float(scale)))
+
+
+def moff_submit(plan, volt):
+    """``volt`` uint8 [T][C][A][P] (numpy, or a CUDA uint8 tensor)."""
+    p, dev = _addr(volt)
+    _check(lib().moff_submit(plan, p, int(volt.shape[0]), dev))
+
+
+def moff_submit_adc(plan, adc):
+    """``adc`` int8 [A][P][S]."""
+    p, dev = _addr(adc)
+    _check(lib().moff_submit_adc(plan, p, int(adc.shape[-1]), dev))
+
+
+def moff_channelise(plan, adc, out, out_kind=0):
+    pi, din = _addr(adc)
+    po, dout = _addr(out)
+    _check(lib().moff_channelise(plan, pi, int(adc.shape[-1]), din, po, int(out_kind), dout))
+
+
+def moff_grid_snapshot(plan, volt, chan, out):
+    p, dev = _addr(volt)
+    o, _ = _addr(out)
+    _check(lib().moff_grid_snapshot(plan, p, dev, int(chan), o))
+
+
+def moff_read_image(plan, out, reset=0, timeout_ms=-1):
+    o, dev = _addr(out)
+    n = ctypes.c_longlong(0)
+    _check(lib().moff_read_image(plan, o, ctypes.byref(n), int(reset), int(timeout_ms), dev))
+    return n.value
+
+
+def moff_sync(plan, timeout_ms=-1):
+    _check(lib().moff_sync(plan, int(timeout_ms)))
+
+
+def moff_reset(plan):
+    _check(lib().moff_reset(plan))
+
+
+def moff_plan_info(plan):
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    e = ctypes.c_longlong()
+    _check(lib().moff_plan_info(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
+                                ctypes.byref(e)))
+    return dict(n_prod=a.value, rows_per_stripe=b.value, time_chunk=c.value, chan_chunk=d.value,
+                device_bytes=e.value)
+
+
+def moff_set_timing(plan, on):
+    _check(lib().moff_set_timing(plan, int(on)))
+
+
+def moff_timing(plan, kind, reset=0):
+    """(total device ms, launch count) of one kernel kind since timing was switched on."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _check(lib().moff_timing(plan, int(kind), ctypes.byref(ms), ctypes.byref(n), int(reset)))
+    return ms.value, n.value
+
+
+def moff_plan_destroy(plan):
+    _check(lib().moff_plan_destroy(plan))
+
+
+# ----------------------------------------------------------------- convenience
+
+class Plan:
+    """One array's imaging plan (owns a ``moff_plan``)."""
+
+    def __init__(self, pos, taps, grid_n, n_chan, n_pol, jones=False, fstage=False, stream=None):
+        flags = (MOFF_JONES if jones else 0) | (MOFF_FSTAGE if fstage else 0)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    # torch's default stream has handle 0, which the ABI reads as
+                    # "make a private stream"; pass cudaStreamLegacy (0x1) so work
+                    # is ordered with tensors produced on that stream.
+                    stream = torch.cuda.current_stream().cuda_stream or 1
+            except ImportError:
+                stream = None
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream or 1
+        self.A = int(np.asarray(pos).shape[0])
+        self.N, self.C, self.P = int(grid_n), int(n_chan), int(n_pol)
+        self.n_prod = 1 if n_pol == 1 else 4
+        self.n_taps = 8
+        self.handle = moff_plan_create(pos, taps, grid_n, n_chan, n_pol, flags, stream)
+
+    def set_gains(self, gains):
+        moff_set_gains(self.handle, gains)
+
+    def set_fstage(self, n_taps=8, coeffs=None, scale=1.0):
+        moff_set_fstage(self.handle, n_taps, coeffs, scale)
+        self.n_taps = int(n_taps)
+
+    def submit(self, volt):
+        moff_submit(self.handle, volt)
+
+    def submit_adc(self, adc):
+        moff_submit_adc(self.handle, adc)
+
+    def channelise(self, adc, kind=0, out=None):
+        if out is None:
+            F = adc.shape[-1] // (2 * self.C) - self.n_taps + 1
+            shape = (F, self.C, self.A, self.P)
+            out = np.empty(shape, dtype=np.uint8) if kind == 0 else np.empty(shape, dtype=np.complex64)
+        moff_channelise(self.handle, adc, out, kind)
+        return out
+
+    def grid_snapshot(self, volt, chan):
+        out = np.empty((self.P, self.N, self.N), dtype=np.complex64)
+        moff_grid_snapshot(self.handle, volt, chan, out)
+        return out
+
+    def read_image(self, reset=False, timeout_ms=-1, out=None):
+        if out is None:
+            out = np.empty((self.C, self.n_prod, self.N, self.N), dtype=np.float32)
+        n = moff_read_image(self.handle, out, int(reset), timeout_ms)
+        return out, n
+
+    def sync(self, timeout_ms=-1):
+        moff_sync(self.handle, timeout_ms)
+
+    def reset(self):
+        moff_reset(self.handle)
+
+    def info(self):
+        return moff_plan_info(self.handle)
+
+    def set_timing(self, on=True):
+        moff_set_timing(self.handle, on)
+
+    def timing(self, kind, reset=False):
+        return moff_timing(self.handle, kind, reset)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            moff_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,7 @@
+// Instantiation of the imaging kernels for a 512x512 grid (one unit per size so
+// the sizes compile in parallel).
+#include "moff_image_kernels.cuh"
+
+namespace moff {
+MOFF_DEFINE_N(512)
+}  // namespace moff

@@ -1,0 +1,987 @@
+// moff_api.cu -- C ABI of libmoff: plans, binning, executor.
+//
+// A plan fixes one array (Morales, arXiv 0812.3669, Sec. 4, Eq. m6): antenna
+// anchors, per-antenna kernels W, grid size, channels and pols.  At creation
+// the kernels are binned by grid-row stripe into per-cell contribution lists
+// (the gather form of the W^T scatter, so every cell sums its contributions
+// in one fixed order and results do not depend on scheduling), twiddle
+// tables are built in FP64 on the host, and device memory for gains, FP64
+// accumulators and the row-transform scratch is reserved.  Submitting a
+// block runs, per (channel chunk, time chunk), the gridding/row-transform
+// kernel and the column-transform/integrate kernel on the plan's stream.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/moff.h"
+#include "moff_fft.cuh"
+#include "moff_image_kernels.cuh"
+#include "moff_internal.h"
+
+using namespace moff;
+
+namespace {
+
+thread_local std::string g_err;
+
+moff_status fail(moff_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define MOFF_CK(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            if (e_ == cudaErrorMemoryAllocation) {                                        \
+                cudaGetLastError();                                                       \
+                return fail(MOFF_ENOMEM, "%s: %s", #call, cudaGetErrorString(e_));        \
+            }                                                                             \
+            return fail(MOFF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));             \
+        }                                                                                 \
+    } while (0)
+
+// Host-side fault injection for tests: MOFF_FAULT=alloc:K makes the K-th
+// device allocation of the process (counting from 1) report out-of-memory.
+std::atomic<long long> g_alloc_count{0};
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    const long long k = ++g_alloc_count;
+    const char *f = getenv("MOFF_FAULT");
+    if (f && strncmp(f, "alloc:", 6) == 0 && atoll(f + 6) == k) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes ? bytes : 16);
+}
+
+// exp(2 pi i m / L) in FP64 with exact quadrant points.
+void root_unity(long long m, long long L, double *c, double *s) {
+    m %= L;
+    if (m < 0) m += L;
+    const long long q = (4 * m) / L, r = (4 * m) % L;
+    double cr = 1.0, sr = 0.0;
+    if (r != 0) {
+        const double ang = (M_PI / 2.0) * (double)r / (double)L;
+        cr = std::cos(ang);
+        sr = std::sin(ang);
+    }
+    switch (q) {
+        case 0: *c = cr; *s = sr; break;
+        case 1: *c = -sr; *s = cr; break;
+        case 2: *c = -cr; *s = -sr; break;
+        default: *c = sr; *s = -cr; break;
+    }
+}
+
+template <int N>
+std::vector<float2> pass_twiddles() {
+    using P = FftPlan<N>;
+    using T = FftTw<N>;
+    std::vector<float2> t(std::max(T::TOTAL, 1));
+    auto fill = [&](int off, int NS, int R) {
+        for (int r = 1; r < R; ++r)
+            for (int m = 0; m < NS; ++m) {
+                double c, s;
+                root_unity((long long)m * r, (long long)NS * R, &c, &s);
+                t[off + (r - 1) * NS + m] = make_float2((float)c, (float)s);
+            }
+    };
+    fill(T::OFF1, P::R0, P::R1);
+    if (P::NP == 3) fill(T::OFF2, P::R0 * P::R1, P::R2);
+    return t;
+}
+
+std::vector<float2> pass_twiddles_n(int n) {
+    switch (n) {
+        case 32: return pass_twiddles<32>();
+        case 64: return pass_twiddles<64>();
+        case 128: return pass_twiddles<128>();
+        case 256: return pass_twiddles<256>();
+        case 512: return pass_twiddles<512>();
+        case 1024: return pass_twiddles<1024>();
+        case 2048: return pass_twiddles<2048>();
+    }
+    return {};
+}
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+__global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ o, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        o[i] = (float)a[i];
+}
+
+}  // namespace
+
+namespace moff {
+
+int fft_tw_total(int n) {
+    switch (n) {
+        case 32: return FftTw<32>::TOTAL;
+        case 64: return FftTw<64>::TOTAL;
+        case 128: return FftTw<128>::TOTAL;
+        case 256: return FftTw<256>::TOTAL;
+        case 512: return FftTw<512>::TOTAL;
+        case 1024: return FftTw<1024>::TOTAL;
+        case 2048: return FftTw<2048>::TOTAL;
+    }
+    return 0;
+}
+
+int col_width(int N) {
+    switch (N) {
+        case 32: return ColShape<32>::W;
+        case 64: return ColShape<64>::W;
+        case 128: return ColShape<128>::W;
+        case 256: return ColShape<256>::W;
+        case 512: return ColShape<512>::W;
+    }
+    return 0;
+}
+
+size_t col_smem_bytes(int N, int P) {
+    switch (N) {
+        case 32: return col_smem_bytes_t<32>(P);
+        case 64: return col_smem_bytes_t<64>(P);
+        case 128: return col_smem_bytes_t<128>(P);
+        case 256: return col_smem_bytes_t<256>(P);
+        case 512: return col_smem_bytes_t<512>(P);
+    }
+    return 0;
+}
+
+cudaError_t launch_grid(int N, int P, bool csmem, bool go, const GridArgs &a, int n_stripes, size_t smem,
+                        cudaStream_t st) {
+    switch (N) {
+        case 32: return launch_grid_n32(P, csmem, go, a, n_stripes, smem, st);
+        case 64: return launch_grid_n64(P, csmem, go, a, n_stripes, smem, st);
+        case 128: return launch_grid_n128(P, csmem, go, a, n_stripes, smem, st);
+        case 256: return launch_grid_n256(P, csmem, go, a, n_stripes, smem, st);
+        case 512: return launch_grid_n512(P, csmem, go, a, n_stripes, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cols(int N, int P, const ColArgs &a, cudaStream_t st) {
+    switch (N) {
+        case 32: return launch_cols_n32(P, a, st);
+        case 64: return launch_cols_n64(P, a, st);
+        case 128: return launch_cols_n128(P, a, st);
+        case 256: return launch_cols_n256(P, a, st);
+        case 512: return launch_cols_n512(P, a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_to_f32(const double *acc, float *out, long long n, cudaStream_t st) {
+    const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+    k_to_f32<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, st>>>(acc, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace moff
+
+struct moff_plan {
+    int A = 0, K = 0, N = 0, C = 0, P = 0, nprod = 0;
+    unsigned flags = 0;
+    bool jones = false, fstage = false;
+    int device = 0;
+    cudaStream_t st = nullptr, cst = nullptr;
+    bool own_stream = false;
+
+    // binning
+    int rows = 0, n_stripes = 0, max_nloc = 0, max_ncon = 0;
+    bool csmem = false;
+    size_t grid_smem = 0;
+    int *d_st_ant_off = nullptr, *d_st_ant = nullptr, *d_st_cell_off = nullptr;
+    long long *d_st_con_off = nullptr;
+    float2 *d_con_tap = nullptr;
+    uint16_t *d_con_y = nullptr;
+    float2 *d_twp = nullptr;
+
+    float2 *d_gains = nullptr;
+    double *d_acc = nullptr;
+    float *d_img = nullptr;
+    float2 *d_H = nullptr;
+    int Tb = 0, Cb = 0;
+
+    void *d_stage[2] = {nullptr, nullptr};
+    size_t stage_bytes[2] = {0, 0};
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_consumed[2] = {nullptr, nullptr};
+    cudaEvent_t ev_done = nullptr;
+    long long nsub = 0;
+
+    // F-stage
+    int ntaps = 8;
+    float scale = 1.f;
+    float *d_h = nullptr;
+    float2 *d_twpC = nullptr, *d_twM = nullptr;
+    uint8_t *d_codes = nullptr;
+    size_t codes_bytes = 0;
+    float2 *d_spec = nullptr;
+    size_t spec_bytes = 0;
+
+    long long n_samples = 0;
+    size_t dev_bytes = 0;
+    std::vector<void *> allocs;
+
+    // optional per-launch timing: (kind, start, stop)
+    bool timing = false;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace {
+
+template <class T>
+moff_status palloc(moff_plan *pl, T **p, size_t bytes) {
+    void *q = nullptr;
+    cudaError_t e = dev_alloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? MOFF_ENOMEM : MOFF_ECUDA, "device allocation of %zu bytes: %s",
+                    bytes, cudaGetErrorString(e));
+    }
+    pl->allocs.push_back(q);
+    pl->dev_bytes += bytes;
+    *p = reinterpret_cast<T *>(q);
+    return MOFF_OK;
+}
+
+void pfree(moff_plan *pl, void *p) {
+    if (!p) return;
+    auto it = std::find(pl->allocs.begin(), pl->allocs.end(), p);
+    if (it != pl->allocs.end()) pl->allocs.erase(it);
+    cudaFree(p);
+}
+
+void destroy_plan(moff_plan *pl) {
+    if (!pl) return;
+    if (pl->st) cudaStreamSynchronize(pl->st);
+    if (pl->cst) cudaStreamSynchronize(pl->cst);
+    for (void *p : pl->allocs) cudaFree(p);
+    for (int i = 0; i < 2; ++i) {
+        if (pl->ev_copied[i]) cudaEventDestroy(pl->ev_copied[i]);
+        if (pl->ev_consumed[i]) cudaEventDestroy(pl->ev_consumed[i]);
+    }
+    if (pl->ev_done) cudaEventDestroy(pl->ev_done);
+    for (auto &r : pl->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (cudaEvent_t e : pl->ev_pool) cudaEventDestroy(e);
+    if (pl->cst) cudaStreamDestroy(pl->cst);
+    if (pl->own_stream && pl->st) cudaStreamDestroy(pl->st);
+    delete pl;
+}
+
+moff_status wait_event(cudaEvent_t ev, int timeout_ms) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return MOFF_OK;
+        if (e != cudaErrorNotReady) return fail(MOFF_ECUDA, "waiting for the GPU: %s", cudaGetErrorString(e));
+        if (timeout_ms >= 0) {
+            const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (ms >= timeout_ms) return fail(MOFF_ETIMEDOUT, "GPU work not finished after %d ms", timeout_ms);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+moff_status sync_plan(moff_plan *pl, int timeout_ms) {
+    MOFF_CK(cudaEventRecord(pl->ev_done, pl->st));
+    return wait_event(pl->ev_done, timeout_ms);
+}
+
+cudaEvent_t pool_event(moff_plan *pl) {
+    if (!pl->ev_pool.empty()) {
+        cudaEvent_t e = pl->ev_pool.back();
+        pl->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one launch with events when timing is on.
+struct TimedLaunch {
+    moff_plan *pl;
+    int kind;
+    cudaEvent_t a = nullptr;
+    TimedLaunch(moff_plan *p, int k) : pl(p), kind(k) {
+        if (pl->timing) {
+            a = pool_event(pl);
+            cudaEventRecord(a, pl->st);
+        }
+    }
+    void done() {
+        if (a) {
+            cudaEvent_t b = pool_event(pl);
+            cudaEventRecord(b, pl->st);
+            pl->recs.push_back(moff_plan::Rec{kind, a, b});
+            a = nullptr;
+        }
+    }
+};
+
+void clear_recs(moff_plan *pl) {
+    for (auto &r : pl->recs) {
+        pl->ev_pool.push_back(r.a);
+        pl->ev_pool.push_back(r.b);
+    }
+    pl->recs.clear();
+}
+
+// Copy a host block into the next staging buffer on the copy stream; the
+// compute stream waits for the copy, and the host waits until the copy has
+// finished (so the caller may reuse its buffer).  Returns the device copy.
+moff_status stage_in(moff_plan *pl, const void *host, size_t bytes, const void **dev, int *slot) {
+    const int i = (int)(pl->nsub & 1);
+    if (pl->stage_bytes[i] < bytes) {
+        MOFF_CK(cudaEventSynchronize(pl->ev_consumed[i]));
+        pfree(pl, pl->d_stage[i]);
+        pl->dev_bytes -= pl->stage_bytes[i];
+        pl->d_stage[i] = nullptr;
+        pl->stage_bytes[i] = 0;
+        moff_status s = palloc(pl, &pl->d_stage[i], bytes);
+        if (s != MOFF_OK) return s;
+        pl->stage_bytes[i] = bytes;
+    }
+    MOFF_CK(cudaStreamWaitEvent(pl->cst, pl->ev_consumed[i], 0));
+    MOFF_CK(cudaMemcpyAsync(pl->d_stage[i], host, bytes, cudaMemcpyHostToDevice, pl->cst));
+    MOFF_CK(cudaEventRecord(pl->ev_copied[i], pl->cst));
+    MOFF_CK(cudaStreamWaitEvent(pl->st, pl->ev_copied[i], 0));
+    *dev = pl->d_stage[i];
+    *slot = i;
+    return MOFF_OK;
+}
+
+// After the compute that reads staging slot i is enqueued: mark it and wait for the copy.
+moff_status stage_done(moff_plan *pl, int i) {
+    MOFF_CK(cudaEventRecord(pl->ev_consumed[i], pl->st));
+    pl->nsub++;
+    return wait_event(pl->ev_copied[i], -1);
+}
+
+moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
+    for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
+        const int nc = std::min(pl->Cb, pl->C - c0);
+        for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
+            const int nt = std::min(pl->Tb, n_time - t0);
+            GridArgs g{};
+            g.volt = volt;
+            g.volt_tstride = tstride;
+            g.t0 = t0;
+            g.nt = nt;
+            g.c0 = c0;
+            g.nc = nc;
+            g.A = pl->A;
+            g.rows = pl->rows;
+            g.max_nloc = pl->max_nloc;
+            g.max_ncon = pl->max_ncon;
+            g.gains = pl->d_gains;
+            g.st_ant_off = pl->d_st_ant_off;
+            g.st_ant = pl->d_st_ant;
+            g.st_cell_off = pl->d_st_cell_off;
+            g.st_con_off = pl->d_st_con_off;
+            g.con_tap = pl->d_con_tap;
+            g.con_y = pl->d_con_y;
+            g.twp = pl->d_twp;
+            g.out = pl->d_H;
+            TimedLaunch tg(pl, 1);
+            MOFF_CK(launch_grid(pl->N, pl->P, pl->csmem, false, g, pl->n_stripes, pl->grid_smem, pl->st));
+            tg.done();
+            ColArgs ca{};
+            ca.H = pl->d_H;
+            ca.nt = nt;
+            ca.c0 = c0;
+            ca.nc = nc;
+            ca.twp = pl->d_twp;
+            ca.acc = pl->d_acc;
+            TimedLaunch tc(pl, 2);
+            MOFF_CK(launch_cols(pl->N, pl->P, ca, pl->st));
+            tc.done();
+        }
+    }
+    return MOFF_OK;
+}
+
+// Per-antenna kernel value (re, im) for output pol po, input pol pi at (iy, ix).
+inline void tap_at(const moff_plan *pl, const float *taps, int a, int po, int pi, int iy, int ix, float *re, float *im) {
+    const int K = pl->K;
+    long long idx;
+    if (pl->jones) {
+        idx = ((((long long)a * 2 + po) * 2 + pi) * K + iy) * K + ix;
+    } else {
+        if (po != pi) { *re = 0.f; *im = 0.f; return; }
+        idx = (((long long)a * pl->P + po) * K + iy) * K + ix;
+    }
+    *re = taps[2 * idx];
+    *im = taps[2 * idx + 1];
+}
+
+struct Contrib {
+    int cell;
+    int y;
+    float2 tap;
+};
+
+moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps) {
+    const int A = pl->A, K = pl->K, N = pl->N, P = pl->P, h = K / 2;
+    std::vector<int> ax(A), ay(A);
+    for (int a = 0; a < A; ++a) {
+        const double x = pos[2 * a], y = pos[2 * a + 1];
+        if (!std::isfinite(x) || !std::isfinite(y) || std::fabs(x) > 1e9 || std::fabs(y) > 1e9)
+            return fail(MOFF_EINVAL, "antenna %d position is not finite or out of range", a);
+        long long fx = (long long)std::floor(x + 0.5), fy = (long long)std::floor(y + 0.5);
+        ax[a] = (int)(((fx % N) + N) % N);
+        ay[a] = (int)(((fy % N) + N) % N);
+    }
+    const int pin_n = pl->jones ? 2 : 1;   // input pols per output pol
+    // contributions landing in each grid row
+    std::vector<long long> row_con(N, 0);
+    for (int a = 0; a < A; ++a)
+        for (int po = 0; po < P; ++po)
+            for (int k = 0; k < pin_n; ++k) {
+                const int pi = pl->jones ? k : po;
+                for (int iy = 0; iy < K; ++iy) {
+                    const int row = (ay[a] + iy - h + N) % N;
+                    for (int ix = 0; ix < K; ++ix) {
+                        float re, im;
+                        tap_at(pl, taps, a, po, pi, iy, ix, &re, &im);
+                        if (re != 0.f || im != 0.f) row_con[row]++;
+                    }
+                }
+            }
+    const int tw_total = fft_tw_total(N);
+    const size_t budget = 110 * 1024;   // two CTAs per SM
+    int best_rows = 0;
+    bool best_csmem = false;
+    int best_nloc = 0;
+    long long best_ncon = 0;
+    for (int rows = std::min(16, N); rows >= 1; rows /= 2) {
+        const int ns = N / rows;
+        std::vector<int> nloc(ns, 0);
+        std::vector<long long> ncon(ns, 0);
+        std::vector<int> seen(ns, -1);
+        for (int a = 0; a < A; ++a)
+            for (int iy = 0; iy < K; ++iy) {
+                const int s = ((ay[a] + iy - h + N) % N) / rows;
+                if (seen[s] != a) { seen[s] = a; nloc[s]++; }
+            }
+        for (int r = 0; r < N; ++r) ncon[r / rows] += row_con[r];
+        const int mnl = *std::max_element(nloc.begin(), nloc.end());
+        const long long mnc = *std::max_element(ncon.begin(), ncon.end());
+        if ((long long)mnl * P >= 65536) continue;
+        const size_t with = grid_smem_bytes(N, P, rows, mnl, (int)std::min<long long>(mnc, 1 << 30), true, tw_total);
+        const size_t without = grid_smem_bytes(N, P, rows, mnl, 0, false, tw_total);
+        if (with <= budget) { best_rows = rows; best_csmem = true; best_nloc = mnl; best_ncon = mnc; break; }
+        if (without <= budget && best_rows == 0) { best_rows = rows; best_csmem = false; best_nloc = mnl; best_ncon = mnc; }
+    }
+    if (best_rows == 0)
+        return fail(MOFF_EINVAL, "array too dense for the gridding kernel (antennas per grid row exceed its limits)");
+    pl->rows = best_rows;
+    pl->csmem = best_csmem;
+    pl->n_stripes = N / best_rows;
+    pl->max_nloc = std::max(best_nloc, 1);
+    pl->max_ncon = (int)std::max<long long>(best_csmem ? best_ncon : 0, 0);
+    pl->grid_smem = grid_smem_bytes(N, P, pl->rows, pl->max_nloc, pl->max_ncon, pl->csmem, tw_total);
+
+    // Build the lists for the chosen stripe height.
+    const int rows = pl->rows, ns = pl->n_stripes;
+    std::vector<std::vector<int>> sant(ns);
+    std::vector<std::vector<Contrib>> scon(ns);
+    for (int a = 0; a < A; ++a) {
+        for (int iy = 0; iy < K; ++iy) {
+            const int s = ((ay[a] + iy - h + N) % N) / rows;
+            if (sant[s].empty() || sant[s].back() != a) sant[s].push_back(a);
+        }
+        for (int po = 0; po < P; ++po)
+            for (int k = 0; k < pin_n; ++k) {
+                const int pi = pl->jones ? k : po;
+                for (int iy = 0; iy < K; ++iy) {
+                    const int row = (ay[a] + iy - h + N) % N;
+                    const int s = row / rows, rl = row % rows;
+                    const int la = (int)sant[s].size() - 1;   // antenna a was appended last
+                    for (int ix = 0; ix < K; ++ix) {
+                        float re, im;
+                        tap_at(pl, taps, a, po, pi, iy, ix, &re, &im);
+                        if (re == 0.f && im == 0.f) continue;
+                        const int col = (ax[a] + ix - h + N) % N;
+                        scon[s].push_back(Contrib{(po * rows + rl) * N + col, la * P + pi, make_float2(re, im)});
+                    }
+                }
+            }
+    }
+    const int ncell = P * rows * N;
+    std::vector<int> ant_off(ns + 1, 0), ant_list;
+    std::vector<int> cell_off((size_t)ns * (ncell + 1), 0);
+    std::vector<long long> con_off(ns + 1, 0);
+    std::vector<float2> con_tap;
+    std::vector<uint16_t> con_y;
+    for (int s = 0; s < ns; ++s) {
+        ant_off[s + 1] = ant_off[s] + (int)sant[s].size();
+        ant_list.insert(ant_list.end(), sant[s].begin(), sant[s].end());
+        auto &v = scon[s];
+        std::stable_sort(v.begin(), v.end(), [](const Contrib &x, const Contrib &y) { return x.cell < y.cell; });
+        int *co = &cell_off[(size_t)s * (ncell + 1)];
+        for (const Contrib &c : v) co[c.cell + 1]++;
+        for (int i = 0; i < ncell; ++i) co[i + 1] += co[i];
+        con_off[s + 1] = con_off[s] + (long long)v.size();
+        for (const Contrib &c : v) {
+            con_tap.push_back(c.tap);
+            con_y.push_back((uint16_t)c.y);
+        }
+    }
+    moff_status s;
+    if ((s = palloc(pl, &pl->d_st_ant_off, ant_off.size() * 4)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_st_ant, std::max<size_t>(ant_list.size(), 1) * 4)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_st_cell_off, cell_off.size() * 4)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_st_con_off, con_off.size() * 8)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_con_tap, std::max<size_t>(con_tap.size(), 1) * 8)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_con_y, std::max<size_t>(con_y.size(), 1) * 2)) != MOFF_OK) return s;
+    MOFF_CK(cudaMemcpy(pl->d_st_ant_off, ant_off.data(), ant_off.size() * 4, cudaMemcpyHostToDevice));
+    if (!ant_list.empty()) MOFF_CK(cudaMemcpy(pl->d_st_ant, ant_list.data(), ant_list.size() * 4, cudaMemcpyHostToDevice));
+    MOFF_CK(cudaMemcpy(pl->d_st_cell_off, cell_off.data(), cell_off.size() * 4, cudaMemcpyHostToDevice));
+    MOFF_CK(cudaMemcpy(pl->d_st_con_off, con_off.data(), con_off.size() * 8, cudaMemcpyHostToDevice));
+    if (!con_tap.empty()) {
+        MOFF_CK(cudaMemcpy(pl->d_con_tap, con_tap.data(), con_tap.size() * 8, cudaMemcpyHostToDevice));
+        MOFF_CK(cudaMemcpy(pl->d_con_y, con_y.data(), con_y.size() * 2, cudaMemcpyHostToDevice));
+    }
+    return MOFF_OK;
+}
+
+moff_status upload_fstage(moff_plan *pl, int ntaps, const float *coeffs, float scale) {
+    const int M = 2 * pl->C;
+    const long long L = (long long)ntaps * M;
+    std::vector<float> h(L);
+    if (coeffs) {
+        for (long long n = 0; n < L; ++n) {
+            if (!std::isfinite(coeffs[n])) return fail(MOFF_EINVAL, "filter coefficient %lld is not finite", n);
+            h[n] = coeffs[n];
+        }
+    } else {
+        // sinc one channel wide, Hann window over the whole filter
+        for (long long n = 0; n < L; ++n) {
+            const double x = ((double)n - (double)(L - 1) / 2.0) / (double)M;
+            const double sinc = x == 0.0 ? 1.0 : std::sin(M_PI * x) / (M_PI * x);
+            const double win = L > 1 ? 0.5 - 0.5 * std::cos(2.0 * M_PI * (double)n / (double)(L - 1)) : 1.0;
+            h[n] = (float)(sinc * win);
+        }
+    }
+    MOFF_CK(cudaMemcpyAsync(pl->d_h, h.data(), L * 4, cudaMemcpyHostToDevice, pl->st));
+    MOFF_CK(cudaStreamSynchronize(pl->st));
+    pl->ntaps = ntaps;
+    pl->scale = scale;
+    return MOFF_OK;
+}
+
+moff_status check_plan(const moff_plan *pl) {
+    if (!pl) return fail(MOFF_EINVAL, "plan is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != pl->device) return fail(MOFF_ESTATE, "plan belongs to device %d but device %d is current", pl->device, dev);
+    return MOFF_OK;
+}
+
+moff_status run_pfb(moff_plan *pl, const int8_t *adc, long long n_samp, int F, int kind, void *out) {
+    PfbArgs p{};
+    p.adc = adc;
+    p.S = n_samp;
+    p.AP = pl->A * pl->P;
+    p.F = F;
+    p.ntaps = pl->ntaps;
+    p.h = pl->d_h;
+    p.scale = pl->scale;
+    p.twp = pl->d_twpC;
+    p.twM = pl->d_twM;
+    p.out_kind = kind;
+    p.codes = kind == 0 ? reinterpret_cast<uint8_t *>(out) : nullptr;
+    p.spec = kind == 1 ? reinterpret_cast<float2 *>(out) : nullptr;
+    TimedLaunch tp(pl, 0);
+    MOFF_CK(launch_pfb(pl->C, p, pl->st));
+    tp.done();
+    return MOFF_OK;
+}
+
+moff_status check_adc(moff_plan *pl, const int8_t *adc, long long n_samp, int *F) {
+    if (!pl->fstage) return fail(MOFF_ESTATE, "plan was created without MOFF_FSTAGE");
+    if (!adc) return fail(MOFF_EINVAL, "adc is NULL");
+    const long long M = 2LL * pl->C;
+    if (n_samp <= 0 || n_samp % M != 0) return fail(MOFF_EINVAL, "n_samp (%lld) must be a positive multiple of 2*n_chan = %lld", n_samp, M);
+    const long long f = n_samp / M - pl->ntaps + 1;
+    if (f < 1) return fail(MOFF_EINVAL, "n_samp (%lld) shorter than one filter (%d frames of %lld)", n_samp, pl->ntaps, M);
+    if (f > (1LL << 30)) return fail(MOFF_EINVAL, "too many frames");
+    *F = (int)f;
+    return MOFF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *moff_last_error(void) { return g_err.c_str(); }
+
+moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int ksize, const float *taps, int grid_n,
+                             int n_chan, int n_pol, unsigned flags, void *cuda_stream) {
+    if (!out) return fail(MOFF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_ant < 1 || n_ant > 65536) return fail(MOFF_EINVAL, "n_ant (%d) must be in [1, 65536]", n_ant);
+    if (!pos || !taps) return fail(MOFF_EINVAL, "pos and taps must not be NULL");
+    if (grid_n != 32 && grid_n != 64 && grid_n != 128 && grid_n != 256 && grid_n != 512)
+        return fail(MOFF_EINVAL, "grid_n (%d) must be 32, 64, 128, 256 or 512", grid_n);
+    if (ksize < 1 || ksize % 2 == 0 || ksize > 15 || ksize > grid_n)
+        return fail(MOFF_EINVAL, "ksize (%d) must be odd, in [1, 15] and <= grid_n", ksize);
+    if (n_chan < 1) return fail(MOFF_EINVAL, "n_chan (%d) must be >= 1", n_chan);
+    if (n_pol != 1 && n_pol != 2) return fail(MOFF_EINVAL, "n_pol (%d) must be 1 or 2", n_pol);
+    if (flags & ~(unsigned)(MOFF_FSTAGE | MOFF_JONES)) return fail(MOFF_EINVAL, "unknown flag bits 0x%x", flags);
+    if ((flags & MOFF_JONES) && n_pol != 2) return fail(MOFF_EINVAL, "MOFF_JONES requires n_pol = 2");
+    if ((flags & MOFF_FSTAGE) && (!is_pow2(n_chan) || n_chan < 32 || n_chan > 2048))
+        return fail(MOFF_EINVAL, "with MOFF_FSTAGE n_chan (%d) must be a power of two in [32, 2048]", n_chan);
+
+    moff_plan *pl = new moff_plan();
+    pl->A = n_ant;
+    pl->K = ksize;
+    pl->N = grid_n;
+    pl->C = n_chan;
+    pl->P = n_pol;
+    pl->nprod = n_pol == 1 ? 1 : 4;
+    pl->flags = flags;
+    pl->jones = (flags & MOFF_JONES) != 0;
+    pl->fstage = (flags & MOFF_FSTAGE) != 0;
+    auto bail = [&](moff_status s) {
+        std::string msg = g_err;
+        destroy_plan(pl);
+        g_err = msg;
+        return s;
+    };
+    if (cudaGetDevice(&pl->device) != cudaSuccess) return bail(fail(MOFF_ECUDA, "no CUDA device"));
+    if (cuda_stream) {
+        pl->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&pl->st, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "stream creation failed"));
+        pl->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&pl->cst, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(MOFF_ECUDA, "copy stream creation failed"));
+    for (int i = 0; i < 2; ++i) {
+        if (cudaEventCreateWithFlags(&pl->ev_copied[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev_consumed[i], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "event creation failed"));
+    }
+    if (cudaEventCreateWithFlags(&pl->ev_done, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(MOFF_ECUDA, "event creation failed"));
+
+    moff_status s = bin_plan(pl, pos, taps);
+    if (s != MOFF_OK) return bail(s);
+
+    // twiddles of the N-point imaging transform
+    {
+        std::vector<float2> tw = pass_twiddles_n(grid_n);
+        if ((s = palloc(pl, &pl->d_twp, tw.size() * 8)) != MOFF_OK) return bail(s);
+        if (cudaMemcpy(pl->d_twp, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "twiddle upload failed"));
+    }
+    // gains = 1
+    {
+        const size_t n = (size_t)n_chan * n_ant * n_pol;
+        if ((s = palloc(pl, &pl->d_gains, n * 8)) != MOFF_OK) return bail(s);
+        std::vector<float2> one(n, make_float2(1.f, 0.f));
+        if (cudaMemcpy(pl->d_gains, one.data(), n * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "gain upload failed"));
+    }
+    // accumulators and image staging
+    {
+        const size_t n = (size_t)n_chan * pl->nprod * grid_n * grid_n;
+        if ((s = palloc(pl, &pl->d_acc, n * 8)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_img, n * 4)) != MOFF_OK) return bail(s);
+        if (cudaMemset(pl->d_acc, 0, n * 8) != cudaSuccess) return bail(fail(MOFF_ECUDA, "memset failed"));
+    }
+    // row-transform scratch: Tb samples x Cb channels per chunk
+    {
+        const size_t per = (size_t)n_pol * grid_n * grid_n * 8;
+        long long budget = 8192LL << 20;
+        if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, atoll(e)) << 20;
+        const long long cb = std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per)));
+        const long long tb = std::max(1LL, std::min<long long>(64, budget / (long long)(cb * per)));
+        pl->Cb = (int)cb;
+        pl->Tb = (int)tb;
+        if ((s = palloc(pl, &pl->d_H, (size_t)tb * cb * per)) != MOFF_OK) return bail(s);
+    }
+    // F-stage tables
+    if (pl->fstage) {
+        const int CN = n_chan, M = 2 * CN;
+        std::vector<float2> tw = pass_twiddles_n(CN);
+        std::vector<float2> twM(CN);
+        for (int k = 0; k < CN; ++k) {
+            double c, sn;
+            root_unity(-(long long)k, M, &c, &sn);
+            twM[k] = make_float2((float)c, (float)sn);
+        }
+        if ((s = palloc(pl, &pl->d_twpC, tw.size() * 8)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_twM, twM.size() * 8)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_h, (size_t)16 * M * 4)) != MOFF_OK) return bail(s);
+        if (cudaMemcpy(pl->d_twpC, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(pl->d_twM, twM.data(), twM.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "F-stage table upload failed"));
+        if ((s = upload_fstage(pl, 8, nullptr, 1.f)) != MOFF_OK) return bail(s);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(MOFF_ECUDA, "plan set-up failed"));
+    *out = pl;
+    g_err.clear();
+    return MOFF_OK;
+}
+
+moff_status moff_plan_destroy(moff_plan *plan) {
+    if (!plan) return MOFF_OK;
+    destroy_plan(plan);
+    return MOFF_OK;
+}
+
+moff_status moff_set_gains(moff_plan *pl, const float *gains, int on_device) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!gains) return fail(MOFF_EINVAL, "gains is NULL");
+    const size_t bytes = (size_t)pl->C * pl->A * pl->P * 8;
+    MOFF_CK(cudaMemcpyAsync(pl->d_gains, gains, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pl->st));
+    if (!on_device) return sync_plan(pl, -1);
+    return MOFF_OK;
+}
+
+moff_status moff_set_fstage(moff_plan *pl, int n_taps, const float *coeffs, float scale) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!pl->fstage) return fail(MOFF_ESTATE, "plan was created without MOFF_FSTAGE");
+    if (n_taps < 1 || n_taps > 16) return fail(MOFF_EINVAL, "n_taps (%d) must be in [1, 16]", n_taps);
+    if (!std::isfinite(scale) || scale <= 0.f) return fail(MOFF_EINVAL, "scale must be finite and > 0");
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    return upload_fstage(pl, n_taps, coeffs, scale);
+}
+
+moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_device) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!volt) return fail(MOFF_EINVAL, "volt is NULL");
+    if (n_time < 1) return fail(MOFF_EINVAL, "n_time (%d) must be >= 1", n_time);
+    const long long tstride = (long long)pl->C * pl->A * pl->P;
+    const size_t bytes = (size_t)n_time * tstride;
+    if (on_device) {
+        if ((s = run_image(pl, volt, n_time, tstride)) != MOFF_OK) return s;
+    } else {
+        const void *dev = nullptr;
+        int slot = 0;
+        if ((s = stage_in(pl, volt, bytes, &dev, &slot)) != MOFF_OK) return s;
+        if ((s = run_image(pl, reinterpret_cast<const uint8_t *>(dev), n_time, tstride)) != MOFF_OK) return s;
+        if ((s = stage_done(pl, slot)) != MOFF_OK) return s;
+    }
+    pl->n_samples += n_time;
+    return MOFF_OK;
+}
+
+moff_status moff_submit_adc(moff_plan *pl, const int8_t *adc, long long n_samp, int on_device) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    int F = 0;
+    if ((s = check_adc(pl, adc, n_samp, &F)) != MOFF_OK) return s;
+    const size_t cbytes = (size_t)F * pl->C * pl->A * pl->P;
+    if (pl->codes_bytes < cbytes) {
+        if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+        pfree(pl, pl->d_codes);
+        pl->dev_bytes -= pl->codes_bytes;
+        pl->d_codes = nullptr;
+        pl->codes_bytes = 0;
+        if ((s = palloc(pl, &pl->d_codes, cbytes)) != MOFF_OK) return s;
+        pl->codes_bytes = cbytes;
+    }
+    const size_t abytes = (size_t)pl->A * pl->P * n_samp;
+    const int8_t *src = adc;
+    int slot = -1;
+    if (!on_device) {
+        const void *dev = nullptr;
+        if ((s = stage_in(pl, adc, abytes, &dev, &slot)) != MOFF_OK) return s;
+        src = reinterpret_cast<const int8_t *>(dev);
+    }
+    if ((s = run_pfb(pl, src, n_samp, F, 0, pl->d_codes)) != MOFF_OK) return s;
+    if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
+    if ((s = run_image(pl, pl->d_codes, F, (long long)pl->C * pl->A * pl->P)) != MOFF_OK) return s;
+    pl->n_samples += F;
+    return MOFF_OK;
+}
+
+moff_status moff_channelise(moff_plan *pl, const int8_t *adc, long long n_samp, int in_on_device, void *out, int out_kind,
+                            int out_on_device) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    int F = 0;
+    if ((s = check_adc(pl, adc, n_samp, &F)) != MOFF_OK) return s;
+    if (!out) return fail(MOFF_EINVAL, "out is NULL");
+    if (out_kind != 0 && out_kind != 1) return fail(MOFF_EINVAL, "out_kind must be 0 (codes) or 1 (spectra)");
+    const size_t n = (size_t)F * pl->C * pl->A * pl->P;
+    const size_t obytes = out_kind == 0 ? n : n * 8;
+    void *dst = out;
+    if (!out_on_device) {
+        if (out_kind == 0) {
+            if (pl->codes_bytes < n) {
+                if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+                pfree(pl, pl->d_codes);
+                pl->dev_bytes -= pl->codes_bytes;
+                pl->d_codes = nullptr;
+                pl->codes_bytes = 0;
+                if ((s = palloc(pl, &pl->d_codes, n)) != MOFF_OK) return s;
+                pl->codes_bytes = n;
+            }
+            dst = pl->d_codes;
+        } else {
+            if (pl->spec_bytes < obytes) {
+                if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+                pfree(pl, pl->d_spec);
+                pl->dev_bytes -= pl->spec_bytes;
+                pl->d_spec = nullptr;
+                pl->spec_bytes = 0;
+                if ((s = palloc(pl, &pl->d_spec, obytes)) != MOFF_OK) return s;
+                pl->spec_bytes = obytes;
+            }
+            dst = pl->d_spec;
+        }
+    }
+    const size_t abytes = (size_t)pl->A * pl->P * n_samp;
+    const int8_t *src = adc;
+    int slot = -1;
+    if (!in_on_device) {
+        const void *dev = nullptr;
+        if ((s = stage_in(pl, adc, abytes, &dev, &slot)) != MOFF_OK) return s;
+        src = reinterpret_cast<const int8_t *>(dev);
+    }
+    if ((s = run_pfb(pl, src, n_samp, F, out_kind, dst)) != MOFF_OK) return s;
+    if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
+    if (!out_on_device) MOFF_CK(cudaMemcpyAsync(out, dst, obytes, cudaMemcpyDeviceToHost, pl->st));
+    return sync_plan(pl, -1);
+}
+
+moff_status moff_grid_snapshot(moff_plan *pl, const uint8_t *volt, int on_device, int chan, float *out) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!volt || !out) return fail(MOFF_EINVAL, "volt and out must not be NULL");
+    if (chan < 0 || chan >= pl->C) return fail(MOFF_EINVAL, "chan (%d) out of range [0, %d)", chan, pl->C);
+    const size_t bytes = (size_t)pl->C * pl->A * pl->P;
+    const uint8_t *src = volt;
+    int slot = -1;
+    if (!on_device) {
+        const void *dev = nullptr;
+        if ((s = stage_in(pl, volt, bytes, &dev, &slot)) != MOFF_OK) return s;
+        src = reinterpret_cast<const uint8_t *>(dev);
+    }
+    GridArgs g{};
+    g.volt = src;
+    g.volt_tstride = 0;
+    g.t0 = 0;
+    g.nt = 1;
+    g.c0 = chan;
+    g.nc = 1;
+    g.A = pl->A;
+    g.rows = pl->rows;
+    g.max_nloc = pl->max_nloc;
+    g.max_ncon = pl->max_ncon;
+    g.gains = pl->d_gains;
+    g.st_ant_off = pl->d_st_ant_off;
+    g.st_ant = pl->d_st_ant;
+    g.st_cell_off = pl->d_st_cell_off;
+    g.st_con_off = pl->d_st_con_off;
+    g.con_tap = pl->d_con_tap;
+    g.con_y = pl->d_con_y;
+    g.twp = pl->d_twp;
+    g.out = pl->d_H;
+    MOFF_CK(launch_grid(pl->N, pl->P, pl->csmem, true, g, pl->n_stripes, pl->grid_smem, pl->st));
+    if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
+    MOFF_CK(cudaMemcpyAsync(out, pl->d_H, (size_t)pl->P * pl->N * pl->N * 8, cudaMemcpyDeviceToHost, pl->st));
+    return sync_plan(pl, -1);
+}
+
+moff_status moff_read_image(moff_plan *pl, float *out, long long *n_samples, int reset, int timeout_ms, int out_on_device) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!out) return fail(MOFF_EINVAL, "out is NULL");
+    if ((s = sync_plan(pl, timeout_ms)) != MOFF_OK) return s;
+    const long long n = (long long)pl->C * pl->nprod * pl->N * pl->N;
+    MOFF_CK(launch_to_f32(pl->d_acc, out_on_device ? out : pl->d_img, n, pl->st));
+    if (!out_on_device) MOFF_CK(cudaMemcpyAsync(out, pl->d_img, (size_t)n * 4, cudaMemcpyDeviceToHost, pl->st));
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    if (n_samples) *n_samples = pl->n_samples;
+    if (reset) {
+        MOFF_CK(cudaMemsetAsync(pl->d_acc, 0, (size_t)n * 8, pl->st));
+        pl->n_samples = 0;
+    }
+    return MOFF_OK;
+}
+
+moff_status moff_sync(moff_plan *pl, int timeout_ms) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    return sync_plan(pl, timeout_ms);
+}
+
+moff_status moff_reset(moff_plan *pl) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    MOFF_CK(cudaMemsetAsync(pl->d_acc, 0, (size_t)pl->C * pl->nprod * pl->N * pl->N * 8, pl->st));
+    pl->n_samples = 0;
+    return MOFF_OK;
+}
+
+moff_status moff_set_timing(moff_plan *pl, int on) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    clear_recs(pl);
+    pl->timing = on != 0;
+    return MOFF_OK;
+}
+
+moff_status moff_timing(moff_plan *pl, int kind, double *total_ms, long long *launches, int reset) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (kind < 0 || kind > 2) return fail(MOFF_EINVAL, "kind (%d) must be 0, 1 or 2", kind);
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    double tot = 0.0;
+    long long n = 0;
+    for (auto &r : pl->recs) {
+        if (r.kind != kind) continue;
+        float ms = 0.f;
+        MOFF_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        tot += ms;
+        ++n;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = n;
+    if (reset) clear_recs(pl);
+    return MOFF_OK;
+}
+
+moff_status moff_plan_info(const moff_plan *pl, int *n_prod, int *rows_per_stripe, int *time_chunk, int *chan_chunk,
+                           long long *device_bytes) {
+    if (!pl) return fail(MOFF_EINVAL, "plan is NULL");
+    if (n_prod) *n_prod = pl->nprod;
+    if (rows_per_stripe) *rows_per_stripe = pl->rows;
+    if (time_chunk) *time_chunk = pl->Tb;
+    if (chan_chunk) *chan_chunk = pl->Cb;
+    if (device_bytes) *device_bytes = (long long)pl->dev_bytes;
+    return MOFF_OK;
+}
+
+}  // extern "C"

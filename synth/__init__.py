@@ -272,3 +272,52 @@ def config_widefield(seed: int = SEED_BASE + 4, nx: int = 256, ny: int = 128, gr
     gains = gains_random(rng, n_chan, pos.shape[0], 2)
     return dict(pos=pos, taps=taps, grid_n=grid_n, n_chan=n_chan, n_pol=2, gains=gains,
                 jones=True, rng=rng)
+
+
+# --------------------------------------------------------------------------- device-side draws (large workloads)
+
+def device_codes(seed: int, n_time: int, n_chan: int, n_ant: int, n_pol: int,
+                 sigma: float = 2.0, chunk: int = 32):
+    """4-bit voltages ``uint8 [T][C][A][P]`` drawn on the GPU with a seeded torch
+    Philox generator: Gaussian noise of ``sigma`` per component, rounded and
+    clipped to [-7, 7], packed re-high/im-low.  For workloads too large to draw
+    on the host; the values are reproducible for a given seed."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed))
+    out = torch.empty((n_time, n_chan, n_ant, n_pol), dtype=torch.uint8, device="cuda")
+    for t0 in range(0, n_time, chunk):
+        n = min(chunk, n_time - t0)
+        shape = (n, n_chan, n_ant, n_pol)
+        re = torch.clamp(torch.round(torch.randn(shape, generator=g, device="cuda") * sigma), -7, 7).to(torch.int32)
+        im = torch.clamp(torch.round(torch.randn(shape, generator=g, device="cuda") * sigma), -7, 7).to(torch.int32)
+        out[t0:t0 + n] = (((re & 15) << 4) | (im & 15)).to(torch.uint8)
+    return out
+
+
+def device_adc(seed: int, pos, n_pol: int, n_samp: int, frame: int, grid_n: int,
+               sigma: float = 20.0, sources=((40, 70, 100, 12.0), (90, 30, 600, 8.0), (64, 64, 900, 6.0)),
+               chunk: int = 32):
+    """8-bit real ADC streams ``int8 [A][P][S]`` drawn on the GPU: Gaussian
+    noise of ``sigma`` plus narrow-band sky sources.  Each source
+    ``(kx, ky, channel, amplitude)`` is a tone at the centre of ``channel``
+    (``channel / frame`` cycles per sample) whose phase at antenna ``a`` is
+    ``-2 pi (x_a kx + y_a ky) / N`` (the Eq. Ea sky model at that channel)."""
+    import math
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed))
+    pos_t = torch.as_tensor(np.asarray(pos, dtype=np.float64), device="cuda")
+    A = pos_t.shape[0]
+    n = torch.arange(n_samp, device="cuda", dtype=torch.int64)
+    out = torch.empty((A, n_pol, n_samp), dtype=torch.int8, device="cuda")
+    for a0 in range(0, A, chunk):
+        a1 = min(A, a0 + chunk)
+        x = torch.randn((a1 - a0, n_pol, n_samp), generator=g, device="cuda") * sigma
+        for (kx, ky, ch, amp) in sources:
+            ph = (-2 * math.pi * (pos_t[a0:a1, 0] * kx + pos_t[a0:a1, 1] * ky) / grid_n).to(torch.float32)
+            # tone phase reduced exactly in integers before going to float32
+            tone = (2 * math.pi / frame) * ((int(ch) * n) % frame).to(torch.float32)
+            x += (amp * torch.cos(tone[None, :] + ph[:, None]))[:, None, :]
+        out[a0:a1] = torch.clamp(torch.round(x), -127, 127).to(torch.int8)
+    return out

@@ -1,0 +1,323 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (written here, derived from the arithmetic):
+  * images: max-normalised error <= 1e-5 per (channel, product) -- FP32
+    gridding, FP32 Stockham transforms (error ~ log2(N^2) * 2^-24 of max|E|),
+    FP32 sums over <= 64 samples folded into FP64 accumulators;
+  * gridded field: max |G_gpu - G_oracle| <= 2e-6 * max |G| (FP32 sums of a
+    few dozen kernel products per cell);
+  * F-stage spectra: <= 1e-5 of the stream's max |X|; 4-bit codes exact
+    except where the oracle's scaled value is within 1e-3 of a rounding
+    boundary, where one step either way is accepted.
+Gains and kernels are handed to the oracle exactly as the library sees them
+(rounded to complex64), so input quantisation is not counted as error.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_0812_3669_gb300 as moff
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-5
+GRID_TOL = 2e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    moff.build()
+    yield
+
+
+def c64(x):
+    return np.asarray(x).astype(np.complex64).astype(np.complex128)
+
+
+def gpu_image(pos, taps, N, C, P, codes, gains, jones=False, scratch_mb=None, on_device=False):
+    old = os.environ.get("MOFF_SCRATCH_MB")
+    if scratch_mb is not None:
+        os.environ["MOFF_SCRATCH_MB"] = str(scratch_mb)
+    try:
+        with moff.Plan(pos, taps, N, C, P, jones=jones) as pl:
+            pl.set_gains(gains)
+            if on_device:
+                pl.submit(torch.from_numpy(np.ascontiguousarray(codes)).cuda())
+            else:
+                pl.submit(np.ascontiguousarray(codes))
+            img, n = pl.read_image()
+            info = pl.info()
+    finally:
+        if scratch_mb is not None:
+            if old is None:
+                os.environ.pop("MOFF_SCRATCH_MB", None)
+            else:
+                os.environ["MOFF_SCRATCH_MB"] = old
+    return img, n, info
+
+
+def random_case(seed, A, N, K, P, C, T, jones=False, spread=None):
+    rng = np.random.default_rng(seed)
+    spread = N if spread is None else spread
+    pos = rng.uniform(0, spread, size=(A, 2)) + (N - spread) / 2
+    if jones:
+        taps = rng.normal(size=(A, 2, 2, K, K)) + 1j * rng.normal(size=(A, 2, 2, K, K))
+    else:
+        taps = rng.normal(size=(A, P, K, K)) + 1j * rng.normal(size=(A, P, K, K))
+    re = np.clip(np.rint(rng.normal(0, 2.5, size=(T, C, A, P))), -8, 7).astype(int)
+    im = np.clip(np.rint(rng.normal(0, 2.5, size=(T, C, A, P))), -8, 7).astype(int)
+    codes = synth.pack_4bit(re, im)
+    gains = synth.gains_random(rng, C, A, P)
+    return pos, c64(taps), codes, c64(gains)
+
+
+def assert_image(img, ref, tol=IMG_TOL):
+    err = oracle.max_norm_err(img, ref)
+    assert err.max() <= tol, f"max-normalised error {err.max():.3e} > {tol:g} (per channel/product {err})"
+    return err
+
+
+# ------------------------------------------------------------------ gridding (Eq. m6 steps 1-2)
+
+@pytest.mark.parametrize("N,P,K,A,jones", [(32, 1, 3, 64, False), (128, 2, 7, 300, False), (64, 2, 5, 40, True)])
+def test_grid_snapshot_matches_oracle(N, P, K, A, jones):
+    pos, taps, codes, gains = random_case(1, A, N, K, P, C=3, T=1, jones=jones)
+    with moff.Plan(pos, taps, N, 3, P, jones=jones) as pl:
+        pl.set_gains(gains)
+        for chan in range(3):
+            G = pl.grid_snapshot(np.ascontiguousarray(codes[0]), chan)
+            W = oracle.grid_matrix(pos, taps, N, P, jones)
+            y = oracle.calibrate(oracle.unpack_4bit(codes[0, chan]), gains[chan])
+            ref = oracle.grid(y[None], W, N, P)[0]
+            assert np.abs(G - ref).max() <= GRID_TOL * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ whole image (Eq. m6)
+
+def test_tiny_workload_image():
+    """64 antennas, one pol, 16 channels, 256 samples, 32x32 grid, shared 3x3 kernel."""
+    cfg = synth.config_tiny()
+    taps, gains = c64(cfg["taps"]), c64(cfg["gains"])
+    img, n, _ = gpu_image(cfg["pos"], taps, 32, 16, 1, cfg["codes"], gains)
+    ref = oracle.moff_image(cfg["codes"], gains, cfg["pos"], taps, 32, 1)
+    assert n == 256
+    assert_image(img, ref)
+
+
+@pytest.mark.parametrize("N", [32, 64, 128, 256, 512])
+@pytest.mark.parametrize("P", [1, 2])
+def test_image_every_grid_size(N, P):
+    """Several stripes and column tiles, ragged time and channel chunks."""
+    K = {32: 3, 64: 5, 128: 7, 256: 7, 512: 7}[N]
+    A = {32: 50, 64: 120, 128: 400, 256: 600, 512: 900}[N]
+    C, T = 3, 37
+    pos, taps, codes, gains = random_case(10 + N + P, A, N, K, P, C, T)
+    per = P * N * N * 8
+    scratch = max(1, (2 * 7 * per) >> 20)          # forces chunks of a few samples
+    img, n, info = gpu_image(pos, taps, N, C, P, codes, gains, scratch_mb=scratch)
+    assert info["time_chunk"] < T
+    ref = oracle.moff_image(codes, gains, pos, taps, N, P)
+    assert_image(img, ref)
+
+
+def test_image_jones_kernels():
+    pos, taps, codes, gains = random_case(20, 60, 64, 5, 2, C=2, T=21, jones=True)
+    img, _, _ = gpu_image(pos, taps, 64, 2, 2, codes, gains, jones=True)
+    ref = oracle.moff_image(codes, gains, pos, taps, 64, 2, jones=True)
+    assert_image(img, ref)
+
+
+def test_dense_core_global_contribution_lists():
+    """So many antennas per grid row that the kernel lists stay in global memory."""
+    rng = np.random.default_rng(21)
+    N, K, A = 64, 15, 1500
+    pos = rng.uniform(0, N, size=(A, 2))
+    taps = c64(rng.normal(size=(A, 1, K, K)) + 1j * rng.normal(size=(A, 1, K, K)))
+    codes = synth.pack_4bit(rng.integers(-7, 8, size=(5, 1, A, 1)), rng.integers(-7, 8, size=(5, 1, A, 1)))
+    gains = c64(synth.gains_random(rng, 1, A, 1))
+    img, _, _ = gpu_image(pos, taps, N, 1, 1, codes, gains)
+    ref = oracle.moff_image(codes, gains, pos, taps, N, 1)
+    assert_image(img, ref)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_single_antenna_wrapping_footprint_and_delta_kernel():
+    N = 32
+    pos = np.array([[31.7, 0.2]])          # anchor (32 -> 0, 0): footprint wraps both axes
+    rng = np.random.default_rng(30)
+    taps = c64(rng.normal(size=(1, 1, 5, 5)) + 1j * rng.normal(size=(1, 1, 5, 5)))
+    codes = synth.pack_4bit(rng.integers(-8, 8, size=(3, 1, 1, 1)), rng.integers(-8, 8, size=(3, 1, 1, 1)))
+    gains = c64(np.array([[[0.7 - 0.2j]]]))
+    img, _, _ = gpu_image(pos, taps, N, 1, 1, codes, gains)
+    assert_image(img, oracle.moff_image(codes, gains, pos, taps, N, 1))
+    # delta kernel: the image is flat and equals sum_t |g x|^2
+    img1, _, _ = gpu_image(pos, np.ones((1, 1, 1, 1)), N, 1, 1, codes, gains)
+    flat = np.sum(np.abs(oracle.unpack_4bit(codes[:, 0, 0, 0]) * gains[0, 0, 0]) ** 2)
+    np.testing.assert_allclose(img1[0, 0], np.full((N, N), flat), rtol=1e-6)
+
+
+def test_zero_voltages_give_zero_and_one_sample_works():
+    pos, taps, codes, gains = random_case(31, 30, 64, 3, 2, C=2, T=1)
+    img, n, _ = gpu_image(pos, taps, 64, 2, 2, np.zeros_like(codes), gains)
+    assert n == 1 and np.all(img == 0)
+    img, _, _ = gpu_image(pos, taps, 64, 2, 2, codes, gains)
+    assert_image(img, oracle.moff_image(codes, gains, pos, taps, 64, 2))
+
+
+def test_accumulation_across_blocks_reset_and_device_input():
+    pos, taps, codes, gains = random_case(32, 80, 64, 5, 2, C=3, T=30)
+    ref = oracle.moff_image(codes, gains, pos, taps, 64, 2)
+    with moff.Plan(pos, taps, 64, 3, 2) as pl:
+        pl.set_gains(gains)
+        pl.submit(np.ascontiguousarray(codes[:11]))
+        pl.submit(torch.from_numpy(np.ascontiguousarray(codes[11:]).copy()).cuda())
+        img, n = pl.read_image(reset=True)
+        assert n == 30
+        assert_image(img, ref)
+        img2, n2 = pl.read_image()
+        assert n2 == 0 and np.all(img2 == 0)
+        # device output buffer
+        pl.submit(np.ascontiguousarray(codes))
+        out = torch.empty((3, 4, 64, 64), dtype=torch.float32, device="cuda")
+        pl.read_image(out=out)
+        assert_image(out.cpu().numpy(), ref)
+
+
+def test_bitwise_deterministic_repeat():
+    pos, taps, codes, gains = random_case(33, 200, 128, 7, 2, C=2, T=9)
+    a, _, _ = gpu_image(pos, taps, 128, 2, 2, codes, gains)
+    b, _, _ = gpu_image(pos, taps, 128, 2, 2, codes, gains, on_device=True)
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ full-size dual-pol array, sampled channels
+
+def test_dualpol_full_size_sampled_channels():
+    """1024-antenna hex core, 128x128 grid, 7x7 complex kernels, 1024 channels,
+    1000 samples -- the launch configuration of the benchmark -- checked on
+    three sampled channels against the oracle."""
+    cfg = synth.config_dualpol()
+    T, C, A, P, N = 1000, cfg["n_chan"], cfg["pos"].shape[0], 2, cfg["grid_n"]
+    taps, gains = c64(cfg["taps"]), c64(cfg["gains"])
+    codes_d = synth.device_codes(8123669 + 101, T, C, A, P)
+    with moff.Plan(cfg["pos"], taps, N, C, P) as pl:
+        pl.set_gains(gains)
+        pl.submit(codes_d)
+        img, n = pl.read_image()
+    assert n == T
+    chans = [0, 517, 1023]
+    sub = codes_d[:, chans].cpu().numpy()
+    ref = oracle.moff_image(sub, gains[chans], cfg["pos"], taps, N, P)
+    assert_image(img[chans], ref)
+
+
+# ------------------------------------------------------------------ F-stage (Eq. FFTofE)
+
+def _pfb_case(seed, A, P, C, ntaps, F):
+    rng = np.random.default_rng(seed)
+    M = 2 * C
+    adc = synth.adc_stream(rng, A, P, (F + ntaps - 1) * M, sigma=20.0,
+                           tones=[(5.0 / M, 30.0), ((C // 3 + 0.25) / M, 25.0)])
+    return adc
+
+
+@pytest.mark.parametrize("C,ntaps,A,P,F", [(32, 4, 5, 2, 9), (256, 8, 3, 2, 5), (1024, 8, 17, 2, 4), (2048, 8, 2, 1, 3)])
+def test_fstage_spectra_and_codes(C, ntaps, A, P, F):
+    adc = _pfb_case(40 + C, A, P, C, ntaps, F)
+    M = 2 * C
+    h = oracle.pfb_window(ntaps, M).astype(np.float32).astype(np.float64)
+    X = oracle.pfb_spectra(adc, h, ntaps, M)                           # [A, P, F, C]
+    Xr = np.transpose(X, (2, 3, 0, 1))                                  # [F, C, A, P]
+    scale = 2.0 / np.std(np.abs(X))
+    pos = np.zeros((A, 2))
+    with moff.Plan(pos, np.ones((A, P, 1, 1)), 32, C, P, fstage=True) as pl:
+        pl.set_fstage(ntaps, None, scale)
+        spec = pl.channelise(adc, kind=1)
+        codes = pl.channelise(adc, kind=0)
+        pl.set_fstage(ntaps, h.astype(np.float32), scale)
+        codes2 = pl.channelise(adc, kind=0)
+    den = np.abs(Xr).max(axis=(0, 1))
+    assert (np.abs(spec - Xr).max(axis=(0, 1)) <= 1e-5 * den).all()
+    re, im = oracle.quantise_4bit(Xr, np.float32(scale))
+    z = oracle.unpack_4bit(codes)
+    amb = oracle.ambiguous_codes(Xr, np.float32(scale), 1e-3)
+    dr, di = np.abs(z.real - re), np.abs(z.imag - im)
+    assert (dr[~amb] == 0).all() and (di[~amb] == 0).all()
+    assert dr.max() <= 1 and di.max() <= 1
+    assert np.array_equal(codes, codes2)
+
+
+def test_adc_to_image_end_to_end():
+    """ADC -> F-stage -> image.  The seed is the first one (from a fixed start)
+    whose oracle spectra have no component within 1e-4 of a rounding boundary,
+    so the 4-bit codes are unique and the image must match to the FP32 bar."""
+    A, P, C, ntaps, F, N = 24, 2, 64, 4, 16, 32
+    M = 2 * C
+    h = oracle.pfb_window(ntaps, M).astype(np.float32).astype(np.float64)
+    for seed in range(500, 600):
+        adc = _pfb_case(seed, A, P, C, ntaps, F)
+        X = oracle.pfb_spectra(adc, h, ntaps, M)
+        scale = np.float32(0.09)
+        if not oracle.ambiguous_codes(X, scale, 1e-4).any():
+            break
+    else:
+        pytest.skip("no boundary-free seed in range")
+    codes_ref, _ = oracle.channelise(adc, h, ntaps, M, scale)
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(4, 28, size=(A, 2))
+    taps = c64(rng.normal(size=(A, P, 3, 3)) + 1j * rng.normal(size=(A, P, 3, 3)))
+    gains = c64(synth.gains_random(rng, C, A, P))
+    with moff.Plan(pos, taps, N, C, P, fstage=True) as pl:
+        pl.set_fstage(ntaps, None, float(scale))
+        pl.set_gains(gains)
+        pl.submit_adc(adc)
+        img, n = pl.read_image()
+    assert n == F
+    ref = oracle.moff_image(codes_ref, gains, pos, taps, N, P)
+    assert_image(img, ref)
+
+
+# ------------------------------------------------------------------ errors and fault injection (host side)
+
+def test_state_and_argument_errors_on_gpu():
+    pos, taps, codes, gains = random_case(50, 10, 32, 3, 1, C=2, T=2)
+    with moff.Plan(pos, taps, 32, 2, 1) as pl:
+        with pytest.raises(moff.MoffError) as e:
+            pl.submit_adc(np.zeros((10, 1, 4096), np.int8))
+        assert e.value.status == -4
+        with pytest.raises(moff.MoffError) as e:
+            moff.moff_submit(pl.handle, np.zeros((0, 2, 10, 1), np.uint8))
+        assert e.value.status == -1
+        with pytest.raises(moff.MoffError):
+            pl.grid_snapshot(np.ascontiguousarray(codes[0]), 5)
+    with moff.Plan(pos, taps, 32, 64, 1, fstage=True) as pl:
+        with pytest.raises(moff.MoffError) as e:
+            pl.submit_adc(np.zeros((10, 1, 1000), np.int8))      # not a multiple of M
+        assert e.value.status == -1
+        with pytest.raises(moff.MoffError) as e:
+            pl.submit_adc(np.zeros((10, 1, 128 * 3), np.int8))   # shorter than the filter
+        assert e.value.status == -1
+
+
+def test_allocation_failure_is_reported_and_recoverable():
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, paper_0812_3669_gb300 as m\n"
+        "pos=np.zeros((4,2)); taps=np.ones((4,1,3,3))\n"
+        "try:\n    m.Plan(pos,taps,32,2,1)\n    print('NOFAIL')\n"
+        "except m.MoffError as e:\n    print('STATUS', e.status)\n"
+        "p=m.Plan(pos,taps,32,2,1); p.submit(np.zeros((2,2,4,1),np.uint8)); img,n=p.read_image(); print('OK', n)\n"
+    )
+    env = dict(os.environ, MOFF_FAULT="alloc:3")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
+    assert "STATUS -2" in r.stdout, r.stdout + r.stderr
+    assert "OK 2" in r.stdout, r.stdout + r.stderr
