@@ -717,7 +717,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     {
         const size_t per = (size_t)n_pol * grid_n * grid_n * 8;
         long long budget = 8192LL << 20;
-        if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, atoll(e)) << 20;
+        if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, (long long)(atof(e) * 1048576.0));
         const long long cb = std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per)));
         const long long tb = std::max(1LL, std::min<long long>(64, budget / (long long)(cb * per)));
         pl->Cb = (int)cb;
