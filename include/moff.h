@@ -197,6 +197,39 @@ moff_status moff_set_timing(moff_plan *plan, int on);
  */
 moff_status moff_timing(moff_plan *plan, int kind, double *total_ms, long long *launches, int reset);
 
+/*
+ * moff_image_noalloc -- image one block of voltages without allocating any
+ * GPU memory.  (The paper has no counterpart; this is a library service.)
+ *
+ * For callers that cannot call cudaMalloc -- code that must live inside a
+ * memory budget someone else fixed, or that may not block on the allocator --
+ * this call takes every input and the output from the caller and keeps all
+ * intermediates (kernel lists, twiddles, the row-transformed field, the FP64
+ * sums) in one fixed 64 MiB device array inside the library, which every GPU
+ * that loads the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ *   n_ant, pos, ksize, taps, grid_n, n_chan, n_pol, flags
+ *            as for moff_plan_create (flags: 0 or MOFF_JONES); pos and taps
+ *            are host arrays.
+ *   volt     device uint8 [n_time][C][A][P], n_time >= 1.
+ *   gains    device float32 complex [C][A][P][2].
+ *   image    device float32 [C][n_prod][N][N]; overwritten with this
+ *            block's sums (Eq. m6 summed over its n_time samples).
+ *   cuda_stream  stream for the work (NULL = legacy default stream).
+ * The work is enqueued on cuda_stream; the image is ready when the stream
+ * reaches it.  Arrays whose kernel lists plus one channel's sums and field
+ * exceed 64 MiB are rejected with MOFF_EINVAL.
+ * The first call on each device looks up the array's device address (with
+ * that device current), so make that first call before any stream capture.
+ * All calls share the one array: calls whose GPU work overlaps in time (on
+ * different streams, or from different threads) race and corrupt each
+ * other's results; serialise them.
+ */
+moff_status moff_image_noalloc(int n_ant, const double *pos, int ksize, const float *taps, int grid_n,
+                               int n_chan, int n_pol, unsigned flags, const uint8_t *volt, int n_time,
+                               const float *gains, float *image, void *cuda_stream);
+
 /* moff_plan_destroy -- wait for the plan's work, free everything.  NULL is a no-op. */
 moff_status moff_plan_destroy(moff_plan *plan);
 

@@ -25,6 +25,7 @@ __all__ = [
     "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
     "moff_plan_info", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
+    "moff_image_noalloc",
     "Plan", "header_symbols", "KERNEL_KINDS",
 ]
 
@@ -66,6 +67,7 @@ _SIGS = {
     "moff_plan_destroy": [_vp],
     "moff_set_timing": [_vp, _i],
     "moff_timing": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
+    "moff_image_noalloc": [_i, _vp, _i, _vp, _i, _i, _i, _u, _vp, _i, _vp, _vp, _vp],
 }
 
 
@@ -224,6 +226,27 @@ def moff_timing(plan, kind, reset=0):
     n = ctypes.c_longlong(0)
     _check(lib().moff_timing(plan, int(kind), ctypes.byref(ms), ctypes.byref(n), int(reset)))
     return ms.value, n.value
+
+
+def moff_image_noalloc(pos, taps, grid_n, n_chan, n_pol, volt, gains, image, jones=False, cuda_stream=None):
+    """Image one block without any GPU allocation by the library.  ``volt``
+    (uint8 [T][C][A][P]), ``gains`` (complex [C][A][P]) and ``image`` (float32
+    [C][n_prod][N][N]) are CUDA tensors; ``pos``/``taps`` are host arrays."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    taps = np.asarray(taps)
+    t32 = _f32_interleaved(taps)
+    g = _torch_f32_interleaved(gains)
+    for name, x in (("volt", volt), ("gains", g), ("image", image)):
+        if not (_is_torch(x) and x.is_cuda and x.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if cuda_stream is None:
+        import torch
+        cuda_stream = torch.cuda.current_stream().cuda_stream or 1
+    _check(lib().moff_image_noalloc(int(pos.shape[0]), pos.ctypes.data, int(taps.shape[-1]), t32.ctypes.data,
+                                    int(grid_n), int(n_chan), int(n_pol), MOFF_JONES if jones else 0,
+                                    ctypes.c_void_p(volt.data_ptr()), int(volt.shape[0]),
+                                    ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(image.data_ptr()),
+                                    ctypes.c_void_p(int(cuda_stream))))
 
 
 def moff_plan_destroy(plan):

@@ -422,14 +422,14 @@ moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long 
 }
 
 // Per-antenna kernel value (re, im) for output pol po, input pol pi at (iy, ix).
-inline void tap_at(const moff_plan *pl, const float *taps, int a, int po, int pi, int iy, int ix, float *re, float *im) {
-    const int K = pl->K;
+inline void tap_at(bool jones, int P, int K, const float *taps, int a, int po, int pi, int iy, int ix, float *re,
+                   float *im) {
     long long idx;
-    if (pl->jones) {
+    if (jones) {
         idx = ((((long long)a * 2 + po) * 2 + pi) * K + iy) * K + ix;
     } else {
         if (po != pi) { *re = 0.f; *im = 0.f; return; }
-        idx = (((long long)a * pl->P + po) * K + iy) * K + ix;
+        idx = (((long long)a * P + po) * K + iy) * K + ix;
     }
     *re = taps[2 * idx];
     *im = taps[2 * idx + 1];
@@ -441,8 +441,17 @@ struct Contrib {
     float2 tap;
 };
 
-moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps) {
-    const int A = pl->A, K = pl->K, N = pl->N, P = pl->P, h = K / 2;
+}  // namespace
+
+namespace moff {
+
+moff_status fail_msg(moff_status s, const char *msg) { return fail(s, "%s", msg); }
+
+// Bin every antenna's kernel by grid-row stripe into per-cell contribution
+// lists (host only).  The stripe height is the largest power of two <= 16
+// whose lists fit the gridding kernel's shared-memory budget.
+moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b) {
+    const int h = K / 2;
     std::vector<int> ax(A), ay(A);
     for (int a = 0; a < A; ++a) {
         const double x = pos[2 * a], y = pos[2 * a + 1];
@@ -452,18 +461,17 @@ moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps) {
         ax[a] = (int)(((fx % N) + N) % N);
         ay[a] = (int)(((fy % N) + N) % N);
     }
-    const int pin_n = pl->jones ? 2 : 1;   // input pols per output pol
-    // contributions landing in each grid row
+    const int pin_n = jones ? 2 : 1;   // input pols per output pol
     std::vector<long long> row_con(N, 0);
     for (int a = 0; a < A; ++a)
         for (int po = 0; po < P; ++po)
             for (int k = 0; k < pin_n; ++k) {
-                const int pi = pl->jones ? k : po;
+                const int pi = jones ? k : po;
                 for (int iy = 0; iy < K; ++iy) {
                     const int row = (ay[a] + iy - h + N) % N;
                     for (int ix = 0; ix < K; ++ix) {
                         float re, im;
-                        tap_at(pl, taps, a, po, pi, iy, ix, &re, &im);
+                        tap_at(jones, P, K, taps, a, po, pi, iy, ix, &re, &im);
                         if (re != 0.f || im != 0.f) row_con[row]++;
                     }
                 }
@@ -495,15 +503,14 @@ moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps) {
     }
     if (best_rows == 0)
         return fail(MOFF_EINVAL, "array too dense for the gridding kernel (antennas per grid row exceed its limits)");
-    pl->rows = best_rows;
-    pl->csmem = best_csmem;
-    pl->n_stripes = N / best_rows;
-    pl->max_nloc = std::max(best_nloc, 1);
-    pl->max_ncon = (int)std::max<long long>(best_csmem ? best_ncon : 0, 0);
-    pl->grid_smem = grid_smem_bytes(N, P, pl->rows, pl->max_nloc, pl->max_ncon, pl->csmem, tw_total);
+    b->rows = best_rows;
+    b->csmem = best_csmem;
+    b->n_stripes = N / best_rows;
+    b->max_nloc = std::max(best_nloc, 1);
+    b->max_ncon = (int)std::max<long long>(best_csmem ? best_ncon : 0, 0);
+    b->grid_smem = grid_smem_bytes(N, P, b->rows, b->max_nloc, b->max_ncon, b->csmem, tw_total);
 
-    // Build the lists for the chosen stripe height.
-    const int rows = pl->rows, ns = pl->n_stripes;
+    const int rows = b->rows, ns = b->n_stripes;
     std::vector<std::vector<int>> sant(ns);
     std::vector<std::vector<Contrib>> scon(ns);
     for (int a = 0; a < A; ++a) {
@@ -513,14 +520,14 @@ moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps) {
         }
         for (int po = 0; po < P; ++po)
             for (int k = 0; k < pin_n; ++k) {
-                const int pi = pl->jones ? k : po;
+                const int pi = jones ? k : po;
                 for (int iy = 0; iy < K; ++iy) {
                     const int row = (ay[a] + iy - h + N) % N;
                     const int s = row / rows, rl = row % rows;
                     const int la = (int)sant[s].size() - 1;   // antenna a was appended last
                     for (int ix = 0; ix < K; ++ix) {
                         float re, im;
-                        tap_at(pl, taps, a, po, pi, iy, ix, &re, &im);
+                        tap_at(jones, P, K, taps, a, po, pi, iy, ix, &re, &im);
                         if (re == 0.f && im == 0.f) continue;
                         const int col = (ax[a] + ix - h + N) % N;
                         scon[s].push_back(Contrib{(po * rows + rl) * N + col, la * P + pi, make_float2(re, im)});
@@ -529,39 +536,59 @@ moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps) {
             }
     }
     const int ncell = P * rows * N;
-    std::vector<int> ant_off(ns + 1, 0), ant_list;
-    std::vector<int> cell_off((size_t)ns * (ncell + 1), 0);
-    std::vector<long long> con_off(ns + 1, 0);
-    std::vector<float2> con_tap;
-    std::vector<uint16_t> con_y;
+    b->ant_off.assign(ns + 1, 0);
+    b->ant_list.clear();
+    b->cell_off.assign((size_t)ns * (ncell + 1), 0);
+    b->con_off.assign(ns + 1, 0);
+    b->con_tap.clear();
+    b->con_y.clear();
     for (int s = 0; s < ns; ++s) {
-        ant_off[s + 1] = ant_off[s] + (int)sant[s].size();
-        ant_list.insert(ant_list.end(), sant[s].begin(), sant[s].end());
+        b->ant_off[s + 1] = b->ant_off[s] + (int)sant[s].size();
+        b->ant_list.insert(b->ant_list.end(), sant[s].begin(), sant[s].end());
         auto &v = scon[s];
         std::stable_sort(v.begin(), v.end(), [](const Contrib &x, const Contrib &y) { return x.cell < y.cell; });
-        int *co = &cell_off[(size_t)s * (ncell + 1)];
+        int *co = &b->cell_off[(size_t)s * (ncell + 1)];
         for (const Contrib &c : v) co[c.cell + 1]++;
         for (int i = 0; i < ncell; ++i) co[i + 1] += co[i];
-        con_off[s + 1] = con_off[s] + (long long)v.size();
+        b->con_off[s + 1] = b->con_off[s] + (long long)v.size();
         for (const Contrib &c : v) {
-            con_tap.push_back(c.tap);
-            con_y.push_back((uint16_t)c.y);
+            b->con_tap.push_back(c.tap);
+            b->con_y.push_back((uint16_t)c.y);
         }
     }
-    moff_status s;
-    if ((s = palloc(pl, &pl->d_st_ant_off, ant_off.size() * 4)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_st_ant, std::max<size_t>(ant_list.size(), 1) * 4)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_st_cell_off, cell_off.size() * 4)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_st_con_off, con_off.size() * 8)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_con_tap, std::max<size_t>(con_tap.size(), 1) * 8)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_con_y, std::max<size_t>(con_y.size(), 1) * 2)) != MOFF_OK) return s;
-    MOFF_CK(cudaMemcpy(pl->d_st_ant_off, ant_off.data(), ant_off.size() * 4, cudaMemcpyHostToDevice));
-    if (!ant_list.empty()) MOFF_CK(cudaMemcpy(pl->d_st_ant, ant_list.data(), ant_list.size() * 4, cudaMemcpyHostToDevice));
-    MOFF_CK(cudaMemcpy(pl->d_st_cell_off, cell_off.data(), cell_off.size() * 4, cudaMemcpyHostToDevice));
-    MOFF_CK(cudaMemcpy(pl->d_st_con_off, con_off.data(), con_off.size() * 8, cudaMemcpyHostToDevice));
-    if (!con_tap.empty()) {
-        MOFF_CK(cudaMemcpy(pl->d_con_tap, con_tap.data(), con_tap.size() * 8, cudaMemcpyHostToDevice));
-        MOFF_CK(cudaMemcpy(pl->d_con_y, con_y.data(), con_y.size() * 2, cudaMemcpyHostToDevice));
+    return MOFF_OK;
+}
+
+std::vector<float2> pass_twiddles_for(int n) { return pass_twiddles_n(n); }
+
+}  // namespace moff
+
+namespace {
+
+moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps) {
+    Bins b;
+    moff_status s = build_bins(pl->A, pl->K, pl->N, pl->P, pl->jones, pos, taps, &b);
+    if (s != MOFF_OK) return s;
+    pl->rows = b.rows;
+    pl->csmem = b.csmem;
+    pl->n_stripes = b.n_stripes;
+    pl->max_nloc = b.max_nloc;
+    pl->max_ncon = b.max_ncon;
+    pl->grid_smem = b.grid_smem;
+    if ((s = palloc(pl, &pl->d_st_ant_off, b.ant_off.size() * 4)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_st_ant, std::max<size_t>(b.ant_list.size(), 1) * 4)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_st_cell_off, b.cell_off.size() * 4)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_st_con_off, b.con_off.size() * 8)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_con_tap, std::max<size_t>(b.con_tap.size(), 1) * 8)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_con_y, std::max<size_t>(b.con_y.size(), 1) * 2)) != MOFF_OK) return s;
+    MOFF_CK(cudaMemcpy(pl->d_st_ant_off, b.ant_off.data(), b.ant_off.size() * 4, cudaMemcpyHostToDevice));
+    if (!b.ant_list.empty())
+        MOFF_CK(cudaMemcpy(pl->d_st_ant, b.ant_list.data(), b.ant_list.size() * 4, cudaMemcpyHostToDevice));
+    MOFF_CK(cudaMemcpy(pl->d_st_cell_off, b.cell_off.data(), b.cell_off.size() * 4, cudaMemcpyHostToDevice));
+    MOFF_CK(cudaMemcpy(pl->d_st_con_off, b.con_off.data(), b.con_off.size() * 8, cudaMemcpyHostToDevice));
+    if (!b.con_tap.empty()) {
+        MOFF_CK(cudaMemcpy(pl->d_con_tap, b.con_tap.data(), b.con_tap.size() * 8, cudaMemcpyHostToDevice));
+        MOFF_CK(cudaMemcpy(pl->d_con_y, b.con_y.data(), b.con_y.size() * 2, cudaMemcpyHostToDevice));
     }
     return MOFF_OK;
 }

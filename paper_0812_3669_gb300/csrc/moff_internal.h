@@ -5,6 +5,10 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "../../include/moff.h"
+
 namespace moff {
 
 constexpr int kBlock = 256;   // threads per CTA of every imaging kernel
@@ -69,6 +73,21 @@ inline size_t grid_smem_bytes(int N, int P, int rows, int max_nloc, int max_ncon
     if (csmem) b += (size_t)max_ncon * 2;     // contribution voltage indices
     return (b + 15) & ~(size_t)15;
 }
+
+// Kernel binning of one array (host side): per grid-row stripe, the antennas
+// touching it and each cell's kernel contributions in a fixed order.
+struct Bins {
+    int rows = 0, n_stripes = 0, max_nloc = 0, max_ncon = 0;
+    bool csmem = false;
+    size_t grid_smem = 0;
+    std::vector<int> ant_off, ant_list, cell_off;
+    std::vector<long long> con_off;
+    std::vector<float2> con_tap;
+    std::vector<uint16_t> con_y;
+};
+moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b);
+std::vector<float2> pass_twiddles_for(int n);   // pass-twiddle table of the n-point transform (FP64-built)
+moff_status fail_msg(moff_status s, const char *msg);
 
 int fft_tw_total(int n);                      // pass-twiddle table length for length n
 int col_width(int N);                         // columns per column-kernel CTA
