@@ -49,8 +49,34 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--frames", type=int, default=WL["frames"], help=argparse.SUPPRESS)
+    ap.add_argument("--frames", type=int, default=WL["frames"],
+                    help="samples per step (smaller values give a profiling case, not a bench line)")
+    ap.add_argument("--channels", type=int, default=WL["n_chan"],
+                    help="channels (smaller values give a profiling case, not a bench line)")
     return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- multi-rank helpers
+
+def rank_info():
+    """(world, rank, local_rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of ``x`` over all ranks (the job ends when the slowest rank ends)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds_max):
+    """Whole-job throughput: every rank processes ``units_per_rank`` independent
+    units (replicas, weak scaling), and the job takes the slowest rank's time."""
+    return units_per_rank * world / seconds_max
 
 
 # ----------------------------------------------------------------------------- algorithmic work
@@ -224,9 +250,7 @@ def run_ours(args):
     import paper_0812_3669_gb300 as moff
     import synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_info()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -241,13 +265,16 @@ def run_ours(args):
         moff.build()
     barrier()
 
-    A, P, C, N, K, ntaps, F = (WL["n_ant"], WL["n_pol"], WL["n_chan"], WL["grid_n"], WL["ksize"], WL["ntaps"],
+    A, P, C, N, K, ntaps, F = (WL["n_ant"], WL["n_pol"], args.channels, WL["grid_n"], WL["ksize"], WL["ntaps"],
                                args.frames)
     M = 2 * C
     S = (F + ntaps - 1) * M
-    cfg = synth.config_dualpol()
+    cfg = synth.config_dualpol(n_chan=C)
     pos, taps, gains = cfg["pos"], cfg["taps"], cfg["gains"]
-    adc = synth.device_adc(SEED + 1000 * rank, pos, P, S, M, N)
+    adc = synth.device_adc(SEED + 1000 * rank, pos, P, S, M, N,
+                           sources=tuple((kx, ky, ch * C // WL["n_chan"], amp)
+                                         for (kx, ky, ch, amp) in ((40, 70, 100, 12.0), (90, 30, 600, 8.0),
+                                                                   (64, 64, 900, 6.0))))
 
     plan = moff.Plan(pos, taps, N, C, P, fstage=True)
     plan.set_gains(gains)
@@ -282,11 +309,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
 
     kern = {}
     for kind, name in moff.KERNEL_KINDS.items():
@@ -296,8 +319,7 @@ def run_ours(args):
     img, nsamp = plan.read_image(reset=True)
     assert nsamp == args.steps * F and np.isfinite(img).all()
 
-    units = args.steps * F * C * world
-    value = units / (ms_max / 1000.0)
+    value = job_rate(args.steps * F * C, world, ms_max / 1000.0)
     snaps = args.steps * F * C
     total_kernel_ms = sum(v["ms_total"] for v in kern.values())
     flops = {
@@ -345,12 +367,8 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             plan.submit_adc(adc_h)
             plan.read_image(out=out_h, reset=True)
-        dt = time.perf_counter() - t0
-        dt_t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
-        dt = float(dt_t.item())
-        e2e = {"value": args.e2e_steps * F * C * world / dt, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": job_rate(args.e2e_steps * F * C, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(adc_h.numel()), "d2h_bytes_per_step": int(out_h.numel() * 4),
                "steps": args.e2e_steps, "api": "moff_submit_adc(host pinned ADC) + moff_read_image(host)"}
     plan.close()

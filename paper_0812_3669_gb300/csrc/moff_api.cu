@@ -164,14 +164,14 @@ size_t col_smem_bytes(int N, int P) {
     return 0;
 }
 
-cudaError_t launch_grid(int N, int P, bool csmem, bool go, const GridArgs &a, int n_stripes, size_t smem,
+cudaError_t launch_grid(int N, int P, int TB, bool staged, bool go, const GridArgs &a, int n_stripes, size_t smem,
                         cudaStream_t st) {
     switch (N) {
-        case 32: return launch_grid_n32(P, csmem, go, a, n_stripes, smem, st);
-        case 64: return launch_grid_n64(P, csmem, go, a, n_stripes, smem, st);
-        case 128: return launch_grid_n128(P, csmem, go, a, n_stripes, smem, st);
-        case 256: return launch_grid_n256(P, csmem, go, a, n_stripes, smem, st);
-        case 512: return launch_grid_n512(P, csmem, go, a, n_stripes, smem, st);
+        case 32: return launch_grid_n32(P, TB, staged, go, a, n_stripes, smem, st);
+        case 64: return launch_grid_n64(P, TB, staged, go, a, n_stripes, smem, st);
+        case 128: return launch_grid_n128(P, TB, staged, go, a, n_stripes, smem, st);
+        case 256: return launch_grid_n256(P, TB, staged, go, a, n_stripes, smem, st);
+        case 512: return launch_grid_n512(P, TB, staged, go, a, n_stripes, smem, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -204,11 +204,12 @@ struct moff_plan {
     bool own_stream = false;
 
     // binning
-    int rows = 0, n_stripes = 0, max_nloc = 0, max_ncon = 0;
-    bool csmem = false;
+    int rows = 0, n_stripes = 0, max_nloc = 0, n_slices = 0, tb = 1, max_entries = 0;
+    bool staged = false;
     size_t grid_smem = 0;
-    int *d_st_ant_off = nullptr, *d_st_ant = nullptr, *d_st_cell_off = nullptr;
-    long long *d_st_con_off = nullptr;
+    int *d_st_ant_off = nullptr, *d_st_ant = nullptr;
+    long long *d_slice_off = nullptr;
+    uint16_t *d_lane_cell = nullptr;
     float2 *d_con_tap = nullptr;
     uint16_t *d_con_y = nullptr;
     float2 *d_twp = nullptr;
@@ -378,33 +379,40 @@ moff_status stage_done(moff_plan *pl, int i) {
     return wait_event(pl->ev_copied[i], -1);
 }
 
+// Gridding-kernel arguments of a plan for channels [c0, c0+nc), samples [t0, t0+nt).
+GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc) {
+    GridArgs g{};
+    g.volt = volt;
+    g.volt_tstride = tstride;
+    g.t0 = t0;
+    g.nt = nt;
+    g.c0 = c0;
+    g.nc = nc;
+    g.A = pl->A;
+    g.rows = pl->rows;
+    g.max_nloc = pl->max_nloc;
+    g.max_entries = pl->max_entries;
+    g.n_slices = pl->n_slices;
+    g.gains = pl->d_gains;
+    g.st_ant_off = pl->d_st_ant_off;
+    g.st_ant = pl->d_st_ant;
+    g.slice_off = pl->d_slice_off;
+    g.lane_cell = pl->d_lane_cell;
+    g.con_tap = pl->d_con_tap;
+    g.con_y = pl->d_con_y;
+    g.twp = pl->d_twp;
+    g.out = pl->d_H;
+    return g;
+}
+
 moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
         const int nc = std::min(pl->Cb, pl->C - c0);
         for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
             const int nt = std::min(pl->Tb, n_time - t0);
-            GridArgs g{};
-            g.volt = volt;
-            g.volt_tstride = tstride;
-            g.t0 = t0;
-            g.nt = nt;
-            g.c0 = c0;
-            g.nc = nc;
-            g.A = pl->A;
-            g.rows = pl->rows;
-            g.max_nloc = pl->max_nloc;
-            g.max_ncon = pl->max_ncon;
-            g.gains = pl->d_gains;
-            g.st_ant_off = pl->d_st_ant_off;
-            g.st_ant = pl->d_st_ant;
-            g.st_cell_off = pl->d_st_cell_off;
-            g.st_con_off = pl->d_st_con_off;
-            g.con_tap = pl->d_con_tap;
-            g.con_y = pl->d_con_y;
-            g.twp = pl->d_twp;
-            g.out = pl->d_H;
+            GridArgs g = grid_args(pl, volt, tstride, t0, nt, c0, nc);
             TimedLaunch tg(pl, 1);
-            MOFF_CK(launch_grid(pl->N, pl->P, pl->csmem, false, g, pl->n_stripes, pl->grid_smem, pl->st));
+            MOFF_CK(launch_grid(pl->N, pl->P, pl->tb, pl->staged, false, g, pl->n_stripes, pl->grid_smem, pl->st));
             tg.done();
             ColArgs ca{};
             ca.H = pl->d_H;
@@ -462,7 +470,11 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
         ay[a] = (int)(((fy % N) + N) % N);
     }
     const int pin_n = jones ? 2 : 1;   // input pols per output pol
-    std::vector<long long> row_con(N, 0);
+    const int tw_total = fft_tw_total(N);
+    const int F = grid_fft_rows(N);
+    const size_t budget = 110 * 1024;   // two CTAs per SM
+    // Contributions per grid cell (p_out, row, col), independent of the stripe shape.
+    std::vector<int> cnt_all((size_t)P * N * N, 0);
     for (int a = 0; a < A; ++a)
         for (int po = 0; po < P; ++po)
             for (int k = 0; k < pin_n; ++k) {
@@ -472,45 +484,73 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
                     for (int ix = 0; ix < K; ++ix) {
                         float re, im;
                         tap_at(jones, P, K, taps, a, po, pi, iy, ix, &re, &im);
-                        if (re != 0.f || im != 0.f) row_con[row]++;
+                        if (re != 0.f || im != 0.f) cnt_all[((size_t)po * N + row) * N + (ax[a] + ix - h + N) % N]++;
                     }
                 }
             }
-    const int tw_total = fft_tw_total(N);
-    const size_t budget = 110 * 1024;   // two CTAs per SM
-    int best_rows = 0;
-    bool best_csmem = false;
-    int best_nloc = 0;
-    long long best_ncon = 0;
-    for (int rows = std::min(16, N); rows >= 1; rows /= 2) {
+    // Stripe shape: F = TB * P * rows rows are transformed together.  Prefer
+    // kernel entries staged in shared memory, then more samples per pass.
+    struct Cand { int tb, rows, nloc; long long entries; size_t sm_staged, sm_plain; };
+    std::vector<Cand> cands;
+    for (int tb = 8; tb >= 1; tb /= 2) {
+        int rows = F / (tb * P);
+        if (rows < 1) continue;
+        rows = std::min(rows, N);
         const int ns = N / rows;
-        std::vector<int> nloc(ns, 0);
-        std::vector<long long> ncon(ns, 0);
-        std::vector<int> seen(ns, -1);
+        std::vector<int> nloc(ns, 0), seen(ns, -1);
         for (int a = 0; a < A; ++a)
             for (int iy = 0; iy < K; ++iy) {
                 const int s = ((ay[a] + iy - h + N) % N) / rows;
                 if (seen[s] != a) { seen[s] = a; nloc[s]++; }
             }
-        for (int r = 0; r < N; ++r) ncon[r / rows] += row_con[r];
-        const int mnl = *std::max_element(nloc.begin(), nloc.end());
-        const long long mnc = *std::max_element(ncon.begin(), ncon.end());
+        const int mnl = std::max(1, *std::max_element(nloc.begin(), nloc.end()));
         if ((long long)mnl * P >= 65536) continue;
-        const size_t with = grid_smem_bytes(N, P, rows, mnl, (int)std::min<long long>(mnc, 1 << 30), true, tw_total);
-        const size_t without = grid_smem_bytes(N, P, rows, mnl, 0, false, tw_total);
-        if (with <= budget) { best_rows = rows; best_csmem = true; best_nloc = mnl; best_ncon = mnc; break; }
-        if (without <= budget && best_rows == 0) { best_rows = rows; best_csmem = false; best_nloc = mnl; best_ncon = mnc; }
+        long long ment = 0;
+        std::vector<int> c((size_t)P * rows * N);
+        for (int s = 0; s < ns; ++s) {
+            size_t n = 0;
+            for (int po = 0; po < P; ++po)
+                for (int rl = 0; rl < rows; ++rl)
+                    for (int x = 0; x < N; ++x) c[n++] = cnt_all[((size_t)po * N + s * rows + rl) * N + x];
+            std::sort(c.begin(), c.end(), [](int x, int y) { return x > y; });
+            long long e = 0;
+            for (size_t k = 0; k < c.size(); k += 32) e += 32LL * c[k];
+            ment = std::max(ment, e);
+        }
+        Cand cd{tb, rows, mnl, ment, grid_smem_bytes(N, P, tb, rows, mnl, tw_total, (int)std::min<long long>(ment, 1 << 28)),
+                grid_smem_bytes(N, P, tb, rows, mnl, tw_total, 0)};
+        cands.push_back(cd);
     }
-    if (best_rows == 0)
+    // Entries are read through L2 by default (more CTAs per SM measured faster
+    // than shared-memory staging); MOFF_GRID_STAGE=1 prefers staging.
+    const char *stage_env = getenv("MOFF_GRID_STAGE");
+    const bool prefer_staged = stage_env && atoi(stage_env) != 0;
+    const Cand *pick = nullptr;
+    bool staged = false;
+    if (prefer_staged)
+        for (const Cand &cd : cands)
+            if (cd.sm_staged <= budget) { pick = &cd; staged = true; break; }
+    if (!pick)
+        for (const Cand &cd : cands)
+            if (cd.sm_plain <= budget || (cd.tb == 1 && cd.sm_plain <= 200 * 1024)) { pick = &cd; break; }
+    if (!pick)
         return fail(MOFF_EINVAL, "array too dense for the gridding kernel (antennas per grid row exceed its limits)");
-    b->rows = best_rows;
-    b->csmem = best_csmem;
-    b->n_stripes = N / best_rows;
-    b->max_nloc = std::max(best_nloc, 1);
-    b->max_ncon = (int)std::max<long long>(best_csmem ? best_ncon : 0, 0);
-    b->grid_smem = grid_smem_bytes(N, P, b->rows, b->max_nloc, b->max_ncon, b->csmem, tw_total);
+    if (pick->rows * pick->tb * P != F)
+        return fail(MOFF_EINVAL, "internal: stripe shape %d x %d x %d does not fill %d rows", pick->tb, P, pick->rows, F);
+    b->rows = pick->rows;
+    b->tb = pick->tb;
+    b->n_stripes = N / pick->rows;
+    b->max_nloc = pick->nloc;
+    b->staged = staged;
+    b->max_entries = staged ? (int)pick->entries : 0;
+    b->grid_smem = staged ? pick->sm_staged : pick->sm_plain;
 
+    // Per stripe: local antennas (ascending) and every cell's contributions,
+    // antenna-major within a cell.
     const int rows = b->rows, ns = b->n_stripes;
+    const int ncell = P * rows * N;                 // a multiple of 32 (N >= 32)
+    const int nsl = ncell / 32;
+    b->n_slices = nsl;
     std::vector<std::vector<int>> sant(ns);
     std::vector<std::vector<Contrib>> scon(ns);
     for (int a = 0; a < A; ++a) {
@@ -535,27 +575,48 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
                 }
             }
     }
-    const int ncell = P * rows * N;
     b->ant_off.assign(ns + 1, 0);
     b->ant_list.clear();
-    b->cell_off.assign((size_t)ns * (ncell + 1), 0);
-    b->con_off.assign(ns + 1, 0);
+    b->slice_off.assign((size_t)ns * nsl + 1, 0);
+    b->lane_cell.assign((size_t)ns * nsl * 32, 0);
     b->con_tap.clear();
     b->con_y.clear();
+    long long base = 0;
+    std::vector<int> cnt(ncell), start(ncell + 1), order(ncell);
     for (int s = 0; s < ns; ++s) {
         b->ant_off[s + 1] = b->ant_off[s] + (int)sant[s].size();
         b->ant_list.insert(b->ant_list.end(), sant[s].begin(), sant[s].end());
         auto &v = scon[s];
         std::stable_sort(v.begin(), v.end(), [](const Contrib &x, const Contrib &y) { return x.cell < y.cell; });
-        int *co = &b->cell_off[(size_t)s * (ncell + 1)];
-        for (const Contrib &c : v) co[c.cell + 1]++;
-        for (int i = 0; i < ncell; ++i) co[i + 1] += co[i];
-        b->con_off[s + 1] = b->con_off[s] + (long long)v.size();
-        for (const Contrib &c : v) {
-            b->con_tap.push_back(c.tap);
-            b->con_y.push_back((uint16_t)c.y);
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (const Contrib &c : v) cnt[c.cell]++;
+        start[0] = 0;
+        for (int i = 0; i < ncell; ++i) start[i + 1] = start[i] + cnt[i];
+        // cells by decreasing contribution count (ties by cell index) -> even slices
+        for (int i = 0; i < ncell; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cnt[x] > cnt[y]; });
+        for (int k = 0; k < nsl; ++k) {
+            const size_t si = (size_t)s * nsl + k;
+            b->slice_off[si] = base;
+            int len = 0;
+            for (int l = 0; l < 32; ++l) len = std::max(len, cnt[order[k * 32 + l]]);
+            for (int i = 0; i < len; ++i)
+                for (int l = 0; l < 32; ++l) {
+                    const int cell = order[k * 32 + l];
+                    if (i < cnt[cell]) {
+                        const Contrib &c = v[start[cell] + i];
+                        b->con_tap.push_back(c.tap);
+                        b->con_y.push_back((uint16_t)c.y);
+                    } else {
+                        b->con_tap.push_back(make_float2(0.f, 0.f));
+                        b->con_y.push_back(0);
+                    }
+                }
+            for (int l = 0; l < 32; ++l) b->lane_cell[si * 32 + l] = (uint16_t)order[k * 32 + l];
+            base += (long long)len * 32;
         }
     }
+    b->slice_off[(size_t)ns * nsl] = base;
     return MOFF_OK;
 }
 
@@ -570,22 +631,24 @@ moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps) {
     moff_status s = build_bins(pl->A, pl->K, pl->N, pl->P, pl->jones, pos, taps, &b);
     if (s != MOFF_OK) return s;
     pl->rows = b.rows;
-    pl->csmem = b.csmem;
+    pl->tb = b.tb;
+    pl->staged = b.staged;
+    pl->max_entries = b.max_entries;
     pl->n_stripes = b.n_stripes;
     pl->max_nloc = b.max_nloc;
-    pl->max_ncon = b.max_ncon;
+    pl->n_slices = b.n_slices;
     pl->grid_smem = b.grid_smem;
     if ((s = palloc(pl, &pl->d_st_ant_off, b.ant_off.size() * 4)) != MOFF_OK) return s;
     if ((s = palloc(pl, &pl->d_st_ant, std::max<size_t>(b.ant_list.size(), 1) * 4)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_st_cell_off, b.cell_off.size() * 4)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_st_con_off, b.con_off.size() * 8)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_slice_off, b.slice_off.size() * 8)) != MOFF_OK) return s;
+    if ((s = palloc(pl, &pl->d_lane_cell, b.lane_cell.size() * 2)) != MOFF_OK) return s;
     if ((s = palloc(pl, &pl->d_con_tap, std::max<size_t>(b.con_tap.size(), 1) * 8)) != MOFF_OK) return s;
     if ((s = palloc(pl, &pl->d_con_y, std::max<size_t>(b.con_y.size(), 1) * 2)) != MOFF_OK) return s;
     MOFF_CK(cudaMemcpy(pl->d_st_ant_off, b.ant_off.data(), b.ant_off.size() * 4, cudaMemcpyHostToDevice));
     if (!b.ant_list.empty())
         MOFF_CK(cudaMemcpy(pl->d_st_ant, b.ant_list.data(), b.ant_list.size() * 4, cudaMemcpyHostToDevice));
-    MOFF_CK(cudaMemcpy(pl->d_st_cell_off, b.cell_off.data(), b.cell_off.size() * 4, cudaMemcpyHostToDevice));
-    MOFF_CK(cudaMemcpy(pl->d_st_con_off, b.con_off.data(), b.con_off.size() * 8, cudaMemcpyHostToDevice));
+    MOFF_CK(cudaMemcpy(pl->d_slice_off, b.slice_off.data(), b.slice_off.size() * 8, cudaMemcpyHostToDevice));
+    MOFF_CK(cudaMemcpy(pl->d_lane_cell, b.lane_cell.data(), b.lane_cell.size() * 2, cudaMemcpyHostToDevice));
     if (!b.con_tap.empty()) {
         MOFF_CK(cudaMemcpy(pl->d_con_tap, b.con_tap.data(), b.con_tap.size() * 8, cudaMemcpyHostToDevice));
         MOFF_CK(cudaMemcpy(pl->d_con_y, b.con_y.data(), b.con_y.size() * 2, cudaMemcpyHostToDevice));
@@ -743,7 +806,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     // row-transform scratch: Tb samples x Cb channels per chunk
     {
         const size_t per = (size_t)n_pol * grid_n * grid_n * 8;
-        long long budget = 8192LL << 20;
+        long long budget = 16384LL << 20;
         if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, (long long)(atof(e) * 1048576.0));
         const long long cb = std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per)));
         const long long tb = std::max(1LL, std::min<long long>(64, budget / (long long)(cb * per)));
@@ -914,27 +977,8 @@ moff_status moff_grid_snapshot(moff_plan *pl, const uint8_t *volt, int on_device
         if ((s = stage_in(pl, volt, bytes, &dev, &slot)) != MOFF_OK) return s;
         src = reinterpret_cast<const uint8_t *>(dev);
     }
-    GridArgs g{};
-    g.volt = src;
-    g.volt_tstride = 0;
-    g.t0 = 0;
-    g.nt = 1;
-    g.c0 = chan;
-    g.nc = 1;
-    g.A = pl->A;
-    g.rows = pl->rows;
-    g.max_nloc = pl->max_nloc;
-    g.max_ncon = pl->max_ncon;
-    g.gains = pl->d_gains;
-    g.st_ant_off = pl->d_st_ant_off;
-    g.st_ant = pl->d_st_ant;
-    g.st_cell_off = pl->d_st_cell_off;
-    g.st_con_off = pl->d_st_con_off;
-    g.con_tap = pl->d_con_tap;
-    g.con_y = pl->d_con_y;
-    g.twp = pl->d_twp;
-    g.out = pl->d_H;
-    MOFF_CK(launch_grid(pl->N, pl->P, pl->csmem, true, g, pl->n_stripes, pl->grid_smem, pl->st));
+    GridArgs g = grid_args(pl, src, 0, 0, 1, chan, 1);
+    MOFF_CK(launch_grid(pl->N, pl->P, pl->tb, false, true, g, pl->n_stripes, pl->grid_smem, pl->st));
     if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
     MOFF_CK(cudaMemcpyAsync(out, pl->d_H, (size_t)pl->P * pl->N * pl->N * 8, cudaMemcpyDeviceToHost, pl->st));
     return sync_plan(pl, -1);

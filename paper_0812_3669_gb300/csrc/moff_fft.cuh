@@ -161,4 +161,25 @@ __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
 template <int N>
 struct PaddedLen { static constexpr int value = N + N / 16; };
 
+// pad16(j + r*NSL) for slot j < NSL of a pass reading at stride NSL = N/R:
+// the padding term splits into a per-slot part and a compile-time part.
+template <int NSL>
+__device__ __forceinline__ int pad_load(int j, int r) {
+    if constexpr (NSL >= 16) return pad16(j) + r * (NSL + NSL / 16);
+    else return j + r * NSL + ((r * NSL) >> 4);   // j + (r*NSL mod 16) < 16
+}
+
+// pad16(stockham_out<R, NS>(j, r)) with the r-dependent part at compile time.
+template <int R, int NS>
+__device__ __forceinline__ int pad_store(int j, int r) {
+    if constexpr (NS >= 16) {
+        return pad16(stockham_out<R, NS>(j, 0)) + r * (NS + NS / 16);
+    } else if constexpr (NS * R >= 16) {
+        const int H = (j / NS) * NS * R, L = j % NS;   // H a multiple of 16, L + (r*NS mod 16) < 16
+        return H + H / 16 + L + r * NS + ((r * NS) >> 4);
+    } else {
+        return pad16(stockham_out<R, NS>(j, r));
+    }
+}
+
 }  // namespace moff

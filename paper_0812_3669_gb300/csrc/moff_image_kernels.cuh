@@ -4,9 +4,10 @@
 //   k_grid_rows : step 1 (complex weight per antenna), step 2 (scatter through
 //                 each antenna's kernel, written as a deterministic gather per
 //                 grid cell) and the first axis of step 3 (row transforms).
-//                 One CTA = one stripe of grid rows of one channel; it keeps
-//                 the stripe's kernel taps in shared memory and walks a chunk
-//                 of time samples, so taps are read once per chunk.
+//                 One CTA = one stripe of grid rows of one channel walking a
+//                 chunk of samples TB at a time: each kernel entry is read
+//                 once (coalesced, sliced-ELL order, from L2) per TB samples,
+//                 and the TB x P x rows rows are transformed in place.
 //   k_cols_acc  : second axis of step 3 (column transforms) fused with step 4
 //                 (|E|^2 and the cross-pol products summed over the chunk in
 //                 registers, then added to FP64 accumulators).
@@ -23,142 +24,220 @@ __device__ __forceinline__ float2 decode4(uint32_t b) {
     return make_float2((float)(hi - ((hi & 8) << 1)), (float)(lo - ((lo & 8) << 1)));
 }
 
-template <int N, int P, bool CSMEM, bool GRID_ONLY>
+// One Stockham pass over the F rows held in shared memory (row f at
+// src + f*LDR, padded index) into dst, or -- LAST -- into the global row
+// returned by `rowptr(f)` (nullptr: row not stored).  Ends with a barrier
+// unless LAST.
+template <int N, int F, int R, int NS, bool LAST, class RowPtr>
+__device__ __forceinline__ void rows_pass(const float2 *src, float2 *dst, const float2 *tw, RowPtr rowptr) {
+    constexpr int LDR = PaddedLen<N>::value;
+    constexpr int NSL = N / R;
+    constexpr int SLOTS = F * NSL;
+    for (int sl = threadIdx.x; sl < SLOTS; sl += kBlock) {
+        const int f = sl / NSL, j = sl - f * NSL;
+        const float2 *in = src + f * LDR;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in[pad_load<NSL>(j, r)];
+        twiddle<R, NS, 1>(v, j, tw);
+        dft<R, 1>(v);
+        if constexpr (LAST) {
+            float2 *o = rowptr(f);
+            if (o) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) o[j + r * NSL] = v[r];
+            }
+        } else {
+            float2 *out = dst + f * LDR;
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[pad_store<R, NS>(j, r)] = v[r];
+        }
+    }
+    if constexpr (!LAST) __syncthreads();
+}
+
+// Stripe height of the gridding kernel: TB samples x P pols x ROWS rows = F rows per pass.
+template <int N, int P, int TB>
+struct GridShape {
+    static constexpr int FR = N >= 256 ? 8 : (N == 128 ? 16 : 32);   // == grid_fft_rows(N)
+    static constexpr int ROWS_ = FR / (TB * P);
+    static constexpr int ROWS = ROWS_ < 1 ? 1 : (ROWS_ > N ? N : ROWS_);
+    static constexpr int PR = P * ROWS;
+    static constexpr int F = TB * PR;
+};
+
+template <int N, int P, int TB, bool STAGED, bool GRID_ONLY>
 __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     using FP = FftPlan<N>;
     using TW = FftTw<N>;
+    using GS = GridShape<N, P, TB>;
     constexpr int LDR = PaddedLen<N>::value;
+    constexpr int YS = VoltStride<TB>::value;
+    constexpr int ROWS = GS::ROWS, PR = GS::PR, F = GS::F;
+    constexpr int YPT = 2;                // voltages per thread whose bytes are prefetched
 
     const int s = blockIdx.x;
     const int cl = blockIdx.y;
     const int c = a.c0 + cl;
     const int tid = threadIdx.x;
-    const int rows = a.rows;
-    const int nf = P * rows;
-    const int ncell = nf * N;
+    const int lane = tid & 31, warp = tid >> 5;
     const int ant0 = a.st_ant_off[s];
     const int nloc = a.st_ant_off[s + 1] - ant0;
-    const long long con0 = a.st_con_off[s];
-    const int ncon = (int)(a.st_con_off[s + 1] - con0);
-    const int *cell_off_g = a.st_cell_off + (long long)s * (ncell + 1);
+    const int nyi = nloc * P;
+    const int nsl = a.n_slices;
+    const long long *soff = a.slice_off + (long long)s * nsl;
+    const uint16_t *lcell = a.lane_cell + (long long)s * nsl * 32;
+    const long long e0 = soff[0];
 
     // Carve (matches grid_smem_bytes).
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *s_tw = reinterpret_cast<float2 *>(smem);
-    float2 *s_buf0 = s_tw + TW::TOTAL;
-    float2 *s_buf1 = s_buf0 + nf * LDR;
-    float2 *s_y = s_buf1 + nf * LDR;
-    float2 *s_g = s_y + a.max_nloc * P;
-    float2 *s_tap = s_g + a.max_nloc * P;
-    int *s_off = reinterpret_cast<int *>(s_tap + (CSMEM ? a.max_ncon : 0));
-    int *s_ant = s_off + (ncell + 1);
-    uint16_t *s_cy = reinterpret_cast<uint16_t *>(s_ant + a.max_nloc);
+    float2 *s_buf = s_tw + TW::TOTAL;                  // gridded rows
+    float2 *s_alt = s_buf + F * LDR;                   // second buffer of the row passes
+    float2 *s_y = s_alt + ((F * LDR + 1) & ~1);        // [nloc*P][YS]: TB samples, padded row (16-byte aligned)
+    float2 *s_g = s_y + YS * a.max_nloc * P;
+    float2 *s_tap = s_g + a.max_nloc * P;              // staged kernel values
+    int *s_ant = reinterpret_cast<int *>(s_tap + (STAGED ? a.max_entries : 0));
+    uint16_t *s_cy = reinterpret_cast<uint16_t *>(s_ant + a.max_nloc);   // staged voltage indices
 
     for (int i = tid; i < TW::TOTAL; i += kBlock) s_tw[i] = a.twp[i];
-    for (int i = tid; i <= ncell; i += kBlock) s_off[i] = cell_off_g[i];
     for (int i = tid; i < nloc; i += kBlock) s_ant[i] = a.st_ant[ant0 + i];
-    for (int i = tid; i < nloc * P; i += kBlock) {
+    for (int i = tid; i < nyi; i += kBlock) {
         const int la = i / P, q = i - la * P;
-        const int ant = a.st_ant[ant0 + la];
-        s_g[i] = a.gains[((long long)c * a.A + ant) * P + q];
+        s_g[i] = a.gains[((long long)c * a.A + a.st_ant[ant0 + la]) * P + q];
     }
-    if constexpr (CSMEM) {
-        for (int i = tid; i < ncon; i += kBlock) {
-            s_tap[i] = a.con_tap[con0 + i];
-            s_cy[i] = a.con_y[con0 + i];
+    if constexpr (STAGED) {
+        const int ne = (int)(soff[nsl] - e0);
+        for (int i = tid; i < ne; i += kBlock) {
+            s_tap[i] = __ldg(a.con_tap + e0 + i);
+            s_cy[i] = __ldg(a.con_y + e0 + i);
         }
     }
     __syncthreads();
-    const float2 *tap = CSMEM ? s_tap : a.con_tap + con0;
-    const uint16_t *cy = CSMEM ? s_cy : a.con_y + con0;
 
-    for (int tt = 0; tt < a.nt; ++tt) {
+    // Voltage bytes: thread owns local voltages yi = tid + m*kBlock and their TB samples.
+    const bool pre = nyi <= YPT * kBlock;
+    const uint8_t *vchan = a.volt + (long long)c * a.A * P;
+    uint32_t vb[YPT][TB];
+    auto fetch = [&](int tbn) {
+        const int nbn = min(TB, a.nt - tbn);
+#pragma unroll
+        for (int m = 0; m < YPT; ++m) {
+            const int yi = tid + m * kBlock;
+            const int la = yi / P, q = yi - la * P;
+            const uint8_t *src = vchan + (long long)(a.t0 + tbn) * a.volt_tstride +
+                                 (yi < nyi ? (long long)s_ant[la] * P + q : 0);
+#pragma unroll
+            for (int t = 0; t < TB; ++t) vb[m][t] = (yi < nyi && t < nbn) ? src[t * a.volt_tstride] : 0u;
+        }
+    };
+    if (pre) fetch(0);
+
+    const int ry0 = s * ROWS;
+    for (int tb0 = 0; tb0 < a.nt; tb0 += TB) {
+        const int nb = min(TB, a.nt - tb0);
         // Step 1: decode and weight the voltages of the antennas touching this stripe.
-        const uint8_t *vrow = a.volt + (long long)(a.t0 + tt) * a.volt_tstride + (long long)c * a.A * P;
-        for (int i = tid; i < nloc * P; i += kBlock) {
-            const int la = i / P, q = i - la * P;
-            s_y[i] = cmul(s_g[i], decode4(vrow[(long long)s_ant[la] * P + q]));
+        if (pre) {
+#pragma unroll
+            for (int m = 0; m < YPT; ++m) {
+                const int yi = tid + m * kBlock;
+                if (yi < nyi) {
+                    const float2 g = s_g[yi];
+                    float2 *yrow = s_y + yi * YS;
+#pragma unroll
+                    for (int t = 0; t < TB; ++t) yrow[t] = t < nb ? cmul(g, decode4(vb[m][t])) : make_float2(0.f, 0.f);
+                }
+            }
+            if (tb0 + TB < a.nt) fetch(tb0 + TB);     // in flight during this pass
+        } else {
+            for (int yi = tid; yi < nyi; yi += kBlock) {
+                const int la = yi / P, q = yi - la * P;
+                const float2 g = s_g[yi];
+                const uint8_t *src = vchan + (long long)(a.t0 + tb0) * a.volt_tstride + (long long)s_ant[la] * P + q;
+                float2 *yrow = s_y + yi * YS;
+                for (int t = 0; t < TB; ++t)
+                    yrow[t] = t < nb ? cmul(g, decode4(src[t * a.volt_tstride])) : make_float2(0.f, 0.f);
+            }
         }
         __syncthreads();
-        // Step 2: each grid cell sums its kernel contributions in a fixed order.
-        for (int cell = tid; cell < ncell; cell += kBlock) {
-            float2 acc = make_float2(0.f, 0.f);
-            const int k1 = s_off[cell + 1];
-            for (int k = s_off[cell]; k < k1; ++k) {
-                const float2 t = tap[k];
-                const float2 y = s_y[cy[k]];
-                acc.x = fmaf(t.x, y.x, fmaf(-t.y, y.y, acc.x));
-                acc.y = fmaf(t.x, y.y, fmaf(t.y, y.x, acc.y));
+        // Step 2: every cell sums its kernel contributions (fixed order), for TB
+        // samples.  Entries are fetched U at a time so their latencies overlap.
+        for (int k = warp; k < nsl; k += kBlock / 32) {
+            const long long b0 = soff[k];
+            const int len = (int)((soff[k + 1] - b0) >> 5);
+            const int cell = lcell[k * 32 + lane];
+            const float2 *tp = (STAGED ? s_tap + (b0 - e0) : a.con_tap + b0) + lane;
+            const uint16_t *yp = (STAGED ? s_cy + (b0 - e0) : a.con_y + b0) + lane;
+            float2 acc[TB];
+#pragma unroll
+            for (int t = 0; t < TB; ++t) acc[t] = make_float2(0.f, 0.f);
+            constexpr int U = 4;
+            for (int i0 = 0; i0 < len; i0 += U) {
+                float2 tv[U];
+                int yv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const bool ok = i0 + u < len;
+                    if constexpr (STAGED) {
+                        tv[u] = ok ? tp[32 * (i0 + u)] : make_float2(0.f, 0.f);
+                        yv[u] = ok ? (int)yp[32 * (i0 + u)] : 0;
+                    } else {
+                        tv[u] = ok ? __ldg(tp + 32 * (i0 + u)) : make_float2(0.f, 0.f);
+                        yv[u] = ok ? (int)__ldg(yp + 32 * (i0 + u)) : 0;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float2 *yy = s_y + yv[u] * YS;
+                    if constexpr (TB >= 2) {
+#pragma unroll
+                        for (int t = 0; t < TB; t += 2) {
+                            const float4 q = *reinterpret_cast<const float4 *>(yy + t);
+                            acc[t].x = fmaf(tv[u].x, q.x, fmaf(-tv[u].y, q.y, acc[t].x));
+                            acc[t].y = fmaf(tv[u].x, q.y, fmaf(tv[u].y, q.x, acc[t].y));
+                            acc[t + 1].x = fmaf(tv[u].x, q.z, fmaf(-tv[u].y, q.w, acc[t + 1].x));
+                            acc[t + 1].y = fmaf(tv[u].x, q.w, fmaf(tv[u].y, q.z, acc[t + 1].y));
+                        }
+                    } else {
+                        const float2 y = yy[0];
+                        acc[0].x = fmaf(tv[u].x, y.x, fmaf(-tv[u].y, y.y, acc[0].x));
+                        acc[0].y = fmaf(tv[u].x, y.y, fmaf(tv[u].y, y.x, acc[0].y));
+                    }
+                }
             }
             const int f = cell / N, e = cell - f * N;
-            s_buf0[f * LDR + pad16(e)] = acc;
+            float2 *dst = s_buf + f * LDR + pad16(e);
+#pragma unroll
+            for (int t = 0; t < TB; ++t) dst[t * PR * LDR] = acc[t];
         }
         __syncthreads();
 
-        const int ry0 = s * rows;
-        float2 *outc = a.out + (long long)(tt * a.nc + cl) * P * N * N;
+        // Global row of transform row fa = t*PR + p*ROWS + rl (nullptr past the chunk).
+        float2 *outb = a.out;
+        auto rowptr = [&](int fa) -> float2 * {
+            const int t = fa / PR, f = fa - t * PR;
+            if (t >= nb) return nullptr;
+            const int p = f / ROWS, rl = f - p * ROWS;
+            return outb + (((long long)(tb0 + t) * a.nc + cl) * P * N + (long long)p * N + ry0 + rl) * N;
+        };
         if constexpr (GRID_ONLY) {
-            for (int i = tid; i < ncell; i += kBlock) {
-                const int f = i / N, e = i - f * N;
-                const int p = f / rows, rl = f - p * rows;
-                outc[((long long)p * N + ry0 + rl) * N + e] = s_buf0[f * LDR + pad16(e)];
+            for (int i = tid; i < F * N; i += kBlock) {
+                const int fa = i / N, e = i - fa * N;
+                float2 *o = rowptr(fa);
+                if (o) o[e] = s_buf[fa * LDR + pad16(e)];
             }
             __syncthreads();
             continue;
         }
-
-        // Step 3, first axis: N-point transform of every row (Stockham passes).
-        {
-            constexpr int R = FP::R0, NSL = N / R;
-            for (int sl = tid; sl < nf * NSL; sl += kBlock) {
-                const int f = sl / NSL, j = sl - f * NSL;
-                const float2 *src = s_buf0 + f * LDR;
-                float2 v[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) v[r] = src[pad16(j + r * NSL)];
-                dft<R, 1>(v);
-                float2 *dst = s_buf1 + f * LDR;
-#pragma unroll
-                for (int r = 0; r < R; ++r) dst[pad16(stockham_out<R, 1>(j, r))] = v[r];
-            }
-        }
-        __syncthreads();
+        // Step 3, first axis: N-point transform of every row (ping-pong buffers).
+        rows_pass<N, F, FP::R0, 1, false>(s_buf, s_alt, s_tw, rowptr);
         if constexpr (FP::NP == 3) {
-            constexpr int R = FP::R1, NS = FP::R0, NSL = N / R;
-            for (int sl = tid; sl < nf * NSL; sl += kBlock) {
-                const int f = sl / NSL, j = sl - f * NSL;
-                const float2 *src = s_buf1 + f * LDR;
-                float2 v[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) v[r] = src[pad16(j + r * NSL)];
-                twiddle<R, NS, 1>(v, j, s_tw + TW::OFF1);
-                dft<R, 1>(v);
-                float2 *dst = s_buf0 + f * LDR;
-#pragma unroll
-                for (int r = 0; r < R; ++r) dst[pad16(stockham_out<R, NS>(j, r))] = v[r];
-            }
-            __syncthreads();
+            rows_pass<N, F, FP::R1, FP::R0, false>(s_alt, s_buf, s_tw + TW::OFF1, rowptr);
+            rows_pass<N, F, FP::R2, FP::R0 * FP::R1, true>(s_buf, nullptr, s_tw + TW::OFF2, rowptr);
+        } else {
+            rows_pass<N, F, FP::R1, FP::R0, true>(s_alt, nullptr, s_tw + TW::OFF1, rowptr);
         }
-        {
-            constexpr int R = FP::NP == 3 ? FP::R2 : FP::R1;
-            constexpr int NS = N / R;
-            const float2 *srcb = FP::NP == 3 ? s_buf0 : s_buf1;
-            const float2 *tw = s_tw + (FP::NP == 3 ? TW::OFF2 : TW::OFF1);
-            for (int sl = tid; sl < nf * NS; sl += kBlock) {
-                const int f = sl / NS, j = sl - f * NS;
-                const float2 *src = srcb + f * LDR;
-                float2 v[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) v[r] = src[pad16(j + r * NS)];
-                twiddle<R, NS, 1>(v, j, tw);
-                dft<R, 1>(v);
-                const int p = f / rows, rl = f - p * rows;
-                float2 *dst = outc + ((long long)p * N + ry0 + rl) * N;
-#pragma unroll
-                for (int r = 0; r < R; ++r) dst[j + r * NS] = v[r];
-            }
-        }
-        __syncthreads();
+        // (the next iteration's first barrier orders these reads before any rewrite)
     }
 }
 
@@ -170,6 +249,15 @@ struct ColShape {
     static constexpr int NS = N / RL;                          // slots per column in the last pass
 };
 
+// 16-byte asynchronous global -> shared copies (completion tracked per group).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
+
 template <int N, int P>
 __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
     using FP = FftPlan<N>;
@@ -178,6 +266,9 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
     constexpr int W = CS::W;
     constexpr int RL = CS::RL;
     constexpr int NPROD = P == 1 ? 1 : 4;
+    constexpr int TILE = P * N * W;                 // float2 per sample: [P][N][W]
+    constexpr int CHUNKS = TILE * 8 / 16;           // 16-byte pieces per tile
+    constexpr int ROWCH = W * 8 / 16;               // pieces per tile row
 
     const int kx0 = blockIdx.x * W;
     const int cl = blockIdx.y;
@@ -186,10 +277,21 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
 
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *s_tw = reinterpret_cast<float2 *>(smem);
-    float2 *s_a = s_tw + TW::TOTAL;            // [P][N][W]
-    float2 *s_b = s_a + P * N * W;             // second buffer (3-pass lengths only)
+    float2 *s_in = s_tw + ((TW::TOTAL + 1) & ~1);  // 2 staging tiles (16-byte aligned)
+    float2 *s_a = s_in + 2 * TILE;                 // pass outputs
+    float2 *s_b = s_a + TILE;                      // second pass buffer (3-pass lengths only)
 
     for (int i = tid; i < TW::TOTAL; i += kBlock) s_tw[i] = a.twp[i];
+
+    // Stage sample tt's [P][N][W] tile of the row-transformed field.
+    auto stage = [&](int tt, float2 *dst) {
+        const float2 *src = a.H + (long long)(tt * a.nc + cl) * P * N * N + kx0;
+        for (int q = tid; q < CHUNKS; q += kBlock) {
+            const int row = q / ROWCH, part = q - row * ROWCH;       // row = p*N + ry
+            cp_async16(dst + row * W + part * 2, src + (long long)row * N + part * 2);
+        }
+        cp_async_commit();
+    };
 
     float acc[NPROD][RL];
 #pragma unroll
@@ -198,11 +300,18 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
         for (int r = 0; r < RL; ++r) acc[q][r] = 0.f;
 
     const int colL = tid % W, jL = tid / W;
-    __syncthreads();
+    if (a.nt > 0) stage(0, s_in);
 
     for (int tt = 0; tt < a.nt; ++tt) {
-        const float2 *Hc = a.H + (long long)(tt * a.nc + cl) * P * N * N + kx0;
-        {   // pass 0: global -> registers -> shared
+        if (tt + 1 < a.nt) {
+            stage(tt + 1, s_in + ((tt + 1) & 1) * TILE);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float2 *tin = s_in + (tt & 1) * TILE;
+        {   // pass 0: staged tile -> registers -> s_a
             constexpr int R = FP::R0, NSL = N / R;
             for (int sl = tid; sl < W * NSL; sl += kBlock) {
                 const int col = sl % W, j = sl / W;
@@ -210,7 +319,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                 for (int p = 0; p < P; ++p) {
                     float2 v[R];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = Hc[((long long)p * N + j + r * NSL) * N + col];
+                    for (int r = 0; r < R; ++r) v[r] = tin[(p * N + j + r * NSL) * W + col];
                     dft<R, 1>(v);
 #pragma unroll
                     for (int r = 0; r < R; ++r) s_a[(p * N + stockham_out<R, 1>(j, r)) * W + col] = v[r];
@@ -262,7 +371,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                 }
             }
         }
-        __syncthreads();
+        // s_a is rewritten by the next pass 0 only after the next barrier.
     }
 
     // Fold this chunk's FP32 sums into the FP64 accumulators (one owner per pixel).
@@ -281,17 +390,38 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
 template <int N>
 size_t col_smem_bytes_t(int P) {
     using FP = FftPlan<N>;
-    const size_t buf = (size_t)P * N * ColShape<N>::W * 8;
-    return (size_t)FftTw<N>::TOTAL * 8 + buf * (FP::NP == 3 ? 2 : 1);
+    const size_t tile = (size_t)P * N * ColShape<N>::W * 8;
+    return (size_t)((FftTw<N>::TOTAL + 1) & ~1) * 8 + tile * 2 + tile * (FP::NP == 3 ? 2 : 1);
 }
 
-template <int N, int P, bool CSMEM, bool GO>
+template <int N, int P, int TB, bool ST, bool GO>
 cudaError_t launch_grid_t(const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st) {
-    auto k = k_grid_rows<N, P, CSMEM, GO>;
+    auto k = k_grid_rows<N, P, TB, ST, GO>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<dim3(n_stripes, a.nc), kBlock, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int N, int P, bool ST, bool GO>
+cudaError_t launch_grid_s(int TB, const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st) {
+    switch (TB) {
+        case 1: return launch_grid_t<N, P, 1, ST, GO>(a, n_stripes, smem, st);
+        case 2: return launch_grid_t<N, P, 2, ST, GO>(a, n_stripes, smem, st);
+        case 4: return launch_grid_t<N, P, 4, ST, GO>(a, n_stripes, smem, st);
+        case 8: return launch_grid_t<N, P, 8, ST, GO>(a, n_stripes, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The stripe height is a compile-time function of TB, so the grid-only
+// variant runs with the plan's TB too (and stores only the first sample).
+template <int N, int P>
+cudaError_t launch_grid_p(int TB, bool staged, bool go, const GridArgs &a, int n_stripes, size_t smem,
+                          cudaStream_t st) {
+    if (go) return launch_grid_s<N, P, false, true>(TB, a, n_stripes, smem, st);
+    return staged ? launch_grid_s<N, P, true, false>(TB, a, n_stripes, smem, st)
+                  : launch_grid_s<N, P, false, false>(TB, a, n_stripes, smem, st);
 }
 
 template <int N, int P>
@@ -305,18 +435,10 @@ cudaError_t launch_cols_t(const ColArgs &a, cudaStream_t st) {
 }
 
 #define MOFF_DEFINE_N(NN)                                                                            \
-    cudaError_t launch_grid_n##NN(int P, bool csmem, bool go, const GridArgs &a, int n_stripes,        \
+    cudaError_t launch_grid_n##NN(int P, int TB, bool staged, bool go, const GridArgs &a, int n_stripes, \
                                   size_t smem, cudaStream_t st) {                                    \
-        if (P == 1) {                                                                                \
-            if (go) return csmem ? launch_grid_t<NN, 1, true, true>(a, n_stripes, smem, st)          \
-                                 : launch_grid_t<NN, 1, false, true>(a, n_stripes, smem, st);        \
-            return csmem ? launch_grid_t<NN, 1, true, false>(a, n_stripes, smem, st)                 \
-                         : launch_grid_t<NN, 1, false, false>(a, n_stripes, smem, st);               \
-        }                                                                                            \
-        if (go) return csmem ? launch_grid_t<NN, 2, true, true>(a, n_stripes, smem, st)              \
-                             : launch_grid_t<NN, 2, false, true>(a, n_stripes, smem, st);            \
-        return csmem ? launch_grid_t<NN, 2, true, false>(a, n_stripes, smem, st)                     \
-                     : launch_grid_t<NN, 2, false, false>(a, n_stripes, smem, st);                   \
+        return P == 1 ? launch_grid_p<NN, 1>(TB, staged, go, a, n_stripes, smem, st)                 \
+                      : launch_grid_p<NN, 2>(TB, staged, go, a, n_stripes, smem, st);                \
     }                                                                                                \
     cudaError_t launch_cols_n##NN(int P, const ColArgs &a, cudaStream_t st) {                        \
         return P == 1 ? launch_cols_t<NN, 1>(a, st) : launch_cols_t<NN, 2>(a, st);                   \

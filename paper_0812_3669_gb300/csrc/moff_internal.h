@@ -15,7 +15,10 @@ constexpr int kBlock = 256;   // threads per CTA of every imaging kernel
 constexpr int kPfbGroup = 32; // antenna-pols per F-stage CTA
 
 // Gridding + row transform (Eq. m6 steps 1-3, first axis).  One CTA owns
-// one stripe of `rows` grid rows of one channel and walks `nt` samples.
+// one stripe of `rows` grid rows of one channel and walks `nt` samples, TB at
+// a time.  Kernel contributions are stored per stripe in 32-cell slices
+// (sliced ELL): entry i of lane l of a slice sits at slice_off + 32 i + l, so
+// a warp reads 32 consecutive entries per step.
 struct GridArgs {
     const uint8_t *volt;      // voltages; sample t of channel c at volt + t*volt_tstride + c*A*P
     long long volt_tstride;   // bytes between consecutive samples
@@ -23,13 +26,15 @@ struct GridArgs {
     int c0, nc;               // first channel and channel count of this launch
     int A;                    // antennas
     int rows;                 // grid rows per stripe
-    int max_nloc, max_ncon;   // per-stripe maxima (shared-memory carve)
+    int max_nloc;             // most antennas touching one stripe (shared-memory carve)
+    int max_entries;          // most sliced-ELL entries of one stripe (shared-memory carve, if staged)
+    int n_slices;             // 32-cell slices per stripe = P*rows*N/32
     const float2 *gains;      // [C][A][P]
     const int *st_ant_off;    // [n_stripes + 1]
-    const int *st_ant;        // antennas touching each stripe
-    const int *st_cell_off;   // [n_stripes][P*rows*N + 1] contribution offsets per cell
-    const long long *st_con_off; // [n_stripes + 1]
-    const float2 *con_tap;    // kernel value of each contribution
+    const int *st_ant;        // antennas touching each stripe, ascending
+    const long long *slice_off; // [n_stripes * n_slices + 1] first entry of each slice
+    const uint16_t *lane_cell;  // [n_stripes * n_slices * 32] stripe cell of each lane
+    const float2 *con_tap;    // kernel value of each entry (0 for padding)
     const uint16_t *con_y;    // local voltage index (local antenna * P + input pol)
     const float2 *twp;        // pass twiddles of the N-point transform
     float2 *out;              // [nt][nc][P][N][N] row-transformed (or raw, grid-only) field
@@ -59,29 +64,38 @@ struct PfbArgs {
     float2 *spec;             // [F][C][AP]
 };
 
+// Row stride (in float2) of the TB calibrated voltages of one antenna-pol in
+// shared memory: padded so that rows of a warp's random gathers spread over
+// all banks; even, so rows are 16-byte aligned for float4 reads.
+template <int TB> struct VoltStride { static constexpr int value = TB == 1 ? 1 : (TB == 8 ? 10 : 6); };
+inline int volt_stride(int TB) { return TB == 1 ? 1 : (TB == 8 ? 10 : 6); }
+
+// Rows transformed together by one gridding CTA: TB samples x P pols x rows.
+inline int grid_fft_rows(int N) { return N >= 256 ? 8 : (N == 128 ? 16 : 32); }
+
 // Shared-memory bytes of the gridding kernel (host and device agree on the carve).
-inline size_t grid_smem_bytes(int N, int P, int rows, int max_nloc, int max_ncon, bool csmem, int tw_total) {
+inline size_t grid_smem_bytes(int N, int P, int TB, int rows, int max_nloc, int tw_total, int staged_entries = 0) {
     const int ldr = N + N / 16;
-    const size_t nf = (size_t)P * rows;
     size_t b = 0;
+    b += (size_t)staged_entries * 10;         // kernel entries staged in shared memory (float2 + u16)
     b += (size_t)tw_total * 8;
-    b += 2 * nf * ldr * 8;                    // ping-pong row buffers
-    b += (size_t)max_nloc * P * 8 * 2;        // calibrated voltages + gains
-    if (csmem) b += (size_t)max_ncon * 8;     // contribution kernel values
-    b += (size_t)(nf * N + 1) * 4;            // cell offsets
+    b += 2 * (size_t)TB * P * rows * ldr * 8 + 8; // ping-pong row buffers of TB samples (+ alignment)
+    b += (size_t)volt_stride(TB) * max_nloc * P * 8;   // calibrated voltages of TB samples
+    b += (size_t)max_nloc * P * 8;            // gains
     b += (size_t)max_nloc * 4;                // antenna indices
-    if (csmem) b += (size_t)max_ncon * 2;     // contribution voltage indices
     return (b + 15) & ~(size_t)15;
 }
 
 // Kernel binning of one array (host side): per grid-row stripe, the antennas
-// touching it and each cell's kernel contributions in a fixed order.
+// touching it and each cell's kernel contributions in a fixed order, packed
+// as sliced ELL with cells sorted by contribution count.
 struct Bins {
-    int rows = 0, n_stripes = 0, max_nloc = 0, max_ncon = 0;
-    bool csmem = false;
+    int rows = 0, n_stripes = 0, tb = 1, max_nloc = 0, n_slices = 0, max_entries = 0;
+    bool staged = false;   // kernel entries staged in shared memory
     size_t grid_smem = 0;
-    std::vector<int> ant_off, ant_list, cell_off;
-    std::vector<long long> con_off;
+    std::vector<int> ant_off, ant_list;
+    std::vector<long long> slice_off;
+    std::vector<uint16_t> lane_cell;
     std::vector<float2> con_tap;
     std::vector<uint16_t> con_y;
 };
@@ -95,7 +109,7 @@ size_t col_smem_bytes(int N, int P);
 size_t pfb_smem_bytes(int CN);
 
 // Launchers (return the launch error, if any).
-cudaError_t launch_grid(int N, int P, bool csmem, bool grid_only, const GridArgs &a, int n_stripes,
+cudaError_t launch_grid(int N, int P, int TB, bool staged, bool grid_only, const GridArgs &a, int n_stripes,
                         size_t smem, cudaStream_t st);
 cudaError_t launch_cols(int N, int P, const ColArgs &a, cudaStream_t st);
 cudaError_t launch_pfb(int CN, const PfbArgs &a, cudaStream_t st);
@@ -103,7 +117,7 @@ cudaError_t launch_to_f32(const double *acc, float *out, long long n, cudaStream
 
 // Per-N instantiations (one translation unit each, compiled in parallel).
 #define MOFF_DECLARE_N(NN)                                                                          \
-    cudaError_t launch_grid_n##NN(int P, bool csmem, bool grid_only, const GridArgs &a, int n_stripes, \
+    cudaError_t launch_grid_n##NN(int P, int TB, bool staged, bool grid_only, const GridArgs &a, int n_stripes, \
                                   size_t smem, cudaStream_t st);                                   \
     cudaError_t launch_cols_n##NN(int P, const ColArgs &a, cudaStream_t st);
 MOFF_DECLARE_N(32)

@@ -101,8 +101,8 @@ extern "C" moff_status moff_image_noalloc(int n_ant, const double *pos, int ksiz
     const size_t o_tw = off;        off = align256(off + tw.size() * 8);
     const size_t o_ant_off = off;   off = align256(off + b.ant_off.size() * 4);
     const size_t o_ant = off;       off = align256(off + std::max<size_t>(b.ant_list.size(), 1) * 4);
-    const size_t o_cell = off;      off = align256(off + b.cell_off.size() * 4);
-    const size_t o_con_off = off;   off = align256(off + b.con_off.size() * 8);
+    const size_t o_soff = off;      off = align256(off + b.slice_off.size() * 8);
+    const size_t o_lcell = off;     off = align256(off + b.lane_cell.size() * 2);
     const size_t o_tap = off;       off = align256(off + std::max<size_t>(b.con_tap.size(), 1) * 8);
     const size_t o_cy = off;        off = align256(off + std::max<size_t>(b.con_y.size(), 1) * 2);
     const size_t fixed = off;
@@ -135,8 +135,8 @@ extern "C" moff_status moff_image_noalloc(int n_ant, const double *pos, int ksiz
     NA_CK(cudaMemcpyAsync(sc + o_ant_off, b.ant_off.data(), b.ant_off.size() * 4, cudaMemcpyHostToDevice, st));
     if (!b.ant_list.empty())
         NA_CK(cudaMemcpyAsync(sc + o_ant, b.ant_list.data(), b.ant_list.size() * 4, cudaMemcpyHostToDevice, st));
-    NA_CK(cudaMemcpyAsync(sc + o_cell, b.cell_off.data(), b.cell_off.size() * 4, cudaMemcpyHostToDevice, st));
-    NA_CK(cudaMemcpyAsync(sc + o_con_off, b.con_off.data(), b.con_off.size() * 8, cudaMemcpyHostToDevice, st));
+    NA_CK(cudaMemcpyAsync(sc + o_soff, b.slice_off.data(), b.slice_off.size() * 8, cudaMemcpyHostToDevice, st));
+    NA_CK(cudaMemcpyAsync(sc + o_lcell, b.lane_cell.data(), b.lane_cell.size() * 2, cudaMemcpyHostToDevice, st));
     if (!b.con_tap.empty()) {
         NA_CK(cudaMemcpyAsync(sc + o_tap, b.con_tap.data(), b.con_tap.size() * 8, cudaMemcpyHostToDevice, st));
         NA_CK(cudaMemcpyAsync(sc + o_cy, b.con_y.data(), b.con_y.size() * 2, cudaMemcpyHostToDevice, st));
@@ -160,17 +160,18 @@ extern "C" moff_status moff_image_noalloc(int n_ant, const double *pos, int ksiz
             g.A = n_ant;
             g.rows = b.rows;
             g.max_nloc = b.max_nloc;
-            g.max_ncon = b.max_ncon;
+            g.max_entries = b.max_entries;
+            g.n_slices = b.n_slices;
             g.gains = reinterpret_cast<const float2 *>(gains);
             g.st_ant_off = reinterpret_cast<const int *>(sc + o_ant_off);
             g.st_ant = reinterpret_cast<const int *>(sc + o_ant);
-            g.st_cell_off = reinterpret_cast<const int *>(sc + o_cell);
-            g.st_con_off = reinterpret_cast<const long long *>(sc + o_con_off);
+            g.slice_off = reinterpret_cast<const long long *>(sc + o_soff);
+            g.lane_cell = reinterpret_cast<const uint16_t *>(sc + o_lcell);
             g.con_tap = reinterpret_cast<const float2 *>(sc + o_tap);
             g.con_y = reinterpret_cast<const uint16_t *>(sc + o_cy);
             g.twp = reinterpret_cast<const float2 *>(sc + o_tw);
             g.out = reinterpret_cast<float2 *>(sc + o_H);
-            NA_CK(launch_grid(N, P, b.csmem, false, g, b.n_stripes, b.grid_smem, st));
+            NA_CK(launch_grid(N, P, b.tb, b.staged, false, g, b.n_stripes, b.grid_smem, st));
             ColArgs ca{};
             ca.H = reinterpret_cast<const float2 *>(sc + o_H);
             ca.nt = nt;
