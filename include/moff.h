@@ -230,6 +230,19 @@ moff_status moff_image_noalloc(int n_ant, const double *pos, int ksize, const fl
                                int n_chan, int n_pol, unsigned flags, const uint8_t *volt, int n_time,
                                const float *gains, float *image, void *cuda_stream);
 
+/*
+ * moff_tc_selftest -- diagnostic: one tensor-core product D = A * B^T with the
+ * building blocks the FP16 DFT kernels use (canonical K-major operands in
+ * shared memory, TMEM accumulator, tcgen05.mma kind::f16, completion through
+ * an mbarrier with a bounded wait, tcgen05.ld).  The paper has no
+ * counterpart; it checks the tensor-core path against a host reference.
+ *   a  device half [128][k];  b  device half [n][k];  d  device float [128][n].
+ *   n  multiple of 32 in [32, 256];  k  multiple of 16 in [16, 256].
+ * Synchronous on cuda_stream.  MOFF_ETIMEDOUT if the product did not finish
+ * within the wait limit (a few seconds).
+ */
+moff_status moff_tc_selftest(const void *a, const void *b, float *d, int n, int k, void *cuda_stream);
+
 /* moff_plan_destroy -- wait for the plan's work, free everything.  NULL is a no-op. */
 moff_status moff_plan_destroy(moff_plan *plan);
 

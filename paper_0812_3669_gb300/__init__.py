@@ -25,7 +25,7 @@ __all__ = [
     "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
     "moff_plan_info", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
-    "moff_image_noalloc",
+    "moff_image_noalloc", "moff_tc_selftest",
     "Plan", "header_symbols", "KERNEL_KINDS",
 ]
 
@@ -68,6 +68,7 @@ _SIGS = {
     "moff_set_timing": [_vp, _i],
     "moff_timing": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
     "moff_image_noalloc": [_i, _vp, _i, _vp, _i, _i, _i, _u, _vp, _i, _vp, _vp, _vp],
+    "moff_tc_selftest": [_vp, _vp, _vp, _i, _i, _vp],
 }
 
 
@@ -247,6 +248,17 @@ def moff_image_noalloc(pos, taps, grid_n, n_chan, n_pol, volt, gains, image, jon
                                     ctypes.c_void_p(volt.data_ptr()), int(volt.shape[0]),
                                     ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(image.data_ptr()),
                                     ctypes.c_void_p(int(cuda_stream))))
+
+
+def moff_tc_selftest(a, b, d, cuda_stream=None):
+    """D = A B^T on the tensor cores (diagnostic): ``a`` half [128][k], ``b`` half [n][k], ``d`` float [128][n]
+    (CUDA tensors)."""
+    if cuda_stream is None:
+        import torch
+        cuda_stream = torch.cuda.current_stream().cuda_stream or 1
+    _check(lib().moff_tc_selftest(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                  ctypes.c_void_p(d.data_ptr()), int(b.shape[0]), int(a.shape[1]),
+                                  ctypes.c_void_p(int(cuda_stream))))
 
 
 def moff_plan_destroy(plan):
