@@ -238,10 +238,13 @@ moff_status moff_image_noalloc(int n_ant, const double *pos, int ksize, const fl
  * counterpart; it checks the tensor-core path against a host reference.
  *   a  device half [128][k];  b  device half [n][k];  d  device float [128][n].
  *   n  multiple of 32 in [32, 256];  k  multiple of 16 in [16, 256].
+ *   mode  bit 0: stage A MN-major (then k <= 64); bit 1: stage B MN-major
+ *         (then k <= 64, n <= 128); bit 2: an MN-major operand's descriptor
+ *         carries its K-direction core-matrix stride as the leading byte offset.
  * Synchronous on cuda_stream.  MOFF_ETIMEDOUT if the product did not finish
  * within the wait limit (a few seconds).
  */
-moff_status moff_tc_selftest(const void *a, const void *b, float *d, int n, int k, void *cuda_stream);
+moff_status moff_tc_selftest(const void *a, const void *b, float *d, int n, int k, int mode, void *cuda_stream);
 
 /* moff_plan_destroy -- wait for the plan's work, free everything.  NULL is a no-op. */
 moff_status moff_plan_destroy(moff_plan *plan);

@@ -68,7 +68,7 @@ _SIGS = {
     "moff_set_timing": [_vp, _i],
     "moff_timing": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
     "moff_image_noalloc": [_i, _vp, _i, _vp, _i, _i, _i, _u, _vp, _i, _vp, _vp, _vp],
-    "moff_tc_selftest": [_vp, _vp, _vp, _i, _i, _vp],
+    "moff_tc_selftest": [_vp, _vp, _vp, _i, _i, _i, _vp],
 }
 
 
@@ -250,14 +250,14 @@ def moff_image_noalloc(pos, taps, grid_n, n_chan, n_pol, volt, gains, image, jon
                                     ctypes.c_void_p(int(cuda_stream))))
 
 
-def moff_tc_selftest(a, b, d, cuda_stream=None):
+def moff_tc_selftest(a, b, d, mode=0, cuda_stream=None):
     """D = A B^T on the tensor cores (diagnostic): ``a`` half [128][k], ``b`` half [n][k], ``d`` float [128][n]
     (CUDA tensors)."""
     if cuda_stream is None:
         import torch
         cuda_stream = torch.cuda.current_stream().cuda_stream or 1
     _check(lib().moff_tc_selftest(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
-                                  ctypes.c_void_p(d.data_ptr()), int(b.shape[0]), int(a.shape[1]),
+                                  ctypes.c_void_p(d.data_ptr()), int(b.shape[0]), int(a.shape[1]), int(mode),
                                   ctypes.c_void_p(int(cuda_stream))))
 
 

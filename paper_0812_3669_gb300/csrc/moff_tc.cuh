@@ -9,6 +9,10 @@
 //     base + (r/8) * SBO + (k/8) * 128
 // so the leading-dimension byte offset (between core matrices along K) is 128
 // and the stride-dimension byte offset (along rows) is SBO = (K/8) * 128.
+// An MN-major tile (rows contiguous for each k; see mnmajor_offset) takes
+// the K-direction core-matrix stride as its leading byte offset and the
+// row-direction stride (128) as its stride byte offset -- checked on the GPU
+// by the self-test, where the opposite reading gives a wrong product.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -24,6 +28,12 @@ __device__ __forceinline__ uint32_t kmajor_offset(int r, int k, int K) {
     return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// Byte offset of element (r, k) of an MN-major tile with R rows: core matrix
+// (r/8, k/8) holds, for each of its 8 k, the 16 bytes of 8 consecutive r.
+__device__ __forceinline__ uint32_t mnmajor_offset(int r, int k, int R) {
+    return (uint32_t)((r >> 3) * 128 + (k >> 3) * (R >> 3) * 128 + (k & 7) * 16 + (r & 7) * 2);
+}
+
 // Shared-memory matrix descriptor (tcgen05): start address, leading and
 // stride byte offsets (all >> 4), fixed version bits 46-48 = 0b001, no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -37,10 +47,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 
 // Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B, both
 // K-major, M x N tile (M = 64 or 128, N a multiple of 16 up to 256).
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool a_mn = false, bool b_mn = false) {
     return (1u << 4)                            // D format: F32
            | (0u << 7) | (0u << 10)            // A, B format: F16
-           | (0u << 15) | (0u << 16)           // A, B K-major
+           | ((a_mn ? 1u : 0u) << 15)          // A major-ness: 0 K-major, 1 MN-major
+           | ((b_mn ? 1u : 0u) << 16)          // B major-ness
            | ((uint32_t)(N >> 3) << 17)        // N / 8
            | ((uint32_t)(M >> 4) << 24);       // M / 16
 }

@@ -15,20 +15,33 @@ namespace {
 __device__ int g_selftest_err;   // time-out flag of the self-test kernel
 
 // D[128][N] = A[128][K] * B[N][K]^T (FP16 in, FP32 out).  128 threads.
+// mode bit 0: A staged MN-major; bit 1: B staged MN-major; bit 2: for an
+// MN-major operand, give the descriptor the K-direction core-matrix stride as
+// its leading byte offset (else the M/N-direction stride).  Operand regions
+// (region_a, region_b bytes) hold every byte either reading can reach.
 __global__ void __launch_bounds__(128) k_tc_selftest(const __half *__restrict__ A, const __half *__restrict__ B,
-                                                     float *__restrict__ D, int N, int K, int *err) {
+                                                     float *__restrict__ D, int N, int K, int mode, int region_a,
+                                                     int region_b, int *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sA = smem;                                 // 128 x K
-    unsigned char *sB = smem + 128 * K * 2;                   // N x K
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sB + N * K * 2);
+    unsigned char *sA = smem;
+    unsigned char *sB = smem + region_a;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sB + region_b);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t ncols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    const bool a_mn = mode & 1, b_mn = mode & 2, lbo_k = mode & 4;
 
-    for (int i = tid; i < 128 * K; i += blockDim.x)
-        *reinterpret_cast<__half *>(sA + tc::kmajor_offset(i / K, i % K, K)) = A[i];
-    for (int i = tid; i < N * K; i += blockDim.x)
-        *reinterpret_cast<__half *>(sB + tc::kmajor_offset(i / K, i % K, K)) = B[i];
+    for (int i = tid; i < region_a / 4; i += blockDim.x) reinterpret_cast<uint32_t *>(sA)[i] = 0u;
+    for (int i = tid; i < region_b / 4; i += blockDim.x) reinterpret_cast<uint32_t *>(sB)[i] = 0u;
+    __syncthreads();
+    for (int i = tid; i < 128 * K; i += blockDim.x) {
+        const int r = i / K, k = i % K;
+        *reinterpret_cast<__half *>(sA + (a_mn ? tc::mnmajor_offset(r, k, 128) : tc::kmajor_offset(r, k, K))) = A[i];
+    }
+    for (int i = tid; i < N * K; i += blockDim.x) {
+        const int r = i / K, k = i % K;
+        *reinterpret_cast<__half *>(sB + (b_mn ? tc::mnmajor_offset(r, k, N) : tc::kmajor_offset(r, k, K))) = B[i];
+    }
     tc::fence_async_smem();
     if (tid == 0) tc::mbar_init(mbar, 1);
     if (warp == 0) {
@@ -41,11 +54,21 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const __half *__restrict__ 
     const uint32_t tbase = *tslot;
 
     if (tid == 0) {
-        const uint32_t idesc = tc::idesc_f16(128, N);
-        const uint32_t sbo = (uint32_t)(K / 8) * 128;
+        const uint32_t idesc = tc::idesc_f16(128, N, a_mn, b_mn);
         for (int ks = 0; ks < K / 16; ++ks) {
-            const uint64_t ad = tc::smem_desc(tc::smem_u32(sA) + ks * 256, 128, sbo);
-            const uint64_t bd = tc::smem_desc(tc::smem_u32(sB) + ks * 256, 128, sbo);
+            uint64_t ad, bd;
+            if (a_mn) {   // strides: along M 128 B, along K (128/8)*128 B; a K-step of 16 = 2 core matrices along K
+                const uint32_t sm = 128, sk = 16 * 128;
+                ad = tc::smem_desc(tc::smem_u32(sA) + ks * 2 * sk, lbo_k ? sk : sm, lbo_k ? sm : sk);
+            } else {
+                ad = tc::smem_desc(tc::smem_u32(sA) + ks * 256, 128, (uint32_t)(K / 8) * 128);
+            }
+            if (b_mn) {
+                const uint32_t sn = 128, sk = (uint32_t)(N / 8) * 128;
+                bd = tc::smem_desc(tc::smem_u32(sB) + ks * 2 * sk, lbo_k ? sk : sn, lbo_k ? sn : sk);
+            } else {
+                bd = tc::smem_desc(tc::smem_u32(sB) + ks * 256, 128, (uint32_t)(K / 8) * 128);
+            }
             tc::mma_f16(tbase, ad, bd, idesc, ks > 0);
         }
         tc::mma_commit(mbar);
@@ -75,12 +98,22 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const __half *__restrict__ 
 
 using namespace moff;
 
-extern "C" moff_status moff_tc_selftest(const void *a, const void *b, float *d, int n, int k, void *cuda_stream) {
+extern "C" moff_status moff_tc_selftest(const void *a, const void *b, float *d, int n, int k, int mode,
+                                        void *cuda_stream) {
     if (!a || !b || !d) return fail_msg(MOFF_EINVAL, "a, b and d must not be NULL");
     if (n < 32 || n > 256 || n % 32 != 0) return fail_msg(MOFF_EINVAL, "n must be a multiple of 32 in [32, 256]");
     if (k < 16 || k > 256 || k % 16 != 0) return fail_msg(MOFF_EINVAL, "k must be a multiple of 16 in [16, 256]");
+    if (mode < 0 || mode > 7) return fail_msg(MOFF_EINVAL, "mode must be in [0, 7]");
+    // Each operand region holds its tile; an MN-major operand's region also
+    // holds every byte either reading of its two descriptor offsets can reach
+    // (below 44 KiB for R <= 128 rows and k <= 64).
+    const int mn_bound = 48 * 1024;
+    const int region_a = (mode & 1) ? mn_bound : 128 * k * 2;
+    const int region_b = (mode & 2) ? mn_bound : n * k * 2;
+    if ((mode & 1) && k > 64) return fail_msg(MOFF_EINVAL, "MN-major A is limited to k <= 64");
+    if ((mode & 2) && (k > 64 || n > 128)) return fail_msg(MOFF_EINVAL, "MN-major B is limited to k <= 64, n <= 128");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-    const size_t smem = (size_t)(128 + n) * k * 2 + 64;
+    const size_t smem = (size_t)region_a + region_b + 64;
     void *perr = nullptr;
     if (cudaGetSymbolAddress(&perr, g_selftest_err) != cudaSuccess)
         return fail_msg(MOFF_ECUDA, "cudaGetSymbolAddress failed");
@@ -88,7 +121,8 @@ extern "C" moff_status moff_tc_selftest(const void *a, const void *b, float *d, 
     if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return fail_msg(MOFF_ECUDA, "memset failed");
     cudaError_t e = cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail_msg(MOFF_ECUDA, cudaGetErrorString(e));
-    k_tc_selftest<<<1, 128, smem, st>>>(static_cast<const __half *>(a), static_cast<const __half *>(b), d, n, k, err);
+    k_tc_selftest<<<1, 128, smem, st>>>(static_cast<const __half *>(a), static_cast<const __half *>(b), d, n, k, mode,
+                                        region_a, region_b, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail_msg(MOFF_ECUDA, cudaGetErrorString(e));
     int h_err = 0;
     if ((e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

@@ -34,6 +34,30 @@ def test_tc_product_matches_host(n, k):
     assert (np.abs(got - ref) <= bound).all(), np.abs(got - ref).max()
 
 
+def _run(n, k, mode, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.normal(size=(128, k)).astype(np.float16)
+    b = rng.normal(size=(n, k)).astype(np.float16)
+    d = torch.full((128, n), float("nan"), dtype=torch.float32, device="cuda")
+    moff.moff_tc_selftest(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), d, mode)
+    got = d.cpu().numpy()
+    ref = a.astype(np.float64) @ b.astype(np.float64).T
+    bound = 1e-5 * (np.abs(a.astype(np.float64)) @ np.abs(b.astype(np.float64)).T) + 1e-6
+    return bool(np.isfinite(got).all() and (np.abs(got - ref) <= bound).all())
+
+
+@pytest.mark.parametrize("operand", ["A", "B"])
+def test_tc_mn_major_operand(operand):
+    """An MN-major operand (rows contiguous for each k) gives the right product when
+    its descriptor's leading byte offset is the K-direction core-matrix stride and
+    the stride byte offset the M/N-direction one (mode bit 2); the other reading
+    of the two offsets gives a wrong product."""
+    bit = 1 if operand == "A" else 2
+    for n, k in [(64, 16), (128, 32), (128, 64)]:
+        assert _run(n, k, bit | 4, 7), (n, k)
+    assert not _run(64, 32, bit, 7)
+
+
 def test_tc_selftest_argument_checks():
     a = torch.zeros((128, 16), dtype=torch.float16, device="cuda")
     b = torch.zeros((40, 16), dtype=torch.float16, device="cuda")
