@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp16tc", action="store_true", help="skip the FP16 tensor-core leg")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--frames", type=int, default=WL["frames"],
                     help="samples per step (smaller values give a profiling case, not a bench line)")
@@ -90,6 +91,17 @@ def flops_per_snapshot(kind, A=WL["n_ant"], P=WL["n_pol"], N=WL["grid_n"], K=WL[
     if kind == 2:      # column transforms + square-and-integrate
         return fft_axis + (16 if P == 2 else 4) * N * N
     raise ValueError(kind)
+
+
+def tc_row_flops_per_snapshot(pos, N=WL["grid_n"], P=WL["n_pol"], K=WL["ksize"], KX=64):
+    """Tensor-core flops per channel-snapshot of the row contraction as executed:
+    per (pol, grid row) 2 * 128-column product width * padded contraction length,
+    per kx tile of 64 (real and imaginary output columns)."""
+    import numpy as np
+    anc = np.floor(np.asarray(pos) + 0.5).astype(int) % N
+    rows = np.bincount(((anc[:, 1][:, None] + np.arange(K)[None, :] - K // 2) % N).ravel(), minlength=N)
+    kp = ((2 * rows + 15) // 16) * 16
+    return P * (N // KX) * float(np.sum(2 * (2 * KX) * kp))
 
 
 def pfb_flops_per_stream_frame(C=WL["n_chan"], ntaps=WL["ntaps"]):
@@ -276,49 +288,55 @@ def run_ours(args):
                                          for (kx, ky, ch, amp) in ((40, 70, 100, 12.0), (90, 30, 600, 8.0),
                                                                    (64, 64, 900, 6.0))))
 
-    plan = moff.Plan(pos, taps, N, C, P, fstage=True)
-    plan.set_gains(gains)
-    # requantisation gain from a short calibration block: noise sigma ~ 2 codes per component
-    calib = adc[:, :, : (ntaps + 3) * M].contiguous()
-    plan.set_fstage(ntaps, None, 1.0)
-    spec = plan.channelise(calib, kind=1)
-    scale = float(2.0 / np.std(np.concatenate([spec.real.ravel(), spec.imag.ravel()])))
-    plan.set_fstage(ntaps, None, scale)
-
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        plan.submit_adc(adc)
-    plan.sync()
-    plan.reset()
-    plan.set_timing(True)
+    def make_plan(fp16tc):
+        pl = moff.Plan(pos, taps, N, C, P, fstage=True, fp16tc=fp16tc)
+        pl.set_gains(gains)
+        # requantisation gain from a short calibration block: noise sigma ~ 2 codes per component
+        calib = adc[:, :, : (ntaps + 3) * M].contiguous()
+        pl.set_fstage(ntaps, None, 1.0)
+        spec = pl.channelise(calib, kind=1)
+        pl.set_fstage(ntaps, None, float(2.0 / np.std(np.concatenate([spec.real.ravel(), spec.imag.ravel()]))))
+        return pl
 
     gpu_idx = local
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis and vis.split(",")[local].strip().isdigit():
         gpu_idx = int(vis.split(",")[local])
-    clocks = ClockSampler(gpu_idx)
 
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        plan.submit_adc(adc)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms_max = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    def measure(pl, steps, warmup, sample_clocks=False):
+        """Time `steps` integrations (CUDA events on the plan stream), max over ranks."""
+        stream = torch.cuda.current_stream()
+        for _ in range(warmup):
+            pl.submit_adc(adc)
+        pl.sync()
+        pl.reset()
+        pl.set_timing(True)
+        clocks = ClockSampler(gpu_idx) if sample_clocks else None
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            pl.submit_adc(adc)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+        kern = {}
+        for kind, name in moff.KERNEL_KINDS.items():
+            tot, n = pl.timing(kind)
+            if n:
+                kern[name] = {"ms_total": tot, "launches": n}
+        pl.set_timing(False)
+        img, nsamp = pl.read_image(reset=True)
+        assert nsamp == steps * F and np.isfinite(img).all()
+        return ms, kern, clk, img
 
-    kern = {}
-    for kind, name in moff.KERNEL_KINDS.items():
-        tot, n = plan.timing(kind)
-        kern[name] = {"ms_total": tot, "launches": n}
-    plan.set_timing(False)
-    img, nsamp = plan.read_image(reset=True)
-    assert nsamp == args.steps * F and np.isfinite(img).all()
-
+    plan = make_plan(False)
+    ms_max, kern, clk, img32 = measure(plan, args.steps, args.warmup, sample_clocks=True)
     value = job_rate(args.steps * F * C, world, ms_max / 1000.0)
     snaps = args.steps * F * C
     total_kernel_ms = sum(v["ms_total"] for v in kern.values())
@@ -336,7 +354,7 @@ def run_ours(args):
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # FP32 FMA TFLOP/s at max SM clock
     for name, v in kern.items():
         v["share"] = v["ms_total"] / total_kernel_ms if total_kernel_ms else None
-        v["tflops"] = flops[name] / (v["ms_total"] / 1e3) / 1e12 if v["ms_total"] else None
+        v["tflops"] = flops[name] / (v["ms_total"] / 1e3) / 1e12 if v["ms_total"] and name in flops else None
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
     src = {"grid_rows": ["paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
            "cols_integrate": ["paper_0812_3669_gb300/csrc/moff_image_kernels.cuh",
@@ -351,6 +369,27 @@ def run_ours(args):
                 "ms_per_launch": kern[dom]["ms_total"] / max(launches, 1),
                 "traffic": traffic_for(dom + "@dualpol1024", src)}
     gpu_launches = sum(v["launches"] for v in kern.values())
+
+    # ---------------------------------------------------------------- FP16 tensor-core variant, same input
+    fp16 = None
+    if not args.no_fp16tc:
+        plan16 = make_plan(True)
+        ms16, kern16, _, img16 = measure(plan16, args.steps, max(1, args.warmup))
+        plan16.close()
+        tc_flops = snaps * tc_row_flops_per_snapshot(pos)
+        den = np.maximum(np.abs(img32).reshape(C, 4, -1).max(-1), 1e-30)
+        den[:, 2:] = np.maximum(den[:, :1], den[:, 1:2])
+        diff = np.abs(img16 - img32).reshape(C, 4, -1).max(-1) / den
+        rk = kern16.get("grid_rows", {})
+        fp16 = {"value": job_rate(args.steps * F * C, world, ms16 / 1000.0), "unit": UNIT,
+                "ms_per_step": ms16 / args.steps, "kernels": kern16,
+                "max_norm_diff_vs_fp32": float(diff.max()),
+                "row_contraction_tensor": {"bound": "tensor", "achieved": tc_flops / (rk["ms_total"] / 1e3) / 1e12
+                                           if rk.get("ms_total") else None,
+                                           "peak": float(peaks.get("bf16_tflops", 1933.3)), "unit": "TFLOP/s",
+                                           "peak_basis": "measured bf16 dense burst (fp16 nominal equal) (of measured)"}}
+        r = fp16["row_contraction_tensor"]
+        r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
 
     # ---------------------------------------------------------------- end to end through host buffers
     e2e = None
@@ -389,7 +428,7 @@ def run_ours(args):
                        "parallelism": f"{world} independent replica(s), one integration each"},
             "fx_equiv_tcmac_per_s": fx_eq / 1e12,
             "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches, "clocks": clk,
-            "e2e": e2e, "cpu_baseline": cpu,
+            "e2e": e2e, "cpu_baseline": cpu, "fp16tc": fp16,
         }), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -63,9 +63,15 @@ typedef enum {
 
 /* Plan flags. */
 enum {
-    MOFF_PREC_FP32 = 0u,   /* all arithmetic in FP32, cross-block sums in FP64 */
-    MOFF_FSTAGE = 1u << 1, /* enable the polyphase F-stage (moff_submit_adc, moff_channelise) */
-    MOFF_JONES = 1u << 2   /* kernels are full 2x2 Jones matrices (n_pol must be 2) */
+    MOFF_PREC_FP32 = 0u,      /* all arithmetic in FP32, cross-block sums in FP64 */
+    MOFF_PREC_FP16TC = 1u,    /* gridding and the row transform (Eq. m6 steps 1-3, first axis) as one
+                                 tensor-core contraction per grid row: FP16 operands (weighted
+                                 voltages and each kernel row's FP64-built row spectrum, both under
+                                 exact power-of-two scales), FP32 accumulation; the column transform
+                                 and the squaring stay FP32, cross-block sums FP64.  Needs at most
+                                 128 kernel rows landing on any one grid row per pol. */
+    MOFF_FSTAGE = 1u << 1,    /* enable the polyphase F-stage (moff_submit_adc, moff_channelise) */
+    MOFF_JONES = 1u << 2      /* kernels are full 2x2 Jones matrices (n_pol must be 2) */
 };
 
 /*
@@ -190,8 +196,10 @@ moff_status moff_set_timing(moff_plan *plan, int on);
  * moff_timing -- device time of the plan's kernels since timing was switched
  * on (or last reset), for one kernel kind:
  *   0  F-stage polyphase filter bank,
- *   1  calibrate + grid + row transform (Eq. m6 steps 1-2, step 3 first axis),
- *   2  column transform + square-and-integrate (step 3 second axis, step 4).
+ *   1  calibrate + grid + row transform (Eq. m6 steps 1-2, step 3 first axis;
+ *      with MOFF_PREC_FP16TC the tensor-core row contraction),
+ *   2  column transform + square-and-integrate (step 3 second axis, step 4),
+ *   3  (MOFF_PREC_FP16TC only) voltage decode, weighting and FP16 transpose.
  * Waits for the recorded work.  total_ms / launches may be NULL.  reset = 1
  * drops the records of every kind after reading.
  */

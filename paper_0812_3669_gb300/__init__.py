@@ -21,7 +21,7 @@ import re
 import numpy as np
 
 __all__ = [
-    "MoffError", "lib", "build", "LIB_PATH", "MOFF_FSTAGE", "MOFF_JONES", "MOFF_PREC_FP32",
+    "MoffError", "lib", "build", "LIB_PATH", "MOFF_FSTAGE", "MOFF_JONES", "MOFF_PREC_FP32", "MOFF_PREC_FP16TC",
     "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
     "moff_plan_info", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
@@ -34,10 +34,11 @@ LIB_PATH = os.path.join(_HERE, "libmoff.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "moff.h")
 
 MOFF_PREC_FP32 = 0
+MOFF_PREC_FP16TC = 1
 MOFF_FSTAGE = 1 << 1
 MOFF_JONES = 1 << 2
 
-KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate"}
+KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep"}
 
 STATUS = {0: "MOFF_OK", -1: "MOFF_EINVAL", -2: "MOFF_ENOMEM", -3: "MOFF_ECUDA",
           -4: "MOFF_ESTATE", -5: "MOFF_ETIMEDOUT", -6: "MOFF_EBUSY"}
@@ -270,8 +271,8 @@ def moff_plan_destroy(plan):
 class Plan:
     """One array's imaging plan (owns a ``moff_plan``)."""
 
-    def __init__(self, pos, taps, grid_n, n_chan, n_pol, jones=False, fstage=False, stream=None):
-        flags = (MOFF_JONES if jones else 0) | (MOFF_FSTAGE if fstage else 0)
+    def __init__(self, pos, taps, grid_n, n_chan, n_pol, jones=False, fstage=False, stream=None, fp16tc=False):
+        flags = (MOFF_JONES if jones else 0) | (MOFF_FSTAGE if fstage else 0) | (MOFF_PREC_FP16TC if fp16tc else 0)
         if stream is None:
             try:
                 import torch

@@ -236,6 +236,16 @@ struct moff_plan {
     float2 *d_spec = nullptr;
     size_t spec_bytes = 0;
 
+    // FP16 tensor-core path
+    bool tc = false;
+    int rs_kp_max = 0, rs_max_seg = 0, rs_cgroups = 1;
+    size_t rs_smem = 0;
+    float rs_inv_sw = 1.f;
+    int *d_rs_kp = nullptr, *d_rs_seg_y = nullptr, *d_err = nullptr;
+    long long *d_rs_seg_off = nullptr, *d_rs_bimg_off = nullptr;
+    __half *d_rs_bimg = nullptr, *d_yre = nullptr, *d_yim = nullptr;
+    float *d_sy = nullptr;
+
     long long n_samples = 0;
     size_t dev_bytes = 0;
     std::vector<void *> allocs;
@@ -348,6 +358,18 @@ void clear_recs(moff_plan *pl) {
     pl->recs.clear();
 }
 
+// Report (and clear) a bounded wait that gave up inside a kernel.
+moff_status check_device_err(moff_plan *pl) {
+    if (!pl->d_err) return MOFF_OK;
+    int h = 0;
+    MOFF_CK(cudaMemcpy(&h, pl->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        MOFF_CK(cudaMemset(pl->d_err, 0, sizeof(int)));
+        return fail(MOFF_ETIMEDOUT, "a tensor-core completion wait inside a kernel ran out of time");
+    }
+    return MOFF_OK;
+}
+
 // Copy a host block into the next staging buffer on the copy stream; the
 // compute stream waits for the copy, and the host waits until the copy has
 // finished (so the caller may reuse its buffer).  Returns the device copy.
@@ -405,7 +427,55 @@ GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, 
     return g;
 }
 
+moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
+    const int AP = pl->A * pl->P;
+    for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
+        const int nc = std::min(pl->Cb, pl->C - c0);
+        for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
+            const int nt = std::min(pl->Tb, n_time - t0);
+            TimedLaunch tv(pl, 3);
+            MOFF_CK(launch_volt_prep(volt, tstride, t0, nt, c0, nc, AP, pl->d_gains, pl->d_sy, pl->Tb, pl->d_yre,
+                                     pl->d_yim, pl->st));
+            tv.done();
+            RowSpecArgs ra{};
+            ra.P = pl->P;
+            ra.nt = nt;
+            ra.nc = nc;
+            ra.c0 = c0;
+            ra.AP = AP;
+            ra.Tpad = pl->Tb;
+            ra.kp_max = pl->rs_kp_max;
+            ra.kp = pl->d_rs_kp;
+            ra.seg_off = pl->d_rs_seg_off;
+            ra.seg_y = pl->d_rs_seg_y;
+            ra.bimg_off = pl->d_rs_bimg_off;
+            ra.bimg = pl->d_rs_bimg;
+            ra.yre = pl->d_yre;
+            ra.yim = pl->d_yim;
+            ra.sy = pl->d_sy;
+            ra.inv_sw = pl->rs_inv_sw;
+            ra.H = pl->d_H;
+            ra.err = pl->d_err;
+            TimedLaunch tg(pl, 1);
+            MOFF_CK(launch_rowspec(pl->N, ra, std::min(pl->rs_cgroups, nc), pl->rs_smem, pl->st));
+            tg.done();
+            ColArgs ca{};
+            ca.H = pl->d_H;
+            ca.nt = nt;
+            ca.c0 = c0;
+            ca.nc = nc;
+            ca.twp = pl->d_twp;
+            ca.acc = pl->d_acc;
+            TimedLaunch tc(pl, 2);
+            MOFF_CK(launch_cols(pl->N, pl->P, ca, pl->st));
+            tc.done();
+        }
+    }
+    return MOFF_OK;
+}
+
 moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
+    if (pl->tc) return run_image_tc(pl, volt, n_time, tstride);
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
         const int nc = std::min(pl->Cb, pl->C - c0);
         for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
@@ -622,6 +692,119 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
 
 std::vector<float2> pass_twiddles_for(int n) { return pass_twiddles_n(n); }
 
+// Row spectra of every kernel row (segment) for the tensor-core path, as
+// K-major core-matrix images per (pol, grid row, kx tile) -- see
+// moff_tc_kernels.cu.  FP64 sums, one power-of-two scale, FP16 rounding.
+moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, RowSpec *rs) {
+    const int h = K / 2;
+    std::vector<int> ax(A), ay(A);
+    for (int a = 0; a < A; ++a) {
+        const double x = pos[2 * a], y = pos[2 * a + 1];
+        if (!std::isfinite(x) || !std::isfinite(y) || std::fabs(x) > 1e9 || std::fabs(y) > 1e9)
+            return fail(MOFF_EINVAL, "antenna %d position is not finite or out of range", a);
+        long long fx = (long long)std::floor(x + 0.5), fy = (long long)std::floor(y + 0.5);
+        ax[a] = (int)(((fx % N) + N) % N);
+        ay[a] = (int)(((fy % N) + N) % N);
+    }
+    const int KX = N < 128 ? N : 128, NT = 2 * KX, ntiles = N / KX;
+    std::vector<double> cw(N), sw(N);
+    for (int m = 0; m < N; ++m) root_unity(m, N, &cw[m], &sw[m]);
+    // segments (antenna, input pol, kernel row) per (output pol, grid row), antenna-major
+    struct Seg { int a, q, dy; };
+    std::vector<std::vector<Seg>> segs((size_t)P * N);
+    const int pin_n = jones ? 2 : 1;
+    for (int a = 0; a < A; ++a)
+        for (int po = 0; po < P; ++po)
+            for (int k = 0; k < pin_n; ++k) {
+                const int pi = jones ? k : po;
+                for (int dy = 0; dy < K; ++dy) {
+                    bool any = false;
+                    for (int dx = 0; dx < K && !any; ++dx) {
+                        float re, im;
+                        tap_at(jones, P, K, taps, a, po, pi, dy, dx, &re, &im);
+                        any = re != 0.f || im != 0.f;
+                    }
+                    if (any) segs[(size_t)po * N + (ay[a] + dy - h + N) % N].push_back(Seg{a, pi, dy});
+                }
+            }
+    rs->ntiles = ntiles;
+    rs->kp.assign((size_t)P * N, 0);
+    rs->seg_off.assign((size_t)P * N + 1, 0);
+    rs->seg_y.clear();
+    rs->kp_max = 0;
+    rs->max_seg = 0;
+    for (size_t r = 0; r < (size_t)P * N; ++r) {
+        const int ns = (int)segs[r].size();
+        rs->kp[r] = ns ? ((2 * ns + 15) / 16) * 16 : 0;
+        rs->kp_max = std::max(rs->kp_max, rs->kp[r]);
+        rs->max_seg = std::max(rs->max_seg, ns);
+        rs->seg_off[r + 1] = rs->seg_off[r] + ns;
+        for (const Seg &g : segs[r]) rs->seg_y.push_back(g.a * P + g.q);
+    }
+    if (rs->kp_max > kRowSpecMaxK)
+        return fail(MOFF_EINVAL,
+                    "tensor-core path: %d kernel rows land on one grid row (at most %d); use the FP32 path",
+                    rs->max_seg, kRowSpecMaxK / 2);
+    // spectra in FP64, then one power-of-two scale for the whole plan
+    std::vector<std::vector<double>> spec_re((size_t)P * N), spec_im((size_t)P * N);
+    double mx = 0.0;
+    for (size_t r = 0; r < (size_t)P * N; ++r) {
+        const int po = (int)(r / N);
+        const auto &sg = segs[r];
+        spec_re[r].assign(sg.size() * N, 0.0);
+        spec_im[r].assign(sg.size() * N, 0.0);
+        for (size_t j = 0; j < sg.size(); ++j) {
+            for (int dx = 0; dx < K; ++dx) {
+                float tr, ti;
+                tap_at(jones, P, K, taps, sg[j].a, po, sg[j].q, sg[j].dy, dx, &tr, &ti);
+                if (tr == 0.f && ti == 0.f) continue;
+                const long long col = (ax[sg[j].a] + dx - h + N) % N;
+                for (int kx = 0; kx < N; ++kx) {
+                    const int m = (int)((kx * col) % N);
+                    spec_re[r][j * N + kx] += (double)tr * cw[m] - (double)ti * sw[m];
+                    spec_im[r][j * N + kx] += (double)tr * sw[m] + (double)ti * cw[m];
+                }
+            }
+            for (int kx = 0; kx < N; ++kx)
+                mx = std::max(mx, std::max(std::fabs(spec_re[r][j * N + kx]), std::fabs(spec_im[r][j * N + kx])));
+        }
+    }
+    int e = 0;
+    if (mx > 0.0) std::frexp(mx, &e);        // mx in [2^(e-1), 2^e)
+    const double scale = std::ldexp(1.0, 14 - e);
+    rs->inv_sw = (float)std::ldexp(1.0, e - 14);
+    // B images: row n < KX -> real part of H at kx = tile*KX + n; n >= KX -> imaginary part.
+    //   Hr = sum_j yr Sr - yi Si ; Hi = sum_j yr Si + yi Sr   (k = 2j: yr, k = 2j+1: yi)
+    rs->bimg_off.assign((size_t)P * N * ntiles, 0);
+    rs->bimg.clear();
+    for (size_t r = 0; r < (size_t)P * N; ++r) {
+        const int kp = rs->kp[r];
+        const int ns = (int)segs[r].size();
+        for (int t = 0; t < ntiles; ++t) {
+            rs->bimg_off[r * ntiles + t] = (long long)rs->bimg.size();
+            if (!kp) continue;
+            std::vector<__half> img((size_t)NT * kp, __float2half_rn(0.f));
+            for (int n = 0; n < NT; ++n) {
+                const int kx = t * KX + (n % KX);
+                const bool imag_row = n >= KX;
+                for (int j = 0; j < ns; ++j) {
+                    const double sr = spec_re[r][(size_t)j * N + kx] * scale, si = spec_im[r][(size_t)j * N + kx] * scale;
+                    const double b0 = imag_row ? si : sr;       // coefficient of yr
+                    const double b1 = imag_row ? sr : -si;      // coefficient of yi
+                    for (int k = 2 * j; k <= 2 * j + 1; ++k) {
+                        const size_t off = ((size_t)(n >> 3) * (kp >> 3) * 128 + (size_t)(k >> 3) * 128 +
+                                            (size_t)(n & 7) * 16 + (size_t)(k & 7) * 2) / 2;
+                        img[off] = __double2half(k == 2 * j ? b0 : b1);
+                    }
+                }
+            }
+            rs->bimg.insert(rs->bimg.end(), img.begin(), img.end());
+        }
+    }
+    return MOFF_OK;
+}
+
+
 }  // namespace moff
 
 namespace {
@@ -739,7 +922,8 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         return fail(MOFF_EINVAL, "ksize (%d) must be odd, in [1, 15] and <= grid_n", ksize);
     if (n_chan < 1) return fail(MOFF_EINVAL, "n_chan (%d) must be >= 1", n_chan);
     if (n_pol != 1 && n_pol != 2) return fail(MOFF_EINVAL, "n_pol (%d) must be 1 or 2", n_pol);
-    if (flags & ~(unsigned)(MOFF_FSTAGE | MOFF_JONES)) return fail(MOFF_EINVAL, "unknown flag bits 0x%x", flags);
+    if (flags & ~(unsigned)(MOFF_FSTAGE | MOFF_JONES | MOFF_PREC_FP16TC))
+        return fail(MOFF_EINVAL, "unknown flag bits 0x%x", flags);
     if ((flags & MOFF_JONES) && n_pol != 2) return fail(MOFF_EINVAL, "MOFF_JONES requires n_pol = 2");
     if ((flags & MOFF_FSTAGE) && (!is_pow2(n_chan) || n_chan < 32 || n_chan > 2048))
         return fail(MOFF_EINVAL, "with MOFF_FSTAGE n_chan (%d) must be a power of two in [32, 2048]", n_chan);
@@ -754,6 +938,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     pl->flags = flags;
     pl->jones = (flags & MOFF_JONES) != 0;
     pl->fstage = (flags & MOFF_FSTAGE) != 0;
+    pl->tc = (flags & MOFF_PREC_FP16TC) != 0;
     auto bail = [&](moff_status s) {
         std::string msg = g_err;
         destroy_plan(pl);
@@ -808,11 +993,49 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         const size_t per = (size_t)n_pol * grid_n * grid_n * 8;
         long long budget = 16384LL << 20;
         if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, (long long)(atof(e) * 1048576.0));
-        const long long cb = std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per)));
-        const long long tb = std::max(1LL, std::min<long long>(64, budget / (long long)(cb * per)));
-        pl->Cb = (int)cb;
-        pl->Tb = (int)tb;
-        if ((s = palloc(pl, &pl->d_H, (size_t)tb * cb * per)) != MOFF_OK) return bail(s);
+        if (pl->tc) {
+            // the tensor-core path works on 128 samples per product
+            const size_t per_c = 128 * per + (size_t)n_ant * n_pol * 128 * 4;
+            pl->Tb = 128;
+            pl->Cb = (int)std::max(1LL, std::min<long long>(n_chan, budget / (long long)per_c));
+        } else {
+            const long long cb = std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per)));
+            const long long tb = std::max(1LL, std::min<long long>(64, budget / (long long)(cb * per)));
+            pl->Cb = (int)cb;
+            pl->Tb = (int)tb;
+        }
+        if ((s = palloc(pl, &pl->d_H, (size_t)pl->Tb * pl->Cb * per)) != MOFF_OK) return bail(s);
+    }
+    if (pl->tc) {
+        RowSpec rs;
+        if ((s = build_rowspec(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps, &rs)) != MOFF_OK) return bail(s);
+        pl->rs_kp_max = std::max(rs.kp_max, 16);
+        pl->rs_max_seg = std::max(rs.max_seg, 1);
+        pl->rs_inv_sw = rs.inv_sw;
+        pl->rs_smem = rowspec_smem_bytes(grid_n, pl->rs_kp_max, pl->rs_max_seg);
+        const int items = n_pol * grid_n * rs.ntiles;
+        pl->rs_cgroups = std::max(1, std::min(pl->Cb, (4 * 152 + items - 1) / items));
+        const size_t ny = (size_t)pl->Cb * n_ant * n_pol * pl->Tb;
+        if ((s = palloc(pl, &pl->d_rs_kp, rs.kp.size() * 4)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_rs_seg_off, rs.seg_off.size() * 8)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_rs_seg_y, std::max<size_t>(rs.seg_y.size(), 1) * 4)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_rs_bimg_off, rs.bimg_off.size() * 8)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_rs_bimg, std::max<size_t>(rs.bimg.size(), 8) * 2)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_yre, ny * 2)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_yim, ny * 2)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_sy, (size_t)n_chan * 4)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_err, 16)) != MOFF_OK) return bail(s);
+        if (cudaMemcpy(pl->d_rs_kp, rs.kp.data(), rs.kp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(pl->d_rs_seg_off, rs.seg_off.data(), rs.seg_off.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+            (!rs.seg_y.empty() &&
+             cudaMemcpy(pl->d_rs_seg_y, rs.seg_y.data(), rs.seg_y.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+            cudaMemcpy(pl->d_rs_bimg_off, rs.bimg_off.data(), rs.bimg_off.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+            (!rs.bimg.empty() &&
+             cudaMemcpy(pl->d_rs_bimg, rs.bimg.data(), rs.bimg.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) ||
+            cudaMemset(pl->d_err, 0, 16) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "tensor-core table upload failed"));
+        if (launch_gain_scale(pl->d_gains, n_chan, n_ant * n_pol, pl->d_sy, pl->st) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "gain scale kernel failed"));
     }
     // F-stage tables
     if (pl->fstage) {
@@ -850,6 +1073,7 @@ moff_status moff_set_gains(moff_plan *pl, const float *gains, int on_device) {
     if (!gains) return fail(MOFF_EINVAL, "gains is NULL");
     const size_t bytes = (size_t)pl->C * pl->A * pl->P * 8;
     MOFF_CK(cudaMemcpyAsync(pl->d_gains, gains, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pl->st));
+    if (pl->tc) MOFF_CK(launch_gain_scale(pl->d_gains, pl->C, pl->A * pl->P, pl->d_sy, pl->st));
     if (!on_device) return sync_plan(pl, -1);
     return MOFF_OK;
 }
@@ -989,6 +1213,7 @@ moff_status moff_read_image(moff_plan *pl, float *out, long long *n_samples, int
     if (s != MOFF_OK) return s;
     if (!out) return fail(MOFF_EINVAL, "out is NULL");
     if ((s = sync_plan(pl, timeout_ms)) != MOFF_OK) return s;
+    if ((s = check_device_err(pl)) != MOFF_OK) return s;
     const long long n = (long long)pl->C * pl->nprod * pl->N * pl->N;
     MOFF_CK(launch_to_f32(pl->d_acc, out_on_device ? out : pl->d_img, n, pl->st));
     if (!out_on_device) MOFF_CK(cudaMemcpyAsync(out, pl->d_img, (size_t)n * 4, cudaMemcpyDeviceToHost, pl->st));
@@ -1004,7 +1229,8 @@ moff_status moff_read_image(moff_plan *pl, float *out, long long *n_samples, int
 moff_status moff_sync(moff_plan *pl, int timeout_ms) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
-    return sync_plan(pl, timeout_ms);
+    if ((s = sync_plan(pl, timeout_ms)) != MOFF_OK) return s;
+    return check_device_err(pl);
 }
 
 moff_status moff_reset(moff_plan *pl) {
@@ -1027,7 +1253,7 @@ moff_status moff_set_timing(moff_plan *pl, int on) {
 moff_status moff_timing(moff_plan *pl, int kind, double *total_ms, long long *launches, int reset) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
-    if (kind < 0 || kind > 2) return fail(MOFF_EINVAL, "kind (%d) must be 0, 1 or 2", kind);
+    if (kind < 0 || kind > 3) return fail(MOFF_EINVAL, "kind (%d) must be 0, 1, 2 or 3", kind);
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
     double tot = 0.0;
     long long n = 0;

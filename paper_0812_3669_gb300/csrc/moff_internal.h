@@ -1,6 +1,7 @@
 // moff_internal.h -- argument blocks and launchers shared by the host code
 // (moff_api.cu) and the kernel translation units.  Not part of the C ABI.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -46,6 +47,22 @@ struct ColArgs {
     int nt, c0, nc;
     const float2 *twp;
     double *acc;              // [C][n_prod][N][N] FP64 accumulators (added to)
+};
+
+// FP16 tensor-core gridding + row transform: per (pol, grid row, kx tile) a
+// product of the row's segment voltages with the segments' row spectra.
+struct RowSpecArgs {
+    int P, nt, nc, c0, AP, Tpad, kp_max;
+    const int *kp;             // [P*N] padded contraction length (real) per (pol, row); 0 = empty row
+    const long long *seg_off;  // [P*N + 1] segments of each (pol, row)
+    const int *seg_y;          // voltage index (antenna * P + input pol) of each segment
+    const long long *bimg_off; // [P*N*ntiles] byte offset of each B image
+    const __half *bimg;        // row spectra, K-major core-matrix images [2*KX][kp]
+    const __half *yre, *yim;   // [nc][AP][Tpad] weighted, scaled voltages
+    const float *sy;           // [C] voltage scales (powers of two)
+    float inv_sw;              // 1 / spectrum scale (power of two)
+    float2 *H;                 // [nt][nc][P][N][N] row-transformed field
+    int *err;                  // set when a bounded wait gives up
 };
 
 // Polyphase F-stage (Eq. FFTofE).
@@ -101,6 +118,16 @@ struct Bins {
 };
 moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b);
 std::vector<float2> pass_twiddles_for(int n);   // pass-twiddle table of the n-point transform (FP64-built)
+
+// Row spectra of the kernel rows for the tensor-core path (host side).
+struct RowSpec {
+    int kp_max = 0, max_seg = 0, ntiles = 1;
+    float inv_sw = 1.f;
+    std::vector<int> kp, seg_y;
+    std::vector<long long> seg_off, bimg_off;   // bimg_off in elements
+    std::vector<__half> bimg;
+};
+moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, RowSpec *rs);
 moff_status fail_msg(moff_status s, const char *msg);
 
 int fft_tw_total(int n);                      // pass-twiddle table length for length n
@@ -114,6 +141,16 @@ cudaError_t launch_grid(int N, int P, int TB, bool staged, bool grid_only, const
 cudaError_t launch_cols(int N, int P, const ColArgs &a, cudaStream_t st);
 cudaError_t launch_pfb(int CN, const PfbArgs &a, cudaStream_t st);
 cudaError_t launch_to_f32(const double *acc, float *out, long long n, cudaStream_t st);
+
+// Tensor-core path (moff_tc_kernels.cu).
+constexpr int kRowSpecMaxK = 256;   // largest contraction length (2 x segments per row, padded) held on chip
+size_t rowspec_smem_bytes(int N, int kp_max, int max_seg);
+int rowspec_ntiles(int N);
+cudaError_t launch_gain_scale(const float2 *gains, int C, int AP, float *sy, cudaStream_t st);
+cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc, int AP,
+                             const float2 *gains, const float *sy, int Tpad, __half *yre, __half *yim,
+                             cudaStream_t st);
+cudaError_t launch_rowspec(int N, const RowSpecArgs &a, int cgroups, size_t smem, cudaStream_t st);
 
 // Per-N instantiations (one translation unit each, compiled in parallel).
 #define MOFF_DECLARE_N(NN)                                                                          \

@@ -120,6 +120,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parit
     return true;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile(
+        "{\n"
+        ".reg .b64 st;\n"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n"
+        "}\n" ::"r"(smem_u32(mbar))
+        : "memory");
+}
+
+// Bounded wait that also gives up when another role of the CTA has raised
+// `abort` (shared memory), so one time-out unwinds every role.
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t *mbar, uint32_t parity, long long max_cycles,
+                                                    volatile int *abort) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > max_cycles) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
 // ---- TMEM -> registers: this warp's 32 lanes x 32 consecutive FP32 columns.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];

@@ -1,0 +1,341 @@
+// moff_tc_kernels.cu -- FP16 tensor-core variant of Eq. m6 steps 1-3 (first
+// axis) of Morales (arXiv 0812.3669): gridding and the row transform as one
+// dense contraction per grid row.
+//
+// The row transform of the gridded field is linear in the weighted voltages:
+//   H(ry, kx) = sum_rx G(ry, rx) e^{+2 pi i kx rx / N}
+//             = sum_{segments j on row ry} y_j * S_j(kx),
+// where a segment is one row dy of one antenna-pol kernel (Eq. m6 step 2) and
+// S_j(kx) = sum_dx taps[dy][dx] e^{+2 pi i kx (anchor_x + dx - K/2) / N} is its
+// row spectrum, computed once per plan in FP64.  Per (pol, grid row) this is a
+// product (samples x 2 nseg) * (2 nseg x 2 KX) in real arithmetic, run on the
+// tensor cores with FP16 operands (exact power-of-two scales) and FP32
+// accumulation in TMEM.  The second transform axis and the squaring stay in
+// the FP32 column kernel.
+//
+//   k_gain_scale   per-channel power-of-two scale keeping weighted voltages in FP16 range
+//   k_volt_prep    decode, weight, scale and transpose the voltages to FP16 planes [c][voltage][t]
+//   k_rowspec_tc   per (pol, row, kx tile): B = row spectra resident in shared memory,
+//                  A = 128 samples of the row's segment voltages (cp.async, MN-major),
+//                  D = TMEM (double buffered), epilogue writes the FP32 row-transformed field.
+#include <cuda_fp16.h>
+
+#include "moff_fft.cuh"
+#include "moff_internal.h"
+#include "moff_tc.cuh"
+
+namespace moff {
+namespace {
+
+__device__ __forceinline__ float2 decode4_tc(uint32_t b) {
+    const int hi = (int)((b >> 4) & 15u), lo = (int)(b & 15u);
+    return make_float2((float)(hi - ((hi & 8) << 1)), (float)(lo - ((lo & 8) << 1)));
+}
+
+// s_y[c] = 2^e with 16 * max|g_c| * 2^e in [2^13, 2^14): |y| <= |g| (|x_re| + |x_im|) <= 16 |g|.
+__global__ void k_gain_scale(const float2 *__restrict__ gains, int AP, float *__restrict__ sy) {
+    const int c = blockIdx.x;
+    float m = 0.f;
+    for (int i = threadIdx.x; i < AP; i += blockDim.x) {
+        const float2 g = gains[(long long)c * AP + i];
+        m = fmaxf(m, fmaxf(fabsf(g.x), fabsf(g.y)));
+    }
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) {
+            float s = 1.f;
+            if (m > 0.f) {
+                int e;
+                frexpf(16.f * m, &e);            // 16 m in [2^(e-1), 2^e)
+                s = ldexpf(1.f, 14 - e);         // 16 m s in [2^13, 2^14)
+            }
+            sy[c] = s;
+        }
+    }
+}
+
+// Voltages of samples [t0, t0+nt) of channels [c0, c0+nc) -> FP16 planes
+// Yre/Yim [nc][AP][Tpad] (t contiguous), zero for t >= nt.  Tile 32 t x 64 voltages.
+__global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ volt, long long tstride, int t0, int nt,
+                                                   int c0, int AP, const float2 *__restrict__ gains,
+                                                   const float *__restrict__ sy, int Tpad, __half *__restrict__ yre,
+                                                   __half *__restrict__ yim) {
+    __shared__ float2 tile[32][65];
+    const int cl = blockIdx.z, c = c0 + cl;
+    const int v0 = blockIdx.x * 64, tb = blockIdx.y * 32;
+    const float s = sy[c];
+    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+        const int tt = i / 64, v = i % 64;
+        const int t = tb + tt, vi = v0 + v;
+        float2 y = make_float2(0.f, 0.f);
+        if (t < nt && vi < AP) {
+            const uint8_t b = volt[(long long)(t0 + t) * tstride + (long long)c * AP + vi];
+            y = cmul(gains[(long long)c * AP + vi], decode4_tc(b));
+            y.x *= s;
+            y.y *= s;
+        }
+        tile[tt][v] = y;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+        const int v = i / 32, tt = i % 32;
+        const int t = tb + tt, vi = v0 + v;
+        if (vi < AP && t < Tpad) {
+            const long long o = ((long long)cl * AP + vi) * Tpad + t;
+            yre[o] = __float2half_rn(tile[tt][v].x);
+            yim[o] = __float2half_rn(tile[tt][v].y);
+        }
+    }
+}
+
+
+template <int N>
+struct TcShape {
+    static constexpr int KX = N < 128 ? N : 128;     // kx per tile
+    static constexpr int NT = 2 * KX;                // MMA N: real parts then imaginary parts
+    static constexpr int NTILES = N / KX;
+    static constexpr int TCOLS = 2 * NT <= 32 ? 32 : 2 * NT;   // two TMEM accumulators
+};
+
+__device__ __forceinline__ void cp_async16_tc(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_u32(smem_dst)), "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_tc() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_tc() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Warp roles: warps 0-3 drain the TMEM accumulators (one lane quarter each),
+// warps 4-7 stage A in K-chunks of 64 with cp.async, warp 8 issues the MMAs
+// (one lane).  A: 3-stage ring of [128 samples x 64] MN-major chunks; B:
+// resident; accumulators: two in TMEM; epilogue: each warp transposes its 32
+// samples x 32 kx through shared memory so every global store instruction
+// writes 256 contiguous bytes of one sample's row.
+constexpr int kEpiWarps = 4, kProdWarps = 4;
+constexpr int kTcRoleThreads = (kEpiWarps + kProdWarps + 1) * 32;
+constexpr int kAStages = 3, kKChunk = 64;
+constexpr int kAChunkBytes = 128 * kKChunk * 2;
+constexpr int kStageLd = 33;                        // float2 per staged row (padded)
+constexpr long long kWaitCycles = 4000000000LL;     // ~2 s at the SM clock
+
+template <int N>
+__global__ void __launch_bounds__(kTcRoleThreads, 1) k_rowspec_tc(const RowSpecArgs a) {
+    using S = TcShape<N>;
+    constexpr int KX = S::KX, NT = S::NT;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int item = blockIdx.x;                      // (p * N + ry) * NTILES + tile
+    const int tile = item % S::NTILES;
+    const int pr = item / S::NTILES;
+    const int p = pr / N, ry = pr % N;
+    const int kp = a.kp[pr];
+    const int nseg = (int)(a.seg_off[pr + 1] - a.seg_off[pr]);
+
+    const int cper = (a.nc + gridDim.y - 1) / gridDim.y;
+    const int cb = blockIdx.y * cper, ce = min(a.nc, cb + cper);
+    if (cb >= ce) return;
+    const int ntb = (a.nt + 127) / 128;
+    const int nitems = (ce - cb) * ntb;
+    const long long hrow = (long long)p * N * N + (long long)ry * N + tile * KX;   // within one (t, c) slab
+    const long long hslab = (long long)a.P * N * N;
+
+    if (kp == 0) {   // no kernel row lands here: the row-transformed field is zero
+        for (int it = 0; it < nitems; ++it) {
+            const int cl = cb + it / ntb, t0b = (it % ntb) * 128;
+            for (int i = tid; i < 128 * KX; i += blockDim.x) {
+                const int tt = i / KX, kx = i % KX, t = t0b + tt;
+                if (t < a.nt) a.H[((long long)t * a.nc + cl) * hslab + hrow + kx] = make_float2(0.f, 0.f);
+            }
+        }
+        return;
+    }
+    const int nchunk = (kp + kKChunk - 1) / kKChunk;
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sB = smem;                                  // NT x kp, K-major (resident)
+    unsigned char *sA = sB + (size_t)NT * a.kp_max * 2;        // kAStages x [128 x 64], MN-major
+    float2 *stage = reinterpret_cast<float2 *>(sA + (size_t)kAStages * kAChunkBytes);   // [4][32][kStageLd]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kEpiWarps * 32 * kStageLd);
+    uint64_t *a_full = bars, *a_empty = bars + kAStages, *d_full = bars + 2 * kAStages,
+             *d_empty = bars + 2 * kAStages + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kAStages + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    int *s_seg = reinterpret_cast<int *>(tslot + 2);
+
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.bimg + a.bimg_off[item]);
+        uint4 *dst = reinterpret_cast<uint4 *>(sB);
+        const int n16 = NT * kp * 2 / 16;
+        for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
+        for (int j = tid; j < nseg; j += blockDim.x) s_seg[j] = a.seg_y[a.seg_off[pr] + j];
+    }
+    if (tid == 0) {
+        for (int b = 0; b < kAStages; ++b) {
+            tc::mbar_init(&a_full[b], kProdWarps * 32);
+            tc::mbar_init(&a_empty[b], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&d_full[b], 1);
+            tc::mbar_init(&d_empty[b], kEpiWarps * 32);
+        }
+        *abort_flag = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, S::TCOLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_async_smem();   // resident B written by generic stores, read by the tensor core
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (warp >= kEpiWarps && warp < kEpiWarps + kProdWarps) {
+        // ---------------- producers: chunk g (global counter) into stage g % kAStages
+        const int ptid = tid - kEpiWarps * 32;
+        int g = 0;
+        for (int i = 0; i < nitems && !*abort_flag; ++i) {
+            const int cl = cb + i / ntb, t0b = (i % ntb) * 128;
+            const __half *re = a.yre + (long long)cl * a.AP * a.Tpad + t0b;
+            const __half *im = a.yim + (long long)cl * a.AP * a.Tpad + t0b;
+            for (int ch = 0; ch < nchunk; ++ch, ++g) {
+                const int st = g % kAStages;
+                if (!tc::mbar_wait_abortable(&a_empty[st], (uint32_t)(((g / kAStages) & 1) ^ 1), kWaitCycles,
+                                             abort_flag))
+                    break;
+                unsigned char *sa = sA + st * kAChunkBytes;
+                for (int q = ptid; q < kKChunk * 16; q += kProdWarps * 32) {
+                    const int kk = q >> 4, m8 = q & 15;
+                    const int k = ch * kKChunk + kk, j = k >> 1;
+                    unsigned char *d = sa + m8 * 128 + (kk >> 3) * 2048 + (kk & 7) * 16;
+                    if (k < kp && j < nseg) {
+                        cp_async16_tc(d, ((k & 1) ? im : re) + (long long)s_seg[j] * a.Tpad + m8 * 8);
+                    } else {
+                        *reinterpret_cast<uint4 *>(d) = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+                cp_async_commit_tc();
+                cp_async_wait_all_tc();
+                tc::fence_async_smem();
+                tc::mbar_arrive(&a_full[st]);
+            }
+        }
+    } else if (warp == kEpiWarps + kProdWarps) {
+        // ---------------- MMA issuer (one lane)
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_f16(128, NT, /*a_mn=*/true, /*b_mn=*/false);
+            const uint32_t sb_sbo = (uint32_t)(kp / 8) * 128;
+            const uint32_t sbb = tc::smem_u32(sB);
+            int g = 0;
+            bool ok = true;
+            for (int i = 0; i < nitems && ok; ++i) {
+                const int b = i & 1;
+                ok = tc::mbar_wait_abortable(&d_empty[b], (uint32_t)(((i >> 1) & 1) ^ 1), kWaitCycles, abort_flag);
+                if (!ok) break;
+                const uint32_t d = tbase + (uint32_t)(b * NT);
+                for (int ch = 0; ch < nchunk; ++ch, ++g) {
+                    const int st = g % kAStages;
+                    ok = tc::mbar_wait_abortable(&a_full[st], (uint32_t)((g / kAStages) & 1), kWaitCycles, abort_flag);
+                    if (!ok) break;
+                    tc::fence_after_sync();
+                    const uint32_t sa = tc::smem_u32(sA + st * kAChunkBytes);
+                    const int kend = min(kKChunk, kp - ch * kKChunk);
+                    for (int ks = 0; ks < kend / 16; ++ks) {
+                        const uint64_t ad = tc::smem_desc(sa + ks * 2 * 2048, 2048, 128);   // MN-major: LBO = K stride
+                        const uint64_t bd = tc::smem_desc(sbb + (ch * (kKChunk / 8) + 2 * ks) * 128, 128, sb_sbo);
+                        tc::mma_f16(d, ad, bd, idesc, ch > 0 || ks > 0);
+                    }
+                    tc::mma_commit(&a_empty[st]);   // stage free once these MMAs finish
+                }
+                if (ok) tc::mma_commit(&d_full[b]); // accumulator ready
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warps 0-3: TMEM lanes 32w..32w+31 = samples
+        float2 *stw = stage + warp * 32 * kStageLd;
+        for (int i = 0; i < nitems; ++i) {
+            const int b = i & 1;
+            if (!tc::mbar_wait_abortable(&d_full[b], (uint32_t)((i >> 1) & 1), kWaitCycles, abort_flag)) break;
+            tc::fence_after_sync();
+            const int cl = cb + i / ntb, t0w = (i % ntb) * 128 + warp * 32;
+            const float inv = a.inv_sw / a.sy[a.c0 + cl];
+            const uint32_t dcol = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * NT);
+            float2 *hbase = a.H + ((long long)t0w * a.nc + cl) * hslab + hrow;
+            const long long tstep = (long long)a.nc * hslab;
+#pragma unroll 1
+            for (int k0 = 0; k0 < KX; k0 += 32) {
+                float vr[32], vi[32];
+                tc::tmem_ld32(dcol + (uint32_t)k0, vr);
+                tc::tmem_ld32(dcol + (uint32_t)(KX + k0), vi);
+                // this lane holds sample t0w + lane, kx k0..k0+31: transpose through shared memory
+#pragma unroll
+                for (int u = 0; u < 32; ++u) stw[lane * kStageLd + u] = make_float2(vr[u] * inv, vi[u] * inv);
+                __syncwarp();
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r)
+                    if (t0w + r < a.nt) hbase[r * tstep + k0 + lane] = stw[r * kStageLd + lane];
+                __syncwarp();
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&d_empty[b]);
+        }
+    }
+    if (*abort_flag && tid == 0) atomicExch(a.err, tc::kErrWaitTimeout);
+    cp_async_wait_all_tc();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tbase, S::TCOLS);
+}
+
+}  // namespace
+
+size_t rowspec_smem_bytes(int N, int kp_max, int max_seg) {
+    const int KX = N < 128 ? N : 128, NT = 2 * KX;
+    size_t b = (size_t)NT * kp_max * 2 + (size_t)kAStages * kAChunkBytes + (size_t)kEpiWarps * 32 * kStageLd * 8 +
+               (size_t)(2 * kAStages + 4) * 8 + 8 + (size_t)max_seg * 4;
+    b = (b + 127) & ~(size_t)127;
+    // one CTA per SM: two CTAs must never wait on each other's TMEM columns
+    return b < 120 * 1024 ? 120 * 1024 : b;
+}
+
+int rowspec_ntiles(int N) { return N < 128 ? 1 : N / 128; }
+
+cudaError_t launch_gain_scale(const float2 *gains, int C, int AP, float *sy, cudaStream_t st) {
+    k_gain_scale<<<C, 256, 0, st>>>(gains, AP, sy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc, int AP,
+                             const float2 *gains, const float *sy, int Tpad, __half *yre, __half *yim,
+                             cudaStream_t st) {
+    dim3 grid((AP + 63) / 64, (Tpad + 31) / 32, nc);
+    k_volt_prep<<<grid, 256, 0, st>>>(volt, tstride, t0, nt, c0, AP, gains, sy, Tpad, yre, yim);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_rowspec_t(const RowSpecArgs &a, int cgroups, size_t smem, cudaStream_t st) {
+    auto k = k_rowspec_tc<N>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(a.P * N * TcShape<N>::NTILES, cgroups), kTcRoleThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowspec(int N, const RowSpecArgs &a, int cgroups, size_t smem, cudaStream_t st) {
+    switch (N) {
+        case 32: return launch_rowspec_t<32>(a, cgroups, smem, st);
+        case 64: return launch_rowspec_t<64>(a, cgroups, smem, st);
+        case 128: return launch_rowspec_t<128>(a, cgroups, smem, st);
+        case 256: return launch_rowspec_t<256>(a, cgroups, smem, st);
+        case 512: return launch_rowspec_t<512>(a, cgroups, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace moff
