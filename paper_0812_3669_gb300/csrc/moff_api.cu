@@ -176,13 +176,13 @@ cudaError_t launch_grid(int N, int P, int TB, bool staged, bool go, const GridAr
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_cols(int N, int P, const ColArgs &a, cudaStream_t st) {
+cudaError_t launch_cols(int N, int P, const ColArgs &a, cudaStream_t st, bool h16) {
     switch (N) {
-        case 32: return launch_cols_n32(P, a, st);
-        case 64: return launch_cols_n64(P, a, st);
-        case 128: return launch_cols_n128(P, a, st);
-        case 256: return launch_cols_n256(P, a, st);
-        case 512: return launch_cols_n512(P, a, st);
+        case 32: return launch_cols_n32(P, a, st, h16);
+        case 64: return launch_cols_n64(P, a, st, h16);
+        case 128: return launch_cols_n128(P, a, st, h16);
+        case 256: return launch_cols_n256(P, a, st, h16);
+        case 512: return launch_cols_n512(P, a, st, h16);
     }
     return cudaErrorInvalidValue;
 }
@@ -243,6 +243,8 @@ struct moff_plan {
     float rs_inv_sw = 1.f;
     int *d_rs_kp = nullptr, *d_rs_seg_y = nullptr, *d_err = nullptr;
     long long *d_rs_seg_off = nullptr, *d_rs_bimg_off = nullptr;
+    float *d_rs_row_sh = nullptr, *d_rs_row_inv = nullptr;
+    CUtensorMap h_map;                 // tensor-core path: store map of the FP16 field
     __half *d_rs_bimg = nullptr, *d_yre = nullptr, *d_yim = nullptr;
     float *d_sy = nullptr;
 
@@ -424,6 +426,10 @@ GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, 
     g.con_y = pl->d_con_y;
     g.twp = pl->d_twp;
     g.out = pl->d_H;
+    // channel-major slabs: a channel's samples of one chunk are contiguous, so the
+    // time batch a CTA writes, and the samples a column CTA reads, share pages
+    g.slab_t = 1;
+    g.slab_c = pl->Tb;
     return g;
 }
 
@@ -454,10 +460,13 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
             ra.yim = pl->d_yim;
             ra.sy = pl->d_sy;
             ra.inv_sw = pl->rs_inv_sw;
-            ra.H = pl->d_H;
+            ra.row_sh = pl->d_rs_row_sh;
+            ra.H = reinterpret_cast<__half2 *>(pl->d_H);
+            ra.slab_t = pl->Cb;   // [Tb][Cb] slabs: the layout the field's tensor map describes
+            ra.slab_c = 1;
             ra.err = pl->d_err;
             TimedLaunch tg(pl, 1);
-            MOFF_CK(launch_rowspec(pl->N, ra, std::min(pl->rs_cgroups, nc), pl->rs_smem, pl->st));
+            MOFF_CK(launch_rowspec(pl->N, ra, pl->h_map, std::min(pl->rs_cgroups, nc), pl->rs_smem, pl->st));
             tg.done();
             ColArgs ca{};
             ca.H = pl->d_H;
@@ -466,8 +475,13 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
             ca.nc = nc;
             ca.twp = pl->d_twp;
             ca.acc = pl->d_acc;
+            ca.slab_t = ra.slab_t;
+            ca.slab_c = ra.slab_c;
+            ca.row_inv = pl->d_rs_row_inv;
+            ca.sy = pl->d_sy;
+            ca.inv_sw = pl->rs_inv_sw;
             TimedLaunch tc(pl, 2);
-            MOFF_CK(launch_cols(pl->N, pl->P, ca, pl->st));
+            MOFF_CK(launch_cols(pl->N, pl->P, ca, pl->st, true));
             tc.done();
         }
     }
@@ -489,6 +503,8 @@ moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long 
             ca.nt = nt;
             ca.c0 = c0;
             ca.nc = nc;
+            ca.slab_t = g.slab_t;
+            ca.slab_c = g.slab_c;
             ca.twp = pl->d_twp;
             ca.acc = pl->d_acc;
             TimedLaunch tc(pl, 2);
@@ -773,6 +789,24 @@ moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *
     if (mx > 0.0) std::frexp(mx, &e);        // mx in [2^(e-1), 2^e)
     const double scale = std::ldexp(1.0, 14 - e);
     rs->inv_sw = (float)std::ldexp(1.0, e - 14);
+    // FP16 field scale per (pol, row): the accumulator is sum_j (y s_y)(S_j s_w) with
+    // |y s_y| < 2^14, so |re|, |im| <= 2^14 * sum_j max_kx (|S_j re| + |S_j im|) s_w; keep that below 2^15.
+    rs->row_sh.assign((size_t)P * N, 1.f);
+    rs->row_inv.assign((size_t)P * N, 1.f);
+    for (size_t r = 0; r < (size_t)P * N; ++r) {
+        double bound = 0.0;
+        for (size_t j = 0; j < segs[r].size(); ++j) {
+            double m = 0.0;
+            for (int kx = 0; kx < N; ++kx)
+                m = std::max(m, std::fabs(spec_re[r][j * N + kx]) + std::fabs(spec_im[r][j * N + kx]));
+            bound += m * scale;
+        }
+        bound *= 16384.0;
+        int eb = 0;
+        if (bound > 0.0) std::frexp(bound, &eb);          // bound in [2^(eb-1), 2^eb)
+        rs->row_sh[r] = bound > 0.0 ? (float)std::ldexp(1.0, 15 - eb) : 1.f;
+        rs->row_inv[r] = bound > 0.0 ? (float)std::ldexp(1.0, eb - 15) : 1.f;
+    }
     // B images: row n < KX -> real part of H at kx = tile*KX + n; n >= KX -> imaginary part.
     //   Hr = sum_j yr Sr - yi Si ; Hi = sum_j yr Si + yi Sr   (k = 2j: yr, k = 2j+1: yi)
     rs->bimg_off.assign((size_t)P * N * ntiles, 0);
@@ -990,7 +1024,8 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     }
     // row-transform scratch: Tb samples x Cb channels per chunk
     {
-        const size_t per = (size_t)n_pol * grid_n * grid_n * 8;
+        // FP32 field (float2) on the FP32 path, FP16 (half2) on the tensor-core path
+        const size_t per = (size_t)n_pol * grid_n * grid_n * (pl->tc ? 4 : 8);
         long long budget = 16384LL << 20;
         if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, (long long)(atof(e) * 1048576.0));
         if (pl->tc) {
@@ -1005,6 +1040,8 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             pl->Tb = (int)tb;
         }
         if ((s = palloc(pl, &pl->d_H, (size_t)pl->Tb * pl->Cb * per)) != MOFF_OK) return bail(s);
+        if (pl->tc && encode_field_map(&pl->h_map, pl->d_H, grid_n, n_pol, pl->Cb, pl->Tb) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded"));
     }
     if (pl->tc) {
         RowSpec rs;
@@ -1025,6 +1062,11 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         if ((s = palloc(pl, &pl->d_yim, ny * 2)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_sy, (size_t)n_chan * 4)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_err, 16)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_rs_row_sh, rs.row_sh.size() * 4)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_rs_row_inv, rs.row_inv.size() * 4)) != MOFF_OK) return bail(s);
+        if (cudaMemcpy(pl->d_rs_row_sh, rs.row_sh.data(), rs.row_sh.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(pl->d_rs_row_inv, rs.row_inv.data(), rs.row_inv.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "tensor-core row scales upload failed"));
         if (cudaMemcpy(pl->d_rs_kp, rs.kp.data(), rs.kp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(pl->d_rs_seg_off, rs.seg_off.data(), rs.seg_off.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
             (!rs.seg_y.empty() &&

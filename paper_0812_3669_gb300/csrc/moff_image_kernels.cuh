@@ -13,6 +13,8 @@
 //                 registers, then added to FP64 accumulators).
 // The row-transformed field goes through global memory between the two.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "moff_fft.cuh"
 #include "moff_internal.h"
 
@@ -218,7 +220,8 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
             const int t = fa / PR, f = fa - t * PR;
             if (t >= nb) return nullptr;
             const int p = f / ROWS, rl = f - p * ROWS;
-            return outb + (((long long)(tb0 + t) * a.nc + cl) * P * N + (long long)p * N + ry0 + rl) * N;
+            return outb + (((long long)(tb0 + t) * a.slab_t + (long long)cl * a.slab_c) * P * N + (long long)p * N +
+                           ry0 + rl) * N;
         };
         if constexpr (GRID_ONLY) {
             for (int i = tid; i < F * N; i += kBlock) {
@@ -258,7 +261,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int NPEND>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 
-template <int N, int P>
+template <int N, int P, bool H16>
 __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
     using FP = FftPlan<N>;
     using TW = FftTw<N>;
@@ -266,9 +269,10 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
     constexpr int W = CS::W;
     constexpr int RL = CS::RL;
     constexpr int NPROD = P == 1 ? 1 : 4;
-    constexpr int TILE = P * N * W;                 // float2 per sample: [P][N][W]
-    constexpr int CHUNKS = TILE * 8 / 16;           // 16-byte pieces per tile
-    constexpr int ROWCH = W * 8 / 16;               // pieces per tile row
+    constexpr int TILE = P * N * W;                 // elements per sample: [P][N][W]
+    constexpr int EB = H16 ? 4 : 8;                 // bytes per input element (half2 or float2)
+    constexpr int CHUNKS = TILE * EB / 16;          // 16-byte pieces per tile
+    constexpr int ROWCH = W * EB / 16;              // pieces per tile row
 
     const int kx0 = blockIdx.x * W;
     const int cl = blockIdx.y;
@@ -277,18 +281,24 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
 
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *s_tw = reinterpret_cast<float2 *>(smem);
-    float2 *s_in = s_tw + ((TW::TOTAL + 1) & ~1);  // 2 staging tiles (16-byte aligned)
-    float2 *s_a = s_in + 2 * TILE;                 // pass outputs
+    unsigned char *s_in = reinterpret_cast<unsigned char *>(s_tw + ((TW::TOTAL + 1) & ~1));  // 2 staging tiles
+    float2 *s_a = reinterpret_cast<float2 *>(s_in + 2 * TILE * EB);   // pass outputs
     float2 *s_b = s_a + TILE;                      // second pass buffer (3-pass lengths only)
+    float *s_rs = reinterpret_cast<float *>(s_b + (FP::NP == 3 ? TILE : 0));   // FP16 path: per-row scale
 
     for (int i = tid; i < TW::TOTAL; i += kBlock) s_tw[i] = a.twp[i];
+    if constexpr (H16) {
+        const float cinv = a.inv_sw / a.sy[c];
+        for (int i = tid; i < P * N; i += kBlock) s_rs[i] = a.row_inv[i] * cinv;
+    }
 
     // Stage sample tt's [P][N][W] tile of the row-transformed field.
-    auto stage = [&](int tt, float2 *dst) {
-        const float2 *src = a.H + (long long)(tt * a.nc + cl) * P * N * N + kx0;
+    auto stage = [&](int tt, unsigned char *dst) {
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(a.H) +
+                                   (((long long)tt * a.slab_t + (long long)cl * a.slab_c) * P * N * N + kx0) * EB;
         for (int q = tid; q < CHUNKS; q += kBlock) {
             const int row = q / ROWCH, part = q - row * ROWCH;       // row = p*N + ry
-            cp_async16(dst + row * W + part * 2, src + (long long)row * N + part * 2);
+            cp_async16(dst + (row * W) * EB + part * 16, src + (long long)row * N * EB + part * 16);
         }
         cp_async_commit();
     };
@@ -304,13 +314,23 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
 
     for (int tt = 0; tt < a.nt; ++tt) {
         if (tt + 1 < a.nt) {
-            stage(tt + 1, s_in + ((tt + 1) & 1) * TILE);
+            stage(tt + 1, s_in + ((tt + 1) & 1) * TILE * EB);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
         __syncthreads();
-        const float2 *tin = s_in + (tt & 1) * TILE;
+        const unsigned char *tin = s_in + (tt & 1) * TILE * EB;
+        auto in_at = [&](int p, int row, int col) -> float2 {
+            const int e = (p * N + row) * W + col;
+            if constexpr (H16) {
+                const float2 f = __half22float2(reinterpret_cast<const __half2 *>(tin)[e]);
+                const float sc = s_rs[p * N + row];
+                return make_float2(f.x * sc, f.y * sc);
+            } else {
+                return reinterpret_cast<const float2 *>(tin)[e];
+            }
+        };
         {   // pass 0: staged tile -> registers -> s_a
             constexpr int R = FP::R0, NSL = N / R;
             for (int sl = tid; sl < W * NSL; sl += kBlock) {
@@ -319,7 +339,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                 for (int p = 0; p < P; ++p) {
                     float2 v[R];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = tin[(p * N + j + r * NSL) * W + col];
+                    for (int r = 0; r < R; ++r) v[r] = in_at(p, j + r * NSL, col);
                     dft<R, 1>(v);
 #pragma unroll
                     for (int r = 0; r < R; ++r) s_a[(p * N + stockham_out<R, 1>(j, r)) * W + col] = v[r];
@@ -388,10 +408,11 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
 }
 
 template <int N>
-size_t col_smem_bytes_t(int P) {
+size_t col_smem_bytes_t(int P, bool h16 = false) {
     using FP = FftPlan<N>;
-    const size_t tile = (size_t)P * N * ColShape<N>::W * 8;
-    return (size_t)((FftTw<N>::TOTAL + 1) & ~1) * 8 + tile * 2 + tile * (FP::NP == 3 ? 2 : 1);
+    const size_t tile = (size_t)P * N * ColShape<N>::W;
+    return (size_t)((FftTw<N>::TOTAL + 1) & ~1) * 8 + tile * (h16 ? 4 : 8) * 2 + tile * 8 * (FP::NP == 3 ? 2 : 1) +
+           (h16 ? (size_t)P * N * 4 : 0);
 }
 
 template <int N, int P, int TB, bool ST, bool GO>
@@ -424,10 +445,10 @@ cudaError_t launch_grid_p(int TB, bool staged, bool go, const GridArgs &a, int n
                   : launch_grid_s<N, P, false, false>(TB, a, n_stripes, smem, st);
 }
 
-template <int N, int P>
+template <int N, int P, bool H16>
 cudaError_t launch_cols_t(const ColArgs &a, cudaStream_t st) {
-    auto k = k_cols_acc<N, P>;
-    const size_t smem = col_smem_bytes_t<N>(P);
+    auto k = k_cols_acc<N, P, H16>;
+    const size_t smem = col_smem_bytes_t<N>(P, H16);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<dim3(N / ColShape<N>::W, a.nc), kBlock, smem, st>>>(a);
@@ -440,8 +461,9 @@ cudaError_t launch_cols_t(const ColArgs &a, cudaStream_t st) {
         return P == 1 ? launch_grid_p<NN, 1>(TB, staged, go, a, n_stripes, smem, st)                 \
                       : launch_grid_p<NN, 2>(TB, staged, go, a, n_stripes, smem, st);                \
     }                                                                                                \
-    cudaError_t launch_cols_n##NN(int P, const ColArgs &a, cudaStream_t st) {                        \
-        return P == 1 ? launch_cols_t<NN, 1>(a, st) : launch_cols_t<NN, 2>(a, st);                   \
+    cudaError_t launch_cols_n##NN(int P, const ColArgs &a, cudaStream_t st, bool h16) {              \
+        if (h16) return P == 1 ? launch_cols_t<NN, 1, true>(a, st) : launch_cols_t<NN, 2, true>(a, st); \
+        return P == 1 ? launch_cols_t<NN, 1, false>(a, st) : launch_cols_t<NN, 2, false>(a, st);      \
     }
 
 }  // namespace moff

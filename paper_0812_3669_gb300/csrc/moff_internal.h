@@ -1,6 +1,7 @@
 // moff_internal.h -- argument blocks and launchers shared by the host code
 // (moff_api.cu) and the kernel translation units.  Not part of the C ABI.
 #pragma once
+#include <cuda.h>   // CUtensorMap (type only; encoded through the runtime's driver entry point)
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -38,15 +39,23 @@ struct GridArgs {
     const float2 *con_tap;    // kernel value of each entry (0 for padding)
     const uint16_t *con_y;    // local voltage index (local antenna * P + input pol)
     const float2 *twp;        // pass twiddles of the N-point transform
-    float2 *out;              // [nt][nc][P][N][N] row-transformed (or raw, grid-only) field
+    float2 *out;              // row-transformed (or raw, grid-only) field: slab [P][N][N] of
+                              // (sample t, channel cl) at index t * slab_t + cl * slab_c
+    long long slab_t, slab_c;
 };
 
 // Column transform + square-and-integrate (Eq. m6 steps 3-4, second axis).
 struct ColArgs {
-    const float2 *H;          // [nt][nc][P][N][N]
+    const float2 *H;          // FP32 field, or (fp16 path) half2: slab [P][N][N] of (sample t,
+                              // channel cl) at index t * slab_t + cl * slab_c
+    long long slab_t, slab_c;
     int nt, c0, nc;
     const float2 *twp;
     double *acc;              // [C][n_prod][N][N] FP64 accumulators (added to)
+    // FP16 field only: value = half2 * row_inv[p*N + ry] * inv_sw / sy[c]
+    const float *row_inv;
+    const float *sy;
+    float inv_sw;
 };
 
 // FP16 tensor-core gridding + row transform: per (pol, grid row, kx tile) a
@@ -61,7 +70,10 @@ struct RowSpecArgs {
     const __half *yre, *yim;   // [nc][AP][Tpad] weighted, scaled voltages
     const float *sy;           // [C] voltage scales (powers of two)
     float inv_sw;              // 1 / spectrum scale (power of two)
-    float2 *H;                 // [nt][nc][P][N][N] row-transformed field
+    const float *row_sh;       // [P*N] per-row FP16 output scale (power of two)
+    __half2 *H;                // row-transformed field, FP16, scaled by row_sh: slab [P][N][N] of
+                               // (sample t, channel cl) at index t * slab_t + cl * slab_c
+    long long slab_t, slab_c;
     int *err;                  // set when a bounded wait gives up
 };
 
@@ -124,6 +136,7 @@ struct RowSpec {
     int kp_max = 0, max_seg = 0, ntiles = 1;
     float inv_sw = 1.f;
     std::vector<int> kp, seg_y;
+    std::vector<float> row_sh, row_inv;         // per (pol, row) FP16 field scale and its inverse
     std::vector<long long> seg_off, bimg_off;   // bimg_off in elements
     std::vector<__half> bimg;
 };
@@ -138,7 +151,7 @@ size_t pfb_smem_bytes(int CN);
 // Launchers (return the launch error, if any).
 cudaError_t launch_grid(int N, int P, int TB, bool staged, bool grid_only, const GridArgs &a, int n_stripes,
                         size_t smem, cudaStream_t st);
-cudaError_t launch_cols(int N, int P, const ColArgs &a, cudaStream_t st);
+cudaError_t launch_cols(int N, int P, const ColArgs &a, cudaStream_t st, bool h16 = false);
 cudaError_t launch_pfb(int CN, const PfbArgs &a, cudaStream_t st);
 cudaError_t launch_to_f32(const double *acc, float *out, long long n, cudaStream_t st);
 
@@ -150,13 +163,17 @@ cudaError_t launch_gain_scale(const float2 *gains, int C, int AP, float *sy, cud
 cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc, int AP,
                              const float2 *gains, const float *sy, int Tpad, __half *yre, __half *yim,
                              cudaStream_t st);
-cudaError_t launch_rowspec(int N, const RowSpecArgs &a, int cgroups, size_t smem, cudaStream_t st);
+cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap, int cgroups, size_t smem,
+                           cudaStream_t st);
+// Tensor map of the FP16 row-transformed field [Tb][Cb][P*N][N] (half2 as 32-bit
+// elements), box 32 kx x 32 samples, 128-byte swizzle: the store target of k_rowspec_tc.
+cudaError_t encode_field_map(CUtensorMap *map, void *H, int N, int P, int Cb, int Tb);
 
 // Per-N instantiations (one translation unit each, compiled in parallel).
 #define MOFF_DECLARE_N(NN)                                                                          \
     cudaError_t launch_grid_n##NN(int P, int TB, bool staged, bool grid_only, const GridArgs &a, int n_stripes, \
                                   size_t smem, cudaStream_t st);                                   \
-    cudaError_t launch_cols_n##NN(int P, const ColArgs &a, cudaStream_t st);
+    cudaError_t launch_cols_n##NN(int P, const ColArgs &a, cudaStream_t st, bool h16);
 MOFF_DECLARE_N(32)
 MOFF_DECLARE_N(64)
 MOFF_DECLARE_N(128)

@@ -171,12 +171,16 @@ extern "C" moff_status moff_image_noalloc(int n_ant, const double *pos, int ksiz
             g.con_y = reinterpret_cast<const uint16_t *>(sc + o_cy);
             g.twp = reinterpret_cast<const float2 *>(sc + o_tw);
             g.out = reinterpret_cast<float2 *>(sc + o_H);
+            g.slab_t = 1;
+            g.slab_c = Tb;
             NA_CK(launch_grid(N, P, b.tb, b.staged, false, g, b.n_stripes, b.grid_smem, st));
             ColArgs ca{};
             ca.H = reinterpret_cast<const float2 *>(sc + o_H);
             ca.nt = nt;
             ca.c0 = 0;              // sums of this chunk are indexed from its first channel
             ca.nc = nc;
+            ca.slab_t = g.slab_t;
+            ca.slab_c = g.slab_c;
             ca.twp = reinterpret_cast<const float2 *>(sc + o_tw);
             ca.acc = acc;
             NA_CK(launch_cols(N, P, ca, st));

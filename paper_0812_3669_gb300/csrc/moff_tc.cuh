@@ -161,6 +161,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// ---- TMA bulk tensor store (shared -> global) of one box of a 4-D tensor map,
+// tracked by this thread's bulk async-groups.  Coordinates are in elements,
+// innermost first; the innermost one times the element size must be a
+// multiple of 16 bytes.
+__device__ __forceinline__ void tma_store_4d(const void *tmap, uint32_t src_smem, int x, int y, int z, int w) {
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];\n" ::"l"(tmap),
+                 "r"(src_smem), "r"(x), "r"(y), "r"(z), "r"(w)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// Wait until at most NPEND of this thread's bulk groups still read shared memory.
+template <int NPEND>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(NPEND) : "memory");
+}
+// Wait until every bulk group of this thread has completed (writes performed).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 // Device-side error word written when a bounded wait gives up.
 constexpr int kErrWaitTimeout = 1;
 

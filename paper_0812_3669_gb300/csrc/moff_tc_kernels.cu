@@ -17,7 +17,8 @@
 //   k_volt_prep    decode, weight, scale and transpose the voltages to FP16 planes [c][voltage][t]
 //   k_rowspec_tc   per (pol, row, kx tile): B = row spectra resident in shared memory,
 //                  A = 128 samples of the row's segment voltages (cp.async, MN-major),
-//                  D = TMEM (double buffered), epilogue writes the FP32 row-transformed field.
+//                  D = TMEM (double buffered), epilogue writes the row-transformed field in
+//                  FP16 under an exact per-row power-of-two scale (undone by the column kernel).
 #include <cuda_fp16.h>
 
 #include "moff_fft.cuh"
@@ -108,22 +109,28 @@ __device__ __forceinline__ void cp_async16_tc(void *smem_dst, const void *gmem_s
 }
 __device__ __forceinline__ void cp_async_commit_tc() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all_tc() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait_tc() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 
 // Warp roles: warps 0-3 drain the TMEM accumulators (one lane quarter each),
 // warps 4-7 stage A in K-chunks of 64 with cp.async, warp 8 issues the MMAs
 // (one lane).  A: 3-stage ring of [128 samples x 64] MN-major chunks; B:
-// resident; accumulators: two in TMEM; epilogue: each warp transposes its 32
-// samples x 32 kx through shared memory so every global store instruction
-// writes 256 contiguous bytes of one sample's row.
+// resident; accumulators: two in TMEM; epilogue: each warp converts its 32
+// samples x 32 kx to FP16 into a 128-byte-swizzled box in shared memory and
+// one lane hands it to the TMA unit (bulk tensor store), two boxes in flight
+// per warp.  Per-thread global stores from four warps could not keep enough
+// writes in flight; the bulk stores can.
 constexpr int kEpiWarps = 4, kProdWarps = 4;
 constexpr int kTcRoleThreads = (kEpiWarps + kProdWarps + 1) * 32;
 constexpr int kAStages = 3, kKChunk = 64;
 constexpr int kAChunkBytes = 128 * kKChunk * 2;
-constexpr int kStageLd = 33;                        // float2 per staged row (padded)
+constexpr int kBoxBytes = 32 * 128;                 // 32 samples x 32 kx x half2
+constexpr int kEpiBufs = 2;                         // boxes per warp
 constexpr long long kWaitCycles = 4000000000LL;     // ~2 s at the SM clock
 
 template <int N>
-__global__ void __launch_bounds__(kTcRoleThreads, 1) k_rowspec_tc(const RowSpecArgs a) {
+__global__ void __launch_bounds__(kTcRoleThreads, 1)
+    k_rowspec_tc(const RowSpecArgs a, const __grid_constant__ CUtensorMap hmap) {
     using S = TcShape<N>;
     constexpr int KX = S::KX, NT = S::NT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -147,18 +154,21 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1) k_rowspec_tc(const RowSpecA
             const int cl = cb + it / ntb, t0b = (it % ntb) * 128;
             for (int i = tid; i < 128 * KX; i += blockDim.x) {
                 const int tt = i / KX, kx = i % KX, t = t0b + tt;
-                if (t < a.nt) a.H[((long long)t * a.nc + cl) * hslab + hrow + kx] = make_float2(0.f, 0.f);
+                if (t < a.nt) a.H[((long long)t * a.slab_t + (long long)cl * a.slab_c) * hslab + hrow + kx] =
+                    __floats2half2_rn(0.f, 0.f);
             }
         }
         return;
     }
     const int nchunk = (kp + kKChunk - 1) / kKChunk;
 
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // swizzled TMA boxes need 1024-byte alignment: round the base up (the size includes the slack)
+    unsigned char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *sB = smem;                                  // NT x kp, K-major (resident)
     unsigned char *sA = sB + (size_t)NT * a.kp_max * 2;        // kAStages x [128 x 64], MN-major
-    float2 *stage = reinterpret_cast<float2 *>(sA + (size_t)kAStages * kAChunkBytes);   // [4][32][kStageLd]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kEpiWarps * 32 * kStageLd);
+    unsigned char *sE = sA + (size_t)kAStages * kAChunkBytes;  // [4 warps][kEpiBufs] boxes, 1024-aligned
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sE + kEpiWarps * kEpiBufs * kBoxBytes);
     uint64_t *a_full = bars, *a_empty = bars + kAStages, *d_full = bars + 2 * kAStages,
              *d_empty = bars + 2 * kAStages + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kAStages + 4);
@@ -194,7 +204,9 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1) k_rowspec_tc(const RowSpecA
     const uint32_t tbase = *tslot;
 
     if (warp >= kEpiWarps && warp < kEpiWarps + kProdWarps) {
-        // ---------------- producers: chunk g (global counter) into stage g % kAStages
+        // ---------------- producers: chunk g (global counter) into stage g % kAStages.
+        // Up to kAStages chunks are in flight: after issuing chunk g the
+        // producers wait only for chunk g - (kAStages - 1) and release it.
         const int ptid = tid - kEpiWarps * 32;
         int g = 0;
         for (int i = 0; i < nitems && !*abort_flag; ++i) {
@@ -208,7 +220,9 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1) k_rowspec_tc(const RowSpecA
                     break;
                 unsigned char *sa = sA + st * kAChunkBytes;
                 for (int q = ptid; q < kKChunk * 16; q += kProdWarps * 32) {
-                    const int kk = q >> 4, m8 = q & 15;
+                    // a warp covers 8 consecutive k x 4 sample groups: four 128-byte bank
+                    // sweeps in shared memory, 64 contiguous bytes per segment in global
+                    const int kk = ((q >> 7) << 3) | (q & 7), m8 = (q >> 3) & 15;
                     const int k = ch * kKChunk + kk, j = k >> 1;
                     unsigned char *d = sa + m8 * 128 + (kk >> 3) * 2048 + (kk & 7) * 16;
                     if (k < kp && j < nseg) {
@@ -218,11 +232,18 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1) k_rowspec_tc(const RowSpecA
                     }
                 }
                 cp_async_commit_tc();
-                cp_async_wait_all_tc();
-                tc::fence_async_smem();
-                tc::mbar_arrive(&a_full[st]);
+                if (g >= kAStages - 1) {
+                    cp_async_wait_tc<kAStages - 1>();          // chunk g - (kAStages-1) has landed
+                    tc::fence_async_smem();
+                    tc::mbar_arrive(&a_full[(g - (kAStages - 1)) % kAStages]);
+                }
             }
         }
+        // release the chunks still in flight, oldest first
+        const int g0 = g - (kAStages - 1) > 0 ? g - (kAStages - 1) : 0;
+        cp_async_wait_all_tc();
+        tc::fence_async_smem();
+        for (int gg = g0; gg < g; ++gg) tc::mbar_arrive(&a_full[gg % kAStages]);
     } else if (warp == kEpiWarps + kProdWarps) {
         // ---------------- MMA issuer (one lane)
         if (lane == 0) {
@@ -256,33 +277,46 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1) k_rowspec_tc(const RowSpecA
         __syncwarp();
     } else {
         // ---------------- epilogue warps 0-3: TMEM lanes 32w..32w+31 = samples
-        float2 *stw = stage + warp * 32 * kStageLd;
+        unsigned char *sw = sE + warp * kEpiBufs * kBoxBytes;
+        int nbox = 0;
         for (int i = 0; i < nitems; ++i) {
             const int b = i & 1;
             if (!tc::mbar_wait_abortable(&d_full[b], (uint32_t)((i >> 1) & 1), kWaitCycles, abort_flag)) break;
             tc::fence_after_sync();
             const int cl = cb + i / ntb, t0w = (i % ntb) * 128 + warp * 32;
-            const float inv = a.inv_sw / a.sy[a.c0 + cl];
+            const float inv = a.row_sh[pr];   // exact power of two: FP16 range for this row
             const uint32_t dcol = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * NT);
-            float2 *hbase = a.H + ((long long)t0w * a.nc + cl) * hslab + hrow;
-            const long long tstep = (long long)a.nc * hslab;
 #pragma unroll 1
-            for (int k0 = 0; k0 < KX; k0 += 32) {
+            for (int k0 = 0; k0 < KX; k0 += 32, ++nbox) {
                 float vr[32], vi[32];
                 tc::tmem_ld32(dcol + (uint32_t)k0, vr);
                 tc::tmem_ld32(dcol + (uint32_t)(KX + k0), vi);
-                // this lane holds sample t0w + lane, kx k0..k0+31: transpose through shared memory
+                unsigned char *box = sw + (nbox % kEpiBufs) * kBoxBytes;
+                if (nbox >= kEpiBufs) {                  // the store that last read this box is done with it
+                    if (lane == 0) tc::bulk_wait_read<kEpiBufs - 1>();
+                    __syncwarp();
+                }
+                // lane = sample t0w + lane: its 32 kx as eight 16-byte chunks of one 128-byte row,
+                // chunk q stored at q ^ (row % 8) (the tensor map's 128-byte swizzle)
 #pragma unroll
-                for (int u = 0; u < 32; ++u) stw[lane * kStageLd + u] = make_float2(vr[u] * inv, vi[u] * inv);
+                for (int q = 0; q < 8; ++q) {
+                    __half2 h[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) h[u] = __floats2half2_rn(vr[4 * q + u] * inv, vi[4 * q + u] * inv);
+                    *reinterpret_cast<uint4 *>(box + lane * 128 + ((q ^ (lane & 7)) << 4)) =
+                        *reinterpret_cast<const uint4 *>(h);
+                }
+                tc::fence_async_smem();
                 __syncwarp();
-#pragma unroll 4
-                for (int r = 0; r < 32; ++r)
-                    if (t0w + r < a.nt) hbase[r * tstep + k0 + lane] = stw[r * kStageLd + lane];
-                __syncwarp();
+                if (lane == 0) {
+                    tc::tma_store_4d(&hmap, tc::smem_u32(box), tile * KX + k0, p * N + ry, cl, t0w);
+                    tc::bulk_commit();
+                }
             }
             tc::fence_before_sync();
             tc::mbar_arrive(&d_empty[b]);
         }
+        if (lane == 0) tc::bulk_wait_all();
     }
     if (*abort_flag && tid == 0) atomicExch(a.err, tc::kErrWaitTimeout);
     cp_async_wait_all_tc();
@@ -296,8 +330,8 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1) k_rowspec_tc(const RowSpecA
 
 size_t rowspec_smem_bytes(int N, int kp_max, int max_seg) {
     const int KX = N < 128 ? N : 128, NT = 2 * KX;
-    size_t b = (size_t)NT * kp_max * 2 + (size_t)kAStages * kAChunkBytes + (size_t)kEpiWarps * 32 * kStageLd * 8 +
-               (size_t)(2 * kAStages + 4) * 8 + 8 + (size_t)max_seg * 4;
+    size_t b = 1024 + (size_t)NT * kp_max * 2 + (size_t)kAStages * kAChunkBytes +
+               (size_t)kEpiWarps * kEpiBufs * kBoxBytes + (size_t)(2 * kAStages + 4) * 8 + 8 + (size_t)max_seg * 4;
     b = (b + 127) & ~(size_t)127;
     // one CTA per SM: two CTAs must never wait on each other's TMEM columns
     return b < 120 * 1024 ? 120 * 1024 : b;
@@ -319,23 +353,45 @@ cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int
 }
 
 template <int N>
-cudaError_t launch_rowspec_t(const RowSpecArgs &a, int cgroups, size_t smem, cudaStream_t st) {
+cudaError_t launch_rowspec_t(const RowSpecArgs &a, const CUtensorMap &hmap, int cgroups, size_t smem,
+                             cudaStream_t st) {
     auto k = k_rowspec_tc<N>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<dim3(a.P * N * TcShape<N>::NTILES, cgroups), kTcRoleThreads, smem, st>>>(a);
+    k<<<dim3(a.P * N * TcShape<N>::NTILES, cgroups), kTcRoleThreads, smem, st>>>(a, hmap);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rowspec(int N, const RowSpecArgs &a, int cgroups, size_t smem, cudaStream_t st) {
+cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap, int cgroups, size_t smem,
+                           cudaStream_t st) {
     switch (N) {
-        case 32: return launch_rowspec_t<32>(a, cgroups, smem, st);
-        case 64: return launch_rowspec_t<64>(a, cgroups, smem, st);
-        case 128: return launch_rowspec_t<128>(a, cgroups, smem, st);
-        case 256: return launch_rowspec_t<256>(a, cgroups, smem, st);
-        case 512: return launch_rowspec_t<512>(a, cgroups, smem, st);
+        case 32: return launch_rowspec_t<32>(a, hmap, cgroups, smem, st);
+        case 64: return launch_rowspec_t<64>(a, hmap, cgroups, smem, st);
+        case 128: return launch_rowspec_t<128>(a, hmap, cgroups, smem, st);
+        case 256: return launch_rowspec_t<256>(a, hmap, cgroups, smem, st);
+        case 512: return launch_rowspec_t<512>(a, hmap, cgroups, smem, st);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t encode_field_map(CUtensorMap *map, void *H, int N, int P, int Cb, int Tb) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const cuuint64_t row = (cuuint64_t)N * 4, slab = (cuuint64_t)P * N * row;
+    const cuuint64_t dims[4] = {(cuuint64_t)N, (cuuint64_t)P * N, (cuuint64_t)Cb, (cuuint64_t)Tb};
+    const cuuint64_t strides[3] = {row, slab, slab * (cuuint64_t)Cb};
+    const cuuint32_t box[4] = {32, 1, 1, 32};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, H, dims, strides, box, estr,
+                                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace moff
