@@ -49,6 +49,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp16tc", action="store_true", help="skip the FP16 tensor-core leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-stream (serving) leg")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-channel-at-a-time FP32 leg")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests per load point of the serving leg")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--frames", type=int, default=WL["frames"],
                     help="samples per step (smaller values give a profiling case, not a bench line)")
@@ -93,11 +96,12 @@ def flops_per_snapshot(kind, A=WL["n_ant"], P=WL["n_pol"], N=WL["grid_n"], K=WL[
     raise ValueError(kind)
 
 
-def tc_row_flops_per_snapshot(pos, N=WL["grid_n"], P=WL["n_pol"], K=WL["ksize"], KX=64):
+def tc_row_flops_per_snapshot(pos, N=WL["grid_n"], P=WL["n_pol"], K=WL["ksize"]):
     """Tensor-core flops per channel-snapshot of the row contraction as executed:
-    per (pol, grid row) 2 * 128-column product width * padded contraction length,
-    per kx tile of 64 (real and imaginary output columns)."""
+    per (pol, grid row, kx tile of KX = min(N, 128)) 2 x (2 KX output columns:
+    real and imaginary parts) x the padded contraction length."""
     import numpy as np
+    KX = min(N, 128)
     anc = np.floor(np.asarray(pos) + 0.5).astype(int) % N
     rows = np.bincount(((anc[:, 1][:, None] + np.arange(K)[None, :] - K // 2) % N).ravel(), minlength=N)
     kp = ((2 * rows + 15) // 16) * 16
@@ -253,6 +257,105 @@ def traffic_for(kernel_key, src_files):
     if rec.get("source_sha1") != h.hexdigest():
         return None
     return rec.get("bytes_per_launch")
+
+
+def serving_leg(args, moff, synth, torch):
+    """Request stream over sub-arrays of uneven size (MOFF_SERVED plans, one
+    moff_server): first a closed burst to find the saturation rate, then Poisson
+    arrivals at fractions of it.  Reports p50/p99 block latency and throughput."""
+    import numpy as np
+    mix = synth.config_serving()
+    plans, blocks = [], []
+    for i, a in enumerate(mix):
+        pl = moff.Plan(a["pos"], a["taps"], a["N"], a["C"], 2, served=True)
+        pl.set_gains(a["gains"])
+        plans.append(pl)
+        blocks.append(synth.device_codes(SEED + 500 + i, a["T"], a["C"], a["A"], 2))
+    torch.cuda.synchronize()
+    units = [a["C"] * a["T"] for a in mix]
+    rng = np.random.default_rng(SEED + 77)
+    srv = moff.Server(24 << 30, 4)
+    try:
+        for i in range(len(plans)):                       # warm every plan once
+            srv.submit(plans[i], blocks[i])
+        srv.wait(0, 600000)
+        srv.stats(reset=True)
+        # saturation: everything at once
+        order = rng.integers(0, len(plans), size=args.serve_requests)
+        t0 = time.perf_counter()
+        for i in order:
+            srv.submit(plans[i], blocks[i])
+        srv.wait(0, 600000)
+        wall = time.perf_counter() - t0
+        sat = srv.stats(reset=True)
+        sat_req_s = len(order) / wall
+        points = []
+        for load in (0.5, 0.9):
+            rate = load * sat_req_s
+            order = rng.integers(0, len(plans), size=args.serve_requests)
+            gaps = rng.exponential(1.0 / rate, size=len(order))
+            t0 = time.perf_counter()
+            due = t0
+            for i, g in zip(order, gaps):
+                due += g
+                while True:
+                    now = time.perf_counter()
+                    if now >= due:
+                        break
+                    time.sleep(min(due - now, 0.002))
+                srv.submit(plans[i], blocks[i])
+            srv.wait(0, 600000)
+            st = srv.stats(reset=True)
+            points.append({"load": load, "offered_req_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                           "throughput": st["throughput"], "requests": st["completed"]})
+    finally:
+        srv.close()
+        for pl in plans:
+            pl.close()
+    return {
+        "unit": UNIT, "precision": "fp32", "slots": 4, "pool_bytes": 24 << 30,
+        "mix": [{"antennas": a["A"], "grid_n": a["N"], "channels": a["C"], "samples": a["T"]} for a in mix],
+        "mix_note": "request sizes scaled to channels in {64,128,256} and 100-300 samples so a sweep takes seconds",
+        "saturation": {"req_per_s": sat_req_s, "throughput": sat["throughput"], "p50_ms": sat["p50_ms"],
+                       "p99_ms": sat["p99_ms"], "requests": sat["completed"]},
+        "points": points, "mean_units_per_request": float(np.mean(units)),
+    }
+
+
+def plain_leg(args, moff, synth, torch):
+    """The plain FP32 form: the same kernels run one channel per launch pair
+    (field scratch sized for a single channel), on the bench array and device
+    codes, 64 channels x 1000 samples."""
+    A, P, N = WL["n_ant"], WL["n_pol"], WL["grid_n"]
+    Cs, F = 64, args.frames
+    cfg = synth.config_dualpol(n_chan=Cs)
+    per = P * N * N * 8
+    old = os.environ.get("MOFF_SCRATCH_MB")
+    os.environ["MOFF_SCRATCH_MB"] = str(32 * per / 1048576.0)
+    try:
+        pl = moff.Plan(cfg["pos"], cfg["taps"], N, Cs, P)
+    finally:
+        if old is None:
+            os.environ.pop("MOFF_SCRATCH_MB", None)
+        else:
+            os.environ["MOFF_SCRATCH_MB"] = old
+    info = pl.info()
+    pl.set_gains(cfg["gains"])
+    codes = synth.device_codes(SEED + 900, F, Cs, A, P)
+    pl.submit(codes)
+    pl.sync()
+    pl.reset()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    pl.submit(codes)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    pl.close()
+    return {"value": Cs * F / (ms / 1e3), "unit": UNIT, "channels": Cs, "samples": F,
+            "chan_chunk": info["chan_chunk"], "time_chunk": info["time_chunk"],
+            "form": "FP32, one channel per grid/column launch pair, codes on device (no F-stage)"}
 
 
 def run_ours(args):
@@ -412,6 +515,13 @@ def run_ours(args):
                "steps": args.e2e_steps, "api": "moff_submit_adc(host pinned ADC) + moff_read_image(host)"}
     plan.close()
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_leg(args, moff, synth, torch)
+    plain = None
+    if not args.no_plain:
+        plain = plain_leg(args, moff, synth, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline_subprocess()
@@ -428,7 +538,7 @@ def run_ours(args):
                        "parallelism": f"{world} independent replica(s), one integration each"},
             "fx_equiv_tcmac_per_s": fx_eq / 1e12,
             "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches, "clocks": clk,
-            "e2e": e2e, "cpu_baseline": cpu, "fp16tc": fp16,
+            "e2e": e2e, "cpu_baseline": cpu, "fp16tc": fp16, "serving": serving, "plain_fp32_one_channel": plain,
         }), flush=True)
     if dist is not None:
         dist.destroy_process_group()

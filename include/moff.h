@@ -71,7 +71,11 @@ enum {
                                  and the squaring stay FP32, cross-block sums FP64.  Needs at most
                                  128 kernel rows landing on any one grid row per pol. */
     MOFF_FSTAGE = 1u << 1,    /* enable the polyphase F-stage (moff_submit_adc, moff_channelise) */
-    MOFF_JONES = 1u << 2      /* kernels are full 2x2 Jones matrices (n_pol must be 2) */
+    MOFF_JONES = 1u << 2,     /* kernels are full 2x2 Jones matrices (n_pol must be 2) */
+    MOFF_SERVED = 1u << 3     /* the plan does not own its per-block scratch (the row-transformed
+                                 field; with MOFF_PREC_FP16TC also the FP16 voltage planes): a
+                                 moff_server lends it from its pool for each block.  Such a plan
+                                 takes blocks only through moff_server_submit. */
 };
 
 /*
@@ -253,6 +257,75 @@ moff_status moff_image_noalloc(int n_ant, const double *pos, int ksize, const fl
  * within the wait limit (a few seconds).
  */
 moff_status moff_tc_selftest(const void *a, const void *b, float *d, int n, int k, int mode, void *cuda_stream);
+
+/*
+ * ---- Serving.  The paper has no counterpart: it treats the correlator as a
+ * stream of channelised blocks (Sec. 2); this is the library's streaming front
+ * end for many arrays at once.
+ *
+ * moff_server_create -- a request loop on the current device over plans created
+ * with MOFF_SERVED (sub-arrays of uneven antenna count and grid size).  Plans keep
+ * their kernels, gains and partial integrations resident; each admitted block
+ * borrows its plan's scratch (plus room for its voltages when they come from host
+ * memory) from one device pool until its GPU work has finished.
+ *   hbm_budget_bytes  size of that pool, allocated once here (>= 1024).
+ *   n_slots           most blocks on the GPU at once, 1..64; each runs on its plan's
+ *                     stream, so blocks of different plans overlap on the device.
+ * Errors: MOFF_EINVAL, MOFF_ENOMEM (pool), MOFF_ECUDA.
+ */
+typedef struct moff_server moff_server; /* opaque, owned by the library */
+moff_status moff_server_create(moff_server **out, long long hbm_budget_bytes, int n_slots);
+
+/*
+ * moff_server_submit -- queue one voltage block (Eq. m6 steps 1-4 over its
+ * samples, added to the plan's integration) and return at once.
+ *   plan      created with MOFF_SERVED on the server's device.
+ *   volt, n_time, on_device  as for moff_submit, except that the caller keeps the
+ *             buffer alive and unmodified until the ticket is done either way (a host
+ *             block is copied when the block starts).
+ *   ticket    receives the block's id (>= 1).
+ * Blocks start in arrival order as slots and pool memory free up: a block whose
+ * plan has one on the GPU waits for it (a plan's blocks run in submission order),
+ * and a later block may start ahead of one that does not fit yet only if it leaves
+ * at least that block's bytes free.  MOFF_ENOMEM: the block can never fit the pool.
+ * MOFF_ESTATE: the plan is not MOFF_SERVED, is on another device, or the server is
+ * shutting down.  From submit until the plan's last ticket is done, call no other
+ * entry point on that plan (thread-safe calls are those on the server).
+ */
+moff_status moff_server_submit(moff_server *srv, moff_plan *plan, const uint8_t *volt, int n_time,
+                               int on_device, long long *ticket);
+
+/*
+ * moff_server_poll -- state of a ticket without waiting: 0 queued, 1 on the GPU,
+ * 2 done, or the (negative) moff_status its block failed with.  latency_ms (may be
+ * NULL) receives the time from submit to the end of the block's GPU work once it is
+ * done, else 0.  The last 65536 finished tickets stay known; older ones give
+ * MOFF_EINVAL.
+ */
+moff_status moff_server_poll(moff_server *srv, long long ticket, int *state, double *latency_ms);
+
+/*
+ * moff_server_wait -- wait until a ticket (ticket = 0: every block submitted so far)
+ * is done; timeout_ms < 0 waits without limit, else MOFF_ETIMEDOUT on expiry.
+ * Returns the block's failure status if it failed.
+ */
+moff_status moff_server_wait(moff_server *srv, long long ticket, int timeout_ms);
+
+/*
+ * moff_server_stats -- over the blocks finished since the last reset: the 50th and
+ * 99th percentile block latency (ms, submit to end of GPU work, nearest rank), the
+ * throughput in channel-snapshots per second (their C x n_time summed, over the span
+ * from the window's first submit to its last completion) and their count.  Any output
+ * may be NULL.  reset = 1 starts a new window after reading.
+ */
+moff_status moff_server_stats(moff_server *srv, double *p50_ms, double *p99_ms, double *throughput,
+                              long long *completed, int reset);
+
+/*
+ * moff_server_destroy -- cancel the blocks that have not started (their tickets end
+ * with MOFF_ESTATE), wait for those on the GPU, free the pool.  NULL is a no-op.
+ */
+moff_status moff_server_destroy(moff_server *srv);
 
 /* moff_plan_destroy -- wait for the plan's work, free everything.  NULL is a no-op. */
 moff_status moff_plan_destroy(moff_plan *plan);

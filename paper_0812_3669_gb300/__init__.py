@@ -25,8 +25,10 @@ __all__ = [
     "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
     "moff_plan_info", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
-    "moff_image_noalloc", "moff_tc_selftest",
-    "Plan", "header_symbols", "KERNEL_KINDS",
+    "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED",
+    "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
+    "moff_server_destroy",
+    "Plan", "Server", "header_symbols", "KERNEL_KINDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -37,6 +39,7 @@ MOFF_PREC_FP32 = 0
 MOFF_PREC_FP16TC = 1
 MOFF_FSTAGE = 1 << 1
 MOFF_JONES = 1 << 2
+MOFF_SERVED = 1 << 3
 
 KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep"}
 
@@ -70,6 +73,13 @@ _SIGS = {
     "moff_timing": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
     "moff_image_noalloc": [_i, _vp, _i, _vp, _i, _i, _i, _u, _vp, _i, _vp, _vp, _vp],
     "moff_tc_selftest": [_vp, _vp, _vp, _i, _i, _i, _vp],
+    "moff_server_create": [ctypes.POINTER(_vp), _ll, _i],
+    "moff_server_submit": [_vp, _vp, _vp, _i, _i, ctypes.POINTER(_ll)],
+    "moff_server_poll": [_vp, _ll, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)],
+    "moff_server_wait": [_vp, _ll, _i],
+    "moff_server_stats": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
+    "moff_server_destroy": [_vp],
 }
 
 
@@ -268,11 +278,101 @@ def moff_plan_destroy(plan):
 
 # ----------------------------------------------------------------- convenience
 
+def moff_server_create(hbm_budget_bytes, n_slots):
+    out = ctypes.c_void_p()
+    _check(lib().moff_server_create(ctypes.byref(out), int(hbm_budget_bytes), int(n_slots)))
+    return out
+
+
+def moff_server_submit(server, plan, volt):
+    """Queue ``volt`` uint8 [T][C][A][P] for a MOFF_SERVED plan; returns the ticket.
+    The caller keeps ``volt`` alive until the ticket is done."""
+    p, dev = _addr(volt)
+    t = ctypes.c_longlong(0)
+    _check(lib().moff_server_submit(server, plan, p, int(volt.shape[0]), dev, ctypes.byref(t)))
+    return t.value
+
+
+def moff_server_poll(server, ticket):
+    """(state, latency_ms): state 0 queued, 1 on the GPU, 2 done, < 0 failed."""
+    st = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().moff_server_poll(server, int(ticket), ctypes.byref(st), ctypes.byref(ms)))
+    return st.value, ms.value
+
+
+def moff_server_wait(server, ticket=0, timeout_ms=-1):
+    _check(lib().moff_server_wait(server, int(ticket), int(timeout_ms)))
+
+
+def moff_server_stats(server, reset=0):
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(lib().moff_server_stats(server, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n),
+                                   int(reset)))
+    return dict(p50_ms=a.value, p99_ms=b.value, throughput=c.value, completed=n.value)
+
+
+def moff_server_destroy(server):
+    _check(lib().moff_server_destroy(server))
+
+
+class Server:
+    """Streaming request loop over MOFF_SERVED plans (owns a ``moff_server``).
+    Keeps every submitted block referenced until its ticket is seen done."""
+
+    def __init__(self, hbm_budget_bytes, n_slots):
+        self.handle = moff_server_create(hbm_budget_bytes, n_slots)
+        self._held = {}
+
+    def submit(self, plan, volt):
+        h = plan.handle if isinstance(plan, Plan) else plan
+        t = moff_server_submit(self.handle, h, volt)
+        self._held[t] = volt
+        return t
+
+    def poll(self, ticket):
+        st, ms = moff_server_poll(self.handle, ticket)
+        if st == 2 or st < 0:
+            self._held.pop(ticket, None)
+        return st, ms
+
+    def wait(self, ticket=0, timeout_ms=-1):
+        moff_server_wait(self.handle, ticket, timeout_ms)
+        if ticket == 0:
+            self._held.clear()
+        else:
+            self._held.pop(ticket, None)
+
+    def stats(self, reset=False):
+        return moff_server_stats(self.handle, int(reset))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            moff_server_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Plan:
     """One array's imaging plan (owns a ``moff_plan``)."""
 
-    def __init__(self, pos, taps, grid_n, n_chan, n_pol, jones=False, fstage=False, stream=None, fp16tc=False):
+    def __init__(self, pos, taps, grid_n, n_chan, n_pol, jones=False, fstage=False, stream=None, fp16tc=False,
+                 served=False):
         flags = (MOFF_JONES if jones else 0) | (MOFF_FSTAGE if fstage else 0) | (MOFF_PREC_FP16TC if fp16tc else 0)
+        flags |= MOFF_SERVED if served else 0
         if stream is None:
             try:
                 import torch

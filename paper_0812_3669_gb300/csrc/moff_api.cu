@@ -245,6 +245,9 @@ struct moff_plan {
     long long *d_rs_seg_off = nullptr, *d_rs_bimg_off = nullptr;
     float *d_rs_row_sh = nullptr, *d_rs_row_inv = nullptr;
     CUtensorMap h_map;                 // tensor-core path: store map of the FP16 field
+    // served plans: per-block scratch (field, FP16 voltage planes) lent by a moff_server
+    bool served = false;
+    size_t h_bytes = 0, y_bytes = 0, scratch_bytes = 0;
     __half *d_rs_bimg = nullptr, *d_yre = nullptr, *d_yim = nullptr;
     float *d_sy = nullptr;
 
@@ -906,6 +909,14 @@ moff_status check_plan(const moff_plan *pl) {
     return MOFF_OK;
 }
 
+// Entry points that need the plan's own scratch.
+moff_status check_unserved(const moff_plan *pl) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (pl->served) return fail(MOFF_ESTATE, "plan was created with MOFF_SERVED: submit its blocks with moff_server_submit");
+    return MOFF_OK;
+}
+
 moff_status run_pfb(moff_plan *pl, const int8_t *adc, long long n_samp, int F, int kind, void *out) {
     PfbArgs p{};
     p.adc = adc;
@@ -940,6 +951,42 @@ moff_status check_adc(moff_plan *pl, const int8_t *adc, long long n_samp, int *F
 
 }  // namespace
 
+namespace moff {
+
+size_t plan_scratch_bytes(const moff_plan *pl) { return pl->scratch_bytes; }
+size_t plan_block_bytes(const moff_plan *pl, int n_time) { return (size_t)n_time * pl->C * pl->A * pl->P; }
+long long plan_units(const moff_plan *pl, int n_time) { return (long long)n_time * pl->C; }
+bool plan_is_served(const moff_plan *pl) { return pl->served; }
+int plan_device(const moff_plan *pl) { return pl->device; }
+cudaStream_t plan_stream(const moff_plan *pl) { return pl->st; }
+
+moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, int n_time, int on_device) {
+    unsigned char *base = static_cast<unsigned char *>(scratch);
+    pl->d_H = reinterpret_cast<float2 *>(base);
+    size_t off = align_up(pl->h_bytes, 1024);
+    if (pl->tc) {
+        pl->d_yre = reinterpret_cast<__half *>(base + off);
+        off += align_up(pl->y_bytes, 1024);
+        pl->d_yim = reinterpret_cast<__half *>(base + off);
+        off += align_up(pl->y_bytes, 1024);
+        if (encode_field_map(&pl->h_map, pl->d_H, pl->N, pl->P, pl->Cb, pl->Tb) != cudaSuccess)
+            return fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded");
+    }
+    const long long tstride = (long long)pl->C * pl->A * pl->P;
+    const uint8_t *src = volt;
+    if (!on_device) {
+        uint8_t *dst = base + off;
+        MOFF_CK(cudaMemcpyAsync(dst, volt, plan_block_bytes(pl, n_time), cudaMemcpyHostToDevice, pl->st));
+        src = dst;
+    }
+    moff_status s = run_image(pl, src, n_time, tstride);
+    if (s != MOFF_OK) return s;
+    pl->n_samples += n_time;
+    return MOFF_OK;
+}
+
+}  // namespace moff
+
 extern "C" {
 
 const char *moff_last_error(void) { return g_err.c_str(); }
@@ -956,7 +1003,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         return fail(MOFF_EINVAL, "ksize (%d) must be odd, in [1, 15] and <= grid_n", ksize);
     if (n_chan < 1) return fail(MOFF_EINVAL, "n_chan (%d) must be >= 1", n_chan);
     if (n_pol != 1 && n_pol != 2) return fail(MOFF_EINVAL, "n_pol (%d) must be 1 or 2", n_pol);
-    if (flags & ~(unsigned)(MOFF_FSTAGE | MOFF_JONES | MOFF_PREC_FP16TC))
+    if (flags & ~(unsigned)(MOFF_FSTAGE | MOFF_JONES | MOFF_PREC_FP16TC | MOFF_SERVED))
         return fail(MOFF_EINVAL, "unknown flag bits 0x%x", flags);
     if ((flags & MOFF_JONES) && n_pol != 2) return fail(MOFF_EINVAL, "MOFF_JONES requires n_pol = 2");
     if ((flags & MOFF_FSTAGE) && (!is_pow2(n_chan) || n_chan < 32 || n_chan > 2048))
@@ -973,6 +1020,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     pl->jones = (flags & MOFF_JONES) != 0;
     pl->fstage = (flags & MOFF_FSTAGE) != 0;
     pl->tc = (flags & MOFF_PREC_FP16TC) != 0;
+    pl->served = (flags & MOFF_SERVED) != 0;
     auto bail = [&](moff_status s) {
         std::string msg = g_err;
         destroy_plan(pl);
@@ -1026,7 +1074,8 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     {
         // FP32 field (float2) on the FP32 path, FP16 (half2) on the tensor-core path
         const size_t per = (size_t)n_pol * grid_n * grid_n * (pl->tc ? 4 : 8);
-        long long budget = 16384LL << 20;
+        // served plans borrow their scratch per block from a shared pool: keep it modest
+        long long budget = pl->served ? (2048LL << 20) : (16384LL << 20);
         if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, (long long)(atof(e) * 1048576.0));
         if (pl->tc) {
             // the tensor-core path works on 128 samples per product
@@ -1039,9 +1088,12 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             pl->Cb = (int)cb;
             pl->Tb = (int)tb;
         }
-        if ((s = palloc(pl, &pl->d_H, (size_t)pl->Tb * pl->Cb * per)) != MOFF_OK) return bail(s);
-        if (pl->tc && encode_field_map(&pl->h_map, pl->d_H, grid_n, n_pol, pl->Cb, pl->Tb) != cudaSuccess)
-            return bail(fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded"));
+        pl->h_bytes = (size_t)pl->Tb * pl->Cb * per;
+        if (!pl->served) {
+            if ((s = palloc(pl, &pl->d_H, pl->h_bytes)) != MOFF_OK) return bail(s);
+            if (pl->tc && encode_field_map(&pl->h_map, pl->d_H, grid_n, n_pol, pl->Cb, pl->Tb) != cudaSuccess)
+                return bail(fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded"));
+        }
     }
     if (pl->tc) {
         RowSpec rs;
@@ -1058,8 +1110,11 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         if ((s = palloc(pl, &pl->d_rs_seg_y, std::max<size_t>(rs.seg_y.size(), 1) * 4)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_rs_bimg_off, rs.bimg_off.size() * 8)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_rs_bimg, std::max<size_t>(rs.bimg.size(), 8) * 2)) != MOFF_OK) return bail(s);
-        if ((s = palloc(pl, &pl->d_yre, ny * 2)) != MOFF_OK) return bail(s);
-        if ((s = palloc(pl, &pl->d_yim, ny * 2)) != MOFF_OK) return bail(s);
+        pl->y_bytes = ny * 2;
+        if (!pl->served) {
+            if ((s = palloc(pl, &pl->d_yre, ny * 2)) != MOFF_OK) return bail(s);
+            if ((s = palloc(pl, &pl->d_yim, ny * 2)) != MOFF_OK) return bail(s);
+        }
         if ((s = palloc(pl, &pl->d_sy, (size_t)n_chan * 4)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_err, 16)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_rs_row_sh, rs.row_sh.size() * 4)) != MOFF_OK) return bail(s);
@@ -1097,6 +1152,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             return bail(fail(MOFF_ECUDA, "F-stage table upload failed"));
         if ((s = upload_fstage(pl, 8, nullptr, 1.f)) != MOFF_OK) return bail(s);
     }
+    pl->scratch_bytes = align_up(pl->h_bytes, 1024) + (pl->tc ? 2 * align_up(pl->y_bytes, 1024) : 0);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(MOFF_ECUDA, "plan set-up failed"));
     *out = pl;
     g_err.clear();
@@ -1131,7 +1187,7 @@ moff_status moff_set_fstage(moff_plan *pl, int n_taps, const float *coeffs, floa
 }
 
 moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_device) {
-    moff_status s = check_plan(pl);
+    moff_status s = check_unserved(pl);
     if (s != MOFF_OK) return s;
     if (!volt) return fail(MOFF_EINVAL, "volt is NULL");
     if (n_time < 1) return fail(MOFF_EINVAL, "n_time (%d) must be >= 1", n_time);
@@ -1151,7 +1207,7 @@ moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_d
 }
 
 moff_status moff_submit_adc(moff_plan *pl, const int8_t *adc, long long n_samp, int on_device) {
-    moff_status s = check_plan(pl);
+    moff_status s = check_unserved(pl);
     if (s != MOFF_OK) return s;
     int F = 0;
     if ((s = check_adc(pl, adc, n_samp, &F)) != MOFF_OK) return s;
@@ -1231,7 +1287,7 @@ moff_status moff_channelise(moff_plan *pl, const int8_t *adc, long long n_samp, 
 }
 
 moff_status moff_grid_snapshot(moff_plan *pl, const uint8_t *volt, int on_device, int chan, float *out) {
-    moff_status s = check_plan(pl);
+    moff_status s = check_unserved(pl);
     if (s != MOFF_OK) return s;
     if (!volt || !out) return fail(MOFF_EINVAL, "volt and out must not be NULL");
     if (chan < 0 || chan >= pl->C) return fail(MOFF_EINVAL, "chan (%d) out of range [0, %d)", chan, pl->C);

@@ -169,6 +169,19 @@ cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap,
 // elements), box 32 kx x 32 samples, 128-byte swizzle: the store target of k_rowspec_tc.
 cudaError_t encode_field_map(CUtensorMap *map, void *H, int N, int P, int Cb, int Tb);
 
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---- served plans (MOFF_SERVED): the hooks the request loop in moff_server.cu uses
+size_t plan_scratch_bytes(const moff_plan *pl);             // per-block scratch lent by the server
+size_t plan_block_bytes(const moff_plan *pl, int n_time);   // voltage bytes of an n_time block
+long long plan_units(const moff_plan *pl, int n_time);      // channel-snapshots of an n_time block
+bool plan_is_served(const moff_plan *pl);
+int plan_device(const moff_plan *pl);
+cudaStream_t plan_stream(const moff_plan *pl);
+// Bind the lent scratch, copy a host block behind it when on_device = 0 (the
+// lent region then holds plan_block_bytes more), and enqueue the block.
+moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, int n_time, int on_device);
+
 // Per-N instantiations (one translation unit each, compiled in parallel).
 #define MOFF_DECLARE_N(NN)                                                                          \
     cudaError_t launch_grid_n##NN(int P, int TB, bool staged, bool grid_only, const GridArgs &a, int n_stripes, \

@@ -276,6 +276,29 @@ def config_widefield(seed: int = SEED_BASE + 4, nx: int = 256, ny: int = 128, gr
 
 # --------------------------------------------------------------------------- device-side draws (large workloads)
 
+def config_serving(seed: int = SEED_BASE + 3, n_arrays: int = 8, chans=(64, 128, 256),
+                   t_range=(100, 300), ksize: int = 7):
+    """Sub-arrays of uneven size for a request stream: A drawn from {256, 1024,
+    4096, 16384} on a square 1 lambda lattice (ceil(sqrt A) per side, 5 % jitter)
+    centred in a grid N drawn from {64, 128, 256, 512} with N >= 2 ceil(sqrt A)
+    cells, dual pol, 7x7 kernels; per array a channel count from ``chans`` and a
+    block length in ``t_range``."""
+    rng = rng_for(seed)
+    out = []
+    for _ in range(n_arrays):
+        A = int(rng.choice([256, 1024, 4096, 16384]))
+        side = int(np.ceil(np.sqrt(A)))
+        N = int(rng.choice([n for n in (64, 128, 256, 512) if n >= 2 * side]))
+        C = int(rng.choice(list(chans)))
+        T = int(rng.integers(t_range[0], t_range[1] + 1))
+        o = N / 2.0 - side
+        pos = positions_lattice(rng, side, side, 1.0, 0.05, (o, o))[:A]
+        taps = taps_gaussian(rng, pos, ksize, 1.2, n_pol=2, subpixel=True, phase_slope=0.3)
+        gains = gains_random(rng, C, A, 2)
+        out.append(dict(A=A, N=N, C=C, T=T, pos=pos, taps=taps, gains=gains))
+    return out
+
+
 def device_codes(seed: int, n_time: int, n_chan: int, n_ant: int, n_pol: int,
                  sigma: float = 2.0, chunk: int = 32):
     """4-bit voltages ``uint8 [T][C][A][P]`` drawn on the GPU with a seeded torch

@@ -42,6 +42,7 @@ def test_argument_errors_without_gpu(L):
         (4, 3, 32, 1, 1, 4),        # Jones with one pol
         (4, 3, 32, 24, 1, 2),       # F-stage with non power-of-two channels
         (4, 3, 32, 1, 1, 1 << 9),   # unknown flag
+        (4, 3, 32, 1, 1, 1 << 4),   # unknown flag next to MOFF_SERVED
     ]
     for (A, K, N, C, P, fl) in bad:
         st = L.moff_plan_create(ctypes.byref(out), A, pos.ctypes.data, K, taps.ctypes.data, N, C, P, fl, None)
@@ -57,3 +58,20 @@ def test_python_binding_raises_on_error(L):
     with pytest.raises(moff.MoffError) as e:
         moff.moff_plan_create(np.zeros((0, 2)), np.ones((0, 1, 3, 3), complex), 32, 1, 1)
     assert e.value.status == -1
+
+
+def test_server_argument_errors_without_gpu(L):
+    out = ctypes.c_void_p()
+    assert L.moff_server_create(None, 1 << 20, 1) == -1
+    assert L.moff_server_create(ctypes.byref(out), 0, 1) == -1          # no pool
+    assert "hbm_budget_bytes" in moff.moff_last_error()
+    assert L.moff_server_create(ctypes.byref(out), 1 << 20, 0) == -1    # no slots
+    assert L.moff_server_create(ctypes.byref(out), 1 << 20, 65) == -1   # too many slots
+    assert not out.value
+    t = ctypes.c_longlong(7)
+    assert L.moff_server_submit(None, None, None, 1, 0, ctypes.byref(t)) == -1
+    st = ctypes.c_int()
+    assert L.moff_server_poll(None, 1, ctypes.byref(st), None) == -1
+    assert L.moff_server_wait(None, 0, 0) == -1
+    assert L.moff_server_stats(None, None, None, None, None, 0) == -1
+    assert L.moff_server_destroy(None) == 0
