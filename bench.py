@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp16tc", action="store_true", help="skip the FP16 tensor-core leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream (serving) leg")
-    ap.add_argument("--no-plain", action="store_true", help="skip the one-channel-at-a-time FP32 leg")
+    ap.add_argument("--no-plain", action="store_true", help="skip the batching leg (graph + autotune vs one channel at a time)")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per load point of the serving leg")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--frames", type=int, default=WL["frames"],
@@ -322,40 +322,63 @@ def serving_leg(args, moff, synth, torch):
     }
 
 
-def plain_leg(args, moff, synth, torch):
-    """The plain FP32 form: the same kernels run one channel per launch pair
-    (field scratch sized for a single channel), on the bench array and device
-    codes, 64 channels x 1000 samples."""
+def batching_leg(args, moff, synth, torch):
+    """All channels and pols of a block in one graph launch (MOFF_GRAPH) with
+    the autotuned gridding shape (MOFF_AUTOTUNE), against the plain FP32 form:
+    the same kernels run one channel per launch pair (field scratch sized for a
+    single channel).  Bench array, 64 channels x 1000 samples of device codes
+    (no F-stage), FP32 throughout."""
     A, P, N = WL["n_ant"], WL["n_pol"], WL["grid_n"]
     Cs, F = 64, args.frames
     cfg = synth.config_dualpol(n_chan=Cs)
+    codes = synth.device_codes(SEED + 900, F, Cs, A, P)
+
+    def timed(pl, reps=3):
+        pl.set_gains(cfg["gains"])
+        pl.submit(codes)
+        pl.sync()
+        pl.reset()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(reps):
+            pl.submit(codes)
+        ev1.record()
+        torch.cuda.synchronize()
+        return reps * Cs * F / (ev0.elapsed_time(ev1) / 1e3)
+
     per = P * N * N * 8
     old = os.environ.get("MOFF_SCRATCH_MB")
     os.environ["MOFF_SCRATCH_MB"] = str(32 * per / 1048576.0)
     try:
-        pl = moff.Plan(cfg["pos"], cfg["taps"], N, Cs, P)
+        plain = moff.Plan(cfg["pos"], cfg["taps"], N, Cs, P)
     finally:
         if old is None:
             os.environ.pop("MOFF_SCRATCH_MB", None)
         else:
             os.environ["MOFF_SCRATCH_MB"] = old
-    info = pl.info()
-    pl.set_gains(cfg["gains"])
-    codes = synth.device_codes(SEED + 900, F, Cs, A, P)
-    pl.submit(codes)
-    pl.sync()
-    pl.reset()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    pl.submit(codes)
-    ev1.record()
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    pl.close()
-    return {"value": Cs * F / (ms / 1e3), "unit": UNIT, "channels": Cs, "samples": F,
-            "chan_chunk": info["chan_chunk"], "time_chunk": info["time_chunk"],
-            "form": "FP32, one channel per grid/column launch pair, codes on device (no F-stage)"}
+    pinfo = plain.info()
+    v_plain = timed(plain, reps=1)
+    plain.close()
+    direct = moff.Plan(cfg["pos"], cfg["taps"], N, Cs, P)
+    v_direct = timed(direct)
+    rule = direct.tuning()
+    direct.close()
+    t0 = time.perf_counter()
+    batched = moff.Plan(cfg["pos"], cfg["taps"], N, Cs, P, autotune=True, graph=True)
+    tune_s = time.perf_counter() - t0
+    v_batched = timed(batched)
+    binfo, tuned = batched.info(), batched.tuning()
+    batched.close()
+    return {"unit": UNIT, "channels": Cs, "samples": F, "dtype": "f32",
+            "plain_one_channel": {"value": v_plain, "chan_chunk": pinfo["chan_chunk"],
+                                  "time_chunk": pinfo["time_chunk"]},
+            "batched_rule_direct": {"value": v_direct, "time_batch": rule["time_batch"], "staged": rule["staged"]},
+            "batched_autotuned_graph": {"value": v_batched, "time_batch": tuned["time_batch"], "staged": tuned["staged"],
+                                        "tune_source": tuned["source"], "plan_create_s": tune_s,
+                                        "chan_chunk": binfo["chan_chunk"], "time_chunk": binfo["time_chunk"],
+                                        "graph_launches_per_block": 1},
+            "speedup_vs_plain": v_batched / v_plain}
 
 
 def run_ours(args):
@@ -392,7 +415,7 @@ def run_ours(args):
                                                                    (64, 64, 900, 6.0))))
 
     def make_plan(fp16tc):
-        pl = moff.Plan(pos, taps, N, C, P, fstage=True, fp16tc=fp16tc)
+        pl = moff.Plan(pos, taps, N, C, P, fstage=True, fp16tc=fp16tc, autotune=not fp16tc)
         pl.set_gains(gains)
         # requantisation gain from a short calibration block: noise sigma ~ 2 codes per component
         calib = adc[:, :, : (ntaps + 3) * M].contiguous()
@@ -518,9 +541,9 @@ def run_ours(args):
     serving = None
     if not args.no_serving:
         serving = serving_leg(args, moff, synth, torch)
-    plain = None
+    batching = None
     if not args.no_plain:
-        plain = plain_leg(args, moff, synth, torch)
+        batching = batching_leg(args, moff, synth, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -538,7 +561,7 @@ def run_ours(args):
                        "parallelism": f"{world} independent replica(s), one integration each"},
             "fx_equiv_tcmac_per_s": fx_eq / 1e12,
             "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches, "clocks": clk,
-            "e2e": e2e, "cpu_baseline": cpu, "fp16tc": fp16, "serving": serving, "plain_fp32_one_channel": plain,
+            "e2e": e2e, "cpu_baseline": cpu, "fp16tc": fp16, "serving": serving, "batching": batching,
         }), flush=True)
     if dist is not None:
         dist.destroy_process_group()

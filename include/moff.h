@@ -72,10 +72,18 @@ enum {
                                  128 kernel rows landing on any one grid row per pol. */
     MOFF_FSTAGE = 1u << 1,    /* enable the polyphase F-stage (moff_submit_adc, moff_channelise) */
     MOFF_JONES = 1u << 2,     /* kernels are full 2x2 Jones matrices (n_pol must be 2) */
-    MOFF_SERVED = 1u << 3     /* the plan does not own its per-block scratch (the row-transformed
+    MOFF_SERVED = 1u << 3,    /* the plan does not own its per-block scratch (the row-transformed
                                  field; with MOFF_PREC_FP16TC also the FP16 voltage planes): a
                                  moff_server lends it from its pool for each block.  Such a plan
                                  takes blocks only through moff_server_submit. */
+    MOFF_AUTOTUNE = 1u << 4,  /* pick the gridding kernel's shape (samples per pass, shared-memory
+                                 staging of the kernel entries) by timing every feasible shape on
+                                 this array at plan creation; results are cached per array and
+                                 device in the process and, if the environment variable
+                                 MOFF_TUNE_CACHE names a file, in that file.  FP32 path only. */
+    MOFF_GRAPH = 1u << 5      /* launch each block's kernel sequence as one CUDA graph: captured
+                                 the first time a (input buffer, scratch, block length) is seen,
+                                 replayed afterwards (8 kept per plan).  Not used while timing is on. */
 };
 
 /*
@@ -188,6 +196,15 @@ moff_status moff_reset(moff_plan *plan);
 /* moff_plan_info -- sizes chosen at plan creation (any pointer may be NULL). */
 moff_status moff_plan_info(const moff_plan *plan, int *n_prod, int *rows_per_stripe,
                            int *time_chunk, int *chan_chunk, long long *device_bytes);
+
+/*
+ * moff_plan_tuning -- how the gridding kernel's shape was chosen (any pointer
+ * may be NULL): time_batch = samples gridded and row-transformed per pass (1, 2,
+ * 4 or 8), staged = 1 if kernel entries are staged in shared memory, source = 0
+ * built-in rule, 1 measured by MOFF_AUTOTUNE at creation, 2 taken from the
+ * tuning cache; best_ms = the measured time of the chosen shape (source 1).
+ */
+moff_status moff_plan_tuning(const moff_plan *plan, int *time_batch, int *staged, int *source, double *best_ms);
 
 /*
  * moff_set_timing -- when on (1), every kernel the plan launches is bracketed

@@ -25,7 +25,7 @@ __all__ = [
     "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
     "moff_plan_info", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
-    "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED",
+    "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "moff_plan_tuning",
     "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
     "moff_server_destroy",
     "Plan", "Server", "header_symbols", "KERNEL_KINDS",
@@ -40,6 +40,8 @@ MOFF_PREC_FP16TC = 1
 MOFF_FSTAGE = 1 << 1
 MOFF_JONES = 1 << 2
 MOFF_SERVED = 1 << 3
+MOFF_AUTOTUNE = 1 << 4
+MOFF_GRAPH = 1 << 5
 
 KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep"}
 
@@ -80,6 +82,8 @@ _SIGS = {
     "moff_server_stats": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
     "moff_server_destroy": [_vp],
+    "moff_plan_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                         ctypes.POINTER(ctypes.c_double)],
 }
 
 
@@ -228,6 +232,13 @@ def moff_plan_info(plan):
                 device_bytes=e.value)
 
 
+def moff_plan_tuning(plan):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    d = ctypes.c_double()
+    _check(lib().moff_plan_tuning(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return dict(time_batch=a.value, staged=b.value, source=c.value, best_ms=d.value)
+
+
 def moff_set_timing(plan, on):
     _check(lib().moff_set_timing(plan, int(on)))
 
@@ -370,9 +381,9 @@ class Plan:
     """One array's imaging plan (owns a ``moff_plan``)."""
 
     def __init__(self, pos, taps, grid_n, n_chan, n_pol, jones=False, fstage=False, stream=None, fp16tc=False,
-                 served=False):
+                 served=False, autotune=False, graph=False):
         flags = (MOFF_JONES if jones else 0) | (MOFF_FSTAGE if fstage else 0) | (MOFF_PREC_FP16TC if fp16tc else 0)
-        flags |= MOFF_SERVED if served else 0
+        flags |= (MOFF_SERVED if served else 0) | (MOFF_AUTOTUNE if autotune else 0) | (MOFF_GRAPH if graph else 0)
         if stream is None:
             try:
                 import torch
@@ -434,6 +445,9 @@ class Plan:
 
     def set_timing(self, on=True):
         moff_set_timing(self.handle, on)
+
+    def tuning(self):
+        return moff_plan_tuning(self.handle)
 
     def timing(self, kind, reset=False):
         return moff_timing(self.handle, kind, reset)

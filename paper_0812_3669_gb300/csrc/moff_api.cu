@@ -17,6 +17,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -255,6 +257,17 @@ struct moff_plan {
     size_t dev_bytes = 0;
     std::vector<void *> allocs;
 
+    // MOFF_GRAPH: each block's launch sequence captured once per (kind, input,
+    // scratch, length) on a private stream and replayed as one graph launch
+    bool graphs = false;
+    cudaStream_t gst = nullptr;
+    struct GraphEnt { int kind; const void *in, *scratch; long long n, stride; cudaGraphExec_t exec; unsigned long long used; };
+    std::vector<GraphEnt> gcache;
+    unsigned long long gclock = 0;
+    // MOFF_AUTOTUNE: how the gridding shape was chosen (0 rule, 1 measured, 2 cache)
+    int tune_source = 0;
+    double tune_best_ms = 0.0;
+
     // optional per-launch timing: (kind, start, stop)
     bool timing = false;
     struct Rec { int kind; cudaEvent_t a, b; };
@@ -299,6 +312,8 @@ void destroy_plan(moff_plan *pl) {
     if (pl->ev_done) cudaEventDestroy(pl->ev_done);
     for (auto &r : pl->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (cudaEvent_t e : pl->ev_pool) cudaEventDestroy(e);
+    for (auto &g : pl->gcache) cudaGraphExecDestroy(g.exec);
+    if (pl->gst) cudaStreamDestroy(pl->gst);
     if (pl->cst) cudaStreamDestroy(pl->cst);
     if (pl->own_stream && pl->st) cudaStreamDestroy(pl->st);
     delete pl;
@@ -491,6 +506,61 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
     return MOFF_OK;
 }
 
+constexpr size_t kGraphCache = 8;
+
+void drop_graphs(moff_plan *pl) {
+    for (auto &g : pl->gcache) cudaGraphExecDestroy(g.exec);
+    pl->gcache.clear();
+}
+
+// Run one block's launch sequence `enqueue` (which launches on pl->st).  With
+// MOFF_GRAPH (and timing off) the sequence is captured on the plan's private
+// capture stream the first time a (kind, input, scratch, length) key is seen
+// and replayed as one graph launch on pl->st afterwards.
+template <class F>
+moff_status launch_block(moff_plan *pl, int kind, const void *in, long long n, long long stride, F &&enqueue) {
+    if (!pl->graphs || pl->timing) return enqueue();
+    const void *scratch = pl->d_H;
+    for (auto &g : pl->gcache)
+        if (g.kind == kind && g.in == in && g.scratch == scratch && g.n == n && g.stride == stride) {
+            g.used = ++pl->gclock;
+            MOFF_CK(cudaGraphLaunch(g.exec, pl->st));
+            return MOFF_OK;
+        }
+    cudaStream_t user = pl->st;
+    pl->st = pl->gst;
+    if (cudaStreamBeginCapture(pl->gst, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        pl->st = user;
+        cudaGetLastError();
+        return fail(MOFF_ECUDA, "stream capture could not start");
+    }
+    moff_status s = enqueue();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(pl->gst, &graph);
+    pl->st = user;
+    if (s != MOFF_OK || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return s != MOFF_OK ? s : fail(MOFF_ECUDA, "stream capture failed: %s", cudaGetErrorString(ec));
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MOFF_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    }
+    if (pl->gcache.size() >= kGraphCache) {
+        auto lru = std::min_element(pl->gcache.begin(), pl->gcache.end(),
+                                    [](const moff_plan::GraphEnt &a, const moff_plan::GraphEnt &b) { return a.used < b.used; });
+        cudaGraphExecDestroy(lru->exec);
+        pl->gcache.erase(lru);
+    }
+    pl->gcache.push_back(moff_plan::GraphEnt{kind, in, scratch, n, stride, exec, ++pl->gclock});
+    MOFF_CK(cudaGraphLaunch(exec, pl->st));
+    return MOFF_OK;
+}
+
 moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
     if (pl->tc) return run_image_tc(pl, volt, n_time, tstride);
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
@@ -547,7 +617,8 @@ moff_status fail_msg(moff_status s, const char *msg) { return fail(s, "%s", msg)
 // Bin every antenna's kernel by grid-row stripe into per-cell contribution
 // lists (host only).  The stripe height is the largest power of two <= 16
 // whose lists fit the gridding kernel's shared-memory budget.
-moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b) {
+moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b,
+                       const GridChoice *force) {
     const int h = K / 2;
     std::vector<int> ax(A), ay(A);
     for (int a = 0; a < A; ++a) {
@@ -616,7 +687,17 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     const bool prefer_staged = stage_env && atoi(stage_env) != 0;
     const Cand *pick = nullptr;
     bool staged = false;
-    if (prefer_staged)
+    if (force) {
+        for (const Cand &cd : cands)
+            if (cd.tb == force->tb) {
+                const bool fits = force->staged ? cd.sm_staged <= budget
+                                                : (cd.sm_plain <= budget || (cd.tb == 1 && cd.sm_plain <= 200 * 1024));
+                if (fits) { pick = &cd; staged = force->staged; }
+                break;
+            }
+        if (!pick) return fail(MOFF_EINVAL, "gridding shape tb=%d staged=%d does not fit", force->tb, (int)force->staged);
+    }
+    if (!pick && prefer_staged)
         for (const Cand &cd : cands)
             if (cd.sm_staged <= budget) { pick = &cd; staged = true; break; }
     if (!pick)
@@ -846,9 +927,9 @@ moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *
 
 namespace {
 
-moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps) {
+moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps, const GridChoice *force = nullptr) {
     Bins b;
-    moff_status s = build_bins(pl->A, pl->K, pl->N, pl->P, pl->jones, pos, taps, &b);
+    moff_status s = build_bins(pl->A, pl->K, pl->N, pl->P, pl->jones, pos, taps, &b, force);
     if (s != MOFF_OK) return s;
     pl->rows = b.rows;
     pl->tb = b.tb;
@@ -896,6 +977,7 @@ moff_status upload_fstage(moff_plan *pl, int ntaps, const float *coeffs, float s
     }
     MOFF_CK(cudaMemcpyAsync(pl->d_h, h.data(), L * 4, cudaMemcpyHostToDevice, pl->st));
     MOFF_CK(cudaStreamSynchronize(pl->st));
+    drop_graphs(pl);   // captured F-stage launches hold the old scale and taps
     pl->ntaps = ntaps;
     pl->scale = scale;
     return MOFF_OK;
@@ -949,6 +1031,137 @@ moff_status check_adc(moff_plan *pl, const int8_t *adc, long long n_samp, int *F
     return MOFF_OK;
 }
 
+// ---- MOFF_AUTOTUNE: the gridding kernel's shape (time batch, and whether the
+// kernel entries are staged in shared memory) measured on the plan's own array.
+// Results are cached per (array, device) in the process and, when
+// MOFF_TUNE_CACHE names a file, in that file (one "key tb staged" per line).
+std::mutex g_tune_mu;
+std::map<std::string, GridChoice> g_tune_cache;
+bool g_tune_loaded = false;
+
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ULL) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ULL;
+    return h;
+}
+
+std::string tune_key(const moff_plan *pl, const double *pos, const float *taps) {
+    const size_t ntap = (size_t)pl->A * (pl->jones ? 4 : pl->P) * pl->K * pl->K * 2;
+    uint64_t h = fnv1a(pos, (size_t)pl->A * 2 * sizeof(double));
+    h = fnv1a(taps, ntap * sizeof(float), h);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, pl->device);
+    h = fnv1a(prop.name, strlen(prop.name), h);
+    char buf[128];
+    snprintf(buf, sizeof buf, "grid1-A%d-K%d-N%d-P%d-J%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P, (int)pl->jones,
+             prop.multiProcessorCount, (unsigned long long)h);
+    return buf;
+}
+
+moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridChoice *out) {
+    const std::string key = tune_key(pl, pos, taps);
+    const char *path = getenv("MOFF_TUNE_CACHE");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (!g_tune_loaded && path) {
+            if (FILE *f = fopen(path, "r")) {
+                char k[256];
+                int tb = 0, st = 0;
+                while (fscanf(f, "%255s %d %d", k, &tb, &st) == 3) g_tune_cache[k] = GridChoice{tb, st != 0};
+                fclose(f);
+            }
+        }
+        g_tune_loaded = true;
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *out = it->second;
+            pl->tune_source = 2;
+            return MOFF_OK;
+        }
+    }
+    // a short block: 32 samples of up to 64 channels, field scratch <= 512 MB
+    const int N = pl->N, P = pl->P, A = pl->A, nt = 32;
+    const size_t per = (size_t)P * N * N * 8;
+    const int nc = (int)std::max<size_t>(1, std::min<size_t>(std::min(pl->C, 64), ((size_t)512 << 20) / (nt * per)));
+    const long long tstride = (long long)nc * A * P;
+    void *volt = nullptr, *gains = nullptr, *H = nullptr, *twp = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<float2> tw = pass_twiddles_n(N);
+    auto cleanup = [&] {
+        cudaFree(volt); cudaFree(gains); cudaFree(H); cudaFree(twp);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&volt, (size_t)nt * tstride) != cudaSuccess || cudaMalloc(&gains, (size_t)nc * A * P * 8) != cudaSuccess ||
+        cudaMalloc(&H, (size_t)nt * nc * per) != cudaSuccess || cudaMalloc(&twp, tw.size() * 8) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(MOFF_ENOMEM, "autotuner scratch allocation failed");
+    }
+    // every voltage (3, 5), unit gains: the gridding work does not depend on the values
+    std::vector<float2> one((size_t)nc * A * P, make_float2(1.f, 0.f));
+    if (cudaMemsetAsync(volt, 0x35, (size_t)nt * tstride, pl->st) != cudaSuccess ||
+        cudaMemcpy(gains, one.data(), one.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(twp, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cleanup();
+        return fail(MOFF_ECUDA, "autotuner set-up failed");
+    }
+    GridChoice best{};
+    float best_ms = 0.f;
+    for (int tb = 8; tb >= 1; tb /= 2)
+        for (int st = 0; st < 2; ++st) {
+            const GridChoice ch{tb, st != 0};
+            moff_plan tmp;
+            tmp.A = A; tmp.K = pl->K; tmp.N = N; tmp.C = nc; tmp.P = P; tmp.jones = pl->jones;
+            tmp.device = pl->device;
+            if (bin_plan(&tmp, pos, taps, &ch) != MOFF_OK) {
+                for (void *q : tmp.allocs) cudaFree(q);
+                continue;
+            }
+            tmp.d_twp = static_cast<float2 *>(twp);
+            tmp.d_gains = static_cast<float2 *>(gains);
+            tmp.d_H = static_cast<float2 *>(H);
+            tmp.Tb = nt;
+            tmp.Cb = nc;
+            const GridArgs g = grid_args(&tmp, static_cast<const uint8_t *>(volt), tstride, 0, nt, 0, nc);
+            float ms = 0.f;
+            bool ok = launch_grid(N, P, tmp.tb, tmp.staged, false, g, tmp.n_stripes, tmp.grid_smem, pl->st) == cudaSuccess;
+            for (int r = 0; ok && r < 3; ++r) {
+                float t = 0.f;
+                ok = cudaEventRecord(e0, pl->st) == cudaSuccess &&
+                     launch_grid(N, P, tmp.tb, tmp.staged, false, g, tmp.n_stripes, tmp.grid_smem, pl->st) == cudaSuccess &&
+                     cudaEventRecord(e1, pl->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                     cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
+                if (ok && (r == 0 || t < ms)) ms = t;
+            }
+            cudaStreamSynchronize(pl->st);
+            for (void *q : tmp.allocs) cudaFree(q);
+            if (!ok) {
+                cleanup();
+                cudaGetLastError();
+                return fail(MOFF_ECUDA, "autotuner launch failed");
+            }
+            if (best.tb == 0 || ms < best_ms) {
+                best = ch;
+                best_ms = ms;
+            }
+        }
+    cleanup();
+    if (best.tb == 0) return fail(MOFF_EINVAL, "array too dense for the gridding kernel (no feasible shape)");
+    *out = best;
+    pl->tune_source = 1;
+    pl->tune_best_ms = best_ms;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+    if (path)
+        if (FILE *f = fopen(path, "a")) {
+            fprintf(f, "%s %d %d\n", key.c_str(), best.tb, (int)best.staged);
+            fclose(f);
+        }
+    return MOFF_OK;
+}
+
 }  // namespace
 
 namespace moff {
@@ -979,7 +1192,7 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
         MOFF_CK(cudaMemcpyAsync(dst, volt, plan_block_bytes(pl, n_time), cudaMemcpyHostToDevice, pl->st));
         src = dst;
     }
-    moff_status s = run_image(pl, src, n_time, tstride);
+    moff_status s = launch_block(pl, 0, src, n_time, tstride, [&] { return run_image(pl, src, n_time, tstride); });
     if (s != MOFF_OK) return s;
     pl->n_samples += n_time;
     return MOFF_OK;
@@ -1003,7 +1216,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         return fail(MOFF_EINVAL, "ksize (%d) must be odd, in [1, 15] and <= grid_n", ksize);
     if (n_chan < 1) return fail(MOFF_EINVAL, "n_chan (%d) must be >= 1", n_chan);
     if (n_pol != 1 && n_pol != 2) return fail(MOFF_EINVAL, "n_pol (%d) must be 1 or 2", n_pol);
-    if (flags & ~(unsigned)(MOFF_FSTAGE | MOFF_JONES | MOFF_PREC_FP16TC | MOFF_SERVED))
+    if (flags & ~(unsigned)(MOFF_FSTAGE | MOFF_JONES | MOFF_PREC_FP16TC | MOFF_SERVED | MOFF_AUTOTUNE | MOFF_GRAPH))
         return fail(MOFF_EINVAL, "unknown flag bits 0x%x", flags);
     if ((flags & MOFF_JONES) && n_pol != 2) return fail(MOFF_EINVAL, "MOFF_JONES requires n_pol = 2");
     if ((flags & MOFF_FSTAGE) && (!is_pow2(n_chan) || n_chan < 32 || n_chan > 2048))
@@ -1021,6 +1234,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     pl->fstage = (flags & MOFF_FSTAGE) != 0;
     pl->tc = (flags & MOFF_PREC_FP16TC) != 0;
     pl->served = (flags & MOFF_SERVED) != 0;
+    pl->graphs = (flags & MOFF_GRAPH) != 0;
     auto bail = [&](moff_status s) {
         std::string msg = g_err;
         destroy_plan(pl);
@@ -1044,8 +1258,15 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     }
     if (cudaEventCreateWithFlags(&pl->ev_done, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(MOFF_ECUDA, "event creation failed"));
+    if (pl->graphs && cudaStreamCreateWithFlags(&pl->gst, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(MOFF_ECUDA, "capture stream creation failed"));
 
-    moff_status s = bin_plan(pl, pos, taps);
+    GridChoice tuned;
+    moff_status s = MOFF_OK;
+    if ((flags & MOFF_AUTOTUNE) && !pl->tc) {
+        if ((s = tune_grid(pl, pos, taps, &tuned)) != MOFF_OK) return bail(s);
+    }
+    s = bin_plan(pl, pos, taps, pl->tune_source ? &tuned : nullptr);
     if (s != MOFF_OK) return bail(s);
 
     // twiddles of the N-point imaging transform
@@ -1193,13 +1414,16 @@ moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_d
     if (n_time < 1) return fail(MOFF_EINVAL, "n_time (%d) must be >= 1", n_time);
     const long long tstride = (long long)pl->C * pl->A * pl->P;
     const size_t bytes = (size_t)n_time * tstride;
+    auto image = [&](const uint8_t *src) {
+        return launch_block(pl, 0, src, n_time, tstride, [&] { return run_image(pl, src, n_time, tstride); });
+    };
     if (on_device) {
-        if ((s = run_image(pl, volt, n_time, tstride)) != MOFF_OK) return s;
+        if ((s = image(volt)) != MOFF_OK) return s;
     } else {
         const void *dev = nullptr;
         int slot = 0;
         if ((s = stage_in(pl, volt, bytes, &dev, &slot)) != MOFF_OK) return s;
-        if ((s = run_image(pl, reinterpret_cast<const uint8_t *>(dev), n_time, tstride)) != MOFF_OK) return s;
+        if ((s = image(reinterpret_cast<const uint8_t *>(dev))) != MOFF_OK) return s;
         if ((s = stage_done(pl, slot)) != MOFF_OK) return s;
     }
     pl->n_samples += n_time;
@@ -1229,9 +1453,12 @@ moff_status moff_submit_adc(moff_plan *pl, const int8_t *adc, long long n_samp, 
         if ((s = stage_in(pl, adc, abytes, &dev, &slot)) != MOFF_OK) return s;
         src = reinterpret_cast<const int8_t *>(dev);
     }
-    if ((s = run_pfb(pl, src, n_samp, F, 0, pl->d_codes)) != MOFF_OK) return s;
+    s = launch_block(pl, 1, src, n_samp, (long long)(void *)pl->d_codes, [&] {
+        moff_status r = run_pfb(pl, src, n_samp, F, 0, pl->d_codes);
+        return r != MOFF_OK ? r : run_image(pl, pl->d_codes, F, (long long)pl->C * pl->A * pl->P);
+    });
+    if (s != MOFF_OK) return s;
     if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
-    if ((s = run_image(pl, pl->d_codes, F, (long long)pl->C * pl->A * pl->P)) != MOFF_OK) return s;
     pl->n_samples += F;
     return MOFF_OK;
 }
@@ -1336,6 +1563,16 @@ moff_status moff_reset(moff_plan *pl) {
     if (s != MOFF_OK) return s;
     MOFF_CK(cudaMemsetAsync(pl->d_acc, 0, (size_t)pl->C * pl->nprod * pl->N * pl->N * 8, pl->st));
     pl->n_samples = 0;
+    return MOFF_OK;
+}
+
+moff_status moff_plan_tuning(const moff_plan *pl, int *time_batch, int *staged, int *source, double *best_ms) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (time_batch) *time_batch = pl->tb;
+    if (staged) *staged = pl->staged ? 1 : 0;
+    if (source) *source = pl->tune_source;
+    if (best_ms) *best_ms = pl->tune_best_ms;
     return MOFF_OK;
 }
 

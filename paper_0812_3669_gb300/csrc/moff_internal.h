@@ -128,7 +128,15 @@ struct Bins {
     std::vector<float2> con_tap;
     std::vector<uint16_t> con_y;
 };
-moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b);
+// Gridding-kernel shape: time batch TB (stripe height follows) and whether
+// the kernel entries are staged in shared memory.
+struct GridChoice {
+    int tb = 0;
+    bool staged = false;
+};
+// force = nullptr: the built-in rule; else exactly that shape (MOFF_EINVAL if infeasible).
+moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b,
+                       const GridChoice *force = nullptr);
 std::vector<float2> pass_twiddles_for(int n);   // pass-twiddle table of the n-point transform (FP64-built)
 
 // Row spectra of the kernel rows for the tensor-core path (host side).
