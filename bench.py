@@ -485,7 +485,7 @@ def run_ours(args):
     src = {"grid_rows": ["paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
            "cols_integrate": ["paper_0812_3669_gb300/csrc/moff_image_kernels.cuh",
                               "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
-           "pfb_fstage": ["paper_0812_3669_gb300/csrc/moff_fstage.cu", "paper_0812_3669_gb300/csrc/moff_fft.cuh"]}[dom]
+           "pfb_fstage": ["paper_0812_3669_gb300/csrc/moff_fstage.cu", "paper_0812_3669_gb300/csrc/moff_fft.cuh"]}.get(dom, [])
     launches = kern[dom]["launches"]
     achieved = kern[dom]["tflops"]
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",

@@ -220,7 +220,9 @@ moff_status moff_set_timing(moff_plan *plan, int on);
  *   1  calibrate + grid + row transform (Eq. m6 steps 1-2, step 3 first axis;
  *      with MOFF_PREC_FP16TC the tensor-core row contraction),
  *   2  column transform + square-and-integrate (step 3 second axis, step 4),
- *   3  (MOFF_PREC_FP16TC only) voltage decode, weighting and FP16 transpose.
+ *   3  (MOFF_PREC_FP16TC only) voltage decode, weighting and FP16 transpose,
+ *   4  F-stage output reorder (the four-step F-stage used for C = 1024 with
+ *      8 taps writes stream-major and reorders to [F][C][A][P]).
  * Waits for the recorded work.  total_ms / launches may be NULL.  reset = 1
  * drops the records of every kind after reading.
  */

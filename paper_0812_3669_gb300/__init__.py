@@ -43,7 +43,7 @@ MOFF_SERVED = 1 << 3
 MOFF_AUTOTUNE = 1 << 4
 MOFF_GRAPH = 1 << 5
 
-KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep"}
+KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep", 4: "fstage_reorder"}
 
 STATUS = {0: "MOFF_OK", -1: "MOFF_EINVAL", -2: "MOFF_ENOMEM", -3: "MOFF_ECUDA",
           -4: "MOFF_ESTATE", -5: "MOFF_ETIMEDOUT", -6: "MOFF_EBUSY"}

@@ -237,6 +237,9 @@ struct moff_plan {
     size_t codes_bytes = 0;
     float2 *d_spec = nullptr;
     size_t spec_bytes = 0;
+    float2 *d_tw4 = nullptr;           // four-step F-stage (C = 1024) twiddles [k2][l]
+    void *d_sm = nullptr;              // its stream-major output before the reorder
+    size_t sm_bytes = 0;
 
     // FP16 tensor-core path
     bool tc = false;
@@ -999,6 +1002,13 @@ moff_status check_unserved(const moff_plan *pl) {
     return MOFF_OK;
 }
 
+// The four-step F-stage applies to C = 1024, 8 taps and a 16-byte aligned ADC block.
+bool pfb_four_step(const moff_plan *pl, const int8_t *adc, int F, int kind) {
+    return pl->C == 1024 && pl->ntaps == 8 && pl->d_tw4 && ((uintptr_t)adc & 15u) == 0 && F <= 65535 &&
+           pl->A * pl->P <= 65535 &&
+           pl->sm_bytes >= (size_t)F * pl->C * pl->A * pl->P * (kind == 0 ? 1 : 8);
+}
+
 moff_status run_pfb(moff_plan *pl, const int8_t *adc, long long n_samp, int F, int kind, void *out) {
     PfbArgs p{};
     p.adc = adc;
@@ -1014,8 +1024,36 @@ moff_status run_pfb(moff_plan *pl, const int8_t *adc, long long n_samp, int F, i
     p.codes = kind == 0 ? reinterpret_cast<uint8_t *>(out) : nullptr;
     p.spec = kind == 1 ? reinterpret_cast<float2 *>(out) : nullptr;
     TimedLaunch tp(pl, 0);
+    if (pfb_four_step(pl, adc, F, kind)) {
+        p.tw4 = pl->d_tw4;
+        p.codes_sm = kind == 0 ? static_cast<uint8_t *>(pl->d_sm) : nullptr;
+        p.spec_sm = kind == 1 ? static_cast<float2 *>(pl->d_sm) : nullptr;
+        MOFF_CK(launch_pfb1024(p, pl->st));
+        tp.done();
+        TimedLaunch tr(pl, 4);
+        MOFF_CK(launch_pfb_reorder(p, pl->st));
+        tr.done();
+        return MOFF_OK;
+    }
     MOFF_CK(launch_pfb(pl->C, p, pl->st));
     tp.done();
+    return MOFF_OK;
+}
+
+// Stream-major scratch of the four-step F-stage for F frames (allocated before
+// any capture; a no-op when that path does not apply).
+moff_status ensure_sm(moff_plan *pl, int F, int kind) {
+    if (pl->C != 1024 || pl->ntaps != 8) return MOFF_OK;
+    const size_t need = (size_t)F * pl->C * pl->A * pl->P * (kind == 0 ? 1 : 8);
+    if (pl->sm_bytes >= need) return MOFF_OK;
+    moff_status s = sync_plan(pl, -1);
+    if (s != MOFF_OK) return s;
+    pfree(pl, pl->d_sm);
+    pl->dev_bytes -= pl->sm_bytes;
+    pl->d_sm = nullptr;
+    pl->sm_bytes = 0;
+    if ((s = palloc(pl, &pl->d_sm, need)) != MOFF_OK) return s;
+    pl->sm_bytes = need;
     return MOFF_OK;
 }
 
@@ -1296,15 +1334,20 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         // FP32 field (float2) on the FP32 path, FP16 (half2) on the tensor-core path
         const size_t per = (size_t)n_pol * grid_n * grid_n * (pl->tc ? 4 : 8);
         // served plans borrow their scratch per block from a shared pool: keep it modest
-        long long budget = pl->served ? (2048LL << 20) : (16384LL << 20);
+        long long budget = pl->served ? (2048LL << 20) : (24576LL << 20);
         if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, (long long)(atof(e) * 1048576.0));
+        // channels split into equal chunks (no ragged last chunk)
+        auto balance = [&](long long cb_max) {
+            const long long n = (n_chan + cb_max - 1) / cb_max;
+            return (n_chan + n - 1) / n;
+        };
         if (pl->tc) {
             // the tensor-core path works on 128 samples per product
             const size_t per_c = 128 * per + (size_t)n_ant * n_pol * 128 * 4;
             pl->Tb = 128;
-            pl->Cb = (int)std::max(1LL, std::min<long long>(n_chan, budget / (long long)per_c));
+            pl->Cb = (int)balance(std::max(1LL, std::min<long long>(n_chan, budget / (long long)per_c)));
         } else {
-            const long long cb = std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per)));
+            const long long cb = balance(std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per))));
             const long long tb = std::max(1LL, std::min<long long>(64, budget / (long long)(cb * per)));
             pl->Cb = (int)cb;
             pl->Tb = (int)tb;
@@ -1325,6 +1368,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         pl->rs_smem = rowspec_smem_bytes(grid_n, pl->rs_kp_max, pl->rs_max_seg);
         const int items = n_pol * grid_n * rs.ntiles;
         pl->rs_cgroups = std::max(1, std::min(pl->Cb, (4 * 152 + items - 1) / items));
+        if (const char *e = getenv("MOFF_TC_CGROUPS")) pl->rs_cgroups = std::max(1, std::min(pl->Cb, atoi(e)));
         const size_t ny = (size_t)pl->Cb * n_ant * n_pol * pl->Tb;
         if ((s = palloc(pl, &pl->d_rs_kp, rs.kp.size() * 4)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_rs_seg_off, rs.seg_off.size() * 8)) != MOFF_OK) return bail(s);
@@ -1372,6 +1416,19 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             cudaMemcpy(pl->d_twM, twM.data(), twM.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(MOFF_ECUDA, "F-stage table upload failed"));
         if ((s = upload_fstage(pl, 8, nullptr, 1.f)) != MOFF_OK) return bail(s);
+        if (CN == 1024) {
+            // exp(-2 pi i l k2 / 1024) stored [k2][l] for the four-step transform
+            std::vector<float2> t4(1024);
+            for (int k2 = 0; k2 < 32; ++k2)
+                for (int l = 0; l < 32; ++l) {
+                    double c, sn;
+                    root_unity(-(long long)l * k2, 1024, &c, &sn);
+                    t4[k2 * 32 + l] = make_float2((float)c, (float)sn);
+                }
+            if ((s = palloc(pl, &pl->d_tw4, t4.size() * 8)) != MOFF_OK) return bail(s);
+            if (cudaMemcpy(pl->d_tw4, t4.data(), t4.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(MOFF_ECUDA, "F-stage table upload failed"));
+        }
     }
     pl->scratch_bytes = align_up(pl->h_bytes, 1024) + (pl->tc ? 2 * align_up(pl->y_bytes, 1024) : 0);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(MOFF_ECUDA, "plan set-up failed"));
@@ -1445,6 +1502,7 @@ moff_status moff_submit_adc(moff_plan *pl, const int8_t *adc, long long n_samp, 
         if ((s = palloc(pl, &pl->d_codes, cbytes)) != MOFF_OK) return s;
         pl->codes_bytes = cbytes;
     }
+    if ((s = ensure_sm(pl, F, 0)) != MOFF_OK) return s;
     const size_t abytes = (size_t)pl->A * pl->P * n_samp;
     const int8_t *src = adc;
     int slot = -1;
@@ -1499,6 +1557,7 @@ moff_status moff_channelise(moff_plan *pl, const int8_t *adc, long long n_samp, 
             dst = pl->d_spec;
         }
     }
+    if ((s = ensure_sm(pl, F, out_kind)) != MOFF_OK) return s;
     const size_t abytes = (size_t)pl->A * pl->P * n_samp;
     const int8_t *src = adc;
     int slot = -1;
@@ -1588,7 +1647,7 @@ moff_status moff_set_timing(moff_plan *pl, int on) {
 moff_status moff_timing(moff_plan *pl, int kind, double *total_ms, long long *launches, int reset) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
-    if (kind < 0 || kind > 3) return fail(MOFF_EINVAL, "kind (%d) must be 0, 1, 2 or 3", kind);
+    if (kind < 0 || kind > 4) return fail(MOFF_EINVAL, "kind (%d) must be in [0, 4]", kind);
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
     double tot = 0.0;
     long long n = 0;

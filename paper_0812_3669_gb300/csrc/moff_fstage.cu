@@ -143,6 +143,208 @@ __global__ void __launch_bounds__(kBlock) k_pfb(const PfbArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Four-step variant for C = 1024 channels (M = 2048) and 8 taps, the
+// benchmark F-stage.  One CTA streams one antenna-pol through kPfbFrames
+// consecutive frames:
+//   FIR   thread t owns samples 4t..4t+3 of every frame; the last 8 frames of
+//         those samples (the FIR window) stay in registers and the filter in
+//         shared memory, so each ADC byte is read once and each frame costs
+//         one 4-byte load, eight 16-byte shared loads and 32 FMAs per thread.
+//         16 frames go to shared memory as z[n] = s[2n] + i s[2n+1].
+//   FFT   each warp transforms one frame: z[l + 32 n2] -> 32-point DFT over
+//         n2 in registers, twiddle w^{l k2} (w = exp(-2 pi i / 1024)), a
+//         32 x 32 transpose through the frame's own shared-memory rows, a
+//         second 32-point DFT -> Z[j + 32 k1] in lane j.  No CTA barrier
+//         inside the transform.
+//   split X[k] = (Z[k] + conj Z[C-k]) / 2 - (i/2) exp(-2 pi i k / M)
+//         (Z[k] - conj Z[C-k]) with Z[C-k] taken from lane (32 - j) % 32 by
+//         shuffle; requantised (or raw) outputs go out stream-major
+//         [AP][F][C] in 32-byte runs, and k_to_time_major reorders them.
+constexpr int kPfbFrames = 64;     // frames per CTA
+constexpr int kPfbBatch = 16;      // frames per FIR / transform round (one warp each)
+constexpr int kPfbThreads = 512;
+constexpr int kPfbLdz = 32 * 33;   // float2 per frame row block (transpose padding)
+
+// The radix-32 twiddles exp(S 2 pi i k / 32), k = 1, 3: cos / sin of pi/16, 3 pi/16.
+#define MOFF_C32 0.98078528040323044913f
+#define MOFF_S32 0.19509032201612826785f
+#define MOFF_C32_3 0.83146961230254523708f
+#define MOFF_S32_3 0.55557023301960222474f
+
+// In-register 32-point DFT, natural order in and out: two 16-point DFTs of
+// the even and odd elements and one radix-2 step.
+template <int S>
+__device__ __forceinline__ void dft32(float2 (&v)[32]) {
+    float2 e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        e[i] = v[2 * i];
+        o[i] = v[2 * i + 1];
+    }
+    dft<16, S>(e);
+    dft<16, S>(o);
+    o[1] = rot<S>(o[1], MOFF_C32, MOFF_S32);
+    o[2] = rot<S>(o[2], MOFF_C16, MOFF_S16);
+    o[3] = rot<S>(o[3], MOFF_C32_3, MOFF_S32_3);
+    o[4] = rot<S>(o[4], MOFF_C8, MOFF_C8);
+    o[5] = rot<S>(o[5], MOFF_S32_3, MOFF_C32_3);
+    o[6] = rot<S>(o[6], MOFF_S16, MOFF_C16);
+    o[7] = rot<S>(o[7], MOFF_S32, MOFF_C32);
+    o[8] = mul_si<S>(o[8]);
+    o[9] = rot<S>(o[9], -MOFF_S32, MOFF_C32);
+    o[10] = rot<S>(o[10], -MOFF_S16, MOFF_C16);
+    o[11] = rot<S>(o[11], -MOFF_S32_3, MOFF_C32_3);
+    o[12] = rot<S>(o[12], -MOFF_C8, MOFF_C8);
+    o[13] = rot<S>(o[13], -MOFF_C32_3, MOFF_S32_3);
+    o[14] = rot<S>(o[14], -MOFF_C16, MOFF_S16);
+    o[15] = rot<S>(o[15], -MOFF_C32, MOFF_S32);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        v[i] = cadd(e[i], o[i]);
+        v[i + 16] = csub(e[i], o[i]);
+    }
+}
+
+__device__ __forceinline__ uint8_t quant4(float2 X, float scale) {
+    int qr = (int)rintf(X.x * scale);
+    int qi = (int)rintf(X.y * scale);
+    qr = qr < -7 ? -7 : (qr > 7 ? 7 : qr);
+    qi = qi < -7 ? -7 : (qi > 7 ? 7 : qi);
+    return (uint8_t)(((qr & 15) << 4) | (qi & 15));
+}
+
+__global__ void __launch_bounds__(kPfbThreads, 1) k_pfb1024(const PfbArgs a) {
+    constexpr int CN = 1024, M = 2048, NT = 8;
+    const int ap = blockIdx.y;
+    const int m0 = blockIdx.x * kPfbFrames;
+    const int m_end = min(a.F, m0 + kPfbFrames);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *s_z = reinterpret_cast<float2 *>(smem);                 // [kPfbBatch][kPfbLdz]
+    float2 *s_tw = s_z + kPfbBatch * kPfbLdz;                        // [32 k2][32 l]
+    float2 *s_twM = s_tw + 1024;                                     // exp(-2 pi i k / M)
+    float4 *s_h = reinterpret_cast<float4 *>(s_twM + 1024);          // [NT][M / 4]
+    for (int i = tid; i < 1024; i += kPfbThreads) {
+        s_tw[i] = a.tw4[i];
+        s_twM[i] = a.twM[i];
+    }
+    for (int i = tid; i < NT * M / 4; i += kPfbThreads) s_h[i] = reinterpret_cast<const float4 *>(a.h)[i];
+
+    // ---- FIR window: the last 8 frames of samples 4 tid .. 4 tid + 3
+    const int8_t *x = a.adc + (long long)ap * a.S + 4 * tid;
+    float w[NT][4];
+    auto load_frame = [&](int f, float (&dst)[4]) {
+        const uint32_t b = *reinterpret_cast<const uint32_t *>(x + (long long)f * M);
+        dst[0] = (float)(int8_t)(b & 0xffu);
+        dst[1] = (float)(int8_t)((b >> 8) & 0xffu);
+        dst[2] = (float)(int8_t)((b >> 16) & 0xffu);
+        dst[3] = (float)(int8_t)(b >> 24);
+    };
+#pragma unroll
+    for (int p = 0; p < NT - 1; ++p) load_frame(m0 + p, w[p]);
+    __syncthreads();
+
+    for (int mb = m0; mb < m_end; mb += kPfbBatch) {
+        // ---- FIR of frames mb .. mb + 15 (window slot of frame m0 + i is i % 8)
+#pragma unroll
+        for (int u = 0; u < kPfbBatch; ++u) {
+            if (mb + u < m_end) {
+                load_frame(mb + u + NT - 1, w[(u + NT - 1) % NT]);
+                float sacc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int p = 0; p < NT; ++p) {
+                    const float4 hq = s_h[p * (M / 4) + tid];
+                    sacc[0] = fmaf(hq.x, w[(u + p) % NT][0], sacc[0]);
+                    sacc[1] = fmaf(hq.y, w[(u + p) % NT][1], sacc[1]);
+                    sacc[2] = fmaf(hq.z, w[(u + p) % NT][2], sacc[2]);
+                    sacc[3] = fmaf(hq.w, w[(u + p) % NT][3], sacc[3]);
+                }
+                *reinterpret_cast<float4 *>(s_z + u * kPfbLdz + 2 * tid) = make_float4(sacc[0], sacc[1], sacc[2], sacc[3]);
+            }
+        }
+        __syncthreads();
+        // ---- one warp per frame: four-step 1024-point transform, split, output
+        const int m = mb + warp;
+        if (m < m_end) {
+            float2 *zf = s_z + warp * kPfbLdz;
+            float2 v[32];
+#pragma unroll
+            for (int n2 = 0; n2 < 32; ++n2) v[n2] = zf[lane + 32 * n2];
+            dft32<-1>(v);
+#pragma unroll
+            for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], s_tw[k2 * 32 + lane]);
+            __syncwarp();
+#pragma unroll
+            for (int k2 = 0; k2 < 32; ++k2) zf[k2 * 33 + lane] = v[k2];
+            __syncwarp();
+#pragma unroll
+            for (int l = 0; l < 32; ++l) v[l] = zf[lane * 33 + l];
+            dft32<-1>(v);   // v[k1] = Z[lane + 32 k1]
+            const int partner = (32 - lane) & 31;
+            const long long obase = ((long long)ap * a.F + m) * CN + lane;
+#pragma unroll
+            for (int k1 = 0; k1 < 32; ++k1) {
+                float2 zm;
+                zm.x = __shfl_sync(0xffffffffu, v[31 - k1].x, partner);
+                zm.y = __shfl_sync(0xffffffffu, v[31 - k1].y, partner);
+                if (lane == 0) zm = v[(32 - k1) & 31];
+                const float2 zk = v[k1];
+                const float2 zc = make_float2(zm.x, -zm.y);
+                const float2 ev = cscale(cadd(zk, zc), 0.5f);
+                const float2 d = csub(zk, zc);
+                const float2 od = make_float2(0.5f * d.y, -0.5f * d.x);   // -(i/2) d
+                const float2 X = cadd(ev, cmul(s_twM[lane + 32 * k1], od));
+                if (a.out_kind == 0)
+                    a.codes_sm[obase + 32 * k1] = quant4(X, a.scale);
+                else
+                    a.spec_sm[obase + 32 * k1] = X;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+size_t pfb1024_smem_bytes() { return ((size_t)kPfbBatch * kPfbLdz + 2048) * sizeof(float2) + 8 * 2048 * sizeof(float); }
+
+// [AP][F][C] -> [F][C][AP] in 32 x 32 tiles (tile = 32 streams x 32 channels of one frame).
+template <class T>
+__global__ void __launch_bounds__(256) k_to_time_major(const T *__restrict__ in, T *__restrict__ out, int AP, int F,
+                                                       int C) {
+    __shared__ T tile[32][33];
+    const int c0 = blockIdx.x * 32, ap0 = blockIdx.y * 32, f = blockIdx.z;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) {
+        const int ap = ap0 + r, c = c0 + tx;
+        if (ap < AP && c < C) tile[r][tx] = in[((long long)ap * F + f) * C + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) {
+        const int c = c0 + r, ap = ap0 + tx;
+        if (ap < AP && c < C) out[((long long)f * C + c) * AP + ap] = tile[tx][r];
+    }
+}
+
+cudaError_t launch_pfb1024(const PfbArgs &a, cudaStream_t st) {
+    const size_t smem = pfb1024_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_pfb1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_pfb1024<<<dim3((a.F + kPfbFrames - 1) / kPfbFrames, a.AP), kPfbThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pfb_reorder(const PfbArgs &a, cudaStream_t st) {
+    const dim3 tg((1024 + 31) / 32, (a.AP + 31) / 32, a.F);
+    if (a.out_kind == 0)
+        k_to_time_major<uint8_t><<<tg, 256, 0, st>>>(a.codes_sm, a.codes, a.AP, a.F, 1024);
+    else
+        k_to_time_major<float2><<<tg, 256, 0, st>>>(a.spec_sm, a.spec, a.AP, a.F, 1024);
+    return cudaGetLastError();
+}
+
 template <int CN>
 size_t pfb_smem_t() {
     using S = PfbShape<CN>;

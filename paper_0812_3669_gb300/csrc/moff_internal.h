@@ -91,6 +91,11 @@ struct PfbArgs {
     int out_kind;             // 0 codes, 1 spectra
     uint8_t *codes;           // [F][C][AP]
     float2 *spec;             // [F][C][AP]
+    // four-step variant (C = 1024, 8 taps): twiddles exp(-2 pi i l k2 / C) as [k2][l],
+    // and its stream-major output [AP][F][C] before the reorder
+    const float2 *tw4;
+    uint8_t *codes_sm;
+    float2 *spec_sm;
 };
 
 // Row stride (in float2) of the TB calibrated voltages of one antenna-pol in
@@ -161,6 +166,10 @@ cudaError_t launch_grid(int N, int P, int TB, bool staged, bool grid_only, const
                         size_t smem, cudaStream_t st);
 cudaError_t launch_cols(int N, int P, const ColArgs &a, cudaStream_t st, bool h16 = false);
 cudaError_t launch_pfb(int CN, const PfbArgs &a, cudaStream_t st);
+// C = 1024, 8 taps, 16-byte aligned ADC: the four-step kernel into codes_sm /
+// spec_sm ([AP][F][C]), then the reorder to codes / spec ([F][C][AP]).
+cudaError_t launch_pfb1024(const PfbArgs &a, cudaStream_t st);
+cudaError_t launch_pfb_reorder(const PfbArgs &a, cudaStream_t st);
 cudaError_t launch_to_f32(const double *acc, float *out, long long n, cudaStream_t st);
 
 // Tensor-core path (moff_tc_kernels.cu).

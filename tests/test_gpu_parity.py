@@ -228,7 +228,8 @@ def _pfb_case(seed, A, P, C, ntaps, F):
     return adc
 
 
-@pytest.mark.parametrize("C,ntaps,A,P,F", [(32, 4, 5, 2, 9), (256, 8, 3, 2, 5), (1024, 8, 17, 2, 4), (2048, 8, 2, 1, 3)])
+@pytest.mark.parametrize("C,ntaps,A,P,F", [(32, 4, 5, 2, 9), (256, 8, 3, 2, 5), (1024, 8, 17, 2, 4), (1024, 8, 3, 2, 70),
+                                           (1024, 4, 2, 1, 5), (2048, 8, 2, 1, 3)])
 def test_fstage_spectra_and_codes(C, ntaps, A, P, F):
     adc = _pfb_case(40 + C, A, P, C, ntaps, F)
     M = 2 * C
