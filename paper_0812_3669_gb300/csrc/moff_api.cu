@@ -250,6 +250,7 @@ struct moff_plan {
     long long *d_rs_seg_off = nullptr, *d_rs_bimg_off = nullptr;
     float *d_rs_row_sh = nullptr, *d_rs_row_inv = nullptr;
     CUtensorMap h_map;                 // tensor-core path: store map of the FP16 field
+    int h_map_nt = 0;                  // its sample extent
     // served plans: per-block scratch (field, FP16 voltage planes) lent by a moff_server
     bool served = false;
     size_t h_bytes = 0, y_bytes = 0, scratch_bytes = 0;
@@ -486,6 +487,11 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
             ra.slab_t = pl->Cb;   // [Tb][Cb] slabs: the layout the field's tensor map describes
             ra.slab_c = 1;
             ra.err = pl->d_err;
+            if (pl->h_map_nt != nt) {   // a short block: drop the stores of the padding samples
+                if (encode_field_map(&pl->h_map, pl->d_H, pl->N, pl->P, pl->Cb, nt) != cudaSuccess)
+                    return fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded");
+                pl->h_map_nt = nt;
+            }
             TimedLaunch tg(pl, 1);
             MOFF_CK(launch_rowspec(pl->N, ra, pl->h_map, std::min(pl->rs_cgroups, nc), pl->rs_smem, pl->st));
             tg.done();
@@ -1222,6 +1228,7 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
         off += align_up(pl->y_bytes, 1024);
         if (encode_field_map(&pl->h_map, pl->d_H, pl->N, pl->P, pl->Cb, pl->Tb) != cudaSuccess)
             return fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded");
+        pl->h_map_nt = pl->Tb;
     }
     const long long tstride = (long long)pl->C * pl->A * pl->P;
     const uint8_t *src = volt;
@@ -1357,6 +1364,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             if ((s = palloc(pl, &pl->d_H, pl->h_bytes)) != MOFF_OK) return bail(s);
             if (pl->tc && encode_field_map(&pl->h_map, pl->d_H, grid_n, n_pol, pl->Cb, pl->Tb) != cudaSuccess)
                 return bail(fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded"));
+            pl->h_map_nt = pl->Tb;
         }
     }
     if (pl->tc) {

@@ -182,9 +182,10 @@ cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int
                              cudaStream_t st);
 cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap, int cgroups, size_t smem,
                            cudaStream_t st);
-// Tensor map of the FP16 row-transformed field [Tb][Cb][P*N][N] (half2 as 32-bit
-// elements), box 32 kx x 32 samples, 128-byte swizzle: the store target of k_rowspec_tc.
-cudaError_t encode_field_map(CUtensorMap *map, void *H, int N, int P, int Cb, int Tb);
+// Tensor map of the FP16 row-transformed field [nt][Cb][P*N][N] (half2 as 32-bit
+// elements), box 32 kx x 32 samples, 128-byte swizzle: the store target of
+// k_rowspec_tc.  Stores of samples >= nt fall outside the map and are dropped.
+cudaError_t encode_field_map(CUtensorMap *map, void *H, int N, int P, int Cb, int nt);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

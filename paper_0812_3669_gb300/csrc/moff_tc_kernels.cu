@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
                 tc::fence_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    tc::tma_store_4d(&hmap, tc::smem_u32(box), tile * KX + k0, p * N + ry, cl, t0w);
+                    // a box wholly past the block's samples is not issued (the map clips partial ones)
+                    if (t0w < a.nt) tc::tma_store_4d(&hmap, tc::smem_u32(box), tile * KX + k0, p * N + ry, cl, t0w);
                     tc::bulk_commit();
                 }
             }
@@ -374,7 +375,7 @@ cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap,
     return cudaErrorInvalidValue;
 }
 
-cudaError_t encode_field_map(CUtensorMap *map, void *H, int N, int P, int Cb, int Tb) {
+cudaError_t encode_field_map(CUtensorMap *map, void *H, int N, int P, int Cb, int nt) {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
@@ -384,7 +385,7 @@ cudaError_t encode_field_map(CUtensorMap *map, void *H, int N, int P, int Cb, in
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     const cuuint64_t row = (cuuint64_t)N * 4, slab = (cuuint64_t)P * N * row;
-    const cuuint64_t dims[4] = {(cuuint64_t)N, (cuuint64_t)P * N, (cuuint64_t)Cb, (cuuint64_t)Tb};
+    const cuuint64_t dims[4] = {(cuuint64_t)N, (cuuint64_t)P * N, (cuuint64_t)Cb, (cuuint64_t)nt};
     const cuuint64_t strides[3] = {row, slab, slab * (cuuint64_t)Cb};
     const cuuint32_t box[4] = {32, 1, 1, 32};
     const cuuint32_t estr[4] = {1, 1, 1, 1};

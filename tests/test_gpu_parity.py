@@ -218,6 +218,46 @@ def test_dualpol_full_size_sampled_channels():
     assert_image(img[chans], ref)
 
 
+def test_filled_aperture_full_array_sampled():
+    """The precision configuration's array at full size -- 16384 antennas filling
+    a 128 x 128 lambda lattice, dual pol, 7x7 kernels, 512 x 512 grid -- on the FP32
+    path, 4 channels x 24 samples against the oracle.  The FP16 tensor-core path
+    refuses this density (more than 128 kernel rows land on a grid row)."""
+    cfg = synth.config_precision(n_chan=4)
+    T, C, A, P, N = 24, 4, cfg["pos"].shape[0], 2, cfg["grid_n"]
+    assert A == 16384 and N == 512
+    taps, gains = c64(cfg["taps"]), c64(cfg["gains"])
+    codes_d = synth.device_codes(8123669 + 102, T, C, A, P)
+    with moff.Plan(cfg["pos"], taps, N, C, P) as pl:
+        pl.set_gains(gains)
+        pl.submit(codes_d)
+        img, n = pl.read_image()
+    assert n == T
+    ref = oracle.moff_image(codes_d.cpu().numpy(), gains, cfg["pos"], taps, N, P)
+    assert_image(img, ref)
+    with pytest.raises(moff.MoffError) as e:
+        moff.Plan(cfg["pos"], taps, N, C, P, fp16tc=True)
+    assert e.value.status == -1
+
+
+def test_widefield_full_array_sampled():
+    """The wide-field configuration's array at full size -- 32768 antennas on a
+    256 x 128 lambda lattice (x wraps the 512-cell grid), 9x9 Jones kernels with a
+    w-phase -- on 2 channels x 6 samples against the oracle."""
+    cfg = synth.config_widefield(n_chan=2)
+    T, C, A, P, N = 6, 2, cfg["pos"].shape[0], 2, cfg["grid_n"]
+    assert A == 32768 and N == 512 and cfg["taps"].shape == (A, 2, 2, 9, 9)
+    taps, gains = c64(cfg["taps"]), c64(cfg["gains"])
+    codes_d = synth.device_codes(8123669 + 104, T, C, A, P)
+    with moff.Plan(cfg["pos"], taps, N, C, P, jones=True) as pl:
+        pl.set_gains(gains)
+        pl.submit(codes_d)
+        img, n = pl.read_image()
+    assert n == T
+    ref = oracle.moff_image(codes_d.cpu().numpy(), gains, cfg["pos"], taps, N, P, jones=True)
+    assert_image(img, ref)
+
+
 # ------------------------------------------------------------------ F-stage (Eq. FFTofE)
 
 def _pfb_case(seed, A, P, C, ntaps, F):
