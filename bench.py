@@ -373,8 +373,10 @@ def batching_leg(args, moff, synth, torch):
     return {"unit": UNIT, "channels": Cs, "samples": F, "dtype": "f32",
             "plain_one_channel": {"value": v_plain, "chan_chunk": pinfo["chan_chunk"],
                                   "time_chunk": pinfo["time_chunk"]},
-            "batched_rule_direct": {"value": v_direct, "time_batch": rule["time_batch"], "staged": rule["staged"]},
+            "batched_rule_direct": {"value": v_direct, "time_batch": rule["time_batch"], "staged": rule["staged"],
+                                    "cell_pairs": rule["cell_pairs"]},
             "batched_autotuned_graph": {"value": v_batched, "time_batch": tuned["time_batch"], "staged": tuned["staged"],
+                                        "cell_pairs": tuned["cell_pairs"],
                                         "tune_source": tuned["source"], "plan_create_s": tune_s,
                                         "chan_chunk": binfo["chan_chunk"], "time_chunk": binfo["time_chunk"],
                                         "graph_launches_per_block": 1},

@@ -200,11 +200,13 @@ moff_status moff_plan_info(const moff_plan *plan, int *n_prod, int *rows_per_str
 /*
  * moff_plan_tuning -- how the gridding kernel's shape was chosen (any pointer
  * may be NULL): time_batch = samples gridded and row-transformed per pass (1, 2,
- * 4 or 8), staged = 1 if kernel entries are staged in shared memory, source = 0
- * built-in rule, 1 measured by MOFF_AUTOTUNE at creation, 2 taken from the
- * tuning cache; best_ms = the measured time of the chosen shape (source 1).
+ * 4 or 8), staged = 1 if kernel entries are staged in shared memory, cell_pairs
+ * = 1 if each lane sums two adjacent grid cells (one voltage read feeds both),
+ * source = 0 built-in rule, 1 measured by MOFF_AUTOTUNE at creation, 2 taken
+ * from the tuning cache; best_ms = the measured time of the chosen shape (source 1).
  */
-moff_status moff_plan_tuning(const moff_plan *plan, int *time_batch, int *staged, int *source, double *best_ms);
+moff_status moff_plan_tuning(const moff_plan *plan, int *time_batch, int *staged, int *cell_pairs, int *source,
+                             double *best_ms);
 
 /*
  * moff_set_timing -- when on (1), every kernel the plan launches is bracketed

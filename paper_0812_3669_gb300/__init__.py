@@ -82,7 +82,7 @@ _SIGS = {
     "moff_server_stats": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
     "moff_server_destroy": [_vp],
-    "moff_plan_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+    "moff_plan_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                          ctypes.POINTER(ctypes.c_double)],
 }
 
@@ -233,10 +233,11 @@ def moff_plan_info(plan):
 
 
 def moff_plan_tuning(plan):
-    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    a, b, p, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     d = ctypes.c_double()
-    _check(lib().moff_plan_tuning(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
-    return dict(time_batch=a.value, staged=b.value, source=c.value, best_ms=d.value)
+    _check(lib().moff_plan_tuning(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(p), ctypes.byref(c),
+                                  ctypes.byref(d)))
+    return dict(time_batch=a.value, staged=b.value, cell_pairs=p.value, source=c.value, best_ms=d.value)
 
 
 def moff_set_timing(plan, on):

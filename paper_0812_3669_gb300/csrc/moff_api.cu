@@ -207,7 +207,7 @@ struct moff_plan {
 
     // binning
     int rows = 0, n_stripes = 0, max_nloc = 0, n_slices = 0, tb = 1, max_entries = 0;
-    bool staged = false;
+    bool staged = false, pairs = false;
     size_t grid_smem = 0;
     int *d_st_ant_off = nullptr, *d_st_ant = nullptr;
     long long *d_slice_off = nullptr;
@@ -452,6 +452,7 @@ GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, 
     // time batch a CTA writes, and the samples a column CTA reads, share pages
     g.slab_t = 1;
     g.slab_c = pl->Tb;
+    g.pairs = pl->pairs ? 1 : 0;
     return g;
 }
 
@@ -659,6 +660,9 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
             }
     // Stripe shape: F = TB * P * rows rows are transformed together.  Prefer
     // kernel entries staged in shared memory, then more samples per pass.
+    // The built-in rule takes cell pairs unless MOFF_GRID_PAIRS=0.
+    const char *pairs_env = getenv("MOFF_GRID_PAIRS");
+    const bool pairs = force ? force->pairs : !(pairs_env && atoi(pairs_env) == 0);
     struct Cand { int tb, rows, nloc; long long entries; size_t sm_staged, sm_plain; };
     std::vector<Cand> cands;
     for (int tb = 8; tb >= 1; tb /= 2) {
@@ -681,13 +685,17 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
             for (int po = 0; po < P; ++po)
                 for (int rl = 0; rl < rows; ++rl)
                     for (int x = 0; x < N; ++x) c[n++] = cnt_all[((size_t)po * N + s * rows + rl) * N + x];
-            std::sort(c.begin(), c.end(), [](int x, int y) { return x > y; });
+            if (pairs)   // a pair's joint list is at most the sum of its two cells' lists
+                for (size_t k = 0; k < c.size() / 2; ++k) c[k] = c[2 * k] + c[2 * k + 1];
+            const size_t nu = pairs ? c.size() / 2 : c.size();
+            std::sort(c.begin(), c.begin() + nu, [](int x, int y) { return x > y; });
             long long e = 0;
-            for (size_t k = 0; k < c.size(); k += 32) e += 32LL * c[k];
+            for (size_t k = 0; k < nu; k += 32) e += 32LL * c[k];
             ment = std::max(ment, e);
         }
-        Cand cd{tb, rows, mnl, ment, grid_smem_bytes(N, P, tb, rows, mnl, tw_total, (int)std::min<long long>(ment, 1 << 28)),
-                grid_smem_bytes(N, P, tb, rows, mnl, tw_total, 0)};
+        Cand cd{tb, rows, mnl, ment,
+                grid_smem_bytes(N, P, tb, rows, mnl, tw_total, (int)std::min<long long>(ment, 1 << 28), pairs),
+                grid_smem_bytes(N, P, tb, rows, mnl, tw_total, 0, pairs)};
         cands.push_back(cd);
     }
     // Entries are read through L2 by default (more CTAs per SM measured faster
@@ -706,12 +714,18 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
             }
         if (!pick) return fail(MOFF_EINVAL, "gridding shape tb=%d staged=%d does not fit", force->tb, (int)force->staged);
     }
+    // Pair lanes relieve the voltage reads, so the rule then prefers 4 samples per
+    // pass (fewer registers per lane) before 8; single-cell lanes prefer 8.
+    std::vector<const Cand *> pref;
+    for (int want : pairs ? std::vector<int>{4, 8, 2, 1} : std::vector<int>{8, 4, 2, 1})
+        for (const Cand &cd : cands)
+            if (cd.tb == want) pref.push_back(&cd);
     if (!pick && prefer_staged)
-        for (const Cand &cd : cands)
-            if (cd.sm_staged <= budget) { pick = &cd; staged = true; break; }
+        for (const Cand *cd : pref)
+            if (cd->sm_staged <= budget) { pick = cd; staged = true; break; }
     if (!pick)
-        for (const Cand &cd : cands)
-            if (cd.sm_plain <= budget || (cd.tb == 1 && cd.sm_plain <= 200 * 1024)) { pick = &cd; break; }
+        for (const Cand *cd : pref)
+            if (cd->sm_plain <= budget || (cd->tb == 1 && cd->sm_plain <= 200 * 1024)) { pick = cd; break; }
     if (!pick)
         return fail(MOFF_EINVAL, "array too dense for the gridding kernel (antennas per grid row exceed its limits)");
     if (pick->rows * pick->tb * P != F)
@@ -721,6 +735,7 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     b->n_stripes = N / pick->rows;
     b->max_nloc = pick->nloc;
     b->staged = staged;
+    b->pairs = pairs;
     b->max_entries = staged ? (int)pick->entries : 0;
     b->grid_smem = staged ? pick->sm_staged : pick->sm_plain;
 
@@ -728,7 +743,9 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     // antenna-major within a cell.
     const int rows = b->rows, ns = b->n_stripes;
     const int ncell = P * rows * N;                 // a multiple of 32 (N >= 32)
-    const int nsl = ncell / 32;
+    const int nunit = pairs ? ncell / 2 : ncell;    // lanes: cells, or pairs (x even, x + 1)
+    if (nunit % 32) return fail(MOFF_EINVAL, "internal: %d gridding lanes per stripe is not a multiple of 32", nunit);
+    const int nsl = nunit / 32;
     b->n_slices = nsl;
     std::vector<std::vector<int>> sant(ns);
     std::vector<std::vector<Contrib>> scon(ns);
@@ -761,37 +778,70 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     b->con_tap.clear();
     b->con_y.clear();
     long long base = 0;
-    std::vector<int> cnt(ncell), start(ncell + 1), order(ncell);
+    // Per unit (cell, or pair of cells) its entry list: (voltage index, tap of the
+    // first cell, tap of the second).  A cell's contributions keep their order
+    // (ascending voltage index = antenna-major), so a pair lane sums each of its
+    // cells in exactly the order a single-cell lane would (plus exact zero terms).
+    struct Ent { int y; float2 t0, t1; };
+    std::vector<std::vector<Ent>> lists(nunit);
+    std::vector<int> order(nunit);
+    const float2 zero = make_float2(0.f, 0.f);
     for (int s = 0; s < ns; ++s) {
         b->ant_off[s + 1] = b->ant_off[s] + (int)sant[s].size();
         b->ant_list.insert(b->ant_list.end(), sant[s].begin(), sant[s].end());
         auto &v = scon[s];
         std::stable_sort(v.begin(), v.end(), [](const Contrib &x, const Contrib &y) { return x.cell < y.cell; });
-        std::fill(cnt.begin(), cnt.end(), 0);
-        for (const Contrib &c : v) cnt[c.cell]++;
-        start[0] = 0;
-        for (int i = 0; i < ncell; ++i) start[i + 1] = start[i] + cnt[i];
-        // cells by decreasing contribution count (ties by cell index) -> even slices
-        for (int i = 0; i < ncell; ++i) order[i] = i;
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cnt[x] > cnt[y]; });
+        for (auto &l : lists) l.clear();
+        size_t i = 0;
+        while (i < v.size()) {
+            const int cell = v[i].cell;
+            size_t j = i;
+            while (j < v.size() && v[j].cell == cell) ++j;
+            if (!pairs) {
+                for (size_t q = i; q < j; ++q) lists[cell].push_back(Ent{v[q].y, v[q].tap, zero});
+            } else {
+                // merge into the pair's list, sorted by voltage index
+                auto &L = lists[cell / 2];
+                const bool second = (cell & 1) != 0;
+                std::vector<Ent> merged;
+                merged.reserve(L.size() + (j - i));
+                size_t a = 0, q = i;
+                while (a < L.size() || q < j) {
+                    if (q >= j || (a < L.size() && L[a].y < v[q].y)) {
+                        merged.push_back(L[a++]);
+                    } else if (a < L.size() && L[a].y == v[q].y) {
+                        Ent e = L[a++];
+                        (second ? e.t1 : e.t0) = v[q++].tap;
+                        merged.push_back(e);
+                    } else {
+                        Ent e{v[q].y, zero, zero};
+                        (second ? e.t1 : e.t0) = v[q++].tap;
+                        merged.push_back(e);
+                    }
+                }
+                L.swap(merged);
+            }
+            i = j;
+        }
+        // units by decreasing list length (ties by unit index) -> even slices
+        for (int u = 0; u < nunit; ++u) order[u] = u;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return lists[x].size() > lists[y].size(); });
         for (int k = 0; k < nsl; ++k) {
             const size_t si = (size_t)s * nsl + k;
             b->slice_off[si] = base;
-            int len = 0;
-            for (int l = 0; l < 32; ++l) len = std::max(len, cnt[order[k * 32 + l]]);
-            for (int i = 0; i < len; ++i)
+            size_t len = 0;
+            for (int l = 0; l < 32; ++l) len = std::max(len, lists[order[k * 32 + l]].size());
+            for (size_t e = 0; e < len; ++e)
                 for (int l = 0; l < 32; ++l) {
-                    const int cell = order[k * 32 + l];
-                    if (i < cnt[cell]) {
-                        const Contrib &c = v[start[cell] + i];
-                        b->con_tap.push_back(c.tap);
-                        b->con_y.push_back((uint16_t)c.y);
-                    } else {
-                        b->con_tap.push_back(make_float2(0.f, 0.f));
-                        b->con_y.push_back(0);
-                    }
+                    const auto &L = lists[order[k * 32 + l]];
+                    const Ent en = e < L.size() ? L[e] : Ent{0, zero, zero};
+                    b->con_tap.push_back(en.t0);
+                    if (pairs) b->con_tap.push_back(en.t1);
+                    b->con_y.push_back((uint16_t)en.y);
                 }
-            for (int l = 0; l < 32; ++l) b->lane_cell[si * 32 + l] = (uint16_t)order[k * 32 + l];
+            for (int l = 0; l < 32; ++l)
+                b->lane_cell[si * 32 + l] = (uint16_t)(pairs ? 2 * order[k * 32 + l] : order[k * 32 + l]);
             base += (long long)len * 32;
         }
     }
@@ -943,6 +993,7 @@ moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps, const 
     pl->rows = b.rows;
     pl->tb = b.tb;
     pl->staged = b.staged;
+    pl->pairs = b.pairs;
     pl->max_entries = b.max_entries;
     pl->n_stripes = b.n_stripes;
     pl->max_nloc = b.max_nloc;
@@ -1097,7 +1148,7 @@ std::string tune_key(const moff_plan *pl, const double *pos, const float *taps) 
     cudaGetDeviceProperties(&prop, pl->device);
     h = fnv1a(prop.name, strlen(prop.name), h);
     char buf[128];
-    snprintf(buf, sizeof buf, "grid1-A%d-K%d-N%d-P%d-J%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P, (int)pl->jones,
+    snprintf(buf, sizeof buf, "grid2-A%d-K%d-N%d-P%d-J%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P, (int)pl->jones,
              prop.multiProcessorCount, (unsigned long long)h);
     return buf;
 }
@@ -1110,8 +1161,8 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
         if (!g_tune_loaded && path) {
             if (FILE *f = fopen(path, "r")) {
                 char k[256];
-                int tb = 0, st = 0;
-                while (fscanf(f, "%255s %d %d", k, &tb, &st) == 3) g_tune_cache[k] = GridChoice{tb, st != 0};
+                int tb = 0, st = 0, pr = 0;
+                while (fscanf(f, "%255s %d %d %d", k, &tb, &st, &pr) == 4) g_tune_cache[k] = GridChoice{tb, st != 0, pr != 0};
                 fclose(f);
             }
         }
@@ -1154,8 +1205,8 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     GridChoice best{};
     float best_ms = 0.f;
     for (int tb = 8; tb >= 1; tb /= 2)
-        for (int st = 0; st < 2; ++st) {
-            const GridChoice ch{tb, st != 0};
+        for (int cand = 0; cand < 4; ++cand) {
+            const GridChoice ch{tb, (cand & 1) != 0, (cand & 2) != 0};
             moff_plan tmp;
             tmp.A = A; tmp.K = pl->K; tmp.N = N; tmp.C = nc; tmp.P = P; tmp.jones = pl->jones;
             tmp.device = pl->device;
@@ -1186,6 +1237,9 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
                 cudaGetLastError();
                 return fail(MOFF_ECUDA, "autotuner launch failed");
             }
+            if (getenv("MOFF_TUNE_VERBOSE"))
+                fprintf(stderr, "moff autotune: tb=%d staged=%d pairs=%d  %.4f ms\n", ch.tb, (int)ch.staged,
+                        (int)ch.pairs, ms);
             if (best.tb == 0 || ms < best_ms) {
                 best = ch;
                 best_ms = ms;
@@ -1200,7 +1254,7 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     g_tune_cache[key] = best;
     if (path)
         if (FILE *f = fopen(path, "a")) {
-            fprintf(f, "%s %d %d\n", key.c_str(), best.tb, (int)best.staged);
+            fprintf(f, "%s %d %d %d\n", key.c_str(), best.tb, (int)best.staged, (int)best.pairs);
             fclose(f);
         }
     return MOFF_OK;
@@ -1633,11 +1687,13 @@ moff_status moff_reset(moff_plan *pl) {
     return MOFF_OK;
 }
 
-moff_status moff_plan_tuning(const moff_plan *pl, int *time_batch, int *staged, int *source, double *best_ms) {
+moff_status moff_plan_tuning(const moff_plan *pl, int *time_batch, int *staged, int *cell_pairs, int *source,
+                             double *best_ms) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
     if (time_batch) *time_batch = pl->tb;
     if (staged) *staged = pl->staged ? 1 : 0;
+    if (cell_pairs) *cell_pairs = pl->pairs ? 1 : 0;
     if (source) *source = pl->tune_source;
     if (best_ms) *best_ms = pl->tune_best_ms;
     return MOFF_OK;

@@ -68,7 +68,7 @@ struct GridShape {
     static constexpr int F = TB * PR;
 };
 
-template <int N, int P, int TB, bool STAGED, bool GRID_ONLY>
+template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, bool PAIRS>
 __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     using FP = FftPlan<N>;
     using TW = FftTw<N>;
@@ -98,8 +98,10 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     float2 *s_alt = s_buf + F * LDR;                   // second buffer of the row passes
     float2 *s_y = s_alt + ((F * LDR + 1) & ~1);        // [nloc*P][YS]: TB samples, padded row (16-byte aligned)
     float2 *s_g = s_y + YS * a.max_nloc * P;
-    float2 *s_tap = s_g + a.max_nloc * P;              // staged kernel values
-    int *s_ant = reinterpret_cast<int *>(s_tap + (STAGED ? a.max_entries : 0));
+    // staged kernel values (two per entry with PAIRS, read as 16-byte vectors: 16-byte aligned)
+    float2 *s_tap = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(s_g + a.max_nloc * P) + 15) & ~uintptr_t(15));
+    constexpr int TPE = PAIRS ? 2 : 1;                 // taps per entry
+    int *s_ant = reinterpret_cast<int *>(s_tap + (STAGED ? TPE * a.max_entries : 0));
     uint16_t *s_cy = reinterpret_cast<uint16_t *>(s_ant + a.max_nloc);   // staged voltage indices
 
     for (int i = tid; i < TW::TOTAL; i += kBlock) s_tw[i] = a.twp[i];
@@ -110,10 +112,8 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     }
     if constexpr (STAGED) {
         const int ne = (int)(soff[nsl] - e0);
-        for (int i = tid; i < ne; i += kBlock) {
-            s_tap[i] = __ldg(a.con_tap + e0 + i);
-            s_cy[i] = __ldg(a.con_y + e0 + i);
-        }
+        for (int i = tid; i < TPE * ne; i += kBlock) s_tap[i] = __ldg(a.con_tap + TPE * e0 + i);
+        for (int i = tid; i < ne; i += kBlock) s_cy[i] = __ldg(a.con_y + e0 + i);
     }
     __syncthreads();
 
@@ -164,29 +164,36 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
         __syncthreads();
         // Step 2: every cell sums its kernel contributions (fixed order), for TB
         // samples.  Entries are fetched U at a time so their latencies overlap.
+        // With PAIRS a lane owns cells (e, e + 1) of one row and each entry
+        // carries both cells' taps, so one read of a voltage row feeds two cells.
         for (int k = warp; k < nsl; k += kBlock / 32) {
             const long long b0 = soff[k];
             const int len = (int)((soff[k + 1] - b0) >> 5);
             const int cell = lcell[k * 32 + lane];
-            const float2 *tp = (STAGED ? s_tap + (b0 - e0) : a.con_tap + b0) + lane;
+            const float2 *tp = (STAGED ? s_tap + TPE * (b0 - e0) : a.con_tap + TPE * b0) + TPE * lane;
             const uint16_t *yp = (STAGED ? s_cy + (b0 - e0) : a.con_y + b0) + lane;
-            float2 acc[TB];
+            float2 acc[TPE][TB];
 #pragma unroll
-            for (int t = 0; t < TB; ++t) acc[t] = make_float2(0.f, 0.f);
-            constexpr int U = 4;
+            for (int c2 = 0; c2 < TPE; ++c2)
+#pragma unroll
+                for (int t = 0; t < TB; ++t) acc[c2][t] = make_float2(0.f, 0.f);
+            constexpr int U = PAIRS ? 2 : 4;
             for (int i0 = 0; i0 < len; i0 += U) {
-                float2 tv[U];
+                float2 tv[U][TPE];
                 int yv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const bool ok = i0 + u < len;
-                    if constexpr (STAGED) {
-                        tv[u] = ok ? tp[32 * (i0 + u)] : make_float2(0.f, 0.f);
-                        yv[u] = ok ? (int)yp[32 * (i0 + u)] : 0;
+                    const float2 *tq = tp + TPE * 32 * (i0 + u);
+                    if constexpr (PAIRS) {
+                        float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (ok) q4 = STAGED ? *reinterpret_cast<const float4 *>(tq) : __ldg(reinterpret_cast<const float4 *>(tq));
+                        tv[u][0] = make_float2(q4.x, q4.y);
+                        tv[u][TPE - 1] = make_float2(q4.z, q4.w);
                     } else {
-                        tv[u] = ok ? __ldg(tp + 32 * (i0 + u)) : make_float2(0.f, 0.f);
-                        yv[u] = ok ? (int)__ldg(yp + 32 * (i0 + u)) : 0;
+                        tv[u][0] = ok ? (STAGED ? tq[0] : __ldg(tq)) : make_float2(0.f, 0.f);
                     }
+                    yv[u] = ok ? (int)(STAGED ? yp[32 * (i0 + u)] : __ldg(yp + 32 * (i0 + u))) : 0;
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -195,22 +202,33 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
 #pragma unroll
                         for (int t = 0; t < TB; t += 2) {
                             const float4 q = *reinterpret_cast<const float4 *>(yy + t);
-                            acc[t].x = fmaf(tv[u].x, q.x, fmaf(-tv[u].y, q.y, acc[t].x));
-                            acc[t].y = fmaf(tv[u].x, q.y, fmaf(tv[u].y, q.x, acc[t].y));
-                            acc[t + 1].x = fmaf(tv[u].x, q.z, fmaf(-tv[u].y, q.w, acc[t + 1].x));
-                            acc[t + 1].y = fmaf(tv[u].x, q.w, fmaf(tv[u].y, q.z, acc[t + 1].y));
+#pragma unroll
+                            for (int c2 = 0; c2 < TPE; ++c2) {
+                                const float2 w = tv[u][c2];
+                                acc[c2][t].x = fmaf(w.x, q.x, fmaf(-w.y, q.y, acc[c2][t].x));
+                                acc[c2][t].y = fmaf(w.x, q.y, fmaf(w.y, q.x, acc[c2][t].y));
+                                acc[c2][t + 1].x = fmaf(w.x, q.z, fmaf(-w.y, q.w, acc[c2][t + 1].x));
+                                acc[c2][t + 1].y = fmaf(w.x, q.w, fmaf(w.y, q.z, acc[c2][t + 1].y));
+                            }
                         }
                     } else {
                         const float2 y = yy[0];
-                        acc[0].x = fmaf(tv[u].x, y.x, fmaf(-tv[u].y, y.y, acc[0].x));
-                        acc[0].y = fmaf(tv[u].x, y.y, fmaf(tv[u].y, y.x, acc[0].y));
+#pragma unroll
+                        for (int c2 = 0; c2 < TPE; ++c2) {
+                            const float2 w = tv[u][c2];
+                            acc[c2][0].x = fmaf(w.x, y.x, fmaf(-w.y, y.y, acc[c2][0].x));
+                            acc[c2][0].y = fmaf(w.x, y.y, fmaf(w.y, y.x, acc[c2][0].y));
+                        }
                     }
                 }
             }
             const int f = cell / N, e = cell - f * N;
-            float2 *dst = s_buf + f * LDR + pad16(e);
 #pragma unroll
-            for (int t = 0; t < TB; ++t) dst[t * PR * LDR] = acc[t];
+            for (int c2 = 0; c2 < TPE; ++c2) {
+                float2 *dst = s_buf + f * LDR + pad16(e + c2);
+#pragma unroll
+                for (int t = 0; t < TB; ++t) dst[t * PR * LDR] = acc[c2][t];
+            }
         }
         __syncthreads();
 
@@ -415,34 +433,41 @@ size_t col_smem_bytes_t(int P, bool h16 = false) {
            (h16 ? (size_t)P * N * 4 : 0);
 }
 
-template <int N, int P, int TB, bool ST, bool GO>
+template <int N, int P, int TB, bool ST, bool GO, bool PR>
 cudaError_t launch_grid_t(const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st) {
-    auto k = k_grid_rows<N, P, TB, ST, GO>;
+    auto k = k_grid_rows<N, P, TB, ST, GO, PR>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<dim3(n_stripes, a.nc), kBlock, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int N, int P, bool ST, bool GO>
+template <int N, int P, bool ST, bool GO, bool PR>
 cudaError_t launch_grid_s(int TB, const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st) {
     switch (TB) {
-        case 1: return launch_grid_t<N, P, 1, ST, GO>(a, n_stripes, smem, st);
-        case 2: return launch_grid_t<N, P, 2, ST, GO>(a, n_stripes, smem, st);
-        case 4: return launch_grid_t<N, P, 4, ST, GO>(a, n_stripes, smem, st);
-        case 8: return launch_grid_t<N, P, 8, ST, GO>(a, n_stripes, smem, st);
+        case 1: return launch_grid_t<N, P, 1, ST, GO, PR>(a, n_stripes, smem, st);
+        case 2: return launch_grid_t<N, P, 2, ST, GO, PR>(a, n_stripes, smem, st);
+        case 4: return launch_grid_t<N, P, 4, ST, GO, PR>(a, n_stripes, smem, st);
+        case 8: return launch_grid_t<N, P, 8, ST, GO, PR>(a, n_stripes, smem, st);
     }
     return cudaErrorInvalidValue;
 }
 
 // The stripe height is a compile-time function of TB, so the grid-only
 // variant runs with the plan's TB too (and stores only the first sample).
+template <int N, int P, bool PR>
+cudaError_t launch_grid_q(int TB, bool staged, bool go, const GridArgs &a, int n_stripes, size_t smem,
+                          cudaStream_t st) {
+    if (go) return launch_grid_s<N, P, false, true, PR>(TB, a, n_stripes, smem, st);
+    return staged ? launch_grid_s<N, P, true, false, PR>(TB, a, n_stripes, smem, st)
+                  : launch_grid_s<N, P, false, false, PR>(TB, a, n_stripes, smem, st);
+}
+
 template <int N, int P>
 cudaError_t launch_grid_p(int TB, bool staged, bool go, const GridArgs &a, int n_stripes, size_t smem,
                           cudaStream_t st) {
-    if (go) return launch_grid_s<N, P, false, true>(TB, a, n_stripes, smem, st);
-    return staged ? launch_grid_s<N, P, true, false>(TB, a, n_stripes, smem, st)
-                  : launch_grid_s<N, P, false, false>(TB, a, n_stripes, smem, st);
+    return a.pairs ? launch_grid_q<N, P, true>(TB, staged, go, a, n_stripes, smem, st)
+                   : launch_grid_q<N, P, false>(TB, staged, go, a, n_stripes, smem, st);
 }
 
 template <int N, int P, bool H16>

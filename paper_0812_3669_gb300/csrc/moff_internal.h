@@ -42,6 +42,7 @@ struct GridArgs {
     float2 *out;              // row-transformed (or raw, grid-only) field: slab [P][N][N] of
                               // (sample t, channel cl) at index t * slab_t + cl * slab_c
     long long slab_t, slab_c;
+    int pairs;                // 1: each lane sums two horizontally adjacent cells (entries carry two taps)
 };
 
 // Column transform + square-and-integrate (Eq. m6 steps 3-4, second axis).
@@ -108,14 +109,15 @@ inline int volt_stride(int TB) { return TB == 1 ? 1 : (TB == 8 ? 10 : 6); }
 inline int grid_fft_rows(int N) { return N >= 256 ? 8 : (N == 128 ? 16 : 32); }
 
 // Shared-memory bytes of the gridding kernel (host and device agree on the carve).
-inline size_t grid_smem_bytes(int N, int P, int TB, int rows, int max_nloc, int tw_total, int staged_entries = 0) {
+inline size_t grid_smem_bytes(int N, int P, int TB, int rows, int max_nloc, int tw_total, int staged_entries = 0,
+                              bool pairs = false) {
     const int ldr = N + N / 16;
     size_t b = 0;
-    b += (size_t)staged_entries * 10;         // kernel entries staged in shared memory (float2 + u16)
+    b += (size_t)staged_entries * (pairs ? 18 : 10);   // staged kernel entries (one or two float2 taps + u16)
     b += (size_t)tw_total * 8;
     b += 2 * (size_t)TB * P * rows * ldr * 8 + 8; // ping-pong row buffers of TB samples (+ alignment)
     b += (size_t)volt_stride(TB) * max_nloc * P * 8;   // calibrated voltages of TB samples
-    b += (size_t)max_nloc * P * 8;            // gains
+    b += (size_t)max_nloc * P * 8 + 8;        // gains (+ padding that 16-byte aligns the staged entries)
     b += (size_t)max_nloc * 4;                // antenna indices
     return (b + 15) & ~(size_t)15;
 }
@@ -126,6 +128,7 @@ inline size_t grid_smem_bytes(int N, int P, int TB, int rows, int max_nloc, int 
 struct Bins {
     int rows = 0, n_stripes = 0, tb = 1, max_nloc = 0, n_slices = 0, max_entries = 0;
     bool staged = false;   // kernel entries staged in shared memory
+    bool pairs = false;    // lanes own pairs of adjacent cells; con_tap holds two taps per entry
     size_t grid_smem = 0;
     std::vector<int> ant_off, ant_list;
     std::vector<long long> slice_off;
@@ -138,6 +141,7 @@ struct Bins {
 struct GridChoice {
     int tb = 0;
     bool staged = false;
+    bool pairs = false;   // each lane sums two horizontally adjacent cells
 };
 // force = nullptr: the built-in rule; else exactly that shape (MOFF_EINVAL if infeasible).
 moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b,
