@@ -247,11 +247,23 @@ __global__ void __launch_bounds__(kPfbThreads, 1) k_pfb1024(const PfbArgs a) {
     __syncthreads();
 
     for (int mb = m0; mb < m_end; mb += kPfbBatch) {
-        // ---- FIR of frames mb .. mb + 15 (window slot of frame m0 + i is i % 8)
+        // ---- FIR of frames mb .. mb + 15 (window slot of frame m0 + i is i % 8); the
+        // batch's 16 new 4-byte loads are all issued before the first is used
+        uint32_t raw[kPfbBatch];
+#pragma unroll
+        for (int u = 0; u < kPfbBatch; ++u)
+            raw[u] = mb + u < m_end ? *reinterpret_cast<const uint32_t *>(x + (long long)(mb + u + NT - 1) * M) : 0u;
 #pragma unroll
         for (int u = 0; u < kPfbBatch; ++u) {
             if (mb + u < m_end) {
-                load_frame(mb + u + NT - 1, w[(u + NT - 1) % NT]);
+                {
+                    float (&d)[4] = w[(u + NT - 1) % NT];
+                    const uint32_t b = raw[u];
+                    d[0] = (float)(int8_t)(b & 0xffu);
+                    d[1] = (float)(int8_t)((b >> 8) & 0xffu);
+                    d[2] = (float)(int8_t)((b >> 16) & 0xffu);
+                    d[3] = (float)(int8_t)(b >> 24);
+                }
                 float sacc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int p = 0; p < NT; ++p) {
