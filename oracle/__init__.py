@@ -19,5 +19,12 @@ Parity status per function (what pins it other than itself):
 * ``pfb_window`` / ``pfb_spectra`` -- 1-tap rectangular case equals a library FFT,
                           a hand-summed 2-tap case, tone-in-bin power.
 * ``quantise_4bit``    -- hand fixtures including half-to-even ties and clipping.
+* ``antenna_beam`` / ``feedback_sums`` -- the antenna shares sum to the image pixel
+                          (FBeq1 = sum over antennas of FBeq2), FBeq3 by brute force
+                          over antenna pairs, the point-source closed form.
+* ``feedback_delta``   -- zero for a calibrated point-source array; a simulated
+                          gain error shrinks to second order in one step with the
+                          N reading, while the printed 2N and the unconjugated
+                          ratio do not converge.
 """
 from .moff_oracle import *  # noqa: F401,F403

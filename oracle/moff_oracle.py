@@ -40,6 +40,7 @@ __all__ = [
     "unpack_4bit", "anchors", "calibrate", "grid_matrix", "grid", "sky_transform",
     "integrate", "moff_image", "fx_image", "footprint", "pfb_window", "pfb_spectra",
     "quantise_4bit", "ambiguous_codes", "channelise", "max_norm_err",
+    "antenna_beam", "feedback_sums_y", "feedback_sums", "feedback_delta",
 ]
 
 
@@ -181,6 +182,85 @@ def moff_image(codes, gains, pos, taps, grid_n: int, n_pol: int, jones: bool = F
             E = sky_transform(G)
             out[ci] += integrate(E)
     return out
+
+
+# ----------------------------------------------------------------------------- feedback calibration (Sec. 6)
+
+def antenna_beam(pos, taps, grid_n: int, k_cal) -> np.ndarray:
+    """One antenna's contribution to the electric-field image per unit voltage:
+    its kernel placed at its anchor and transformed with the imaging transform
+    (Eq. m6 steps 2-3 for a single antenna), at pixel k_cal = (kx, ky).
+
+    ``taps`` complex [A][P][K][K] (one kernel per pol); returns complex [A, P].
+    """
+    t = np.asarray(taps, dtype=np.complex128)
+    A, P, K, _ = t.shape
+    N = grid_n
+    kx, ky = k_cal
+    anc = anchors(pos)
+    h = K // 2
+    d = np.arange(K) - h
+    out = np.zeros((A, P), dtype=np.complex128)
+    for a in range(A):
+        ey = np.exp(2j * np.pi * ky * (anc[a, 1] + d) / N)      # over dy
+        ex = np.exp(2j * np.pi * kx * (anc[a, 0] + d) / N)      # over dx
+        for p in range(P):
+            out[a, p] = np.sum(t[a, p] * ey[:, None] * ex[None, :])
+    return out
+
+
+def feedback_sums_y(y, pos, taps, grid_n: int, k_cal):
+    """Sec. 6, Eqs. FBeq1 and FBeq2, summed over the block, for calibrated
+    voltages ``y`` complex [T, A, P] (one kernel per pol):
+
+      S[p]    = sum_t |E_t,p(k_cal)|^2                       (FBeq1)
+      R[a, p] = sum_t E_t,p(k_cal) conj(y_t,a,p B_a,p)         (FBeq2)
+
+    where E is the electric-field image of the imaging path (grid, then
+    transform) at the calibrator pixel and B = ``antenna_beam`` turns antenna
+    a's calibrated voltage into its share of that pixel.  Returns (R, S).
+    """
+    y = np.asarray(y, dtype=np.complex128)
+    T, A, P = y.shape
+    kx, ky = k_cal
+    W = grid_matrix(pos, taps, grid_n, P)
+    E = sky_transform(grid(y, W, grid_n, P))[:, :, ky, kx]      # [T, P]
+    B = antenna_beam(pos, taps, grid_n, k_cal)                  # [A, P]
+    S = np.sum(np.abs(E) ** 2, axis=0)
+    R = np.sum(E[:, None, :] * np.conj(y * B[None]), axis=0)
+    return R, S
+
+
+def feedback_sums(codes, gains, pos, taps, grid_n: int, k_cal, channels=None):
+    """``feedback_sums_y`` per channel of a block of 4-bit voltages.
+
+    ``codes`` uint8 [T, C, A, P]; ``gains`` complex [C, A, P]; returns
+    R complex [len(channels), A, P] and S float [len(channels), P].
+    """
+    codes = np.asarray(codes)
+    Tn, C, A, P = codes.shape
+    chans = range(C) if channels is None else list(channels)
+    Rs, Ss = [], []
+    for c in chans:
+        y = calibrate(unpack_4bit(codes[:, c]), np.asarray(gains)[c])
+        R, S = feedback_sums_y(y, pos, taps, grid_n, k_cal)
+        Rs.append(R)
+        Ss.append(S)
+    return np.stack(Rs), np.stack(Ss)
+
+
+def feedback_delta(R, S, gains, n_ant: int):
+    """Sec. 6 gain-error estimate, read with N (the antenna count) where the
+    paper prints 2N, and with the correlation conjugated:
+
+        delta_g = g (1 - N conj(R) / S)
+
+    For a dominant calibrator and residual gains a = g h (h the instrument),
+    N conj(R) / S = a / mean(a), so g + delta_g moves every antenna's residual
+    to the array mean to first order and is zero for a calibrated array.
+    ``R`` [C, A, P], ``S`` [C, P], ``gains`` [C, A, P]."""
+    g = np.asarray(gains, dtype=np.complex128)
+    return g * (1.0 - n_ant * np.conj(R) / np.asarray(S)[:, None, :])
 
 
 # ----------------------------------------------------------------------------- FX form

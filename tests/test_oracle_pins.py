@@ -346,3 +346,98 @@ def test_dual_pol_products_are_per_pol_images():
     for p in range(2):
         Ip = oracle.moff_image(codes[..., p:p + 1], gains[..., p:p + 1], pos, taps[:, p:p + 1], 16, 1)
         np.testing.assert_allclose(I[:, p], Ip[:, 0], rtol=1e-12, atol=1e-9)
+
+
+# ----------------------------------------------------------------------------- feedback calibration (Sec. 6)
+
+def _fb_case(seed, A=24, N=32, K=3, P=2, T=9):
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(3, N - 3, size=(A, 2))
+    taps = rng.normal(size=(A, P, K, K)) + 1j * rng.normal(size=(A, P, K, K))
+    y = rng.normal(size=(T, A, P)) + 1j * rng.normal(size=(T, A, P))
+    return pos, taps, y
+
+
+def test_feedback_antenna_shares_sum_to_the_image_pixel():
+    """FBeq1 = sum over antennas of FBeq2: the image pixel (grid + transform)
+    must equal the sum of the antennas' beam-weighted voltages."""
+    pos, taps, y = _fb_case(1)
+    for k in [(0, 0), (5, 11), (31, 2)]:
+        R, S = oracle.feedback_sums_y(y, pos, taps, 32, k)
+        assert np.allclose(R.sum(axis=0), S, rtol=1e-12, atol=0)
+        assert np.abs(R.sum(axis=0).imag).max() <= 1e-10 * S.max()
+
+
+def test_feedback_fbeq3_by_antenna_pairs():
+    """FBeq3: <|E|^2> - <E conj(c_i)> = sum over pairs (j, k != i) of <c_j conj(c_k)>,
+    with c the per-antenna pixel shares taken from single-antenna images."""
+    pos, taps, y = _fb_case(2, A=7, N=16, K=3, P=1, T=5)
+    k = (3, 9)
+    R, S = oracle.feedback_sums_y(y, pos, taps, 16, k)
+    # per-antenna shares from the imaging path run on one antenna at a time
+    c = np.zeros((y.shape[0], 7), dtype=complex)
+    for a in range(7):
+        ya = np.zeros_like(y)
+        ya[:, a] = y[:, a]
+        W = oracle.grid_matrix(pos, taps, 16, 1)
+        c[:, a] = oracle.sky_transform(oracle.grid(ya, W, 16, 1))[:, 0, k[1], k[0]]
+    for i in range(7):
+        pairs = sum(np.sum(c[:, j] * np.conj(c[:, kk])) for j in range(7) for kk in range(7) if kk != i)
+        assert abs((S[0] - R[i, 0]) - pairs) <= 1e-10 * S[0]
+
+
+def test_feedback_point_source_closed_form():
+    """Delta kernels, integer anchors, unit gains, one source at theta_s with
+    phases exp(-2 pi i p.theta_s/N) that are multiples of pi/2 (exact 4-bit):
+    E(theta_s) = A x, so N conj(R)/S = 1 and the gain error estimate is 0;
+    the printed factor 2N would give -g instead."""
+    N, A, T = 32, 12, 4
+    rng = np.random.default_rng(3)
+    cells = rng.choice(N * N, size=A, replace=False)
+    pos = np.stack([cells % N, cells // N], axis=1).astype(float)
+    th = (8, 0)                                   # theta_s: phases i^(-px)
+    x = 7 * np.exp(-2j * np.pi * (pos[:, 0] * th[0] + pos[:, 1] * th[1]) / N)
+    re, im = np.rint(x.real).astype(int), np.rint(x.imag).astype(int)
+    codes = np.repeat(synth.pack_4bit(re, im)[None, None, :, None], T, axis=0)   # [T, 1, A, 1]
+    gains = np.ones((1, A, 1), complex)
+    taps = np.ones((A, 1, 1, 1), complex)
+    R, S = oracle.feedback_sums(codes, gains, pos, taps, N, th)
+    assert np.isclose(S[0, 0], T * 49 * A ** 2)          # E(theta_s) = 7 A per sample
+    assert np.allclose(R[0, :, 0], T * 49 * A)           # E conj(x_a B_a) = 7 A * 7
+    assert np.allclose(oracle.feedback_delta(R, S, gains, A), 0, atol=1e-12)
+    assert np.allclose(gains * (1 - 2 * A * np.conj(R) / S[:, None, :]), -gains)
+
+
+def _simulated_step(eps, factor, conj=True, seed=4):
+    """One feedback step on a simulated point source with residual gain errors
+    (1 + eps); returns the largest relative residual before and after."""
+    N, A, T = 32, len(eps), 64
+    rng = np.random.default_rng(seed)
+    cells = rng.choice(N * N, size=A, replace=False)
+    pos = np.stack([cells % N, cells // N], axis=1).astype(float)
+    th = (5, 13)
+    geo = np.exp(-2j * np.pi * (pos[:, 0] * th[0] + pos[:, 1] * th[1]) / N)
+    h = (0.8 + 0.4 * rng.random(A)) * np.exp(2j * np.pi * rng.random(A))   # instrument gains
+    s = rng.normal(size=T) + 1j * rng.normal(size=T)                        # source signal
+    x = (s[:, None] * (h * geo)[None, :])[:, :, None]                       # [T, A, 1]
+    g = (1 / h) * (1 + np.asarray(eps))
+    taps = np.ones((A, 1, 1, 1), complex)
+    R, S = oracle.feedback_sums_y(x * g[None, :, None], pos, taps, N, th)
+    ratio = np.conj(R[:, 0]) if conj else R[:, 0]
+    g_new = g + g * (1 - factor * ratio / S[0])
+    spread = lambda a: np.abs(a / a.mean() - 1).max()
+    return spread(g * h), spread(g_new * h)
+
+
+def test_feedback_update_removes_a_simulated_gain_error():
+    """The N reading with the conjugated ratio cancels a 5 % amplitude and phase
+    error to second order in one step; the printed 2N and the unconjugated
+    ratio do not converge."""
+    rng = np.random.default_rng(5)
+    eps = 0.05 * (rng.normal(size=20) + 1j * rng.normal(size=20)) / np.sqrt(2)
+    before, after = _simulated_step(eps, factor=20)
+    assert before > 0.05 and after < 0.15 * before
+    b2, a2 = _simulated_step(eps, factor=40)
+    assert a2 > 0.9 * b2
+    b3, a3 = _simulated_step(1j * np.abs(eps), factor=20, conj=False)
+    assert a3 > 0.9 * b3
