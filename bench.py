@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp16tc", action="store_true", help="skip the FP16 tensor-core leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream (serving) leg")
+    ap.add_argument("--no-feedback", action="store_true", help="skip the feedback-calibration leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the batching leg (graph + autotune vs one channel at a time)")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per load point of the serving leg")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -519,6 +520,26 @@ def run_ours(args):
         r = fp16["row_contraction_tensor"]
         r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
 
+    # ---------------------------------------------------------------- feedback calibration leg (Sec. 6)
+    feedback = None
+    if not args.no_feedback:
+        planfb = make_plan(False)
+        planfb.set_calibrator(40, 70)            # the first injected source's pixel
+        msfb, kernfb, _, _ = measure(planfb, max(1, args.steps // 2), 1)
+        R, S, nfb = planfb.read_feedback()
+        planfb.close()
+        fk = kernfb.get("feedback_corr", {})
+        fb_bytes = (args.steps // 2 or 1) * F * C * A * P          # codes re-read per step (pixel taps are tiny)
+        feedback = {"value": job_rate(max(1, args.steps // 2) * F * C, world, msfb / 1000.0), "unit": UNIT,
+                    "ms_per_step": msfb / max(1, args.steps // 2), "kernels": kernfb, "calibrator_pixel": [40, 70],
+                    "samples_summed": nfb,
+                    "corr_kernel_roofline": {"bound": "hbm", "achieved": fb_bytes / (fk["ms_total"] / 1e3) / 1e9
+                                             if fk.get("ms_total") else None,
+                                             "peak": float(peaks.get("hbm_gbs", 6779.0)), "unit": "GB/s",
+                                             "peak_basis": "measured HBM copy (of measured)"}}
+        r = feedback["corr_kernel_roofline"]
+        r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
+
     # ---------------------------------------------------------------- end to end through host buffers
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
@@ -563,7 +584,7 @@ def run_ours(args):
                        "parallelism": f"{world} independent replica(s), one integration each"},
             "fx_equiv_tcmac_per_s": fx_eq / 1e12,
             "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches, "clocks": clk,
-            "e2e": e2e, "cpu_baseline": cpu, "fp16tc": fp16, "serving": serving, "batching": batching,
+            "e2e": e2e, "cpu_baseline": cpu, "fp16tc": fp16, "serving": serving, "batching": batching, "feedback": feedback,
         }), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -198,6 +198,47 @@ moff_status moff_plan_info(const moff_plan *plan, int *n_prod, int *rows_per_str
                            int *time_chunk, int *chan_chunk, long long *device_bytes);
 
 /*
+ * ---- Feedback calibration (Sec. 6, Eqs. FBeq1-FBeq3): correlate the
+ * electric-field image pixel towards a calibrator with every antenna's
+ * calibrated signal -- feeding the correlator output back to its input.
+ *
+ * moff_set_calibrator -- from the next block on, also accumulate per channel,
+ * pol p and antenna a over the submitted samples
+ *     S_p   = sum_t |E_t,p(k)|^2                                  (FBeq1)
+ *     R_a,p = sum_t E_t,p(k) conj(y_t,a,p B_a,p)                    (FBeq2)
+ * where E_t,p(k) is the image's field at pixel k = (kx, ky) (before squaring),
+ * y the calibrated voltage and B_a,p antenna a's kernel placed at its anchor
+ * and transformed at k (its share of the pixel per unit voltage), so that
+ * sum_a R_a,p = S_p.  Resets both sums.  kx = ky = -1 switches the sums off.
+ * MOFF_EINVAL for a pixel outside the image or a MOFF_JONES plan.  moff_reset
+ * zeros these sums too.
+ */
+moff_status moff_set_calibrator(moff_plan *plan, int kx, int ky);
+
+/*
+ * moff_read_feedback -- the sums since the calibrator was set (or last reset):
+ *   corr    host float32 complex [C][A][P][2]: R (may be NULL);
+ *   power   host float64 [C][P]: S (may be NULL);
+ *   n_samples  samples summed (may be NULL); reset = 1 zeros the sums after reading;
+ *   timeout_ms  bounded wait for outstanding work (< 0: none).
+ * MOFF_ESTATE if no calibrator is set.
+ */
+moff_status moff_read_feedback(moff_plan *plan, float *corr, double *power, long long *n_samples, int reset,
+                               int timeout_ms);
+
+/*
+ * moff_feedback_gains -- the Sec. 6 gain-error estimate from the current sums,
+ *     delta_g_a,p = g_a,p (1 - A conj(R_a,p) / S_p)
+ * read with the antenna count A where the paper prints 2N (at convergence the
+ * printed factor gives -g, not 0) and with the conjugated ratio (so that
+ * g + delta_g moves each antenna's residual gain to the array mean, to first
+ * order, for a dominant calibrator).  delta: host float32 complex [C][A][P][2]
+ * (may be NULL).  apply = 1 adds delta_g to the plan's gains for the next block.
+ * The relative solution leaves the array's overall gain and phase free (Sec. 6).
+ */
+moff_status moff_feedback_gains(moff_plan *plan, float *delta, int apply);
+
+/*
  * moff_plan_tuning -- how the gridding kernel's shape was chosen (any pointer
  * may be NULL): time_batch = samples gridded and row-transformed per pass (1, 2,
  * 4 or 8), staged = 1 if kernel entries are staged in shared memory, cell_pairs
@@ -224,7 +265,8 @@ moff_status moff_set_timing(moff_plan *plan, int on);
  *   2  column transform + square-and-integrate (step 3 second axis, step 4),
  *   3  (MOFF_PREC_FP16TC only) voltage decode, weighting and FP16 transpose,
  *   4  F-stage output reorder (the four-step F-stage used for C = 1024 with
- *      8 taps writes stream-major and reorders to [F][C][A][P]).
+ *      8 taps writes stream-major and reorders to [F][C][A][P]),
+ *   5  feedback-calibration correlation (when a calibrator is set).
  * Waits for the recorded work.  total_ms / launches may be NULL.  reset = 1
  * drops the records of every kind after reading.
  */

@@ -27,7 +27,7 @@ __all__ = [
     "moff_plan_info", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
     "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "moff_plan_tuning",
     "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
-    "moff_server_destroy",
+    "moff_server_destroy", "moff_set_calibrator", "moff_read_feedback", "moff_feedback_gains",
     "Plan", "Server", "header_symbols", "KERNEL_KINDS",
 ]
 
@@ -43,7 +43,8 @@ MOFF_SERVED = 1 << 3
 MOFF_AUTOTUNE = 1 << 4
 MOFF_GRAPH = 1 << 5
 
-KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep", 4: "fstage_reorder"}
+KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep", 4: "fstage_reorder",
+                5: "feedback_corr"}
 
 STATUS = {0: "MOFF_OK", -1: "MOFF_EINVAL", -2: "MOFF_ENOMEM", -3: "MOFF_ECUDA",
           -4: "MOFF_ESTATE", -5: "MOFF_ETIMEDOUT", -6: "MOFF_EBUSY"}
@@ -82,6 +83,9 @@ _SIGS = {
     "moff_server_stats": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
     "moff_server_destroy": [_vp],
+    "moff_set_calibrator": [_vp, _i, _i],
+    "moff_read_feedback": [_vp, _vp, _vp, ctypes.POINTER(_ll), _i, _i],
+    "moff_feedback_gains": [_vp, _vp, _i],
     "moff_plan_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                          ctypes.POINTER(ctypes.c_double)],
 }
@@ -238,6 +242,27 @@ def moff_plan_tuning(plan):
     _check(lib().moff_plan_tuning(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(p), ctypes.byref(c),
                                   ctypes.byref(d)))
     return dict(time_batch=a.value, staged=b.value, cell_pairs=p.value, source=c.value, best_ms=d.value)
+
+
+def moff_set_calibrator(plan, kx, ky):
+    _check(lib().moff_set_calibrator(plan, int(kx), int(ky)))
+
+
+def moff_read_feedback(plan, C, A, P, reset=0, timeout_ms=-1):
+    """(R complex64 [C, A, P], S float64 [C, P], n_samples) of Sec. 6."""
+    corr = np.empty((C, A, P), dtype=np.complex64)
+    power = np.empty((C, P), dtype=np.float64)
+    n = ctypes.c_longlong(0)
+    _check(lib().moff_read_feedback(plan, corr.ctypes.data, power.ctypes.data, ctypes.byref(n), int(reset),
+                                    int(timeout_ms)))
+    return corr, power, n.value
+
+
+def moff_feedback_gains(plan, C, A, P, apply=0):
+    """Gain-error estimate delta_g complex64 [C, A, P] (Sec. 6); apply=1 adds it to the plan's gains."""
+    d = np.empty((C, A, P), dtype=np.complex64)
+    _check(lib().moff_feedback_gains(plan, d.ctypes.data, int(apply)))
+    return d
 
 
 def moff_set_timing(plan, on):
@@ -449,6 +474,15 @@ class Plan:
 
     def tuning(self):
         return moff_plan_tuning(self.handle)
+
+    def set_calibrator(self, kx, ky):
+        moff_set_calibrator(self.handle, kx, ky)
+
+    def read_feedback(self, reset=False, timeout_ms=-1):
+        return moff_read_feedback(self.handle, self.C, self.A, self.P, int(reset), timeout_ms)
+
+    def feedback_gains(self, apply=False):
+        return moff_feedback_gains(self.handle, self.C, self.A, self.P, int(apply))
 
     def timing(self, kind, reset=False):
         return moff_timing(self.handle, kind, reset)

@@ -272,6 +272,18 @@ struct moff_plan {
     int tune_source = 0;
     double tune_best_ms = 0.0;
 
+    // feedback calibration (Sec. 6): pixel tap, sums, antenna beams towards the pixel
+    bool fb_on = false;
+    int fb_kx = -1, fb_ky = -1;
+    float2 *d_etap = nullptr;          // [Tb][Cb][P]
+    double2 *d_fb_corr = nullptr;      // [C][A*P]
+    double *d_fb_power = nullptr;      // [C][P]
+    double2 *d_fb_beam = nullptr;      // [A*P]
+    float2 *d_fb_out = nullptr;        // [C][A*P] staging of R / delta_g
+    long long fb_samples = 0;
+    std::vector<float> h_taps;         // host copy of the kernels (per-pol plans)
+    std::vector<double> h_pos;
+
     // optional per-launch timing: (kind, start, stop)
     bool timing = false;
     struct Rec { int kind; cudaEvent_t a, b; };
@@ -456,6 +468,40 @@ GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, 
     return g;
 }
 
+#define MOFF_CK_S(call)                     \
+    do {                                    \
+        moff_status s_ = (call);            \
+        if (s_ != MOFF_OK) return s_;       \
+    } while (0)
+
+void set_tap(const moff_plan *pl, ColArgs *ca) {
+    ca->etap = pl->fb_on ? pl->d_etap : nullptr;
+    ca->tap_kx = pl->fb_kx;
+    ca->tap_ky = pl->fb_ky;
+}
+
+// Feedback calibration sums of one chunk (after its column launch wrote the pixel tap).
+moff_status run_feedback(moff_plan *pl, const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc) {
+    if (!pl->fb_on) return MOFF_OK;
+    FbArgs f{};
+    f.volt = volt;
+    f.tstride = tstride;
+    f.t0 = t0;
+    f.nt = nt;
+    f.c0 = c0;
+    f.nc = nc;
+    f.AP = pl->A * pl->P;
+    f.P = pl->P;
+    f.gains = pl->d_gains;
+    f.etap = pl->d_etap;
+    f.corr = pl->d_fb_corr;
+    f.power = pl->d_fb_power;
+    TimedLaunch tf(pl, 5);
+    MOFF_CK(launch_fb_corr(f, pl->st));
+    tf.done();
+    return MOFF_OK;
+}
+
 moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
     const int AP = pl->A * pl->P;
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
@@ -508,9 +554,11 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
             ca.row_inv = pl->d_rs_row_inv;
             ca.sy = pl->d_sy;
             ca.inv_sw = pl->rs_inv_sw;
+            set_tap(pl, &ca);
             TimedLaunch tc(pl, 2);
             MOFF_CK(launch_cols(pl->N, pl->P, ca, pl->st, true));
             tc.done();
+            MOFF_CK_S(run_feedback(pl, volt, tstride, t0, nt, c0, nc));
         }
     }
     return MOFF_OK;
@@ -590,9 +638,11 @@ moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long 
             ca.slab_c = g.slab_c;
             ca.twp = pl->d_twp;
             ca.acc = pl->d_acc;
+            set_tap(pl, &ca);
             TimedLaunch tc(pl, 2);
             MOFF_CK(launch_cols(pl->N, pl->P, ca, pl->st));
             tc.done();
+            MOFF_CK_S(run_feedback(pl, volt, tstride, t0, nt, c0, nc));
         }
     }
     return MOFF_OK;
@@ -1294,6 +1344,7 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
     moff_status s = launch_block(pl, 0, src, n_time, tstride, [&] { return run_image(pl, src, n_time, tstride); });
     if (s != MOFF_OK) return s;
     pl->n_samples += n_time;
+    if (pl->fb_on) pl->fb_samples += n_time;
     return MOFF_OK;
 }
 
@@ -1334,6 +1385,10 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     pl->tc = (flags & MOFF_PREC_FP16TC) != 0;
     pl->served = (flags & MOFF_SERVED) != 0;
     pl->graphs = (flags & MOFF_GRAPH) != 0;
+    if (!pl->jones) {
+        pl->h_taps.assign(taps, taps + (size_t)n_ant * n_pol * ksize * ksize * 2);
+        pl->h_pos.assign(pos, pos + (size_t)n_ant * 2);
+    }
     auto bail = [&](moff_status s) {
         std::string msg = g_err;
         destroy_plan(pl);
@@ -1546,6 +1601,7 @@ moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_d
         if ((s = stage_done(pl, slot)) != MOFF_OK) return s;
     }
     pl->n_samples += n_time;
+    if (pl->fb_on) pl->fb_samples += n_time;
     return MOFF_OK;
 }
 
@@ -1580,6 +1636,7 @@ moff_status moff_submit_adc(moff_plan *pl, const int8_t *adc, long long n_samp, 
     if (s != MOFF_OK) return s;
     if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
     pl->n_samples += F;
+    if (pl->fb_on) pl->fb_samples += F;
     return MOFF_OK;
 }
 
@@ -1684,7 +1741,101 @@ moff_status moff_reset(moff_plan *pl) {
     if (s != MOFF_OK) return s;
     MOFF_CK(cudaMemsetAsync(pl->d_acc, 0, (size_t)pl->C * pl->nprod * pl->N * pl->N * 8, pl->st));
     pl->n_samples = 0;
+    if (pl->fb_on) {
+        MOFF_CK(cudaMemsetAsync(pl->d_fb_corr, 0, (size_t)pl->C * pl->A * pl->P * 16, pl->st));
+        MOFF_CK(cudaMemsetAsync(pl->d_fb_power, 0, (size_t)pl->C * pl->P * 8, pl->st));
+        pl->fb_samples = 0;
+    }
     return MOFF_OK;
+}
+
+moff_status moff_set_calibrator(moff_plan *pl, int kx, int ky) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (kx < 0 && ky < 0) {
+        if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+        pl->fb_on = false;
+        drop_graphs(pl);
+        return MOFF_OK;
+    }
+    if (pl->jones) return fail(MOFF_EINVAL, "feedback calibration needs one kernel per pol (not MOFF_JONES)");
+    if (kx < 0 || kx >= pl->N || ky < 0 || ky >= pl->N)
+        return fail(MOFF_EINVAL, "calibrator pixel (%d, %d) outside the %d x %d image", kx, ky, pl->N, pl->N);
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    const int A = pl->A, P = pl->P, K = pl->K, N = pl->N, h = K / 2;
+    const size_t AP = (size_t)A * P;
+    if (!pl->d_etap) {
+        if ((s = palloc(pl, &pl->d_etap, (size_t)pl->Tb * pl->Cb * P * 8)) != MOFF_OK) return s;
+        if ((s = palloc(pl, &pl->d_fb_corr, (size_t)pl->C * AP * 16)) != MOFF_OK) return s;
+        if ((s = palloc(pl, &pl->d_fb_power, (size_t)pl->C * P * 8)) != MOFF_OK) return s;
+        if ((s = palloc(pl, &pl->d_fb_beam, AP * 16)) != MOFF_OK) return s;
+        if ((s = palloc(pl, &pl->d_fb_out, (size_t)pl->C * AP * 8)) != MOFF_OK) return s;
+    }
+    // B_a,p = sum_{dy,dx} taps[a][p][dy][dx] exp(+2 pi i (ky (ay + dy - h) + kx (ax + dx - h)) / N), FP64
+    std::vector<double2> beam(AP);
+    for (int a = 0; a < A; ++a) {
+        const long long fx = (long long)std::floor(pl->h_pos[2 * a] + 0.5), fy = (long long)std::floor(pl->h_pos[2 * a + 1] + 0.5);
+        const long long ax = ((fx % N) + N) % N, ay = ((fy % N) + N) % N;
+        for (int p = 0; p < P; ++p) {
+            double br = 0.0, bi = 0.0;
+            for (int dy = 0; dy < K; ++dy)
+                for (int dx = 0; dx < K; ++dx) {
+                    const float *t = &pl->h_taps[((((size_t)a * P + p) * K + dy) * K + dx) * 2];
+                    const long long m = ((long long)ky * (ay + dy - h) + (long long)kx * (ax + dx - h)) % N;
+                    double c, sn;
+                    root_unity(m < 0 ? m + N : m, N, &c, &sn);
+                    br += (double)t[0] * c - (double)t[1] * sn;
+                    bi += (double)t[0] * sn + (double)t[1] * c;
+                }
+            beam[(size_t)a * P + p] = make_double2(br, bi);
+        }
+    }
+    MOFF_CK(cudaMemcpy(pl->d_fb_beam, beam.data(), AP * 16, cudaMemcpyHostToDevice));
+    MOFF_CK(cudaMemsetAsync(pl->d_fb_corr, 0, (size_t)pl->C * AP * 16, pl->st));
+    MOFF_CK(cudaMemsetAsync(pl->d_fb_power, 0, (size_t)pl->C * P * 8, pl->st));
+    pl->fb_kx = kx;
+    pl->fb_ky = ky;
+    pl->fb_on = true;
+    pl->fb_samples = 0;
+    drop_graphs(pl);   // the captured launch sequences change
+    return sync_plan(pl, -1);
+}
+
+moff_status moff_read_feedback(moff_plan *pl, float *corr, double *power, long long *n_samples, int reset,
+                               int timeout_ms) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!pl->fb_on) return fail(MOFF_ESTATE, "no calibrator set (moff_set_calibrator)");
+    if ((s = sync_plan(pl, timeout_ms)) != MOFF_OK) return s;
+    if ((s = check_device_err(pl)) != MOFF_OK) return s;
+    const size_t n = (size_t)pl->C * pl->A * pl->P;
+    if (corr) {
+        MOFF_CK(launch_fb_finish(pl->d_fb_corr, pl->d_fb_power, pl->d_fb_beam, pl->d_gains, pl->C, pl->A * pl->P, pl->P,
+                                 pl->A, pl->d_fb_out, nullptr, 0, pl->st));
+        MOFF_CK(cudaMemcpyAsync(corr, pl->d_fb_out, n * 8, cudaMemcpyDeviceToHost, pl->st));
+    }
+    if (power) MOFF_CK(cudaMemcpyAsync(power, pl->d_fb_power, (size_t)pl->C * pl->P * 8, cudaMemcpyDeviceToHost, pl->st));
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    if (n_samples) *n_samples = pl->fb_samples;
+    if (reset) {
+        MOFF_CK(cudaMemsetAsync(pl->d_fb_corr, 0, n * 16, pl->st));
+        MOFF_CK(cudaMemsetAsync(pl->d_fb_power, 0, (size_t)pl->C * pl->P * 8, pl->st));
+        pl->fb_samples = 0;
+    }
+    return MOFF_OK;
+}
+
+moff_status moff_feedback_gains(moff_plan *pl, float *delta, int apply) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!pl->fb_on) return fail(MOFF_ESTATE, "no calibrator set (moff_set_calibrator)");
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    const size_t n = (size_t)pl->C * pl->A * pl->P;
+    MOFF_CK(launch_fb_finish(pl->d_fb_corr, pl->d_fb_power, pl->d_fb_beam, pl->d_gains, pl->C, pl->A * pl->P, pl->P,
+                             pl->A, nullptr, pl->d_fb_out, apply ? 1 : 0, pl->st));
+    if (apply && pl->tc) MOFF_CK(launch_gain_scale(pl->d_gains, pl->C, pl->A * pl->P, pl->d_sy, pl->st));
+    if (delta) MOFF_CK(cudaMemcpyAsync(delta, pl->d_fb_out, n * 8, cudaMemcpyDeviceToHost, pl->st));
+    return sync_plan(pl, -1);
 }
 
 moff_status moff_plan_tuning(const moff_plan *pl, int *time_batch, int *staged, int *cell_pairs, int *source,
@@ -1711,7 +1862,7 @@ moff_status moff_set_timing(moff_plan *pl, int on) {
 moff_status moff_timing(moff_plan *pl, int kind, double *total_ms, long long *launches, int reset) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
-    if (kind < 0 || kind > 4) return fail(MOFF_EINVAL, "kind (%d) must be in [0, 4]", kind);
+    if (kind < 0 || kind > 5) return fail(MOFF_EINVAL, "kind (%d) must be in [0, 5]", kind);
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
     double tot = 0.0;
     long long n = 0;

@@ -391,7 +391,14 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
             for (int r = 0; r < RL; ++r) vx[r] = src[(jL + r * NS) * W + colL];
             twiddle<RL, NS, 1>(vx, jL, tw);
             dft<RL, 1>(vx);
+            // feedback calibration: this thread holds ky = jL + r NS of column kx0 + colL
+            const bool tap = a.etap && kx0 + colL == a.tap_kx && (a.tap_ky - jL) % NS == 0 && a.tap_ky >= jL;
             if constexpr (P == 1) {
+                if (tap) {
+#pragma unroll
+                    for (int r = 0; r < RL; ++r)
+                        if (jL + r * NS == a.tap_ky) a.etap[(long long)tt * a.nc + cl] = vx[r];
+                }
 #pragma unroll
                 for (int r = 0; r < RL; ++r) acc[0][r] = fmaf(vx[r].x, vx[r].x, fmaf(vx[r].y, vx[r].y, acc[0][r]));
             } else {
@@ -400,6 +407,14 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                 for (int r = 0; r < RL; ++r) vy[r] = src[(N + jL + r * NS) * W + colL];
                 twiddle<RL, NS, 1>(vy, jL, tw);
                 dft<RL, 1>(vy);
+                if (tap) {
+#pragma unroll
+                    for (int r = 0; r < RL; ++r)
+                        if (jL + r * NS == a.tap_ky) {
+                            a.etap[((long long)tt * a.nc + cl) * 2] = vx[r];
+                            a.etap[((long long)tt * a.nc + cl) * 2 + 1] = vy[r];
+                        }
+                }
 #pragma unroll
                 for (int r = 0; r < RL; ++r) {
                     acc[0][r] = fmaf(vx[r].x, vx[r].x, fmaf(vx[r].y, vx[r].y, acc[0][r]));

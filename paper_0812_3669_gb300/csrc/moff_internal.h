@@ -57,6 +57,9 @@ struct ColArgs {
     const float *row_inv;
     const float *sy;
     float inv_sw;
+    // feedback calibration: E_t,p(tap_kx, tap_ky) -> etap[t][cl][p] (null: off)
+    float2 *etap;
+    int tap_kx, tap_ky;
 };
 
 // FP16 tensor-core gridding + row transform: per (pol, grid row, kx tile) a
@@ -77,6 +80,20 @@ struct RowSpecArgs {
     long long slab_t, slab_c;
     int *err;                  // set when a bounded wait gives up
 };
+
+// Feedback calibration sums (Sec. 6) over one chunk.
+struct FbArgs {
+    const uint8_t *volt;      // codes [T][C][A][P]
+    long long tstride;        // bytes between samples
+    int t0, nt, c0, nc, AP, P;
+    const float2 *gains;      // [C][A][P]
+    const float2 *etap;       // [nt][nc][P] image pixel towards the calibrator
+    double2 *corr;            // [C][A*P] sums of E conj(y), added to
+    double *power;            // [C][P] sums of |E|^2, added to
+};
+cudaError_t launch_fb_corr(const FbArgs &a, cudaStream_t st);
+cudaError_t launch_fb_finish(const double2 *corr, const double *power, const double2 *beam, float2 *gains, int C,
+                             int AP, int P, int n_ant, float2 *r_out, float2 *delta, int apply, cudaStream_t st);
 
 // Polyphase F-stage (Eq. FFTofE).
 struct PfbArgs {
