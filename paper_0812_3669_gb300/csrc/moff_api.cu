@@ -693,6 +693,7 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     const int tw_total = fft_tw_total(N);
     const int F = grid_fft_rows(N);
     const size_t budget = 110 * 1024;   // two CTAs per SM
+    const size_t big = 225 * 1024;      // one CTA per SM: dense arrays, where more samples per pass reuse each tap
     // Contributions per grid cell (p_out, row, col), independent of the stripe shape.
     std::vector<int> cnt_all((size_t)P * N * N, 0);
     for (int a = 0; a < A; ++a)
@@ -757,8 +758,7 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     if (force) {
         for (const Cand &cd : cands)
             if (cd.tb == force->tb) {
-                const bool fits = force->staged ? cd.sm_staged <= budget
-                                                : (cd.sm_plain <= budget || (cd.tb == 1 && cd.sm_plain <= 200 * 1024));
+                const bool fits = (force->staged ? cd.sm_staged : cd.sm_plain) <= big;
                 if (fits) { pick = &cd; staged = force->staged; }
                 break;
             }
@@ -775,7 +775,10 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
             if (cd->sm_staged <= budget) { pick = cd; staged = true; break; }
     if (!pick)
         for (const Cand *cd : pref)
-            if (cd->sm_plain <= budget || (cd->tb == 1 && cd->sm_plain <= 200 * 1024)) { pick = cd; break; }
+            if (cd->sm_plain <= budget) { pick = cd; break; }
+    if (!pick)   // dense arrays: one CTA per SM, still preferring more samples per pass
+        for (const Cand *cd : pref)
+            if (cd->sm_plain <= big) { pick = cd; break; }
     if (!pick)
         return fail(MOFF_EINVAL, "array too dense for the gridding kernel (antennas per grid row exceed its limits)");
     if (pick->rows * pick->tb * P != F)
@@ -1198,8 +1201,8 @@ std::string tune_key(const moff_plan *pl, const double *pos, const float *taps) 
     cudaGetDeviceProperties(&prop, pl->device);
     h = fnv1a(prop.name, strlen(prop.name), h);
     char buf[128];
-    snprintf(buf, sizeof buf, "grid2-A%d-K%d-N%d-P%d-J%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P, (int)pl->jones,
-             prop.multiProcessorCount, (unsigned long long)h);
+    snprintf(buf, sizeof buf, "grid3-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P,
+             (int)pl->jones, pl->Tb, std::min(pl->Cb, pl->C), prop.multiProcessorCount, (unsigned long long)h);
     return buf;
 }
 
@@ -1224,21 +1227,26 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
             return MOFF_OK;
         }
     }
-    // a short block: 32 samples of up to 64 channels, field scratch <= 512 MB
-    const int N = pl->N, P = pl->P, A = pl->A, nt = 32;
-    const size_t per = (size_t)P * N * N * 8;
-    const int nc = (int)std::max<size_t>(1, std::min<size_t>(std::min(pl->C, 64), ((size_t)512 << 20) / (nt * per)));
+    // one chunk of the plan's own shape (Tb samples x Cb channels) into its field scratch
+    // (a temporary one for a served plan), so the timing sees the launch the plan will make
+    const int N = pl->N, P = pl->P, A = pl->A, nt = pl->Tb;
+    const int nc = std::min(pl->Cb, pl->C);
     const long long tstride = (long long)nc * A * P;
-    void *volt = nullptr, *gains = nullptr, *H = nullptr, *twp = nullptr;
+    void *volt = nullptr, *gains = nullptr, *Htmp = nullptr, *twp = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     std::vector<float2> tw = pass_twiddles_n(N);
     auto cleanup = [&] {
-        cudaFree(volt); cudaFree(gains); cudaFree(H); cudaFree(twp);
+        cudaFree(volt); cudaFree(gains); cudaFree(Htmp); cudaFree(twp);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
+    if (!pl->d_H && cudaMalloc(&Htmp, pl->h_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MOFF_ENOMEM, "autotuner scratch allocation failed");
+    }
+    void *H = pl->d_H ? static_cast<void *>(pl->d_H) : Htmp;
     if (cudaMalloc(&volt, (size_t)nt * tstride) != cudaSuccess || cudaMalloc(&gains, (size_t)nc * A * P * 8) != cudaSuccess ||
-        cudaMalloc(&H, (size_t)nt * nc * per) != cudaSuccess || cudaMalloc(&twp, tw.size() * 8) != cudaSuccess ||
+        cudaMalloc(&twp, tw.size() * 8) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cleanup();
         cudaGetLastError();
@@ -1415,13 +1423,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     if (pl->graphs && cudaStreamCreateWithFlags(&pl->gst, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(MOFF_ECUDA, "capture stream creation failed"));
 
-    GridChoice tuned;
     moff_status s = MOFF_OK;
-    if ((flags & MOFF_AUTOTUNE) && !pl->tc) {
-        if ((s = tune_grid(pl, pos, taps, &tuned)) != MOFF_OK) return bail(s);
-    }
-    s = bin_plan(pl, pos, taps, pl->tune_source ? &tuned : nullptr);
-    if (s != MOFF_OK) return bail(s);
 
     // twiddles of the N-point imaging transform
     {
@@ -1475,6 +1477,14 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
                 return bail(fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded"));
             pl->h_map_nt = pl->Tb;
         }
+    }
+    // gridding shape: measured on the plan's own chunk (MOFF_AUTOTUNE), else the built-in rule
+    {
+        GridChoice tuned;
+        if ((flags & MOFF_AUTOTUNE) && !pl->tc) {
+            if ((s = tune_grid(pl, pos, taps, &tuned)) != MOFF_OK) return bail(s);
+        }
+        if ((s = bin_plan(pl, pos, taps, pl->tune_source ? &tuned : nullptr)) != MOFF_OK) return bail(s);
     }
     if (pl->tc) {
         RowSpec rs;
