@@ -15,7 +15,10 @@ Parity status per function (what pins it other than itself):
                           polarisation-scaled inputs.
 * ``moff_image``       -- all of the above composed.
 * ``fx_image``         -- agreement with ``moff_image`` (independent formulation),
-                          single-antenna flat image.
+                          single-antenna flat image; with ``autos=False`` the
+                          baselines-only image equals ``moff_image`` minus ``auto_image``.
+* ``auto_image``       -- the same identity; a single delta-kernel antenna gives a
+                          flat image of its power.
 * ``pfb_window`` / ``pfb_spectra`` -- 1-tap rectangular case equals a library FFT,
                           a hand-summed 2-tap case, tone-in-bin power.
 * ``quantise_4bit``    -- hand fixtures including half-to-even ties and clipping.

@@ -40,7 +40,7 @@ __all__ = [
     "unpack_4bit", "anchors", "calibrate", "grid_matrix", "grid", "sky_transform",
     "integrate", "moff_image", "fx_image", "footprint", "pfb_window", "pfb_spectra",
     "quantise_4bit", "ambiguous_codes", "channelise", "max_norm_err",
-    "antenna_beam", "feedback_sums_y", "feedback_sums", "feedback_delta",
+    "antenna_beam", "feedback_sums_y", "feedback_sums", "feedback_delta", "auto_image",
 ]
 
 
@@ -281,11 +281,13 @@ def footprint(pos, taps, grid_n: int, n_pol: int, jones: bool = False) -> np.nda
 
 
 def fx_image(codes, gains, pos, taps, grid_n: int, n_pol: int, jones: bool = False,
-             channel: int = 0) -> np.ndarray:
+             channel: int = 0, autos: bool = True) -> np.ndarray:
     """Brute-force FX route to the same image (Eqs. visDef, Bdef, RBeamEq / m1).
 
     1. visibilities v_ab^{qq'} = sum_t y_aq conj(y_bq') for every antenna pair,
-       autocorrelations included (Eq. visDef);
+       autocorrelations included (Eq. visDef) unless ``autos`` is False, which
+       leaves the baselines only: the software-holography image of the
+       visibilities (Sec. 3);
     2. the uv response of a pair is the correlation of the two antennas'
        kernels (Eq. Bdef): with kernel a placed at anchor_a and kernel b at
        anchor_b, B_ab(u) = sum_{d,d'} T_a[d] conj(T_b[d']) at the baseline
@@ -303,6 +305,8 @@ def fx_image(codes, gains, pos, taps, grid_n: int, n_pol: int, jones: bool = Fal
     Po, K = Tf.shape[1], Tf.shape[3]
     anc = anchors(pos)
     vis = np.einsum("taq,tbs->aqbs", y, np.conj(y))                              # [A, Pi, A, Pi]
+    if not autos:
+        vis[np.arange(A), :, np.arange(A), :] = 0.0
     # w[a, b, p, p'] for one kernel-cell pair (d, d'):
     #   sum_{q,q'} v_ab^{qq'} T_a[p, q, d] conj(T_b[p', q', d'])
     dA = (anc[:, None, :] - anc[None, :, :])                                     # [A, A, 2] (x, y)
@@ -327,6 +331,21 @@ def fx_image(codes, gains, pos, taps, grid_n: int, n_pol: int, jones: bool = Fal
     if Po == 1:
         return I[0, 0].real[None]
     return np.stack([I[0, 0].real, I[1, 1].real, I[0, 1].real, I[0, 1].imag])
+
+
+def auto_image(codes, gains, pos, taps, grid_n: int, n_pol: int, channel: int = 0) -> np.ndarray:
+    """The autocorrelation part of the MOFF image: the sum over antennas of the
+    image each antenna makes alone (the a = b terms of <|sum_a c_a|^2>_t), by
+    running the imaging path on one antenna at a time.  One kernel per pol.
+    Returns float64 [n_prod, N, N]."""
+    codes = np.asarray(codes)[:, channel:channel + 1]
+    g = np.asarray(gains)[channel:channel + 1]
+    A = codes.shape[2]
+    out = 0.0
+    for a in range(A):
+        out = out + moff_image(codes[:, :, a:a + 1], g[:, a:a + 1], np.asarray(pos)[a:a + 1],
+                               np.asarray(taps)[a:a + 1], grid_n, n_pol)[0]
+    return out
 
 
 # ----------------------------------------------------------------------------- F-stage

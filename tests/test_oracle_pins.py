@@ -441,3 +441,37 @@ def test_feedback_update_removes_a_simulated_gain_error():
     assert a2 > 0.9 * b2
     b3, a3 = _simulated_step(1j * np.abs(eps), factor=20, conj=False)
     assert a3 > 0.9 * b3
+
+
+# ----------------------------------------------------------------------------- autocorrelation subtraction
+
+@pytest.mark.parametrize("P,K", [(1, 3), (2, 3)])
+def test_baselines_only_image_is_image_minus_autos(P, K):
+    """The FX route without the a = b visibilities equals the MOFF image minus
+    the sum of single-antenna images (two independent routes)."""
+    rng = np.random.default_rng(20 + P)
+    A, N, T = 9, 16, 6
+    pos = rng.uniform(2, 14, size=(A, 2))
+    taps = rng.normal(size=(A, P, K, K)) + 1j * rng.normal(size=(A, P, K, K))
+    codes = synth.pack_4bit(rng.integers(-7, 8, size=(T, 1, A, P)), rng.integers(-7, 8, size=(T, 1, A, P)))
+    gains = synth.gains_random(rng, 1, A, P)
+    full = oracle.moff_image(codes, gains, pos, taps, N, P)[0]
+    autos = oracle.auto_image(codes, gains, pos, taps, N, P)
+    cross = oracle.fx_image(codes, gains, pos, taps, N, P, autos=False)
+    assert np.allclose(full - autos, cross, rtol=0, atol=1e-9 * np.abs(full).max())
+    # the autocorrelation image does not depend on where the antennas are
+    moved = oracle.auto_image(codes, gains, pos + rng.integers(-2, 3, size=(A, 2)), taps, N, P)
+    assert np.allclose(moved, autos, rtol=0, atol=1e-9 * np.abs(autos).max())
+
+
+def test_autos_of_a_delta_antenna_are_flat():
+    """One antenna, delta kernel: its image is flat at sum_t |y|^2 (and so its
+    baselines-only image is zero)."""
+    rng = np.random.default_rng(30)
+    codes = synth.pack_4bit(rng.integers(-7, 8, size=(5, 1, 1, 1)), rng.integers(-7, 8, size=(5, 1, 1, 1)))
+    gains = np.array([[[1.5 - 0.5j]]])
+    y = oracle.calibrate(oracle.unpack_4bit(codes[:, 0]), gains[0])
+    autos = oracle.auto_image(codes, gains, np.array([[3.0, 4.0]]), np.ones((1, 1, 1, 1)), 8, 1)
+    assert np.allclose(autos, np.sum(np.abs(y) ** 2))
+    cross = oracle.fx_image(codes, gains, np.array([[3.0, 4.0]]), np.ones((1, 1, 1, 1)), 8, 1, autos=False)
+    assert np.abs(cross).max() == 0.0
