@@ -239,6 +239,46 @@ moff_status moff_read_feedback(moff_plan *plan, float *corr, double *power, long
 moff_status moff_feedback_gains(moff_plan *plan, float *delta, int apply);
 
 /*
+ * ---- Autocorrelation subtraction.  Software holography (Sec. 3, Eq. RBeamEq)
+ * images the visibilities of antenna pairs; the MOFF image <|sum_a c_a|^2>_t
+ * (Sec. 4) also holds every antenna's own term.
+ *
+ * moff_set_autocorr -- on = 1: from the next block on, also sum per channel
+ * and antenna |y_x|^2, |y_y|^2 and y_x conj(y_y) (one pol: |y|^2); on = 0: stop.
+ * Switching on resets those sums.  MOFF_EINVAL for a MOFF_JONES plan.
+ */
+moff_status moff_set_autocorr(moff_plan *plan, int on);
+
+/*
+ * moff_read_image_cross -- as moff_read_image, minus the autocorrelation part
+ *   sum_a P_a,pq K^_a,p(k) conj(K^_a,q(k))
+ * (P the antenna's summed products, K^ its kernel's transform; positions drop
+ * out): the image of the baselines only.  Done in FP64 before the conversion.
+ * MOFF_ESTATE unless the autocorrelation sums cover exactly the image's samples
+ * (switch them on before the integration starts).  reset = 1 zeros both.
+ */
+moff_status moff_read_image_cross(moff_plan *plan, float *out, long long *n_samples, int reset, int timeout_ms,
+                                  int out_on_device);
+
+/*
+ * ---- Tied-array beams (Sec. 7: the electric-field image can be tapped, each
+ * pixel being a calibrated tied-array beam).
+ *
+ * moff_set_beams -- from the next block on, write the field E_t,p(k_j) (before
+ * squaring) at up to 16 pixels k_j = (kx[j], ky[j]) for every sample of each
+ * block; n_beams = 0 stops.  MOFF_EINVAL for a pixel outside the image.
+ */
+moff_status moff_set_beams(moff_plan *plan, int n_beams, const int *kx, const int *ky);
+
+/*
+ * moff_read_beams -- the beams of the most recent block: out float32 complex
+ * [T][C][n_beams][P][2] (host, or device when out_on_device = 1; may be NULL to
+ * query), n_time receives T.  Bounded wait as moff_read_image.  MOFF_ESTATE if
+ * no beams are set.
+ */
+moff_status moff_read_beams(moff_plan *plan, float *out, int *n_time, int timeout_ms, int out_on_device);
+
+/*
  * moff_plan_tuning -- how the gridding kernel's shape was chosen (any pointer
  * may be NULL): time_batch = samples gridded and row-transformed per pass (1, 2,
  * 4 or 8), staged = 1 if kernel entries are staged in shared memory, cell_pairs
@@ -266,7 +306,8 @@ moff_status moff_set_timing(moff_plan *plan, int on);
  *   3  (MOFF_PREC_FP16TC only) voltage decode, weighting and FP16 transpose,
  *   4  F-stage output reorder (the four-step F-stage used for C = 1024 with
  *      8 taps writes stream-major and reorders to [F][C][A][P]),
- *   5  feedback-calibration correlation (when a calibrator is set).
+ *   5  feedback-calibration correlation (when a calibrator is set),
+ *   6  autocorrelation sums (when switched on).
  * Waits for the recorded work.  total_ms / launches may be NULL.  reset = 1
  * drops the records of every kind after reading.
  */

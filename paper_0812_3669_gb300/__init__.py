@@ -28,6 +28,7 @@ __all__ = [
     "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "moff_plan_tuning",
     "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
     "moff_server_destroy", "moff_set_calibrator", "moff_read_feedback", "moff_feedback_gains",
+    "moff_set_autocorr", "moff_read_image_cross", "moff_set_beams", "moff_read_beams",
     "Plan", "Server", "header_symbols", "KERNEL_KINDS",
 ]
 
@@ -44,7 +45,7 @@ MOFF_AUTOTUNE = 1 << 4
 MOFF_GRAPH = 1 << 5
 
 KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep", 4: "fstage_reorder",
-                5: "feedback_corr"}
+                5: "feedback_corr", 6: "autocorr"}
 
 STATUS = {0: "MOFF_OK", -1: "MOFF_EINVAL", -2: "MOFF_ENOMEM", -3: "MOFF_ECUDA",
           -4: "MOFF_ESTATE", -5: "MOFF_ETIMEDOUT", -6: "MOFF_EBUSY"}
@@ -84,6 +85,10 @@ _SIGS = {
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
     "moff_server_destroy": [_vp],
     "moff_set_calibrator": [_vp, _i, _i],
+    "moff_set_autocorr": [_vp, _i],
+    "moff_read_image_cross": [_vp, _vp, ctypes.POINTER(_ll), _i, _i, _i],
+    "moff_set_beams": [_vp, _i, _vp, _vp],
+    "moff_read_beams": [_vp, _vp, ctypes.POINTER(_i), _i, _i],
     "moff_read_feedback": [_vp, _vp, _vp, ctypes.POINTER(_ll), _i, _i],
     "moff_feedback_gains": [_vp, _vp, _i],
     "moff_plan_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -263,6 +268,34 @@ def moff_feedback_gains(plan, C, A, P, apply=0):
     d = np.empty((C, A, P), dtype=np.complex64)
     _check(lib().moff_feedback_gains(plan, d.ctypes.data, int(apply)))
     return d
+
+
+def moff_set_autocorr(plan, on):
+    _check(lib().moff_set_autocorr(plan, int(on)))
+
+
+def moff_read_image_cross(plan, out, reset=0, timeout_ms=-1):
+    o, dev = _addr(out)
+    n = ctypes.c_longlong(0)
+    _check(lib().moff_read_image_cross(plan, o, ctypes.byref(n), int(reset), int(timeout_ms), dev))
+    return n.value
+
+
+def moff_set_beams(plan, kx, ky):
+    kx = np.ascontiguousarray(kx, dtype=np.int32)
+    ky = np.ascontiguousarray(ky, dtype=np.int32)
+    if kx.shape != ky.shape:
+        raise ValueError("kx and ky must have the same length")
+    _check(lib().moff_set_beams(plan, int(kx.size), kx.ctypes.data if kx.size else None,
+                                ky.ctypes.data if ky.size else None))
+
+
+def moff_read_beams(plan, out=None, timeout_ms=-1):
+    """Number of samples in the last block's beams; fills ``out`` [T][C][n_beams][P] complex64 if given."""
+    n = ctypes.c_int(0)
+    o, dev = _addr(out) if out is not None else (None, 0)
+    _check(lib().moff_read_beams(plan, o, ctypes.byref(n), int(timeout_ms), dev))
+    return n.value
 
 
 def moff_set_timing(plan, on):
@@ -483,6 +516,25 @@ class Plan:
 
     def feedback_gains(self, apply=False):
         return moff_feedback_gains(self.handle, self.C, self.A, self.P, int(apply))
+
+    def set_autocorr(self, on=True):
+        moff_set_autocorr(self.handle, on)
+
+    def read_image_cross(self, reset=False, timeout_ms=-1, out=None):
+        if out is None:
+            out = np.empty((self.C, self.n_prod, self.N, self.N), dtype=np.float32)
+        n = moff_read_image_cross(self.handle, out, int(reset), timeout_ms)
+        return out, n
+
+    def set_beams(self, kx, ky):
+        moff_set_beams(self.handle, kx, ky)
+        self.n_beams = len(kx)
+
+    def read_beams(self, timeout_ms=-1):
+        T = moff_read_beams(self.handle, None, timeout_ms)
+        out = np.empty((T, self.C, self.n_beams, self.P), dtype=np.complex64)
+        moff_read_beams(self.handle, out, timeout_ms)
+        return out
 
     def timing(self, kind, reset=False):
         return moff_timing(self.handle, kind, reset)

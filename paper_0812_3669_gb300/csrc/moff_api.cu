@@ -283,6 +283,19 @@ struct moff_plan {
     long long fb_samples = 0;
     std::vector<float> h_taps;         // host copy of the kernels (per-pol plans)
     std::vector<double> h_pos;
+    // autocorrelation subtraction: per-antenna power sums and kernel cross-correlation patches
+    bool auto_on = false;
+    double2 *d_auto_pw = nullptr;      // [C][A][3]
+    double2 *d_auto_X = nullptr;       // [A][NQ][(2K-1)^2]
+    double2 *d_auto_Q = nullptr;       // [C][NQ][(2K-1)^2]
+    double *d_auto_img = nullptr;      // [C][n_prod][N][N]
+    double2 *d_wN = nullptr;           // exp(+2 pi i m / N)
+    long long auto_samples = 0;
+    // tied-array beams: the field at up to kMaxBeams pixels for every sample of the last block
+    int n_beam = 0, beam_kx[kMaxBeams] = {}, beam_ky[kMaxBeams] = {};
+    float2 *d_beam = nullptr;
+    size_t beam_bytes = 0;
+    int beam_T = 0;
 
     // optional per-launch timing: (kind, start, stop)
     bool timing = false;
@@ -474,14 +487,39 @@ GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, 
         if (s_ != MOFF_OK) return s_;       \
     } while (0)
 
-void set_tap(const moff_plan *pl, ColArgs *ca) {
+void set_tap(const moff_plan *pl, ColArgs *ca, int t0) {
     ca->etap = pl->fb_on ? pl->d_etap : nullptr;
     ca->tap_kx = pl->fb_kx;
     ca->tap_ky = pl->fb_ky;
+    ca->n_beam = pl->n_beam;
+    ca->beam_out = pl->n_beam ? pl->d_beam : nullptr;
+    ca->beam_t0 = t0;
+    ca->beam_C = pl->C;
+    for (int j = 0; j < pl->n_beam; ++j) {
+        ca->beam_kx[j] = pl->beam_kx[j];
+        ca->beam_ky[j] = pl->beam_ky[j];
+    }
 }
 
-// Feedback calibration sums of one chunk (after its column launch wrote the pixel tap).
+// Feedback calibration and autocorrelation sums of one chunk (after its column
+// launch wrote the pixel tap).
 moff_status run_feedback(moff_plan *pl, const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc) {
+    if (pl->auto_on) {
+        FbArgs f{};
+        f.volt = volt;
+        f.tstride = tstride;
+        f.t0 = t0;
+        f.nt = nt;
+        f.c0 = c0;
+        f.nc = nc;
+        f.AP = pl->A * pl->P;
+        f.P = pl->P;
+        f.gains = pl->d_gains;
+        f.corr = pl->d_auto_pw;
+        TimedLaunch ta(pl, 6);
+        MOFF_CK(launch_auto_acc(f, pl->st));
+        ta.done();
+    }
     if (!pl->fb_on) return MOFF_OK;
     FbArgs f{};
     f.volt = volt;
@@ -554,7 +592,7 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
             ca.row_inv = pl->d_rs_row_inv;
             ca.sy = pl->d_sy;
             ca.inv_sw = pl->rs_inv_sw;
-            set_tap(pl, &ca);
+            set_tap(pl, &ca, t0);
             TimedLaunch tc(pl, 2);
             MOFF_CK(launch_cols(pl->N, pl->P, ca, pl->st, true));
             tc.done();
@@ -638,7 +676,7 @@ moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long 
             ca.slab_c = g.slab_c;
             ca.twp = pl->d_twp;
             ca.acc = pl->d_acc;
-            set_tap(pl, &ca);
+            set_tap(pl, &ca, t0);
             TimedLaunch tc(pl, 2);
             MOFF_CK(launch_cols(pl->N, pl->P, ca, pl->st));
             tc.done();
@@ -1150,6 +1188,23 @@ moff_status run_pfb(moff_plan *pl, const int8_t *adc, long long n_samp, int F, i
     return MOFF_OK;
 }
 
+// Beam output for a block of n_time samples (allocated before any capture).
+moff_status ensure_beams(moff_plan *pl, int n_time) {
+    if (!pl->n_beam) return MOFF_OK;
+    const size_t need = (size_t)n_time * pl->C * pl->n_beam * pl->P * 8;
+    if (pl->beam_bytes >= need) return MOFF_OK;
+    moff_status s = sync_plan(pl, -1);
+    if (s != MOFF_OK) return s;
+    pfree(pl, pl->d_beam);
+    pl->dev_bytes -= pl->beam_bytes;
+    pl->d_beam = nullptr;
+    pl->beam_bytes = 0;
+    drop_graphs(pl);   // captured launches hold the old buffer
+    if ((s = palloc(pl, &pl->d_beam, need)) != MOFF_OK) return s;
+    pl->beam_bytes = need;
+    return MOFF_OK;
+}
+
 // Stream-major scratch of the four-step F-stage for F frames (allocated before
 // any capture; a no-op when that path does not apply).
 moff_status ensure_sm(moff_plan *pl, int F, int kind) {
@@ -1330,6 +1385,8 @@ int plan_device(const moff_plan *pl) { return pl->device; }
 cudaStream_t plan_stream(const moff_plan *pl) { return pl->st; }
 
 moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, int n_time, int on_device) {
+    moff_status sb = ensure_beams(pl, n_time);
+    if (sb != MOFF_OK) return sb;
     unsigned char *base = static_cast<unsigned char *>(scratch);
     pl->d_H = reinterpret_cast<float2 *>(base);
     size_t off = align_up(pl->h_bytes, 1024);
@@ -1353,6 +1410,8 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
     if (s != MOFF_OK) return s;
     pl->n_samples += n_time;
     if (pl->fb_on) pl->fb_samples += n_time;
+    if (pl->auto_on) pl->auto_samples += n_time;
+    pl->beam_T = n_time;
     return MOFF_OK;
 }
 
@@ -1598,6 +1657,7 @@ moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_d
     if (n_time < 1) return fail(MOFF_EINVAL, "n_time (%d) must be >= 1", n_time);
     const long long tstride = (long long)pl->C * pl->A * pl->P;
     const size_t bytes = (size_t)n_time * tstride;
+    if ((s = ensure_beams(pl, n_time)) != MOFF_OK) return s;
     auto image = [&](const uint8_t *src) {
         return launch_block(pl, 0, src, n_time, tstride, [&] { return run_image(pl, src, n_time, tstride); });
     };
@@ -1612,6 +1672,8 @@ moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_d
     }
     pl->n_samples += n_time;
     if (pl->fb_on) pl->fb_samples += n_time;
+    if (pl->auto_on) pl->auto_samples += n_time;
+    pl->beam_T = n_time;
     return MOFF_OK;
 }
 
@@ -1631,6 +1693,7 @@ moff_status moff_submit_adc(moff_plan *pl, const int8_t *adc, long long n_samp, 
         pl->codes_bytes = cbytes;
     }
     if ((s = ensure_sm(pl, F, 0)) != MOFF_OK) return s;
+    if ((s = ensure_beams(pl, F)) != MOFF_OK) return s;
     const size_t abytes = (size_t)pl->A * pl->P * n_samp;
     const int8_t *src = adc;
     int slot = -1;
@@ -1647,6 +1710,8 @@ moff_status moff_submit_adc(moff_plan *pl, const int8_t *adc, long long n_samp, 
     if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
     pl->n_samples += F;
     if (pl->fb_on) pl->fb_samples += F;
+    if (pl->auto_on) pl->auto_samples += F;
+    pl->beam_T = F;
     return MOFF_OK;
 }
 
@@ -1755,6 +1820,131 @@ moff_status moff_reset(moff_plan *pl) {
         MOFF_CK(cudaMemsetAsync(pl->d_fb_corr, 0, (size_t)pl->C * pl->A * pl->P * 16, pl->st));
         MOFF_CK(cudaMemsetAsync(pl->d_fb_power, 0, (size_t)pl->C * pl->P * 8, pl->st));
         pl->fb_samples = 0;
+    }
+    if (pl->auto_on) {
+        MOFF_CK(cudaMemsetAsync(pl->d_auto_pw, 0, (size_t)pl->C * pl->A * 3 * 16, pl->st));
+        pl->auto_samples = 0;
+    }
+    return MOFF_OK;
+}
+
+moff_status moff_set_autocorr(moff_plan *pl, int on) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    drop_graphs(pl);   // the captured launch sequences change
+    if (!on) {
+        pl->auto_on = false;
+        return MOFF_OK;
+    }
+    if (pl->jones) return fail(MOFF_EINVAL, "autocorrelation subtraction needs one kernel per pol (not MOFF_JONES)");
+    const int A = pl->A, P = pl->P, K = pl->K, N = pl->N, L = 2 * K - 1, U = L * L, NQ = P == 1 ? 1 : 3;
+    if (!pl->d_auto_pw) {
+        if ((s = palloc(pl, &pl->d_auto_pw, (size_t)pl->C * A * 3 * 16)) != MOFF_OK) return s;
+        if ((s = palloc(pl, &pl->d_auto_X, (size_t)A * NQ * U * 16)) != MOFF_OK) return s;
+        if ((s = palloc(pl, &pl->d_auto_Q, (size_t)pl->C * NQ * U * 16)) != MOFF_OK) return s;
+        if ((s = palloc(pl, &pl->d_auto_img, (size_t)pl->C * pl->nprod * N * N * 8)) != MOFF_OK) return s;
+        if ((s = palloc(pl, &pl->d_wN, (size_t)N * 16)) != MOFF_OK) return s;
+    }
+    // X_a,q(u) = sum_{d - d' = u} T_a,p[d] conj(T_a,p'[d']),  q = (p, p') in {(x,x), (y,y), (x,y)}
+    std::vector<double2> X((size_t)A * NQ * U, make_double2(0.0, 0.0));
+    const int qp[3][2] = {{0, 0}, {1, 1}, {0, 1}};
+    for (int a = 0; a < A; ++a)
+        for (int q = 0; q < NQ; ++q) {
+            const float *T0 = &pl->h_taps[(((size_t)a * P + qp[q][0]) * K * K) * 2];
+            const float *T1 = &pl->h_taps[(((size_t)a * P + qp[q][1]) * K * K) * 2];
+            double2 *Xa = &X[((size_t)a * NQ + q) * U];
+            for (int dy = 0; dy < K; ++dy)
+                for (int dx = 0; dx < K; ++dx) {
+                    const double ar = T0[(dy * K + dx) * 2], ai = T0[(dy * K + dx) * 2 + 1];
+                    if (ar == 0.0 && ai == 0.0) continue;
+                    for (int ey = 0; ey < K; ++ey)
+                        for (int ex = 0; ex < K; ++ex) {
+                            const double br = T1[(ey * K + ex) * 2], bi = -T1[(ey * K + ex) * 2 + 1];
+                            double2 &x = Xa[(dy - ey + K - 1) * L + (dx - ex + K - 1)];
+                            x.x += ar * br - ai * bi;
+                            x.y += ar * bi + ai * br;
+                        }
+                }
+        }
+    std::vector<double2> w(N);
+    for (int m = 0; m < N; ++m) {
+        double c, sn;
+        root_unity(m, N, &c, &sn);
+        w[m] = make_double2(c, sn);
+    }
+    MOFF_CK(cudaMemcpy(pl->d_auto_X, X.data(), X.size() * 16, cudaMemcpyHostToDevice));
+    MOFF_CK(cudaMemcpy(pl->d_wN, w.data(), w.size() * 16, cudaMemcpyHostToDevice));
+    MOFF_CK(cudaMemsetAsync(pl->d_auto_pw, 0, (size_t)pl->C * A * 3 * 16, pl->st));
+    pl->auto_on = true;
+    pl->auto_samples = 0;
+    return sync_plan(pl, -1);
+}
+
+moff_status moff_read_image_cross(moff_plan *pl, float *out, long long *n_samples, int reset, int timeout_ms,
+                                  int out_on_device) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!out) return fail(MOFF_EINVAL, "out is NULL");
+    if (!pl->auto_on) return fail(MOFF_ESTATE, "autocorrelation sums are off (moff_set_autocorr)");
+    if (pl->auto_samples != pl->n_samples)
+        return fail(MOFF_ESTATE, "autocorrelation sums cover %lld of the image's %lld samples (switch them on before the "
+                    "integration starts, or reset)", pl->auto_samples, pl->n_samples);
+    if ((s = sync_plan(pl, timeout_ms)) != MOFF_OK) return s;
+    if ((s = check_device_err(pl)) != MOFF_OK) return s;
+    const long long n = (long long)pl->C * pl->nprod * pl->N * pl->N;
+    MOFF_CK(launch_auto_image(pl->d_auto_pw, pl->d_auto_X, pl->C, pl->A, pl->P, pl->K, pl->N, pl->d_wN, pl->d_auto_Q,
+                              pl->d_auto_img, pl->st));
+    MOFF_CK(launch_sub_to_f32(pl->d_acc, pl->d_auto_img, out_on_device ? out : pl->d_img, n, pl->st));
+    if (!out_on_device) MOFF_CK(cudaMemcpyAsync(out, pl->d_img, (size_t)n * 4, cudaMemcpyDeviceToHost, pl->st));
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    if (n_samples) *n_samples = pl->n_samples;
+    if (reset) {
+        MOFF_CK(cudaMemsetAsync(pl->d_acc, 0, (size_t)n * 8, pl->st));
+        MOFF_CK(cudaMemsetAsync(pl->d_auto_pw, 0, (size_t)pl->C * pl->A * 3 * 16, pl->st));
+        pl->n_samples = 0;
+        pl->auto_samples = 0;
+    }
+    return MOFF_OK;
+}
+
+moff_status moff_set_beams(moff_plan *pl, int n_beams, const int *kx, const int *ky) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (n_beams < 0 || n_beams > kMaxBeams) return fail(MOFF_EINVAL, "n_beams (%d) must be in [0, %d]", n_beams, kMaxBeams);
+    if (n_beams && (!kx || !ky)) return fail(MOFF_EINVAL, "kx and ky must not be NULL");
+    for (int j = 0; j < n_beams; ++j)
+        if (kx[j] < 0 || kx[j] >= pl->N || ky[j] < 0 || ky[j] >= pl->N)
+            return fail(MOFF_EINVAL, "beam %d pixel (%d, %d) outside the %d x %d image", j, kx[j], ky[j], pl->N, pl->N);
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    pl->n_beam = n_beams;
+    for (int j = 0; j < n_beams; ++j) {
+        pl->beam_kx[j] = kx[j];
+        pl->beam_ky[j] = ky[j];
+    }
+    pl->beam_T = 0;
+    if (pl->d_beam) {   // a buffer sized for another beam count: drop it
+        pfree(pl, pl->d_beam);
+        pl->dev_bytes -= pl->beam_bytes;
+        pl->d_beam = nullptr;
+        pl->beam_bytes = 0;
+    }
+    drop_graphs(pl);
+    return MOFF_OK;
+}
+
+moff_status moff_read_beams(moff_plan *pl, float *out, int *n_time, int timeout_ms, int out_on_device) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!pl->n_beam) return fail(MOFF_ESTATE, "no beams set (moff_set_beams)");
+    if ((s = sync_plan(pl, timeout_ms)) != MOFF_OK) return s;
+    if ((s = check_device_err(pl)) != MOFF_OK) return s;
+    if (n_time) *n_time = pl->beam_T;
+    if (out && pl->beam_T) {
+        const size_t bytes = (size_t)pl->beam_T * pl->C * pl->n_beam * pl->P * 8;
+        MOFF_CK(cudaMemcpyAsync(out, pl->d_beam, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                pl->st));
+        return sync_plan(pl, -1);
     }
     return MOFF_OK;
 }
@@ -1872,7 +2062,7 @@ moff_status moff_set_timing(moff_plan *pl, int on) {
 moff_status moff_timing(moff_plan *pl, int kind, double *total_ms, long long *launches, int reset) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
-    if (kind < 0 || kind > 5) return fail(MOFF_EINVAL, "kind (%d) must be in [0, 5]", kind);
+    if (kind < 0 || kind > 6) return fail(MOFF_EINVAL, "kind (%d) must be in [0, 6]", kind);
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
     double tot = 0.0;
     long long n = 0;

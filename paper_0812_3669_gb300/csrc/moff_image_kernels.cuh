@@ -393,12 +393,23 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
             dft<RL, 1>(vx);
             // feedback calibration: this thread holds ky = jL + r NS of column kx0 + colL
             const bool tap = a.etap && kx0 + colL == a.tap_kx && (a.tap_ky - jL) % NS == 0 && a.tap_ky >= jL;
+            // tied-array beams: the field at each beam pixel this thread holds, every sample
+            auto beams = [&](const float2 (&v)[RL], int p) {
+                for (int j = 0; j < a.n_beam; ++j)
+                    if (kx0 + colL == a.beam_kx[j]) {
+#pragma unroll
+                        for (int r = 0; r < RL; ++r)
+                            if (jL + r * NS == a.beam_ky[j])
+                                a.beam_out[(((long long)(a.beam_t0 + tt) * a.beam_C + c) * a.n_beam + j) * P + p] = v[r];
+                    }
+            };
             if constexpr (P == 1) {
                 if (tap) {
 #pragma unroll
                     for (int r = 0; r < RL; ++r)
                         if (jL + r * NS == a.tap_ky) a.etap[(long long)tt * a.nc + cl] = vx[r];
                 }
+                if (a.n_beam) beams(vx, 0);
 #pragma unroll
                 for (int r = 0; r < RL; ++r) acc[0][r] = fmaf(vx[r].x, vx[r].x, fmaf(vx[r].y, vx[r].y, acc[0][r]));
             } else {
@@ -414,6 +425,10 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                             a.etap[((long long)tt * a.nc + cl) * 2] = vx[r];
                             a.etap[((long long)tt * a.nc + cl) * 2 + 1] = vy[r];
                         }
+                }
+                if (a.n_beam) {
+                    beams(vx, 0);
+                    beams(vy, 1);
                 }
 #pragma unroll
                 for (int r = 0; r < RL; ++r) {

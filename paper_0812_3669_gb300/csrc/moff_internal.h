@@ -15,6 +15,7 @@ namespace moff {
 
 constexpr int kBlock = 256;   // threads per CTA of every imaging kernel
 constexpr int kPfbGroup = 32; // antenna-pols per F-stage CTA
+constexpr int kMaxBeams = 16; // tied-array beam pixels per plan
 
 // Gridding + row transform (Eq. m6 steps 1-3, first axis).  One CTA owns
 // one stripe of `rows` grid rows of one channel and walks `nt` samples, TB at
@@ -60,6 +61,10 @@ struct ColArgs {
     // feedback calibration: E_t,p(tap_kx, tap_ky) -> etap[t][cl][p] (null: off)
     float2 *etap;
     int tap_kx, tap_ky;
+    // tied-array beams: E_t,p at n_beam pixels -> beam_out[beam_t0 + t][c0 + cl][j][p]
+    float2 *beam_out;
+    int beam_t0, beam_C, n_beam;
+    int beam_kx[kMaxBeams], beam_ky[kMaxBeams];
 };
 
 // FP16 tensor-core gridding + row transform: per (pol, grid row, kx tile) a
@@ -92,6 +97,14 @@ struct FbArgs {
     double *power;            // [C][P] sums of |E|^2, added to
 };
 cudaError_t launch_fb_corr(const FbArgs &a, cudaStream_t st);
+// Autocorrelation sums per (channel, antenna): |y_x|^2, |y_y|^2, y_x conj(y_y) over a chunk
+// (FbArgs: corr = [C][A][3] double2 sums; etap and power unused).
+cudaError_t launch_auto_acc(const FbArgs &a, cudaStream_t st);
+// The autocorrelation image of every channel and product from the sums and the
+// kernels' cross-correlation patches X [A][NQ][(2K-1)^2] (FP64), into img [C][n_prod][N][N].
+cudaError_t launch_auto_image(const double2 *pw, const double2 *X, int C, int A, int P, int K, int N,
+                              const double2 *wN, double2 *Q, double *img, cudaStream_t st);
+cudaError_t launch_sub_to_f32(const double *acc, const double *sub, float *out, long long n, cudaStream_t st);
 cudaError_t launch_fb_finish(const double2 *corr, const double *power, const double2 *beam, float2 *gains, int C,
                              int AP, int P, int n_ant, float2 *r_out, float2 *delta, int apply, cudaStream_t st);
 
