@@ -255,7 +255,8 @@ moff_status moff_set_autocorr(moff_plan *plan, int on);
  * (P the antenna's summed products, K^ its kernel's transform; positions drop
  * out): the image of the baselines only.  Done in FP64 before the conversion.
  * MOFF_ESTATE unless the autocorrelation sums cover exactly the image's samples
- * (switch them on before the integration starts).  reset = 1 zeros both.
+ * (switch them on before the integration starts).  reset = 1 zeros both, as do
+ * moff_reset and moff_read_image with reset = 1.
  */
 moff_status moff_read_image_cross(moff_plan *plan, float *out, long long *n_samples, int reset, int timeout_ms,
                                   int out_on_device);

@@ -1800,6 +1800,10 @@ moff_status moff_read_image(moff_plan *pl, float *out, long long *n_samples, int
     if (reset) {
         MOFF_CK(cudaMemsetAsync(pl->d_acc, 0, (size_t)n * 8, pl->st));
         pl->n_samples = 0;
+        if (pl->auto_on) {   // the autocorrelation sums follow the integration
+            MOFF_CK(cudaMemsetAsync(pl->d_auto_pw, 0, (size_t)pl->C * pl->A * 3 * 16, pl->st));
+            pl->auto_samples = 0;
+        }
     }
     return MOFF_OK;
 }
