@@ -91,6 +91,18 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     const uint16_t *lcell = a.lane_cell + (long long)s * nsl * 32;
     const long long e0 = soff[0];
 
+    if (nloc == 0) {   // no kernel reaches these rows: their field (and its transform) is zero
+        constexpr int PER_T = P * ROWS * N / 2;     // 16-byte stores per sample
+        for (int i = tid; i < a.nt * PER_T; i += kBlock) {
+            const int t = i / PER_T, e = 2 * (i - t * PER_T);
+            const int p = e / (ROWS * N), rem = e - p * (ROWS * N), rl = rem / N, x = rem - rl * N;
+            float2 *o = a.out + (((long long)t * a.slab_t + (long long)cl * a.slab_c) * P * N + (long long)p * N +
+                                 (long long)s * ROWS + rl) * N + x;
+            *reinterpret_cast<float4 *>(o) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return;
+    }
+
     // Carve (matches grid_smem_bytes).
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *s_tw = reinterpret_cast<float2 *>(smem);
@@ -279,7 +291,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int NPEND>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 
-template <int N, int P, bool H16>
+template <int N, int P, bool H16, bool TAPS>
 __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
     using FP = FftPlan<N>;
     using TW = FftTw<N>;
@@ -392,7 +404,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
             twiddle<RL, NS, 1>(vx, jL, tw);
             dft<RL, 1>(vx);
             // feedback calibration: this thread holds ky = jL + r NS of column kx0 + colL
-            const bool tap = a.etap && kx0 + colL == a.tap_kx && (a.tap_ky - jL) % NS == 0 && a.tap_ky >= jL;
+            const bool tap = TAPS && a.etap && kx0 + colL == a.tap_kx && (a.tap_ky - jL) % NS == 0 && a.tap_ky >= jL;
             // tied-array beams: the field at each beam pixel this thread holds, every sample
             auto beams = [&](const float2 (&v)[RL], int p) {
                 for (int j = 0; j < a.n_beam; ++j)
@@ -409,7 +421,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                     for (int r = 0; r < RL; ++r)
                         if (jL + r * NS == a.tap_ky) a.etap[(long long)tt * a.nc + cl] = vx[r];
                 }
-                if (a.n_beam) beams(vx, 0);
+                if (TAPS && a.n_beam) beams(vx, 0);
 #pragma unroll
                 for (int r = 0; r < RL; ++r) acc[0][r] = fmaf(vx[r].x, vx[r].x, fmaf(vx[r].y, vx[r].y, acc[0][r]));
             } else {
@@ -426,7 +438,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                             a.etap[((long long)tt * a.nc + cl) * 2 + 1] = vy[r];
                         }
                 }
-                if (a.n_beam) {
+                if (TAPS && a.n_beam) {
                     beams(vx, 0);
                     beams(vy, 1);
                 }
@@ -502,7 +514,8 @@ cudaError_t launch_grid_p(int TB, bool staged, bool go, const GridArgs &a, int n
 
 template <int N, int P, bool H16>
 cudaError_t launch_cols_t(const ColArgs &a, cudaStream_t st) {
-    auto k = k_cols_acc<N, P, H16>;
+    // pixel taps (feedback calibration, beams) compiled in only where asked for
+    auto k = (a.etap || a.n_beam) ? k_cols_acc<N, P, H16, true> : k_cols_acc<N, P, H16, false>;
     const size_t smem = col_smem_bytes_t<N>(P, H16);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
