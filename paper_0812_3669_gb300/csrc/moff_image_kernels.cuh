@@ -178,7 +178,12 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
         // samples.  Entries are fetched U at a time so their latencies overlap.
         // With PAIRS a lane owns cells (e, e + 1) of one row and each entry
         // carries both cells' taps, so one read of a voltage row feeds two cells.
-        for (int k = warp; k < nsl; k += kBlock / 32) {
+        // Slices come longest first; warps take them in snake order (w, 2W-1-w, 2W+w, ...)
+        // so that each warp's total stays close to the mean.
+        constexpr int NW = kBlock / 32;
+        for (int r = 0; r * NW < nsl; ++r) {
+            const int k = r * NW + ((r & 1) ? NW - 1 - warp : warp);
+            if (k >= nsl) continue;
             const long long b0 = soff[k];
             const int len = (int)((soff[k + 1] - b0) >> 5);
             const int cell = lcell[k * 32 + lane];
