@@ -207,7 +207,7 @@ struct moff_plan {
 
     // binning
     int rows = 0, n_stripes = 0, max_nloc = 0, n_slices = 0, tb = 1, max_entries = 0;
-    bool staged = false, pairs = false;
+    bool staged = false, pairs = false, wide = false;
     size_t grid_smem = 0;
     int *d_st_ant_off = nullptr, *d_st_ant = nullptr;
     long long *d_slice_off = nullptr;
@@ -478,6 +478,7 @@ GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, 
     g.slab_t = 1;
     g.slab_c = pl->Tb;
     g.pairs = pl->pairs ? 1 : 0;
+    g.wide = pl->wide ? 1 : 0;
     return g;
 }
 
@@ -729,7 +730,9 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     }
     const int pin_n = jones ? 2 : 1;   // input pols per output pol
     const int tw_total = fft_tw_total(N);
-    const int F = grid_fft_rows(N);
+    const char *wide_env = getenv("MOFF_GRID_WIDE");
+    const bool wide = force ? force->wide : (wide_env && atoi(wide_env) != 0);
+    const int F = grid_fft_rows(N) * (wide ? 2 : 1);
     const size_t budget = 110 * 1024;   // two CTAs per SM
     const size_t big = 225 * 1024;      // one CTA per SM: dense arrays, where more samples per pass reuse each tap
     // Contributions per grid cell (p_out, row, col), independent of the stripe shape.
@@ -827,6 +830,7 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     b->max_nloc = pick->nloc;
     b->staged = staged;
     b->pairs = pairs;
+    b->wide = wide;
     b->max_entries = staged ? (int)pick->entries : 0;
     b->grid_smem = staged ? pick->sm_staged : pick->sm_plain;
 
@@ -1085,6 +1089,7 @@ moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps, const 
     pl->tb = b.tb;
     pl->staged = b.staged;
     pl->pairs = b.pairs;
+    pl->wide = b.wide;
     pl->max_entries = b.max_entries;
     pl->n_stripes = b.n_stripes;
     pl->max_nloc = b.max_nloc;
@@ -1256,7 +1261,7 @@ std::string tune_key(const moff_plan *pl, const double *pos, const float *taps) 
     cudaGetDeviceProperties(&prop, pl->device);
     h = fnv1a(prop.name, strlen(prop.name), h);
     char buf[128];
-    snprintf(buf, sizeof buf, "grid3-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P,
+    snprintf(buf, sizeof buf, "grid4-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P,
              (int)pl->jones, pl->Tb, std::min(pl->Cb, pl->C), prop.multiProcessorCount, (unsigned long long)h);
     return buf;
 }
@@ -1269,8 +1274,9 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
         if (!g_tune_loaded && path) {
             if (FILE *f = fopen(path, "r")) {
                 char k[256];
-                int tb = 0, st = 0, pr = 0;
-                while (fscanf(f, "%255s %d %d %d", k, &tb, &st, &pr) == 4) g_tune_cache[k] = GridChoice{tb, st != 0, pr != 0};
+                int tb = 0, st = 0, pr = 0, wd = 0;
+                while (fscanf(f, "%255s %d %d %d %d", k, &tb, &st, &pr, &wd) == 5)
+                    g_tune_cache[k] = GridChoice{tb, st != 0, pr != 0, wd != 0};
                 fclose(f);
             }
         }
@@ -1318,8 +1324,8 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     GridChoice best{};
     float best_ms = 0.f;
     for (int tb = 8; tb >= 1; tb /= 2)
-        for (int cand = 0; cand < 4; ++cand) {
-            const GridChoice ch{tb, (cand & 1) != 0, (cand & 2) != 0};
+        for (int cand = 0; cand < 8; ++cand) {
+            const GridChoice ch{tb, (cand & 1) != 0, (cand & 2) != 0, (cand & 4) != 0};
             moff_plan tmp;
             tmp.A = A; tmp.K = pl->K; tmp.N = N; tmp.C = nc; tmp.P = P; tmp.jones = pl->jones;
             tmp.device = pl->device;
@@ -1351,8 +1357,8 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
                 return fail(MOFF_ECUDA, "autotuner launch failed");
             }
             if (getenv("MOFF_TUNE_VERBOSE"))
-                fprintf(stderr, "moff autotune: tb=%d staged=%d pairs=%d  %.4f ms\n", ch.tb, (int)ch.staged,
-                        (int)ch.pairs, ms);
+                fprintf(stderr, "moff autotune: tb=%d staged=%d pairs=%d wide=%d  %.4f ms\n", ch.tb, (int)ch.staged,
+                        (int)ch.pairs, (int)ch.wide, ms);
             if (best.tb == 0 || ms < best_ms) {
                 best = ch;
                 best_ms = ms;
@@ -1367,7 +1373,7 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     g_tune_cache[key] = best;
     if (path)
         if (FILE *f = fopen(path, "a")) {
-            fprintf(f, "%s %d %d %d\n", key.c_str(), best.tb, (int)best.staged, (int)best.pairs);
+            fprintf(f, "%s %d %d %d %d\n", key.c_str(), best.tb, (int)best.staged, (int)best.pairs, (int)best.wide);
             fclose(f);
         }
     return MOFF_OK;

@@ -59,20 +59,21 @@ __device__ __forceinline__ void rows_pass(const float2 *src, float2 *dst, const 
 }
 
 // Stripe height of the gridding kernel: TB samples x P pols x ROWS rows = F rows per pass.
-template <int N, int P, int TB>
+template <int N, int P, int TB, bool WIDE = false>
 struct GridShape {
-    static constexpr int FR = N >= 256 ? 8 : (N == 128 ? 16 : 32);   // == grid_fft_rows(N)
+    // rows per pass: grid_fft_rows(N), or twice that for the wide variant
+    static constexpr int FR = (N >= 256 ? 8 : (N == 128 ? 16 : 32)) * (WIDE ? 2 : 1);
     static constexpr int ROWS_ = FR / (TB * P);
     static constexpr int ROWS = ROWS_ < 1 ? 1 : (ROWS_ > N ? N : ROWS_);
     static constexpr int PR = P * ROWS;
     static constexpr int F = TB * PR;
 };
 
-template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, bool PAIRS>
+template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, bool PAIRS, bool WIDE>
 __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     using FP = FftPlan<N>;
     using TW = FftTw<N>;
-    using GS = GridShape<N, P, TB>;
+    using GS = GridShape<N, P, TB, WIDE>;
     constexpr int LDR = PaddedLen<N>::value;
     constexpr int YS = VoltStride<TB>::value;
     constexpr int ROWS = GS::ROWS, PR = GS::PR, F = GS::F;
@@ -480,41 +481,44 @@ size_t col_smem_bytes_t(int P, bool h16 = false) {
            (h16 ? (size_t)P * N * 4 : 0);
 }
 
-template <int N, int P, int TB, bool ST, bool GO, bool PR>
+template <int N, int P, int TB, bool ST, bool GO, bool PR, bool WD>
 cudaError_t launch_grid_t(const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st) {
-    auto k = k_grid_rows<N, P, TB, ST, GO, PR>;
+    auto k = k_grid_rows<N, P, TB, ST, GO, PR, WD>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<dim3(n_stripes, a.nc), kBlock, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int N, int P, bool ST, bool GO, bool PR>
+template <int N, int P, bool ST, bool GO, bool PR, bool WD>
 cudaError_t launch_grid_s(int TB, const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st) {
     switch (TB) {
-        case 1: return launch_grid_t<N, P, 1, ST, GO, PR>(a, n_stripes, smem, st);
-        case 2: return launch_grid_t<N, P, 2, ST, GO, PR>(a, n_stripes, smem, st);
-        case 4: return launch_grid_t<N, P, 4, ST, GO, PR>(a, n_stripes, smem, st);
-        case 8: return launch_grid_t<N, P, 8, ST, GO, PR>(a, n_stripes, smem, st);
+        case 1: return launch_grid_t<N, P, 1, ST, GO, PR, WD>(a, n_stripes, smem, st);
+        case 2: return launch_grid_t<N, P, 2, ST, GO, PR, WD>(a, n_stripes, smem, st);
+        case 4: return launch_grid_t<N, P, 4, ST, GO, PR, WD>(a, n_stripes, smem, st);
+        case 8: return launch_grid_t<N, P, 8, ST, GO, PR, WD>(a, n_stripes, smem, st);
     }
     return cudaErrorInvalidValue;
 }
 
 // The stripe height is a compile-time function of TB, so the grid-only
 // variant runs with the plan's TB too (and stores only the first sample).
-template <int N, int P, bool PR>
+template <int N, int P, bool PR, bool WD>
 cudaError_t launch_grid_q(int TB, bool staged, bool go, const GridArgs &a, int n_stripes, size_t smem,
                           cudaStream_t st) {
-    if (go) return launch_grid_s<N, P, false, true, PR>(TB, a, n_stripes, smem, st);
-    return staged ? launch_grid_s<N, P, true, false, PR>(TB, a, n_stripes, smem, st)
-                  : launch_grid_s<N, P, false, false, PR>(TB, a, n_stripes, smem, st);
+    if (go) return launch_grid_s<N, P, false, true, PR, WD>(TB, a, n_stripes, smem, st);
+    return staged ? launch_grid_s<N, P, true, false, PR, WD>(TB, a, n_stripes, smem, st)
+                  : launch_grid_s<N, P, false, false, PR, WD>(TB, a, n_stripes, smem, st);
 }
 
 template <int N, int P>
 cudaError_t launch_grid_p(int TB, bool staged, bool go, const GridArgs &a, int n_stripes, size_t smem,
                           cudaStream_t st) {
-    return a.pairs ? launch_grid_q<N, P, true>(TB, staged, go, a, n_stripes, smem, st)
-                   : launch_grid_q<N, P, false>(TB, staged, go, a, n_stripes, smem, st);
+    if (a.wide)
+        return a.pairs ? launch_grid_q<N, P, true, true>(TB, staged, go, a, n_stripes, smem, st)
+                       : launch_grid_q<N, P, false, true>(TB, staged, go, a, n_stripes, smem, st);
+    return a.pairs ? launch_grid_q<N, P, true, false>(TB, staged, go, a, n_stripes, smem, st)
+                   : launch_grid_q<N, P, false, false>(TB, staged, go, a, n_stripes, smem, st);
 }
 
 template <int N, int P, bool H16>

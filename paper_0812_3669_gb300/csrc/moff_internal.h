@@ -44,6 +44,7 @@ struct GridArgs {
                               // (sample t, channel cl) at index t * slab_t + cl * slab_c
     long long slab_t, slab_c;
     int pairs;                // 1: each lane sums two horizontally adjacent cells (entries carry two taps)
+    int wide;                 // 1: twice grid_fft_rows(N) rows per pass
 };
 
 // Column transform + square-and-integrate (Eq. m6 steps 3-4, second axis).
@@ -159,6 +160,7 @@ struct Bins {
     int rows = 0, n_stripes = 0, tb = 1, max_nloc = 0, n_slices = 0, max_entries = 0;
     bool staged = false;   // kernel entries staged in shared memory
     bool pairs = false;    // lanes own pairs of adjacent cells; con_tap holds two taps per entry
+    bool wide = false;     // twice grid_fft_rows(N) rows transformed per pass
     size_t grid_smem = 0;
     std::vector<int> ant_off, ant_list;
     std::vector<long long> slice_off;
@@ -172,6 +174,7 @@ struct GridChoice {
     int tb = 0;
     bool staged = false;
     bool pairs = false;   // each lane sums two horizontally adjacent cells
+    bool wide = false;    // twice grid_fft_rows(N) rows per pass (more gather work per barrier)
 };
 // force = nullptr: the built-in rule; else exactly that shape (MOFF_EINVAL if infeasible).
 moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b,
