@@ -113,14 +113,14 @@ template <int NPEND>
 __device__ __forceinline__ void cp_async_wait_tc() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 
 // Warp roles: warps 0-3 drain the TMEM accumulators (one lane quarter each),
-// warps 4-7 stage A in K-chunks of 64 with cp.async, warp 8 issues the MMAs
+// warps 4-15 stage A in K-chunks of 64 with cp.async, warp 16 issues the MMAs
 // (one lane).  A: 3-stage ring of [128 samples x 64] MN-major chunks; B:
 // resident; accumulators: two in TMEM; epilogue: each warp converts its 32
 // samples x 32 kx to FP16 into a 128-byte-swizzled box in shared memory and
 // one lane hands it to the TMA unit (bulk tensor store), two boxes in flight
 // per warp.  Per-thread global stores from four warps could not keep enough
 // writes in flight; the bulk stores can.
-constexpr int kEpiWarps = 4, kProdWarps = 4;
+constexpr int kEpiWarps = 4, kProdWarps = 12;   // 12 producer warps keep more A gathers in flight
 constexpr int kTcRoleThreads = (kEpiWarps + kProdWarps + 1) * 32;
 constexpr int kAStages = 3, kKChunk = 64;
 constexpr int kAChunkBytes = 128 * kKChunk * 2;
