@@ -295,7 +295,9 @@ struct moff_plan {
     int n_beam = 0, beam_kx[kMaxBeams] = {}, beam_ky[kMaxBeams] = {};
     float2 *d_beam = nullptr;
     size_t beam_bytes = 0;
-    int beam_T = 0;
+    int beam_T = 0, beam_base = 0;     // beam_base: first sample of the block segment being imaged
+    // pipelined host-ADC staging: one event per frame segment
+    cudaEvent_t seg_ev[16] = {};
 
     // optional per-launch timing: (kind, start, stop)
     bool timing = false;
@@ -342,6 +344,8 @@ void destroy_plan(moff_plan *pl) {
     for (auto &r : pl->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (cudaEvent_t e : pl->ev_pool) cudaEventDestroy(e);
     for (auto &g : pl->gcache) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : pl->seg_ev)
+        if (e) cudaEventDestroy(e);
     if (pl->gst) cudaStreamDestroy(pl->gst);
     if (pl->cst) cudaStreamDestroy(pl->cst);
     if (pl->own_stream && pl->st) cudaStreamDestroy(pl->st);
@@ -494,7 +498,7 @@ void set_tap(const moff_plan *pl, ColArgs *ca, int t0) {
     ca->tap_ky = pl->fb_ky;
     ca->n_beam = pl->n_beam;
     ca->beam_out = pl->n_beam ? pl->d_beam : nullptr;
-    ca->beam_t0 = t0;
+    ca->beam_t0 = pl->beam_base + t0;
     ca->beam_C = pl->C;
     for (int j = 0; j < pl->n_beam; ++j) {
         ca->beam_kx[j] = pl->beam_kx[j];
@@ -1683,6 +1687,56 @@ moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_d
     return MOFF_OK;
 }
 
+// Host ADC block staged in frame segments: each segment's copy (cudaMemcpy2DAsync
+// of its sample range, every stream, on the copy stream) is followed on the
+// plan's stream by that segment's F-stage and imaging, so later copies overlap
+// earlier compute.  Segments overlap by n_taps - 1 frames of samples.
+constexpr int kSegFrames = 128;
+
+moff_status submit_adc_pipelined(moff_plan *pl, const int8_t *adc, long long n_samp, int F) {
+    const int i = (int)(pl->nsub & 1);
+    const size_t abytes = (size_t)pl->A * pl->P * n_samp;
+    moff_status s = MOFF_OK;
+    if (pl->stage_bytes[i] < abytes) {
+        MOFF_CK(cudaEventSynchronize(pl->ev_consumed[i]));
+        pfree(pl, pl->d_stage[i]);
+        pl->dev_bytes -= pl->stage_bytes[i];
+        pl->d_stage[i] = nullptr;
+        pl->stage_bytes[i] = 0;
+        if ((s = palloc(pl, &pl->d_stage[i], abytes)) != MOFF_OK) return s;
+        pl->stage_bytes[i] = abytes;
+    }
+    for (cudaEvent_t &e : pl->seg_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return fail(MOFF_ECUDA, "event creation failed");
+    const int nseg_max = (int)(sizeof(pl->seg_ev) / sizeof(pl->seg_ev[0]));
+    int seg = kSegFrames;
+    while ((F + seg - 1) / seg > nseg_max) seg += kSegFrames;
+    const long long M = 2LL * pl->C, tstride = (long long)pl->C * pl->A * pl->P;
+    const int AP = pl->A * pl->P;
+    int8_t *dst = static_cast<int8_t *>(pl->d_stage[i]);
+    MOFF_CK(cudaStreamWaitEvent(pl->cst, pl->ev_consumed[i], 0));
+    int e = 0;
+    for (int f0 = 0; f0 < F; f0 += seg, ++e) {
+        const int f1 = std::min(F, f0 + seg);
+        const long long c0 = (long long)f0 * M, c1 = (long long)(f1 + pl->ntaps - 1) * M;
+        MOFF_CK(cudaMemcpy2DAsync(dst + c0, (size_t)n_samp, adc + c0, (size_t)n_samp, (size_t)(c1 - c0), (size_t)AP,
+                                  cudaMemcpyHostToDevice, pl->cst));
+        MOFF_CK(cudaEventRecord(pl->seg_ev[e], pl->cst));
+        MOFF_CK(cudaStreamWaitEvent(pl->st, pl->seg_ev[e], 0));
+        uint8_t *codes = pl->d_codes + (size_t)f0 * tstride;
+        if ((s = run_pfb(pl, dst + c0, n_samp, f1 - f0, 0, codes)) != MOFF_OK) break;
+        pl->beam_base = f0;
+        if ((s = run_image(pl, codes, f1 - f0, tstride)) != MOFF_OK) break;
+    }
+    pl->beam_base = 0;
+    MOFF_CK(cudaEventRecord(pl->ev_copied[i], pl->cst));
+    MOFF_CK(cudaEventRecord(pl->ev_consumed[i], pl->st));
+    pl->nsub++;
+    moff_status w = wait_event(pl->ev_copied[i], -1);   // the caller's buffer is free once copied
+    return s != MOFF_OK ? s : w;
+}
+
 moff_status moff_submit_adc(moff_plan *pl, const int8_t *adc, long long n_samp, int on_device) {
     moff_status s = check_unserved(pl);
     if (s != MOFF_OK) return s;
@@ -1701,19 +1755,24 @@ moff_status moff_submit_adc(moff_plan *pl, const int8_t *adc, long long n_samp, 
     if ((s = ensure_sm(pl, F, 0)) != MOFF_OK) return s;
     if ((s = ensure_beams(pl, F)) != MOFF_OK) return s;
     const size_t abytes = (size_t)pl->A * pl->P * n_samp;
-    const int8_t *src = adc;
-    int slot = -1;
-    if (!on_device) {
-        const void *dev = nullptr;
-        if ((s = stage_in(pl, adc, abytes, &dev, &slot)) != MOFF_OK) return s;
-        src = reinterpret_cast<const int8_t *>(dev);
+    static const bool pipeline = !(getenv("MOFF_STAGE_PIPELINE") && atoi(getenv("MOFF_STAGE_PIPELINE")) == 0);
+    if (pipeline && !on_device && !pl->graphs && F > kSegFrames) {
+        if ((s = submit_adc_pipelined(pl, adc, n_samp, F)) != MOFF_OK) return s;
+    } else {
+        const int8_t *src = adc;
+        int slot = -1;
+        if (!on_device) {
+            const void *dev = nullptr;
+            if ((s = stage_in(pl, adc, abytes, &dev, &slot)) != MOFF_OK) return s;
+            src = reinterpret_cast<const int8_t *>(dev);
+        }
+        s = launch_block(pl, 1, src, n_samp, (long long)(void *)pl->d_codes, [&] {
+            moff_status r = run_pfb(pl, src, n_samp, F, 0, pl->d_codes);
+            return r != MOFF_OK ? r : run_image(pl, pl->d_codes, F, (long long)pl->C * pl->A * pl->P);
+        });
+        if (s != MOFF_OK) return s;
+        if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
     }
-    s = launch_block(pl, 1, src, n_samp, (long long)(void *)pl->d_codes, [&] {
-        moff_status r = run_pfb(pl, src, n_samp, F, 0, pl->d_codes);
-        return r != MOFF_OK ? r : run_image(pl, pl->d_codes, F, (long long)pl->C * pl->A * pl->P);
-    });
-    if (s != MOFF_OK) return s;
-    if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
     pl->n_samples += F;
     if (pl->fb_on) pl->fb_samples += F;
     if (pl->auto_on) pl->auto_samples += F;

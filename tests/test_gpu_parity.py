@@ -410,3 +410,27 @@ def test_cell_pair_lanes_are_bit_identical(monkeypatch, N, P, K, A, jones, stage
     assert np.array_equal(out["0"][0], out["1"][0])
     assert np.array_equal(out["0"][1], out["1"][1])
     assert_image(out["1"][0], oracle.moff_image(codes, gains, pos, taps, N, P, jones=jones))
+
+
+def test_host_adc_pipelined_staging_equals_device_input():
+    """A host ADC block longer than one staging segment (128 frames) is copied in
+    frame segments that overlap the F-stage and imaging of earlier ones; the
+    result (image, F-stage frames, beams) must equal the device-input submit."""
+    A, P, C, N, ntaps, F = 6, 2, 64, 32, 8, 300
+    rng = np.random.default_rng(77)
+    pos = rng.uniform(4, 28, size=(A, 2))
+    taps = c64(rng.normal(size=(A, P, 3, 3)) + 1j * rng.normal(size=(A, P, 3, 3)))
+    adc = synth.adc_stream(rng, A, P, (F + ntaps - 1) * 2 * C, sigma=20.0)
+    out = []
+    for host in (True, False):
+        with moff.Plan(pos, taps, N, C, P, fstage=True) as pl:
+            pl.set_fstage(ntaps, None, 0.03)
+            pl.set_beams([3, 17], [5, 30])
+            src = adc if host else torch.from_numpy(adc).cuda()
+            pl.submit_adc(src)
+            beams = pl.read_beams()
+            img, n = pl.read_image()
+        assert n == F and beams.shape == (F, C, 2, P)
+        out.append((img, beams))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
