@@ -260,15 +260,26 @@ def traffic_for(kernel_key, src_files):
     return rec.get("bytes_per_launch")
 
 
-def serving_leg(args, moff, synth, torch):
+def serving_leg(args, moff, synth, torch, fp16tc=False):
     """Request stream over sub-arrays of uneven size (MOFF_SERVED plans, one
     moff_server): first a closed burst to find the saturation rate, then Poisson
-    arrivals at fractions of it.  Reports p50/p99 block latency and throughput."""
+    arrivals at fractions of it.  Reports p50/p99 block latency and throughput.
+    With fp16tc, each sub-array takes the FP16 tensor-core path where its density
+    allows (at most 128 kernel rows per grid row) and FP32 otherwise."""
     import numpy as np
     mix = synth.config_serving()
-    plans, blocks = [], []
+    plans, blocks, prec = [], [], []
     for i, a in enumerate(mix):
-        pl = moff.Plan(a["pos"], a["taps"], a["N"], a["C"], 2, served=True)
+        pl = None
+        if fp16tc:
+            try:
+                pl = moff.Plan(a["pos"], a["taps"], a["N"], a["C"], 2, served=True, fp16tc=True)
+                prec.append("fp16tc")
+            except moff.MoffError:
+                pl = None
+        if pl is None:
+            pl = moff.Plan(a["pos"], a["taps"], a["N"], a["C"], 2, served=True)
+            prec.append("fp32")
         pl.set_gains(a["gains"])
         plans.append(pl)
         blocks.append(synth.device_codes(SEED + 500 + i, a["T"], a["C"], a["A"], 2))
@@ -314,8 +325,10 @@ def serving_leg(args, moff, synth, torch):
         for pl in plans:
             pl.close()
     return {
-        "unit": UNIT, "precision": "fp32", "slots": 4, "pool_bytes": 24 << 30,
-        "mix": [{"antennas": a["A"], "grid_n": a["N"], "channels": a["C"], "samples": a["T"]} for a in mix],
+        "unit": UNIT, "precision": "fp16tc where the array allows, else fp32" if fp16tc else "fp32",
+        "slots": 4, "pool_bytes": 24 << 30,
+        "mix": [{"antennas": a["A"], "grid_n": a["N"], "channels": a["C"], "samples": a["T"], "path": p}
+                for a, p in zip(mix, prec)],
         "mix_note": "request sizes scaled to channels in {64,128,256} and 100-300 samples so a sweep takes seconds",
         "saturation": {"req_per_s": sat_req_s, "throughput": sat["throughput"], "p50_ms": sat["p50_ms"],
                        "p99_ms": sat["p99_ms"], "requests": sat["completed"]},
@@ -593,6 +606,7 @@ def run_ours(args):
     serving = None
     if not args.no_serving:
         serving = serving_leg(args, moff, synth, torch)
+        serving["fp16tc_stream"] = serving_leg(args, moff, synth, torch, fp16tc=True)
     batching = None
     if not args.no_plain:
         batching = batching_leg(args, moff, synth, torch)
