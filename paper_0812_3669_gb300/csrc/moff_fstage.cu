@@ -348,7 +348,36 @@ cudaError_t launch_pfb1024(const PfbArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Byte reorder with 16-byte accesses: a CTA moves a 64-stream x 64-channel tile of
+// one frame; each thread loads 16 channels of one stream and stores 16 streams of
+// one channel.  Needs AP a multiple of 64 (C is 1024 here).
+__global__ void __launch_bounds__(256) k_to_time_major_u8x16(const uint8_t *__restrict__ in, uint8_t *__restrict__ out,
+                                                             int AP, int F, int C) {
+    __shared__ __align__(16) uint8_t tile[64][64 + 16];
+    const int c0 = blockIdx.x * 64, ap0 = blockIdx.y * 64, f = blockIdx.z;
+    const int tid = threadIdx.x;
+    {
+        const int r = tid >> 2, q = tid & 3;      // stream ap0 + r, channels c0 + 16 q ..
+        const uint4 v = *reinterpret_cast<const uint4 *>(in + ((long long)(ap0 + r) * F + f) * C + c0 + 16 * q);
+        *reinterpret_cast<uint4 *>(&tile[r][16 * q]) = v;
+    }
+    __syncthreads();
+    {
+        const int cc = tid >> 2, q = tid & 3;     // channel c0 + cc, streams ap0 + 16 q ..
+        uint32_t w[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            w[b] = (uint32_t)tile[16 * q + 4 * b][cc] | ((uint32_t)tile[16 * q + 4 * b + 1][cc] << 8) |
+                   ((uint32_t)tile[16 * q + 4 * b + 2][cc] << 16) | ((uint32_t)tile[16 * q + 4 * b + 3][cc] << 24);
+        *reinterpret_cast<uint4 *>(out + ((long long)f * C + c0 + cc) * AP + ap0 + 16 * q) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 cudaError_t launch_pfb_reorder(const PfbArgs &a, cudaStream_t st) {
+    if (a.out_kind == 0 && a.AP % 64 == 0 && ((uintptr_t)a.codes & 15) == 0 && ((uintptr_t)a.codes_sm & 15) == 0) {
+        k_to_time_major_u8x16<<<dim3(1024 / 64, a.AP / 64, a.F), 256, 0, st>>>(a.codes_sm, a.codes, a.AP, a.F, 1024);
+        return cudaGetLastError();
+    }
     const dim3 tg((1024 + 31) / 32, (a.AP + 31) / 32, a.F);
     if (a.out_kind == 0)
         k_to_time_major<uint8_t><<<tg, 256, 0, st>>>(a.codes_sm, a.codes, a.AP, a.F, 1024);

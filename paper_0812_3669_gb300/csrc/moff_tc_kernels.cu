@@ -61,7 +61,9 @@ __global__ void k_gain_scale(const float2 *__restrict__ gains, int AP, float *__
 }
 
 // Voltages of samples [t0, t0+nt) of channels [c0, c0+nc) -> FP16 planes
-// Yre/Yim [nc][AP][Tpad] (t contiguous), zero for t >= nt.  Tile 32 t x 64 voltages.
+// Yre/Yim [nc][AP][Tpad] (t contiguous), zero for t >= nt.  Tile 32 t x 64 voltages:
+// each thread loads four voltages of one sample (4 bytes) and stores two samples of
+// one voltage (half2) per plane.
 __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ volt, long long tstride, int t0, int nt,
                                                    int c0, int AP, const float2 *__restrict__ gains,
                                                    const float *__restrict__ sy, int Tpad, __half *__restrict__ yre,
@@ -70,26 +72,41 @@ __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ v
     const int cl = blockIdx.z, c = c0 + cl;
     const int v0 = blockIdx.x * 64, tb = blockIdx.y * 32;
     const float s = sy[c];
-    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
-        const int tt = i / 64, v = i % 64;
-        const int t = tb + tt, vi = v0 + v;
-        float2 y = make_float2(0.f, 0.f);
-        if (t < nt && vi < AP) {
-            const uint8_t b = volt[(long long)(t0 + t) * tstride + (long long)c * AP + vi];
-            y = cmul(gains[(long long)c * AP + vi], decode4_tc(b));
-            y.x *= s;
-            y.y *= s;
+    const bool vec = (AP & 3) == 0 && (tstride & 3) == 0 && ((uintptr_t)volt & 3) == 0;
+    for (int i = threadIdx.x; i < 32 * 16; i += 256) {
+        const int tt = i / 16, v4 = (i % 16) * 4;
+        const int t = tb + tt;
+        uint32_t b4 = 0;
+        if (t < nt) {
+            const uint8_t *src = volt + (long long)(t0 + t) * tstride + (long long)c * AP + v0 + v4;
+            if (vec && v0 + v4 + 3 < AP) {
+                b4 = *reinterpret_cast<const uint32_t *>(src);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (v0 + v4 + u < AP) b4 |= (uint32_t)src[u] << (8 * u);
+            }
         }
-        tile[tt][v] = y;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int vi = v0 + v4 + u;
+            float2 y = make_float2(0.f, 0.f);
+            if (t < nt && vi < AP) {
+                y = cmul(gains[(long long)c * AP + vi], decode4_tc((b4 >> (8 * u)) & 0xffu));
+                y.x *= s;
+                y.y *= s;
+            }
+            tile[tt][v4 + u] = y;
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
-        const int v = i / 32, tt = i % 32;
+    for (int i = threadIdx.x; i < 64 * 16; i += 256) {
+        const int v = i / 16, tt = (i % 16) * 2;
         const int t = tb + tt, vi = v0 + v;
         if (vi < AP && t < Tpad) {
-            const long long o = ((long long)cl * AP + vi) * Tpad + t;
-            yre[o] = __float2half_rn(tile[tt][v].x);
-            yim[o] = __float2half_rn(tile[tt][v].y);
+            const long long o = ((long long)cl * AP + vi) * Tpad + t;   // t even, Tpad even: 4-byte aligned
+            *reinterpret_cast<__half2 *>(yre + o) = __floats2half2_rn(tile[tt][v].x, tile[tt + 1][v].x);
+            *reinterpret_cast<__half2 *>(yim + o) = __floats2half2_rn(tile[tt][v].y, tile[tt + 1][v].y);
         }
     }
 }
