@@ -285,10 +285,12 @@ moff_status moff_read_beams(moff_plan *plan, float *out, int *n_time, int timeou
  * 4 or 8), staged = 1 if kernel entries are staged in shared memory, cell_pairs
  * = 1 if each lane sums two adjacent grid cells (one voltage read feeds both),
  * source = 0 built-in rule, 1 measured by MOFF_AUTOTUNE at creation, 2 taken
- * from the tuning cache; best_ms = the measured time of the chosen shape (source 1).
+ * from the tuning cache; best_ms = the measured time of the chosen shape (source
+ * 1); wide_rows = 1 if twice the usual number of grid rows is transformed per
+ * pass (more gather work between barriers).
  */
 moff_status moff_plan_tuning(const moff_plan *plan, int *time_batch, int *staged, int *cell_pairs, int *source,
-                             double *best_ms);
+                             double *best_ms, int *wide_rows);
 
 /*
  * moff_set_timing -- when on (1), every kernel the plan launches is bracketed

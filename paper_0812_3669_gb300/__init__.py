@@ -92,7 +92,7 @@ _SIGS = {
     "moff_read_feedback": [_vp, _vp, _vp, ctypes.POINTER(_ll), _i, _i],
     "moff_feedback_gains": [_vp, _vp, _i],
     "moff_plan_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
-                         ctypes.POINTER(ctypes.c_double)],
+                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)],
 }
 
 
@@ -242,11 +242,12 @@ def moff_plan_info(plan):
 
 
 def moff_plan_tuning(plan):
-    a, b, p, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    a, b, p, c, w = (ctypes.c_int() for _ in range(5))
     d = ctypes.c_double()
     _check(lib().moff_plan_tuning(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(p), ctypes.byref(c),
-                                  ctypes.byref(d)))
-    return dict(time_batch=a.value, staged=b.value, cell_pairs=p.value, source=c.value, best_ms=d.value)
+                                  ctypes.byref(d), ctypes.byref(w)))
+    return dict(time_batch=a.value, staged=b.value, cell_pairs=p.value, source=c.value, best_ms=d.value,
+                wide_rows=w.value)
 
 
 def moff_set_calibrator(plan, kx, ky):

@@ -2108,7 +2108,7 @@ moff_status moff_feedback_gains(moff_plan *pl, float *delta, int apply) {
 }
 
 moff_status moff_plan_tuning(const moff_plan *pl, int *time_batch, int *staged, int *cell_pairs, int *source,
-                             double *best_ms) {
+                             double *best_ms, int *wide_rows) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
     if (time_batch) *time_batch = pl->tb;
@@ -2116,6 +2116,7 @@ moff_status moff_plan_tuning(const moff_plan *pl, int *time_batch, int *staged, 
     if (cell_pairs) *cell_pairs = pl->pairs ? 1 : 0;
     if (source) *source = pl->tune_source;
     if (best_ms) *best_ms = pl->tune_best_ms;
+    if (wide_rows) *wide_rows = pl->wide ? 1 : 0;
     return MOFF_OK;
 }
 
