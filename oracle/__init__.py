@@ -13,7 +13,12 @@ Parity status per function (what pins it other than itself):
 * ``sky_transform``    -- naive DFT on tiny grids, point-source closed form (sign).
 * ``integrate``        -- FX identity (conjugation order of XY), Cauchy-Schwarz,
                           polarisation-scaled inputs.
-* ``moff_image``       -- all of the above composed.
+* ``moff_image``       -- all of the above composed; edge padding (a grid twice as
+                          large, footprints not wrapping) samples the same image at
+                          every second pixel.
+* ``moff_image_sets``  -- a point source imaged through frequency-scaled
+                          positions peaks at the same pixel with the closed-form
+                          value in every channel; one set equals ``moff_image``.
 * ``fx_image``         -- agreement with ``moff_image`` (independent formulation),
                           single-antenna flat image; with ``autos=False`` the
                           baselines-only image equals ``moff_image`` minus ``auto_image``.

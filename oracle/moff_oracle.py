@@ -40,7 +40,7 @@ __all__ = [
     "unpack_4bit", "anchors", "calibrate", "grid_matrix", "grid", "sky_transform",
     "integrate", "moff_image", "fx_image", "footprint", "pfb_window", "pfb_spectra",
     "quantise_4bit", "ambiguous_codes", "channelise", "max_norm_err",
-    "antenna_beam", "feedback_sums_y", "feedback_sums", "feedback_delta", "auto_image",
+    "antenna_beam", "feedback_sums_y", "feedback_sums", "feedback_delta", "auto_image", "moff_image_sets",
 ]
 
 
@@ -181,6 +181,25 @@ def moff_image(codes, gains, pos, taps, grid_n: int, n_pol: int, jones: bool = F
             G = grid(y, W, grid_n, n_pol)
             E = sky_transform(G)
             out[ci] += integrate(E)
+    return out
+
+
+def moff_image_sets(codes, gains, pos_sets, taps_sets, chan_group, grid_n: int, n_pol: int,
+                    jones: bool = False) -> np.ndarray:
+    """Eq. m6 with channel-dependent antenna positions and kernels.
+
+    Positions in wavelengths scale with frequency, and the kernels (the
+    antennas' illumination, Sec. 4 also folds w-projection into them) may change
+    with it; channel c is imaged exactly as ``moff_image`` would with the set
+    ``chan_group[c]``: ``pos_sets`` [G, A, 2], ``taps_sets`` [G, A, ...].
+    """
+    codes = np.asarray(codes)
+    C = codes.shape[1]
+    grp = np.asarray(chan_group, dtype=int)
+    out = np.zeros((C, 1 if n_pol == 1 else 4, grid_n, grid_n))
+    for g in sorted(set(grp.tolist())):
+        chans = [c for c in range(C) if grp[c] == g]
+        out[chans] = moff_image(codes, gains, pos_sets[g], taps_sets[g], grid_n, n_pol, jones, channels=chans)
     return out
 
 

@@ -109,6 +109,53 @@ def test_point_source_closed_form_and_sign():
     assert abs(I[th[1], th[0]] - 49 * T * A * A) < 1e-6
 
 
+def test_frequency_scaled_positions_keep_the_source_pixel():
+    """Channel-dependent positions (Sec. 4 names frequency-dependent imaging effects;
+    uv positions in wavelengths scale with frequency): channel c sees the array at
+    s_c times its reference positions.  A source at theta_s observed with each
+    channel's own positions peaks at +theta_s in every channel with 49 T A^2 and the
+    closed-form PSF of that channel's positions; a set mix-up would misplace it."""
+    rng = np.random.default_rng(21)
+    N, A, T = 32, 12, 3
+    base = _integer_layout(rng, A, N // 3, 1)                       # 0..10, so 3x stays on the grid
+    scale = [1, 2, 3, 2]                                            # chan_group = [0, 1, 2, 1]
+    sets = np.stack([base * s for s in (1, 2, 3)])
+    grp = [0, 1, 2, 1]
+    th = np.array([8, 16])
+    codes = np.zeros((T, len(grp), A, 1), dtype=np.uint8)
+    for c, g in enumerate(grp):
+        x = 7 * np.exp(-2j * np.pi * (sets[g] @ th) / N)           # in {+-7, +-7i}
+        codes[:, c, :, 0] = _codes_from_complex(x)[None]
+    taps = np.ones((3, A, 1, 1, 1), dtype=complex)
+    gains = np.ones((len(grp), A, 1), dtype=complex)
+    I = oracle.moff_image_sets(codes, gains, sets, taps, grp, N, 1)
+    k = np.stack(np.meshgrid(np.arange(N), np.arange(N), indexing="xy"), axis=-1)
+    for c, g in enumerate(grp):
+        phase = np.exp(2j * np.pi * np.einsum("yxc,ac->yxa", k - th, sets[g]) / N)
+        np.testing.assert_allclose(I[c, 0], 49 * T * np.abs(phase.sum(axis=-1)) ** 2, rtol=1e-12, atol=1e-9)
+        assert abs(I[c, 0, th[1], th[0]] - 49 * T * A * A) < 1e-6
+    assert scale[3] == scale[1] and np.array_equal(I[1], I[3])
+    # one set for every channel is the plain image
+    one = oracle.moff_image_sets(codes, gains, sets[:1], taps[:1], [0] * len(grp), N, 1)
+    np.testing.assert_array_equal(one, oracle.moff_image(codes, gains, sets[0], taps[0], N, 1))
+
+
+def test_edge_padding_samples_the_same_image():
+    """Image oversampling by edge padding of the FFT input (Sec. 4): with footprints
+    that wrap on neither grid, the image on a 2N grid at even pixels equals the
+    N-grid image (a DFT of a zero-padded field, sampled at every second frequency)."""
+    rng = np.random.default_rng(22)
+    N, A, T, K, P = 16, 7, 4, 3, 2
+    pos = rng.uniform(2, N - 3, size=(A, 2))
+    taps = rng.normal(size=(A, P, K, K)) + 1j * rng.normal(size=(A, P, K, K))
+    codes = _codes_from_complex(rng.integers(-7, 8, size=(T, 1, A, P)) + 1j * rng.integers(-7, 8, size=(T, 1, A, P)))
+    gains = np.exp(1j * rng.uniform(0, 6, size=(1, A, P)))
+    I1 = oracle.moff_image(codes, gains, pos, taps, N, P)
+    I2 = oracle.moff_image(codes, gains, pos, taps, 2 * N, P)
+    np.testing.assert_allclose(I2[:, :, ::2, ::2], I1, rtol=0, atol=1e-9 * np.abs(I1).max())
+    assert np.abs(I2[:, :2, 1::2, 1::2]).max() > 0          # the padded grid adds the in-between pixels
+
+
 def test_shared_kernel_multiplies_by_kernel_power():
     """A kernel shared by every antenna multiplies the delta-kernel image by |K^(k)|^2,
     K^(k) = sum_d t[d] exp(+2 pi i k.(d - K//2)/N)."""
