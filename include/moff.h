@@ -122,6 +122,30 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
 moff_status moff_set_gains(moff_plan *plan, const float *gains, int on_device);
 
 /*
+ * moff_set_channel_groups -- channel-dependent antenna positions and kernels.
+ * Antenna positions in grid cells (wavelengths) scale with frequency, and so
+ * do the kernels that describe each antenna's illumination; Sec. 4 also folds
+ * w-projection into the kernels.  The plan takes n_groups sets, each laid out
+ * as in moff_plan_create:
+ *   pos         host float64 [n_groups][A][2]
+ *   taps        host float32 complex [n_groups][A][P][K][K][2] (MOFF_JONES:
+ *               [n_groups][A][2][2][K][K][2])
+ *   chan_group  host int [C]: the set of each channel (may be NULL when
+ *               n_groups = 1, which replaces the creation-time set)
+ * All copied.  Channels of one set are imaged exactly as a plan created with
+ * that set.  The gridding shape stays the plan's where every set fits it, else
+ * the first of the built-in rule's shapes that all sets fit.  Waits for the
+ * plan's work in flight; applies to blocks submitted afterwards (the running
+ * integration is kept: reset first to start a new one).  Calibrator beams and
+ * autocorrelation patches follow the new sets.  FP32 path only.
+ * Errors: MOFF_EINVAL (MOFF_PREC_FP16TC plan, n_groups outside [1, C], a
+ * chan_group entry outside [0, n_groups), a position not finite, or a set too
+ * dense for the gridding kernel; the plan is unchanged), MOFF_ENOMEM, MOFF_ECUDA.
+ */
+moff_status moff_set_channel_groups(moff_plan *plan, int n_groups, const double *pos, const float *taps,
+                                   const int *chan_group);
+
+/*
  * moff_set_fstage -- configure the polyphase F-stage (Sec. 2, Eq. FFTofE).
  *   n_taps  filter length in frames, 1 <= n_taps <= 16.
  *   coeffs  host float32 [n_taps * M] prototype filter h[n], or NULL for the

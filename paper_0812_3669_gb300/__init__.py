@@ -28,7 +28,7 @@ __all__ = [
     "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "moff_plan_tuning",
     "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
     "moff_server_destroy", "moff_set_calibrator", "moff_read_feedback", "moff_feedback_gains",
-    "moff_set_autocorr", "moff_read_image_cross", "moff_set_beams", "moff_read_beams",
+    "moff_set_autocorr", "moff_read_image_cross", "moff_set_beams", "moff_read_beams", "moff_set_channel_groups",
     "Plan", "Server", "header_symbols", "KERNEL_KINDS",
 ]
 
@@ -62,6 +62,7 @@ _vp, _i, _u, _ll, _f = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_lo
 _SIGS = {
     "moff_plan_create": [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _i, _i, _i, _u, _vp],
     "moff_set_gains": [_vp, _vp, _i],
+    "moff_set_channel_groups": [_vp, _i, _vp, _vp, _vp],
     "moff_set_fstage": [_vp, _i, _vp, _f],
     "moff_submit": [_vp, _vp, _i, _i],
     "moff_submit_adc": [_vp, _vp, _ll, _i],
@@ -186,6 +187,16 @@ def moff_set_gains(plan, gains):
     else:
         g = _f32_interleaved(gains)
         _check(lib().moff_set_gains(plan, g.ctypes.data, 0))
+
+
+def moff_set_channel_groups(plan, pos, taps, chan_group=None):
+    """Channel-dependent positions and kernels: ``pos`` float64 [G][A][2], ``taps``
+    complex [G][A][...] laid out as for moff_plan_create, ``chan_group`` int [C]."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    t32 = _f32_interleaved(taps)
+    g = None if chan_group is None else np.ascontiguousarray(chan_group, dtype=np.int32)
+    _check(lib().moff_set_channel_groups(plan, int(pos.shape[0]), pos.ctypes.data, t32.ctypes.data,
+                                         None if g is None else g.ctypes.data))
 
 
 def moff_set_fstage(plan, n_taps, coeffs=None, scale=1.0):
@@ -464,6 +475,9 @@ class Plan:
 
     def set_gains(self, gains):
         moff_set_gains(self.handle, gains)
+
+    def set_channel_groups(self, pos, taps, chan_group=None):
+        moff_set_channel_groups(self.handle, pos, taps, chan_group)
 
     def set_fstage(self, n_taps=8, coeffs=None, scale=1.0):
         moff_set_fstage(self.handle, n_taps, coeffs, scale)

@@ -281,8 +281,12 @@ struct moff_plan {
     double2 *d_fb_beam = nullptr;      // [A*P]
     float2 *d_fb_out = nullptr;        // [C][A*P] staging of R / delta_g
     long long fb_samples = 0;
-    std::vector<float> h_taps;         // host copy of the kernels (per-pol plans)
-    std::vector<double> h_pos;
+    std::vector<float> h_taps;         // host copy of the kernels (per-pol plans), one block per set
+    std::vector<double> h_pos;         // host copy of the positions, one block per set
+    // channel-dependent positions and kernels (moff_set_channel_groups): n_groups sets,
+    // d_chan_group [C] the set of each channel (nullptr while there is one set)
+    int n_groups = 1;
+    int *d_chan_group = nullptr;
     // autocorrelation subtraction: per-antenna power sums and kernel cross-correlation patches
     bool auto_on = false;
     double2 *d_auto_pw = nullptr;      // [C][A][3]
@@ -483,6 +487,7 @@ GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, 
     g.slab_c = pl->Tb;
     g.pairs = pl->pairs ? 1 : 0;
     g.wide = pl->wide ? 1 : 0;
+    g.chan_group = pl->d_chan_group;
     return g;
 }
 
@@ -1085,10 +1090,109 @@ moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *
 
 namespace {
 
-moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps, const GridChoice *force = nullptr) {
-    Bins b;
-    moff_status s = build_bins(pl->A, pl->K, pl->N, pl->P, pl->jones, pos, taps, &b, force);
-    if (s != MOFF_OK) return s;
+// Kernel bins of n_sets sets of positions and kernels ([sets][A] blocks laid out as for
+// moff_plan_create) with one common gridding shape, concatenated into one Bins: set g's
+// stripe offsets, slice offsets and lane cells follow set g - 1's, with their values
+// rebased so that one antenna list and one entry list serve all sets (GridArgs::chan_group).
+// One set: the built-in rule or force.  Several: the shape in force (else the rule's
+// preferences) that every set fits, with shared memory sized for the densest set.
+moff_status build_bin_sets(const moff_plan *pl, int n_sets, const double *pos, const float *taps,
+                           const GridChoice *force, Bins *out) {
+    const int A = pl->A, K = pl->K, N = pl->N, P = pl->P;
+    if (n_sets == 1) return build_bins(A, K, N, P, pl->jones, pos, taps, out, force);
+    const size_t pos_set = (size_t)A * 2;
+    const size_t tap_set = (size_t)A * P * (pl->jones ? 2 : 1) * K * K * 2;
+    std::vector<GridChoice> cands;
+    if (force) cands.push_back(*force);
+    for (bool pr : {pl->pairs, !pl->pairs})
+        for (int tb : {4, 8, 2, 1}) cands.push_back(GridChoice{tb, false, pr, false});
+    const int nthr = (int)std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 32u));
+    std::vector<Bins> bins(n_sets);
+    std::vector<moff_status> st(n_sets);
+    for (const GridChoice &ch : cands) {
+        std::vector<std::thread> workers;
+        for (int w = 0; w < std::min(nthr, n_sets); ++w)
+            workers.emplace_back([&, w] {
+                for (int g = w; g < n_sets; g += nthr) {
+                    bins[g] = Bins{};
+                    st[g] = build_bins(A, K, N, P, pl->jones, pos + g * pos_set, taps + g * tap_set, &bins[g], &ch);
+                }
+            });
+        for (std::thread &t : workers) t.join();
+        int bad = -1;
+        for (int g = 0; g < n_sets && bad < 0; ++g)
+            if (st[g] != MOFF_OK) bad = g;
+        if (bad >= 0) {
+            if (&ch == &cands.back()) {   // the message of the first set that fits no shape
+                Bins tmp;
+                return build_bins(A, K, N, P, pl->jones, pos + bad * pos_set, taps + bad * tap_set, &tmp, &ch);
+            }
+            continue;
+        }
+        Bins &o = *out;
+        o = Bins{};
+        const Bins &b0 = bins[0];
+        o.rows = b0.rows; o.tb = b0.tb; o.n_stripes = b0.n_stripes; o.n_slices = b0.n_slices;
+        o.staged = b0.staged; o.pairs = b0.pairs; o.wide = b0.wide;
+        for (const Bins &b : bins) {
+            if (b.n_slices != b0.n_slices || b.n_stripes != b0.n_stripes)
+                return fail(MOFF_EINVAL, "internal: sets binned to different stripe shapes");
+            o.max_nloc = std::max(o.max_nloc, b.max_nloc);
+            o.max_entries = std::max(o.max_entries, b.max_entries);
+        }
+        o.grid_smem = grid_smem_bytes(N, P, o.tb, o.rows, o.max_nloc, fft_tw_total(N), o.staged ? o.max_entries : 0,
+                                      o.pairs);
+        if (o.grid_smem > 225 * 1024) continue;
+        const size_t tpe = o.pairs ? 2 : 1;
+        long long ebase = 0;
+        int abase = 0;
+        for (const Bins &b : bins) {
+            if (b.slice_off.back() != (long long)b.con_y.size() || b.con_tap.size() != tpe * b.con_y.size())
+                return fail(MOFF_EINVAL, "internal: inconsistent kernel bins");
+            for (int v : b.ant_off) o.ant_off.push_back(v + abase);
+            for (long long v : b.slice_off) o.slice_off.push_back(v + ebase);
+            o.ant_list.insert(o.ant_list.end(), b.ant_list.begin(), b.ant_list.end());
+            o.lane_cell.insert(o.lane_cell.end(), b.lane_cell.begin(), b.lane_cell.end());
+            o.con_tap.insert(o.con_tap.end(), b.con_tap.begin(), b.con_tap.end());
+            o.con_y.insert(o.con_y.end(), b.con_y.begin(), b.con_y.end());
+            abase += (int)b.ant_list.size();
+            ebase += (long long)b.con_y.size();
+        }
+        return MOFF_OK;
+    }
+    return fail(MOFF_EINVAL, "no gridding shape fits every set of positions and kernels in shared memory");
+}
+
+// Upload bins and adopt their shape; the plan keeps its old bins if an allocation fails.
+moff_status upload_bins(moff_plan *pl, const Bins &b) {
+    int *ant_off = nullptr, *ant = nullptr;
+    long long *soff = nullptr;
+    uint16_t *lcell = nullptr, *cy = nullptr;
+    float2 *ctap = nullptr;
+    auto undo = [&](moff_status s) {
+        pfree(pl, ant_off); pfree(pl, ant); pfree(pl, soff); pfree(pl, lcell); pfree(pl, ctap); pfree(pl, cy);
+        return s;
+    };
+    moff_status s;
+    if ((s = palloc(pl, &ant_off, b.ant_off.size() * 4)) != MOFF_OK) return undo(s);
+    if ((s = palloc(pl, &ant, std::max<size_t>(b.ant_list.size(), 1) * 4)) != MOFF_OK) return undo(s);
+    if ((s = palloc(pl, &soff, b.slice_off.size() * 8)) != MOFF_OK) return undo(s);
+    if ((s = palloc(pl, &lcell, b.lane_cell.size() * 2)) != MOFF_OK) return undo(s);
+    if ((s = palloc(pl, &ctap, std::max<size_t>(b.con_tap.size(), 1) * 8)) != MOFF_OK) return undo(s);
+    if ((s = palloc(pl, &cy, std::max<size_t>(b.con_y.size(), 1) * 2)) != MOFF_OK) return undo(s);
+    bool ok = cudaMemcpy(ant_off, b.ant_off.data(), b.ant_off.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(soff, b.slice_off.data(), b.slice_off.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(lcell, b.lane_cell.data(), b.lane_cell.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && !b.ant_list.empty())
+        ok = cudaMemcpy(ant, b.ant_list.data(), b.ant_list.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && !b.con_tap.empty())
+        ok = cudaMemcpy(ctap, b.con_tap.data(), b.con_tap.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(cy, b.con_y.data(), b.con_y.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) return undo(fail(MOFF_ECUDA, "upload of the kernel bins failed"));
+    pfree(pl, pl->d_st_ant_off); pfree(pl, pl->d_st_ant); pfree(pl, pl->d_slice_off);
+    pfree(pl, pl->d_lane_cell); pfree(pl, pl->d_con_tap); pfree(pl, pl->d_con_y);
+    pl->d_st_ant_off = ant_off; pl->d_st_ant = ant; pl->d_slice_off = soff;
+    pl->d_lane_cell = lcell; pl->d_con_tap = ctap; pl->d_con_y = cy;
     pl->rows = b.rows;
     pl->tb = b.tb;
     pl->staged = b.staged;
@@ -1099,22 +1203,13 @@ moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps, const 
     pl->max_nloc = b.max_nloc;
     pl->n_slices = b.n_slices;
     pl->grid_smem = b.grid_smem;
-    if ((s = palloc(pl, &pl->d_st_ant_off, b.ant_off.size() * 4)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_st_ant, std::max<size_t>(b.ant_list.size(), 1) * 4)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_slice_off, b.slice_off.size() * 8)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_lane_cell, b.lane_cell.size() * 2)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_con_tap, std::max<size_t>(b.con_tap.size(), 1) * 8)) != MOFF_OK) return s;
-    if ((s = palloc(pl, &pl->d_con_y, std::max<size_t>(b.con_y.size(), 1) * 2)) != MOFF_OK) return s;
-    MOFF_CK(cudaMemcpy(pl->d_st_ant_off, b.ant_off.data(), b.ant_off.size() * 4, cudaMemcpyHostToDevice));
-    if (!b.ant_list.empty())
-        MOFF_CK(cudaMemcpy(pl->d_st_ant, b.ant_list.data(), b.ant_list.size() * 4, cudaMemcpyHostToDevice));
-    MOFF_CK(cudaMemcpy(pl->d_slice_off, b.slice_off.data(), b.slice_off.size() * 8, cudaMemcpyHostToDevice));
-    MOFF_CK(cudaMemcpy(pl->d_lane_cell, b.lane_cell.data(), b.lane_cell.size() * 2, cudaMemcpyHostToDevice));
-    if (!b.con_tap.empty()) {
-        MOFF_CK(cudaMemcpy(pl->d_con_tap, b.con_tap.data(), b.con_tap.size() * 8, cudaMemcpyHostToDevice));
-        MOFF_CK(cudaMemcpy(pl->d_con_y, b.con_y.data(), b.con_y.size() * 2, cudaMemcpyHostToDevice));
-    }
     return MOFF_OK;
+}
+
+moff_status bin_plan(moff_plan *pl, const double *pos, const float *taps, const GridChoice *force = nullptr) {
+    Bins b;
+    moff_status s = build_bin_sets(pl, 1, pos, taps, force, &b);
+    return s != MOFF_OK ? s : upload_bins(pl, b);
 }
 
 moff_status upload_fstage(moff_plan *pl, int ntaps, const float *coeffs, float scale) {
@@ -1380,6 +1475,78 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
             fprintf(f, "%s %d %d %d %d\n", key.c_str(), best.tb, (int)best.staged, (int)best.pairs, (int)best.wide);
             fclose(f);
         }
+    return MOFF_OK;
+}
+
+// Every antenna's beam towards the calibrator pixel (kx, ky), per set of positions and
+// kernels: B_a,p = sum_{dy,dx} taps[a][p][dy][dx] exp(+2 pi i (ky (ay + dy - h) + kx (ax + dx - h)) / N),
+// FP64 [sets][A][P].
+moff_status upload_fb_beams(moff_plan *pl, int kx, int ky) {
+    const int A = pl->A, P = pl->P, K = pl->K, N = pl->N, h = K / 2, G = pl->n_groups;
+    std::vector<double2> beam((size_t)G * A * P);
+    for (int ga = 0; ga < G * A; ++ga) {      // antenna ga % A of set ga / A ([sets][A] host blocks)
+        const long long fx = (long long)std::floor(pl->h_pos[2 * (size_t)ga] + 0.5);
+        const long long fy = (long long)std::floor(pl->h_pos[2 * (size_t)ga + 1] + 0.5);
+        const long long ax = ((fx % N) + N) % N, ay = ((fy % N) + N) % N;
+        for (int p = 0; p < P; ++p) {
+            double br = 0.0, bi = 0.0;
+            for (int dy = 0; dy < K; ++dy)
+                for (int dx = 0; dx < K; ++dx) {
+                    const float *t = &pl->h_taps[((((size_t)ga * P + p) * K + dy) * K + dx) * 2];
+                    const long long m = ((long long)ky * (ay + dy - h) + (long long)kx * (ax + dx - h)) % N;
+                    double c, sn;
+                    root_unity(m < 0 ? m + N : m, N, &c, &sn);
+                    br += (double)t[0] * c - (double)t[1] * sn;
+                    bi += (double)t[0] * sn + (double)t[1] * c;
+                }
+            beam[(size_t)ga * P + p] = make_double2(br, bi);
+        }
+    }
+    double2 *d = nullptr;
+    moff_status s = palloc(pl, &d, beam.size() * 16);
+    if (s != MOFF_OK) return s;
+    if (cudaMemcpy(d, beam.data(), beam.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
+        pfree(pl, d);
+        return fail(MOFF_ECUDA, "upload of the calibrator beams failed");
+    }
+    pfree(pl, pl->d_fb_beam);
+    pl->d_fb_beam = d;
+    return MOFF_OK;
+}
+
+// The kernels' cross-correlation patches of every set, X_a,q(u) = sum_{d - d' = u}
+// T_a,p[d] conj(T_a,p'[d']) with q = (p, p') in {(x,x), (y,y), (x,y)}, FP64 [sets][A][NQ][U].
+moff_status upload_auto_patches(moff_plan *pl) {
+    const int A = pl->A, P = pl->P, K = pl->K, L = 2 * K - 1, U = L * L, NQ = P == 1 ? 1 : 3, G = pl->n_groups;
+    std::vector<double2> X((size_t)G * A * NQ * U, make_double2(0.0, 0.0));
+    const int qp[3][2] = {{0, 0}, {1, 1}, {0, 1}};
+    for (int ga = 0; ga < G * A; ++ga)           // antenna ga % A of set ga / A ([sets][A] host blocks)
+        for (int q = 0; q < NQ; ++q) {
+            const float *T0 = &pl->h_taps[(((size_t)ga * P + qp[q][0]) * K * K) * 2];
+            const float *T1 = &pl->h_taps[(((size_t)ga * P + qp[q][1]) * K * K) * 2];
+            double2 *Xa = &X[((size_t)ga * NQ + q) * U];
+            for (int dy = 0; dy < K; ++dy)
+                for (int dx = 0; dx < K; ++dx) {
+                    const double ar = T0[(dy * K + dx) * 2], ai = T0[(dy * K + dx) * 2 + 1];
+                    if (ar == 0.0 && ai == 0.0) continue;
+                    for (int ey = 0; ey < K; ++ey)
+                        for (int ex = 0; ex < K; ++ex) {
+                            const double br = T1[(ey * K + ex) * 2], bi = -T1[(ey * K + ex) * 2 + 1];
+                            double2 &x = Xa[(dy - ey + K - 1) * L + (dx - ex + K - 1)];
+                            x.x += ar * br - ai * bi;
+                            x.y += ar * bi + ai * br;
+                        }
+                }
+        }
+    double2 *d = nullptr;
+    moff_status s = palloc(pl, &d, X.size() * 16);
+    if (s != MOFF_OK) return s;
+    if (cudaMemcpy(d, X.data(), X.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
+        pfree(pl, d);
+        return fail(MOFF_ECUDA, "upload of the autocorrelation patches failed");
+    }
+    pfree(pl, pl->d_auto_X);
+    pl->d_auto_X = d;
     return MOFF_OK;
 }
 
@@ -1650,6 +1817,47 @@ moff_status moff_set_gains(moff_plan *pl, const float *gains, int on_device) {
     return MOFF_OK;
 }
 
+moff_status moff_set_channel_groups(moff_plan *pl, int n_groups, const double *pos, const float *taps,
+                                   const int *chan_group) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (pl->tc) return fail(MOFF_EINVAL, "channel-dependent positions and kernels run on the FP32 path (not MOFF_PREC_FP16TC)");
+    if (n_groups < 1 || n_groups > pl->C) return fail(MOFF_EINVAL, "n_groups (%d) must be in [1, C = %d]", n_groups, pl->C);
+    if (!pos || !taps) return fail(MOFF_EINVAL, "pos and taps must not be NULL");
+    if (n_groups > 1 && !chan_group) return fail(MOFF_EINVAL, "chan_group must not be NULL with more than one set");
+    if (chan_group)
+        for (int c = 0; c < pl->C; ++c)
+            if (chan_group[c] < 0 || chan_group[c] >= n_groups)
+                return fail(MOFF_EINVAL, "chan_group[%d] = %d outside [0, %d)", c, chan_group[c], n_groups);
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    const GridChoice cur{pl->tb, pl->staged, pl->pairs, pl->wide};
+    Bins b;
+    if ((s = build_bin_sets(pl, n_groups, pos, taps, &cur, &b)) != MOFF_OK) return s;
+    int *d_grp = nullptr;
+    if (n_groups > 1) {
+        if ((s = palloc(pl, &d_grp, (size_t)pl->C * 4)) != MOFF_OK) return s;
+        if (cudaMemcpy(d_grp, chan_group, (size_t)pl->C * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            pfree(pl, d_grp);
+            return fail(MOFF_ECUDA, "upload of the channel sets failed");
+        }
+    }
+    if ((s = upload_bins(pl, b)) != MOFF_OK) {
+        pfree(pl, d_grp);
+        return s;
+    }
+    pfree(pl, pl->d_chan_group);
+    pl->d_chan_group = d_grp;
+    pl->n_groups = n_groups;
+    if (!pl->jones) {
+        pl->h_pos.assign(pos, pos + (size_t)n_groups * pl->A * 2);
+        pl->h_taps.assign(taps, taps + (size_t)n_groups * pl->A * pl->P * pl->K * pl->K * 2);
+    }
+    drop_graphs(pl);   // captured launches hold the old bins
+    if (pl->fb_on && (s = upload_fb_beams(pl, pl->fb_kx, pl->fb_ky)) != MOFF_OK) return s;
+    if (pl->auto_on && (s = upload_auto_patches(pl)) != MOFF_OK) return s;
+    return MOFF_OK;
+}
+
 moff_status moff_set_fstage(moff_plan *pl, int n_taps, const float *coeffs, float scale) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
@@ -1910,39 +2118,17 @@ moff_status moff_set_autocorr(moff_plan *pl, int on) {
     const int A = pl->A, P = pl->P, K = pl->K, N = pl->N, L = 2 * K - 1, U = L * L, NQ = P == 1 ? 1 : 3;
     if (!pl->d_auto_pw) {
         if ((s = palloc(pl, &pl->d_auto_pw, (size_t)pl->C * A * 3 * 16)) != MOFF_OK) return s;
-        if ((s = palloc(pl, &pl->d_auto_X, (size_t)A * NQ * U * 16)) != MOFF_OK) return s;
         if ((s = palloc(pl, &pl->d_auto_Q, (size_t)pl->C * NQ * U * 16)) != MOFF_OK) return s;
         if ((s = palloc(pl, &pl->d_auto_img, (size_t)pl->C * pl->nprod * N * N * 8)) != MOFF_OK) return s;
         if ((s = palloc(pl, &pl->d_wN, (size_t)N * 16)) != MOFF_OK) return s;
     }
-    // X_a,q(u) = sum_{d - d' = u} T_a,p[d] conj(T_a,p'[d']),  q = (p, p') in {(x,x), (y,y), (x,y)}
-    std::vector<double2> X((size_t)A * NQ * U, make_double2(0.0, 0.0));
-    const int qp[3][2] = {{0, 0}, {1, 1}, {0, 1}};
-    for (int a = 0; a < A; ++a)
-        for (int q = 0; q < NQ; ++q) {
-            const float *T0 = &pl->h_taps[(((size_t)a * P + qp[q][0]) * K * K) * 2];
-            const float *T1 = &pl->h_taps[(((size_t)a * P + qp[q][1]) * K * K) * 2];
-            double2 *Xa = &X[((size_t)a * NQ + q) * U];
-            for (int dy = 0; dy < K; ++dy)
-                for (int dx = 0; dx < K; ++dx) {
-                    const double ar = T0[(dy * K + dx) * 2], ai = T0[(dy * K + dx) * 2 + 1];
-                    if (ar == 0.0 && ai == 0.0) continue;
-                    for (int ey = 0; ey < K; ++ey)
-                        for (int ex = 0; ex < K; ++ex) {
-                            const double br = T1[(ey * K + ex) * 2], bi = -T1[(ey * K + ex) * 2 + 1];
-                            double2 &x = Xa[(dy - ey + K - 1) * L + (dx - ex + K - 1)];
-                            x.x += ar * br - ai * bi;
-                            x.y += ar * bi + ai * br;
-                        }
-                }
-        }
+    if ((s = upload_auto_patches(pl)) != MOFF_OK) return s;
     std::vector<double2> w(N);
     for (int m = 0; m < N; ++m) {
         double c, sn;
         root_unity(m, N, &c, &sn);
         w[m] = make_double2(c, sn);
     }
-    MOFF_CK(cudaMemcpy(pl->d_auto_X, X.data(), X.size() * 16, cudaMemcpyHostToDevice));
     MOFF_CK(cudaMemcpy(pl->d_wN, w.data(), w.size() * 16, cudaMemcpyHostToDevice));
     MOFF_CK(cudaMemsetAsync(pl->d_auto_pw, 0, (size_t)pl->C * A * 3 * 16, pl->st));
     pl->auto_on = true;
@@ -1962,7 +2148,7 @@ moff_status moff_read_image_cross(moff_plan *pl, float *out, long long *n_sample
     if ((s = sync_plan(pl, timeout_ms)) != MOFF_OK) return s;
     if ((s = check_device_err(pl)) != MOFF_OK) return s;
     const long long n = (long long)pl->C * pl->nprod * pl->N * pl->N;
-    MOFF_CK(launch_auto_image(pl->d_auto_pw, pl->d_auto_X, pl->C, pl->A, pl->P, pl->K, pl->N, pl->d_wN, pl->d_auto_Q,
+    MOFF_CK(launch_auto_image(pl->d_auto_pw, pl->d_auto_X, pl->d_chan_group, pl->C, pl->A, pl->P, pl->K, pl->N, pl->d_wN, pl->d_auto_Q,
                               pl->d_auto_img, pl->st));
     MOFF_CK(launch_sub_to_f32(pl->d_acc, pl->d_auto_img, out_on_device ? out : pl->d_img, n, pl->st));
     if (!out_on_device) MOFF_CK(cudaMemcpyAsync(out, pl->d_img, (size_t)n * 4, cudaMemcpyDeviceToHost, pl->st));
@@ -2031,35 +2217,15 @@ moff_status moff_set_calibrator(moff_plan *pl, int kx, int ky) {
     if (kx < 0 || kx >= pl->N || ky < 0 || ky >= pl->N)
         return fail(MOFF_EINVAL, "calibrator pixel (%d, %d) outside the %d x %d image", kx, ky, pl->N, pl->N);
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
-    const int A = pl->A, P = pl->P, K = pl->K, N = pl->N, h = K / 2;
-    const size_t AP = (size_t)A * P;
+    const int P = pl->P;
+    const size_t AP = (size_t)pl->A * P;
     if (!pl->d_etap) {
         if ((s = palloc(pl, &pl->d_etap, (size_t)pl->Tb * pl->Cb * P * 8)) != MOFF_OK) return s;
         if ((s = palloc(pl, &pl->d_fb_corr, (size_t)pl->C * AP * 16)) != MOFF_OK) return s;
         if ((s = palloc(pl, &pl->d_fb_power, (size_t)pl->C * P * 8)) != MOFF_OK) return s;
-        if ((s = palloc(pl, &pl->d_fb_beam, AP * 16)) != MOFF_OK) return s;
         if ((s = palloc(pl, &pl->d_fb_out, (size_t)pl->C * AP * 8)) != MOFF_OK) return s;
     }
-    // B_a,p = sum_{dy,dx} taps[a][p][dy][dx] exp(+2 pi i (ky (ay + dy - h) + kx (ax + dx - h)) / N), FP64
-    std::vector<double2> beam(AP);
-    for (int a = 0; a < A; ++a) {
-        const long long fx = (long long)std::floor(pl->h_pos[2 * a] + 0.5), fy = (long long)std::floor(pl->h_pos[2 * a + 1] + 0.5);
-        const long long ax = ((fx % N) + N) % N, ay = ((fy % N) + N) % N;
-        for (int p = 0; p < P; ++p) {
-            double br = 0.0, bi = 0.0;
-            for (int dy = 0; dy < K; ++dy)
-                for (int dx = 0; dx < K; ++dx) {
-                    const float *t = &pl->h_taps[((((size_t)a * P + p) * K + dy) * K + dx) * 2];
-                    const long long m = ((long long)ky * (ay + dy - h) + (long long)kx * (ax + dx - h)) % N;
-                    double c, sn;
-                    root_unity(m < 0 ? m + N : m, N, &c, &sn);
-                    br += (double)t[0] * c - (double)t[1] * sn;
-                    bi += (double)t[0] * sn + (double)t[1] * c;
-                }
-            beam[(size_t)a * P + p] = make_double2(br, bi);
-        }
-    }
-    MOFF_CK(cudaMemcpy(pl->d_fb_beam, beam.data(), AP * 16, cudaMemcpyHostToDevice));
+    if ((s = upload_fb_beams(pl, kx, ky)) != MOFF_OK) return s;
     MOFF_CK(cudaMemsetAsync(pl->d_fb_corr, 0, (size_t)pl->C * AP * 16, pl->st));
     MOFF_CK(cudaMemsetAsync(pl->d_fb_power, 0, (size_t)pl->C * P * 8, pl->st));
     pl->fb_kx = kx;
@@ -2079,7 +2245,7 @@ moff_status moff_read_feedback(moff_plan *pl, float *corr, double *power, long l
     if ((s = check_device_err(pl)) != MOFF_OK) return s;
     const size_t n = (size_t)pl->C * pl->A * pl->P;
     if (corr) {
-        MOFF_CK(launch_fb_finish(pl->d_fb_corr, pl->d_fb_power, pl->d_fb_beam, pl->d_gains, pl->C, pl->A * pl->P, pl->P,
+        MOFF_CK(launch_fb_finish(pl->d_fb_corr, pl->d_fb_power, pl->d_fb_beam, pl->d_chan_group, pl->d_gains, pl->C, pl->A * pl->P, pl->P,
                                  pl->A, pl->d_fb_out, nullptr, 0, pl->st));
         MOFF_CK(cudaMemcpyAsync(corr, pl->d_fb_out, n * 8, cudaMemcpyDeviceToHost, pl->st));
     }
@@ -2100,7 +2266,7 @@ moff_status moff_feedback_gains(moff_plan *pl, float *delta, int apply) {
     if (!pl->fb_on) return fail(MOFF_ESTATE, "no calibrator set (moff_set_calibrator)");
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
     const size_t n = (size_t)pl->C * pl->A * pl->P;
-    MOFF_CK(launch_fb_finish(pl->d_fb_corr, pl->d_fb_power, pl->d_fb_beam, pl->d_gains, pl->C, pl->A * pl->P, pl->P,
+    MOFF_CK(launch_fb_finish(pl->d_fb_corr, pl->d_fb_power, pl->d_fb_beam, pl->d_chan_group, pl->d_gains, pl->C, pl->A * pl->P, pl->P,
                              pl->A, nullptr, pl->d_fb_out, apply ? 1 : 0, pl->st));
     if (apply && pl->tc) MOFF_CK(launch_gain_scale(pl->d_gains, pl->C, pl->A * pl->P, pl->d_sy, pl->st));
     if (delta) MOFF_CK(cudaMemcpyAsync(delta, pl->d_fb_out, n * 8, cudaMemcpyDeviceToHost, pl->st));

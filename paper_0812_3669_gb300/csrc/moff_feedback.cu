@@ -59,12 +59,13 @@ __global__ void __launch_bounds__(256) k_fb_corr(const FbArgs a) {
 // R = conj(B) * sums (FP64), written as float2; and, if delta is set, the
 // gain-error estimate g (1 - N conj(R) / S) (added to the gains if apply).
 __global__ void k_fb_finish(const double2 *__restrict__ corr, const double *__restrict__ power,
-                            const double2 *__restrict__ beam, float2 *gains, int C, int AP, int P, int n_ant,
-                            float2 *__restrict__ r_out, float2 *__restrict__ delta, int apply) {
+                            const double2 *__restrict__ beam, const int *__restrict__ chan_group, float2 *gains,
+                            int C, int AP, int P, int n_ant, float2 *__restrict__ r_out, float2 *__restrict__ delta,
+                            int apply) {
     const long long n = (long long)C * AP;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(k % AP), c = (int)(k / AP), p = i % P;
-        const double2 s = corr[k], b = beam[i];
+        const double2 s = corr[k], b = beam[(chan_group ? (long long)chan_group[c] * AP : 0) + i];
         const double rr = b.x * s.x + b.y * s.y, ri = b.x * s.y - b.y * s.x;   // conj(b) s
         if (r_out) r_out[k] = make_float2((float)rr, (float)ri);
         if (delta) {
@@ -114,9 +115,11 @@ __global__ void __launch_bounds__(256) k_auto_acc(const FbArgs a) {
 
 // Q[c][q][u] = sum_a pw[c][a][q] X[a][q][u]: the antennas' kernel cross-correlation
 // patches weighted by their autocorrelation sums (FP64).  One thread per (q, u) of a channel.
-__global__ void k_auto_patch(const double2 *__restrict__ pw, const double2 *__restrict__ X, int A, int NQ, int U,
-                             double2 *__restrict__ Q) {
+// With channel-dependent kernels, X holds one [A][NQ][U] block per set and chan_group[c] picks it.
+__global__ void k_auto_patch(const double2 *__restrict__ pw, const double2 *__restrict__ X,
+                             const int *__restrict__ chan_group, int A, int NQ, int U, double2 *__restrict__ Q) {
     const int c = blockIdx.y;
+    if (chan_group) X += (long long)chan_group[c] * A * NQ * U;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;    // q * U + u
     if (k >= NQ * U) return;
     const int q = k / U;
@@ -191,10 +194,10 @@ cudaError_t launch_auto_acc(const FbArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_auto_image(const double2 *pw, const double2 *X, int C, int A, int P, int K, int N,
-                              const double2 *wN, double2 *Q, double *img, cudaStream_t st) {
+cudaError_t launch_auto_image(const double2 *pw, const double2 *X, const int *chan_group, int C, int A, int P, int K,
+                              int N, const double2 *wN, double2 *Q, double *img, cudaStream_t st) {
     const int NQ = P == 1 ? 1 : 3, L = 2 * K - 1, U = L * L;
-    k_auto_patch<<<dim3((NQ * U + 255) / 256, C), 256, 0, st>>>(pw, X, A, NQ, U, Q);
+    k_auto_patch<<<dim3((NQ * U + 255) / 256, C), 256, 0, st>>>(pw, X, chan_group, A, NQ, U, Q);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = ((size_t)N + U + (size_t)L * 64) * sizeof(double2);
@@ -215,11 +218,12 @@ cudaError_t launch_fb_corr(const FbArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fb_finish(const double2 *corr, const double *power, const double2 *beam, float2 *gains, int C,
-                             int AP, int P, int n_ant, float2 *r_out, float2 *delta, int apply, cudaStream_t st) {
+cudaError_t launch_fb_finish(const double2 *corr, const double *power, const double2 *beam, const int *chan_group,
+                             float2 *gains, int C, int AP, int P, int n_ant, float2 *r_out, float2 *delta, int apply,
+                             cudaStream_t st) {
     const long long n = (long long)C * AP;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
-    k_fb_finish<<<blocks, 256, 0, st>>>(corr, power, beam, gains, C, AP, P, n_ant, r_out, delta, apply);
+    k_fb_finish<<<blocks, 256, 0, st>>>(corr, power, beam, chan_group, gains, C, AP, P, n_ant, r_out, delta, apply);
     return cudaGetLastError();
 }
 

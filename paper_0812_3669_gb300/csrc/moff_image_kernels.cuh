@@ -84,12 +84,15 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     const int c = a.c0 + cl;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int ant0 = a.st_ant_off[s];
-    const int nloc = a.st_ant_off[s + 1] - ant0;
-    const int nyi = nloc * P;
     const int nsl = a.n_slices;
-    const long long *soff = a.slice_off + (long long)s * nsl;
-    const uint16_t *lcell = a.lane_cell + (long long)s * nsl * 32;
+    const int grp = a.chan_group ? a.chan_group[c] : 0;      // this channel's set of positions and kernels
+    const long long gs = (long long)grp * gridDim.x + s;     // stripe s of that set
+    const int *sao = a.st_ant_off + grp + gs;                // set g's offsets start at g (n_stripes + 1)
+    const int ant0 = sao[0];
+    const int nloc = sao[1] - ant0;
+    const int nyi = nloc * P;
+    const long long *soff = a.slice_off + grp + gs * nsl;
+    const uint16_t *lcell = a.lane_cell + gs * nsl * 32;
     const long long e0 = soff[0];
 
     if (nloc == 0) {   // no kernel reaches these rows: their field (and its transform) is zero

@@ -45,6 +45,11 @@ struct GridArgs {
     long long slab_t, slab_c;
     int pairs;                // 1: each lane sums two horizontally adjacent cells (entries carry two taps)
     int wide;                 // 1: twice grid_fft_rows(N) rows per pass
+    // Channel-dependent positions and kernels: chan_group[c] (absolute channel) picks one of
+    // several sets; set g's stripe arrays start at st_ant_off + g (n_stripes + 1), slice_off +
+    // g (n_stripes n_slices + 1) and lane_cell + g n_stripes n_slices 32, and their values
+    // already index the shared st_ant / con_tap / con_y.  nullptr: one set.
+    const int *chan_group;
 };
 
 // Column transform + square-and-integrate (Eq. m6 steps 3-4, second axis).
@@ -102,12 +107,15 @@ cudaError_t launch_fb_corr(const FbArgs &a, cudaStream_t st);
 // (FbArgs: corr = [C][A][3] double2 sums; etap and power unused).
 cudaError_t launch_auto_acc(const FbArgs &a, cudaStream_t st);
 // The autocorrelation image of every channel and product from the sums and the
-// kernels' cross-correlation patches X [A][NQ][(2K-1)^2] (FP64), into img [C][n_prod][N][N].
-cudaError_t launch_auto_image(const double2 *pw, const double2 *X, int C, int A, int P, int K, int N,
-                              const double2 *wN, double2 *Q, double *img, cudaStream_t st);
+// kernels' cross-correlation patches X [A][NQ][(2K-1)^2] (FP64; one such block per set of
+// kernels, chosen by chan_group[c] when it is not nullptr), into img [C][n_prod][N][N].
+cudaError_t launch_auto_image(const double2 *pw, const double2 *X, const int *chan_group, int C, int A, int P, int K,
+                              int N, const double2 *wN, double2 *Q, double *img, cudaStream_t st);
 cudaError_t launch_sub_to_f32(const double *acc, const double *sub, float *out, long long n, cudaStream_t st);
-cudaError_t launch_fb_finish(const double2 *corr, const double *power, const double2 *beam, float2 *gains, int C,
-                             int AP, int P, int n_ant, float2 *r_out, float2 *delta, int apply, cudaStream_t st);
+// beam: [A*P] antenna beams towards the calibrator, or [sets][A*P] picked by chan_group[c].
+cudaError_t launch_fb_finish(const double2 *corr, const double *power, const double2 *beam, const int *chan_group,
+                             float2 *gains, int C, int AP, int P, int n_ant, float2 *r_out, float2 *delta, int apply,
+                             cudaStream_t st);
 
 // Polyphase F-stage (Eq. FFTofE).
 struct PfbArgs {
