@@ -388,9 +388,9 @@ def batching_leg(args, moff, synth, torch):
             "plain_one_channel": {"value": v_plain, "chan_chunk": pinfo["chan_chunk"],
                                   "time_chunk": pinfo["time_chunk"]},
             "batched_rule_direct": {"value": v_direct, "time_batch": rule["time_batch"], "staged": rule["staged"],
-                                    "cell_pairs": rule["cell_pairs"]},
+                                    "cells_per_lane": rule["cells_per_lane"]},
             "batched_autotuned_graph": {"value": v_batched, "time_batch": tuned["time_batch"], "staged": tuned["staged"],
-                                        "cell_pairs": tuned["cell_pairs"],
+                                        "cells_per_lane": tuned["cells_per_lane"], "wide_rows": tuned["wide_rows"],
                                         "tune_source": tuned["source"], "plan_create_s": tune_s,
                                         "chan_chunk": binfo["chan_chunk"], "time_chunk": binfo["time_chunk"],
                                         "graph_launches_per_block": 1},

@@ -306,15 +306,15 @@ moff_status moff_read_beams(moff_plan *plan, float *out, int *n_time, int timeou
 /*
  * moff_plan_tuning -- how the gridding kernel's shape was chosen (any pointer
  * may be NULL): time_batch = samples gridded and row-transformed per pass (1, 2,
- * 4 or 8), staged = 1 if kernel entries are staged in shared memory, cell_pairs
- * = 1 if each lane sums two adjacent grid cells (one voltage read feeds both),
- * source = 0 built-in rule, 1 measured by MOFF_AUTOTUNE at creation, 2 taken
+ * 4 or 8), staged = 1 if kernel entries are staged in shared memory,
+ * cells_per_lane = grid cells each lane sums (1; 2 adjacent cells of a row; 4 = a
+ * 2 x 2 block), so that one voltage read feeds all of them, source = 0 built-in rule, 1 measured by MOFF_AUTOTUNE at creation, 2 taken
  * from the tuning cache; best_ms = the measured time of the chosen shape (source
  * 1); wide_rows = 1 if twice the usual number of grid rows is transformed per
  * pass (more gather work between barriers).
  */
-moff_status moff_plan_tuning(const moff_plan *plan, int *time_batch, int *staged, int *cell_pairs, int *source,
-                             double *best_ms, int *wide_rows);
+moff_status moff_plan_tuning(const moff_plan *plan, int *time_batch, int *staged, int *cells_per_lane,
+                             int *source, double *best_ms, int *wide_rows);
 
 /*
  * moff_set_timing -- when on (1), every kernel the plan launches is bracketed

@@ -257,7 +257,8 @@ def moff_plan_tuning(plan):
     d = ctypes.c_double()
     _check(lib().moff_plan_tuning(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(p), ctypes.byref(c),
                                   ctypes.byref(d), ctypes.byref(w)))
-    return dict(time_batch=a.value, staged=b.value, cell_pairs=p.value, source=c.value, best_ms=d.value,
+    return dict(time_batch=a.value, staged=b.value, cells_per_lane=p.value, cell_pairs=int(p.value == 2),
+                source=c.value, best_ms=d.value,
                 wide_rows=w.value)
 
 

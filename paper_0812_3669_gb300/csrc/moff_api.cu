@@ -207,7 +207,7 @@ struct moff_plan {
 
     // binning
     int rows = 0, n_stripes = 0, max_nloc = 0, n_slices = 0, tb = 1, max_entries = 0;
-    bool staged = false, pairs = false, wide = false;
+    bool staged = false, pairs = false, wide = false, quads = false;
     size_t grid_smem = 0;
     int *d_st_ant_off = nullptr, *d_st_ant = nullptr;
     long long *d_slice_off = nullptr;
@@ -486,6 +486,7 @@ GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, 
     g.slab_t = 1;
     g.slab_c = pl->Tb;
     g.pairs = pl->pairs ? 1 : 0;
+    g.quads = pl->quads ? 1 : 0;
     g.wide = pl->wide ? 1 : 0;
     g.chan_group = pl->d_chan_group;
     return g;
@@ -763,7 +764,10 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     // kernel entries staged in shared memory, then more samples per pass.
     // The built-in rule takes cell pairs unless MOFF_GRID_PAIRS=0.
     const char *pairs_env = getenv("MOFF_GRID_PAIRS");
-    const bool pairs = force ? force->pairs : !(pairs_env && atoi(pairs_env) == 0);
+    const char *quads_env = getenv("MOFF_GRID_QUADS");
+    // 2 x 2 cell blocks per lane (entries through L2, even stripe height); else pairs or single cells
+    const bool quads = force ? force->quads : (quads_env && atoi(quads_env) != 0);
+    const bool pairs = !quads && (force ? force->pairs : !(pairs_env && atoi(pairs_env) == 0));
     struct Cand { int tb, rows, nloc; long long entries; size_t sm_staged, sm_plain; };
     std::vector<Cand> cands;
     for (int tb = 8; tb >= 1; tb /= 2) {
@@ -808,19 +812,22 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     if (force) {
         for (const Cand &cd : cands)
             if (cd.tb == force->tb) {
-                const bool fits = (force->staged ? cd.sm_staged : cd.sm_plain) <= big;
+                const bool fits = (force->staged ? cd.sm_staged : cd.sm_plain) <= big &&
+                                  !(quads && (force->staged || cd.rows % 2));
                 if (fits) { pick = &cd; staged = force->staged; }
                 break;
             }
-        if (!pick) return fail(MOFF_EINVAL, "gridding shape tb=%d staged=%d does not fit", force->tb, (int)force->staged);
+        if (!pick)
+            return fail(MOFF_EINVAL, "gridding shape tb=%d staged=%d quads=%d does not fit", force->tb,
+                        (int)force->staged, (int)quads);
     }
     // Pair lanes relieve the voltage reads, so the rule then prefers 4 samples per
     // pass (fewer registers per lane) before 8; single-cell lanes prefer 8.
     std::vector<const Cand *> pref;
-    for (int want : pairs ? std::vector<int>{4, 8, 2, 1} : std::vector<int>{8, 4, 2, 1})
+    for (int want : pairs || quads ? std::vector<int>{4, 8, 2, 1} : std::vector<int>{8, 4, 2, 1})
         for (const Cand &cd : cands)
-            if (cd.tb == want) pref.push_back(&cd);
-    if (!pick && prefer_staged)
+            if (cd.tb == want && !(quads && cd.rows % 2)) pref.push_back(&cd);
+    if (!pick && prefer_staged && !quads)
         for (const Cand *cd : pref)
             if (cd->sm_staged <= budget) { pick = cd; staged = true; break; }
     if (!pick)
@@ -839,6 +846,7 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     b->max_nloc = pick->nloc;
     b->staged = staged;
     b->pairs = pairs;
+    b->quads = quads;
     b->wide = wide;
     b->max_entries = staged ? (int)pick->entries : 0;
     b->grid_smem = staged ? pick->sm_staged : pick->sm_plain;
@@ -847,7 +855,8 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     // antenna-major within a cell.
     const int rows = b->rows, ns = b->n_stripes;
     const int ncell = P * rows * N;                 // a multiple of 32 (N >= 32)
-    const int nunit = pairs ? ncell / 2 : ncell;    // lanes: cells, or pairs (x even, x + 1)
+    const int cpl = quads ? 4 : (pairs ? 2 : 1);    // cells per lane
+    const int nunit = ncell / cpl;                  // lanes: cells, pairs (x even, x + 1) or 2 x 2 blocks
     if (nunit % 32) return fail(MOFF_EINVAL, "internal: %d gridding lanes per stripe is not a multiple of 32", nunit);
     const int nsl = nunit / 32;
     b->n_slices = nsl;
@@ -882,11 +891,25 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     b->con_tap.clear();
     b->con_y.clear();
     long long base = 0;
-    // Per unit (cell, or pair of cells) its entry list: (voltage index, tap of the
-    // first cell, tap of the second).  A cell's contributions keep their order
-    // (ascending voltage index = antenna-major), so a pair lane sums each of its
-    // cells in exactly the order a single-cell lane would (plus exact zero terms).
-    struct Ent { int y; float2 t0, t1; };
+    // Per unit (cell, pair of cells or 2 x 2 block) its entry list: (voltage index,
+    // tap of each of the unit's cells).  A cell's contributions keep their order
+    // (ascending voltage index = antenna-major), so a pair or block lane sums each
+    // of its cells in exactly the order a single-cell lane would (plus exact zero terms).
+    // Unit of cell (row f, column x): a pair is (f, x / 2), a block (f / 2, x / 2); the
+    // cell's slot in the unit is x & 1 (+ 2 (f & 1) in a block).
+    struct Ent { int y; float2 t[4]; };
+    auto unit_of = [&](int cell, int *slot) {
+        if (cpl == 1) { *slot = 0; return cell; }
+        if (cpl == 2) { *slot = cell & 1; return cell / 2; }
+        const int f = cell / N, x = cell % N;
+        *slot = (x & 1) + 2 * (f & 1);
+        return (f / 2) * (N / 2) + x / 2;
+    };
+    auto first_cell = [&](int u) {
+        if (cpl == 1) return u;
+        if (cpl == 2) return 2 * u;
+        return 2 * (u / (N / 2)) * N + 2 * (u % (N / 2));
+    };
     std::vector<std::vector<Ent>> lists(nunit);
     std::vector<int> order(nunit);
     const float2 zero = make_float2(0.f, 0.f);
@@ -901,12 +924,12 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
             const int cell = v[i].cell;
             size_t j = i;
             while (j < v.size() && v[j].cell == cell) ++j;
-            if (!pairs) {
-                for (size_t q = i; q < j; ++q) lists[cell].push_back(Ent{v[q].y, v[q].tap, zero});
+            int slot = 0;
+            auto &L = lists[unit_of(cell, &slot)];
+            if (cpl == 1) {
+                for (size_t q = i; q < j; ++q) lists[cell].push_back(Ent{v[q].y, {v[q].tap, zero, zero, zero}});
             } else {
-                // merge into the pair's list, sorted by voltage index
-                auto &L = lists[cell / 2];
-                const bool second = (cell & 1) != 0;
+                // merge into the unit's list, sorted by voltage index
                 std::vector<Ent> merged;
                 merged.reserve(L.size() + (j - i));
                 size_t a = 0, q = i;
@@ -915,11 +938,11 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
                         merged.push_back(L[a++]);
                     } else if (a < L.size() && L[a].y == v[q].y) {
                         Ent e = L[a++];
-                        (second ? e.t1 : e.t0) = v[q++].tap;
+                        e.t[slot] = v[q++].tap;
                         merged.push_back(e);
                     } else {
-                        Ent e{v[q].y, zero, zero};
-                        (second ? e.t1 : e.t0) = v[q++].tap;
+                        Ent e{v[q].y, {zero, zero, zero, zero}};
+                        e.t[slot] = v[q++].tap;
                         merged.push_back(e);
                     }
                 }
@@ -939,13 +962,12 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
             for (size_t e = 0; e < len; ++e)
                 for (int l = 0; l < 32; ++l) {
                     const auto &L = lists[order[k * 32 + l]];
-                    const Ent en = e < L.size() ? L[e] : Ent{0, zero, zero};
-                    b->con_tap.push_back(en.t0);
-                    if (pairs) b->con_tap.push_back(en.t1);
+                    const Ent en = e < L.size() ? L[e] : Ent{0, {zero, zero, zero, zero}};
+                    for (int c2 = 0; c2 < cpl; ++c2) b->con_tap.push_back(en.t[c2]);
                     b->con_y.push_back((uint16_t)en.y);
                 }
             for (int l = 0; l < 32; ++l)
-                b->lane_cell[si * 32 + l] = (uint16_t)(pairs ? 2 * order[k * 32 + l] : order[k * 32 + l]);
+                b->lane_cell[si * 32 + l] = (uint16_t)first_cell(order[k * 32 + l]);
             base += (long long)len * 32;
         }
     }
@@ -1105,7 +1127,7 @@ moff_status build_bin_sets(const moff_plan *pl, int n_sets, const double *pos, c
     std::vector<GridChoice> cands;
     if (force) cands.push_back(*force);
     for (bool pr : {pl->pairs, !pl->pairs})
-        for (int tb : {4, 8, 2, 1}) cands.push_back(GridChoice{tb, false, pr, false});
+        for (int tb : {4, 8, 2, 1}) cands.push_back(GridChoice{tb, false, pr, false, false});
     const int nthr = (int)std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 32u));
     std::vector<Bins> bins(n_sets);
     std::vector<moff_status> st(n_sets);
@@ -1133,7 +1155,7 @@ moff_status build_bin_sets(const moff_plan *pl, int n_sets, const double *pos, c
         o = Bins{};
         const Bins &b0 = bins[0];
         o.rows = b0.rows; o.tb = b0.tb; o.n_stripes = b0.n_stripes; o.n_slices = b0.n_slices;
-        o.staged = b0.staged; o.pairs = b0.pairs; o.wide = b0.wide;
+        o.staged = b0.staged; o.pairs = b0.pairs; o.wide = b0.wide; o.quads = b0.quads;
         for (const Bins &b : bins) {
             if (b.n_slices != b0.n_slices || b.n_stripes != b0.n_stripes)
                 return fail(MOFF_EINVAL, "internal: sets binned to different stripe shapes");
@@ -1143,7 +1165,7 @@ moff_status build_bin_sets(const moff_plan *pl, int n_sets, const double *pos, c
         o.grid_smem = grid_smem_bytes(N, P, o.tb, o.rows, o.max_nloc, fft_tw_total(N), o.staged ? o.max_entries : 0,
                                       o.pairs);
         if (o.grid_smem > 225 * 1024) continue;
-        const size_t tpe = o.pairs ? 2 : 1;
+        const size_t tpe = o.quads ? 4 : (o.pairs ? 2 : 1);
         long long ebase = 0;
         int abase = 0;
         for (const Bins &b : bins) {
@@ -1197,6 +1219,7 @@ moff_status upload_bins(moff_plan *pl, const Bins &b) {
     pl->tb = b.tb;
     pl->staged = b.staged;
     pl->pairs = b.pairs;
+    pl->quads = b.quads;
     pl->wide = b.wide;
     pl->max_entries = b.max_entries;
     pl->n_stripes = b.n_stripes;
@@ -1360,7 +1383,7 @@ std::string tune_key(const moff_plan *pl, const double *pos, const float *taps) 
     cudaGetDeviceProperties(&prop, pl->device);
     h = fnv1a(prop.name, strlen(prop.name), h);
     char buf[128];
-    snprintf(buf, sizeof buf, "grid4-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P,
+    snprintf(buf, sizeof buf, "grid5-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P,
              (int)pl->jones, pl->Tb, std::min(pl->Cb, pl->C), prop.multiProcessorCount, (unsigned long long)h);
     return buf;
 }
@@ -1373,9 +1396,9 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
         if (!g_tune_loaded && path) {
             if (FILE *f = fopen(path, "r")) {
                 char k[256];
-                int tb = 0, st = 0, pr = 0, wd = 0;
-                while (fscanf(f, "%255s %d %d %d %d", k, &tb, &st, &pr, &wd) == 5)
-                    g_tune_cache[k] = GridChoice{tb, st != 0, pr != 0, wd != 0};
+                int tb = 0, st = 0, pr = 0, wd = 0, qd = 0;
+                while (fscanf(f, "%255s %d %d %d %d %d", k, &tb, &st, &pr, &wd, &qd) == 6)
+                    g_tune_cache[k] = GridChoice{tb, st != 0, pr != 0, wd != 0, qd != 0};
                 fclose(f);
             }
         }
@@ -1423,8 +1446,10 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     GridChoice best{};
     float best_ms = 0.f;
     for (int tb = 8; tb >= 1; tb /= 2)
-        for (int cand = 0; cand < 8; ++cand) {
-            const GridChoice ch{tb, (cand & 1) != 0, (cand & 2) != 0, (cand & 4) != 0};
+        for (int cand = 0; cand < 10; ++cand) {
+            // cand 0-7: staged x pairs x wide; 8, 9: 2 x 2 blocks (entries through L2), without and with wide
+            const GridChoice ch = cand < 8 ? GridChoice{tb, (cand & 1) != 0, (cand & 2) != 0, (cand & 4) != 0, false}
+                                           : GridChoice{tb, false, false, cand == 9, true};
             moff_plan tmp;
             tmp.A = A; tmp.K = pl->K; tmp.N = N; tmp.C = nc; tmp.P = P; tmp.jones = pl->jones;
             tmp.device = pl->device;
@@ -1456,8 +1481,8 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
                 return fail(MOFF_ECUDA, "autotuner launch failed");
             }
             if (getenv("MOFF_TUNE_VERBOSE"))
-                fprintf(stderr, "moff autotune: tb=%d staged=%d pairs=%d wide=%d  %.4f ms\n", ch.tb, (int)ch.staged,
-                        (int)ch.pairs, (int)ch.wide, ms);
+                fprintf(stderr, "moff autotune: tb=%d staged=%d pairs=%d wide=%d quads=%d  %.4f ms\n", ch.tb,
+                        (int)ch.staged, (int)ch.pairs, (int)ch.wide, (int)ch.quads, ms);
             if (best.tb == 0 || ms < best_ms) {
                 best = ch;
                 best_ms = ms;
@@ -1472,7 +1497,8 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     g_tune_cache[key] = best;
     if (path)
         if (FILE *f = fopen(path, "a")) {
-            fprintf(f, "%s %d %d %d %d\n", key.c_str(), best.tb, (int)best.staged, (int)best.pairs, (int)best.wide);
+            fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), best.tb, (int)best.staged, (int)best.pairs, (int)best.wide,
+                    (int)best.quads);
             fclose(f);
         }
     return MOFF_OK;
@@ -1830,7 +1856,7 @@ moff_status moff_set_channel_groups(moff_plan *pl, int n_groups, const double *p
             if (chan_group[c] < 0 || chan_group[c] >= n_groups)
                 return fail(MOFF_EINVAL, "chan_group[%d] = %d outside [0, %d)", c, chan_group[c], n_groups);
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
-    const GridChoice cur{pl->tb, pl->staged, pl->pairs, pl->wide};
+    const GridChoice cur{pl->tb, pl->staged, pl->pairs, pl->wide, pl->quads};
     Bins b;
     if ((s = build_bin_sets(pl, n_groups, pos, taps, &cur, &b)) != MOFF_OK) return s;
     int *d_grp = nullptr;
@@ -2273,13 +2299,13 @@ moff_status moff_feedback_gains(moff_plan *pl, float *delta, int apply) {
     return sync_plan(pl, -1);
 }
 
-moff_status moff_plan_tuning(const moff_plan *pl, int *time_batch, int *staged, int *cell_pairs, int *source,
+moff_status moff_plan_tuning(const moff_plan *pl, int *time_batch, int *staged, int *cells_per_lane, int *source,
                              double *best_ms, int *wide_rows) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
     if (time_batch) *time_batch = pl->tb;
     if (staged) *staged = pl->staged ? 1 : 0;
-    if (cell_pairs) *cell_pairs = pl->pairs ? 1 : 0;
+    if (cells_per_lane) *cells_per_lane = pl->quads ? 4 : (pl->pairs ? 2 : 1);
     if (source) *source = pl->tune_source;
     if (best_ms) *best_ms = pl->tune_best_ms;
     if (wide_rows) *wide_rows = pl->wide ? 1 : 0;

@@ -69,8 +69,11 @@ struct GridShape {
     static constexpr int F = TB * PR;
 };
 
-template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, bool PAIRS, bool WIDE>
+// CPL = grid cells per lane: 1, 2 (cells (f, e), (f, e + 1) of one row) or 4 (the 2 x 2
+// block (f, e), (f, e + 1), (f + 1, e), (f + 1, e + 1), f even); each entry carries CPL taps.
+template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE>
 __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
+    constexpr bool PAIRS = CPL >= 2;
     using FP = FftPlan<N>;
     using TW = FftTw<N>;
     using GS = GridShape<N, P, TB, WIDE>;
@@ -114,9 +117,9 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     float2 *s_alt = s_buf + F * LDR;                   // second buffer of the row passes
     float2 *s_y = s_alt + ((F * LDR + 1) & ~1);        // [nloc*P][YS]: TB samples, padded row (16-byte aligned)
     float2 *s_g = s_y + YS * a.max_nloc * P;
-    // staged kernel values (two per entry with PAIRS, read as 16-byte vectors: 16-byte aligned)
+    // staged kernel values (CPL per entry, read as 16-byte vectors when CPL >= 2: 16-byte aligned)
     float2 *s_tap = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(s_g + a.max_nloc * P) + 15) & ~uintptr_t(15));
-    constexpr int TPE = PAIRS ? 2 : 1;                 // taps per entry
+    constexpr int TPE = CPL;                           // taps per entry
     int *s_ant = reinterpret_cast<int *>(s_tap + (STAGED ? TPE * a.max_entries : 0));
     uint16_t *s_cy = reinterpret_cast<uint16_t *>(s_ant + a.max_nloc);   // staged voltage indices
 
@@ -180,8 +183,8 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
         __syncthreads();
         // Step 2: every cell sums its kernel contributions (fixed order), for TB
         // samples.  Entries are fetched U at a time so their latencies overlap.
-        // With PAIRS a lane owns cells (e, e + 1) of one row and each entry
-        // carries both cells' taps, so one read of a voltage row feeds two cells.
+        // With CPL = 2 a lane owns cells (e, e + 1) of one row, with CPL = 4 a 2 x 2 block;
+        // each entry carries every cell's tap, so one read of a voltage row feeds CPL cells.
         // Slices come longest first; warps take them in snake order (w, 2W-1-w, 2W+w, ...)
         // so that each warp's total stays close to the mean.
         constexpr int NW = kBlock / 32;
@@ -198,15 +201,24 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
             for (int c2 = 0; c2 < TPE; ++c2)
 #pragma unroll
                 for (int t = 0; t < TB; ++t) acc[c2][t] = make_float2(0.f, 0.f);
-            constexpr int U = PAIRS ? 2 : 4;
-            for (int i0 = 0; i0 < len; i0 += U) {
-                float2 tv[U][TPE];
-                int yv[U];
+            constexpr int U = CPL == 4 ? 2 : (PAIRS ? 2 : 4);
+            // Entries i0 .. i0 + U - 1 (zero past the slice): taps and voltage indices.
+            auto load_ent = [&](int i0, float2 (&tv)[U][TPE], int (&yv)[U]) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const bool ok = i0 + u < len;
                     const float2 *tq = tp + TPE * 32 * (i0 + u);
-                    if constexpr (PAIRS) {
+                    if constexpr (CPL == 4) {
+                        float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f), r4 = q4;
+                        if (ok) {
+                            q4 = __ldg(reinterpret_cast<const float4 *>(tq));
+                            r4 = __ldg(reinterpret_cast<const float4 *>(tq) + 1);
+                        }
+                        tv[u][0] = make_float2(q4.x, q4.y);
+                        tv[u][1] = make_float2(q4.z, q4.w);
+                        tv[u][2] = make_float2(r4.x, r4.y);
+                        tv[u][3] = make_float2(r4.z, r4.w);
+                    } else if constexpr (PAIRS) {
                         float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (ok) q4 = STAGED ? *reinterpret_cast<const float4 *>(tq) : __ldg(reinterpret_cast<const float4 *>(tq));
                         tv[u][0] = make_float2(q4.x, q4.y);
@@ -216,6 +228,16 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
                     }
                     yv[u] = ok ? (int)(STAGED ? yp[32 * (i0 + u)] : __ldg(yp + 32 * (i0 + u))) : 0;
                 }
+            };
+            // The next group's entries are loaded while this group is summed, so the
+            // L2 latency of the entries overlaps the arithmetic.
+            float2 tv[U][TPE];
+            int yv[U];
+            load_ent(0, tv, yv);
+            for (int i0 = 0; i0 < len; i0 += U) {
+                float2 tn[U][TPE];
+                int yn[U];
+                load_ent(i0 + U, tn, yn);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const float2 *yy = s_y + yv[u] * YS;
@@ -242,11 +264,17 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
                         }
                     }
                 }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    yv[u] = yn[u];
+#pragma unroll
+                    for (int c2 = 0; c2 < TPE; ++c2) tv[u][c2] = tn[u][c2];
+                }
             }
             const int f = cell / N, e = cell - f * N;
 #pragma unroll
             for (int c2 = 0; c2 < TPE; ++c2) {
-                float2 *dst = s_buf + f * LDR + pad16(e + c2);
+                float2 *dst = s_buf + (f + (c2 >> 1)) * LDR + pad16(e + (c2 & 1));
 #pragma unroll
                 for (int t = 0; t < TB; ++t) dst[t * PR * LDR] = acc[c2][t];
             }
@@ -484,44 +512,55 @@ size_t col_smem_bytes_t(int P, bool h16 = false) {
            (h16 ? (size_t)P * N * 4 : 0);
 }
 
-template <int N, int P, int TB, bool ST, bool GO, bool PR, bool WD>
+template <int N, int P, int TB, bool ST, bool GO, int CPL, bool WD>
 cudaError_t launch_grid_t(const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st) {
-    auto k = k_grid_rows<N, P, TB, ST, GO, PR, WD>;
+    // 2 x 2 blocks need an even stripe height and entries read through L2
+    if constexpr (CPL == 4 && (ST || GridShape<N, P, TB, WD>::ROWS % 2 != 0)) {
+        return cudaErrorInvalidValue;
+    } else {
+    auto k = k_grid_rows<N, P, TB, ST, GO, CPL, WD>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<dim3(n_stripes, a.nc), kBlock, smem, st>>>(a);
     return cudaGetLastError();
+    }
 }
 
-template <int N, int P, bool ST, bool GO, bool PR, bool WD>
+template <int N, int P, bool ST, bool GO, int CPL, bool WD>
 cudaError_t launch_grid_s(int TB, const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st) {
     switch (TB) {
-        case 1: return launch_grid_t<N, P, 1, ST, GO, PR, WD>(a, n_stripes, smem, st);
-        case 2: return launch_grid_t<N, P, 2, ST, GO, PR, WD>(a, n_stripes, smem, st);
-        case 4: return launch_grid_t<N, P, 4, ST, GO, PR, WD>(a, n_stripes, smem, st);
-        case 8: return launch_grid_t<N, P, 8, ST, GO, PR, WD>(a, n_stripes, smem, st);
+        case 1: return launch_grid_t<N, P, 1, ST, GO, CPL, WD>(a, n_stripes, smem, st);
+        case 2: return launch_grid_t<N, P, 2, ST, GO, CPL, WD>(a, n_stripes, smem, st);
+        case 4: return launch_grid_t<N, P, 4, ST, GO, CPL, WD>(a, n_stripes, smem, st);
+        case 8: return launch_grid_t<N, P, 8, ST, GO, CPL, WD>(a, n_stripes, smem, st);
     }
     return cudaErrorInvalidValue;
 }
 
 // The stripe height is a compile-time function of TB, so the grid-only
 // variant runs with the plan's TB too (and stores only the first sample).
-template <int N, int P, bool PR, bool WD>
+template <int N, int P, int CPL, bool WD>
 cudaError_t launch_grid_q(int TB, bool staged, bool go, const GridArgs &a, int n_stripes, size_t smem,
                           cudaStream_t st) {
-    if (go) return launch_grid_s<N, P, false, true, PR, WD>(TB, a, n_stripes, smem, st);
-    return staged ? launch_grid_s<N, P, true, false, PR, WD>(TB, a, n_stripes, smem, st)
-                  : launch_grid_s<N, P, false, false, PR, WD>(TB, a, n_stripes, smem, st);
+    if (go) return launch_grid_s<N, P, false, true, CPL, WD>(TB, a, n_stripes, smem, st);
+    if (CPL == 4) return staged ? cudaErrorInvalidValue : launch_grid_s<N, P, false, false, CPL, WD>(TB, a, n_stripes, smem, st);
+    return staged ? launch_grid_s<N, P, true, false, CPL, WD>(TB, a, n_stripes, smem, st)
+                  : launch_grid_s<N, P, false, false, CPL, WD>(TB, a, n_stripes, smem, st);
+}
+
+template <int N, int P, bool WD>
+cudaError_t launch_grid_w(int TB, bool staged, bool go, const GridArgs &a, int n_stripes, size_t smem,
+                          cudaStream_t st) {
+    if (a.quads) return launch_grid_q<N, P, 4, WD>(TB, staged, go, a, n_stripes, smem, st);
+    return a.pairs ? launch_grid_q<N, P, 2, WD>(TB, staged, go, a, n_stripes, smem, st)
+                   : launch_grid_q<N, P, 1, WD>(TB, staged, go, a, n_stripes, smem, st);
 }
 
 template <int N, int P>
 cudaError_t launch_grid_p(int TB, bool staged, bool go, const GridArgs &a, int n_stripes, size_t smem,
                           cudaStream_t st) {
-    if (a.wide)
-        return a.pairs ? launch_grid_q<N, P, true, true>(TB, staged, go, a, n_stripes, smem, st)
-                       : launch_grid_q<N, P, false, true>(TB, staged, go, a, n_stripes, smem, st);
-    return a.pairs ? launch_grid_q<N, P, true, false>(TB, staged, go, a, n_stripes, smem, st)
-                   : launch_grid_q<N, P, false, false>(TB, staged, go, a, n_stripes, smem, st);
+    return a.wide ? launch_grid_w<N, P, true>(TB, staged, go, a, n_stripes, smem, st)
+                  : launch_grid_w<N, P, false>(TB, staged, go, a, n_stripes, smem, st);
 }
 
 template <int N, int P, bool H16>

@@ -44,6 +44,7 @@ struct GridArgs {
                               // (sample t, channel cl) at index t * slab_t + cl * slab_c
     long long slab_t, slab_c;
     int pairs;                // 1: each lane sums two horizontally adjacent cells (entries carry two taps)
+    int quads;                // 1: each lane sums a 2 x 2 block of cells (entries carry four taps; pairs ignored)
     int wide;                 // 1: twice grid_fft_rows(N) rows per pass
     // Channel-dependent positions and kernels: chan_group[c] (absolute channel) picks one of
     // several sets; set g's stripe arrays start at st_ant_off + g (n_stripes + 1), slice_off +
@@ -169,6 +170,7 @@ struct Bins {
     bool staged = false;   // kernel entries staged in shared memory
     bool pairs = false;    // lanes own pairs of adjacent cells; con_tap holds two taps per entry
     bool wide = false;     // twice grid_fft_rows(N) rows transformed per pass
+    bool quads = false;    // lanes own 2 x 2 blocks of cells; con_tap holds four taps per entry
     size_t grid_smem = 0;
     std::vector<int> ant_off, ant_list;
     std::vector<long long> slice_off;
@@ -183,6 +185,7 @@ struct GridChoice {
     bool staged = false;
     bool pairs = false;   // each lane sums two horizontally adjacent cells
     bool wide = false;    // twice grid_fft_rows(N) rows per pass (more gather work per barrier)
+    bool quads = false;   // each lane sums a 2 x 2 block of cells (pairs ignored; entries through L2)
 };
 // force = nullptr: the built-in rule; else exactly that shape (MOFF_EINVAL if infeasible).
 moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b,

@@ -174,6 +174,7 @@ extern "C" moff_status moff_image_noalloc(int n_ant, const double *pos, int ksiz
             g.slab_t = 1;
             g.slab_c = Tb;
             g.pairs = b.pairs ? 1 : 0;
+            g.quads = b.quads ? 1 : 0;
             g.wide = b.wide ? 1 : 0;
             NA_CK(launch_grid(N, P, b.tb, b.staged, false, g, b.n_stripes, b.grid_smem, st));
             ColArgs ca{};

@@ -122,7 +122,7 @@ def test_autotuned_plan_matches_oracle_and_is_cached():
     with moff.Plan(pos, taps, N, C, P, autotune=True) as pl:
         tu = pl.tuning()
         assert tu["source"] in (1, 2) and tu["time_batch"] in (1, 2, 4, 8) and tu["staged"] in (0, 1)
-        assert tu["cell_pairs"] in (0, 1) and tu["wide_rows"] in (0, 1)
+        assert tu["cells_per_lane"] in (1, 2, 4) and tu["wide_rows"] in (0, 1)
         pl.set_gains(gains)
         pl.submit(blk)
         img, n = pl.read_image()
@@ -132,8 +132,8 @@ def test_autotuned_plan_matches_oracle_and_is_cached():
     assert err.max() <= TOL32
     with moff.Plan(pos, taps, N, C, P, autotune=True) as pl2:
         tu2 = pl2.tuning()
-    assert tu2["source"] == 2 and (tu2["time_batch"], tu2["staged"], tu2["cell_pairs"]) == (
-        tu["time_batch"], tu["staged"], tu["cell_pairs"])
+    assert tu2["source"] == 2 and (tu2["time_batch"], tu2["staged"], tu2["cells_per_lane"], tu2["wide_rows"]) == (
+        tu["time_batch"], tu["staged"], tu["cells_per_lane"], tu["wide_rows"])
     with moff.Plan(pos, taps, N, C, P) as pl3:
         assert pl3.tuning()["source"] == 0
 
@@ -146,7 +146,7 @@ def test_tuning_cache_file_is_shared_between_processes(tmp_path):
         "rng = np.random.default_rng(80)\n"
         "pos = rng.uniform(10, 50, size=(150, 2)); taps = np.ones((150, 1, 5, 5), complex)\n"
         "pl = moff.Plan(pos, taps, 64, 2, 1, autotune=True)\n"
-        "t = pl.tuning(); print('SRC', t['source'], t['time_batch'], t['staged'], t['cell_pairs'])\n" % ROOT)
+        "t = pl.tuning(); print('SRC', t['source'], t['time_batch'], t['staged'], t['cells_per_lane'], t['wide_rows'])\n" % ROOT)
     env = dict(os.environ, MOFF_TUNE_CACHE=path)
     outs = []
     for _ in range(2):

@@ -93,7 +93,7 @@ def test_a_channel_equals_a_plan_created_with_its_set(monkeypatch):
         p1.set_gains(gains)
         p1.submit(codes)
         one, _ = p1.read_image()
-    assert (tu["time_batch"], tu["cell_pairs"], tu["staged"]) == (t1["time_batch"], t1["cell_pairs"], t1["staged"])
+    assert (tu["time_batch"], tu["cells_per_lane"], tu["staged"]) == (t1["time_batch"], t1["cells_per_lane"], t1["staged"])
     assert np.array_equal(two[1:3], one[1:3])
 
 

@@ -391,25 +391,28 @@ def test_adc_path_equals_channelise_then_submit():
 @pytest.mark.parametrize("N,P,K,A,jones,stage", [(64, 2, 5, 150, False, "0"), (128, 2, 7, 300, False, "1"),
                                                   (64, 2, 5, 40, True, "0"), (256, 1, 3, 200, False, "1"),
                                                   (32, 1, 3, 64, False, "0")])
-def test_cell_pair_lanes_are_bit_identical(monkeypatch, N, P, K, A, jones, stage):
-    """Pair lanes sum each cell's contributions in the single-cell order (plus
-    exact zero terms), so the images and the gridded snapshot must match the
-    single-cell kernel bit for bit, with entries read through L2 or staged."""
+def test_cell_pair_and_block_lanes_are_bit_identical(monkeypatch, N, P, K, A, jones, stage):
+    """Pair lanes and 2 x 2 block lanes sum each cell's contributions in the
+    single-cell order (plus exact zero terms), so the images and the gridded
+    snapshot must match the single-cell kernel bit for bit, with entries read
+    through L2 or staged (blocks always read them through L2)."""
     pos, taps, codes, gains = random_case(500 + N, A, N, K, P, C=3, T=21, jones=jones)
     monkeypatch.setenv("MOFF_GRID_STAGE", stage)
     out = {}
-    for pairs in ("0", "1"):
+    for cpl, pairs, quads in ((1, "0", "0"), (2, "1", "0"), (4, "1", "1")):
         monkeypatch.setenv("MOFF_GRID_PAIRS", pairs)
+        monkeypatch.setenv("MOFF_GRID_QUADS", quads)
         with moff.Plan(pos, taps, N, 3, P, jones=jones) as pl:
-            assert pl.tuning()["cell_pairs"] == int(pairs)
+            assert pl.tuning()["cells_per_lane"] == cpl
             pl.set_gains(gains)
             pl.submit(codes)
             img, n = pl.read_image()
             snap = pl.grid_snapshot(codes[4], 1)
-        out[pairs] = (img, snap)
-    assert np.array_equal(out["0"][0], out["1"][0])
-    assert np.array_equal(out["0"][1], out["1"][1])
-    assert_image(out["1"][0], oracle.moff_image(codes, gains, pos, taps, N, P, jones=jones))
+        out[cpl] = (img, snap)
+    for cpl in (2, 4):
+        assert np.array_equal(out[1][0], out[cpl][0])
+        assert np.array_equal(out[1][1], out[cpl][1])
+    assert_image(out[4][0], oracle.moff_image(codes, gains, pos, taps, N, P, jones=jones))
 
 
 def test_host_adc_pipelined_staging_equals_device_input():
