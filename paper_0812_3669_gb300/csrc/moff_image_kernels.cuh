@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
             for (int c2 = 0; c2 < TPE; ++c2)
 #pragma unroll
                 for (int t = 0; t < TB; ++t) acc[c2][t] = make_float2(0.f, 0.f);
-            constexpr int U = CPL == 4 ? 2 : (PAIRS ? 2 : 4);
+            constexpr int U = PAIRS ? 2 : 4;
             // Entries i0 .. i0 + U - 1 (zero past the slice): taps and voltage indices.
             auto load_ent = [&](int i0, float2 (&tv)[U][TPE], int (&yv)[U]) {
 #pragma unroll
@@ -377,6 +377,15 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
         for (int r = 0; r < RL; ++r) acc[q][r] = 0.f;
 
     const int colL = tid % W, jL = tid / W;
+    // tied-array beam pixels this thread holds (bit j: beam j), fixed for the CTA; the
+    // thread's pixels are ky = jL + r NS (r < RL) of column kx0 + colL
+    uint32_t bmask = 0;
+    if constexpr (TAPS) {
+        for (int j = 0; j < a.n_beam; ++j) {
+            const int ky = a.beam_ky[j];
+            if (kx0 + colL == a.beam_kx[j] && ky >= jL && (ky - jL) % CS::NS == 0) bmask |= 1u << j;
+        }
+    }
     if (a.nt > 0) stage(0, s_in);
 
     for (int tt = 0; tt < a.nt; ++tt) {
@@ -444,13 +453,15 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
             const bool tap = TAPS && a.etap && kx0 + colL == a.tap_kx && (a.tap_ky - jL) % NS == 0 && a.tap_ky >= jL;
             // tied-array beams: the field at each beam pixel this thread holds, every sample
             auto beams = [&](const float2 (&v)[RL], int p) {
-                for (int j = 0; j < a.n_beam; ++j)
-                    if (kx0 + colL == a.beam_kx[j]) {
+                for (uint32_t m = bmask; m; m &= m - 1) {
+                    const int j = __ffs(m) - 1;
+                    const int rj = (a.beam_ky[j] - jL) / NS;
+                    float2 val = v[0];
 #pragma unroll
-                        for (int r = 0; r < RL; ++r)
-                            if (jL + r * NS == a.beam_ky[j])
-                                a.beam_out[(((long long)(a.beam_t0 + tt) * a.beam_C + c) * a.n_beam + j) * P + p] = v[r];
-                    }
+                    for (int r = 1; r < RL; ++r)
+                        if (r == rj) val = v[r];
+                    a.beam_out[(((long long)(a.beam_t0 + tt) * a.beam_C + c) * a.n_beam + j) * P + p] = val;
+                }
             };
             if constexpr (P == 1) {
                 if (tap) {
@@ -458,7 +469,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                     for (int r = 0; r < RL; ++r)
                         if (jL + r * NS == a.tap_ky) a.etap[(long long)tt * a.nc + cl] = vx[r];
                 }
-                if (TAPS && a.n_beam) beams(vx, 0);
+                if (TAPS && bmask) beams(vx, 0);
 #pragma unroll
                 for (int r = 0; r < RL; ++r) acc[0][r] = fmaf(vx[r].x, vx[r].x, fmaf(vx[r].y, vx[r].y, acc[0][r]));
             } else {
@@ -475,7 +486,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                             a.etap[((long long)tt * a.nc + cl) * 2 + 1] = vy[r];
                         }
                 }
-                if (TAPS && a.n_beam) {
+                if (TAPS && bmask) {
                     beams(vx, 0);
                     beams(vy, 1);
                 }
