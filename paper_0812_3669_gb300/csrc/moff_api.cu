@@ -1062,6 +1062,8 @@ moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *
     // |y s_y| < 2^14, so |re|, |im| <= 2^14 * sum_j max_kx (|S_j re| + |S_j im|) s_w; keep that below 2^15.
     rs->row_sh.assign((size_t)P * N, 1.f);
     rs->row_inv.assign((size_t)P * N, 1.f);
+    float sh = 1.f;
+    bool any = false;
     for (size_t r = 0; r < (size_t)P * N; ++r) {
         double bound = 0.0;
         for (size_t j = 0; j < segs[r].size(); ++j) {
@@ -1075,7 +1077,16 @@ moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *
         if (bound > 0.0) std::frexp(bound, &eb);          // bound in [2^(eb-1), 2^eb)
         rs->row_sh[r] = bound > 0.0 ? (float)std::ldexp(1.0, 15 - eb) : 1.f;
         rs->row_inv[r] = bound > 0.0 ? (float)std::ldexp(1.0, eb - 15) : 1.f;
+        if (bound > 0.0 && (!any || rs->row_sh[r] < sh)) {
+            sh = rs->row_sh[r];
+            any = true;
+        }
     }
+    // One scale for all rows: the smallest row scale keeps every row in FP16 range, and
+    // a power-of-two scale changes no rounding (FP16 rounding is relative), so the column
+    // kernel transforms the scaled rows and undoes one scale per channel.
+    rs->row_sh.assign((size_t)P * N, sh);
+    rs->row_inv.assign((size_t)P * N, 1.f / sh);
     // B images: row n < KX -> real part of H at kx = tile*KX + n; n >= KX -> imaginary part.
     //   Hr = sum_j yr Sr - yi Si ; Hi = sum_j yr Si + yi Sr   (k = 2j: yr, k = 2j+1: yi)
     rs->bimg_off.assign((size_t)P * N * ntiles, 0);

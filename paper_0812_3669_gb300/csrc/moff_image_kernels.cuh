@@ -351,13 +351,12 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
     unsigned char *s_in = reinterpret_cast<unsigned char *>(s_tw + ((TW::TOTAL + 1) & ~1));  // 2 staging tiles
     float2 *s_a = reinterpret_cast<float2 *>(s_in + 2 * TILE * EB);   // pass outputs
     float2 *s_b = s_a + TILE;                      // second pass buffer (3-pass lengths only)
-    float *s_rs = reinterpret_cast<float *>(s_b + (FP::NP == 3 ? TILE : 0));   // FP16 path: per-row scale
 
     for (int i = tid; i < TW::TOTAL; i += kBlock) s_tw[i] = a.twp[i];
-    if constexpr (H16) {
-        const float cinv = a.inv_sw / a.sy[c];
-        for (int i = tid; i < P * N; i += kBlock) s_rs[i] = a.row_inv[i] * cinv;
-    }
+    // FP16 field: one power-of-two scale for every row of the channel, so the transform
+    // runs on the scaled values (exactly proportional) and the scale is undone on the
+    // field taps and, squared, on the chunk's sums
+    const float sc = H16 ? a.row_inv[0] * a.inv_sw / a.sy[c] : 1.f;
 
     // Stage sample tt's [P][N][W] tile of the row-transformed field.
     auto stage = [&](int tt, unsigned char *dst) {
@@ -400,9 +399,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
         auto in_at = [&](int p, int row, int col) -> float2 {
             const int e = (p * N + row) * W + col;
             if constexpr (H16) {
-                const float2 f = __half22float2(reinterpret_cast<const __half2 *>(tin)[e]);
-                const float sc = s_rs[p * N + row];
-                return make_float2(f.x * sc, f.y * sc);
+                return __half22float2(reinterpret_cast<const __half2 *>(tin)[e]);
             } else {
                 return reinterpret_cast<const float2 *>(tin)[e];
             }
@@ -460,14 +457,16 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
 #pragma unroll
                     for (int r = 1; r < RL; ++r)
                         if (r == rj) val = v[r];
-                    a.beam_out[(((long long)(a.beam_t0 + tt) * a.beam_C + c) * a.n_beam + j) * P + p] = val;
+                    a.beam_out[(((long long)(a.beam_t0 + tt) * a.beam_C + c) * a.n_beam + j) * P + p] =
+                        make_float2(val.x * sc, val.y * sc);
                 }
             };
             if constexpr (P == 1) {
                 if (tap) {
 #pragma unroll
                     for (int r = 0; r < RL; ++r)
-                        if (jL + r * NS == a.tap_ky) a.etap[(long long)tt * a.nc + cl] = vx[r];
+                        if (jL + r * NS == a.tap_ky)
+                            a.etap[(long long)tt * a.nc + cl] = make_float2(vx[r].x * sc, vx[r].y * sc);
                 }
                 if (TAPS && bmask) beams(vx, 0);
 #pragma unroll
@@ -482,8 +481,8 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
 #pragma unroll
                     for (int r = 0; r < RL; ++r)
                         if (jL + r * NS == a.tap_ky) {
-                            a.etap[((long long)tt * a.nc + cl) * 2] = vx[r];
-                            a.etap[((long long)tt * a.nc + cl) * 2 + 1] = vy[r];
+                            a.etap[((long long)tt * a.nc + cl) * 2] = make_float2(vx[r].x * sc, vx[r].y * sc);
+                            a.etap[((long long)tt * a.nc + cl) * 2 + 1] = make_float2(vy[r].x * sc, vy[r].y * sc);
                         }
                 }
                 if (TAPS && bmask) {
@@ -503,6 +502,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
     }
 
     // Fold this chunk's FP32 sums into the FP64 accumulators (one owner per pixel).
+    const double sc2 = (double)sc * (double)sc;
     const int kx = kx0 + colL;
 #pragma unroll
     for (int q = 0; q < NPROD; ++q) {
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
             const int ky = jL + r * CS::NS;
-            d[(long long)ky * N] += (double)acc[q][r];
+            d[(long long)ky * N] += H16 ? (double)acc[q][r] * sc2 : (double)acc[q][r];
         }
     }
 }
@@ -519,8 +519,7 @@ template <int N>
 size_t col_smem_bytes_t(int P, bool h16 = false) {
     using FP = FftPlan<N>;
     const size_t tile = (size_t)P * N * ColShape<N>::W;
-    return (size_t)((FftTw<N>::TOTAL + 1) & ~1) * 8 + tile * (h16 ? 4 : 8) * 2 + tile * 8 * (FP::NP == 3 ? 2 : 1) +
-           (h16 ? (size_t)P * N * 4 : 0);
+    return (size_t)((FftTw<N>::TOTAL + 1) & ~1) * 8 + tile * (h16 ? 4 : 8) * 2 + tile * 8 * (FP::NP == 3 ? 2 : 1);
 }
 
 template <int N, int P, int TB, bool ST, bool GO, int CPL, bool WD>

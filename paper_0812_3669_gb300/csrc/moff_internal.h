@@ -86,7 +86,7 @@ struct RowSpecArgs {
     const __half *yre, *yim;   // [nc][AP][Tpad] weighted, scaled voltages
     const float *sy;           // [C] voltage scales (powers of two)
     float inv_sw;              // 1 / spectrum scale (power of two)
-    const float *row_sh;       // [P*N] per-row FP16 output scale (power of two)
+    const float *row_sh;       // [P*N] FP16 output scale (one power of two for every row)
     __half2 *H;                // row-transformed field, FP16, scaled by row_sh: slab [P][N][N] of
                                // (sample t, channel cl) at index t * slab_t + cl * slab_c
     long long slab_t, slab_c;
@@ -197,7 +197,7 @@ struct RowSpec {
     int kp_max = 0, max_seg = 0, ntiles = 1;
     float inv_sw = 1.f;
     std::vector<int> kp, seg_y;
-    std::vector<float> row_sh, row_inv;         // per (pol, row) FP16 field scale and its inverse
+    std::vector<float> row_sh, row_inv;         // FP16 field scale and its inverse (equal for every (pol, row))
     std::vector<long long> seg_off, bimg_off;   // bimg_off in elements
     std::vector<__half> bimg;
 };

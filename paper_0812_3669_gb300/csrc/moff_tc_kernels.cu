@@ -18,7 +18,7 @@
 //   k_rowspec_tc   per (pol, row, kx tile): B = row spectra resident in shared memory,
 //                  A = 128 samples of the row's segment voltages (cp.async, MN-major),
 //                  D = TMEM (double buffered), epilogue writes the row-transformed field in
-//                  FP16 under an exact per-row power-of-two scale (undone by the column kernel).
+//                  FP16 under an exact power-of-two scale (undone by the column kernel).
 #include <cuda_fp16.h>
 
 #include "moff_fft.cuh"
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
             if (!tc::mbar_wait_abortable(&d_full[b], (uint32_t)((i >> 1) & 1), kWaitCycles, abort_flag)) break;
             tc::fence_after_sync();
             const int cl = cb + i / ntb, t0w = (i % ntb) * 128 + warp * 32;
-            const float inv = a.row_sh[pr];   // exact power of two: FP16 range for this row
+            const float inv = a.row_sh[pr];   // exact power of two: FP16 range for every row
             const uint32_t dcol = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * NT);
 #pragma unroll 1
             for (int k0 = 0; k0 < KX; k0 += 32, ++nbox) {
