@@ -50,7 +50,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp16tc", action="store_true", help="skip the FP16 tensor-core leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream (serving) leg")
-    ap.add_argument("--no-feedback", action="store_true", help="skip the feedback-calibration leg")
+    ap.add_argument("--no-feedback", action="store_true",
+                    help="skip the legs of the method's extensions (feedback calibration, beams and autocorrelation "
+                         "subtraction, channel-dependent positions and kernels, edge-padded oversampling)")
     ap.add_argument("--no-plain", action="store_true", help="skip the batching leg (graph + autotune vs one channel at a time)")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per load point of the serving leg")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -581,6 +583,53 @@ def run_ours(args):
         r = taps_leg["autocorr_kernel_roofline"]
         r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
 
+    # ---------------------------------------------------------------- channel-dependent positions/kernels leg
+    # Positions in wavelengths scale with frequency: 32 sets across the band (0.9 to 1.1 of the
+    # reference positions about the grid centre), kernels re-evaluated at each set's subpixel
+    # offsets; channel c takes set 32 c / C.  Then the same array edge-padded onto a 2N grid.
+    sets_leg = None
+    if not args.no_feedback:
+        G = 32
+        scales = 0.9 + 0.2 * np.arange(G) / (G - 1)
+        cen = N / 2.0
+        pos_sets = np.stack([cen + (pos - cen) * sc for sc in scales])
+        taps_sets = np.stack([synth.taps_gaussian(np.random.default_rng(synth.SEED_BASE + 50), ps, WL["ksize"], 1.2,
+                                                  n_pol=P, subpixel=True, phase_slope=0.3) for ps in pos_sets])
+        grp = (np.arange(C) * G) // C
+        plans = make_plan(False)
+        t0 = time.perf_counter()
+        plans.set_channel_groups(pos_sets, taps_sets, grp)
+        bin_s = time.perf_counter() - t0
+        nst = max(1, args.steps // 2)
+        mss, kerns, _, _ = measure(plans, nst, 1)
+        tun = plans.tuning()
+        plans.close()
+        gk = kerns.get("grid_rows", {})
+        g_flops = nst * F * C * flops_per_snapshot(1)
+        sets_leg = {"value": job_rate(nst * F * C, world, mss / 1000.0), "unit": UNIT, "ms_per_step": mss / nst,
+                    "sets": G, "scale_range": [0.9, 1.1], "binning_s": bin_s, "kernels": kerns,
+                    "grid_shape": {"time_batch": tun["time_batch"], "cells_per_lane": tun["cells_per_lane"],
+                                   "wide_rows": tun["wide_rows"]},
+                    "grid_kernel_roofline": {"bound": "alu",
+                                             "achieved": g_flops / (gk["ms_total"] / 1e3) / 1e12
+                                             if gk.get("ms_total") else None,
+                                             "peak": alu_peak, "unit": "TFLOP/s",
+                                             "peak_basis": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
+                                                           "(of derived peak)"}}
+        r = sets_leg["grid_kernel_roofline"]
+        r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
+        # image oversampling by edge padding: the array centred on a 2N grid
+        plo = moff.Plan(pos + N / 2.0, taps, 2 * N, C, P, fstage=True, autotune=True)
+        plo.set_gains(gains)
+        calib = adc[:, :, : (ntaps + 3) * M].contiguous()
+        plo.set_fstage(ntaps, None, 1.0)
+        spec = plo.channelise(calib, kind=1)
+        plo.set_fstage(ntaps, None, float(2.0 / np.std(np.concatenate([spec.real.ravel(), spec.imag.ravel()]))))
+        mso, kerno, _, _ = measure(plo, 1, 1)
+        plo.close()
+        sets_leg["oversampled_2x"] = {"grid_n": 2 * N, "value": job_rate(F * C, world, mso / 1000.0), "unit": UNIT,
+                                      "ms_per_step": mso, "kernels": kerno}
+
     # ---------------------------------------------------------------- end to end through host buffers
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
@@ -628,7 +677,7 @@ def run_ours(args):
             "fx_equiv_tcmac_per_s": fx_eq / 1e12,
             "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches, "clocks": clk,
             "e2e": e2e, "cpu_baseline": cpu, "fp16tc": fp16, "serving": serving, "batching": batching, "feedback": feedback,
-            "beams_autocorr": taps_leg,
+            "beams_autocorr": taps_leg, "channel_sets": sets_leg,
         }), flush=True)
     if dist is not None:
         dist.destroy_process_group()
