@@ -73,11 +73,14 @@ def test_channel_sets_match_the_oracle(N, P, K, A, jones):
     assert oracle.max_norm_err(img[1:2], alt).max() > 1e-2
 
 
-def test_a_channel_equals_a_plan_created_with_its_set(monkeypatch):
-    """Same gridding shape (forced by the environment rule knobs): the channels of
-    set 1 in a two-set plan are bit-identical to a plan created with set 1."""
+@pytest.mark.parametrize("quads", ["0", "1"])
+def test_a_channel_equals_a_plan_created_with_its_set(monkeypatch, quads):
+    """Same gridding shape (forced by the environment rule knobs; pair lanes or
+    2 x 2 block lanes): the channels of set 1 in a two-set plan are bit-identical
+    to a plan created with set 1."""
     N, P, K, A, C, T = 64, 2, 5, 150, 4, 29
     monkeypatch.setenv("MOFF_GRID_PAIRS", "1")
+    monkeypatch.setenv("MOFF_GRID_QUADS", quads)
     monkeypatch.setenv("MOFF_GRID_STAGE", "0")
     pos, taps = scaled_sets(830, A, N, K, P, [1.0, 1.1])
     codes, gains = codes_for(831, T, C, A, P)
@@ -94,6 +97,7 @@ def test_a_channel_equals_a_plan_created_with_its_set(monkeypatch):
         p1.submit(codes)
         one, _ = p1.read_image()
     assert (tu["time_batch"], tu["cells_per_lane"], tu["staged"]) == (t1["time_batch"], t1["cells_per_lane"], t1["staged"])
+    assert tu["cells_per_lane"] == (4 if quads == "1" else 2)
     assert np.array_equal(two[1:3], one[1:3])
 
 
