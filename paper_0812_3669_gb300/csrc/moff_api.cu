@@ -214,6 +214,7 @@ struct moff_plan {
     uint16_t *d_lane_cell = nullptr;
     float2 *d_con_tap = nullptr;
     uint16_t *d_con_y = nullptr;
+    uint32_t *d_row_nz = nullptr;   // [N / 32] grid rows any kernel footprint reaches
     float2 *d_twp = nullptr;
 
     float2 *d_gains = nullptr;
@@ -489,6 +490,7 @@ GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, 
     g.quads = pl->quads ? 1 : 0;
     g.wide = pl->wide ? 1 : 0;
     g.chan_group = pl->d_chan_group;
+    g.row_nz = pl->d_row_nz;
     return g;
 }
 
@@ -598,6 +600,7 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
             ca.nc = nc;
             ca.twp = pl->d_twp;
             ca.acc = pl->d_acc;
+            ca.row_nz = pl->d_row_nz;
             ca.slab_t = ra.slab_t;
             ca.slab_c = ra.slab_c;
             ca.row_inv = pl->d_rs_row_inv;
@@ -687,6 +690,7 @@ moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long 
             ca.slab_c = g.slab_c;
             ca.twp = pl->d_twp;
             ca.acc = pl->d_acc;
+            ca.row_nz = pl->d_row_nz;
             set_tap(pl, &ca, t0);
             TimedLaunch tc(pl, 2);
             MOFF_CK(launch_cols(pl->N, pl->P, ca, pl->st));
@@ -884,6 +888,12 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
                 }
             }
     }
+    b->row_nz.assign((size_t)(N + 31) / 32, 0u);
+    for (int a = 0; a < A; ++a)
+        for (int iy = 0; iy < K; ++iy) {
+            const int row = (ay[a] + iy - h + N) % N;
+            b->row_nz[row >> 5] |= 1u << (row & 31);
+        }
     b->ant_off.assign(ns + 1, 0);
     b->ant_list.clear();
     b->slice_off.assign((size_t)ns * nsl + 1, 0);
@@ -1167,6 +1177,9 @@ moff_status build_bin_sets(const moff_plan *pl, int n_sets, const double *pos, c
         const Bins &b0 = bins[0];
         o.rows = b0.rows; o.tb = b0.tb; o.n_stripes = b0.n_stripes; o.n_slices = b0.n_slices;
         o.staged = b0.staged; o.pairs = b0.pairs; o.wide = b0.wide; o.quads = b0.quads;
+        o.row_nz.assign(b0.row_nz.size(), 0u);
+        for (const Bins &b : bins)
+            for (size_t w = 0; w < o.row_nz.size(); ++w) o.row_nz[w] |= b.row_nz[w];
         for (const Bins &b : bins) {
             if (b.n_slices != b0.n_slices || b.n_stripes != b0.n_stripes)
                 return fail(MOFF_EINVAL, "internal: sets binned to different stripe shapes");
@@ -1202,8 +1215,10 @@ moff_status upload_bins(moff_plan *pl, const Bins &b) {
     long long *soff = nullptr;
     uint16_t *lcell = nullptr, *cy = nullptr;
     float2 *ctap = nullptr;
+    uint32_t *rnz = nullptr;
     auto undo = [&](moff_status s) {
         pfree(pl, ant_off); pfree(pl, ant); pfree(pl, soff); pfree(pl, lcell); pfree(pl, ctap); pfree(pl, cy);
+        pfree(pl, rnz);
         return s;
     };
     moff_status s;
@@ -1213,7 +1228,9 @@ moff_status upload_bins(moff_plan *pl, const Bins &b) {
     if ((s = palloc(pl, &lcell, b.lane_cell.size() * 2)) != MOFF_OK) return undo(s);
     if ((s = palloc(pl, &ctap, std::max<size_t>(b.con_tap.size(), 1) * 8)) != MOFF_OK) return undo(s);
     if ((s = palloc(pl, &cy, std::max<size_t>(b.con_y.size(), 1) * 2)) != MOFF_OK) return undo(s);
-    bool ok = cudaMemcpy(ant_off, b.ant_off.data(), b.ant_off.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+    if ((s = palloc(pl, &rnz, b.row_nz.size() * 4)) != MOFF_OK) return undo(s);
+    bool ok = cudaMemcpy(rnz, b.row_nz.data(), b.row_nz.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ant_off, b.ant_off.data(), b.ant_off.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(soff, b.slice_off.data(), b.slice_off.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(lcell, b.lane_cell.data(), b.lane_cell.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok && !b.ant_list.empty())
@@ -1223,7 +1240,8 @@ moff_status upload_bins(moff_plan *pl, const Bins &b) {
              cudaMemcpy(cy, b.con_y.data(), b.con_y.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return undo(fail(MOFF_ECUDA, "upload of the kernel bins failed"));
     pfree(pl, pl->d_st_ant_off); pfree(pl, pl->d_st_ant); pfree(pl, pl->d_slice_off);
-    pfree(pl, pl->d_lane_cell); pfree(pl, pl->d_con_tap); pfree(pl, pl->d_con_y);
+    pfree(pl, pl->d_lane_cell); pfree(pl, pl->d_con_tap); pfree(pl, pl->d_con_y); pfree(pl, pl->d_row_nz);
+    pl->d_row_nz = rnz;
     pl->d_st_ant_off = ant_off; pl->d_st_ant = ant; pl->d_slice_off = soff;
     pl->d_lane_cell = lcell; pl->d_con_tap = ctap; pl->d_con_y = cy;
     pl->rows = b.rows;

@@ -99,6 +99,14 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     const long long e0 = soff[0];
 
     if (nloc == 0) {   // no kernel reaches these rows: their field (and its transform) is zero
+        if (!GRID_ONLY && a.row_nz) {   // rows the column kernel will not read are not written
+            bool any = false;
+            for (int rl = 0; rl < ROWS; ++rl) {
+                const int ry = s * ROWS + rl;
+                any |= ((a.row_nz[ry >> 5] >> (ry & 31)) & 1u) != 0;
+            }
+            if (!any) return;
+        }
         constexpr int PER_T = P * ROWS * N / 2;     // 16-byte stores per sample
         for (int i = tid; i < a.nt * PER_T; i += kBlock) {
             const int t = i / PER_T, e = 2 * (i - t * PER_T);
@@ -358,13 +366,30 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
     // field taps and, squared, on the chunk's sums
     const float sc = H16 ? a.row_inv[0] * a.inv_sw / a.sy[c] : 1.f;
 
+    // Rows no kernel reaches are zero: cleared once in both staging tiles and never read.
+    // Piece q = tid + k kBlock of a tile is read only if bit k of `act` is set.
+    static_assert(CHUNKS % kBlock == 0 && CHUNKS / kBlock <= 32, "staging pieces per thread");
+    constexpr int ITER = CHUNKS / kBlock;
+    uint32_t act = 0;
+#pragma unroll
+    for (int k = 0; k < ITER; ++k) {
+        const int q = tid + k * kBlock, row = q / ROWCH, part = q - row * ROWCH, ry = row % N;
+        if (!a.row_nz || ((a.row_nz[ry >> 5] >> (ry & 31)) & 1u)) {
+            act |= 1u << k;
+        } else {
+            *reinterpret_cast<uint4 *>(s_in + (row * W) * EB + part * 16) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(s_in + TILE * EB + (row * W) * EB + part * 16) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+
     // Stage sample tt's [P][N][W] tile of the row-transformed field.
     auto stage = [&](int tt, unsigned char *dst) {
         const unsigned char *src = reinterpret_cast<const unsigned char *>(a.H) +
                                    (((long long)tt * a.slab_t + (long long)cl * a.slab_c) * P * N * N + kx0) * EB;
-        for (int q = tid; q < CHUNKS; q += kBlock) {
-            const int row = q / ROWCH, part = q - row * ROWCH;       // row = p*N + ry
-            cp_async16(dst + (row * W) * EB + part * 16, src + (long long)row * N * EB + part * 16);
+#pragma unroll
+        for (int k = 0; k < ITER; ++k) {
+            const int q = tid + k * kBlock, row = q / ROWCH, part = q - row * ROWCH;   // row = p*N + ry
+            if ((act >> k) & 1u) cp_async16(dst + (row * W) * EB + part * 16, src + (long long)row * N * EB + part * 16);
         }
         cp_async_commit();
     };

@@ -46,6 +46,10 @@ struct GridArgs {
     int pairs;                // 1: each lane sums two horizontally adjacent cells (entries carry two taps)
     int quads;                // 1: each lane sums a 2 x 2 block of cells (entries carry four taps; pairs ignored)
     int wide;                 // 1: twice grid_fft_rows(N) rows per pass
+    // Grid rows any kernel footprint reaches (bit ry of word ry / 32, every set of positions and
+    // kernels).  With it, a stripe none of whose rows is set writes nothing: the column kernel
+    // reads only the set rows.  nullptr: every stripe is written.
+    const uint32_t *row_nz;
     // Channel-dependent positions and kernels: chan_group[c] (absolute channel) picks one of
     // several sets; set g's stripe arrays start at st_ant_off + g (n_stripes + 1), slice_off +
     // g (n_stripes n_slices + 1) and lane_cell + g n_stripes n_slices 32, and their values
@@ -61,6 +65,7 @@ struct ColArgs {
     int nt, c0, nc;
     const float2 *twp;
     double *acc;              // [C][n_prod][N][N] FP64 accumulators (added to)
+    const uint32_t *row_nz;   // rows to read (bit ry); other rows are zero (nullptr: read all)
     // FP16 field only: value = half2 * row_inv[p*N + ry] * inv_sw / sy[c]
     const float *row_inv;
     const float *sy;
@@ -171,6 +176,7 @@ struct Bins {
     bool pairs = false;    // lanes own pairs of adjacent cells; con_tap holds two taps per entry
     bool wide = false;     // twice grid_fft_rows(N) rows transformed per pass
     bool quads = false;    // lanes own 2 x 2 blocks of cells; con_tap holds four taps per entry
+    std::vector<uint32_t> row_nz;   // [N / 32] grid rows any kernel footprint reaches
     size_t grid_smem = 0;
     std::vector<int> ant_off, ant_list;
     std::vector<long long> slice_off;
