@@ -1743,7 +1743,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         // FP32 field (float2) on the FP32 path, FP16 (half2) on the tensor-core path
         const size_t per = (size_t)n_pol * grid_n * grid_n * (pl->tc ? 4 : 8);
         // served plans borrow their scratch per block from a shared pool: keep it modest
-        long long budget = pl->served ? (2048LL << 20) : (24576LL << 20);
+        long long budget = pl->served ? (2048LL << 20) : (32768LL << 20);
         if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, (long long)(atof(e) * 1048576.0));
         // channels split into equal chunks (no ragged last chunk)
         auto balance = [&](long long cb_max) {
@@ -1757,7 +1757,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             pl->Cb = (int)balance(std::max(1LL, std::min<long long>(n_chan, budget / (long long)per_c)));
         } else {
             const long long cb = balance(std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per))));
-            const long long tb = std::max(1LL, std::min<long long>(64, budget / (long long)(cb * per)));
+            const long long tb = std::max(1LL, std::min<long long>(128, budget / (long long)(cb * per)));
             pl->Cb = (int)cb;
             pl->Tb = (int)tb;
         }
@@ -1973,8 +1973,10 @@ moff_status submit_adc_pipelined(moff_plan *pl, const int8_t *adc, long long n_s
         if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
             return fail(MOFF_ECUDA, "event creation failed");
     const int nseg_max = (int)(sizeof(pl->seg_ev) / sizeof(pl->seg_ev[0]));
-    int seg = kSegFrames;
-    while ((F + seg - 1) / seg > nseg_max) seg += kSegFrames;
+    // segments hold whole imaging chunks (so the launches, and the image, equal a device-input submit's)
+    const int step = pl->tc ? pl->Tb : ((kSegFrames + pl->Tb - 1) / pl->Tb) * pl->Tb;
+    int seg = step;
+    while ((F + seg - 1) / seg > nseg_max) seg += step;
     const long long M = 2LL * pl->C, tstride = (long long)pl->C * pl->A * pl->P;
     const int AP = pl->A * pl->P;
     int8_t *dst = static_cast<int8_t *>(pl->d_stage[i]);
