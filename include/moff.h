@@ -383,7 +383,9 @@ moff_status moff_image_noalloc(int n_ant, const double *pos, int ksize, const fl
  *   n  multiple of 32 in [32, 256];  k  multiple of 16 in [16, 256].
  *   mode  bit 0: stage A MN-major (then k <= 64); bit 1: stage B MN-major
  *         (then k <= 64, n <= 128); bit 2: an MN-major operand's descriptor
- *         carries its K-direction core-matrix stride as the leading byte offset.
+ *         carries its K-direction core-matrix stride as the leading byte offset;
+ *         bit 3: stage A MN-major with the 128-byte swizzle of a TMA load
+ *         (then k <= 64).
  * Synchronous on cuda_stream.  MOFF_ETIMEDOUT if the product did not finish
  * within the wait limit (a few seconds).
  */

@@ -45,6 +45,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
+// Byte offset of element (r, k) of an MN-major tile with 128-byte swizzling, as a TMA load
+// with SWIZZLE_128B writes it (1024-byte aligned base): 64-row halves one after the other,
+// each K rows of 128 bytes (64 consecutive r), the 16-byte chunk index XOR-ed with k % 8.
+__device__ __forceinline__ uint32_t mn_sw128_offset(int r, int k, int K) {
+    return (uint32_t)((r >> 6) * K * 128 + k * 128 + ((((r & 63) >> 3) ^ (k & 7)) << 4) + (r & 7) * 2);
+}
+
+// The same descriptor with the 128-byte swizzle layout (bits 61-63 = 2).  For an MN-major
+// operand so laid out, the leading byte offset is the MN-direction stride (between 64-element
+// halves) and the stride byte offset the K-direction one (1024 bytes per 8 rows) -- the
+// reverse of the unswizzled MN-major reading, checked on the GPU by the self-test.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return smem_desc(saddr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B, both
 // K-major, M x N tile (M = 64 or 128, N a multiple of 16 up to 256).
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool a_mn = false, bool b_mn = false) {

@@ -58,6 +58,19 @@ def test_tc_mn_major_operand(operand):
     assert not _run(64, 32, bit, 7)
 
 
+def test_tc_swizzled_mn_major_a():
+    """A staged MN-major with the 128-byte swizzle (the layout a TMA load with
+    SWIZZLE_128B writes): the product is right when the descriptor's leading
+    byte offset is the M-direction stride (between 64-row halves) and its stride
+    byte offset the K-direction one (1024 bytes per 8 rows) -- the opposite of
+    the unswizzled MN-major reading -- and wrong the other way round."""
+    res = {}
+    for lbo_k in (0, 4):
+        res[lbo_k] = [_run(n, k, 8 | lbo_k, 11) for n, k in [(64, 16), (128, 32), (128, 64), (256, 48)]]
+    print("swizzled MN-major A, K-direction stride as leading offset:", res[4], "; as stride offset:", res[0])
+    assert all(res[0]) and not any(res[4])
+
+
 def test_tc_selftest_argument_checks():
     a = torch.zeros((128, 16), dtype=torch.float16, device="cuda")
     b = torch.zeros((40, 16), dtype=torch.float16, device="cuda")
