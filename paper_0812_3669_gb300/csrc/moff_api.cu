@@ -244,11 +244,13 @@ struct moff_plan {
 
     // FP16 tensor-core path
     bool tc = false;
-    int rs_kp_max = 0, rs_max_seg = 0, rs_cgroups = 1;
+    int rs_kp_max = 0, rs_cgroups = 1;
     size_t rs_smem = 0;
     float rs_inv_sw = 1.f;
-    int *d_rs_kp = nullptr, *d_rs_seg_y = nullptr, *d_err = nullptr;
-    long long *d_rs_seg_off = nullptr, *d_rs_bimg_off = nullptr;
+    int *d_rs_kp = nullptr, *d_rs_chunk_row = nullptr, *d_rs_chunk_off = nullptr, *d_rs_perm = nullptr,
+        *d_err = nullptr;
+    long long *d_rs_bimg_off = nullptr;
+    CUtensorMap a_map_re{}, a_map_im{};   // TMA maps of the voltage planes (d_yre, d_yim)
     float *d_rs_row_sh = nullptr, *d_rs_row_inv = nullptr;
     CUtensorMap h_map;                 // tensor-core path: store map of the FP16 field
     int h_map_nt = 0;                  // its sample extent
@@ -560,24 +562,22 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
         for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
             const int nt = std::min(pl->Tb, n_time - t0);
             TimedLaunch tv(pl, 3);
-            MOFF_CK(launch_volt_prep(volt, tstride, t0, nt, c0, nc, AP, pl->d_gains, pl->d_sy, pl->Tb, pl->d_yre,
-                                     pl->d_yim, pl->st));
+            MOFF_CK(launch_volt_prep(volt, tstride, t0, nt, c0, nc, AP, AP + kRowSpecPad, pl->d_gains, pl->d_sy,
+                                     pl->d_rs_perm, pl->Tb, pl->d_yre, pl->d_yim, pl->st));
             tv.done();
             RowSpecArgs ra{};
             ra.P = pl->P;
             ra.nt = nt;
             ra.nc = nc;
             ra.c0 = c0;
-            ra.AP = AP;
+            ra.AP = AP + kRowSpecPad;
             ra.Tpad = pl->Tb;
             ra.kp_max = pl->rs_kp_max;
             ra.kp = pl->d_rs_kp;
-            ra.seg_off = pl->d_rs_seg_off;
-            ra.seg_y = pl->d_rs_seg_y;
+            ra.chunk_off = pl->d_rs_chunk_off;
+            ra.chunk_row = pl->d_rs_chunk_row;
             ra.bimg_off = pl->d_rs_bimg_off;
             ra.bimg = pl->d_rs_bimg;
-            ra.yre = pl->d_yre;
-            ra.yim = pl->d_yim;
             ra.sy = pl->d_sy;
             ra.inv_sw = pl->rs_inv_sw;
             ra.row_sh = pl->d_rs_row_sh;
@@ -591,7 +591,8 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
                 pl->h_map_nt = nt;
             }
             TimedLaunch tg(pl, 1);
-            MOFF_CK(launch_rowspec(pl->N, ra, pl->h_map, std::min(pl->rs_cgroups, nc), pl->rs_smem, pl->st));
+            MOFF_CK(launch_rowspec(pl->N, ra, pl->h_map, pl->a_map_re, pl->a_map_im, std::min(pl->rs_cgroups, nc),
+                                   pl->rs_smem, pl->st));
             tg.done();
             ColArgs ca{};
             ca.H = pl->d_H;
@@ -1004,42 +1005,71 @@ moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *
     const int KX = N < 128 ? N : 128, NT = 2 * KX, ntiles = N / KX;
     std::vector<double> cw(N), sw(N);
     for (int m = 0; m < N; ++m) root_unity(m, N, &cw[m], &sw[m]);
-    // segments (antenna, input pol, kernel row) per (output pol, grid row), antenna-major
+    // Voltage planes list antennas by anchor row (then index): plane row v = q * A + rank(a).
+    // The kernel rows landing on grid row ry come from the antennas whose anchor row lies in
+    // the cyclic window [ry - h, ry + h], consecutive ranks (two runs where the window
+    // wraps), so per (output pol, grid row) the A operand is a few runs of consecutive plane
+    // rows, cut into chunks of 32 (one TMA tile each of real and imaginary parts).  A chunk
+    // slot past its run's end reads another antenna's voltage (or zero past the plane) and
+    // gets zero spectra.
+    std::vector<int> order(A), rank(A), ays(A);
+    for (int a = 0; a < A; ++a) order[a] = a;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ay[x] < ay[y]; });
+    for (int i = 0; i < A; ++i) {
+        rank[order[i]] = i;
+        ays[i] = ay[order[i]];
+    }
+    rs->perm.assign((size_t)A * P, 0);
+    for (int q = 0; q < P; ++q)
+        for (int i = 0; i < A; ++i) rs->perm[(size_t)q * A + i] = order[i] * P + q;
+    auto first_ge = [&](int y) { return (int)(std::lower_bound(ays.begin(), ays.end(), y) - ays.begin()); };
+    // slots (antenna, input pol, kernel row) per (output pol, grid row) in chunk order; a = -1: padding
     struct Seg { int a, q, dy; };
     std::vector<std::vector<Seg>> segs((size_t)P * N);
-    const int pin_n = jones ? 2 : 1;
-    for (int a = 0; a < A; ++a)
-        for (int po = 0; po < P; ++po)
-            for (int k = 0; k < pin_n; ++k) {
-                const int pi = jones ? k : po;
-                for (int dy = 0; dy < K; ++dy) {
-                    bool any = false;
-                    for (int dx = 0; dx < K && !any; ++dx) {
-                        float re, im;
-                        tap_at(jones, P, K, taps, a, po, pi, dy, dx, &re, &im);
-                        any = re != 0.f || im != 0.f;
-                    }
-                    if (any) segs[(size_t)po * N + (ay[a] + dy - h + N) % N].push_back(Seg{a, pi, dy});
-                }
-            }
     rs->ntiles = ntiles;
     rs->kp.assign((size_t)P * N, 0);
-    rs->seg_off.assign((size_t)P * N + 1, 0);
-    rs->seg_y.clear();
+    rs->chunk_off.assign((size_t)P * N + 1, 0);
+    rs->chunk_row.clear();
     rs->kp_max = 0;
-    rs->max_seg = 0;
-    for (size_t r = 0; r < (size_t)P * N; ++r) {
-        const int ns = (int)segs[r].size();
-        rs->kp[r] = ns ? ((2 * ns + 15) / 16) * 16 : 0;
-        rs->kp_max = std::max(rs->kp_max, rs->kp[r]);
-        rs->max_seg = std::max(rs->max_seg, ns);
-        rs->seg_off[r + 1] = rs->seg_off[r] + ns;
-        for (const Seg &g : segs[r]) rs->seg_y.push_back(g.a * P + g.q);
-    }
+    const int pin_n = jones ? 2 : 1;
+    for (int po = 0; po < P; ++po)
+        for (int ry = 0; ry < N; ++ry) {
+            const size_t r = (size_t)po * N + ry;
+            int iv[2][2], niv = 0;      // anchor-row intervals of the window
+            if (ry - h < 0) {
+                iv[niv][0] = 0; iv[niv][1] = ry + h; ++niv;
+                iv[niv][0] = N + ry - h; iv[niv][1] = N - 1; ++niv;
+            } else if (ry + h >= N) {
+                iv[niv][0] = ry - h; iv[niv][1] = N - 1; ++niv;
+                iv[niv][0] = 0; iv[niv][1] = ry + h - N; ++niv;
+            } else {
+                iv[niv][0] = ry - h; iv[niv][1] = ry + h; ++niv;
+            }
+            for (int k = 0; k < pin_n; ++k) {
+                const int q = jones ? k : po;
+                for (int w = 0; w < niv; ++w) {
+                    const int lo = first_ge(iv[w][0]), n = first_ge(iv[w][1] + 1) - lo;
+                    for (int c0 = 0; c0 < n; c0 += 32) {
+                        rs->chunk_row.push_back(q * A + lo + c0);
+                        for (int i = 0; i < 32; ++i) {
+                            if (c0 + i < n) {
+                                const int a = order[lo + c0 + i];
+                                segs[r].push_back(Seg{a, q, (ry - ay[a] + h + N) % N});
+                            } else {
+                                segs[r].push_back(Seg{-1, q, 0});
+                            }
+                        }
+                    }
+                }
+            }
+            rs->chunk_off[r + 1] = (int)rs->chunk_row.size();
+            rs->kp[r] = 2 * (int)segs[r].size();
+            rs->kp_max = std::max(rs->kp_max, rs->kp[r]);
+        }
     if (rs->kp_max > kRowSpecMaxK)
         return fail(MOFF_EINVAL,
-                    "tensor-core path: %d kernel rows land on one grid row (at most %d); use the FP32 path",
-                    rs->max_seg, kRowSpecMaxK / 2);
+                    "tensor-core path: the kernel rows landing on one grid row need %d voltage chunks of 32 (at most "
+                    "%d); use the FP32 path", rs->kp_max / 64, kRowSpecMaxK / 64);
     // spectra in FP64, then one power-of-two scale for the whole plan
     std::vector<std::vector<double>> spec_re((size_t)P * N), spec_im((size_t)P * N);
     double mx = 0.0;
@@ -1049,6 +1079,7 @@ moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *
         spec_re[r].assign(sg.size() * N, 0.0);
         spec_im[r].assign(sg.size() * N, 0.0);
         for (size_t j = 0; j < sg.size(); ++j) {
+            if (sg[j].a < 0) continue;   // padding slot: zero spectrum
             for (int dx = 0; dx < K; ++dx) {
                 float tr, ti;
                 tap_at(jones, P, K, taps, sg[j].a, po, sg[j].q, sg[j].dy, dx, &tr, &ti);
@@ -1098,7 +1129,8 @@ moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *
     rs->row_sh.assign((size_t)P * N, sh);
     rs->row_inv.assign((size_t)P * N, 1.f / sh);
     // B images: row n < KX -> real part of H at kx = tile*KX + n; n >= KX -> imaginary part.
-    //   Hr = sum_j yr Sr - yi Si ; Hi = sum_j yr Si + yi Sr   (k = 2j: yr, k = 2j+1: yi)
+    //   Hr = sum_j yr Sr - yi Si ; Hi = sum_j yr Si + yi Sr
+    // Slot j = 32 c + i: chunk c's K rows 64 c + i (yr, the real plane's tile) and 64 c + 32 + i (yi).
     rs->bimg_off.assign((size_t)P * N * ntiles, 0);
     rs->bimg.clear();
     for (size_t r = 0; r < (size_t)P * N; ++r) {
@@ -1115,10 +1147,11 @@ moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *
                     const double sr = spec_re[r][(size_t)j * N + kx] * scale, si = spec_im[r][(size_t)j * N + kx] * scale;
                     const double b0 = imag_row ? si : sr;       // coefficient of yr
                     const double b1 = imag_row ? sr : -si;      // coefficient of yi
-                    for (int k = 2 * j; k <= 2 * j + 1; ++k) {
+                    const int kre = 64 * (j / 32) + (j % 32);
+                    for (int k = kre; k <= kre + 32; k += 32) {
                         const size_t off = ((size_t)(n >> 3) * (kp >> 3) * 128 + (size_t)(k >> 3) * 128 +
                                             (size_t)(n & 7) * 16 + (size_t)(k & 7) * 2) / 2;
-                        img[off] = __double2half(k == 2 * j ? b0 : b1);
+                        img[off] = __double2half(k == kre ? b0 : b1);
                     }
                 }
             }
@@ -1629,6 +1662,10 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
         off += align_up(pl->y_bytes, 1024);
         if (encode_field_map(&pl->h_map, pl->d_H, pl->N, pl->P, pl->Cb, pl->Tb) != cudaSuccess)
             return fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded");
+        const long long rows = (long long)pl->Cb * (pl->A * pl->P + kRowSpecPad);
+        if (encode_plane_map(&pl->a_map_re, pl->d_yre, pl->Tb, rows) != cudaSuccess ||
+            encode_plane_map(&pl->a_map_im, pl->d_yim, pl->Tb, rows) != cudaSuccess)
+            return fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded");
         pl->h_map_nt = pl->Tb;
     }
     const long long tstride = (long long)pl->C * pl->A * pl->P;
@@ -1752,7 +1789,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         };
         if (pl->tc) {
             // the tensor-core path works on 128 samples per product
-            const size_t per_c = 128 * per + (size_t)n_ant * n_pol * 128 * 4;
+            const size_t per_c = 128 * per + ((size_t)n_ant * n_pol + kRowSpecPad) * 128 * 4;
             pl->Tb = 128;
             pl->Cb = (int)balance(std::max(1LL, std::min<long long>(n_chan, budget / (long long)per_c)));
         } else {
@@ -1781,22 +1818,27 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         RowSpec rs;
         if ((s = build_rowspec(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps, &rs)) != MOFF_OK) return bail(s);
         pl->rs_kp_max = std::max(rs.kp_max, 16);
-        pl->rs_max_seg = std::max(rs.max_seg, 1);
         pl->rs_inv_sw = rs.inv_sw;
-        pl->rs_smem = rowspec_smem_bytes(grid_n, pl->rs_kp_max, pl->rs_max_seg);
+        pl->rs_smem = rowspec_smem_bytes(grid_n, pl->rs_kp_max);
         const int items = n_pol * grid_n * rs.ntiles;
         pl->rs_cgroups = std::max(1, std::min(pl->Cb, (4 * 152 + items - 1) / items));
         if (const char *e = getenv("MOFF_TC_CGROUPS")) pl->rs_cgroups = std::max(1, std::min(pl->Cb, atoi(e)));
-        const size_t ny = (size_t)pl->Cb * n_ant * n_pol * pl->Tb;
+        const size_t ny = (size_t)pl->Cb * (n_ant * n_pol + kRowSpecPad) * pl->Tb;
         if ((s = palloc(pl, &pl->d_rs_kp, rs.kp.size() * 4)) != MOFF_OK) return bail(s);
-        if ((s = palloc(pl, &pl->d_rs_seg_off, rs.seg_off.size() * 8)) != MOFF_OK) return bail(s);
-        if ((s = palloc(pl, &pl->d_rs_seg_y, std::max<size_t>(rs.seg_y.size(), 1) * 4)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_rs_chunk_off, rs.chunk_off.size() * 4)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_rs_chunk_row, std::max<size_t>(rs.chunk_row.size(), 1) * 4)) != MOFF_OK)
+            return bail(s);
+        if ((s = palloc(pl, &pl->d_rs_perm, rs.perm.size() * 4)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_rs_bimg_off, rs.bimg_off.size() * 8)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_rs_bimg, std::max<size_t>(rs.bimg.size(), 8) * 2)) != MOFF_OK) return bail(s);
         pl->y_bytes = ny * 2;
         if (!pl->served) {
             if ((s = palloc(pl, &pl->d_yre, ny * 2)) != MOFF_OK) return bail(s);
             if ((s = palloc(pl, &pl->d_yim, ny * 2)) != MOFF_OK) return bail(s);
+            const long long rows = (long long)pl->Cb * (n_ant * n_pol + kRowSpecPad);
+            if (encode_plane_map(&pl->a_map_re, pl->d_yre, pl->Tb, rows) != cudaSuccess ||
+                encode_plane_map(&pl->a_map_im, pl->d_yim, pl->Tb, rows) != cudaSuccess)
+                return bail(fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded"));
         }
         if ((s = palloc(pl, &pl->d_sy, (size_t)n_chan * 4)) != MOFF_OK) return bail(s);
         if ((s = palloc(pl, &pl->d_err, 16)) != MOFF_OK) return bail(s);
@@ -1806,9 +1848,11 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             cudaMemcpy(pl->d_rs_row_inv, rs.row_inv.data(), rs.row_inv.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(MOFF_ECUDA, "tensor-core row scales upload failed"));
         if (cudaMemcpy(pl->d_rs_kp, rs.kp.data(), rs.kp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(pl->d_rs_seg_off, rs.seg_off.data(), rs.seg_off.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-            (!rs.seg_y.empty() &&
-             cudaMemcpy(pl->d_rs_seg_y, rs.seg_y.data(), rs.seg_y.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+            cudaMemcpy(pl->d_rs_chunk_off, rs.chunk_off.data(), rs.chunk_off.size() * 4, cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            (!rs.chunk_row.empty() && cudaMemcpy(pl->d_rs_chunk_row, rs.chunk_row.data(), rs.chunk_row.size() * 4,
+                                                 cudaMemcpyHostToDevice) != cudaSuccess) ||
+            cudaMemcpy(pl->d_rs_perm, rs.perm.data(), rs.perm.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(pl->d_rs_bimg_off, rs.bimg_off.data(), rs.bimg_off.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
             (!rs.bimg.empty() &&
              cudaMemcpy(pl->d_rs_bimg, rs.bimg.data(), rs.bimg.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) ||

@@ -82,13 +82,13 @@ struct ColArgs {
 // FP16 tensor-core gridding + row transform: per (pol, grid row, kx tile) a
 // product of the row's segment voltages with the segments' row spectra.
 struct RowSpecArgs {
-    int P, nt, nc, c0, AP, Tpad, kp_max;
-    const int *kp;             // [P*N] padded contraction length (real) per (pol, row); 0 = empty row
-    const long long *seg_off;  // [P*N + 1] segments of each (pol, row)
-    const int *seg_y;          // voltage index (antenna * P + input pol) of each segment
+    int P, nt, nc, c0, AP, Tpad, kp_max;   // AP: plane rows per channel (voltages + kRowSpecPad)
+    const int *kp;             // [P*N] contraction length (64 per chunk) per (pol, row); 0 = empty row
+    const int *chunk_off;      // [P*N + 1] first chunk of each (pol, row)
+    const int *chunk_row;      // plane row (within a channel) of each chunk's first voltage; a chunk
+                               // is 32 consecutive plane rows, read as a TMA tile of re and of im
     const long long *bimg_off; // [P*N*ntiles] byte offset of each B image
     const __half *bimg;        // row spectra, K-major core-matrix images [2*KX][kp]
-    const __half *yre, *yim;   // [nc][AP][Tpad] weighted, scaled voltages
     const float *sy;           // [C] voltage scales (powers of two)
     float inv_sw;              // 1 / spectrum scale (power of two)
     const float *row_sh;       // [P*N] FP16 output scale (one power of two for every row)
@@ -200,11 +200,13 @@ std::vector<float2> pass_twiddles_for(int n);   // pass-twiddle table of the n-p
 
 // Row spectra of the kernel rows for the tensor-core path (host side).
 struct RowSpec {
-    int kp_max = 0, max_seg = 0, ntiles = 1;
+    int kp_max = 0, ntiles = 1;
     float inv_sw = 1.f;
-    std::vector<int> kp, seg_y;
+    std::vector<int> kp;                        // [P*N] 64 per chunk
+    std::vector<int> chunk_off, chunk_row;      // chunks per (pol, row); first plane row of each
+    std::vector<int> perm;                      // [A*P] plane row -> voltage index (antennas by anchor row)
     std::vector<float> row_sh, row_inv;         // FP16 field scale and its inverse (equal for every (pol, row))
-    std::vector<long long> seg_off, bimg_off;   // bimg_off in elements
+    std::vector<long long> bimg_off;            // in elements
     std::vector<__half> bimg;
 };
 moff_status build_rowspec(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, RowSpec *rs);
@@ -227,15 +229,21 @@ cudaError_t launch_pfb_reorder(const PfbArgs &a, cudaStream_t st);
 cudaError_t launch_to_f32(const double *acc, float *out, long long n, cudaStream_t st);
 
 // Tensor-core path (moff_tc_kernels.cu).
-constexpr int kRowSpecMaxK = 256;   // largest contraction length (2 x segments per row, padded) held on chip
-size_t rowspec_smem_bytes(int N, int kp_max, int max_seg);
+constexpr int kRowSpecMaxK = 256;   // largest contraction length (64 per 32-voltage chunk) held on chip
+size_t rowspec_smem_bytes(int N, int kp_max);
 int rowspec_ntiles(int N);
 cudaError_t launch_gain_scale(const float2 *gains, int C, int AP, float *sy, cudaStream_t st);
+// Voltage planes: plane row v < AP of a channel holds voltage perm[v] (antenna * P + input
+// pol); rows AP .. APpad - 1 are zero.  APpad = AP + kRowSpecPad.
+constexpr int kRowSpecPad = 32;
 cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc, int AP,
-                             const float2 *gains, const float *sy, int Tpad, __half *yre, __half *yim,
-                             cudaStream_t st);
-cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap, int cgroups, size_t smem,
-                           cudaStream_t st);
+                             int APpad, const float2 *gains, const float *sy, const int *perm, int Tpad, __half *yre,
+                             __half *yim, cudaStream_t st);
+cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap, const CUtensorMap &amap_re,
+                           const CUtensorMap &amap_im, int cgroups, size_t smem, cudaStream_t st);
+// Tensor map of one FP16 voltage plane [rows][Tpad] (rows = Cb * A * P), box 64 samples x
+// 32 rows, 128-byte swizzle, rows past the end read as zero: the A loads of k_rowspec_tc.
+cudaError_t encode_plane_map(CUtensorMap *map, void *plane, int Tpad, long long rows);
 // Tensor map of the FP16 row-transformed field [nt][Cb][P*N][N] (half2 as 32-bit
 // elements), box 32 kx x 32 samples, 128-byte swizzle: the store target of
 // k_rowspec_tc.  Stores of samples >= nt fall outside the map and are dropped.

@@ -176,6 +176,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// ---- TMA tile load (global -> shared) of one box of a 2-D tensor map, completing
+// `bytes` of transaction count on an mbarrier armed with mbar_arrive_expect_tx.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+// x (innermost, elements) times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst_smem, const void *tmap, int x, int y, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(dst_smem),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(mbar))
+        : "memory");
+}
+
 // ---- TMA bulk tensor store (shared -> global) of one box of a 4-D tensor map,
 // tracked by this thread's bulk async-groups.  Coordinates are in elements,
 // innermost first; the innermost one times the element size must be a

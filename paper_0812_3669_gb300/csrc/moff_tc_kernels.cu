@@ -14,9 +14,11 @@
 // the FP32 column kernel.
 //
 //   k_gain_scale   per-channel power-of-two scale keeping weighted voltages in FP16 range
-//   k_volt_prep    decode, weight, scale and transpose the voltages to FP16 planes [c][voltage][t]
+//   k_volt_prep    decode, weight, scale and transpose the voltages to FP16 planes [c][voltage][t],
+//                  antennas ordered by anchor row so a grid row's segments are consecutive plane rows
 //   k_rowspec_tc   per (pol, row, kx tile): B = row spectra resident in shared memory,
-//                  A = 128 samples of the row's segment voltages (cp.async, MN-major),
+//                  A = 128 samples of the row's segment voltages (TMA tiles of 32 plane rows,
+//                  128-byte swizzled, MN-major),
 //                  D = TMEM (double buffered), epilogue writes the row-transformed field in
 //                  FP16 under an exact power-of-two scale (undone by the column kernel).
 #include <cuda_fp16.h>
@@ -61,53 +63,76 @@ __global__ void k_gain_scale(const float2 *__restrict__ gains, int AP, float *__
 }
 
 // Voltages of samples [t0, t0+nt) of channels [c0, c0+nc) -> FP16 planes
-// Yre/Yim [nc][AP][Tpad] (t contiguous), zero for t >= nt.  Tile 32 t x 64 voltages:
-// each thread loads four voltages of one sample (4 bytes) and stores two samples of
-// one voltage (half2) per plane.
+// Yre/Yim [nc][APpad][Tpad] (t contiguous), zero for t >= nt and for rows v >= AP (the
+// pad rows a chunk running past the last voltage reads); plane row v < AP holds voltage
+// perm[v].  A CTA stages the voltage bytes of TT samples of one channel (coalesced
+// 16-byte loads) and writes every plane row's TT samples (half2 per sample pair).
 __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ volt, long long tstride, int t0, int nt,
-                                                   int c0, int AP, const float2 *__restrict__ gains,
-                                                   const float *__restrict__ sy, int Tpad, __half *__restrict__ yre,
-                                                   __half *__restrict__ yim) {
-    __shared__ float2 tile[32][65];
-    const int cl = blockIdx.z, c = c0 + cl;
-    const int v0 = blockIdx.x * 64, tb = blockIdx.y * 32;
+                                                   int c0, int AP, int APpad, const float2 *__restrict__ gains,
+                                                   const float *__restrict__ sy, const int *__restrict__ perm, int Tpad,
+                                                   int TT, __half *__restrict__ yre, __half *__restrict__ yim) {
+    extern __shared__ __align__(16) unsigned char s_v[];   // [TT][APr] voltage bytes
+    const int cl = blockIdx.y, c = c0 + cl;
+    const int tb = blockIdx.x * TT;
+    const int APr = (AP + 15) & ~15, nq = APr / 16;
     const float s = sy[c];
-    const bool vec = (AP & 3) == 0 && (tstride & 3) == 0 && ((uintptr_t)volt & 3) == 0;
-    for (int i = threadIdx.x; i < 32 * 16; i += 256) {
-        const int tt = i / 16, v4 = (i % 16) * 4;
-        const int t = tb + tt;
-        uint32_t b4 = 0;
+    const uint8_t *vc = volt + (long long)c * AP;
+    const bool vec = (AP & 15) == 0 && (tstride & 15) == 0 && ((reinterpret_cast<uintptr_t>(vc)) & 15) == 0;
+    for (int i = threadIdx.x; i < TT * nq; i += blockDim.x) {
+        const int tt = i / nq, q = i - tt * nq, t = tb + tt;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (t < nt) {
-            const uint8_t *src = volt + (long long)(t0 + t) * tstride + (long long)c * AP + v0 + v4;
-            if (vec && v0 + v4 + 3 < AP) {
-                b4 = *reinterpret_cast<const uint32_t *>(src);
+            const uint8_t *src = vc + (long long)(t0 + t) * tstride + q * 16;
+            if (vec) {
+                v = *reinterpret_cast<const uint4 *>(src);
             } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (v0 + v4 + u < AP) b4 |= (uint32_t)src[u] << (8 * u);
+                uint32_t w[4] = {0u, 0u, 0u, 0u};
+                for (int u = 0; u < 16 && q * 16 + u < AP; ++u) w[u >> 2] |= (uint32_t)src[u] << (8 * (u & 3));
+                v = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int vi = v0 + v4 + u;
-            float2 y = make_float2(0.f, 0.f);
-            if (t < nt && vi < AP) {
-                y = cmul(gains[(long long)c * AP + vi], decode4_tc((b4 >> (8 * u)) & 0xffu));
-                y.x *= s;
-                y.y *= s;
-            }
-            tile[tt][v4 + u] = y;
-        }
+        *reinterpret_cast<uint4 *>(s_v + tt * APr + q * 16) = v;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 64 * 16; i += 256) {
-        const int v = i / 16, tt = (i % 16) * 2;
-        const int t = tb + tt, vi = v0 + v;
-        if (vi < AP && t < Tpad) {
-            const long long o = ((long long)cl * AP + vi) * Tpad + t;   // t even, Tpad even: 4-byte aligned
-            *reinterpret_cast<__half2 *>(yre + o) = __floats2half2_rn(tile[tt][v].x, tile[tt + 1][v].x);
-            *reinterpret_cast<__half2 *>(yim + o) = __floats2half2_rn(tile[tt][v].y, tile[tt + 1][v].y);
+    if (TT >= 8) {   // 8 samples of one plane row per thread: one 16-byte store per plane
+        const int ng = TT / 8;
+        for (int i = threadIdx.x; i < APpad * ng; i += blockDim.x) {
+            const int v = i / ng, t8 = 8 * (i - v * ng);
+            uint4 re = make_uint4(0u, 0u, 0u, 0u), im = re;
+            if (v < AP) {
+                const int sv = perm[v];
+                const float2 g = gains[(long long)c * AP + sv];
+                __half2 hr[4], hi[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 y0 = cmul(g, decode4_tc(s_v[(t8 + 2 * u) * APr + sv]));
+                    const float2 y1 = cmul(g, decode4_tc(s_v[(t8 + 2 * u + 1) * APr + sv]));
+                    hr[u] = __floats2half2_rn(y0.x * s, y1.x * s);
+                    hi[u] = __floats2half2_rn(y0.y * s, y1.y * s);
+                }
+                re = *reinterpret_cast<const uint4 *>(hr);
+                im = *reinterpret_cast<const uint4 *>(hi);
+            }
+            const long long o = ((long long)cl * APpad + v) * Tpad + tb + t8;   // 16-byte aligned (Tpad % 8 == 0)
+            *reinterpret_cast<uint4 *>(yre + o) = re;
+            *reinterpret_cast<uint4 *>(yim + o) = im;
         }
+        return;
+    }
+    const int np = TT / 2;
+    for (int i = threadIdx.x; i < APpad * np; i += blockDim.x) {
+        const int v = i / np, tp = 2 * (i - v * np), t = tb + tp;
+        __half2 re = __floats2half2_rn(0.f, 0.f), im = re;
+        if (v < AP) {
+            const int sv = perm[v];
+            const float2 g = gains[(long long)c * AP + sv];
+            float2 y0 = cmul(g, decode4_tc(s_v[tp * APr + sv])), y1 = cmul(g, decode4_tc(s_v[(tp + 1) * APr + sv]));
+            re = __floats2half2_rn(y0.x * s, y1.x * s);
+            im = __floats2half2_rn(y0.y * s, y1.y * s);
+        }
+        const long long o = ((long long)cl * APpad + v) * Tpad + t;   // t even, Tpad even: 4-byte aligned
+        *reinterpret_cast<__half2 *>(yre + o) = re;
+        *reinterpret_cast<__half2 *>(yim + o) = im;
     }
 }
 
@@ -120,34 +145,28 @@ struct TcShape {
     static constexpr int TCOLS = 2 * NT <= 32 ? 32 : 2 * NT;   // two TMEM accumulators
 };
 
-__device__ __forceinline__ void cp_async16_tc(void *smem_dst, const void *gmem_src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_u32(smem_dst)), "l"(gmem_src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_tc() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all_tc() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait_tc() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
-
 // Warp roles: warps 0-3 drain the TMEM accumulators (one lane quarter each),
-// warps 4-15 stage A in K-chunks of 64 with cp.async, warp 16 issues the MMAs
-// (one lane).  A: 3-stage ring of [128 samples x 64] MN-major chunks; B:
-// resident; accumulators: two in TMEM; epilogue: each warp converts its 32
-// samples x 32 kx to FP16 into a 128-byte-swizzled box in shared memory and
-// one lane hands it to the TMA unit (bulk tensor store), two boxes in flight
-// per warp.  Per-thread global stores from four warps could not keep enough
-// writes in flight; the bulk stores can.
-constexpr int kEpiWarps = 4, kProdWarps = 12;   // 12 producer warps keep more A gathers in flight
-constexpr int kTcRoleThreads = (kEpiWarps + kProdWarps + 1) * 32;
+// one lane of warp 4 loads A with TMA, one lane of warp 5 issues the MMAs.
+// A: 3-stage ring of K-chunks of 64 = 32 consecutive plane rows (real parts,
+// then imaginary parts) x 128 samples, MN-major with the 128-byte swizzle: two
+// 64-sample halves of 8 KB, each 64 rows of 128 bytes; four TMA tiles of
+// 64 samples x 32 rows per chunk.  B: resident; accumulators: two in TMEM;
+// epilogue: each warp converts its 32 samples x 32 kx to FP16 into a
+// 128-byte-swizzled box in shared memory and one lane hands it to the TMA unit
+// (bulk tensor store), two boxes in flight per warp.
+constexpr int kEpiWarps = 4;
+constexpr int kTcRoleThreads = (kEpiWarps + 2) * 32;
 constexpr int kAStages = 3, kKChunk = 64;
 constexpr int kAChunkBytes = 128 * kKChunk * 2;
+constexpr int kAHalfBytes = kAChunkBytes / 2;          // one 64-sample half: 64 rows x 128 bytes
 constexpr int kBoxBytes = 32 * 128;                 // 32 samples x 32 kx x half2
 constexpr int kEpiBufs = 2;                         // boxes per warp
 constexpr long long kWaitCycles = 4000000000LL;     // ~2 s at the SM clock
 
 template <int N>
 __global__ void __launch_bounds__(kTcRoleThreads, 1)
-    k_rowspec_tc(const RowSpecArgs a, const __grid_constant__ CUtensorMap hmap) {
+    k_rowspec_tc(const RowSpecArgs a, const __grid_constant__ CUtensorMap hmap,
+                 const __grid_constant__ CUtensorMap amap_re, const __grid_constant__ CUtensorMap amap_im) {
     using S = TcShape<N>;
     constexpr int KX = S::KX, NT = S::NT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -156,7 +175,7 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
     const int pr = item / S::NTILES;
     const int p = pr / N, ry = pr % N;
     const int kp = a.kp[pr];
-    const int nseg = (int)(a.seg_off[pr + 1] - a.seg_off[pr]);
+    const int ch0 = a.chunk_off[pr];
 
     const int cper = (a.nc + gridDim.y - 1) / gridDim.y;
     const int cb = blockIdx.y * cper, ce = min(a.nc, cb + cper);
@@ -177,31 +196,29 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
         }
         return;
     }
-    const int nchunk = (kp + kKChunk - 1) / kKChunk;
+    const int nchunk = kp / kKChunk;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // swizzled TMA boxes need 1024-byte alignment: round the base up (the size includes the slack)
     unsigned char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *sB = smem;                                  // NT x kp, K-major (resident)
-    unsigned char *sA = sB + (size_t)NT * a.kp_max * 2;        // kAStages x [128 x 64], MN-major
+    unsigned char *sA = sB + (size_t)NT * a.kp_max * 2;        // kAStages x [128 x 64], MN-major, 1024-aligned
     unsigned char *sE = sA + (size_t)kAStages * kAChunkBytes;  // [4 warps][kEpiBufs] boxes, 1024-aligned
     uint64_t *bars = reinterpret_cast<uint64_t *>(sE + kEpiWarps * kEpiBufs * kBoxBytes);
     uint64_t *a_full = bars, *a_empty = bars + kAStages, *d_full = bars + 2 * kAStages,
              *d_empty = bars + 2 * kAStages + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kAStages + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
-    int *s_seg = reinterpret_cast<int *>(tslot + 2);
 
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.bimg + a.bimg_off[item]);
         uint4 *dst = reinterpret_cast<uint4 *>(sB);
         const int n16 = NT * kp * 2 / 16;
         for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
-        for (int j = tid; j < nseg; j += blockDim.x) s_seg[j] = a.seg_y[a.seg_off[pr] + j];
     }
     if (tid == 0) {
         for (int b = 0; b < kAStages; ++b) {
-            tc::mbar_init(&a_full[b], kProdWarps * 32);
+            tc::mbar_init(&a_full[b], 1);        // the producer's arrive + the chunk's TMA bytes
             tc::mbar_init(&a_empty[b], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -220,48 +237,40 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
 
-    if (warp >= kEpiWarps && warp < kEpiWarps + kProdWarps) {
-        // ---------------- producers: chunk g (global counter) into stage g % kAStages.
-        // Up to kAStages chunks are in flight: after issuing chunk g the
-        // producers wait only for chunk g - (kAStages - 1) and release it.
-        const int ptid = tid - kEpiWarps * 32;
-        int g = 0;
-        for (int i = 0; i < nitems && !*abort_flag; ++i) {
-            const int cl = cb + i / ntb, t0b = (i % ntb) * 128;
-            const __half *re = a.yre + (long long)cl * a.AP * a.Tpad + t0b;
-            const __half *im = a.yim + (long long)cl * a.AP * a.Tpad + t0b;
-            for (int ch = 0; ch < nchunk; ++ch, ++g) {
-                const int st = g % kAStages;
-                if (!tc::mbar_wait_abortable(&a_empty[st], (uint32_t)(((g / kAStages) & 1) ^ 1), kWaitCycles,
-                                             abort_flag))
-                    break;
-                unsigned char *sa = sA + st * kAChunkBytes;
-                for (int q = ptid; q < kKChunk * 16; q += kProdWarps * 32) {
-                    // a warp covers 8 consecutive k x 4 sample groups: four 128-byte bank
-                    // sweeps in shared memory, 64 contiguous bytes per segment in global
-                    const int kk = ((q >> 7) << 3) | (q & 7), m8 = (q >> 3) & 15;
-                    const int k = ch * kKChunk + kk, j = k >> 1;
-                    unsigned char *d = sa + m8 * 128 + (kk >> 3) * 2048 + (kk & 7) * 16;
-                    if (k < kp && j < nseg) {
-                        cp_async16_tc(d, ((k & 1) ? im : re) + (long long)s_seg[j] * a.Tpad + m8 * 8);
-                    } else {
-                        *reinterpret_cast<uint4 *>(d) = make_uint4(0u, 0u, 0u, 0u);
+    if (warp == kEpiWarps) {
+        // ---------------- producer (one lane): chunk g (global counter) into stage g % kAStages,
+        // four TMA tiles (re / im x two 64-sample halves) completing on a_full.
+        if (lane == 0) {
+            int g = 0;
+            for (int i = 0; i < nitems && !*abort_flag; ++i) {
+                const int cl = cb + i / ntb, t0b = (i % ntb) * 128;
+                bool ok = true;
+                for (int ch = 0; ch < nchunk; ++ch, ++g) {
+                    const int st = g % kAStages;
+                    if (!tc::mbar_wait_abortable(&a_empty[st], (uint32_t)(((g / kAStages) & 1) ^ 1), kWaitCycles,
+                                                 abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = tc::smem_u32(sA + st * kAChunkBytes);
+                    const int y = cl * a.AP + a.chunk_row[ch0 + ch];
+                    tc::mbar_arrive_expect_tx(&a_full[st], kAChunkBytes);
+#pragma unroll
+                    for (int hm = 0; hm < 2; ++hm) {
+                        tc::tma_load_2d(sa + hm * kAHalfBytes, &amap_re, t0b + 64 * hm, y, &a_full[st]);
+                        tc::tma_load_2d(sa + hm * kAHalfBytes + kAHalfBytes / 2, &amap_im, t0b + 64 * hm, y,
+                                        &a_full[st]);
                     }
                 }
-                cp_async_commit_tc();
-                if (g >= kAStages - 1) {
-                    cp_async_wait_tc<kAStages - 1>();          // chunk g - (kAStages-1) has landed
-                    tc::fence_async_smem();
-                    tc::mbar_arrive(&a_full[(g - (kAStages - 1)) % kAStages]);
-                }
+                if (!ok) break;
             }
+            // tiles still landing (the MMA lane stopped early): let them finish before the
+            // shared memory is released
+            for (int gg = g - kAStages > 0 ? g - kAStages : 0; gg < g; ++gg)
+                tc::mbar_wait_bounded(&a_full[gg % kAStages], (uint32_t)((gg / kAStages) & 1), kWaitCycles);
         }
-        // release the chunks still in flight, oldest first
-        const int g0 = g - (kAStages - 1) > 0 ? g - (kAStages - 1) : 0;
-        cp_async_wait_all_tc();
-        tc::fence_async_smem();
-        for (int gg = g0; gg < g; ++gg) tc::mbar_arrive(&a_full[gg % kAStages]);
-    } else if (warp == kEpiWarps + kProdWarps) {
+        __syncwarp();
+    } else if (warp == kEpiWarps + 1) {
         // ---------------- MMA issuer (one lane)
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_f16(128, NT, /*a_mn=*/true, /*b_mn=*/false);
@@ -280,9 +289,9 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
                     if (!ok) break;
                     tc::fence_after_sync();
                     const uint32_t sa = tc::smem_u32(sA + st * kAChunkBytes);
-                    const int kend = min(kKChunk, kp - ch * kKChunk);
-                    for (int ks = 0; ks < kend / 16; ++ks) {
-                        const uint64_t ad = tc::smem_desc(sa + ks * 2 * 2048, 2048, 128);   // MN-major: LBO = K stride
+                    for (int ks = 0; ks < kKChunk / 16; ++ks) {
+                        // 128-byte swizzled MN-major: LBO = the 64-sample halves' stride, SBO = 8 rows
+                        const uint64_t ad = tc::smem_desc_sw128(sa + ks * 16 * 128, kAHalfBytes, 1024);
                         const uint64_t bd = tc::smem_desc(sbb + (ch * (kKChunk / 8) + 2 * ks) * 128, 128, sb_sbo);
                         tc::mma_f16(d, ad, bd, idesc, ch > 0 || ks > 0);
                     }
@@ -337,7 +346,6 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
         if (lane == 0) tc::bulk_wait_all();
     }
     if (*abort_flag && tid == 0) atomicExch(a.err, tc::kErrWaitTimeout);
-    cp_async_wait_all_tc();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -346,10 +354,10 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
 
 }  // namespace
 
-size_t rowspec_smem_bytes(int N, int kp_max, int max_seg) {
+size_t rowspec_smem_bytes(int N, int kp_max) {
     const int KX = N < 128 ? N : 128, NT = 2 * KX;
     size_t b = 1024 + (size_t)NT * kp_max * 2 + (size_t)kAStages * kAChunkBytes +
-               (size_t)kEpiWarps * kEpiBufs * kBoxBytes + (size_t)(2 * kAStages + 4) * 8 + 8 + (size_t)max_seg * 4;
+               (size_t)kEpiWarps * kEpiBufs * kBoxBytes + (size_t)(2 * kAStages + 4) * 8 + 8;
     b = (b + 127) & ~(size_t)127;
     // one CTA per SM: two CTAs must never wait on each other's TMEM columns
     return b < 120 * 1024 ? 120 * 1024 : b;
@@ -363,33 +371,61 @@ cudaError_t launch_gain_scale(const float2 *gains, int C, int AP, float *sy, cud
 }
 
 cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc, int AP,
-                             const float2 *gains, const float *sy, int Tpad, __half *yre, __half *yim,
-                             cudaStream_t st) {
-    dim3 grid((AP + 63) / 64, (Tpad + 31) / 32, nc);
-    k_volt_prep<<<grid, 256, 0, st>>>(volt, tstride, t0, nt, c0, AP, gains, sy, Tpad, yre, yim);
+                             int APpad, const float2 *gains, const float *sy, const int *perm, int Tpad, __half *yre,
+                             __half *yim, cudaStream_t st) {
+    // samples per CTA: 32, or fewer (even, dividing Tpad) so the staged bytes stay within 96 KB
+    const size_t APr = (size_t)((AP + 15) & ~15);
+    int TT = 32;
+    while (TT > 2 && (TT * APr > 96 * 1024 || Tpad % TT)) TT /= 2;
+    if (Tpad % TT || TT * APr > 200 * 1024) return cudaErrorInvalidValue;
+    const size_t smem = TT * APr;
+    cudaError_t e = cudaFuncSetAttribute(k_volt_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(Tpad / TT, nc);
+    k_volt_prep<<<grid, 256, smem, st>>>(volt, tstride, t0, nt, c0, AP, APpad, gains, sy, perm, Tpad, TT, yre, yim);
     return cudaGetLastError();
 }
 
 template <int N>
-cudaError_t launch_rowspec_t(const RowSpecArgs &a, const CUtensorMap &hmap, int cgroups, size_t smem,
-                             cudaStream_t st) {
+cudaError_t launch_rowspec_t(const RowSpecArgs &a, const CUtensorMap &hmap, const CUtensorMap &are,
+                             const CUtensorMap &aim, int cgroups, size_t smem, cudaStream_t st) {
     auto k = k_rowspec_tc<N>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<dim3(a.P * N * TcShape<N>::NTILES, cgroups), kTcRoleThreads, smem, st>>>(a, hmap);
+    k<<<dim3(a.P * N * TcShape<N>::NTILES, cgroups), kTcRoleThreads, smem, st>>>(a, hmap, are, aim);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap, int cgroups, size_t smem,
-                           cudaStream_t st) {
+cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap, const CUtensorMap &amap_re,
+                           const CUtensorMap &amap_im, int cgroups, size_t smem, cudaStream_t st) {
     switch (N) {
-        case 32: return launch_rowspec_t<32>(a, hmap, cgroups, smem, st);
-        case 64: return launch_rowspec_t<64>(a, hmap, cgroups, smem, st);
-        case 128: return launch_rowspec_t<128>(a, hmap, cgroups, smem, st);
-        case 256: return launch_rowspec_t<256>(a, hmap, cgroups, smem, st);
-        case 512: return launch_rowspec_t<512>(a, hmap, cgroups, smem, st);
+        case 32: return launch_rowspec_t<32>(a, hmap, amap_re, amap_im, cgroups, smem, st);
+        case 64: return launch_rowspec_t<64>(a, hmap, amap_re, amap_im, cgroups, smem, st);
+        case 128: return launch_rowspec_t<128>(a, hmap, amap_re, amap_im, cgroups, smem, st);
+        case 256: return launch_rowspec_t<256>(a, hmap, amap_re, amap_im, cgroups, smem, st);
+        case 512: return launch_rowspec_t<512>(a, hmap, amap_re, amap_im, cgroups, smem, st);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t encode_plane_map(CUtensorMap *map, void *plane, int Tpad, long long rows) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const cuuint64_t dims[2] = {(cuuint64_t)Tpad, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Tpad * 2};
+    const cuuint32_t box[2] = {64, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, plane, dims, strides, box,
+                                                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t encode_field_map(CUtensorMap *map, void *H, int N, int P, int Cb, int nt) {
