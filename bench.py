@@ -102,12 +102,24 @@ def flops_per_snapshot(kind, A=WL["n_ant"], P=WL["n_pol"], N=WL["grid_n"], K=WL[
 def tc_row_flops_per_snapshot(pos, N=WL["grid_n"], P=WL["n_pol"], K=WL["ksize"]):
     """Tensor-core flops per channel-snapshot of the row contraction as executed:
     per (pol, grid row, kx tile of KX = min(N, 128)) 2 x (2 KX output columns:
-    real and imaginary parts) x the padded contraction length."""
+    real and imaginary parts) x the contraction length (64 per chunk of 32 voltages,
+    padding included)."""
     import numpy as np
     KX = min(N, 128)
-    anc = np.floor(np.asarray(pos) + 0.5).astype(int) % N
-    rows = np.bincount(((anc[:, 1][:, None] + np.arange(K)[None, :] - K // 2) % N).ravel(), minlength=N)
-    kp = ((2 * rows + 15) // 16) * 16
+    h = K // 2
+    ay = np.floor(np.asarray(pos)[:, 1] + 0.5).astype(int) % N
+    cnt = np.bincount(ay, minlength=N)          # antennas per anchor row
+    kp = np.zeros(N)
+    for ry in range(N):
+        # the antennas anchored in the cyclic window [ry - h, ry + h]: one run, two where it wraps;
+        # each run is cut into chunks of 32 voltages, 64 contraction rows (real, imaginary) each
+        if ry - h < 0:
+            runs = [cnt[: ry + h + 1].sum(), cnt[N + ry - h:].sum()]
+        elif ry + h >= N:
+            runs = [cnt[ry - h:].sum(), cnt[: ry + h - N + 1].sum()]
+        else:
+            runs = [cnt[ry - h: ry + h + 1].sum()]
+        kp[ry] = sum(64 * ((n + 31) // 32) for n in runs)
     return P * (N // KX) * float(np.sum(2 * (2 * KX) * kp))
 
 
