@@ -145,22 +145,22 @@ struct TcShape {
     static constexpr int TCOLS = 2 * NT <= 32 ? 32 : 2 * NT;   // two TMEM accumulators
 };
 
-// Warp roles: warps 0-3 drain the TMEM accumulators (one lane quarter each),
-// one lane of warp 4 loads A with TMA, one lane of warp 5 issues the MMAs.
+// Warp roles: warps 0-7 drain the TMEM accumulators (lane quarter w % 4, kx half
+// w / 4), one lane of warp 8 loads A with TMA, one lane of warp 9 issues the MMAs.
 // A: 3-stage ring of K-chunks of 64 = 32 consecutive plane rows (real parts,
 // then imaginary parts) x 128 samples, MN-major with the 128-byte swizzle: two
 // 64-sample halves of 8 KB, each 64 rows of 128 bytes; four TMA tiles of
 // 64 samples x 32 rows per chunk.  B: resident; accumulators: two in TMEM;
 // epilogue: each warp converts its 32 samples x 32 kx to FP16 into a
 // 128-byte-swizzled box in shared memory and one lane hands it to the TMA unit
-// (bulk tensor store), two boxes in flight per warp.
-constexpr int kEpiWarps = 4;
+// (bulk tensor store); a warp reuses its box once the store has read it.
+constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, each draining half of the kx columns
 constexpr int kTcRoleThreads = (kEpiWarps + 2) * 32;
 constexpr int kAStages = 3, kKChunk = 64;
 constexpr int kAChunkBytes = 128 * kKChunk * 2;
 constexpr int kAHalfBytes = kAChunkBytes / 2;          // one 64-sample half: 64 rows x 128 bytes
 constexpr int kBoxBytes = 32 * 128;                 // 32 samples x 32 kx x half2
-constexpr int kEpiBufs = 2;                         // boxes per warp
+constexpr int kEpiBufs = 1;                         // boxes per warp
 constexpr long long kWaitCycles = 4000000000LL;     // ~2 s at the SM clock
 
 template <int N>
@@ -302,18 +302,22 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue warps 0-3: TMEM lanes 32w..32w+31 = samples
+        // ---------------- epilogue warps 0-7: TMEM lanes 32 (w % 4) .. + 31 = samples
         unsigned char *sw = sE + warp * kEpiBufs * kBoxBytes;
         int nbox = 0;
         for (int i = 0; i < nitems; ++i) {
             const int b = i & 1;
             if (!tc::mbar_wait_abortable(&d_full[b], (uint32_t)((i >> 1) & 1), kWaitCycles, abort_flag)) break;
             tc::fence_after_sync();
-            const int cl = cb + i / ntb, t0w = (i % ntb) * 128 + warp * 32;
+            const int q4 = warp & 3;                     // TMEM lane quarter of this warp
+            const int cl = cb + i / ntb, t0w = (i % ntb) * 128 + q4 * 32;
             const float inv = a.row_sh[pr];   // exact power of two: FP16 range for every row
-            const uint32_t dcol = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * NT);
+            const uint32_t dcol = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * NT);
+            // kx columns of this warp: one half each for the two warps of a quarter (all for KX = 32)
+            const int kx_lo = KX >= 64 ? (warp >> 2) * (KX / 2) : ((warp >> 2) ? KX : 0);
+            const int kx_hi = KX >= 64 ? kx_lo + KX / 2 : KX;
 #pragma unroll 1
-            for (int k0 = 0; k0 < KX; k0 += 32, ++nbox) {
+            for (int k0 = kx_lo; k0 < kx_hi; k0 += 32, ++nbox) {
                 float vr[32], vi[32];
                 tc::tmem_ld32(dcol + (uint32_t)k0, vr);
                 tc::tmem_ld32(dcol + (uint32_t)(KX + k0), vi);
