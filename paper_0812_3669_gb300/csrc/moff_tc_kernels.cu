@@ -147,7 +147,7 @@ struct TcShape {
 
 // Warp roles: warps 0-7 drain the TMEM accumulators (lane quarter w % 4, kx half
 // w / 4), one lane of warp 8 loads A with TMA, one lane of warp 9 issues the MMAs.
-// A: 3-stage ring of K-chunks of 64 = 32 consecutive plane rows (real parts,
+// A: ring of kAStages K-chunks of 64 = 32 consecutive plane rows (real parts,
 // then imaginary parts) x 128 samples, MN-major with the 128-byte swizzle: two
 // 64-sample halves of 8 KB, each 64 rows of 128 bytes; four TMA tiles of
 // 64 samples x 32 rows per chunk.  B: resident; accumulators: two in TMEM;
@@ -156,7 +156,7 @@ struct TcShape {
 // (bulk tensor store); a warp reuses its box once the store has read it.
 constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, each draining half of the kx columns
 constexpr int kTcRoleThreads = (kEpiWarps + 2) * 32;
-constexpr int kAStages = 3, kKChunk = 64;
+constexpr int kAStages = 4, kKChunk = 64;
 constexpr int kAChunkBytes = 128 * kKChunk * 2;
 constexpr int kAHalfBytes = kAChunkBytes / 2;          // one 64-sample half: 64 rows x 128 bytes
 constexpr int kBoxBytes = 32 * 128;                 // 32 samples x 32 kx x half2
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
     unsigned char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *sB = smem;                                  // NT x kp, K-major (resident)
     unsigned char *sA = sB + (size_t)NT * a.kp_max * 2;        // kAStages x [128 x 64], MN-major, 1024-aligned
-    unsigned char *sE = sA + (size_t)kAStages * kAChunkBytes;  // [4 warps][kEpiBufs] boxes, 1024-aligned
+    unsigned char *sE = sA + (size_t)kAStages * kAChunkBytes;  // [kEpiWarps][kEpiBufs] boxes, 1024-aligned
     uint64_t *bars = reinterpret_cast<uint64_t *>(sE + kEpiWarps * kEpiBufs * kBoxBytes);
     uint64_t *a_full = bars, *a_empty = bars + kAStages, *d_full = bars + 2 * kAStages,
              *d_empty = bars + 2 * kAStages + 2;
@@ -313,9 +313,10 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
             const int cl = cb + i / ntb, t0w = (i % ntb) * 128 + q4 * 32;
             const float inv = a.row_sh[pr];   // exact power of two: FP16 range for every row
             const uint32_t dcol = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * NT);
-            // kx columns of this warp: one half each for the two warps of a quarter (all for KX = 32)
-            const int kx_lo = KX >= 64 ? (warp >> 2) * (KX / 2) : ((warp >> 2) ? KX : 0);
-            const int kx_hi = KX >= 64 ? kx_lo + KX / 2 : KX;
+            // kx columns of this warp: the 32-column boxes dealt out to the warps of its lane quarter
+            constexpr int kPerQuarter = kEpiWarps / 4;
+            const int nbx = KX / 32, per = (nbx + kPerQuarter - 1) / kPerQuarter;
+            const int kx_lo = min(nbx, (warp >> 2) * per) * 32, kx_hi = min(nbx, (warp >> 2) * per + per) * 32;
 #pragma unroll 1
             for (int k0 = kx_lo; k0 < kx_hi; k0 += 32, ++nbox) {
                 float vr[32], vi[32];
