@@ -185,3 +185,24 @@ def test_block_larger_than_pool_is_refused_and_destroy_cancels_queue():
         img, n = pl.read_image()
         assert 0 <= n <= 500 and n % 10 == 0
         assert np.isfinite(img).all()
+
+
+def test_served_tensor_core_plan_equals_unserved():
+    """A MOFF_SERVED plan on the FP16 tensor-core path borrows its field scratch and
+    voltage planes from the pool per block (tensor maps encoded per block): its
+    image equals the same plan's unserved image bit for bit."""
+    pos, taps, gains = subarray(41, 400, 128, 7, 2, 5, 90)
+    blks = blocks(42, [70, 33], 5, 400, 2)
+    with moff.Plan(pos, taps, 128, 5, 2, fp16tc=True) as pu:
+        pu.set_gains(gains)
+        for b in blks:
+            pu.submit(b)
+        ref, nr = pu.read_image()
+    with moff.Plan(pos, taps, 128, 5, 2, fp16tc=True, served=True) as ps, moff.Server(8 << 30, 2) as srv:
+        ps.set_gains(gains)
+        for b in blks:
+            srv.submit(ps, b)
+        srv.wait(0, 120000)
+        img, n = ps.read_image()
+    assert n == nr == 103
+    assert np.array_equal(img, ref)
