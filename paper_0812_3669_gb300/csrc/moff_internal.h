@@ -142,6 +142,7 @@ struct PfbArgs {
     const float2 *tw4;
     uint8_t *codes_sm;
     float2 *spec_sm;
+    int frames_per_cta;       // four-step variant: frames one CTA streams (a multiple of 16)
 };
 
 // Row stride (in float2) of the TB calibrated voltages of one antenna-pol in
