@@ -1821,7 +1821,9 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         pl->rs_inv_sw = rs.inv_sw;
         pl->rs_smem = rowspec_smem_bytes(grid_n, pl->rs_kp_max);
         const int items = n_pol * grid_n * rs.ntiles;
-        pl->rs_cgroups = std::max(1, std::min(pl->Cb, (4 * 152 + items - 1) / items));
+        // channel groups: about twelve CTAs per SM over the launch (a sweep on the benchmark array: 3, 8, 19,
+        // 38 groups gave 33.0, 31.0, 31.6, 34.2 ms per step)
+        pl->rs_cgroups = std::max(1, std::min(pl->Cb, (12 * 152 + items - 1) / items));
         if (const char *e = getenv("MOFF_TC_CGROUPS")) pl->rs_cgroups = std::max(1, std::min(pl->Cb, atoi(e)));
         const size_t ny = (size_t)pl->Cb * (n_ant * n_pol + kRowSpecPad) * pl->Tb;
         if ((s = palloc(pl, &pl->d_rs_kp, rs.kp.size() * 4)) != MOFF_OK) return bail(s);
