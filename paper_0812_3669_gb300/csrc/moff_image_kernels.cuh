@@ -429,12 +429,16 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
                 return reinterpret_cast<const float2 *>(tin)[e];
             }
         };
-        {   // pass 0: staged tile -> registers -> s_a
+        {   // pass 0: staged tile -> registers -> s_a.  FP32 field: one (pol, slot) per thread and
+            // turn (every thread busy); FP16 field: both pols of a slot per thread (measured faster there)
             constexpr int R = FP::R0, NSL = N / R;
-            for (int sl = tid; sl < W * NSL; sl += kBlock) {
+            constexpr int PS = H16 ? 1 : P;     // pols spread over threads
+            for (int it = tid; it < PS * W * NSL; it += kBlock) {
+                const int p0 = it / (W * NSL), sl = it - p0 * (W * NSL);
                 const int col = sl % W, j = sl / W;
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
+                for (int pp = 0; pp < P / PS; ++pp) {
+                    const int p = p0 + pp;
                     float2 v[R];
 #pragma unroll
                     for (int r = 0; r < R; ++r) v[r] = in_at(p, j + r * NSL, col);
@@ -447,18 +451,16 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
         __syncthreads();
         if constexpr (FP::NP == 3) {
             constexpr int R = FP::R1, NS = FP::R0, NSL = N / R;
-            for (int sl = tid; sl < W * NSL; sl += kBlock) {
+            for (int it = tid; it < P * W * NSL; it += kBlock) {
+                const int p = it / (W * NSL), sl = it - p * (W * NSL);
                 const int col = sl % W, j = sl / W;
+                float2 v[R];
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    float2 v[R];
+                for (int r = 0; r < R; ++r) v[r] = s_a[(p * N + j + r * NSL) * W + col];
+                twiddle<R, NS, 1>(v, j, s_tw + TW::OFF1);
+                dft<R, 1>(v);
 #pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = s_a[(p * N + j + r * NSL) * W + col];
-                    twiddle<R, NS, 1>(v, j, s_tw + TW::OFF1);
-                    dft<R, 1>(v);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) s_b[(p * N + stockham_out<R, NS>(j, r)) * W + col] = v[r];
-                }
+                for (int r = 0; r < R; ++r) s_b[(p * N + stockham_out<R, NS>(j, r)) * W + col] = v[r];
             }
             __syncthreads();
         }
