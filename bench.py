@@ -256,7 +256,32 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def traffic_for(kernel_key, src_files):
+def source_sha1(src):
+    """SHA-1 of a kernel's source: each entry is a file, or (file, marker) for the
+    part of the file before the first line containing marker (the kernel and what
+    precedes it, not the kernels after it)."""
+    h = hashlib.sha1()
+    for f in src:
+        path, marker = (f, None) if isinstance(f, str) else f
+        text = open(os.path.join(ROOT, path), "rb").read()
+        if marker is not None:
+            cut = text.find(marker.encode())
+            text = text[:cut] if cut >= 0 else text
+        h.update(text)
+    return h.hexdigest()
+
+
+# The source each traffic figure depends on (see profiles/traffic.json).
+KERNEL_SOURCES = {
+    "grid_rows": [("paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "struct ColShape"),
+                  "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
+    "cols_integrate": [("paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "size_t col_smem_bytes_t"),
+                       "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
+    "pfb_fstage": ["paper_0812_3669_gb300/csrc/moff_fstage.cu", "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
+}
+
+
+def traffic_for(kernel_key, src):
     """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
     source is unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -264,12 +289,7 @@ def traffic_for(kernel_key, src_files):
         rec = json.load(open(path)).get(kernel_key)
     except (OSError, ValueError):
         return None
-    if not rec:
-        return None
-    h = hashlib.sha1()
-    for f in src_files:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    if rec.get("source_sha1") != h.hexdigest():
+    if not rec or rec.get("source_sha1") != source_sha1(src):
         return None
     return rec.get("bytes_per_launch")
 
@@ -512,10 +532,7 @@ def run_ours(args):
         v["share"] = v["ms_total"] / total_kernel_ms if total_kernel_ms else None
         v["tflops"] = flops[name] / (v["ms_total"] / 1e3) / 1e12 if v["ms_total"] and name in flops else None
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
-    src = {"grid_rows": ["paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
-           "cols_integrate": ["paper_0812_3669_gb300/csrc/moff_image_kernels.cuh",
-                              "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
-           "pfb_fstage": ["paper_0812_3669_gb300/csrc/moff_fstage.cu", "paper_0812_3669_gb300/csrc/moff_fft.cuh"]}.get(dom, [])
+    src = KERNEL_SOURCES.get(dom, [])
     launches = kern[dom]["launches"]
     achieved = kern[dom]["tflops"]
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
