@@ -299,7 +299,7 @@ def serving_leg(args, moff, synth, torch, fp16tc=False):
     moff_server): first a closed burst to find the saturation rate, then Poisson
     arrivals at fractions of it.  Reports p50/p99 block latency and throughput.
     With fp16tc, each sub-array takes the FP16 tensor-core path where its density
-    allows (at most 128 kernel rows per grid row) and FP32 otherwise."""
+    allows (at most 128 antennas' kernel rows on a grid row) and FP32 otherwise."""
     import numpy as np
     mix = synth.config_serving()
     plans, blocks, prec = [], [], []

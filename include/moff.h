@@ -69,7 +69,8 @@ enum {
                                  voltages and each kernel row's FP64-built row spectrum, both under
                                  exact power-of-two scales), FP32 accumulation; the column transform
                                  and the squaring stay FP32, cross-block sums FP64.  Needs at most
-                                 128 kernel rows landing on any one grid row per pol. */
+                                 128 antennas (4 chunks of 32) whose kernel rows land on any one grid
+                                 row per pol. */
     MOFF_FSTAGE = 1u << 1,    /* enable the polyphase F-stage (moff_submit_adc, moff_channelise) */
     MOFF_JONES = 1u << 2,     /* kernels are full 2x2 Jones matrices (n_pol must be 2) */
     MOFF_SERVED = 1u << 3,    /* the plan does not own its per-block scratch (the row-transformed

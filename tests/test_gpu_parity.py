@@ -222,7 +222,7 @@ def test_filled_aperture_full_array_sampled():
     """The precision configuration's array at full size -- 16384 antennas filling
     a 128 x 128 lambda lattice, dual pol, 7x7 kernels, 512 x 512 grid -- on the FP32
     path, 4 channels x 24 samples against the oracle.  The FP16 tensor-core path
-    refuses this density (more than 128 kernel rows land on a grid row)."""
+    refuses this density (more than 128 antennas' kernel rows land on a grid row)."""
     cfg = synth.config_precision(n_chan=4)
     T, C, A, P, N = 24, 4, cfg["pos"].shape[0], 2, cfg["grid_n"]
     assert A == 16384 and N == 512
