@@ -317,26 +317,35 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
             constexpr int kPerQuarter = kEpiWarps / 4;
             const int nbx = KX / 32, per = (nbx + kPerQuarter - 1) / kPerQuarter;
             const int kx_lo = min(nbx, (warp >> 2) * per) * 32, kx_hi = min(nbx, (warp >> 2) * per + per) * 32;
+            const int nb = (kx_hi - kx_lo) / 32;
 #pragma unroll 1
-            for (int k0 = kx_lo; k0 < kx_hi; k0 += 32, ++nbox) {
+            for (int k0 = kx_lo, bi = 0; k0 < kx_hi; k0 += 32, ++nbox, ++bi) {
                 float vr[32], vi[32];
                 tc::tmem_ld32(dcol + (uint32_t)k0, vr);
                 tc::tmem_ld32(dcol + (uint32_t)(KX + k0), vi);
-                unsigned char *box = sw + (nbox % kEpiBufs) * kBoxBytes;
-                if (nbox >= kEpiBufs) {                  // the store that last read this box is done with it
-                    if (lane == 0) tc::bulk_wait_read<kEpiBufs - 1>();
-                    __syncwarp();
+                if (bi == nb - 1) {                      // this item's last TMEM read: the accumulator is free
+                    tc::fence_before_sync();
+                    tc::mbar_arrive(&d_empty[b]);
                 }
                 // lane = sample t0w + lane: its 32 kx as eight 16-byte chunks of one 128-byte row,
-                // chunk q stored at q ^ (row % 8) (the tensor map's 128-byte swizzle)
+                // chunk q stored at q ^ (row % 8) (the tensor map's 128-byte swizzle); packed
+                // before waiting for the box so the conversion overlaps the previous store's read
+                uint4 pk[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     __half2 h[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) h[u] = __floats2half2_rn(vr[4 * q + u] * inv, vi[4 * q + u] * inv);
-                    *reinterpret_cast<uint4 *>(box + lane * 128 + ((q ^ (lane & 7)) << 4)) =
-                        *reinterpret_cast<const uint4 *>(h);
+                    pk[q] = *reinterpret_cast<const uint4 *>(h);
                 }
+                unsigned char *box = sw + (nbox % kEpiBufs) * kBoxBytes;
+                if (nbox >= kEpiBufs) {                  // the store that last read this box is done with it
+                    if (lane == 0) tc::bulk_wait_read<kEpiBufs - 1>();
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    *reinterpret_cast<uint4 *>(box + lane * 128 + ((q ^ (lane & 7)) << 4)) = pk[q];
                 tc::fence_async_smem();
                 __syncwarp();
                 if (lane == 0) {
@@ -345,8 +354,10 @@ __global__ void __launch_bounds__(kTcRoleThreads, 1)
                     tc::bulk_commit();
                 }
             }
-            tc::fence_before_sync();
-            tc::mbar_arrive(&d_empty[b]);
+            if (nb == 0) {                               // no kx columns for this warp (narrow grids)
+                tc::fence_before_sync();
+                tc::mbar_arrive(&d_empty[b]);
+            }
         }
         if (lane == 0) tc::bulk_wait_all();
     }
