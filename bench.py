@@ -257,15 +257,20 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- GPU arm
 
 def source_sha1(src):
-    """SHA-1 of a kernel's source: each entry is a file, or (file, marker) for the
-    part of the file before the first line containing marker (the kernel and what
-    precedes it, not the kernels after it)."""
+    """SHA-1 of a kernel's source: each entry is a file, (file, end) for the part
+    of the file before the first occurrence of `end` (the kernel and what precedes
+    it, not the kernels after it), or (file, start, end) for the part from the
+    first occurrence of `start` up to the next `end` (the kernel and its own
+    helpers only)."""
     h = hashlib.sha1()
     for f in src:
-        path, marker = (f, None) if isinstance(f, str) else f
+        path, start, end = (f, None, None) if isinstance(f, str) else ((f[0], None, f[1]) if len(f) == 2 else f)
         text = open(os.path.join(ROOT, path), "rb").read()
-        if marker is not None:
-            cut = text.find(marker.encode())
+        if start is not None:
+            i = text.find(start.encode())
+            text = text[i:] if i >= 0 else text
+        if end is not None:
+            cut = text.find(end.encode())
             text = text[:cut] if cut >= 0 else text
         h.update(text)
     return h.hexdigest()
@@ -275,7 +280,8 @@ def source_sha1(src):
 KERNEL_SOURCES = {
     "grid_rows": [("paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "struct ColShape"),
                   "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
-    "cols_integrate": [("paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "size_t col_smem_bytes_t"),
+    "cols_integrate": [("paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "template <int N>\nstruct ColShape",
+                        "size_t col_smem_bytes_t"),
                        "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
     "pfb_fstage": ["paper_0812_3669_gb300/csrc/moff_fstage.cu", "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
 }

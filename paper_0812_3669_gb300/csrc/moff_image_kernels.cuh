@@ -28,15 +28,22 @@ __device__ __forceinline__ float2 decode4(uint32_t b) {
 
 // One Stockham pass over the F rows held in shared memory (row f at
 // src + f*LDR, padded index) into dst, or -- LAST -- into the global row
-// returned by `rowptr(f)` (nullptr: row not stored).  Ends with a barrier
-// unless LAST.
+// returned by `rowptr(f)` (nullptr: row not stored).  When the warps can
+// share the rows evenly, warp w owns rows [w F/NW, (w+1) F/NW) in every pass,
+// so a pass reads only what its own warp wrote and a warp barrier orders the
+// passes; otherwise the slots are dealt out over the block and a block barrier
+// ends each pass.  No barrier after a LAST pass.
 template <int N, int F, int R, int NS, bool LAST, class RowPtr>
 __device__ __forceinline__ void rows_pass(const float2 *src, float2 *dst, const float2 *tw, RowPtr rowptr) {
     constexpr int LDR = PaddedLen<N>::value;
     constexpr int NSL = N / R;
-    constexpr int SLOTS = F * NSL;
-    for (int sl = threadIdx.x; sl < SLOTS; sl += kBlock) {
-        const int f = sl / NSL, j = sl - f * NSL;
+    constexpr int NW = kBlock / 32;
+    constexpr bool WL = F % NW == 0;                 // warp-local rows
+    constexpr int SLOTS = WL ? (F / NW) * NSL : F * NSL;
+    constexpr int STEP = WL ? 32 : kBlock;
+    const int base = WL ? (int)(threadIdx.x >> 5) * (F / NW) : 0;
+    for (int sl = WL ? (int)(threadIdx.x & 31) : (int)threadIdx.x; sl < SLOTS; sl += STEP) {
+        const int fl = sl / NSL, j = sl - fl * NSL, f = base + fl;
         const float2 *in = src + f * LDR;
         float2 v[R];
 #pragma unroll
@@ -55,7 +62,10 @@ __device__ __forceinline__ void rows_pass(const float2 *src, float2 *dst, const 
             for (int r = 0; r < R; ++r) out[pad_store<R, NS>(j, r)] = v[r];
         }
     }
-    if constexpr (!LAST) __syncthreads();
+    if constexpr (!LAST) {
+        if constexpr (WL) __syncwarp();
+        else __syncthreads();
+    }
 }
 
 // Stripe height of the gridding kernel: TB samples x P pols x ROWS rows = F rows per pass.
