@@ -32,8 +32,10 @@ __device__ __forceinline__ float2 decode4(uint32_t b) {
 // share the rows evenly, warp w owns rows [w F/NW, (w+1) F/NW) in every pass,
 // so a pass reads only what its own warp wrote and a warp barrier orders the
 // passes; otherwise the slots are dealt out over the block and a block barrier
-// ends each pass.  No barrier after a LAST pass.
-template <int N, int F, int R, int NS, bool LAST, class RowPtr>
+// ends each pass.  IP (in place, dst == src): each lane holds one slot, reads
+// it, and writes it back after the warp has read all its rows.  No barrier
+// after a LAST pass.
+template <int N, int F, int R, int NS, bool LAST, bool IP, class RowPtr>
 __device__ __forceinline__ void rows_pass(const float2 *src, float2 *dst, const float2 *tw, RowPtr rowptr) {
     constexpr int LDR = PaddedLen<N>::value;
     constexpr int NSL = N / R;
@@ -42,29 +44,46 @@ __device__ __forceinline__ void rows_pass(const float2 *src, float2 *dst, const 
     constexpr int SLOTS = WL ? (F / NW) * NSL : F * NSL;
     constexpr int STEP = WL ? 32 : kBlock;
     const int base = WL ? (int)(threadIdx.x >> 5) * (F / NW) : 0;
-    for (int sl = WL ? (int)(threadIdx.x & 31) : (int)threadIdx.x; sl < SLOTS; sl += STEP) {
+    if constexpr (IP && !LAST) {
+        static_assert(WL && SLOTS == 32, "in-place pass: one slot per lane");
+        const int sl = (int)(threadIdx.x & 31);
         const int fl = sl / NSL, j = sl - fl * NSL, f = base + fl;
-        const float2 *in = src + f * LDR;
         float2 v[R];
+        const float2 *in = src + f * LDR;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = in[pad_load<NSL>(j, r)];
         twiddle<R, NS, 1>(v, j, tw);
         dft<R, 1>(v);
-        if constexpr (LAST) {
-            float2 *o = rowptr(f);
-            if (o) {
+        __syncwarp();                                // the warp's rows are read
+        float2 *out = dst + f * LDR;
 #pragma unroll
-                for (int r = 0; r < R; ++r) o[j + r * NSL] = v[r];
+        for (int r = 0; r < R; ++r) out[pad_store<R, NS>(j, r)] = v[r];
+        __syncwarp();
+    } else {
+        for (int sl = WL ? (int)(threadIdx.x & 31) : (int)threadIdx.x; sl < SLOTS; sl += STEP) {
+            const int fl = sl / NSL, j = sl - fl * NSL, f = base + fl;
+            const float2 *in = src + f * LDR;
+            float2 v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = in[pad_load<NSL>(j, r)];
+            twiddle<R, NS, 1>(v, j, tw);
+            dft<R, 1>(v);
+            if constexpr (LAST) {
+                float2 *o = rowptr(f);
+                if (o) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) o[j + r * NSL] = v[r];
+                }
+            } else {
+                float2 *out = dst + f * LDR;
+#pragma unroll
+                for (int r = 0; r < R; ++r) out[pad_store<R, NS>(j, r)] = v[r];
             }
-        } else {
-            float2 *out = dst + f * LDR;
-#pragma unroll
-            for (int r = 0; r < R; ++r) out[pad_store<R, NS>(j, r)] = v[r];
         }
-    }
-    if constexpr (!LAST) {
-        if constexpr (WL) __syncwarp();
-        else __syncthreads();
+        if constexpr (!LAST) {
+            if constexpr (WL) __syncwarp();
+            else __syncthreads();
+        }
     }
 }
 
@@ -77,12 +96,35 @@ struct GridShape {
     static constexpr int ROWS = ROWS_ < 1 ? 1 : (ROWS_ > N ? N : ROWS_);
     static constexpr int PR = P * ROWS;
     static constexpr int F = TB * PR;
+    // one row buffer (passes in place)
+    static constexpr bool IN_PLACE = grid_rows_in_place(N, F);
 };
+
+// CTAs per SM the register allocation is sized for when the row passes run in
+// place (one row buffer, so more CTAs fit an SM's shared memory): four (64
+// registers) up to 4 samples per pass, three (80) for 2 x 2 block lanes at 4
+// samples on wide stripes, two (128) for 2 x 2 blocks at 4 samples otherwise and at
+// 8 samples.
+template <int N, int P, int TB, int CPL, bool WIDE>
+constexpr int grid_min_blocks() {
+    if (TB >= 8) return 2;
+    if (CPL == 4 && TB == 4) return WIDE ? 3 : 2;
+    return 4;
+}
+
+static_assert(fft_radix(32, 0) == FftPlan<32>::R0 && fft_radix(32, 1) == FftPlan<32>::R1 &&
+              fft_radix(64, 0) == FftPlan<64>::R0 && fft_radix(64, 1) == FftPlan<64>::R1 &&
+              fft_radix(128, 0) == FftPlan<128>::R0 && fft_radix(128, 1) == FftPlan<128>::R1 &&
+              fft_radix(256, 0) == FftPlan<256>::R0 && fft_radix(256, 1) == FftPlan<256>::R1 &&
+              fft_radix(512, 0) == FftPlan<512>::R0 && fft_radix(512, 1) == FftPlan<512>::R1 &&
+              fft_radix(512, 2) == FftPlan<512>::R2 && fft_radix(1024, 0) == FftPlan<1024>::R0 &&
+              fft_radix(1024, 1) == FftPlan<1024>::R1 && fft_radix(2048, 1) == FftPlan<2048>::R1,
+              "host radix table matches the FFT plan");
 
 // CPL = grid cells per lane: 1, 2 (cells (f, e), (f, e + 1) of one row) or 4 (the 2 x 2
 // block (f, e), (f, e + 1), (f + 1, e), (f + 1, e + 1), f even); each entry carries CPL taps.
 template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE>
-__global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
+__device__ __forceinline__ void grid_rows(const GridArgs &a) {
     constexpr bool PAIRS = CPL >= 2;
     using FP = FftPlan<N>;
     using TW = FftTw<N>;
@@ -131,8 +173,9 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     // Carve (matches grid_smem_bytes).
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *s_tw = reinterpret_cast<float2 *>(smem);
+    constexpr bool IP = GS::IN_PLACE;
     float2 *s_buf = s_tw + TW::TOTAL;                  // gridded rows
-    float2 *s_alt = s_buf + F * LDR;                   // second buffer of the row passes
+    float2 *s_alt = IP ? s_buf : s_buf + F * LDR;      // second buffer of the row passes (none in place)
     float2 *s_y = s_alt + ((F * LDR + 1) & ~1);        // [nloc*P][YS]: TB samples, padded row (16-byte aligned)
     float2 *s_g = s_y + YS * a.max_nloc * P;
     // staged kernel values (CPL per entry, read as 16-byte vectors when CPL >= 2: 16-byte aligned)
@@ -317,16 +360,29 @@ __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
             __syncthreads();
             continue;
         }
-        // Step 3, first axis: N-point transform of every row (ping-pong buffers).
-        rows_pass<N, F, FP::R0, 1, false>(s_buf, s_alt, s_tw, rowptr);
+        // Step 3, first axis: N-point transform of every row (ping-pong buffers, or one in place).
+        rows_pass<N, F, FP::R0, 1, false, IP>(s_buf, s_alt, s_tw, rowptr);
         if constexpr (FP::NP == 3) {
-            rows_pass<N, F, FP::R1, FP::R0, false>(s_alt, s_buf, s_tw + TW::OFF1, rowptr);
-            rows_pass<N, F, FP::R2, FP::R0 * FP::R1, true>(s_buf, nullptr, s_tw + TW::OFF2, rowptr);
+            rows_pass<N, F, FP::R1, FP::R0, false, IP>(s_alt, s_buf, s_tw + TW::OFF1, rowptr);
+            rows_pass<N, F, FP::R2, FP::R0 * FP::R1, true, IP>(s_buf, nullptr, s_tw + TW::OFF2, rowptr);
         } else {
-            rows_pass<N, F, FP::R1, FP::R0, true>(s_alt, nullptr, s_tw + TW::OFF1, rowptr);
+            rows_pass<N, F, FP::R1, FP::R0, true, IP>(s_alt, nullptr, s_tw + TW::OFF1, rowptr);
         }
         // (the next iteration's first barrier orders these reads before any rewrite)
     }
+}
+
+// Row transform out of place: the register count is the compiler's choice (an
+// explicit minimum of one CTA per SM lets it take about twice as many).
+template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE>
+__global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
+    grid_rows<N, P, TB, STAGED, GRID_ONLY, CPL, WIDE>(a);
+}
+
+// Row transform in place: registers capped so that grid_min_blocks CTAs fit an SM.
+template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE>
+__global__ void __launch_bounds__(kBlock, grid_min_blocks<N, P, TB, CPL, WIDE>()) k_grid_rows_ip(const GridArgs a) {
+    grid_rows<N, P, TB, STAGED, GRID_ONLY, CPL, WIDE>(a);
 }
 
 template <int N>
@@ -565,7 +621,9 @@ cudaError_t launch_grid_t(const GridArgs &a, int n_stripes, size_t smem, cudaStr
     if constexpr (CPL == 4 && (ST || GridShape<N, P, TB, WD>::ROWS % 2 != 0)) {
         return cudaErrorInvalidValue;
     } else {
-    auto k = k_grid_rows<N, P, TB, ST, GO, CPL, WD>;
+    void (*k)(GridArgs);
+    if constexpr (GridShape<N, P, TB, WD>::IN_PLACE) k = k_grid_rows_ip<N, P, TB, ST, GO, CPL, WD>;
+    else k = k_grid_rows<N, P, TB, ST, GO, CPL, WD>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<dim3(n_stripes, a.nc), kBlock, smem, st>>>(a);

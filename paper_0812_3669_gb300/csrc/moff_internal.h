@@ -154,14 +154,37 @@ inline int volt_stride(int TB) { return TB == 1 ? 1 : (TB == 8 ? 10 : 6); }
 // Rows transformed together by one gridding CTA: TB samples x P pols x rows.
 inline int grid_fft_rows(int N) { return N >= 256 ? 8 : (N == 128 ? 16 : 32); }
 
+// Radices of the N-point transform's passes (pass 0, 1, 2; 1 = no such pass);
+// the device FFT plan (FftPlan<N>) asserts it agrees.
+constexpr int fft_radix(int N, int pass) {
+    return pass == 0 ? (N == 128 || N == 256 || N >= 1024 ? 16 : 8)
+                     : pass == 1 ? (N == 32 ? 4 : (N == 256 || N == 2048 ? 16 : 8)) : (N >= 512 ? 8 : 1);
+}
+
+// The gridding kernel's row transform runs in place (one shared buffer of F rows)
+// when the CTA's warps share the F rows evenly and, in every pass but the last,
+// the slots of a warp's rows are exactly 32 (one per lane, held in registers
+// while the warp reads its rows, written back after a warp barrier).  With idle
+// lanes the compiler asked for more registers than the CTAs per SM allow.
+constexpr bool grid_rows_in_place(int N, int F) {
+    const int nw = 8;   // warps per gridding CTA (kBlock / 32)
+    if (F % nw) return false;
+    const int rpw = F / nw, np = N >= 512 ? 3 : 2;
+    for (int p = 0; p + 1 < np; ++p)
+        if (rpw * (N / fft_radix(N, p)) != 32) return false;
+    return true;
+}
+
 // Shared-memory bytes of the gridding kernel (host and device agree on the carve).
 inline size_t grid_smem_bytes(int N, int P, int TB, int rows, int max_nloc, int tw_total, int staged_entries = 0,
                               bool pairs = false) {
     const int ldr = N + N / 16;
+    const int F = TB * P * rows;
     size_t b = 0;
     b += (size_t)staged_entries * (pairs ? 18 : 10);   // staged kernel entries (one or two float2 taps + u16)
     b += (size_t)tw_total * 8;
-    b += 2 * (size_t)TB * P * rows * ldr * 8 + 8; // ping-pong row buffers of TB samples (+ alignment)
+    // row buffer of TB samples, and a second one unless the passes run in place (+ alignment)
+    b += (grid_rows_in_place(N, F) ? 1 : 2) * (size_t)F * ldr * 8 + 8;
     b += (size_t)volt_stride(TB) * max_nloc * P * 8;   // calibrated voltages of TB samples
     b += (size_t)max_nloc * P * 8 + 8;        // gains (+ padding that 16-byte aligns the staged entries)
     b += (size_t)max_nloc * 4;                // antenna indices
