@@ -1445,7 +1445,8 @@ std::string tune_key(const moff_plan *pl, const double *pos, const float *taps) 
     cudaGetDeviceProperties(&prop, pl->device);
     h = fnv1a(prop.name, strlen(prop.name), h);
     char buf[128];
-    snprintf(buf, sizeof buf, "grid5-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P,
+    // the prefix changes with the gridding kernels, so picks timed on an older build are not reused
+    snprintf(buf, sizeof buf, "grid6-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P,
              (int)pl->jones, pl->Tb, std::min(pl->Cb, pl->C), prop.multiProcessorCount, (unsigned long long)h);
     return buf;
 }
