@@ -1,0 +1,37 @@
+"""The benchmark reports a kernel's DRAM traffic only while the kernel's source
+is the one the ncu capture ran: check that every hashed region is found in its
+file (a missing marker would silently hash the whole file) and that every
+recorded capture names a kernel the benchmark hashes."""
+import json
+import os
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_hashed_regions_exist_and_are_nonempty():
+    for key, src in bench.KERNEL_SOURCES.items():
+        for f in src:
+            if isinstance(f, str):
+                assert os.path.isfile(os.path.join(ROOT, f)), (key, f)
+                continue
+            path, start, end = (f[0], None, f[1]) if len(f) == 2 else f
+            text = open(os.path.join(ROOT, path)).read()
+            i = 0
+            if start is not None:
+                i = text.find(start)
+                assert i >= 0, (key, "start marker missing", start)
+            j = text.find(end, i)
+            assert j > i, (key, "end marker missing or before start", end)
+        assert len(bench.source_sha1(src)) == 40
+
+
+def test_recorded_captures_name_hashed_kernels():
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for name, r in rec.items():
+        kernel = name.split("@")[0]
+        assert kernel in bench.KERNEL_SOURCES, name
+        assert r["bytes_per_launch"] > 0 and len(r["source_sha1"]) == 40
+        # a different region never matches the recorded hash
+        assert bench.source_sha1(["include/moff.h"]) != r["source_sha1"]
