@@ -415,6 +415,46 @@ def test_cell_pair_and_block_lanes_are_bit_identical(monkeypatch, N, P, K, A, jo
     assert_image(out[4][0], oracle.moff_image(codes, gains, pos, taps, N, P, jones=jones))
 
 
+@pytest.mark.parametrize("N,P,K,A", [(32, 1, 3, 60), (64, 2, 5, 150), (128, 2, 7, 300), (256, 2, 5, 250),
+                                     (512, 1, 3, 120)])
+def test_wide_stripes_and_in_place_row_passes_are_bit_identical(monkeypatch, N, P, K, A):
+    """Stripes of twice the rows (wide) run the first row-transform pass in place
+    where each lane holds one slot (N = 32, 128, 256 wide; N = 64 plain), with one
+    row buffer and capped registers; the other shapes keep two buffers.  The
+    per-cell sums and the per-row passes are the same arithmetic in every shape,
+    so every (wide, lanes) combination must give the same image and gridded
+    snapshot bit for bit, and match the oracle."""
+    C, T = 2, 19                     # T not a multiple of the samples per pass
+    pos, taps, codes, gains = random_case(900 + N, A, N, K, P, C=C, T=T)
+    monkeypatch.setenv("MOFF_GRID_STAGE", "0")
+    out = {}
+    for wide in ("0", "1"):
+        for cpl, pairs, quads in ((1, "0", "0"), (2, "1", "0"), (4, "1", "1")):
+            monkeypatch.setenv("MOFF_GRID_WIDE", wide)
+            monkeypatch.setenv("MOFF_GRID_PAIRS", pairs)
+            monkeypatch.setenv("MOFF_GRID_QUADS", quads)
+            try:
+                pl = moff.Plan(pos, taps, N, C, P)
+            except moff.MoffError:
+                assert cpl == 4              # 2 x 2 blocks need an even stripe height
+                continue
+            with pl:
+                tu = pl.tuning()
+                assert (tu["cells_per_lane"], tu["wide_rows"]) == (cpl, int(wide))
+                pl.set_gains(gains)
+                pl.submit(codes)
+                img, n = pl.read_image()
+                snap = pl.grid_snapshot(codes[3], 1)
+            assert n == T
+            out[(wide, cpl)] = (img, snap)
+    assert ("0", 1) in out and ("1", 1) in out and len(out) >= 4
+    base = out[("0", 1)]
+    for key, (img, snap) in out.items():
+        assert np.array_equal(img, base[0]), key
+        assert np.array_equal(snap, base[1]), key
+    assert_image(base[0], oracle.moff_image(codes, gains, pos, taps, N, P))
+
+
 def test_host_adc_pipelined_staging_equals_device_input():
     """A host ADC block longer than one staging segment (128 frames) is copied in
     frame segments that overlap the F-stage and imaging of earlier ones; the
