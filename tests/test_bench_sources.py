@@ -1,7 +1,8 @@
-"""The benchmark reports a kernel's DRAM traffic only while the kernel's source
-is the one the ncu capture ran: check that every hashed region is found in its
-file (a missing marker would silently hash the whole file) and that every
-recorded capture names a kernel the benchmark hashes."""
+"""Host-side parts of the benchmark.  It reports a kernel's DRAM traffic only
+while the kernel's source is the one the ncu capture ran: check that every
+hashed region is found in its file (a missing marker would silently hash the
+whole file) and that every recorded capture names a kernel the benchmark
+hashes.  And the algorithmic byte model of the tensor-core row contraction."""
 import json
 import os
 
@@ -35,3 +36,13 @@ def test_recorded_captures_name_hashed_kernels():
         assert r["bytes_per_launch"] > 0 and len(r["source_sha1"]) == 40
         # a different region never matches the recorded hash
         assert bench.source_sha1(["include/moff.h"]) != r["source_sha1"]
+
+
+def test_row_contraction_byte_model():
+    """Rows reached by some kernel row (anchor rows +- K//2, cyclic) times the
+    half2 row, plus the FP16 real and imaginary voltage planes."""
+    import numpy as np
+    pos = np.array([[3.2, 5.4], [9.0, 6.0], [1.0, 12.49]])      # anchor rows 5, 6, 12
+    assert bench.tc_row_bytes_per_snapshot(pos, N=16, P=2, K=3) == 2 * 7 * 16 * 4 + 3 * 2 * 2 * 2
+    wrap = np.array([[0.0, 15.6]])                                # anchor row 16 -> 0: rows 15, 0, 1
+    assert bench.tc_row_bytes_per_snapshot(wrap, N=16, P=1, K=3) == 1 * 3 * 16 * 4 + 1 * 1 * 2 * 2
