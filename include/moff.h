@@ -64,13 +64,21 @@ typedef enum {
 /* Plan flags. */
 enum {
     MOFF_PREC_FP32 = 0u,      /* all arithmetic in FP32, cross-block sums in FP64 */
-    MOFF_PREC_FP16TC = 1u,    /* gridding and the row transform (Eq. m6 steps 1-3, first axis) as one
-                                 tensor-core contraction per grid row: FP16 operands (weighted
-                                 voltages and each kernel row's FP64-built row spectrum, both under
-                                 exact power-of-two scales), FP32 accumulation; the column transform
-                                 and the squaring stay FP32, cross-block sums FP64.  Needs at most
-                                 128 antennas (4 chunks of 32) whose kernel rows land on any one grid
-                                 row per pol. */
+    MOFF_PREC_FP16TC = 1u,    /* FP16 tensor-core path (FP16 operands under exact power-of-two
+                                 scales, FP32 accumulation, cross-block sums FP64), by one of two
+                                 routes (moff_plan_route):
+                                 row spectra -- gridding and the row transform (Eq. m6 steps 1-3,
+                                   first axis) as one contraction per grid row (weighted voltages x
+                                   each kernel row's FP64-built row spectrum); the column transform
+                                   and the squaring stay FP32.  Taken where at most 128 antennas
+                                   (4 chunks of 32) land their kernel rows on any one grid row per pol;
+                                 factored DFT -- N = 256 or 512 (denser arrays, or environment
+                                   variable MOFF_TC_DFT=1): FP32 gridding, then both transform axes
+                                   as factored DFT contractions (N = 16 x N/16, twiddles between the
+                                   two factors; DFT and twiddle tables built in FP64), the column
+                                   half fused with the squaring; the field between the two axes is
+                                   FP16.  Feedback calibration and tied-array beams are not
+                                   available on this route (MOFF_EINVAL). */
     MOFF_FSTAGE = 1u << 1,    /* enable the polyphase F-stage (moff_submit_adc, moff_channelise) */
     MOFF_JONES = 1u << 2,     /* kernels are full 2x2 Jones matrices (n_pol must be 2) */
     MOFF_SERVED = 1u << 3,    /* the plan does not own its per-block scratch (the row-transformed
@@ -221,6 +229,15 @@ moff_status moff_reset(moff_plan *plan);
 /* moff_plan_info -- sizes chosen at plan creation (any pointer may be NULL). */
 moff_status moff_plan_info(const moff_plan *plan, int *n_prod, int *rows_per_stripe,
                            int *time_chunk, int *chan_chunk, long long *device_bytes);
+
+/*
+ * moff_plan_route -- which arithmetic the plan's imaging takes: 0 the FP32 path
+ * (gather gridding, both transform axes as FP32 FFTs), 1 the FP16 row-spectrum
+ * contraction + FP32 column FFT, 2 FP32 gridding + both axes as factored
+ * tensor-core DFT contractions (see MOFF_PREC_FP16TC).  MOFF_EINVAL for a NULL
+ * argument.
+ */
+moff_status moff_plan_route(const moff_plan *plan, int *route);
 
 /*
  * ---- Feedback calibration (Sec. 6, Eqs. FBeq1-FBeq3): correlate the

@@ -24,7 +24,7 @@ __all__ = [
     "MoffError", "lib", "build", "LIB_PATH", "MOFF_FSTAGE", "MOFF_JONES", "MOFF_PREC_FP32", "MOFF_PREC_FP16TC",
     "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
-    "moff_plan_info", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
+    "moff_plan_info", "moff_plan_route", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
     "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "moff_plan_tuning",
     "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
     "moff_server_destroy", "moff_set_calibrator", "moff_read_feedback", "moff_feedback_gains",
@@ -73,6 +73,7 @@ _SIGS = {
     "moff_reset": [_vp],
     "moff_plan_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                        ctypes.POINTER(_ll)],
+    "moff_plan_route": [_vp, ctypes.POINTER(_i)],
     "moff_plan_destroy": [_vp],
     "moff_set_timing": [_vp, _i],
     "moff_timing": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
@@ -250,6 +251,16 @@ def moff_plan_info(plan):
                                 ctypes.byref(e)))
     return dict(n_prod=a.value, rows_per_stripe=b.value, time_chunk=c.value, chan_chunk=d.value,
                 device_bytes=e.value)
+
+
+ROUTES = {0: "fp32", 1: "fp16_rowspec", 2: "fp16_dft"}
+
+
+def moff_plan_route(plan) -> str:
+    """The plan's arithmetic route: "fp32", "fp16_rowspec" or "fp16_dft" (see MOFF_PREC_FP16TC)."""
+    r = ctypes.c_int()
+    _check(lib().moff_plan_route(plan, ctypes.byref(r)))
+    return ROUTES[r.value]
 
 
 def moff_plan_tuning(plan):
@@ -517,6 +528,9 @@ class Plan:
 
     def info(self):
         return moff_plan_info(self.handle)
+
+    def route(self):
+        return moff_plan_route(self.handle)
 
     def set_timing(self, on=True):
         moff_set_timing(self.handle, on)

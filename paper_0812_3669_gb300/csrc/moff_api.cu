@@ -259,6 +259,14 @@ struct moff_plan {
     size_t h_bytes = 0, y_bytes = 0, scratch_bytes = 0;
     __half *d_rs_bimg = nullptr, *d_yre = nullptr, *d_yim = nullptr;
     float *d_sy = nullptr;
+    // dense tensor-core transform (MOFF_PREC_FP16TC at N = 256 or 512 where the row-spectrum
+    // contraction does not apply, or MOFF_TC_DFT=1): factored-DFT table image, the kernel scale
+    // (power of two: the gridded field times sy[c] * dft_s_t stays within FP16), and the
+    // gridding kernel's shared memory for a grid-only (FP32 transform) launch
+    bool dft = false;
+    unsigned char *d_dft_tab = nullptr;
+    float dft_s_t = 1.f;
+    size_t grid_smem_fft = 0;
 
     long long n_samples = 0;
     size_t dev_bytes = 0;
@@ -672,7 +680,48 @@ moff_status launch_block(moff_plan *pl, int kind, const void *in, long long n, l
     return MOFF_OK;
 }
 
+// Dense FP16 path: gridding + row transform on the tensor cores, then the column transform
+// + square-and-integrate on the tensor cores, per (Tb, Cb) chunk.
+moff_status run_image_dft(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
+    const int cpl = pl->quads ? 4 : (pl->pairs ? 2 : 1);
+    for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
+        const int nc = std::min(pl->Cb, pl->C - c0);
+        for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
+            const int nt = std::min(pl->Tb, n_time - t0);
+            GridArgs g = grid_args(pl, volt, tstride, t0, nt, c0, nc);
+            g.out = nullptr;
+            g.h16 = reinterpret_cast<__half *>(pl->d_H);
+            g.sy = pl->d_sy;
+            g.s_t = pl->dft_s_t;
+            g.dft_tab = pl->d_dft_tab;
+            g.err = pl->d_err;
+            TimedLaunch tg(pl, 1);
+            MOFF_CK(launch_grid_dft(pl->N, pl->P, pl->tb, cpl, g, pl->n_stripes, pl->grid_smem, pl->st));
+            tg.done();
+            ColDftArgs ca{};
+            ca.H = reinterpret_cast<const __half *>(pl->d_H);
+            ca.slab_t = g.slab_t;
+            ca.slab_c = g.slab_c;
+            ca.nt = nt;
+            ca.c0 = c0;
+            ca.nc = nc;
+            ca.acc = pl->d_acc;
+            ca.row_nz = pl->d_row_nz;
+            ca.sy = pl->d_sy;
+            ca.s_t = pl->dft_s_t;
+            ca.dft_tab = pl->d_dft_tab;
+            ca.err = pl->d_err;
+            TimedLaunch tc(pl, 2);
+            MOFF_CK(launch_cols_dft(pl->N, pl->P, ca, pl->st));
+            tc.done();
+            MOFF_CK_S(run_feedback(pl, volt, tstride, t0, nt, c0, nc));
+        }
+    }
+    return MOFF_OK;
+}
+
 moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
+    if (pl->dft) return run_image_dft(pl, volt, n_time, tstride);
     if (pl->tc) return run_image_tc(pl, volt, n_time, tstride);
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
         const int nc = std::min(pl->Cb, pl->C - c0);
@@ -732,7 +781,7 @@ moff_status fail_msg(moff_status s, const char *msg) { return fail(s, "%s", msg)
 // lists (host only).  The stripe height is the largest power of two <= 16
 // whose lists fit the gridding kernel's shared-memory budget.
 moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b,
-                       const GridChoice *force) {
+                       const GridChoice *force, bool dft) {
     const int h = K / 2;
     std::vector<int> ax(A), ay(A);
     for (int a = 0; a < A; ++a) {
@@ -746,7 +795,8 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
     const int pin_n = jones ? 2 : 1;   // input pols per output pol
     const int tw_total = fft_tw_total(N);
     const char *wide_env = getenv("MOFF_GRID_WIDE");
-    const bool wide = force ? force->wide : (wide_env && atoi(wide_env) != 0);
+    // the tensor-core row transform runs on stripes of grid_fft_rows(N) rows with entries through L2
+    const bool wide = !dft && (force ? force->wide : (wide_env && atoi(wide_env) != 0));
     const int F = grid_fft_rows(N) * (wide ? 2 : 1);
     const size_t budget = 110 * 1024;   // two CTAs per SM
     const size_t big = 225 * 1024;      // one CTA per SM: dense arrays, where more samples per pass reuse each tap
@@ -804,20 +854,21 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
             ment = std::max(ment, e);
         }
         Cand cd{tb, rows, mnl, ment,
-                grid_smem_bytes(N, P, tb, rows, mnl, tw_total, (int)std::min<long long>(ment, 1 << 28), pairs),
-                grid_smem_bytes(N, P, tb, rows, mnl, tw_total, 0, pairs)};
+                dft ? (size_t)1 << 40
+                    : grid_smem_bytes(N, P, tb, rows, mnl, tw_total, (int)std::min<long long>(ment, 1 << 28), pairs),
+                dft ? grid_smem_bytes_dft(N, P, tb, rows, mnl) : grid_smem_bytes(N, P, tb, rows, mnl, tw_total, 0, pairs)};
         cands.push_back(cd);
     }
     // Entries are read through L2 by default (more CTAs per SM measured faster
     // than shared-memory staging); MOFF_GRID_STAGE=1 prefers staging.
     const char *stage_env = getenv("MOFF_GRID_STAGE");
-    const bool prefer_staged = stage_env && atoi(stage_env) != 0;
+    const bool prefer_staged = !dft && stage_env && atoi(stage_env) != 0;
     const Cand *pick = nullptr;
     bool staged = false;
     if (force) {
         for (const Cand &cd : cands)
             if (cd.tb == force->tb) {
-                const bool fits = (force->staged ? cd.sm_staged : cd.sm_plain) <= big &&
+                const bool fits = !(dft && force->staged) && (force->staged ? cd.sm_staged : cd.sm_plain) <= big &&
                                   !(quads && (force->staged || cd.rows % 2));
                 if (fits) { pick = &cd; staged = force->staged; }
                 break;
@@ -987,6 +1038,35 @@ moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos
 }
 
 std::vector<float2> pass_twiddles_for(int n) { return pass_twiddles_n(n); }
+
+// Power of two s with s * max over grid cells (each output pol) of the sum of |tap| of the
+// kernel contributions landing there <= 1: with |y sy[c]| < 2^14 (k_gain_scale) the gridded
+// field times sy[c] * s stays below 2^14 in magnitude, and so does every stage of the
+// factored transform (each stage's growth is undone by its power-of-two factor).
+float dft_kernel_scale(int A, int K, int N, int P, bool jones, const double *pos, const float *taps) {
+    const int h = K / 2, pin_n = jones ? 2 : 1;
+    std::vector<double> sum((size_t)P * N * N, 0.0);
+    for (int a = 0; a < A; ++a) {
+        const long long fx = (long long)std::floor(pos[2 * a] + 0.5), fy = (long long)std::floor(pos[2 * a + 1] + 0.5);
+        const int ax = (int)(((fx % N) + N) % N), ay = (int)(((fy % N) + N) % N);
+        for (int po = 0; po < P; ++po)
+            for (int k = 0; k < pin_n; ++k) {
+                const int pi = jones ? k : po;
+                for (int iy = 0; iy < K; ++iy)
+                    for (int ix = 0; ix < K; ++ix) {
+                        float re, im;
+                        tap_at(jones, P, K, taps, a, po, pi, iy, ix, &re, &im);
+                        sum[((size_t)po * N + (ay + iy - h + N) % N) * N + (ax + ix - h + N) % N] +=
+                            std::sqrt((double)re * re + (double)im * im);
+                    }
+            }
+    }
+    const double mx = *std::max_element(sum.begin(), sum.end());
+    if (!(mx > 0.0)) return 1.f;
+    int e = 0;
+    std::frexp(mx, &e);   // mx in [2^(e-1), 2^e)
+    return (float)std::ldexp(1.0, -e);
+}
 
 // Row spectra of every kernel row (segment) for the tensor-core path, as
 // K-major core-matrix images per (pol, grid row, kx tile) -- see
@@ -1175,7 +1255,7 @@ namespace {
 moff_status build_bin_sets(const moff_plan *pl, int n_sets, const double *pos, const float *taps,
                            const GridChoice *force, Bins *out) {
     const int A = pl->A, K = pl->K, N = pl->N, P = pl->P;
-    if (n_sets == 1) return build_bins(A, K, N, P, pl->jones, pos, taps, out, force);
+    if (n_sets == 1) return build_bins(A, K, N, P, pl->jones, pos, taps, out, force, pl->dft);
     const size_t pos_set = (size_t)A * 2;
     const size_t tap_set = (size_t)A * P * (pl->jones ? 2 : 1) * K * K * 2;
     std::vector<GridChoice> cands;
@@ -1191,7 +1271,8 @@ moff_status build_bin_sets(const moff_plan *pl, int n_sets, const double *pos, c
             workers.emplace_back([&, w] {
                 for (int g = w; g < n_sets; g += nthr) {
                     bins[g] = Bins{};
-                    st[g] = build_bins(A, K, N, P, pl->jones, pos + g * pos_set, taps + g * tap_set, &bins[g], &ch);
+                    st[g] = build_bins(A, K, N, P, pl->jones, pos + g * pos_set, taps + g * tap_set, &bins[g], &ch,
+                                       pl->dft);
                 }
             });
         for (std::thread &t : workers) t.join();
@@ -1201,7 +1282,7 @@ moff_status build_bin_sets(const moff_plan *pl, int n_sets, const double *pos, c
         if (bad >= 0) {
             if (&ch == &cands.back()) {   // the message of the first set that fits no shape
                 Bins tmp;
-                return build_bins(A, K, N, P, pl->jones, pos + bad * pos_set, taps + bad * tap_set, &tmp, &ch);
+                return build_bins(A, K, N, P, pl->jones, pos + bad * pos_set, taps + bad * tap_set, &tmp, &ch, pl->dft);
             }
             continue;
         }
@@ -1219,8 +1300,9 @@ moff_status build_bin_sets(const moff_plan *pl, int n_sets, const double *pos, c
             o.max_nloc = std::max(o.max_nloc, b.max_nloc);
             o.max_entries = std::max(o.max_entries, b.max_entries);
         }
-        o.grid_smem = grid_smem_bytes(N, P, o.tb, o.rows, o.max_nloc, fft_tw_total(N), o.staged ? o.max_entries : 0,
-                                      o.pairs);
+        o.grid_smem = pl->dft ? grid_smem_bytes_dft(N, P, o.tb, o.rows, o.max_nloc)
+                              : grid_smem_bytes(N, P, o.tb, o.rows, o.max_nloc, fft_tw_total(N),
+                                                o.staged ? o.max_entries : 0, o.pairs);
         if (o.grid_smem > 225 * 1024) continue;
         const size_t tpe = o.quads ? 4 : (o.pairs ? 2 : 1);
         long long ebase = 0;
@@ -1288,6 +1370,8 @@ moff_status upload_bins(moff_plan *pl, const Bins &b) {
     pl->max_nloc = b.max_nloc;
     pl->n_slices = b.n_slices;
     pl->grid_smem = b.grid_smem;
+    pl->grid_smem_fft = pl->dft ? grid_smem_bytes(pl->N, pl->P, b.tb, b.rows, b.max_nloc, fft_tw_total(pl->N), 0, b.pairs)
+                                : b.grid_smem;
     return MOFF_OK;
 }
 
@@ -1446,8 +1530,9 @@ std::string tune_key(const moff_plan *pl, const double *pos, const float *taps) 
     h = fnv1a(prop.name, strlen(prop.name), h);
     char buf[128];
     // the prefix changes with the gridding kernels, so picks timed on an older build are not reused
-    snprintf(buf, sizeof buf, "grid6-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->A, pl->K, pl->N, pl->P,
-             (int)pl->jones, pl->Tb, std::min(pl->Cb, pl->C), prop.multiProcessorCount, (unsigned long long)h);
+    snprintf(buf, sizeof buf, "%s-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->dft ? "gdft1" : "grid6", pl->A, pl->K,
+             pl->N, pl->P, (int)pl->jones, pl->Tb, std::min(pl->Cb, pl->C), prop.multiProcessorCount,
+             (unsigned long long)h);
     return buf;
 }
 
@@ -1478,11 +1563,11 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     const int N = pl->N, P = pl->P, A = pl->A, nt = pl->Tb;
     const int nc = std::min(pl->Cb, pl->C);
     const long long tstride = (long long)nc * A * P;
-    void *volt = nullptr, *gains = nullptr, *Htmp = nullptr, *twp = nullptr;
+    void *volt = nullptr, *gains = nullptr, *Htmp = nullptr, *twp = nullptr, *sy = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     std::vector<float2> tw = pass_twiddles_n(N);
     auto cleanup = [&] {
-        cudaFree(volt); cudaFree(gains); cudaFree(Htmp); cudaFree(twp);
+        cudaFree(volt); cudaFree(gains); cudaFree(Htmp); cudaFree(twp); cudaFree(sy);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
@@ -1492,7 +1577,7 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     }
     void *H = pl->d_H ? static_cast<void *>(pl->d_H) : Htmp;
     if (cudaMalloc(&volt, (size_t)nt * tstride) != cudaSuccess || cudaMalloc(&gains, (size_t)nc * A * P * 8) != cudaSuccess ||
-        cudaMalloc(&twp, tw.size() * 8) != cudaSuccess ||
+        cudaMalloc(&twp, tw.size() * 8) != cudaSuccess || cudaMalloc(&sy, (size_t)nc * 4) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cleanup();
         cudaGetLastError();
@@ -1500,7 +1585,9 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     }
     // every voltage (3, 5), unit gains: the gridding work does not depend on the values
     std::vector<float2> one((size_t)nc * A * P, make_float2(1.f, 0.f));
+    std::vector<float> ones((size_t)nc, 1.f);
     if (cudaMemsetAsync(volt, 0x35, (size_t)nt * tstride, pl->st) != cudaSuccess ||
+        cudaMemcpy(sy, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(gains, one.data(), one.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(twp, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
         cleanup();
@@ -1510,12 +1597,15 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
     float best_ms = 0.f;
     for (int tb = 8; tb >= 1; tb /= 2)
         for (int cand = 0; cand < 10; ++cand) {
-            // cand 0-7: staged x pairs x wide; 8, 9: 2 x 2 blocks (entries through L2), without and with wide
+            // cand 0-7: staged x pairs x wide; 8, 9: 2 x 2 blocks (entries through L2), without and with wide.
+            // The tensor-core row transform: entries through L2, no wide stripes (cand 0, 2, 8).
+            if (pl->dft && cand != 0 && cand != 2 && cand != 8) continue;
             const GridChoice ch = cand < 8 ? GridChoice{tb, (cand & 1) != 0, (cand & 2) != 0, (cand & 4) != 0, false}
                                            : GridChoice{tb, false, false, cand == 9, true};
             moff_plan tmp;
             tmp.A = A; tmp.K = pl->K; tmp.N = N; tmp.C = nc; tmp.P = P; tmp.jones = pl->jones;
             tmp.device = pl->device;
+            tmp.dft = pl->dft;
             if (bin_plan(&tmp, pos, taps, &ch) != MOFF_OK) {
                 for (void *q : tmp.allocs) cudaFree(q);
                 continue;
@@ -1525,13 +1615,25 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
             tmp.d_H = static_cast<float2 *>(H);
             tmp.Tb = nt;
             tmp.Cb = nc;
-            const GridArgs g = grid_args(&tmp, static_cast<const uint8_t *>(volt), tstride, 0, nt, 0, nc);
+            GridArgs g = grid_args(&tmp, static_cast<const uint8_t *>(volt), tstride, 0, nt, 0, nc);
+            if (pl->dft) {
+                g.out = nullptr;
+                g.h16 = static_cast<__half *>(H);
+                g.sy = static_cast<const float *>(sy);
+                g.s_t = pl->dft_s_t;
+                g.dft_tab = pl->d_dft_tab;
+                g.err = pl->d_err;
+            }
+            const int cpl = tmp.quads ? 4 : (tmp.pairs ? 2 : 1);
+            auto launch = [&] {
+                return pl->dft ? launch_grid_dft(N, P, tmp.tb, cpl, g, tmp.n_stripes, tmp.grid_smem, pl->st)
+                               : launch_grid(N, P, tmp.tb, tmp.staged, false, g, tmp.n_stripes, tmp.grid_smem, pl->st);
+            };
             float ms = 0.f;
-            bool ok = launch_grid(N, P, tmp.tb, tmp.staged, false, g, tmp.n_stripes, tmp.grid_smem, pl->st) == cudaSuccess;
+            bool ok = launch() == cudaSuccess;
             for (int r = 0; ok && r < 3; ++r) {
                 float t = 0.f;
-                ok = cudaEventRecord(e0, pl->st) == cudaSuccess &&
-                     launch_grid(N, P, tmp.tb, tmp.staged, false, g, tmp.n_stripes, tmp.grid_smem, pl->st) == cudaSuccess &&
+                ok = cudaEventRecord(e0, pl->st) == cudaSuccess && launch() == cudaSuccess &&
                      cudaEventRecord(e1, pl->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
                      cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
                 if (ok && (r == 0 || t < ms)) ms = t;
@@ -1656,7 +1758,7 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
     unsigned char *base = static_cast<unsigned char *>(scratch);
     pl->d_H = reinterpret_cast<float2 *>(base);
     size_t off = align_up(pl->h_bytes, 1024);
-    if (pl->tc) {
+    if (pl->tc && !pl->dft) {
         pl->d_yre = reinterpret_cast<__half *>(base + off);
         off += align_up(pl->y_bytes, 1024);
         pl->d_yim = reinterpret_cast<__half *>(base + off);
@@ -1721,6 +1823,21 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     pl->fstage = (flags & MOFF_FSTAGE) != 0;
     pl->tc = (flags & MOFF_PREC_FP16TC) != 0;
     pl->served = (flags & MOFF_SERVED) != 0;
+    // FP16 path at N = 256 / 512: the row-spectrum contraction where the array's rows are sparse
+    // enough for it, else (or with MOFF_TC_DFT=1) the factored DFT contractions
+    RowSpec rs_probe;
+    bool have_probe = false;
+    if (pl->tc && (grid_n == 256 || grid_n == 512)) {
+        const char *e = getenv("MOFF_TC_DFT");
+        if (e && atoi(e) == 1) {
+            pl->dft = true;
+        } else if (!(e && atoi(e) == 0)) {
+            if (build_rowspec(n_ant, ksize, grid_n, n_pol, (flags & MOFF_JONES) != 0, pos, taps, &rs_probe) == MOFF_OK)
+                have_probe = true;
+            else
+                pl->dft = true;   // too dense for the row-spectrum contraction (or invalid: reported below)
+        }
+    }
     pl->graphs = (flags & MOFF_GRAPH) != 0;
     if (!pl->jones) {
         pl->h_taps.assign(taps, taps + (size_t)n_ant * n_pol * ksize * ksize * 2);
@@ -1788,7 +1905,13 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             const long long n = (n_chan + cb_max - 1) / cb_max;
             return (n_chan + n - 1) / n;
         };
-        if (pl->tc) {
+        if (pl->dft) {
+            // FP16 field only; up to 128 samples per chunk (FP32 sums per chunk, then FP64)
+            const long long cb = balance(std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per))));
+            const long long tb = std::max(1LL, std::min<long long>(128, budget / (long long)(cb * per)));
+            pl->Cb = (int)cb;
+            pl->Tb = (int)tb;
+        } else if (pl->tc) {
             // the tensor-core path works on 128 samples per product
             const size_t per_c = 128 * per + ((size_t)n_ant * n_pol + kRowSpecPad) * 128 * 4;
             pl->Tb = 128;
@@ -1802,22 +1925,39 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         pl->h_bytes = (size_t)pl->Tb * pl->Cb * per;
         if (!pl->served) {
             if ((s = palloc(pl, &pl->d_H, pl->h_bytes)) != MOFF_OK) return bail(s);
-            if (pl->tc && encode_field_map(&pl->h_map, pl->d_H, grid_n, n_pol, pl->Cb, pl->Tb) != cudaSuccess)
+            if (pl->tc && !pl->dft && encode_field_map(&pl->h_map, pl->d_H, grid_n, n_pol, pl->Cb, pl->Tb) != cudaSuccess)
                 return bail(fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded"));
             pl->h_map_nt = pl->Tb;
         }
     }
+    if (pl->dft) {
+        // factored-DFT tables, and the kernel scale: every cell's sum of |tap| over its contributions
+        // (all output pols) times dft_s_t is at most 1, so |G| sy[c] dft_s_t <= 2^14
+        std::vector<unsigned char> tab = build_dft_table(grid_n);
+        if ((s = palloc(pl, &pl->d_dft_tab, tab.size())) != MOFF_OK) return bail(s);
+        if (cudaMemcpy(pl->d_dft_tab, tab.data(), tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "tensor-core DFT table upload failed"));
+        pl->dft_s_t = dft_kernel_scale(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps);
+        if ((s = palloc(pl, &pl->d_sy, (size_t)n_chan * 4)) != MOFF_OK) return bail(s);
+        if ((s = palloc(pl, &pl->d_err, 16)) != MOFF_OK) return bail(s);
+        if (cudaMemset(pl->d_err, 0, 16) != cudaSuccess) return bail(fail(MOFF_ECUDA, "memset failed"));
+        if (launch_gain_scale(pl->d_gains, n_chan, n_ant * n_pol, pl->d_sy, pl->st) != cudaSuccess)
+            return bail(fail(MOFF_ECUDA, "gain scale kernel failed"));
+    }
     // gridding shape: measured on the plan's own chunk (MOFF_AUTOTUNE), else the built-in rule
     {
         GridChoice tuned;
-        if ((flags & MOFF_AUTOTUNE) && !pl->tc) {
+        if ((flags & MOFF_AUTOTUNE) && (!pl->tc || pl->dft)) {
             if ((s = tune_grid(pl, pos, taps, &tuned)) != MOFF_OK) return bail(s);
         }
         if ((s = bin_plan(pl, pos, taps, pl->tune_source ? &tuned : nullptr)) != MOFF_OK) return bail(s);
     }
-    if (pl->tc) {
+    if (pl->tc && !pl->dft) {
         RowSpec rs;
-        if ((s = build_rowspec(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps, &rs)) != MOFF_OK) return bail(s);
+        if (have_probe)
+            rs = std::move(rs_probe);
+        else if ((s = build_rowspec(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps, &rs)) != MOFF_OK)
+            return bail(s);
         pl->rs_kp_max = std::max(rs.kp_max, 16);
         pl->rs_inv_sw = rs.inv_sw;
         pl->rs_smem = rowspec_smem_bytes(grid_n, pl->rs_kp_max);
@@ -1895,7 +2035,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
                 return bail(fail(MOFF_ECUDA, "F-stage table upload failed"));
         }
     }
-    pl->scratch_bytes = align_up(pl->h_bytes, 1024) + (pl->tc ? 2 * align_up(pl->y_bytes, 1024) : 0);
+    pl->scratch_bytes = align_up(pl->h_bytes, 1024) + (pl->tc && !pl->dft ? 2 * align_up(pl->y_bytes, 1024) : 0);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(MOFF_ECUDA, "plan set-up failed"));
     *out = pl;
     g_err.clear();
@@ -2157,7 +2297,7 @@ moff_status moff_grid_snapshot(moff_plan *pl, const uint8_t *volt, int on_device
         src = reinterpret_cast<const uint8_t *>(dev);
     }
     GridArgs g = grid_args(pl, src, 0, 0, 1, chan, 1);
-    MOFF_CK(launch_grid(pl->N, pl->P, pl->tb, false, true, g, pl->n_stripes, pl->grid_smem, pl->st));
+    MOFF_CK(launch_grid(pl->N, pl->P, pl->tb, false, true, g, pl->n_stripes, pl->grid_smem_fft, pl->st));
     if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
     MOFF_CK(cudaMemcpyAsync(out, pl->d_H, (size_t)pl->P * pl->N * pl->N * 8, cudaMemcpyDeviceToHost, pl->st));
     return sync_plan(pl, -1);
@@ -2272,6 +2412,8 @@ moff_status moff_set_beams(moff_plan *pl, int n_beams, const int *kx, const int 
     if (s != MOFF_OK) return s;
     if (n_beams < 0 || n_beams > kMaxBeams) return fail(MOFF_EINVAL, "n_beams (%d) must be in [0, %d]", n_beams, kMaxBeams);
     if (n_beams && (!kx || !ky)) return fail(MOFF_EINVAL, "kx and ky must not be NULL");
+    if (n_beams && pl->dft)
+        return fail(MOFF_EINVAL, "tied-array beams are not available on the factored-DFT tensor-core route");
     for (int j = 0; j < n_beams; ++j)
         if (kx[j] < 0 || kx[j] >= pl->N || ky[j] < 0 || ky[j] >= pl->N)
             return fail(MOFF_EINVAL, "beam %d pixel (%d, %d) outside the %d x %d image", j, kx[j], ky[j], pl->N, pl->N);
@@ -2318,6 +2460,7 @@ moff_status moff_set_calibrator(moff_plan *pl, int kx, int ky) {
         return MOFF_OK;
     }
     if (pl->jones) return fail(MOFF_EINVAL, "feedback calibration needs one kernel per pol (not MOFF_JONES)");
+    if (pl->dft) return fail(MOFF_EINVAL, "feedback calibration is not available on the factored-DFT tensor-core route");
     if (kx < 0 || kx >= pl->N || ky < 0 || ky >= pl->N)
         return fail(MOFF_EINVAL, "calibrator pixel (%d, %d) outside the %d x %d image", kx, ky, pl->N, pl->N);
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
@@ -2416,6 +2559,12 @@ moff_status moff_timing(moff_plan *pl, int kind, double *total_ms, long long *la
     if (total_ms) *total_ms = tot;
     if (launches) *launches = n;
     if (reset) clear_recs(pl);
+    return MOFF_OK;
+}
+
+moff_status moff_plan_route(const moff_plan *pl, int *route) {
+    if (!pl || !route) return fail(MOFF_EINVAL, "plan and route must not be NULL");
+    *route = pl->dft ? 2 : (pl->tc ? 1 : 0);
     return MOFF_OK;
 }
 

@@ -1,0 +1,360 @@
+// moff_dft_kernels.cu -- the column half of Eq. m6 step 3 (Morales, arXiv
+// 0812.3669) as factored DFT contractions on the tensor cores, fused with step 4
+// (|E|^2 and the cross-pol products summed over a chunk, then added to the FP64
+// accumulators), for the dense FP16 path.  The row half runs inside the
+// gridding kernel (k_grid_rows_dft, moff_dft.cuh).
+//
+//   k_cols_dft  one CTA = 16 columns of one channel walking a chunk of samples.
+//               Per sample: the FP16 field's 16-column strip (cp.async, 32-byte
+//               pieces of the reached rows) lands as the stage-1 A operand
+//               (rows (b, x), k = (a, re/im)); stage 1 on the tensor cores; the
+//               twiddled FP32 result is written back as the stage-2 A operand
+//               (128-byte swizzled, rows (c, x)); stage 2 leaves E in TMEM,
+//               where the epilogue squares and sums it.  Loads of sample t + 1 and
+//               stage 1 of sample t run while the epilogue of sample t - 1 works.
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "moff_dft.cuh"
+#include "moff_fft.cuh"
+#include "moff_internal.h"
+#include "moff_tc.cuh"
+
+namespace moff {
+namespace {
+
+// exp(2 pi i m / L) with the angle reduced exactly (m mod L), in FP64.
+void unit_root(long long m, long long L, double *c, double *s) {
+    long long r = m % L;
+    if (r < 0) r += L;
+    const double ang = 2.0 * 3.14159265358979323846264338327950288 * (double)r / (double)L;
+    *c = std::cos(ang);
+    *s = std::sin(ang);
+}
+
+// Byte offset of element (n, k) of a K-major operand image with K columns
+// (8 x 8 core matrices of 128 bytes; along K 128 bytes apart, along rows (K/8) * 128).
+size_t kmajor_at(int n, int k, int K) {
+    return (size_t)(n >> 3) * (K >> 3) * 128 + (size_t)(k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+}
+
+template <int N, int P>
+struct ColDftShape {
+    using S = DftShape<N>;
+    static constexpr int W = 16;                       // columns per CTA
+    static constexpr int N2 = S::N2;
+    static constexpr int M1 = W * N2;                  // stage-1 rows per pol: m = 16 b + x
+    static constexpr int T1 = M1 / 128;
+    static constexpr int LBO1 = (M1 / 8) * 128;        // stage-1 A: K-direction core-matrix stride
+    static constexpr int A1P = M1 * S::K1 * 2;         // bytes of one pol's stage-1 A
+    static constexpr int M2 = 16 * W;                  // stage-2 rows per pol: m2 = 128 c_hi + 8 x + c_lo
+    static constexpr int T2 = M2 / 128;
+    static constexpr int A2P = M2 * S::K2 * 2;         // bytes of one pol's stage-2 A (128-byte swizzled)
+    static constexpr int D1 = P * T1 * S::C1;          // TMEM columns: stage-1 accumulators
+    static constexpr int D2 = P * T2 * S::C2;          // then stage-2 accumulators
+    static constexpr int TC_ = D1 + D2;
+    static constexpr int TCOLS = TC_ <= 32 ? 32 : (TC_ <= 64 ? 64 : (TC_ <= 128 ? 128 : (TC_ <= 256 ? 256 : 512)));
+    static constexpr int NPIECE = P * N * 4;           // 16-byte pieces per sample: (p, ry, re/im, x half)
+    static constexpr int ITER = NPIECE / kBlock;
+    static constexpr size_t SMEM = 1024 + (size_t)P * A2P + 2 * (size_t)P * A1P + S::TAB_BYTES + 32;
+    static_assert(T2 == 2 && TC_ <= 512 && NPIECE % kBlock == 0 && ITER <= 32, "column-kernel shape");
+};
+
+template <int N, int P>
+__global__ void __launch_bounds__(kBlock, 1) k_cols_dft(const ColDftArgs a) {
+    using S = DftShape<N>;
+    using CS = ColDftShape<N, P>;
+    constexpr int W = CS::W, N2 = S::N2, K2 = S::K2, C2 = S::C2;
+    constexpr int NPROD = P == 1 ? 1 : 4;
+    const int x0 = blockIdx.x * W, cl = blockIdx.y, c = a.c0 + cl;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3;
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // the swizzled stage-2 operand needs a 1024-byte aligned base (the size includes the slack)
+    unsigned char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char *sA2 = smem;                                   // [P][A2P]
+    unsigned char *sA1 = sA2 + P * CS::A2P;                      // [2 buffers][P][A1P]
+    unsigned char *sTab = sA1 + 2 * P * CS::A1P;
+    const unsigned char *sB1 = sTab, *sB2 = sTab + S::B1_BYTES;
+    const float2 *sTw = reinterpret_cast<const float2 *>(sB2 + S::B2_BYTES);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sTab + S::TAB_BYTES);   // [0] stage 1, [1] stage 2
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+
+    dftc::load_table(sTab, a.dft_tab, S::TAB_BYTES);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, CS::TCOLS);
+        tc::tmem_relinquish();
+    }
+    // Piece i = tid + k kBlock of a sample: pol p, row ry, re/im ri, column half h.  Rows no
+    // kernel reaches are zero: cleared once in both buffers and never loaded.
+    auto piece_dst = [&](int i) -> uint32_t {
+        const int p = i / (4 * N), r = i - p * 4 * N, ry = r >> 2, ri = (r >> 1) & 1, h = r & 1;
+        const int aa = ry / N2, b = ry - aa * N2, k = 2 * aa + ri;
+        return (uint32_t)(p * CS::A1P + (2 * b + h) * 128 + (k >> 3) * CS::LBO1 + (k & 7) * 16);
+    };
+    uint32_t act = 0;
+#pragma unroll
+    for (int k = 0; k < CS::ITER; ++k) {
+        const int i = tid + k * kBlock, ry = (i % (4 * N)) >> 2;
+        if ((a.row_nz[ry >> 5] >> (ry & 31)) & 1u) {
+            act |= 1u << k;
+        } else {
+            const uint32_t d = piece_dst(i);
+            *reinterpret_cast<uint4 *>(sA1 + d) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(sA1 + P * CS::A1P + d) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    auto stage = [&](int tt, int buf) {
+        const __half *src = a.H + ((long long)tt * a.slab_t + (long long)cl * a.slab_c) * P * N * 2 * N + x0;
+        unsigned char *dst = sA1 + buf * P * CS::A1P;
+#pragma unroll
+        for (int k = 0; k < CS::ITER; ++k) {
+            if ((act >> k) & 1u) {
+                const int i = tid + k * kBlock;
+                const int p = i / (4 * N), r = i - p * 4 * N, ry = r >> 2, ri = (r >> 1) & 1, h = r & 1;
+                cp_async16(dst + piece_dst(i), src + ((long long)(p * N + ry) * 2 + ri) * N + 8 * h);
+            }
+        }
+        cp_async_commit();
+    };
+    auto issue_s1 = [&](int buf) {
+        tc::fence_after_sync();
+        const uint32_t id1 = tc::idesc_f16(128, S::C1, true, false);
+        const uint32_t a0 = tc::smem_u32(sA1 + buf * P * CS::A1P), b0 = tc::smem_u32(sB1);
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+            for (int j = 0; j < CS::T1; ++j)
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks)
+                    tc::mma_f16(tbase + (uint32_t)((p * CS::T1 + j) * S::C1),
+                                tc::smem_desc(a0 + p * CS::A1P + j * 2048 + ks * 2 * CS::LBO1, CS::LBO1, 128),
+                                tc::smem_desc(b0 + ks * 256, 128, 512), id1, ks > 0);
+        tc::mma_commit(&mbar[0]);
+    };
+    auto issue_s2 = [&]() {
+        tc::fence_after_sync();
+        const uint32_t id2 = tc::idesc_f16(128, C2, true, false);
+        const uint32_t a0 = tc::smem_u32(sA2), b0 = tc::smem_u32(sB2);
+        constexpr uint32_t SBOB = (K2 / 8) * 128;
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+            for (int j = 0; j < CS::T2; ++j)
+#pragma unroll
+                for (int ks = 0; ks < K2 / 16; ++ks)
+                    tc::mma_f16(tbase + (uint32_t)(CS::D1 + (p * CS::T2 + j) * C2),
+                                tc::smem_desc_sw128(a0 + p * CS::A2P + j * 2 * K2 * 128 + ks * 2048, K2 * 128, 1024),
+                                tc::smem_desc(b0 + ks * 256, 128, SBOB), id2, ks > 0);
+        tc::mma_commit(&mbar[1]);
+    };
+    // Twiddle stage 1's result and write it as stage 2's A: thread (b, x) of tile (p, j)
+    // writes, for c = 8 ch .. 8 ch + 7, the re piece at k = b and the im piece at k = N2 + b.
+    auto epi1 = [&]() {
+        for (int idx = warp >> 2; idx < P * CS::T1; idx += kBlock / 128) {
+            const int p = idx / CS::T1, j = idx - p * CS::T1;
+            const int m = 128 * j + 32 * q + lane, b = m >> 4, x = m & 15;
+            float v[32];
+            tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(idx * S::C1), v);
+            uint32_t re[8], im[8];
+#pragma unroll
+            for (int cc = 0; cc < 16; cc += 2) {
+                const float2 t0 = sTw[cc * N2 + b], t1 = sTw[(cc + 1) * N2 + b];
+                const float x0r = v[2 * cc] * t0.x - v[2 * cc + 1] * t0.y;
+                const float x0i = v[2 * cc] * t0.y + v[2 * cc + 1] * t0.x;
+                const float x1r = v[2 * cc + 2] * t1.x - v[2 * cc + 3] * t1.y;
+                const float x1i = v[2 * cc + 2] * t1.y + v[2 * cc + 3] * t1.x;
+                re[cc >> 1] = dftc::pack_hh(x0r, x1r);
+                im[cc >> 1] = dftc::pack_hh(x0i, x1i);
+            }
+            unsigned char *a2 = sA2 + p * CS::A2P;
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                const int m2 = ch * 128 + x * 8;
+                const int hb = (m2 >> 6) * K2 * 128, cg = (m2 & 63) >> 3;
+                const int kr = b, ki = N2 + b;
+                *reinterpret_cast<uint4 *>(a2 + hb + kr * 128 + ((cg ^ (kr & 7)) << 4)) =
+                    make_uint4(re[4 * ch], re[4 * ch + 1], re[4 * ch + 2], re[4 * ch + 3]);
+                *reinterpret_cast<uint4 *>(a2 + hb + ki * 128 + ((cg ^ (ki & 7)) << 4)) =
+                    make_uint4(im[4 * ch], im[4 * ch + 1], im[4 * ch + 2], im[4 * ch + 3]);
+            }
+        }
+    };
+    // Square and sum: warp (j2, q) holds pixels (ky = 8 j2 + c_lo + 16 d, kx = x0 + x) with
+    // 32 q + lane = 8 x + c_lo, for every d.
+    const int j2 = warp >> 2;
+    float acc[NPROD][N2];
+#pragma unroll
+    for (int pq = 0; pq < NPROD; ++pq)
+#pragma unroll
+        for (int d = 0; d < N2; ++d) acc[pq][d] = 0.f;
+    auto epi2 = [&]() {
+#pragma unroll
+        for (int db = 0; db < N2 / 16; ++db) {
+            float ex[32];
+            tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(CS::D1 + j2 * C2 + 32 * db), ex);
+            if constexpr (P == 1) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    acc[0][16 * db + i] = fmaf(ex[2 * i], ex[2 * i], fmaf(ex[2 * i + 1], ex[2 * i + 1], acc[0][16 * db + i]));
+            } else {
+                float ey[32];
+                tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(CS::D1 + (CS::T2 + j2) * C2 + 32 * db), ey);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float xr = ex[2 * i], xi = ex[2 * i + 1], yr = ey[2 * i], yi = ey[2 * i + 1];
+                    const int d = 16 * db + i;
+                    acc[0][d] = fmaf(xr, xr, fmaf(xi, xi, acc[0][d]));
+                    acc[1][d] = fmaf(yr, yr, fmaf(yi, yi, acc[1][d]));
+                    acc[2][d] = fmaf(xr, yr, fmaf(xi, yi, acc[2][d]));
+                    acc[3][d] = fmaf(xi, yr, fmaf(-xr, yi, acc[3][d]));
+                }
+            }
+        }
+    };
+
+    bool ok = true;
+    if (a.nt > 0) stage(0, 0);
+    for (int t = 0; t < a.nt; ++t) {
+        const int buf = t & 1;
+        cp_async_wait<0>();                    // sample t's strip has landed
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (tid == 0) issue_s1(buf);
+        if (t + 1 < a.nt) stage(t + 1, buf ^ 1);   // its buffer was read by stage 1 of t - 1 (done)
+        if (t > 0) {
+            ok &= tc::mbar_wait_bounded(&mbar[1], (uint32_t)((t - 1) & 1), dftc::kWaitCycles);
+            tc::fence_after_sync();
+            epi2();
+        }
+        ok &= tc::mbar_wait_bounded(&mbar[0], (uint32_t)(t & 1), dftc::kWaitCycles);
+        tc::fence_after_sync();
+        epi1();
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (tid == 0) issue_s2();
+    }
+    if (ok && a.nt > 0) {
+        ok &= tc::mbar_wait_bounded(&mbar[1], (uint32_t)((a.nt - 1) & 1), dftc::kWaitCycles);
+        tc::fence_after_sync();
+        epi2();
+    }
+    cp_async_wait<0>();
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok);
+    tc::fence_after_sync();
+    if (ok) {
+        // undo the field's scale s_G / (16 N) (exact powers of two), squared, and fold into FP64
+        const double un = 16.0 * (double)N / ((double)a.sy[c] * (double)a.s_t);
+        const double sc2 = un * un;
+        const int l = 32 * q + lane, x = l >> 3, cy = 8 * j2 + (l & 7);
+#pragma unroll
+        for (int pq = 0; pq < NPROD; ++pq) {
+            double *dst = a.acc + ((long long)c * NPROD + pq) * N * N + x0 + x;
+#pragma unroll
+            for (int d = 0; d < N2; ++d) dst[(long long)(cy + 16 * d) * N] += (double)acc[pq][d] * sc2;
+        }
+    } else if (tid == 0) {
+        atomicExch(a.err, tc::kErrWaitTimeout);
+    }
+    if (warp == 0) tc::tmem_dealloc(tbase, CS::TCOLS);
+}
+
+template <int N, int P>
+cudaError_t launch_cols_dft_t(const ColDftArgs &a, cudaStream_t st) {
+    auto k = k_cols_dft<N, P>;
+    const size_t smem = ColDftShape<N, P>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(N / ColDftShape<N, P>::W, a.nc), kBlock, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// B1 [n = 2c + re/im][k = 2a + re/im] = the real form of exp(+2 pi i a c / 16);
+// B2 [n = 2d + re/im][k = re/im N2 + b] = that of exp(+2 pi i b d / N2) (both K-major
+// images); twiddles [c][b] = exp(+2 pi i b c / N) / 16.  All in FP64, then rounded once.
+std::vector<unsigned char> build_dft_table(int N) {
+    const int N2 = N / 16, K2 = 2 * N2;
+    std::vector<unsigned char> img((size_t)dft_table_bytes(N), 0);
+    auto put = [&](size_t off, double v) {
+        const __half h = __float2half_rn((float)v);
+        std::memcpy(img.data() + off, &h, 2);
+    };
+    for (int cc = 0; cc < 16; ++cc)
+        for (int aa = 0; aa < 16; ++aa) {
+            double wc, ws;
+            unit_root((long long)aa * cc, 16, &wc, &ws);
+            put(kmajor_at(2 * cc, 2 * aa, 32), wc);
+            put(kmajor_at(2 * cc, 2 * aa + 1, 32), -ws);
+            put(kmajor_at(2 * cc + 1, 2 * aa, 32), ws);
+            put(kmajor_at(2 * cc + 1, 2 * aa + 1, 32), wc);
+        }
+    const size_t b2 = 2048;
+    for (int d = 0; d < N2; ++d)
+        for (int b = 0; b < N2; ++b) {
+            double vc, vs;
+            unit_root((long long)b * d, N2, &vc, &vs);
+            put(b2 + kmajor_at(2 * d, b, K2), vc);
+            put(b2 + kmajor_at(2 * d, N2 + b, K2), -vs);
+            put(b2 + kmajor_at(2 * d + 1, b, K2), vs);
+            put(b2 + kmajor_at(2 * d + 1, N2 + b, K2), vc);
+        }
+    const size_t tw = b2 + (size_t)K2 * K2 * 2;
+    for (int cc = 0; cc < 16; ++cc)
+        for (int b = 0; b < N2; ++b) {
+            double wc, ws;
+            unit_root((long long)b * cc, N, &wc, &ws);
+            const float2 v = make_float2((float)(wc / 16.0), (float)(ws / 16.0));
+            std::memcpy(img.data() + tw + ((size_t)cc * N2 + b) * 8, &v, 8);
+        }
+    return img;
+}
+
+size_t cols_dft_smem_bytes(int N, int P) {
+    if (N == 512) return P == 1 ? ColDftShape<512, 1>::SMEM : ColDftShape<512, 2>::SMEM;
+    if (N == 256) return P == 1 ? ColDftShape<256, 1>::SMEM : ColDftShape<256, 2>::SMEM;
+    return 0;
+}
+
+cudaError_t launch_cols_dft(int N, int P, const ColDftArgs &a, cudaStream_t st) {
+    if (N == 512) return P == 1 ? launch_cols_dft_t<512, 1>(a, st) : launch_cols_dft_t<512, 2>(a, st);
+    if (N == 256) return P == 1 ? launch_cols_dft_t<256, 1>(a, st) : launch_cols_dft_t<256, 2>(a, st);
+    return cudaErrorInvalidValue;
+}
+
+size_t grid_smem_bytes_dft(int N, int P, int TB, int rows, int max_nloc) {
+    const int ldr = N + N / 16;
+    const int F = TB * P * rows;
+    size_t b = (dft_row_region_bytes(N, F) + 15) / 16 * 16;
+    b += (size_t)F * ldr * 8 + 8;                       // one row buffer (+ alignment)
+    b += (size_t)volt_stride(TB) * max_nloc * P * 8;    // calibrated voltages of TB samples
+    b += (size_t)max_nloc * P * 8 + 8;                  // gains (+ padding)
+    b += (size_t)max_nloc * 4;                          // antenna indices
+    return (b + 15) & ~(size_t)15;
+}
+
+cudaError_t launch_grid_dft(int N, int P, int TB, int CPL, const GridArgs &a, int n_stripes, size_t smem,
+                            cudaStream_t st) {
+    if (N == 512) return launch_grid_dft_n512(P, TB, CPL, a, n_stripes, smem, st);
+    if (N == 256) return launch_grid_dft_n256(P, TB, CPL, a, n_stripes, smem, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace moff

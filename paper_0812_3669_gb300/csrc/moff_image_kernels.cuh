@@ -15,6 +15,7 @@
 #pragma once
 #include <cuda_fp16.h>
 
+#include "moff_dft.cuh"
 #include "moff_fft.cuh"
 #include "moff_internal.h"
 
@@ -123,7 +124,9 @@ static_assert(fft_radix(32, 0) == FftPlan<32>::R0 && fft_radix(32, 1) == FftPlan
 
 // CPL = grid cells per lane: 1, 2 (cells (f, e), (f, e + 1) of one row) or 4 (the 2 x 2
 // block (f, e), (f, e + 1), (f + 1, e), (f + 1, e + 1), f even); each entry carries CPL taps.
-template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE>
+// DFT: the row transform runs as factored DFT contractions on the tensor cores
+// (moff_dft.cuh) and the field leaves as FP16 rows [re N][im N] (a.h16).
+template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE, bool DFT = false>
 __device__ __forceinline__ void grid_rows(const GridArgs &a) {
     constexpr bool PAIRS = CPL >= 2;
     using FP = FftPlan<N>;
@@ -159,6 +162,17 @@ __device__ __forceinline__ void grid_rows(const GridArgs &a) {
             }
             if (!any) return;
         }
+        if constexpr (DFT) {   // FP16 rows [re N][im N]: 8 halves per 16-byte store
+            constexpr int PER_T16 = P * ROWS * 2 * N / 8;
+            for (int i = tid; i < a.nt * PER_T16; i += kBlock) {
+                const int t = i / PER_T16, e = 8 * (i - t * PER_T16);
+                const int p = e / (ROWS * 2 * N), rem = e - p * (ROWS * 2 * N), rl = rem / (2 * N), x = rem - rl * 2 * N;
+                __half *o = a.h16 + (((long long)t * a.slab_t + (long long)cl * a.slab_c) * P * N + (long long)p * N +
+                                     (long long)s * ROWS + rl) * 2 * N + x;
+                *reinterpret_cast<uint4 *>(o) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            return;
+        }
         constexpr int PER_T = P * ROWS * N / 2;     // 16-byte stores per sample
         for (int i = tid; i < a.nt * PER_T; i += kBlock) {
             const int t = i / PER_T, e = 2 * (i - t * PER_T);
@@ -170,12 +184,16 @@ __device__ __forceinline__ void grid_rows(const GridArgs &a) {
         return;
     }
 
-    // Carve (matches grid_smem_bytes).
+    // Carve (matches grid_smem_bytes; DFT: the transform region replaces the pass
+    // twiddles and the second row buffer).
     extern __shared__ __align__(16) unsigned char smem[];
-    float2 *s_tw = reinterpret_cast<float2 *>(smem);
-    constexpr bool IP = GS::IN_PLACE;
-    float2 *s_buf = s_tw + TW::TOTAL;                  // gridded rows
-    float2 *s_alt = IP ? s_buf : s_buf + F * LDR;      // second buffer of the row passes (none in place)
+    constexpr bool IP = GS::IN_PLACE;                 // row passes in place (FFT variant)
+    constexpr bool ONEBUF = GS::IN_PLACE || DFT;      // one row buffer
+    constexpr size_t DREG = DFT ? (dft_row_region_bytes(N, F) + 15) / 16 * 16 : 0;
+    unsigned char *s_dft = smem;
+    float2 *s_tw = reinterpret_cast<float2 *>(smem + DREG);
+    float2 *s_buf = s_tw + (DFT ? 0 : TW::TOTAL);      // gridded rows
+    float2 *s_alt = ONEBUF ? s_buf : s_buf + F * LDR;  // second buffer of the row passes (none in place)
     float2 *s_y = s_alt + ((F * LDR + 1) & ~1);        // [nloc*P][YS]: TB samples, padded row (16-byte aligned)
     float2 *s_g = s_y + YS * a.max_nloc * P;
     // staged kernel values (CPL per entry, read as 16-byte vectors when CPL >= 2: 16-byte aligned)
@@ -184,7 +202,23 @@ __device__ __forceinline__ void grid_rows(const GridArgs &a) {
     int *s_ant = reinterpret_cast<int *>(s_tap + (STAGED ? TPE * a.max_entries : 0));
     uint16_t *s_cy = reinterpret_cast<uint16_t *>(s_ant + a.max_nloc);   // staged voltage indices
 
-    for (int i = tid; i < TW::TOTAL; i += kBlock) s_tw[i] = a.twp[i];
+    if constexpr (!DFT) {
+        for (int i = tid; i < TW::TOTAL; i += kBlock) s_tw[i] = a.twp[i];
+    }
+    // DFT: table image, the MMA mbarrier and this CTA's TMEM columns
+    uint64_t *s_mbar = reinterpret_cast<uint64_t *>(s_dft + (DFT ? dft_row_region_bytes(N, F) - 16 : 0));
+    uint32_t *s_tslot = reinterpret_cast<uint32_t *>(s_mbar + 1);
+    constexpr int TCOLS = DFT ? dft_row_tmem_cols(N, F) : 32;
+    if constexpr (DFT) {
+        dftc::load_table(s_dft + (size_t)F * (N / 16) * 64, a.dft_tab, DftShape<N>::TAB_BYTES);
+        if (tid == 0) tc::mbar_init(s_mbar, 1);
+        if (warp == 0) {
+            tc::tmem_alloc(s_tslot, TCOLS);
+            tc::tmem_relinquish();
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+    }
     for (int i = tid; i < nloc; i += kBlock) s_ant[i] = a.st_ant[ant0 + i];
     for (int i = tid; i < nyi; i += kBlock) {
         const int la = i / P, q = i - la * P;
@@ -196,6 +230,14 @@ __device__ __forceinline__ void grid_rows(const GridArgs &a) {
         for (int i = tid; i < ne; i += kBlock) s_cy[i] = __ldg(a.con_y + e0 + i);
     }
     __syncthreads();
+    uint32_t tbase = 0, mphase = 0;
+    float sG = 1.f;
+    bool dft_ok = true;
+    if constexpr (DFT) {
+        tc::fence_after_sync();
+        tbase = *s_tslot;
+        sG = a.sy[c] * a.s_t;
+    }
 
     // Voltage bytes: thread owns local voltages yi = tid + m*kBlock and their TB samples.
     const bool pre = nyi <= YPT * kBlock;
@@ -351,6 +393,20 @@ __device__ __forceinline__ void grid_rows(const GridArgs &a) {
             return outb + (((long long)(tb0 + t) * a.slab_t + (long long)cl * a.slab_c) * P * N + (long long)p * N +
                            ry0 + rl) * N;
         };
+        if constexpr (DFT) {
+            // Global FP16 row [re N][im N] of transform row fa (nullptr past the chunk).
+            auto rowout = [&](int fa) -> __half * {
+                const int t = fa / PR, f = fa - t * PR;
+                if (t >= nb) return nullptr;
+                const int p = f / ROWS, rl = f - p * ROWS;
+                return a.h16 + (((long long)(tb0 + t) * a.slab_t + (long long)cl * a.slab_c) * P * N +
+                                (long long)p * N + ry0 + rl) * 2 * N;
+            };
+            dft_ok = dftc::rows_dft<N, F, LDR, kBlock>(s_buf, sG, s_dft, s_mbar, tbase, mphase,
+                                                      reinterpret_cast<__half *>(s_buf), rowout);
+            if (!dft_ok) break;   // uniform: the wait's result is agreed by a block barrier
+            continue;
+        }
         if constexpr (GRID_ONLY) {
             for (int i = tid; i < F * N; i += kBlock) {
                 const int fa = i / N, e = i - fa * N;
@@ -370,6 +426,13 @@ __device__ __forceinline__ void grid_rows(const GridArgs &a) {
         }
         // (the next iteration's first barrier orders these reads before any rewrite)
     }
+    if constexpr (DFT) {
+        if (!dft_ok && tid == 0) atomicExch(a.err, tc::kErrWaitTimeout);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (warp == 0) tc::tmem_dealloc(tbase, TCOLS);
+    }
 }
 
 // Row transform out of place: the register count is the compiler's choice (an
@@ -377,6 +440,12 @@ __device__ __forceinline__ void grid_rows(const GridArgs &a) {
 template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE>
 __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
     grid_rows<N, P, TB, STAGED, GRID_ONLY, CPL, WIDE>(a);
+}
+
+// Gridding with the row transform on the tensor cores (FP16 field out).
+template <int N, int P, int TB, int CPL>
+__global__ void __launch_bounds__(kBlock) k_grid_rows_dft(const GridArgs a) {
+    grid_rows<N, P, TB, false, false, CPL, false, true>(a);
 }
 
 // Row transform in place: registers capped so that grid_min_blocks CTAs fit an SM.
@@ -392,15 +461,6 @@ struct ColShape {
     static constexpr int W = kBlock * RL / N;                  // columns per CTA
     static constexpr int NS = N / RL;                          // slots per column in the last pass
 };
-
-// 16-byte asynchronous global -> shared copies (completion tracked per group).
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 
 template <int N, int P, bool H16, bool TAPS>
 __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {

@@ -55,6 +55,28 @@ struct GridArgs {
     // g (n_stripes n_slices + 1) and lane_cell + g n_stripes n_slices 32, and their values
     // already index the shared st_ant / con_tap / con_y.  nullptr: one set.
     const int *chan_group;
+    // Dense tensor-core transform (k_grid_rows_dft): the row-transformed field as FP16 rows
+    // [re N][im N] (slab [P][N] rows of 2N halves at index t * slab_t + cl * slab_c), scaled by
+    // sy[c] * s_t (powers of two) / N; dft_tab the factored-DFT table image; err set when an
+    // MMA does not complete within its wait limit.
+    __half *h16;
+    const float *sy;
+    float s_t;
+    const unsigned char *dft_tab;
+    int *err;
+};
+
+// Dense tensor-core column transform + square-and-integrate (k_cols_dft).
+struct ColDftArgs {
+    const __half *H;          // FP16 rows [re N][im N]; slab [P][N] at t * slab_t + cl * slab_c
+    long long slab_t, slab_c;
+    int nt, c0, nc;
+    double *acc;              // [C][n_prod][N][N] FP64 accumulators (added to)
+    const uint32_t *row_nz;   // rows to read (bit ry); other rows are zero
+    const float *sy;          // per-channel voltage scale; the field carries sy[c] * s_t / N
+    float s_t;
+    const unsigned char *dft_tab;
+    int *err;
 };
 
 // Column transform + square-and-integrate (Eq. m6 steps 3-4, second axis).
@@ -191,6 +213,9 @@ inline size_t grid_smem_bytes(int N, int P, int TB, int rows, int max_nloc, int 
     return (b + 15) & ~(size_t)15;
 }
 
+// Shared-memory bytes of the gridding kernel with the tensor-core row transform.
+size_t grid_smem_bytes_dft(int N, int P, int TB, int rows, int max_nloc);
+
 // Kernel binning of one array (host side): per grid-row stripe, the antennas
 // touching it and each cell's kernel contributions in a fixed order, packed
 // as sliced ELL with cells sorted by contribution count.
@@ -218,8 +243,9 @@ struct GridChoice {
     bool quads = false;   // each lane sums a 2 x 2 block of cells (pairs ignored; entries through L2)
 };
 // force = nullptr: the built-in rule; else exactly that shape (MOFF_EINVAL if infeasible).
+// dft: shapes of the gridding kernel with the tensor-core row transform (k_grid_rows_dft).
 moff_status build_bins(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, Bins *b,
-                       const GridChoice *force = nullptr);
+                       const GridChoice *force = nullptr, bool dft = false);
 std::vector<float2> pass_twiddles_for(int n);   // pass-twiddle table of the n-point transform (FP64-built)
 
 // Row spectra of the kernel rows for the tensor-core path (host side).
@@ -240,6 +266,19 @@ int fft_tw_total(int n);                      // pass-twiddle table length for l
 int col_width(int N);                         // columns per column-kernel CTA
 size_t col_smem_bytes(int N, int P);
 size_t pfb_smem_bytes(int CN);
+
+// Dense tensor-core path (moff_dft_kernels.cu): the factored-DFT table image of an
+// N-point transform (B1 | B2 | twiddles; built in FP64), the column kernel, and the
+// gridding kernel with the row transform on the tensor cores (TB, CPL as the plain one;
+// entries through L2, stripes of grid_fft_rows(N) rows).
+std::vector<unsigned char> build_dft_table(int N);
+float dft_kernel_scale(int A, int K, int N, int P, bool jones, const double *pos, const float *taps);
+size_t cols_dft_smem_bytes(int N, int P);
+cudaError_t launch_cols_dft(int N, int P, const ColDftArgs &a, cudaStream_t st);
+cudaError_t launch_grid_dft(int N, int P, int TB, int CPL, const GridArgs &a, int n_stripes, size_t smem,
+                            cudaStream_t st);
+cudaError_t launch_grid_dft_n256(int P, int TB, int CPL, const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st);
+cudaError_t launch_grid_dft_n512(int P, int TB, int CPL, const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st);
 
 // Launchers (return the launch error, if any).
 cudaError_t launch_grid(int N, int P, int TB, bool staged, bool grid_only, const GridArgs &a, int n_stripes,
