@@ -1,18 +1,25 @@
 #!/usr/bin/env python3
 """Throughput of the MOFF imaging hot path on one GB300 (or N replicas).
 
-Workload (one step = one integration): 1024 dual-pol antennas hex-packed at
-1.5 lambda with 5 % jitter; real 8-bit ADC streams (noise sigma 20 plus three
-narrow-band sky sources) channelised by an 8-tap, 2048-sample polyphase
-filter bank into 1024 channels and requantised to 4+4 bits; each channel
-gridded on a 128x128 grid through 7x7 complex per-antenna kernels,
-transformed, squared and summed over 1000 samples into XX, YY, Re XY, Im XY.
-All arithmetic FP32 (FP64 cross-chunk sums).  A step processes
-1000 x 1024 = 1,024,000 channel-snapshots; its 4.2 GB of ADC input is far
-larger than L2, so no flush is needed between steps.
+Headline workload (the largest single-GPU configuration): a wide-field array
+of 32768 antennas on a 256 x 128 wavelength lattice (1 lambda pitch, 5 %
+jitter; 512 x 256 cells, so x wraps the 512 grid), full pol with per-antenna
+9x9 kernels whose taps are 2x2 Jones matrices (seeded smooth beam, leakage and
+a non-coplanar w-phase), 4096 channels, 512 x 512 grid, integrations of 4000
+samples accumulated in FP64 across blocks.  It runs on the FP16 tensor-core
+path (the factored-DFT route: FP32 gridding, both transform axes as tcgen05
+contractions).  One step = one block of 32 samples of every channel =
+131,072 channel-snapshots; its 8.6 GB of voltages are far larger than L2, so
+no flush is needed between steps.
+
+Named legs: the same array on the FP32 path; the 16384-antenna filled-aperture
+precision workload (512 grid, 7x7 kernels, FP16 tensor-core and FP32); the
+1024-antenna dual-pol workload with the 8-bit ADC F-stage (128 grid, FP32 and
+the FP16 row-spectrum route, feedback calibration, beams, channel sets,
+oversampling); serving and batching.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on a bounded sample of the same workload instead.
+oracle on a bounded sample of the headline workload instead.
 """
 from __future__ import annotations
 
@@ -21,6 +28,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -31,12 +39,27 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WL = dict(n_ant=1024, n_pol=2, n_chan=1024, grid_n=128, ksize=7, ntaps=8, frames=1000)
-SEED = 8123669 + 1
 METRIC = "MOFF channel-snapshots/s"
 UNIT = "channel-snapshots/s"
-WORKLOAD_NAME = ("dual-pol 1024-antenna hex core (1.5 lambda, 5% jitter), 8-bit ADC -> 8-tap x 2048 PFB "
-                 "-> 1024 channels 4+4-bit, 128x128 grid, 7x7 complex kernels, XX/YY/XY, 1000 samples per step")
+
+# Dense workloads: (synth config, sizes, block of samples per step, integration length).
+DENSE = {
+    "widefield": dict(cfg="config_widefield", n_ant=32768, n_pol=2, n_chan=4096, grid_n=512, ksize=9, jones=True,
+                      block=32, t_int=4000, seed=8123669 + 4,
+                      name="wide-field 32768-antenna 256x128-lambda lattice (1 lambda pitch, 5% jitter), 9x9 Jones "
+                           "kernels with w-phase, full pol, 4096 channels, 512x512 grid, XX/YY/XY, 4000-sample "
+                           "integrations accumulated in FP64 across blocks of 32 samples (one step = one block)"),
+    "precision": dict(cfg="config_precision", n_ant=16384, n_pol=2, n_chan=1024, grid_n=512, ksize=7, jones=False,
+                      block=64, t_int=2000, seed=8123669 + 2,
+                      name="filled aperture 16384 antennas on a 128x128-lambda lattice (5% jitter), dual pol, 7x7 "
+                           "kernels, 1024 channels, 512x512 grid (zero-padded x2), 2000-sample integrations in "
+                           "blocks of 64 samples"),
+}
+# The F-stage workload (the round's former headline, now a named leg).
+WL = dict(n_ant=1024, n_pol=2, n_chan=1024, grid_n=128, ksize=7, ntaps=8, frames=1000)
+SEED = 8123669 + 1
+DUALPOL_NAME = ("dual-pol 1024-antenna hex core (1.5 lambda, 5% jitter), 8-bit ADC -> 8-tap x 2048 PFB -> 1024 "
+                "channels 4+4-bit, 128x128 grid, 7x7 complex kernels, XX/YY/XY, 1000 samples per step")
 
 
 def parse_args():
@@ -45,21 +68,28 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="widefield", choices=sorted(DENSE),
+                    help="headline dense workload (widefield is the bench line; precision gives a profiling case)")
+    ap.add_argument("--block", type=int, default=0, help="samples per step (0: the workload's block)")
+    ap.add_argument("--chan", type=int, default=0, help="channels (0: the workload's; fewer give a profiling case)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-fp16tc", action="store_true", help="skip the FP16 tensor-core leg")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison on the headline workload")
+    ap.add_argument("--no-precision", action="store_true", help="skip the filled-aperture precision leg")
+    ap.add_argument("--no-dualpol", action="store_true", help="skip the dual-pol F-stage legs")
+    ap.add_argument("--no-fp16tc", action="store_true", help="skip the dual-pol FP16 row-spectrum leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream (serving) leg")
     ap.add_argument("--no-feedback", action="store_true",
                     help="skip the legs of the method's extensions (feedback calibration, beams and autocorrelation "
                          "subtraction, channel-dependent positions and kernels, edge-padded oversampling)")
     ap.add_argument("--no-plain", action="store_true", help="skip the batching leg (graph + autotune vs one channel at a time)")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per load point of the serving leg")
-    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-sample", default="", help=argparse.SUPPRESS)
     ap.add_argument("--frames", type=int, default=WL["frames"],
-                    help="samples per step (smaller values give a profiling case, not a bench line)")
+                    help="dual-pol leg: samples per step (smaller values give a profiling case, not a bench line)")
     ap.add_argument("--channels", type=int, default=WL["n_chan"],
-                    help="channels (smaller values give a profiling case, not a bench line)")
+                    help="dual-pol leg: channels (smaller values give a profiling case, not a bench line)")
     return ap.parse_args()
 
 
@@ -87,6 +117,96 @@ def job_rate(units_per_rank, world, seconds_max):
 
 
 # ----------------------------------------------------------------------------- algorithmic work
+
+def reached_rows(pos, N, K):
+    """Grid rows some kernel footprint reaches (rows no kernel reaches carry no field)."""
+    import numpy as np
+    h = K // 2
+    ay = np.floor(np.asarray(pos)[:, 1] + 0.5).astype(int) % N
+    r = np.zeros(N, bool)
+    for d in range(-h, h + 1):
+        r[(ay + d) % N] = True
+    return int(r.sum())
+
+
+def dense_work(route, pos, taps, N, P, Tb):
+    """Method's work per channel-snapshot of each kernel kind of a route:
+    {kind: {"alu": FP32 flops, "tensor": tensor flops, "bytes": DRAM bytes}}.
+
+    Gridding: 8 flops per nonzero kernel tap (complex multiply-add, Jones taps
+    counted per (p_out, p_in)) + 6 per voltage weighting.  Transforms: FP32 path
+    5 N log2 N per N-point transform (radix-2 count); tensor-core path the
+    factored DFT's real products, 8 N (16 + N/16) per N-point transform.  Only
+    reached grid rows carry a row transform.  Bytes: the 4-bit voltages, the FP16
+    (8 B FP32) field between the two axes written once and read once, and the FP64
+    accumulators read and written once per chunk of Tb samples."""
+    import numpy as np
+    A = len(pos)
+    nnz = int(np.count_nonzero(np.asarray(taps)))
+    R = reached_rows(pos, N, int(np.asarray(taps).shape[-1]))
+    nprod = 1 if P == 1 else 4
+    acc_b = 2 * nprod * N * N * 8 / max(Tb, 1)
+    sq = (16 if P == 2 else 4) * N * N
+    if route == "fp16_dft":
+        fac = 8 * N * (16 + N // 16)
+        return {"grid_rows": {"alu": 8 * nnz + 6 * A * P, "tensor": R * P * fac, "bytes": A * P + R * P * N * 4},
+                "cols_integrate": {"alu": sq, "tensor": N * P * fac, "bytes": R * P * N * 4 + acc_b}}
+    rad = 5 * N * math.log2(N)
+    return {"grid_rows": {"alu": 8 * nnz + 6 * A * P + R * P * rad, "tensor": 0, "bytes": A * P + R * P * N * 8},
+            "cols_integrate": {"alu": N * P * rad + sq, "tensor": 0, "bytes": R * P * N * 8 + acc_b}}
+
+
+def device_peaks(torch):
+    """Measured peaks (MEASURED_PEAKS.json) and the derived FP32 FMA peak of this device."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    return {"hbm_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_basis": "of measured" if "hbm_gbs" in peaks else "of fallback",
+            "bf16_tflops": float(peaks.get("bf16_tflops", 1900.0)),
+            "bf16_tflops_sustained": float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))),
+            "tensor_basis": "of measured" if "bf16_tflops" in peaks else "of fallback",
+            "alu_tflops": sms * 128 * 2 * sm_max * 1e6 / 1e12, "sms": sms, "sm_max_mhz": sm_max}
+
+
+def kernel_rooflines(kern, work, snaps, peaks):
+    """Per kernel kind: achieved FP32 / tensor / HBM rates from the method's work
+    and the live CUDA-event time, each against its peak (tensor: the measured
+    sustained bf16 dense figure, FP16 nominally equal -- these kernels run inside
+    seconds-long steps; HBM: the measured copy; FP32: derived from the unit
+    counts and the maximum SM clock)."""
+    out = {}
+    for name, v in kern.items():
+        w = work.get(name)
+        if not w or not v.get("ms_total"):
+            continue
+        sec = v["ms_total"] / 1e3
+        r = {"ms_per_launch": v["ms_total"] / max(v["launches"], 1), "launches": v["launches"]}
+        cand = []
+        if w["alu"]:
+            a = snaps * w["alu"] / sec / 1e12
+            r["alu"] = {"achieved": a, "peak": peaks["alu_tflops"], "unit": "TFLOP/s", "frac": a / peaks["alu_tflops"],
+                        "basis": f"FP32 FMA {peaks['sms']} SMs x 128 x 2 flop x {peaks['sm_max_mhz']:.0f} MHz (of derived)"}
+            cand.append(("alu", r["alu"]))
+        if w["tensor"]:
+            a = snaps * w["tensor"] / sec / 1e12
+            pk = peaks["bf16_tflops_sustained"]
+            r["tensor"] = {"achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                           "basis": f"factored-DFT real products; bf16 dense sustained ({peaks['tensor_basis']})"}
+            cand.append(("tensor", r["tensor"]))
+        a = snaps * w["bytes"] / sec / 1e9
+        r["hbm"] = {"achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
+                    "bytes_per_snapshot": w["bytes"], "basis": f"HBM copy ({peaks['hbm_basis']})"}
+        cand.append(("hbm", r["hbm"]))
+        r["bound"] = max(cand, key=lambda c: c[1]["frac"])[0]
+        out[name] = r
+    return out
+
+
+# ----------------------------------------------------------------------------- dual-pol work model
 
 def flops_per_snapshot(kind, A=WL["n_ant"], P=WL["n_pol"], N=WL["grid_n"], K=WL["ksize"]):
     """Algorithmic FP32 flops per channel-snapshot of each kernel (5 N log2 N per
@@ -194,76 +314,136 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------- oracle (CPU) sample
+# ----------------------------------------------------------------------------- oracle (CPU) samples
 
-def oracle_step(n_frames=2, seed=SEED):
-    """The FP64 oracle on a bounded sample of the workload: the whole array's
-    F-stage for ``n_frames`` frames, then every channel imaged for those frames.
-    Returns (channel-snapshots, seconds)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return platform.processor() or platform.machine()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_setup(wl_name, n_chan, n_time, seed):
+    """Inputs of a bounded oracle sample of a dense workload: the gridding matrix
+    (the plan's set-up, untimed), gains of ``n_chan`` channels and 4-bit noise
+    voltages (sigma 2 per component) of ``n_chan`` channels x ``n_time`` samples."""
     import numpy as np
 
     import oracle
     import synth
-    cfg = synth.config_dualpol()
-    A, P, C, N, ntaps = WL["n_ant"], WL["n_pol"], WL["n_chan"], WL["grid_n"], WL["ntaps"]
-    M = 2 * C
+    wl = DENSE[wl_name]
+    cfg = getattr(synth, wl["cfg"])(n_chan=n_chan)
     rng = np.random.default_rng(seed)
-    adc = synth.adc_stream(rng, A, P, (n_frames + ntaps - 1) * M, sigma=20.0,
-                           tones=[(100.0 / M, 12.0), (600.0 / M, 8.0)])
-    gains = cfg["gains"]
-    W = oracle.grid_matrix(cfg["pos"], cfg["taps"], N, P)      # plan set-up, not timed
-    t0 = time.perf_counter()
-    h = oracle.pfb_window(ntaps, M)
-    X = oracle.pfb_spectra(adc, h, ntaps, M)
-    scale = 2.0 / np.std(np.concatenate([X.real.ravel(), X.imag.ravel()]))
-    codes, _ = oracle.channelise(adc, h, ntaps, M, scale)
-    img = np.zeros((4, N, N))
-    for c in range(C):
+    shape = (n_time, n_chan, wl["n_ant"], wl["n_pol"])
+    re = np.clip(np.rint(rng.normal(0, 2, size=shape)), -7, 7).astype(int)
+    im = np.clip(np.rint(rng.normal(0, 2, size=shape)), -7, 7).astype(int)
+    W = oracle.grid_matrix(cfg["pos"], cfg["taps"], wl["grid_n"], wl["n_pol"], jones=wl["jones"])
+    return W, synth.pack_4bit(re, im), cfg["gains"]
+
+
+def oracle_channels(W, codes, gains, N, P):
+    """Eq. m6 for every channel of a sample, in the oracle's steps (decode, weight,
+    grid, transform, square and sum); returns the channel-snapshots imaged."""
+    import oracle
+    for c in range(codes.shape[1]):
         y = oracle.calibrate(oracle.unpack_4bit(codes[:, c]), gains[c])
-        img += oracle.integrate(oracle.sky_transform(oracle.grid(y, W, N, P)))
-    dt = time.perf_counter() - t0
-    return n_frames * C, dt
+        oracle.integrate(oracle.sky_transform(oracle.grid(y, W, N, P)))
+    return codes.shape[0] * codes.shape[1]
 
 
-def cpu_baseline_subprocess():
+_POOL_W = None
+
+
+def _pool_init(W):
+    global _POOL_W
+    _POOL_W = W
+
+
+def _pool_task(item):
+    codes, gains, N, P = item
+    return oracle_channels(_POOL_W, codes, gains, N, P)
+
+
+def run_cpu_sample(wl_name):
+    """One-core and all-core oracle rates on a bounded sample of the workload (run in
+    a process without a GPU; the all-core leg is a spawn pool, one channel per core)."""
+    import multiprocessing as mp
+    wl = DENSE[wl_name]
+    N, P = wl["grid_n"], wl["n_pol"]
+    cores = host_cores()
+    T1, C1, Tm = 32, 8, 64
+    W, codes, gains = oracle_setup(wl_name, max(C1, cores), T1, 8123669 + 77)
+    oracle_channels(W, codes[:2, :1], gains[:1], N, P)                # warm
+    t0 = time.perf_counter()
+    n1 = oracle_channels(W, codes[:, :C1], gains[:C1], N, P)
+    dt1 = time.perf_counter() - t0
+    ctx = mp.get_context("spawn")
+    items = [(codes[:Tm, c:c + 1].copy(), gains[c:c + 1], N, P) for c in range(cores)]
+    with ctx.Pool(cores, initializer=_pool_init, initargs=(W,)) as pool:
+        pool.map(_pool_task, [(it[0][:2], it[1], N, P) for it in items])   # start-up and warm-up
+        t0 = time.perf_counter()
+        nm = sum(pool.map(_pool_task, items))
+        dtm = time.perf_counter() - t0
+    print(json.dumps({
+        "value": n1 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt1,
+        "sample": f"{C1} channels x {T1} samples of the {wl_name} workload ({n1} channel-snapshots), "
+                  "FP64 numpy/scipy, gridding matrix built beforehand (plan set-up), 1 thread",
+        "all_core": {"value": nm / dtm, "unit": UNIT, "cores": cores, "seconds": dtm,
+                     "sample": f"{cores} channels x {Tm} samples ({nm} channel-snapshots), one channel per "
+                               "single-threaded process"},
+        "nproc": cores, "cpu_model": cpu_model(), "machine": platform.machine()}), flush=True)
+
+
+def cpu_baseline_subprocess(wl_name):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"], env=env, capture_output=True,
-                       text=True, timeout=900)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", wl_name], env=env,
+                       capture_output=True, text=True, timeout=1200)
     for line in r.stdout.splitlines()[::-1]:
         if line.startswith("{"):
             return json.loads(line)
     return {"error": (r.stderr or r.stdout)[-300:]}
 
 
-def run_cpu_sample():
-    units, dt = oracle_step(n_frames=6)
-    print(json.dumps({"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
-                      "sample": f"whole-array F-stage for 6 frames + all {WL['n_chan']} channels imaged "
-                                f"({units} channel-snapshots), FP64 numpy/scipy, 1 thread"}))
-
-
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on the
+    headline workload, each step a bounded sample (one channel x 8 samples)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     os.environ.setdefault("OMP_NUM_THREADS", "1")
+    wl = DENSE[args.workload]
+    N, P = wl["grid_n"], wl["n_pol"]
+    T = 8
+    W, codes, gains = oracle_setup(args.workload, 1, T, 8123669 + 78)
     for _ in range(args.warmup):
-        oracle_step(n_frames=1)
-    units = 0
-    secs = 0.0
+        oracle_channels(W, codes[:2], gains, N, P)
+    units, secs = 0, 0.0
     for _ in range(args.steps):
-        u, dt = oracle_step()
-        units += u
-        secs += dt
+        t0 = time.perf_counter()
+        units += oracle_channels(W, codes, gains, N, P)
+        secs += time.perf_counter() - t0
     v = units / secs
+    sample = f"each step: 1 channel x {T} samples of the {args.workload} workload, gridding matrix built beforehand"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "sample_frames_per_step": 2, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: whole-array F-stage for 2 frames + all 1024 channels imaged"},
+        "config": {"workload": wl["name"], "sample_snapshots_per_step": T, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model(), "nproc": host_cores()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -298,7 +478,13 @@ KERNEL_SOURCES = {
                         "size_t col_smem_bytes_t"),
                        "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
     "pfb_fstage": ["paper_0812_3669_gb300/csrc/moff_fstage.cu", "paper_0812_3669_gb300/csrc/moff_fft.cuh"],
+    # the factored-DFT tensor-core route of the dense workloads
+    "grid_rows_dft": [("paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "struct ColShape"),
+                      "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
+    "cols_dft": ["paper_0812_3669_gb300/csrc/moff_dft_kernels.cu", "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
 }
+# kernel kind (moff_timing) -> its name in KERNEL_SOURCES, per route
+ROUTE_KERNELS = {"fp16_dft": {"grid_rows": "grid_rows_dft", "cols_integrate": "cols_dft"}}
 
 
 def traffic_for(kernel_key, src):
@@ -451,27 +637,17 @@ def batching_leg(args, moff, synth, torch):
             "speedup_vs_plain": v_batched / v_plain}
 
 
-def run_ours(args):
-    import numpy as np
-    import torch
-
-    import paper_0812_3669_gb300 as moff
-    import synth
-
-    world, rank, local = rank_info()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+def dualpol_leg(args, ctx):
+    """The 1024-antenna dual-pol workload with the F-stage: 8-bit ADC streams in,
+    FP32 imaging (autotuned gridding), and on the same input the FP16 row-spectrum
+    route, feedback calibration, beams + autocorrelation subtraction, channel-
+    dependent positions and kernels, edge-padded oversampling, and end to end
+    through pinned host ADC buffers.  One step = one 1000-sample integration."""
+    moff, synth, torch, np = ctx.moff, ctx.synth, ctx.torch, ctx.np
+    world, rank, local, dist = ctx.world, ctx.rank, ctx.local, ctx.dist
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    if rank == 0 or world > 1:
-        moff.build()
-    barrier()
+        ctx.barrier()
 
     A, P, C, N, K, ntaps, F = (WL["n_ant"], WL["n_pol"], args.channels, WL["grid_n"], WL["ksize"], WL["ntaps"],
                                args.frames)
@@ -546,8 +722,8 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # FP32 FMA TFLOP/s at max SM clock
+    sm_max = ctx.peaks["sm_max_mhz"]
+    alu_peak = ctx.peaks["alu_tflops"]                       # FP32 FMA TFLOP/s at max SM clock
     for name, v in kern.items():
         v["share"] = v["ms_total"] / total_kernel_ms if total_kernel_ms else None
         v["tflops"] = flops[name] / (v["ms_total"] / 1e3) / 1e12 if v["ms_total"] and name in flops else None
@@ -557,11 +733,23 @@ def run_ours(args):
     achieved = kern[dom]["tflops"]
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak if achieved else None,
-                "peak_basis": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (of derived peak)",
+                "peak_basis": f"FP32 FMA: {ctx.peaks['sms']} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (of derived peak)",
                 "flops_per_launch": flops[dom] / max(launches, 1),
                 "ms_per_launch": kern[dom]["ms_total"] / max(launches, 1),
                 "traffic": traffic_for(dom + "@dualpol1024", src)}
     gpu_launches = sum(v["launches"] for v in kern.values())
+    # DRAM traffic against the method's own bytes: the gridding kernel's algorithmic input is
+    # the 4-bit voltages (the row-transformed field it writes is an intermediate); the column
+    # kernel's is its share of the FP64 accumulators (read and written once per chunk)
+    snaps_launch = snaps / max(launches, 1)
+    alg = {"grid_rows": A * P * snaps_launch,
+           "cols_integrate": 2 * 4 * N * N * 8 * C / max(kern.get("cols_integrate", {}).get("launches", 1), 1)}
+    for name in ("grid_rows", "cols_integrate"):
+        if name in kern:
+            t = traffic_for(name + "@dualpol1024", KERNEL_SOURCES.get(name, []))
+            kern[name]["algorithmic_bytes_per_launch"] = alg[name]
+            kern[name]["traffic_bytes_per_launch"] = t
+            kern[name]["traffic_over_algorithmic"] = t / alg[name] if t else None
 
     # ---------------------------------------------------------------- FP16 tensor-core variant, same input
     fp16 = None
@@ -590,6 +778,17 @@ def run_ours(args):
                                        "bytes_per_snapshot": tc_row_bytes_per_snapshot(pos),
                                        "peak_basis": "measured HBM copy (of measured)"}
         r = fp16["row_contraction_hbm"]
+        r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
+        # the same contraction against the method's own work: gridding (8 flops per tap) and the
+        # row transform (5 N log2 N per row), not the padded product the tensor cores execute
+        meth = snaps * (flops_per_snapshot(1) - 6 * A * P)
+        fp16["row_contraction_method"] = {"bound": "tensor", "achieved": meth / (rk["ms_total"] / 1e3) / 1e12
+                                          if rk.get("ms_total") else None,
+                                          "peak": float(peaks.get("bf16_tflops", 1933.3)), "unit": "TFLOP/s",
+                                          "flops_per_snapshot": flops_per_snapshot(1) - 6 * A * P,
+                                          "peak_basis": "method's flops (gridding + row FFT) over the measured bf16 "
+                                                        "dense burst (of measured)"}
+        r = fp16["row_contraction_method"]
         r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
 
     # ---------------------------------------------------------------- feedback calibration leg (Sec. 6)
@@ -671,7 +870,7 @@ def run_ours(args):
                                              "achieved": g_flops / (gk["ms_total"] / 1e3) / 1e12
                                              if gk.get("ms_total") else None,
                                              "peak": alu_peak, "unit": "TFLOP/s",
-                                             "peak_basis": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
+                                             "peak_basis": f"FP32 FMA: {ctx.peaks['sms']} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
                                                            "(of derived peak)"}}
         r = sets_leg["grid_kernel_roofline"]
         r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
@@ -709,6 +908,215 @@ def run_ours(args):
                "steps": args.e2e_steps, "api": "moff_submit_adc(host pinned ADC) + moff_read_image(host)"}
     plan.close()
 
+    fx_eq = value * A * (A - 1) / 2 * 4
+    return {"workload": DUALPOL_NAME, "value": value, "unit": UNIT, "ms_per_step": ms_max / args.steps,
+            "steps": args.steps, "dtype": "f32", "fx_equiv_tcmac_per_s": fx_eq / 1e12,
+            "config": {"antennas": A, "pols": P, "channels": C, "grid_n": N, "kernel": K, "pfb_taps": ntaps,
+                       "samples_per_step": F, "channel_snapshots_per_step": F * C},
+            "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches, "clocks": clk, "e2e": e2e,
+            "fp16tc_rowspec": fp16, "feedback": feedback, "beams_autocorr": taps_leg, "channel_sets": sets_leg}
+
+
+# ----------------------------------------------------------------------------- dense workloads
+
+class Ctx:
+    """What every leg needs: the modules, the rank layout and the device's peaks."""
+
+    def __init__(self, moff, synth, torch, np, world, rank, local, dist, peaks, gpu_idx):
+        self.moff, self.synth, self.torch, self.np = moff, synth, torch, np
+        self.world, self.rank, self.local, self.dist = world, rank, local, dist
+        self.peaks, self.gpu_idx = peaks, gpu_idx
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+
+def measure_blocks(ctx, pl, codes, steps, warmup, sample_clocks=False):
+    """Submit ``steps`` blocks of device voltages (after ``warmup`` untimed ones),
+    timed with CUDA events on the plan's stream, max over ranks.  Returns
+    (ms, per-kernel device times, clock record)."""
+    torch, moff = ctx.torch, ctx.moff
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        pl.submit(codes)
+    pl.sync()
+    pl.reset()
+    pl.set_timing(True)
+    clocks = ClockSampler(ctx.gpu_idx) if sample_clocks else None
+    ctx.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        pl.submit(codes)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ctx.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ctx.dist, "cuda")
+    kern = {}
+    for kind, name in moff.KERNEL_KINDS.items():
+        tot, n = pl.timing(kind)
+        if n:
+            kern[name] = {"ms_total": tot, "launches": n}
+    pl.set_timing(False)
+    total = sum(v["ms_total"] for v in kern.values())
+    for v in kern.values():
+        v["share"] = v["ms_total"] / total if total else None
+    return ms, kern, clk
+
+
+def image_diff(torch, a, b):
+    """Max-normalised difference per (channel, product) of two device images
+    [C][4][N][N] (cross products normalised by max(max XX, max YY)); its maximum."""
+    C, Q = a.shape[0], a.shape[1]
+    err = (a - b).abs().reshape(C, Q, -1).amax(-1)
+    den = b.abs().reshape(C, Q, -1).amax(-1)
+    if Q == 4:
+        d = torch.maximum(den[:, 0], den[:, 1])
+        den = torch.stack([den[:, 0], den[:, 1], d, d], 1)
+    return float((err / den.clamp_min(1e-30)).max())
+
+
+def dense_leg(args, ctx, wl_name, steps, warmup, fp16=True, headline=False, keep_image=False):
+    """One dense workload on the FP16 tensor-core path (fp16) or the FP32 path:
+    blocks of device voltages into the plan's FP64 accumulators."""
+    moff, synth, torch, np = ctx.moff, ctx.synth, ctx.torch, ctx.np
+    wl = DENSE[wl_name]
+    C = args.chan or wl["n_chan"]
+    B = args.block or wl["block"]
+    A, P, N = wl["n_ant"], wl["n_pol"], wl["grid_n"]
+    cfg = getattr(synth, wl["cfg"])(n_chan=C, with_gains=False)
+    pos, taps = cfg["pos"], cfg["taps"]
+    gains = synth.device_gains(wl["seed"] + 11, C, A, P)
+    codes = synth.device_codes(wl["seed"] + 1000 * ctx.rank, B, C, A, P)
+    t0 = time.perf_counter()
+    pl = moff.Plan(pos, taps, N, C, P, jones=wl["jones"], fp16tc=fp16)
+    setup_s = time.perf_counter() - t0
+    pl.set_gains(gains)
+    ms, kern, clk = measure_blocks(ctx, pl, codes, steps, warmup, sample_clocks=headline)
+    snaps = steps * B * C
+    info, route, tun = pl.info(), pl.route(), pl.tuning()
+    work = dense_work(route, pos, taps, N, P, info["time_chunk"])
+    roofs = kernel_rooflines(kern, work, snaps, ctx.peaks)
+    out = {"value": job_rate(snaps, ctx.world, ms / 1000.0), "unit": UNIT, "ms_per_step": ms / steps,
+           "steps": steps, "warmup": warmup, "route": route, "dtype": "f16 tensor-core, f32 accumulate" if fp16 else "f32",
+           "samples_per_step": B, "channels": C, "plan_create_s": setup_s, "chunk": [info["time_chunk"], info["chan_chunk"]],
+           "grid_shape": {"time_batch": tun["time_batch"], "cells_per_lane": tun["cells_per_lane"]},
+           "kernels": kern, "kernel_rooflines": roofs, "gpu_launches": sum(v["launches"] for v in kern.values()),
+           "clocks": clk}
+    img = None
+    if keep_image:
+        img = torch.empty((C, 4 if P == 2 else 1, N, N), dtype=torch.float32, device="cuda")
+        _, n = pl.read_image(out=img)
+        img /= float(n)
+    if headline and not args.no_e2e and args.e2e_steps > 0:
+        out["e2e"] = dense_e2e(args, ctx, pl, codes, C, P, N, B)
+    pl.close()
+    del codes
+    torch.cuda.empty_cache()
+    return out, img, (pos, taps)
+
+
+def dense_e2e(args, ctx, pl, codes, C, P, N, B):
+    """End to end through the C ABI with host buffers: every step copies its block
+    of 4-bit voltages from pinned host memory (moff_submit with a host pointer
+    stages it on the plan's copy stream); the integration's image is read back to
+    pinned host memory once at the end (its bytes shared over the steps)."""
+    torch = ctx.torch
+    host = torch.empty(codes.shape, dtype=torch.uint8, pin_memory=True)
+    host.copy_(codes)
+    nq = 4 if P == 2 else 1
+    out_h = torch.empty((C, nq, N, N), dtype=torch.float32, pin_memory=True)
+    for _ in range(2):                          # warm both staging buffers and the read-back
+        pl.submit(host)
+    pl.read_image(out=out_h, reset=True)
+    ctx.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        pl.submit(host)
+    pl.read_image(out=out_h, reset=True)
+    dt = max_over_ranks(time.perf_counter() - t0, ctx.dist, "cuda")
+    n = args.e2e_steps
+    return {"value": job_rate(n * B * C, ctx.world, dt), "unit": UNIT, "h2d_bytes_per_step": int(host.numel()),
+            "d2h_bytes_per_step": int(out_h.numel() * 4 // n), "steps": n,
+            "api": "moff_submit(host pinned voltages) per step + moff_read_image(host) of the integration at the end"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_0812_3669_gb300 as moff
+    import synth
+
+    world, rank, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world > 1:
+        moff.build()
+    if dist is not None:
+        dist.barrier()
+    gpu_idx = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis and vis.split(",")[local].strip().isdigit():
+        gpu_idx = int(vis.split(",")[local])
+    ctx = Ctx(moff, synth, torch, np, world, rank, local, dist, device_peaks(torch), gpu_idx)
+
+    # ---------------------------------------------------------------- headline: the largest workload, FP16 tensor core
+    wl = DENSE[args.workload]
+    head, img16, (pos, taps) = dense_leg(args, ctx, args.workload, args.steps, args.warmup, fp16=True, headline=True,
+                                         keep_image=not args.no_fp32)
+    roofs = head["kernel_rooflines"]
+    dom = max(roofs, key=lambda k: roofs[k]["ms_per_launch"] * roofs[k]["launches"])
+    b = roofs[dom]["bound"]
+    rd = roofs[dom][b]
+    kname = ROUTE_KERNELS.get(head["route"], {}).get(dom, dom)
+    traffic = traffic_for(kname + "@" + args.workload, KERNEL_SOURCES.get(kname, []))
+    work = dense_work(head["route"], pos, taps, wl["grid_n"], wl["n_pol"], head["chunk"][0])[dom]
+    per_launch = head["steps"] * head["samples_per_step"] * head["channels"] / max(roofs[dom]["launches"], 1)
+    roofline = {"bound": b, "kernel": kname, "achieved": rd["achieved"], "peak": rd["peak"], "unit": rd["unit"],
+                "frac": rd["frac"], "peak_basis": rd["basis"], "traffic": traffic,
+                "work_per_launch": (work["tensor"] if b == "tensor" else work["alu"] if b == "alu" else work["bytes"])
+                * per_launch,
+                "ms_per_launch": roofs[dom]["ms_per_launch"],
+                "traffic_over_algorithmic": traffic / (work["bytes"] * per_launch) if traffic else None}
+
+    # ---------------------------------------------------------------- the same workload on the FP32 path
+    fp32 = None
+    if not args.no_fp32:
+        fp32, img32, _ = dense_leg(args, ctx, args.workload, 2, 1, fp16=False, keep_image=True)
+        fp32["max_norm_diff_fp16_vs_fp32"] = image_diff(torch, img16, img32)
+        fp32["fp16_speedup"] = head["value"] / fp32["value"]
+        del img32
+    del img16
+    torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- filled-aperture precision workload
+    precision = None
+    if not args.no_precision and args.workload != "precision":
+        save = (args.chan, args.block)
+        args.chan, args.block = 0, 0
+        p16, i16, _ = dense_leg(args, ctx, "precision", 3, 1, fp16=True, keep_image=True)
+        p32, i32, _ = dense_leg(args, ctx, "precision", 2, 1, fp16=False, keep_image=True)
+        args.chan, args.block = save
+        precision = {"workload": DENSE["precision"]["name"], "fp16tc": p16, "fp32": p32,
+                     "fp16_speedup": p16["value"] / p32["value"],
+                     "max_norm_diff_fp16_vs_fp32": image_diff(torch, i16, i32)}
+        del i16, i32
+        torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- dual-pol F-stage workload and its legs
+    dualpol = None
+    if not args.no_dualpol:
+        dualpol = dualpol_leg(args, ctx)
     serving = None
     if not args.no_serving:
         serving = serving_leg(args, moff, synth, torch)
@@ -719,22 +1127,28 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline_subprocess()
+        cpu = cpu_baseline_subprocess(args.workload)
 
     if rank == 0:
-        fx_eq = value * A * (A - 1) / 2 * 4
+        A, P = wl["n_ant"], wl["n_pol"]
+        value = head["value"]
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "antennas": A, "pols": P, "channels": C, "grid_n": N,
-                       "kernel": K, "pfb_taps": ntaps, "samples_per_step": F, "channel_snapshots_per_step": F * C,
-                       "l2": "inputs larger than L2 (4.2 GB of ADC per step), no flush",
-                       "parallelism": f"{world} independent replica(s), one integration each"},
-            "fx_equiv_tcmac_per_s": fx_eq / 1e12,
-            "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches, "clocks": clk,
-            "e2e": e2e, "cpu_baseline": cpu, "fp16tc": fp16, "serving": serving, "batching": batching, "feedback": feedback,
-            "beams_autocorr": taps_leg, "channel_sets": sets_leg,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16 tensor-core (f32 accumulate, f64 across blocks)",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "antennas": A, "pols": P, "jones": wl["jones"],
+                       "channels": head["channels"], "grid_n": wl["grid_n"], "kernel": wl["ksize"],
+                       "samples_per_step": head["samples_per_step"], "integration_samples": wl["t_int"],
+                       "channel_snapshots_per_step": head["samples_per_step"] * head["channels"],
+                       "route": head["route"], "l2": "inputs larger than L2 (voltages per step >> 129 MB), no flush",
+                       "parallelism": f"{world} independent replica(s), one block stream each"},
+            "fx_equiv_tcmac_per_s": value * A * (A - 1) / 2 * 4 / 1e12,
+            "roofline": roofline, "kernels": head["kernels"], "kernel_rooflines": roofs,
+            "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "e2e": head.get("e2e"),
+            "cpu_baseline": cpu, "plan_create_s": head["plan_create_s"],
+            "legs": {"fp32_same_workload": fp32, "precision_filled_aperture": precision, "dualpol_fstage": dualpol,
+                     "serving": serving, "batching": batching},
         }), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -743,7 +1157,7 @@ def run_ours(args):
 def main():
     args = parse_args()
     if args.cpu_sample:
-        run_cpu_sample()
+        run_cpu_sample(args.cpu_sample)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -382,7 +382,12 @@ moff_status moff_timing(moff_plan *plan, int kind, double *total_ms, long long *
  * reaches it.  Arrays whose kernel lists plus one channel's sums and field
  * exceed 64 MiB are rejected with MOFF_EINVAL.
  * The first call on each device looks up the array's device address (with
- * that device current), so make that first call before any stream capture.
+ * that device current).  With lazy module loading (the CUDA default) that
+ * lookup is also when the library's kernels and the 64 MiB array are loaded
+ * onto that device, so a caller inside a fixed memory budget should make its
+ * first call during set-up, before the budget is in force.  Every call copies
+ * the kernel lists from pageable host memory, so no call may be made while its
+ * stream is being captured into a graph: such a call returns MOFF_ESTATE.
  * All calls share the one array: calls whose GPU work overlaps in time (on
  * different streams, or from different threads) race and corrupt each
  * other's results; serialise them.
@@ -390,6 +395,23 @@ moff_status moff_timing(moff_plan *plan, int kind, double *total_ms, long long *
 moff_status moff_image_noalloc(int n_ant, const double *pos, int ksize, const float *taps, int grid_n,
                                int n_chan, int n_pol, unsigned flags, const uint8_t *volt, int n_time,
                                const float *gains, float *image, void *cuda_stream);
+
+/*
+ * moff_voltage_planes -- diagnostic (the paper has no counterpart): the FP16
+ * voltage planes the row-spectrum tensor-core route builds for one channel
+ * (Eq. m6 step 1: each 4-bit voltage decoded, times its gain, times the
+ * channel's power-of-two scale, rounded to FP16), read back so the decoding can
+ * be checked bit for bit.
+ *   volt     uint8 [n_time][C][A][P] (host, or device with on_device = 1),
+ *            1 <= n_time <= the plan's time chunk (moff_plan_info).
+ *   out      host float32 complex [n_time][A][P][2]: the FP16 plane values,
+ *            converted exactly, in voltage order.
+ *   scale    the channel's power-of-two scale (may be NULL).
+ * Synchronous.  MOFF_EINVAL unless the plan takes the row-spectrum route
+ * (moff_plan_route = 1) and is not served.
+ */
+moff_status moff_voltage_planes(moff_plan *plan, const uint8_t *volt, int n_time, int on_device, int chan,
+                                float *out, float *scale);
 
 /*
  * moff_tc_selftest -- diagnostic: one tensor-core product D = A * B^T with the

@@ -24,8 +24,10 @@ Parity status per function (what pins it other than itself):
                           baselines-only image equals ``moff_image`` minus ``auto_image``.
 * ``auto_image``       -- the same identity; a single delta-kernel antenna gives a
                           flat image of its power.
-* ``pfb_window`` / ``pfb_spectra`` -- 1-tap rectangular case equals a library FFT,
-                          a hand-summed 2-tap case, tone-in-bin power.
+* ``pfb_window``       -- the 8 coefficients of a 2-tap, M = 4 window against closed
+                          forms worked by hand; symmetry; tone-in-bin power.
+* ``pfb_spectra``      -- 1-tap rectangular case equals a library FFT, a hand-summed
+                          2-tap case, tone-in-bin power.
 * ``quantise_4bit``    -- hand fixtures including half-to-even ties and clipping.
 * ``antenna_beam`` / ``feedback_sums`` -- the antenna shares sum to the image pixel
                           (FBeq1 = sum over antennas of FBeq2), FBeq3 by brute force

@@ -38,7 +38,7 @@ import scipy.sparse as sp
 
 __all__ = [
     "unpack_4bit", "anchors", "calibrate", "grid_matrix", "grid", "sky_transform",
-    "integrate", "moff_image", "fx_image", "footprint", "pfb_window", "pfb_spectra",
+    "integrate", "moff_image", "fx_image", "pfb_window", "pfb_spectra",
     "quantise_4bit", "ambiguous_codes", "channelise", "max_norm_err",
     "antenna_beam", "feedback_sums_y", "feedback_sums", "feedback_delta", "auto_image", "moff_image_sets",
 ]
@@ -283,21 +283,6 @@ def feedback_delta(R, S, gains, n_ant: int):
 
 
 # ----------------------------------------------------------------------------- FX form
-
-def footprint(pos, taps, grid_n: int, n_pol: int, jones: bool = False) -> np.ndarray:
-    """Each antenna's kernel placed on the grid: complex [A, P_out, P_in, N, N]."""
-    T = _full_taps(taps, n_pol, jones)
-    A, Po, Pi, K, _ = T.shape
-    N = grid_n
-    anc = anchors(pos)
-    h = K // 2
-    F = np.zeros((A, Po, Pi, N, N), dtype=np.complex128)
-    for a in range(A):
-        for iy in range(K):
-            for ix in range(K):
-                F[a, :, :, (anc[a, 1] + iy - h) % N, (anc[a, 0] + ix - h) % N] += T[a, :, :, iy, ix]
-    return F
-
 
 def fx_image(codes, gains, pos, taps, grid_n: int, n_pol: int, jones: bool = False,
              channel: int = 0, autos: bool = True) -> np.ndarray:

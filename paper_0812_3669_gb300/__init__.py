@@ -24,7 +24,7 @@ __all__ = [
     "MoffError", "lib", "build", "LIB_PATH", "MOFF_FSTAGE", "MOFF_JONES", "MOFF_PREC_FP32", "MOFF_PREC_FP16TC",
     "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
-    "moff_plan_info", "moff_plan_route", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
+    "moff_plan_info", "moff_plan_route", "moff_voltage_planes", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
     "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "moff_plan_tuning",
     "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
     "moff_server_destroy", "moff_set_calibrator", "moff_read_feedback", "moff_feedback_gains",
@@ -74,6 +74,7 @@ _SIGS = {
     "moff_plan_info": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                        ctypes.POINTER(_ll)],
     "moff_plan_route": [_vp, ctypes.POINTER(_i)],
+    "moff_voltage_planes": [_vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_f)],
     "moff_plan_destroy": [_vp],
     "moff_set_timing": [_vp, _i],
     "moff_timing": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _i],
@@ -263,6 +264,17 @@ def moff_plan_route(plan) -> str:
     return ROUTES[r.value]
 
 
+def moff_voltage_planes(plan, volt, chan, n_ant, n_pol):
+    """The row-spectrum route's FP16 voltage planes of one channel (diagnostic):
+    returns (complex64 [T][A][P] plane values, the channel's power-of-two scale)."""
+    a, dev = _addr(volt)
+    T = int(volt.shape[0])
+    out = np.empty((T, n_ant, n_pol, 2), dtype=np.float32)
+    sc = ctypes.c_float(0.0)
+    _check(lib().moff_voltage_planes(plan, a, T, dev, int(chan), out.ctypes.data, ctypes.byref(sc)))
+    return out[..., 0] + 1j * out[..., 1], sc.value
+
+
 def moff_plan_tuning(plan):
     a, b, p, c, w = (ctypes.c_int() for _ in range(5))
     d = ctypes.c_double()
@@ -338,6 +350,7 @@ def moff_image_noalloc(pos, taps, grid_n, n_chan, n_pol, volt, gains, image, jon
     """Image one block without any GPU allocation by the library.  ``volt``
     (uint8 [T][C][A][P]), ``gains`` (complex [C][A][P]) and ``image`` (float32
     [C][n_prod][N][N]) are CUDA tensors; ``pos``/``taps`` are host arrays."""
+    import torch
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     taps = np.asarray(taps)
     t32 = _f32_interleaved(taps)
@@ -345,8 +358,22 @@ def moff_image_noalloc(pos, taps, grid_n, n_chan, n_pol, volt, gains, image, jon
     for name, x in (("volt", volt), ("gains", g), ("image", image)):
         if not (_is_torch(x) and x.is_cuda and x.is_contiguous()):
             raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    # the library reads and writes exactly these extents: refuse anything else here
+    A, P, C, N = int(pos.shape[0]), int(n_pol), int(n_chan), int(grid_n)
+    n_prod = 1 if P == 1 else 4
+    if pos.ndim != 2 or pos.shape[1] != 2:
+        raise ValueError("pos must be float64 [A][2]")
+    K = int(taps.shape[-1])
+    want_taps = (A, 2, 2, K, K) if jones else (A, P, K, K)
+    if tuple(taps.shape) != want_taps:
+        raise ValueError(f"taps must have shape {want_taps}, got {tuple(taps.shape)}")
+    if volt.dtype != torch.uint8 or volt.dim() != 4 or tuple(volt.shape[1:]) != (C, A, P):
+        raise ValueError(f"volt must be uint8 [T][{C}][{A}][{P}], got {volt.dtype} {tuple(volt.shape)}")
+    if g.dtype != torch.float32 or g.numel() != C * A * P * 2:
+        raise ValueError(f"gains must hold {C}x{A}x{P} complex values")
+    if image.dtype != torch.float32 or image.numel() != C * n_prod * N * N:
+        raise ValueError(f"image must be float32 with {C}x{n_prod}x{N}x{N} elements")
     if cuda_stream is None:
-        import torch
         cuda_stream = torch.cuda.current_stream().cuda_stream or 1
     _check(lib().moff_image_noalloc(int(pos.shape[0]), pos.ctypes.data, int(taps.shape[-1]), t32.ctypes.data,
                                     int(grid_n), int(n_chan), int(n_pol), MOFF_JONES if jones else 0,
@@ -531,6 +558,9 @@ class Plan:
 
     def route(self):
         return moff_plan_route(self.handle)
+
+    def voltage_planes(self, volt, chan):
+        return moff_voltage_planes(self.handle, volt, chan, self.A, self.P)
 
     def set_timing(self, on=True):
         moff_set_timing(self.handle, on)

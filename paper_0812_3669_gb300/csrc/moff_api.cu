@@ -2288,6 +2288,9 @@ moff_status moff_grid_snapshot(moff_plan *pl, const uint8_t *volt, int on_device
     if (s != MOFF_OK) return s;
     if (!volt || !out) return fail(MOFF_EINVAL, "volt and out must not be NULL");
     if (chan < 0 || chan >= pl->C) return fail(MOFF_EINVAL, "chan (%d) out of range [0, %d)", chan, pl->C);
+    // the snapshot is written as FP32 into the field scratch (FP16-sized on the tensor-core path)
+    if (pl->h_bytes < (size_t)pl->P * pl->N * pl->N * 8)
+        return fail(MOFF_EINVAL, "the plan's field scratch is too small for an FP32 snapshot");
     const size_t bytes = (size_t)pl->C * pl->A * pl->P;
     const uint8_t *src = volt;
     int slot = -1;
@@ -2301,6 +2304,45 @@ moff_status moff_grid_snapshot(moff_plan *pl, const uint8_t *volt, int on_device
     if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
     MOFF_CK(cudaMemcpyAsync(out, pl->d_H, (size_t)pl->P * pl->N * pl->N * 8, cudaMemcpyDeviceToHost, pl->st));
     return sync_plan(pl, -1);
+}
+
+moff_status moff_voltage_planes(moff_plan *pl, const uint8_t *volt, int n_time, int on_device, int chan, float *out,
+                                float *scale) {
+    moff_status s = check_unserved(pl);
+    if (s != MOFF_OK) return s;
+    if (!pl->tc || pl->dft)
+        return fail(MOFF_EINVAL, "voltage planes exist only on the row-spectrum tensor-core route");
+    if (!volt || !out) return fail(MOFF_EINVAL, "volt and out must not be NULL");
+    if (n_time < 1 || n_time > pl->Tb) return fail(MOFF_EINVAL, "n_time (%d) must be in [1, %d]", n_time, pl->Tb);
+    if (chan < 0 || chan >= pl->C) return fail(MOFF_EINVAL, "chan (%d) out of range [0, %d)", chan, pl->C);
+    const int AP = pl->A * pl->P, APpad = AP + kRowSpecPad;
+    const long long tstride = (long long)pl->C * AP;
+    const uint8_t *src = volt;
+    int slot = -1;
+    if (!on_device) {
+        const void *dev = nullptr;
+        if ((s = stage_in(pl, volt, (size_t)n_time * tstride, &dev, &slot)) != MOFF_OK) return s;
+        src = reinterpret_cast<const uint8_t *>(dev);
+    }
+    MOFF_CK(launch_volt_prep(src, tstride, 0, n_time, chan, 1, AP, APpad, pl->d_gains, pl->d_sy, pl->d_rs_perm, pl->Tb,
+                             pl->d_yre, pl->d_yim, pl->st));
+    if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
+    std::vector<__half> re((size_t)AP * pl->Tb), im((size_t)AP * pl->Tb);
+    std::vector<int> perm(AP);
+    float sy = 0.f;
+    MOFF_CK(cudaMemcpyAsync(re.data(), pl->d_yre, re.size() * 2, cudaMemcpyDeviceToHost, pl->st));
+    MOFF_CK(cudaMemcpyAsync(im.data(), pl->d_yim, im.size() * 2, cudaMemcpyDeviceToHost, pl->st));
+    MOFF_CK(cudaMemcpyAsync(perm.data(), pl->d_rs_perm, (size_t)AP * 4, cudaMemcpyDeviceToHost, pl->st));
+    MOFF_CK(cudaMemcpyAsync(&sy, pl->d_sy + chan, 4, cudaMemcpyDeviceToHost, pl->st));
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    for (int v = 0; v < AP; ++v)
+        for (int t = 0; t < n_time; ++t) {
+            const size_t o = ((size_t)t * AP + perm[v]) * 2;
+            out[o] = __half2float(re[(size_t)v * pl->Tb + t]);
+            out[o + 1] = __half2float(im[(size_t)v * pl->Tb + t]);
+        }
+    if (scale) *scale = sy;
+    return MOFF_OK;
 }
 
 moff_status moff_read_image(moff_plan *pl, float *out, long long *n_samples, int reset, int timeout_ms, int out_on_device) {

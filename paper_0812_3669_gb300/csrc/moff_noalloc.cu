@@ -90,6 +90,13 @@ extern "C" moff_status moff_image_noalloc(int n_ant, const double *pos, int ksiz
 
     const int N = grid_n, P = n_pol, C = n_chan, nprod = P == 1 ? 1 : 4;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    {   // the host lists are copied from pageable memory: not capturable
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(st, &cs);
+        if (e != cudaSuccess) return failf(MOFF_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+        if (cs != cudaStreamCaptureStatusNone)
+            return failf(MOFF_ESTATE, "moff_image_noalloc cannot run while its stream is being captured");
+    }
 
     Bins b;
     moff_status s = build_bins(n_ant, ksize, N, P, jones, pos, taps, &b);

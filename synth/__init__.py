@@ -29,7 +29,8 @@ import numpy as np
 __all__ = [
     "rng_for", "pack_4bit", "positions_uniform", "positions_hex", "positions_lattice",
     "taps_gaussian", "taps_jones", "gains_random", "voltages", "adc_stream",
-    "config_tiny", "config_dualpol", "config_precision", "config_widefield",
+    "config_tiny", "config_dualpol", "config_precision", "config_widefield", "device_codes", "device_gains",
+    "device_adc",
 ]
 
 SEED_BASE = 8123669
@@ -250,26 +251,28 @@ def config_dualpol(seed: int = SEED_BASE + 1, n_ant: int = 1024, grid_n: int = 1
 
 
 def config_precision(seed: int = SEED_BASE + 2, side: int = 128, grid_n: int = 512,
-                     n_chan: int = 1024, ksize: int = 7):
+                     n_chan: int = 1024, ksize: int = 7, with_gains: bool = True):
     """Filled aperture: side x side antennas on a 1 lambda lattice (5 % jitter),
-    dual pol, 7x7 kernels, in the centre of a grid zero-padded by two."""
+    dual pol, 7x7 kernels, in the centre of a grid zero-padded by two.
+    ``with_gains=False`` skips the host gains (draw them with ``device_gains``)."""
     rng = rng_for(seed)
     o = grid_n / 2.0 - side          # lattice spans 2*side cells, centred
     pos = positions_lattice(rng, side, side, 1.0, 0.05, (o, o))
     taps = taps_gaussian(rng, pos, ksize, 1.2, n_pol=2, subpixel=True, phase_slope=0.3)
-    gains = gains_random(rng, n_chan, pos.shape[0], 2)
+    gains = gains_random(rng, n_chan, pos.shape[0], 2) if with_gains else None
     return dict(pos=pos, taps=taps, grid_n=grid_n, n_chan=n_chan, n_pol=2, gains=gains,
                 jones=False, rng=rng)
 
 
 def config_widefield(seed: int = SEED_BASE + 4, nx: int = 256, ny: int = 128, grid_n: int = 512,
-                     n_chan: int = 4096, ksize: int = 9):
+                     n_chan: int = 4096, ksize: int = 9, with_gains: bool = True):
     """Wide-field: nx x ny antennas at 1 lambda pitch (x wraps the grid), full
-    pol with 9x9 Jones kernels carrying a w-phase."""
+    pol with 9x9 Jones kernels carrying a w-phase.  ``with_gains=False`` skips
+    the host gains (draw them with ``device_gains``)."""
     rng = rng_for(seed)
     pos = positions_lattice(rng, nx, ny, 1.0, 0.05, (0.0, grid_n / 2.0 - ny))
     taps = taps_jones(rng, pos, ksize, 1.5)
-    gains = gains_random(rng, n_chan, pos.shape[0], 2)
+    gains = gains_random(rng, n_chan, pos.shape[0], 2) if with_gains else None
     return dict(pos=pos, taps=taps, grid_n=grid_n, n_chan=n_chan, n_pol=2, gains=gains,
                 jones=True, rng=rng)
 
@@ -316,6 +319,20 @@ def device_codes(seed: int, n_time: int, n_chan: int, n_ant: int, n_pol: int,
         im = torch.clamp(torch.round(torch.randn(shape, generator=g, device="cuda") * sigma), -7, 7).to(torch.int32)
         out[t0:t0 + n] = (((re & 15) << 4) | (im & 15)).to(torch.uint8)
     return out
+
+
+def device_gains(seed: int, n_chan: int, n_ant: int, n_pol: int, amp=(0.8, 1.2)):
+    """Complex gains ``complex64 [C][A][P]`` drawn on the GPU (seeded torch Philox):
+    amplitude U(amp), phase U(0, 2 pi), as ``gains_random`` draws them on the host.
+    For channel counts whose gains are too large to draw on the host."""
+    import math
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed))
+    shape = (n_chan, n_ant, n_pol)
+    a = amp[0] + (amp[1] - amp[0]) * torch.rand(shape, generator=g, device="cuda")
+    ph = 2 * math.pi * torch.rand(shape, generator=g, device="cuda")
+    return torch.polar(a, ph).to(torch.complex64)
 
 
 def device_adc(seed: int, pos, n_pol: int, n_samp: int, frame: int, grid_n: int,

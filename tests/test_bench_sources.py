@@ -46,3 +46,23 @@ def test_row_contraction_byte_model():
     assert bench.tc_row_bytes_per_snapshot(pos, N=16, P=2, K=3) == 2 * 7 * 16 * 4 + 3 * 2 * 2 * 2
     wrap = np.array([[0.0, 15.6]])                                # anchor row 16 -> 0: rows 15, 0, 1
     assert bench.tc_row_bytes_per_snapshot(wrap, N=16, P=1, K=3) == 1 * 3 * 16 * 4 + 1 * 1 * 2 * 2
+
+
+def test_dense_work_model():
+    """Method's work per snapshot of the dense routes on a hand-countable array:
+    two antennas with 3x3 one-pol kernels on a 256 grid, anchor rows 10 and 11."""
+    import numpy as np
+    pos = np.array([[5.0, 10.0], [40.2, 11.4]])
+    taps = np.ones((2, 1, 3, 3), dtype=complex)
+    taps[1, 0, 0, 0] = 0                                 # 17 nonzero taps
+    assert bench.reached_rows(pos, 256, 3) == 4          # rows 9-12
+    w = bench.dense_work("fp16_dft", pos, taps, 256, 1, Tb=64)
+    fac = 8 * 256 * (16 + 16)
+    assert w["grid_rows"]["alu"] == 8 * 17 + 6 * 2
+    assert w["grid_rows"]["tensor"] == 4 * fac
+    assert w["cols_integrate"]["tensor"] == 256 * fac
+    assert w["grid_rows"]["bytes"] == 2 + 4 * 256 * 4
+    assert w["cols_integrate"]["bytes"] == 4 * 256 * 4 + 2 * 256 * 256 * 8 / 64
+    w32 = bench.dense_work("fp32", pos, taps, 256, 1, Tb=64)
+    assert w32["grid_rows"]["alu"] == 8 * 17 + 6 * 2 + 4 * 5 * 256 * 8
+    assert w32["cols_integrate"]["bytes"] == 4 * 256 * 8 + 2 * 256 * 256 * 8 / 64

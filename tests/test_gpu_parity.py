@@ -6,9 +6,11 @@ Tolerances (written here, derived from the arithmetic):
     FP32 sums over <= 64 samples folded into FP64 accumulators;
   * gridded field: max |G_gpu - G_oracle| <= 2e-6 * max |G| (FP32 sums of a
     few dozen kernel products per cell);
-  * F-stage spectra: <= 1e-5 of the stream's max |X|; 4-bit codes exact
-    except where the oracle's scaled value is within 1e-3 of a rounding
-    boundary, where one step either way is accepted.
+  * F-stage spectra: <= 1e-5 of the stream's max |X|, and within 1e-4 of the
+    oracle in scaled (code) units; 4-bit codes exact except where the
+    oracle's scaled value is within 1e-4 of a rounding boundary, where one
+    step either way is accepted (the FP32 and FP64 spectra may round apart
+    only there).
 Gains and kernels are handed to the oracle exactly as the library sees them
 (rounded to complex64), so input quantisation is not counted as error.
 """
@@ -286,9 +288,13 @@ def test_fstage_spectra_and_codes(C, ntaps, A, P, F):
         codes2 = pl.channelise(adc, kind=0)
     den = np.abs(Xr).max(axis=(0, 1))
     assert (np.abs(spec - Xr).max(axis=(0, 1)) <= 1e-5 * den).all()
+    # the band below must cover the FP32-FP64 difference in the units the rounding sees
+    d_scaled = float(np.abs(spec - Xr).max()) * float(np.float32(scale))
+    print(f"C={C} taps={ntaps}: max FP32-FP64 spectrum difference {d_scaled:.2e} codes")
+    assert d_scaled < 1e-4
     re, im = oracle.quantise_4bit(Xr, np.float32(scale))
     z = oracle.unpack_4bit(codes)
-    amb = oracle.ambiguous_codes(Xr, np.float32(scale), 1e-3)
+    amb = oracle.ambiguous_codes(Xr, np.float32(scale), 1e-4)
     dr, di = np.abs(z.real - re), np.abs(z.imag - im)
     assert (dr[~amb] == 0).all() and (di[~amb] == 0).all()
     assert dr.max() <= 1 and di.max() <= 1

@@ -324,6 +324,20 @@ def test_pfb_one_tap_rectangular_is_plain_fft():
     np.testing.assert_allclose(X, want, rtol=0, atol=1e-9)
 
 
+def test_pfb_window_hand_values():
+    """The window's coefficients for 2 taps of M = 4, against the closed forms
+    worked by hand in tests/golden/pfb_window_2tap_m4.txt: both Hann endpoints
+    vanish (L - 1 in the cosine's denominator, not L) and the sinc is centred
+    at (L - 1) / 2 (half a sample off would break the symmetry and move every
+    value)."""
+    rows = read_golden("pfb_window_2tap_m4.txt")
+    want = np.array([float(r[1]) for r in rows])
+    assert [int(r[0]) for r in rows] == list(range(8))
+    h = oracle.pfb_window(2, 4)
+    assert h.shape == (8,)
+    np.testing.assert_allclose(h, want, rtol=1e-13, atol=1e-15)
+
+
 def test_pfb_window_channel_response():
     """Windowed-sinc PFB: a tone at a channel centre keeps >= 99 % of its power in
     that channel; at a channel edge the two neighbours see it about equally."""
