@@ -73,12 +73,15 @@ enum {
                                    and the squaring stay FP32.  Taken where at most 128 antennas
                                    (4 chunks of 32) land their kernel rows on any one grid row per pol;
                                  factored DFT -- N = 256 or 512 (denser arrays, or environment
-                                   variable MOFF_TC_DFT=1): FP32 gridding, then both transform axes
-                                   as factored DFT contractions (N = 16 x N/16, twiddles between the
-                                   two factors; DFT and twiddle tables built in FP64), the column
-                                   half fused with the squaring; the field between the two axes is
-                                   FP16.  Feedback calibration and tied-array beams are not
-                                   available on this route (MOFF_EINVAL). */
+                                   variable MOFF_TC_DFT=1): both transform axes as factored DFT
+                                   contractions (N = 16 x N/16, twiddles between the two factors;
+                                   DFT and twiddle tables built in FP64), the column half fused with
+                                   the squaring; the gridding as tensor-core contractions over tiles
+                                   of 8 x 8 cells (weighted FP16 voltages x each tile's FP16 kernel
+                                   values), or, with MOFF_TC_GRID=0 or tiles too large for shared
+                                   memory, the FP32 gather fused with the row transform; the fields
+                                   between the steps are FP16.  Feedback calibration and tied-array
+                                   beams are not available on this route (MOFF_EINVAL). */
     MOFF_FSTAGE = 1u << 1,    /* enable the polyphase F-stage (moff_submit_adc, moff_channelise) */
     MOFF_JONES = 1u << 2,     /* kernels are full 2x2 Jones matrices (n_pol must be 2) */
     MOFF_SERVED = 1u << 3,    /* the plan does not own its per-block scratch (the row-transformed
@@ -234,8 +237,8 @@ moff_status moff_plan_info(const moff_plan *plan, int *n_prod, int *rows_per_str
  * moff_plan_route -- which arithmetic the plan's imaging takes: 0 the FP32 path
  * (gather gridding, both transform axes as FP32 FFTs), 1 the FP16 row-spectrum
  * contraction + FP32 column FFT, 2 FP32 gridding + both axes as factored
- * tensor-core DFT contractions (see MOFF_PREC_FP16TC).  MOFF_EINVAL for a NULL
- * argument.
+ * tensor-core DFT contractions, 3 the same transforms with the gridding on the
+ * tensor cores too (see MOFF_PREC_FP16TC).  MOFF_EINVAL for a NULL argument.
  */
 moff_status moff_plan_route(const moff_plan *plan, int *route);
 
@@ -352,7 +355,10 @@ moff_status moff_set_timing(moff_plan *plan, int on);
  *   4  F-stage output reorder (the four-step F-stage used for C = 1024 with
  *      8 taps writes stream-major and reorders to [F][C][A][P]),
  *   5  feedback-calibration correlation (when a calibrator is set),
- *   6  autocorrelation sums (when switched on).
+ *   6  autocorrelation sums (when switched on),
+ *   7  (tensor-core gridding route only) the row transform of the gridded field.
+ * On the tensor-core gridding route kind 1 is the cell-tile gridding alone and
+ * kind 3 writes the voltage planes it reads.
  * Waits for the recorded work.  total_ms / launches may be NULL.  reset = 1
  * drops the records of every kind after reading.
  */

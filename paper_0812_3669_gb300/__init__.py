@@ -45,7 +45,7 @@ MOFF_AUTOTUNE = 1 << 4
 MOFF_GRAPH = 1 << 5
 
 KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep", 4: "fstage_reorder",
-                5: "feedback_corr", 6: "autocorr"}
+                5: "feedback_corr", 6: "autocorr", 7: "row_transform"}
 
 STATUS = {0: "MOFF_OK", -1: "MOFF_EINVAL", -2: "MOFF_ENOMEM", -3: "MOFF_ECUDA",
           -4: "MOFF_ESTATE", -5: "MOFF_ETIMEDOUT", -6: "MOFF_EBUSY"}
@@ -254,11 +254,11 @@ def moff_plan_info(plan):
                 device_bytes=e.value)
 
 
-ROUTES = {0: "fp32", 1: "fp16_rowspec", 2: "fp16_dft"}
+ROUTES = {0: "fp32", 1: "fp16_rowspec", 2: "fp16_dft", 3: "fp16_tcgrid"}
 
 
 def moff_plan_route(plan) -> str:
-    """The plan's arithmetic route: "fp32", "fp16_rowspec" or "fp16_dft" (see MOFF_PREC_FP16TC)."""
+    """The plan's arithmetic route: "fp32", "fp16_rowspec", "fp16_dft" or "fp16_tcgrid" (see MOFF_PREC_FP16TC)."""
     r = ctypes.c_int()
     _check(lib().moff_plan_route(plan, ctypes.byref(r)))
     return ROUTES[r.value]

@@ -267,6 +267,19 @@ struct moff_plan {
     unsigned char *d_dft_tab = nullptr;
     float dft_s_t = 1.f;
     size_t grid_smem_fft = 0;
+    // ... with the gridding on the tensor cores too (cell tiles; MOFF_TC_GRID=0 keeps the FP32 gather):
+    // tile tables, voltage planes in raster order of anchors (TMA maps of 16-row boxes), and the
+    // FP16 gridded field (d_G, the row transform's input; the row-transformed field is d_H)
+    bool gtc = false;
+    int gt_tiles = 0, gt_kp_max = 0, gt_cgroups = 1, gt_rows = 0;   // gt_rows: plane rows per channel incl. padding
+    size_t gt_smem = 0;
+    int *d_gt_tile_cell = nullptr, *d_gt_kp = nullptr, *d_gt_chunk_off = nullptr, *d_gt_chunk_row = nullptr,
+        *d_gt_perm = nullptr;
+    long long *d_gt_bimg_off = nullptr;
+    __half *d_gt_bimg = nullptr;
+    unsigned char *d_gt_active = nullptr;
+    CUtensorMap gt_map_re{}, gt_map_im{};
+    __half *d_G = nullptr;
 
     long long n_samples = 0;
     size_t dev_bytes = 0;
@@ -720,7 +733,79 @@ moff_status run_image_dft(moff_plan *pl, const uint8_t *volt, int n_time, long l
     return MOFF_OK;
 }
 
+// Dense FP16 path with the gridding on the tensor cores: voltage planes, cell-tile gridding,
+// row transform, column transform + square-and-integrate, per (Tb, Cb) chunk.
+moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
+    const int AP = pl->A * pl->P;
+    for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
+        const int nc = std::min(pl->Cb, pl->C - c0);
+        for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
+            const int nt = std::min(pl->Tb, n_time - t0);
+            TimedLaunch tv(pl, 3);
+            MOFF_CK(launch_volt_prep(volt, tstride, t0, nt, c0, nc, AP, pl->gt_rows, pl->d_gains, pl->d_sy,
+                                     pl->d_gt_perm, pl->Tb, pl->d_yre, pl->d_yim, pl->st, pl->gt_rows - kRowSpecPad));
+            tv.done();
+            GridTcArgs ga{};
+            ga.P = pl->P;
+            ga.N = pl->N;
+            ga.nt = nt;
+            ga.nc = nc;
+            ga.c0 = c0;
+            ga.AP = pl->gt_rows;
+            ga.kp_max = pl->gt_kp_max;
+            ga.tile_cell = pl->d_gt_tile_cell;
+            ga.kp = pl->d_gt_kp;
+            ga.chunk_off = pl->d_gt_chunk_off;
+            ga.chunk_row = pl->d_gt_chunk_row;
+            ga.bimg_off = pl->d_gt_bimg_off;
+            ga.bimg = pl->d_gt_bimg;
+            ga.G = pl->d_G;
+            ga.slab_t = 1;     // channel-major slabs [Cb][Tb]: a CTA's samples of one channel are contiguous
+            ga.slab_c = pl->Tb;
+            ga.err = pl->d_err;
+            TimedLaunch tg(pl, 1);
+            MOFF_CK(launch_grid_tc(ga, pl->gt_map_re, pl->gt_map_im, pl->gt_tiles, std::min(pl->gt_cgroups, nc),
+                                   pl->gt_smem, pl->st));
+            tg.done();
+            RowDftArgs ra{};
+            ra.G = pl->d_G;
+            ra.H = reinterpret_cast<__half *>(pl->d_H);
+            ra.slab_t = 1;
+            ra.slab_c = pl->Tb;
+            ra.nt = nt;
+            ra.c0 = c0;
+            ra.nc = nc;
+            ra.row_nz = pl->d_row_nz;
+            ra.active = pl->d_gt_active;
+            ra.dft_tab = pl->d_dft_tab;
+            ra.err = pl->d_err;
+            TimedLaunch tr(pl, 7);
+            MOFF_CK(launch_rows_dft(pl->N, pl->P, ra, pl->st));
+            tr.done();
+            ColDftArgs ca{};
+            ca.H = reinterpret_cast<const __half *>(pl->d_H);
+            ca.slab_t = 1;
+            ca.slab_c = pl->Tb;
+            ca.nt = nt;
+            ca.c0 = c0;
+            ca.nc = nc;
+            ca.acc = pl->d_acc;
+            ca.row_nz = pl->d_row_nz;
+            ca.sy = pl->d_sy;
+            ca.s_t = pl->dft_s_t;
+            ca.dft_tab = pl->d_dft_tab;
+            ca.err = pl->d_err;
+            TimedLaunch tc(pl, 2);
+            MOFF_CK(launch_cols_dft(pl->N, pl->P, ca, pl->st));
+            tc.done();
+            MOFF_CK_S(run_feedback(pl, volt, tstride, t0, nt, c0, nc));
+        }
+    }
+    return MOFF_OK;
+}
+
 moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
+    if (pl->gtc) return run_image_gtc(pl, volt, n_time, tstride);
     if (pl->dft) return run_image_dft(pl, volt, n_time, tstride);
     if (pl->tc) return run_image_tc(pl, volt, n_time, tstride);
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
@@ -1758,6 +1843,18 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
     unsigned char *base = static_cast<unsigned char *>(scratch);
     pl->d_H = reinterpret_cast<float2 *>(base);
     size_t off = align_up(pl->h_bytes, 1024);
+    if (pl->gtc) {
+        pl->d_G = reinterpret_cast<__half *>(base + off);
+        off += align_up(pl->h_bytes, 1024);
+        pl->d_yre = reinterpret_cast<__half *>(base + off);
+        off += align_up(pl->y_bytes, 1024);
+        pl->d_yim = reinterpret_cast<__half *>(base + off);
+        off += align_up(pl->y_bytes, 1024);
+        const long long rows = (long long)pl->Cb * pl->gt_rows;
+        if (encode_plane_map(&pl->gt_map_re, pl->d_yre, pl->Tb, rows, 16) != cudaSuccess ||
+            encode_plane_map(&pl->gt_map_im, pl->d_yim, pl->Tb, rows, 16) != cudaSuccess)
+            return fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded");
+    }
     if (pl->tc && !pl->dft) {
         pl->d_yre = reinterpret_cast<__half *>(base + off);
         off += align_up(pl->y_bytes, 1024);
@@ -1886,6 +1983,20 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         if (cudaMemcpy(pl->d_gains, one.data(), n * 8, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(MOFF_ECUDA, "gain upload failed"));
     }
+    // Tensor-core gridding tables (FP16 path, factored-DFT route): B images scaled by the same power
+    // of two as the gather's FP16 field (the kernel scale), so the row transform sees one field.
+    GridTc gtab;
+    if (pl->dft) {
+        const char *e = getenv("MOFF_TC_GRID");
+        if (!(e && atoi(e) == 0)) {
+            pl->dft_s_t = dft_kernel_scale(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps);
+            if ((s = build_gridtc(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps, pl->dft_s_t, &gtab)) != MOFF_OK)
+                return bail(s);
+            // one CTA per SM: the tile's kernel matrix, the A ring and the barriers must fit shared memory
+            pl->gtc = !gtab.tile_cell.empty() && gridtc_smem_bytes(n_pol, gtab.kp_max) <= 227 * 1024;
+            pl->gt_rows = gtab.n_rows + kRowSpecPad;
+        }
+    }
     // accumulators and image staging
     {
         const size_t n = (size_t)n_chan * pl->nprod * grid_n * grid_n;
@@ -1905,7 +2016,13 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             const long long n = (n_chan + cb_max - 1) / cb_max;
             return (n_chan + n - 1) / n;
         };
-        if (pl->dft) {
+        if (pl->gtc) {
+            // 128 samples per chunk (the tensor-core gridding's product height): the FP16 gridded and
+            // row-transformed fields and the FP16 voltage planes of every sample of every channel
+            const size_t per_c = 128 * (2 * per + (size_t)pl->gt_rows * 4);
+            pl->Tb = 128;
+            pl->Cb = (int)balance(std::max(1LL, std::min<long long>(n_chan, budget / (long long)per_c)));
+        } else if (pl->dft) {
             // FP16 field only; up to 128 samples per chunk (FP32 sums per chunk, then FP64)
             const long long cb = balance(std::max(1LL, std::min<long long>(n_chan, budget / (long long)(32 * per))));
             const long long tb = std::max(1LL, std::min<long long>(128, budget / (long long)(cb * per)));
@@ -1923,8 +2040,18 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             pl->Tb = (int)tb;
         }
         pl->h_bytes = (size_t)pl->Tb * pl->Cb * per;
+        if (pl->gtc) pl->y_bytes = (size_t)pl->Cb * pl->gt_rows * pl->Tb * 2;
         if (!pl->served) {
             if ((s = palloc(pl, &pl->d_H, pl->h_bytes)) != MOFF_OK) return bail(s);
+            if (pl->gtc) {
+                if ((s = palloc(pl, &pl->d_G, pl->h_bytes)) != MOFF_OK) return bail(s);
+                if ((s = palloc(pl, &pl->d_yre, pl->y_bytes)) != MOFF_OK) return bail(s);
+                if ((s = palloc(pl, &pl->d_yim, pl->y_bytes)) != MOFF_OK) return bail(s);
+                const long long rows = (long long)pl->Cb * pl->gt_rows;
+                if (encode_plane_map(&pl->gt_map_re, pl->d_yre, pl->Tb, rows, 16) != cudaSuccess ||
+                    encode_plane_map(&pl->gt_map_im, pl->d_yim, pl->Tb, rows, 16) != cudaSuccess)
+                    return bail(fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded"));
+            }
             if (pl->tc && !pl->dft && encode_field_map(&pl->h_map, pl->d_H, grid_n, n_pol, pl->Cb, pl->Tb) != cudaSuccess)
                 return bail(fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded"));
             pl->h_map_nt = pl->Tb;
@@ -1937,8 +2064,31 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         if ((s = palloc(pl, &pl->d_dft_tab, tab.size())) != MOFF_OK) return bail(s);
         if (cudaMemcpy(pl->d_dft_tab, tab.data(), tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(MOFF_ECUDA, "tensor-core DFT table upload failed"));
-        pl->dft_s_t = dft_kernel_scale(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps);
+        if (!pl->gtc) pl->dft_s_t = dft_kernel_scale(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps);
         if ((s = palloc(pl, &pl->d_sy, (size_t)n_chan * 4)) != MOFF_OK) return bail(s);
+        if (pl->gtc) {
+            pl->gt_tiles = (int)gtab.tile_cell.size();
+            pl->gt_kp_max = gtab.kp_max;
+            pl->gt_smem = gridtc_smem_bytes(n_pol, gtab.kp_max);
+            // channel groups: about two CTAs' worth of tiles per SM over a launch
+            int sms = 152;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
+            pl->gt_cgroups = std::max(1, std::min(pl->Cb, (2 * sms + pl->gt_tiles - 1) / pl->gt_tiles));
+            if (const char *e = getenv("MOFF_TC_CGROUPS")) pl->gt_cgroups = std::max(1, std::min(pl->Cb, atoi(e)));
+            auto up = [&](auto **dst, const auto &v) -> moff_status {
+                moff_status st = palloc(pl, dst, std::max<size_t>(v.size(), 1) * sizeof(v[0]));
+                if (st != MOFF_OK) return st;
+                if (!v.empty() && cudaMemcpy(*dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice) != cudaSuccess)
+                    return fail(MOFF_ECUDA, "tensor-core gridding table upload failed");
+                return MOFF_OK;
+            };
+            if ((s = up(&pl->d_gt_tile_cell, gtab.tile_cell)) != MOFF_OK || (s = up(&pl->d_gt_kp, gtab.kp)) != MOFF_OK ||
+                (s = up(&pl->d_gt_chunk_off, gtab.chunk_off)) != MOFF_OK ||
+                (s = up(&pl->d_gt_chunk_row, gtab.chunk_row)) != MOFF_OK || (s = up(&pl->d_gt_perm, gtab.perm)) != MOFF_OK ||
+                (s = up(&pl->d_gt_bimg_off, gtab.bimg_off)) != MOFF_OK || (s = up(&pl->d_gt_bimg, gtab.bimg)) != MOFF_OK ||
+                (s = up(&pl->d_gt_active, gtab.active)) != MOFF_OK)
+                return bail(s);
+        }
         if ((s = palloc(pl, &pl->d_err, 16)) != MOFF_OK) return bail(s);
         if (cudaMemset(pl->d_err, 0, 16) != cudaSuccess) return bail(fail(MOFF_ECUDA, "memset failed"));
         if (launch_gain_scale(pl->d_gains, n_chan, n_ant * n_pol, pl->d_sy, pl->st) != cudaSuccess)
@@ -1947,7 +2097,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     // gridding shape: measured on the plan's own chunk (MOFF_AUTOTUNE), else the built-in rule
     {
         GridChoice tuned;
-        if ((flags & MOFF_AUTOTUNE) && (!pl->tc || pl->dft)) {
+        if ((flags & MOFF_AUTOTUNE) && (!pl->tc || pl->dft) && !pl->gtc) {
             if ((s = tune_grid(pl, pos, taps, &tuned)) != MOFF_OK) return bail(s);
         }
         if ((s = bin_plan(pl, pos, taps, pl->tune_source ? &tuned : nullptr)) != MOFF_OK) return bail(s);
@@ -2035,7 +2185,8 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
                 return bail(fail(MOFF_ECUDA, "F-stage table upload failed"));
         }
     }
-    pl->scratch_bytes = align_up(pl->h_bytes, 1024) + (pl->tc && !pl->dft ? 2 * align_up(pl->y_bytes, 1024) : 0);
+    pl->scratch_bytes = align_up(pl->h_bytes, 1024) + (pl->tc && !pl->dft ? 2 * align_up(pl->y_bytes, 1024) : 0) +
+                        (pl->gtc ? align_up(pl->h_bytes, 1024) + 2 * align_up(pl->y_bytes, 1024) : 0);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(MOFF_ECUDA, "plan set-up failed"));
     *out = pl;
     g_err.clear();
@@ -2587,7 +2738,7 @@ moff_status moff_set_timing(moff_plan *pl, int on) {
 moff_status moff_timing(moff_plan *pl, int kind, double *total_ms, long long *launches, int reset) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
-    if (kind < 0 || kind > 6) return fail(MOFF_EINVAL, "kind (%d) must be in [0, 6]", kind);
+    if (kind < 0 || kind > 7) return fail(MOFF_EINVAL, "kind (%d) must be in [0, 7]", kind);
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
     double tot = 0.0;
     long long n = 0;
@@ -2606,7 +2757,7 @@ moff_status moff_timing(moff_plan *pl, int kind, double *total_ms, long long *la
 
 moff_status moff_plan_route(const moff_plan *pl, int *route) {
     if (!pl || !route) return fail(MOFF_EINVAL, "plan and route must not be NULL");
-    *route = pl->dft ? 2 : (pl->tc ? 1 : 0);
+    *route = pl->gtc ? 3 : (pl->dft ? 2 : (pl->tc ? 1 : 0));
     return MOFF_OK;
 }
 

@@ -275,6 +275,248 @@ __global__ void __launch_bounds__(kBlock, 1) k_cols_dft(const ColDftArgs a) {
     if (warp == 0) tc::tmem_dealloc(tbase, CS::TCOLS);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Row transform of a gridded field that is already in global memory (FP16 rows [re N][im N],
+// written by the tensor-core gridding): one CTA = a stripe of RS grid rows (both pols) of one
+// channel walking a chunk of samples.  Per sample the F = P RS rows land by 16-byte cp.async
+// pieces as the stage-1 A operand, MN-major (row m = f N2 + b, k = 2 a + re/im: each piece is 8
+// consecutive b of one (f, a, re/im)); pieces of cells no tile reaches are zero, cleared once.
+// Stage 1, twiddle, stage 2 and the FP16 store of the row-transformed rows as in the gridding
+// kernel's row transform; loads of sample t + 1 and stage 1 of sample t overlap the epilogue of
+// sample t - 1.
+template <int N, int P>
+struct RowDftShape {
+    using S = DftShape<N>;
+    static constexpr int RS = 8 / P;                    // grid rows per stripe (8 transform rows, inside one tile band)
+    static constexpr int F = P * RS;                    // transform rows per sample, f = p RS + rl
+    static constexpr int N2 = S::N2;
+    static constexpr int M1 = F * N2, T1 = M1 / 128;    // stage-1 rows (f, b)
+    static constexpr int LBO1 = (M1 / 8) * 128;
+    static constexpr int A1B = M1 * S::K1 * 2;
+    static constexpr int M2 = 16 * F, T2 = M2 / 128;    // stage-2 rows (f, c)
+    static constexpr int LBO2 = (M2 / 8) * 128;
+    static constexpr int A2B = M2 * S::K2 * 2;
+    static constexpr int SLD = N + 8;                   // staging row (halves)
+    static constexpr int STB = F * 2 * SLD * 2;
+    static constexpr int D1 = T1 * S::C1, D2 = T2 * S::C2;
+    static constexpr int TC_ = D1 + D2;
+    static constexpr int TCOLS = TC_ <= 32 ? 32 : (TC_ <= 64 ? 64 : (TC_ <= 128 ? 128 : (TC_ <= 256 ? 256 : 512)));
+    static constexpr int NPIECE = F * 16 * 2 * (N2 / 8);   // (f, a, re/im, b8)
+    static constexpr int ITER = NPIECE / kBlock;
+    static constexpr size_t SMEM = 16 + 2 * (size_t)A1B + A2B + STB + S::TAB_BYTES + 32;
+    static_assert(M1 % 128 == 0 && M2 % 128 == 0 && NPIECE % kBlock == 0 && ITER <= 32, "row-transform shape");
+};
+
+template <int N, int P>
+__global__ void __launch_bounds__(kBlock) k_rows_dft(const RowDftArgs a) {
+    using S = DftShape<N>;
+    using RD = RowDftShape<N, P>;
+    constexpr int N2 = S::N2, K2 = S::K2, C2 = S::C2, F = RD::F, RS = RD::RS;
+    const int s = blockIdx.x, cl = blockIdx.y, c = a.c0 + cl;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3;
+    const int ry0 = s * RS;
+    {   // stripes no kernel reaches carry no field: nothing to transform or store
+        bool any = false;
+        for (int rl = 0; rl < RS; ++rl) any |= ((a.row_nz[(ry0 + rl) >> 5] >> ((ry0 + rl) & 31)) & 1u) != 0;
+        if (!any) return;
+    }
+    (void)c;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *sA1 = smem;                                   // [2][A1B]
+    unsigned char *sA2 = sA1 + 2 * RD::A1B;
+    __half *stage = reinterpret_cast<__half *>(sA2 + RD::A2B);
+    unsigned char *sTab = sA2 + RD::A2B + RD::STB;
+    const unsigned char *sB1 = sTab, *sB2 = sTab + S::B1_BYTES;
+    const float2 *sTw = reinterpret_cast<const float2 *>(sB2 + S::B2_BYTES);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sTab + S::TAB_BYTES);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+
+    dftc::load_table(sTab, a.dft_tab, S::TAB_BYTES);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, RD::TCOLS);
+        tc::tmem_relinquish();
+    }
+    auto piece = [&](int i, int &f, int &aa, int &ri, int &b8) {
+        b8 = i % (N2 / 8);
+        int r = i / (N2 / 8);
+        ri = r & 1;
+        r >>= 1;
+        aa = r & 15;
+        f = r >> 4;
+    };
+    auto piece_dst = [&](int f, int aa, int ri, int b8) -> uint32_t {
+        const int k = 2 * aa + ri;
+        return (uint32_t)((f * (N2 / 8) + b8) * 128 + (k >> 3) * RD::LBO1 + (k & 7) * 16);
+    };
+    const int ty = ry0 >> 3, nty = N / 8;
+    uint32_t act = 0;
+#pragma unroll
+    for (int k = 0; k < RD::ITER; ++k) {
+        int f, aa, ri, b8;
+        piece(tid + k * kBlock, f, aa, ri, b8);
+        const int tx = (N2 * aa + 8 * b8) >> 3;
+        if (a.active[ty * nty + tx]) {
+            act |= 1u << k;
+        } else {
+            const uint32_t d = piece_dst(f, aa, ri, b8);
+            *reinterpret_cast<uint4 *>(sA1 + d) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(sA1 + RD::A1B + d) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+    const float sc = 1.0f / (float)N2;
+
+    auto row_base = [&](const __half *base, int tt, int f) -> long long {
+        const int p = f / RS, rl = f - p * RS;
+        return (((long long)tt * a.slab_t + (long long)cl * a.slab_c) * P + p) * N * 2 * N +
+               (long long)(ry0 + rl) * 2 * N;
+    };
+    auto load = [&](int tt, int buf) {
+        unsigned char *dst = sA1 + buf * RD::A1B;
+#pragma unroll
+        for (int k = 0; k < RD::ITER; ++k) {
+            if ((act >> k) & 1u) {
+                int f, aa, ri, b8;
+                piece(tid + k * kBlock, f, aa, ri, b8);
+                cp_async16(dst + piece_dst(f, aa, ri, b8), a.G + row_base(a.G, tt, f) + ri * N + N2 * aa + 8 * b8);
+            }
+        }
+        cp_async_commit();
+    };
+    auto issue_s1 = [&](int buf) {
+        tc::fence_after_sync();
+        const uint32_t id1 = tc::idesc_f16(128, S::C1, true, false);
+        const uint32_t a0 = tc::smem_u32(sA1 + buf * RD::A1B), b0 = tc::smem_u32(sB1);
+#pragma unroll
+        for (int j = 0; j < RD::T1; ++j)
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks)
+                tc::mma_f16(tbase + (uint32_t)(j * S::C1),
+                            tc::smem_desc(a0 + j * 2048 + ks * 2 * RD::LBO1, RD::LBO1, 128),
+                            tc::smem_desc(b0 + ks * 256, 128, 512), id1, ks > 0);
+        tc::mma_commit(&mbar[0]);
+    };
+    auto issue_s2 = [&]() {
+        tc::fence_after_sync();
+        const uint32_t id2 = tc::idesc_f16(128, C2, true, false);
+        const uint32_t a0 = tc::smem_u32(sA2), b0 = tc::smem_u32(sB2);
+        constexpr uint32_t SBOB = (K2 / 8) * 128;
+#pragma unroll
+        for (int j = 0; j < RD::T2; ++j)
+#pragma unroll
+            for (int ks = 0; ks < K2 / 16; ++ks)
+                tc::mma_f16(tbase + (uint32_t)(RD::D1 + j * C2),
+                            tc::smem_desc(a0 + j * 2048 + ks * 2 * RD::LBO2, RD::LBO2, 128),
+                            tc::smem_desc(b0 + ks * 256, 128, SBOB), id2, ks > 0);
+        tc::mma_commit(&mbar[1]);
+    };
+    // twiddle, then stage-2 A: thread (f, b) writes 8 consecutive c at k = b (re) and N2 + b (im)
+    auto epi1 = [&]() {
+        for (int u = warp >> 2; u < RD::T1; u += kBlock / 128) {
+            const int m = 128 * u + 32 * q + lane;
+            const int f = m / N2, b = m - f * N2;
+            float v[32];
+            tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * u), v);
+            uint32_t re[8], im[8];
+#pragma unroll
+            for (int cc = 0; cc < 16; cc += 2) {
+                const float2 t0 = sTw[cc * N2 + b], t1 = sTw[(cc + 1) * N2 + b];
+                re[cc >> 1] = dftc::pack_hh(v[2 * cc] * t0.x - v[2 * cc + 1] * t0.y,
+                                            v[2 * cc + 2] * t1.x - v[2 * cc + 3] * t1.y);
+                im[cc >> 1] = dftc::pack_hh(v[2 * cc] * t0.y + v[2 * cc + 1] * t0.x,
+                                            v[2 * cc + 2] * t1.y + v[2 * cc + 3] * t1.x);
+            }
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                const int mg = 2 * f + ch, kr = b, ki = N2 + b;
+                *reinterpret_cast<uint4 *>(sA2 + mg * 128 + (kr >> 3) * RD::LBO2 + (kr & 7) * 16) =
+                    make_uint4(re[4 * ch], re[4 * ch + 1], re[4 * ch + 2], re[4 * ch + 3]);
+                *reinterpret_cast<uint4 *>(sA2 + mg * 128 + (ki >> 3) * RD::LBO2 + (ki & 7) * 16) =
+                    make_uint4(im[4 * ch], im[4 * ch + 1], im[4 * ch + 2], im[4 * ch + 3]);
+            }
+        }
+    };
+    // stage-2 accumulators -> FP16 (x 1/N2) staging rows [f][re/im][SLD], then 16-byte stores
+    auto epi2 = [&](int tt) {
+        constexpr int NCB = C2 / 32;
+        for (int u = warp >> 2; u < RD::T2 * NCB; u += kBlock / 128) {
+            const int j = u / NCB, cb2 = u - j * NCB;
+            const int m2 = 128 * j + 32 * q + lane;
+            const int f = m2 >> 4, cc = m2 & 15;
+            float v[32];
+            tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(RD::D1 + j * C2 + 32 * cb2), v);
+            __half *sr = stage + (2 * f) * RD::SLD + cc + 16 * 16 * cb2;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                sr[16 * i] = __float2half_rn(v[2 * i] * sc);
+                sr[RD::SLD + 16 * i] = __float2half_rn(v[2 * i + 1] * sc);
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        constexpr int PR = N / 8;
+        for (int i = tid; i < F * 2 * PR; i += kBlock) {
+            const int rr = i / PR, pc = i - rr * PR;
+            *reinterpret_cast<uint4 *>(a.H + row_base(a.H, tt, rr >> 1) + (rr & 1) * N + 8 * pc) =
+                *reinterpret_cast<const uint4 *>(stage + rr * RD::SLD + 8 * pc);
+        }
+    };
+
+    bool ok = true;
+    if (a.nt > 0) load(0, 0);
+    for (int t = 0; t < a.nt; ++t) {
+        const int buf = t & 1;
+        cp_async_wait<0>();
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (tid == 0) issue_s1(buf);
+        if (t + 1 < a.nt) load(t + 1, buf ^ 1);
+        if (t > 0) {
+            ok &= tc::mbar_wait_bounded(&mbar[1], (uint32_t)((t - 1) & 1), dftc::kWaitCycles);
+            tc::fence_after_sync();
+            epi2(t - 1);
+        }
+        ok &= tc::mbar_wait_bounded(&mbar[0], (uint32_t)(t & 1), dftc::kWaitCycles);
+        tc::fence_after_sync();
+        epi1();
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (tid == 0) issue_s2();
+    }
+    if (ok && a.nt > 0) {
+        ok &= tc::mbar_wait_bounded(&mbar[1], (uint32_t)((a.nt - 1) & 1), dftc::kWaitCycles);
+        tc::fence_after_sync();
+        epi2(a.nt - 1);
+    }
+    cp_async_wait<0>();
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok);
+    tc::fence_after_sync();
+    if (!ok && tid == 0) atomicExch(a.err, tc::kErrWaitTimeout);
+    if (warp == 0) tc::tmem_dealloc(tbase, RD::TCOLS);
+}
+
+template <int N, int P>
+cudaError_t launch_rows_dft_t(const RowDftArgs &a, cudaStream_t st) {
+    auto k = k_rows_dft<N, P>;
+    const size_t smem = RowDftShape<N, P>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(N / RowDftShape<N, P>::RS, a.nc), kBlock, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int N, int P>
 cudaError_t launch_cols_dft_t(const ColDftArgs &a, cudaStream_t st) {
     auto k = k_cols_dft<N, P>;
@@ -336,6 +578,12 @@ size_t cols_dft_smem_bytes(int N, int P) {
 cudaError_t launch_cols_dft(int N, int P, const ColDftArgs &a, cudaStream_t st) {
     if (N == 512) return P == 1 ? launch_cols_dft_t<512, 1>(a, st) : launch_cols_dft_t<512, 2>(a, st);
     if (N == 256) return P == 1 ? launch_cols_dft_t<256, 1>(a, st) : launch_cols_dft_t<256, 2>(a, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rows_dft(int N, int P, const RowDftArgs &a, cudaStream_t st) {
+    if (N == 512) return P == 1 ? launch_rows_dft_t<512, 1>(a, st) : launch_rows_dft_t<512, 2>(a, st);
+    if (N == 256) return P == 1 ? launch_rows_dft_t<256, 1>(a, st) : launch_rows_dft_t<256, 2>(a, st);
     return cudaErrorInvalidValue;
 }
 

@@ -79,6 +79,50 @@ struct ColDftArgs {
     int *err;
 };
 
+// Dense tensor-core row transform of a gridded field in global memory (k_rows_dft).
+struct RowDftArgs {
+    const __half *G;          // FP16 gridded rows [re N][im N]; slab [P][N] at t * slab_t + cl * slab_c
+    __half *H;                // FP16 row-transformed rows, same layout; the value carries 1/N more
+    long long slab_t, slab_c;
+    int nt, c0, nc;
+    const uint32_t *row_nz;   // stripes with no reached row are skipped
+    const unsigned char *active;   // [N/8][N/8] 8x8 cell tiles the gridding writes (others zero)
+    const unsigned char *dft_tab;
+    int *err;
+};
+
+// Tensor-core gridding of dense arrays (k_grid_tc, moff_gridtc.cu): per tile of 8 x 8 cells a
+// product of the tile's antenna voltages (FP16 planes, raster order of anchors) with the
+// tile's kernel values.
+struct GridTcArgs {
+    int P, N, nt, nc, c0, AP, kp_max;   // AP: plane rows per channel (voltages + kRowSpecPad)
+    const int *tile_cell;      // [tiles] (ty << 16) | tx: cells 8 ty .. 8 ty + 7, 8 tx .. 8 tx + 7
+    const int *kp;             // [tiles] contraction length (32 per chunk of 16 plane rows)
+    const int *chunk_off;      // [tiles + 1]
+    const int *chunk_row;      // first plane row (within a channel) of each chunk
+    const long long *bimg_off; // [tiles] byte offset of each tile's B image [2 P 64][kp] K-major
+    const __half *bimg;
+    __half *G;                 // FP16 gridded rows [re N][im N]; slab [P][N] at t * slab_t + cl * slab_c
+    long long slab_t, slab_c;
+    int *err;
+};
+struct GridTc {
+    int kp_max = 0;
+    int n_rows = 0;                             // voltage-plane rows per channel (antenna-pols, with copies)
+    std::vector<int> perm;                      // [n_rows] plane row -> voltage index (anchor rows ascending, each
+                                                // by column, then copies of its first columns; pols interleaved)
+    std::vector<int> tile_cell, kp, chunk_off, chunk_row;
+    std::vector<long long> bimg_off;
+    std::vector<__half> bimg;
+    std::vector<unsigned char> active;          // [N/8][N/8]
+};
+moff_status build_gridtc(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, float scale,
+                         GridTc *gt);
+size_t gridtc_smem_bytes(int P, int kp_max);
+cudaError_t launch_grid_tc(const GridTcArgs &a, const CUtensorMap &are, const CUtensorMap &aim, int n_tiles,
+                           int cgroups, size_t smem, cudaStream_t st);
+cudaError_t launch_rows_dft(int N, int P, const RowDftArgs &a, cudaStream_t st);
+
 // Column transform + square-and-integrate (Eq. m6 steps 3-4, second axis).
 struct ColArgs {
     const float2 *H;          // FP32 field, or (fp16 path) half2: slab [P][N][N] of (sample t,
@@ -299,14 +343,15 @@ cudaError_t launch_gain_scale(const float2 *gains, int C, int AP, float *sy, cud
 // Voltage planes: plane row v < AP of a channel holds voltage perm[v] (antenna * P + input
 // pol); rows AP .. APpad - 1 are zero.  APpad = AP + kRowSpecPad.
 constexpr int kRowSpecPad = 32;
+// Plane rows v < n_rows hold voltage perm[v]; rows n_rows .. APpad - 1 are zero (n_rows < 0: AP).
 cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc, int AP,
                              int APpad, const float2 *gains, const float *sy, const int *perm, int Tpad, __half *yre,
-                             __half *yim, cudaStream_t st);
+                             __half *yim, cudaStream_t st, int n_rows = -1);
 cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap, const CUtensorMap &amap_re,
                            const CUtensorMap &amap_im, int cgroups, size_t smem, cudaStream_t st);
 // Tensor map of one FP16 voltage plane [rows][Tpad] (rows = Cb * A * P), box 64 samples x
 // 32 rows, 128-byte swizzle, rows past the end read as zero: the A loads of k_rowspec_tc.
-cudaError_t encode_plane_map(CUtensorMap *map, void *plane, int Tpad, long long rows);
+cudaError_t encode_plane_map(CUtensorMap *map, void *plane, int Tpad, long long rows, int box_rows = 32);
 // Tensor map of the FP16 row-transformed field [nt][Cb][P*N][N] (half2 as 32-bit
 // elements), box 32 kx x 32 samples, 128-byte swizzle: the store target of
 // k_rowspec_tc.  Stores of samples >= nt fall outside the map and are dropped.

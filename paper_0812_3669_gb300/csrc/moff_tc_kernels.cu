@@ -70,7 +70,8 @@ __global__ void k_gain_scale(const float2 *__restrict__ gains, int AP, float *__
 __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ volt, long long tstride, int t0, int nt,
                                                    int c0, int AP, int APpad, const float2 *__restrict__ gains,
                                                    const float *__restrict__ sy, const int *__restrict__ perm, int Tpad,
-                                                   int TT, __half *__restrict__ yre, __half *__restrict__ yim) {
+                                                   int TT, __half *__restrict__ yre, __half *__restrict__ yim,
+                                                   int n_rows) {
     extern __shared__ __align__(16) unsigned char s_v[];   // [TT][APr] voltage bytes
     const int cl = blockIdx.y, c = c0 + cl;
     const int tb = blockIdx.x * TT;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ v
         for (int i = threadIdx.x; i < APpad * ng; i += blockDim.x) {
             const int v = i / ng, t8 = 8 * (i - v * ng);
             uint4 re = make_uint4(0u, 0u, 0u, 0u), im = re;
-            if (v < AP) {
+            if (v < n_rows) {
                 const int sv = perm[v];
                 const float2 g = gains[(long long)c * AP + sv];
                 __half2 hr[4], hi[4];
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ v
     for (int i = threadIdx.x; i < APpad * np; i += blockDim.x) {
         const int v = i / np, tp = 2 * (i - v * np), t = tb + tp;
         __half2 re = __floats2half2_rn(0.f, 0.f), im = re;
-        if (v < AP) {
+        if (v < n_rows) {
             const int sv = perm[v];
             const float2 g = gains[(long long)c * AP + sv];
             float2 y0 = cmul(g, decode4_tc(s_v[tp * APr + sv])), y1 = cmul(g, decode4_tc(s_v[(tp + 1) * APr + sv]));
@@ -379,7 +380,7 @@ cudaError_t launch_gain_scale(const float2 *gains, int C, int AP, float *sy, cud
 
 cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc, int AP,
                              int APpad, const float2 *gains, const float *sy, const int *perm, int Tpad, __half *yre,
-                             __half *yim, cudaStream_t st) {
+                             __half *yim, cudaStream_t st, int n_rows) {
     // samples per CTA: 32, or fewer (even, dividing Tpad) so the staged bytes stay within 96 KB
     const size_t APr = (size_t)((AP + 15) & ~15);
     int TT = 32;
@@ -389,7 +390,8 @@ cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int
     cudaError_t e = cudaFuncSetAttribute(k_volt_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(Tpad / TT, nc);
-    k_volt_prep<<<grid, 256, smem, st>>>(volt, tstride, t0, nt, c0, AP, APpad, gains, sy, perm, Tpad, TT, yre, yim);
+    k_volt_prep<<<grid, 256, smem, st>>>(volt, tstride, t0, nt, c0, AP, APpad, gains, sy, perm, Tpad, TT, yre, yim,
+                                         n_rows < 0 ? AP : n_rows);
     return cudaGetLastError();
 }
 
@@ -415,7 +417,7 @@ cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap,
     return cudaErrorInvalidValue;
 }
 
-cudaError_t encode_plane_map(CUtensorMap *map, void *plane, int Tpad, long long rows) {
+cudaError_t encode_plane_map(CUtensorMap *map, void *plane, int Tpad, long long rows, int box_rows) {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
@@ -426,7 +428,7 @@ cudaError_t encode_plane_map(CUtensorMap *map, void *plane, int Tpad, long long 
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     const cuuint64_t dims[2] = {(cuuint64_t)Tpad, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)Tpad * 2};
-    const cuuint32_t box[2] = {64, 32};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = reinterpret_cast<Encode>(fn)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, plane, dims, strides, box,
                                                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,

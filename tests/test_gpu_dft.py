@@ -1,5 +1,7 @@
 """Factored-DFT tensor-core route of the FP16 path (both transform axes as
-tcgen05 contractions, N = 16 x N/16) against the FP64 oracle.
+tcgen05 contractions, N = 16 x N/16) against the FP64 oracle, with the
+gridding on the tensor cores (cell tiles, the default) and as the FP32 gather
+fused with the row transform (MOFF_TC_GRID=0).
 
 Bar: max-normalised error <= 3e-3 per (channel, product), the reduced-precision
 tolerance.  Error budget: the gridded field, the stage-1 results and the
@@ -44,9 +46,20 @@ def case(seed, A, N, K, P, C, T, jones=False, spread=None, sigma=2.5):
     return pos, c64(taps), synth.pack_4bit(re, im), c64(synth.gains_random(rng, C, A, P))
 
 
-def dft_image(pos, taps, N, C, P, codes, gains, jones=False, autotune=False):
+ROUTES = ("fp16_dft", "fp16_tcgrid")
+
+
+@pytest.fixture(params=["tcgrid", "gather"])
+def grid_kind(request, monkeypatch):
+    """Both gridding variants of the route: on the tensor cores, or the FP32 gather."""
+    if request.param == "gather":
+        monkeypatch.setenv("MOFF_TC_GRID", "0")
+    return "fp16_tcgrid" if request.param == "tcgrid" else "fp16_dft"
+
+
+def dft_image(pos, taps, N, C, P, codes, gains, jones=False, autotune=False, route=None):
     with moff.Plan(pos, taps, N, C, P, jones=jones, fp16tc=True, autotune=autotune) as pl:
-        assert pl.route() == "fp16_dft"
+        assert pl.route() in ROUTES and (route is None or pl.route() == route), pl.route()
         pl.set_gains(gains)
         pl.submit(np.ascontiguousarray(codes))
         img, n = pl.read_image()
@@ -69,17 +82,18 @@ def check(img, ref, label, tol=TOL16):
     (512, 1, 3, 100, 10, False, 5),       # 5 samples per chunk, channel chunks of 1
     (512, 2, 5, 150, 9, True, None),      # Jones kernels
 ])
-def test_dft_route_shapes(monkeypatch, N, P, K, A, T, jones, scratch_mb):
+def test_dft_route_shapes(monkeypatch, grid_kind, N, P, K, A, T, jones, scratch_mb):
     monkeypatch.setenv("MOFF_TC_DFT", "1")
     if scratch_mb:
         monkeypatch.setenv("MOFF_SCRATCH_MB", str(scratch_mb))
     C = 3
     pos, taps, codes, gains = case(700 + N + 10 * P + K, A, N, K, P, C, T, jones=jones)
-    img = dft_image(pos, taps, N, C, P, codes, gains, jones=jones)
-    check(img, oracle.moff_image(codes, gains, pos, taps, N, P, jones=jones), f"N={N} P={P} K={K} jones={jones}")
+    img = dft_image(pos, taps, N, C, P, codes, gains, jones=jones, route=grid_kind)
+    check(img, oracle.moff_image(codes, gains, pos, taps, N, P, jones=jones),
+          f"{grid_kind} N={N} P={P} K={K} jones={jones}")
 
 
-def test_dft_route_dense_array_is_automatic():
+def test_dft_route_dense_array_is_automatic(grid_kind):
     """A filled lattice too dense for the row-spectrum contraction takes the
     factored-DFT route on its own (no environment override), at N = 256."""
     rng = np.random.default_rng(71)
@@ -90,11 +104,11 @@ def test_dft_route_dense_array_is_automatic():
     re = np.clip(np.rint(rng.normal(0, 2, size=(T, C, pos.shape[0], P))), -7, 7).astype(int)
     im = np.clip(np.rint(rng.normal(0, 2, size=(T, C, pos.shape[0], P))), -7, 7).astype(int)
     codes = synth.pack_4bit(re, im)
-    img = dft_image(pos, taps, N, C, P, codes, gains)
-    check(img, oracle.moff_image(codes, gains, pos, taps, N, P), "dense 48x48 lattice, N=256")
+    img = dft_image(pos, taps, N, C, P, codes, gains, route=grid_kind)
+    check(img, oracle.moff_image(codes, gains, pos, taps, N, P), f"{grid_kind} dense 48x48 lattice, N=256")
 
 
-def test_dft_route_deterministic_and_gain_rescale(monkeypatch):
+def test_dft_route_deterministic_and_gain_rescale(monkeypatch, grid_kind):
     monkeypatch.setenv("MOFF_TC_DFT", "1")
     pos, taps, codes, gains = case(760, 120, 256, 5, 2, C=2, T=11)
     a = dft_image(pos, taps, 256, 2, 2, codes, gains)
@@ -126,6 +140,7 @@ def test_dft_route_autotuned_shape(monkeypatch):
     whichever it picks, the image stays within the tolerance."""
     monkeypatch.setenv("MOFF_TC_DFT", "1")
     pos, taps, codes, gains = case(780, 250, 512, 5, 2, C=2, T=8)
+    monkeypatch.setenv("MOFF_TC_GRID", "0")          # the autotuner times the gather's shapes
     with moff.Plan(pos, taps, 512, 2, 2, fp16tc=True, autotune=True) as pl:
         assert pl.route() == "fp16_dft"
         t = pl.tuning()
