@@ -760,8 +760,7 @@ moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long l
             ga.bimg_off = pl->d_gt_bimg_off;
             ga.bimg = pl->d_gt_bimg;
             ga.G = pl->d_G;
-            ga.slab_t = 1;     // channel-major slabs [Cb][Tb]: a CTA's samples of one channel are contiguous
-            ga.slab_c = pl->Tb;
+            ga.Tb = pl->Tb;
             ga.err = pl->d_err;
             TimedLaunch tg(pl, 1);
             MOFF_CK(launch_grid_tc(ga, pl->gt_map_re, pl->gt_map_im, pl->gt_tiles, std::min(pl->gt_cgroups, nc),
@@ -769,6 +768,7 @@ moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long l
             tg.done();
             RowDftArgs ra{};
             ra.G = pl->d_G;
+            ra.Tb = pl->Tb;
             ra.H = reinterpret_cast<__half *>(pl->d_H);
             ra.slab_t = 1;
             ra.slab_c = pl->Tb;

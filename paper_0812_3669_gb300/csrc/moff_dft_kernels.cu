@@ -296,14 +296,12 @@ struct RowDftShape {
     static constexpr int M2 = 16 * F, T2 = M2 / 128;    // stage-2 rows (f, c)
     static constexpr int LBO2 = (M2 / 8) * 128;
     static constexpr int A2B = M2 * S::K2 * 2;
-    static constexpr int SLD = N + 8;                   // staging row (halves)
-    static constexpr int STB = F * 2 * SLD * 2;
     static constexpr int D1 = T1 * S::C1, D2 = T2 * S::C2;
     static constexpr int TC_ = D1 + D2;
     static constexpr int TCOLS = TC_ <= 32 ? 32 : (TC_ <= 64 ? 64 : (TC_ <= 128 ? 128 : (TC_ <= 256 ? 256 : 512)));
     static constexpr int NPIECE = F * 16 * 2 * (N2 / 8);   // (f, a, re/im, b8)
     static constexpr int ITER = NPIECE / kBlock;
-    static constexpr size_t SMEM = 16 + 2 * (size_t)A1B + A2B + STB + S::TAB_BYTES + 32;
+    static constexpr size_t SMEM = 16 + 2 * (size_t)A1B + A2B + S::TAB_BYTES + 32;
     static_assert(M1 % 128 == 0 && M2 % 128 == 0 && NPIECE % kBlock == 0 && ITER <= 32, "row-transform shape");
 };
 
@@ -324,8 +322,7 @@ __global__ void __launch_bounds__(kBlock) k_rows_dft(const RowDftArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *sA1 = smem;                                   // [2][A1B]
     unsigned char *sA2 = sA1 + 2 * RD::A1B;
-    __half *stage = reinterpret_cast<__half *>(sA2 + RD::A2B);
-    unsigned char *sTab = sA2 + RD::A2B + RD::STB;
+    unsigned char *sTab = sA2 + RD::A2B;
     const unsigned char *sB1 = sTab, *sB2 = sTab + S::B1_BYTES;
     const float2 *sTw = reinterpret_cast<const float2 *>(sB2 + S::B2_BYTES);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sTab + S::TAB_BYTES);
@@ -352,7 +349,7 @@ __global__ void __launch_bounds__(kBlock) k_rows_dft(const RowDftArgs a) {
         const int k = 2 * aa + ri;
         return (uint32_t)((f * (N2 / 8) + b8) * 128 + (k >> 3) * RD::LBO1 + (k & 7) * 16);
     };
-    const int ty = ry0 >> 3, nty = N / 8;
+    const int ty = ry0 >> 3, nty = N / 8;   // the stripe lies in one tile row (RS <= 8, aligned)
     uint32_t act = 0;
 #pragma unroll
     for (int k = 0; k < RD::ITER; ++k) {
@@ -373,11 +370,14 @@ __global__ void __launch_bounds__(kBlock) k_rows_dft(const RowDftArgs a) {
     const uint32_t tbase = *tslot;
     const float sc = 1.0f / (float)N2;
 
-    auto row_base = [&](const __half *base, int tt, int f) -> long long {
+    // output row f of sample tt: [re N][im N] halves
+    auto row_base = [&](int tt, int f) -> long long {
         const int p = f / RS, rl = f - p * RS;
         return (((long long)tt * a.slab_t + (long long)cl * a.slab_c) * P + p) * N * 2 * N +
                (long long)(ry0 + rl) * 2 * N;
     };
+    // input piece: the tile-major field, [channel][pol][tile row][tile col][sample][cy][re/im][cx]
+    const long long tstride = (long long)a.Tb * 128;
     auto load = [&](int tt, int buf) {
         unsigned char *dst = sA1 + buf * RD::A1B;
 #pragma unroll
@@ -385,7 +385,10 @@ __global__ void __launch_bounds__(kBlock) k_rows_dft(const RowDftArgs a) {
             if ((act >> k) & 1u) {
                 int f, aa, ri, b8;
                 piece(tid + k * kBlock, f, aa, ri, b8);
-                cp_async16(dst + piece_dst(f, aa, ri, b8), a.G + row_base(a.G, tt, f) + ri * N + N2 * aa + 8 * b8);
+                const int p = f / RS, ry = ry0 + (f - p * RS), tx = (N2 * aa + 8 * b8) >> 3;
+                const __half *src = a.G + ((((long long)cl * P + p) * nty + ty) * nty + tx) * tstride +
+                                    (long long)tt * 128 + ((ry & 7) * 2 + ri) * 8;
+                cp_async16(dst + piece_dst(f, aa, ri, b8), src);
             }
         }
         cp_async_commit();
@@ -443,29 +446,23 @@ __global__ void __launch_bounds__(kBlock) k_rows_dft(const RowDftArgs a) {
             }
         }
     };
-    // stage-2 accumulators -> FP16 (x 1/N2) staging rows [f][re/im][SLD], then 16-byte stores
+    // stage-2 accumulators -> FP16 (x 1/N2) rows: lane (f, c) holds k = c + 16 d; even lanes store
+    // the real parts of (c, c + 1), odd lanes the imaginary parts (pairs swapped by one shuffle)
     auto epi2 = [&](int tt) {
         constexpr int NCB = C2 / 32;
         for (int u = warp >> 2; u < RD::T2 * NCB; u += kBlock / 128) {
             const int j = u / NCB, cb2 = u - j * NCB;
             const int m2 = 128 * j + 32 * q + lane;
-            const int f = m2 >> 4, cc = m2 & 15;
+            const int f = m2 >> 4, cc = m2 & 15, odd = cc & 1;
             float v[32];
             tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(RD::D1 + j * C2 + 32 * cb2), v);
-            __half *sr = stage + (2 * f) * RD::SLD + cc + 16 * 16 * cb2;
+            __half *row = a.H + row_base(tt, f) + (odd ? N : 0) + (cc & ~1) + 16 * 16 * cb2;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                sr[16 * i] = __float2half_rn(v[2 * i] * sc);
-                sr[RD::SLD + 16 * i] = __float2half_rn(v[2 * i + 1] * sc);
+                const float re = v[2 * i] * sc, im = v[2 * i + 1] * sc;
+                const float re_o = __shfl_xor_sync(0xffffffffu, re, 1), im_o = __shfl_xor_sync(0xffffffffu, im, 1);
+                *reinterpret_cast<__half2 *>(row + 16 * i) = odd ? __floats2half2_rn(im_o, im) : __floats2half2_rn(re, re_o);
             }
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        constexpr int PR = N / 8;
-        for (int i = tid; i < F * 2 * PR; i += kBlock) {
-            const int rr = i / PR, pc = i - rr * PR;
-            *reinterpret_cast<uint4 *>(a.H + row_base(a.H, tt, rr >> 1) + (rr & 1) * N + 8 * pc) =
-                *reinterpret_cast<const uint4 *>(stage + rr * RD::SLD + 8 * pc);
         }
     };
 

@@ -175,7 +175,11 @@ __global__ void __launch_bounds__(kGtThreads, 1)
             tc::fence_after_sync();
             const int cl = cb + i / ntb, t = (i % ntb) * 128 + q4 * 32 + lane;
             const uint32_t dcol = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * NT);
-            __half *gs = a.G + (((long long)t * a.slab_t + (long long)cl * a.slab_c) * P) * a.N * 2 * a.N;
+            // tile-major field: [channel][pol][tile row][tile col][sample][cy][re/im][cx], 256 bytes per
+            // (pol, tile, sample), so a warp's 32 samples write 8 KB in one run
+            const int nty = a.N >> 3;
+            const long long tstride = (long long)a.Tb * 128;               // halves per (pol, tile)
+            __half *gs = a.G + (((long long)cl * P * nty + ty) * nty + tx) * tstride + (long long)t * 128;
             constexpr int NLD = NT / 2 / 32;              // 32-column loads per warp
 #pragma unroll 1
             for (int l = 0; l < NLD; ++l) {
@@ -190,11 +194,11 @@ __global__ void __launch_bounds__(kGtThreads, 1)
 #pragma unroll
                     for (int pc = 0; pc < 4; ++pc) {
                         const int grp = (c0 >> 3) + pc;   // (p 8 + cy) 2 + re/im
-                        const int ri = grp & 1, pr = grp >> 1, p = pr >> 3, cy = pr & 7;
+                        const int pr = grp >> 1, p = pr >> 3;
                         __half2 h[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) h[u] = __floats2half2_rn(v[8 * pc + 2 * u], v[8 * pc + 2 * u + 1]);
-                        __half *dst = gs + ((long long)(p * a.N + 8 * ty + cy) * 2 + ri) * a.N + 8 * tx;
+                        __half *dst = gs + (long long)p * nty * nty * tstride + (grp & 15) * 8;   // (cy 2 + re/im) 8 halves
                         *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
                     }
                 }

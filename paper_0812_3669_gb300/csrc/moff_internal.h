@@ -81,8 +81,10 @@ struct ColDftArgs {
 
 // Dense tensor-core row transform of a gridded field in global memory (k_rows_dft).
 struct RowDftArgs {
-    const __half *G;          // FP16 gridded rows [re N][im N]; slab [P][N] at t * slab_t + cl * slab_c
-    __half *H;                // FP16 row-transformed rows, same layout; the value carries 1/N more
+    const __half *G;          // FP16 gridded field, tile-major [Cb][P][N/8][N/8][Tb][8 cy][re/im][8 cx]
+    int Tb;
+    __half *H;                // FP16 row-transformed rows [re N][im N]; slab [P][N] at t * slab_t + cl * slab_c;
+                              // the value carries 1/N more than the field
     long long slab_t, slab_c;
     int nt, c0, nc;
     const uint32_t *row_nz;   // stripes with no reached row are skipped
@@ -102,8 +104,8 @@ struct GridTcArgs {
     const int *chunk_row;      // first plane row (within a channel) of each chunk
     const long long *bimg_off; // [tiles] byte offset of each tile's B image [2 P 64][kp] K-major
     const __half *bimg;
-    __half *G;                 // FP16 gridded rows [re N][im N]; slab [P][N] at t * slab_t + cl * slab_c
-    long long slab_t, slab_c;
+    __half *G;                 // FP16 gridded field, tile-major: [Cb][P][N/8][N/8][Tb][8 cy][re/im][8 cx]
+    int Tb;                    // samples per (pol, tile) block of G
     int *err;
 };
 struct GridTc {

@@ -137,6 +137,46 @@ __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ v
     }
 }
 
+// Large arrays (a channel's voltage bytes of eight samples exceed the staging budget): one
+// thread per plane row and 32 samples.  Consecutive plane rows that hold consecutive
+// voltages read consecutive bytes of each sample; each thread writes its row's 32 samples as
+// four 16-byte pieces per plane.
+__global__ void __launch_bounds__(256) k_volt_prep_rows(const uint8_t *__restrict__ volt, long long tstride, int t0,
+                                                        int nt, int c0, int AP, int APpad, int n_rows,
+                                                        const float2 *__restrict__ gains, const float *__restrict__ sy,
+                                                        const int *__restrict__ perm, int Tpad,
+                                                        __half *__restrict__ yre, __half *__restrict__ yim) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tb = blockIdx.y * 32;
+    const int cl = blockIdx.z, c = c0 + cl;
+    if (v >= APpad) return;
+    uint32_t re[16], im[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
+    if (v < n_rows) {
+        const int sv = perm[v];
+        const float2 g = gains[(long long)c * AP + sv];
+        const float s = sy[c];
+        const uint8_t *src = volt + (long long)(t0 + tb) * tstride + (long long)c * AP + sv;
+        uint32_t b[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) b[t] = tb + t < nt ? (uint32_t)__ldg(src + (long long)t * tstride) : 0u;
+#pragma unroll
+        for (int t = 0; t < 32; t += 2) {
+            const float2 y0 = cmul(g, decode4_tc(b[t])), y1 = cmul(g, decode4_tc(b[t + 1]));
+            const __half2 hr = __floats2half2_rn(y0.x * s, y1.x * s), hi = __floats2half2_rn(y0.y * s, y1.y * s);
+            re[t >> 1] = *reinterpret_cast<const uint32_t *>(&hr);
+            im[t >> 1] = *reinterpret_cast<const uint32_t *>(&hi);
+        }
+    }
+    uint4 *ore = reinterpret_cast<uint4 *>(yre + ((long long)cl * APpad + v) * Tpad + tb);
+    uint4 *oim = reinterpret_cast<uint4 *>(yim + ((long long)cl * APpad + v) * Tpad + tb);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        ore[k] = make_uint4(re[4 * k], re[4 * k + 1], re[4 * k + 2], re[4 * k + 3]);
+        oim[k] = make_uint4(im[4 * k], im[4 * k + 1], im[4 * k + 2], im[4 * k + 3]);
+    }
+}
 
 template <int N>
 struct TcShape {
@@ -383,6 +423,13 @@ cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int
                              __half *yim, cudaStream_t st, int n_rows) {
     // samples per CTA: 32, or fewer (even, dividing Tpad) so the staged bytes stay within 96 KB
     const size_t APr = (size_t)((AP + 15) & ~15);
+    const int rows = n_rows < 0 ? AP : n_rows;
+    if (8 * APr > 96 * 1024 && Tpad % 32 == 0) {   // too large to stage 8 samples: one thread per plane row
+        dim3 grid((APpad + 255) / 256, Tpad / 32, nc);
+        k_volt_prep_rows<<<grid, 256, 0, st>>>(volt, tstride, t0, nt, c0, AP, APpad, rows, gains, sy, perm, Tpad, yre,
+                                               yim);
+        return cudaGetLastError();
+    }
     int TT = 32;
     while (TT > 2 && (TT * APr > 96 * 1024 || Tpad % TT)) TT /= 2;
     if (Tpad % TT || TT * APr > 200 * 1024) return cudaErrorInvalidValue;
@@ -391,7 +438,7 @@ cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int
     if (e != cudaSuccess) return e;
     dim3 grid(Tpad / TT, nc);
     k_volt_prep<<<grid, 256, smem, st>>>(volt, tstride, t0, nt, c0, AP, APpad, gains, sy, perm, Tpad, TT, yre, yim,
-                                         n_rows < 0 ? AP : n_rows);
+                                         rows);
     return cudaGetLastError();
 }
 
