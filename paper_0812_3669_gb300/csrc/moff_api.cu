@@ -278,7 +278,7 @@ struct moff_plan {
     long long *d_gt_bimg_off = nullptr;
     __half *d_gt_bimg = nullptr;
     unsigned char *d_gt_active = nullptr;
-    CUtensorMap gt_map_re{}, gt_map_im{};
+    CUtensorMap gt_map_re{}, gt_map_im{}, gt_map_g{};
     __half *d_G = nullptr;
 
     long long n_samples = 0;
@@ -763,8 +763,8 @@ moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long l
             ga.Tb = pl->Tb;
             ga.err = pl->d_err;
             TimedLaunch tg(pl, 1);
-            MOFF_CK(launch_grid_tc(ga, pl->gt_map_re, pl->gt_map_im, pl->gt_tiles, std::min(pl->gt_cgroups, nc),
-                                   pl->gt_smem, pl->st));
+            MOFF_CK(launch_grid_tc(ga, pl->gt_map_re, pl->gt_map_im, pl->gt_map_g, pl->gt_tiles,
+                                   std::min(pl->gt_cgroups, nc), pl->gt_smem, pl->st));
             tg.done();
             RowDftArgs ra{};
             ra.G = pl->d_G;
@@ -1854,6 +1854,8 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
         if (encode_plane_map(&pl->gt_map_re, pl->d_yre, pl->Tb, rows, 16) != cudaSuccess ||
             encode_plane_map(&pl->gt_map_im, pl->d_yim, pl->Tb, rows, 16) != cudaSuccess)
             return fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded");
+        if (encode_gridtc_store_map(&pl->gt_map_g, pl->d_G, (long long)(pl->h_bytes / 256)) != cudaSuccess)
+            return fail(MOFF_ECUDA, "tensor map of the gridded field could not be encoded");
     }
     if (pl->tc && !pl->dft) {
         pl->d_yre = reinterpret_cast<__half *>(base + off);
@@ -2051,6 +2053,8 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
                 if (encode_plane_map(&pl->gt_map_re, pl->d_yre, pl->Tb, rows, 16) != cudaSuccess ||
                     encode_plane_map(&pl->gt_map_im, pl->d_yim, pl->Tb, rows, 16) != cudaSuccess)
                     return bail(fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded"));
+                if (encode_gridtc_store_map(&pl->gt_map_g, pl->d_G, (long long)(pl->h_bytes / 256)) != cudaSuccess)
+                    return bail(fail(MOFF_ECUDA, "tensor map of the gridded field could not be encoded"));
             }
             if (pl->tc && !pl->dft && encode_field_map(&pl->h_map, pl->d_H, grid_n, n_pol, pl->Cb, pl->Tb) != cudaSuccess)
                 return bail(fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded"));

@@ -91,21 +91,32 @@ __global__ void __launch_bounds__(kBlock, 1) k_cols_dft(const ColDftArgs a) {
         tc::tmem_alloc(tslot, CS::TCOLS);
         tc::tmem_relinquish();
     }
-    // Piece i = tid + k kBlock of a sample: pol p, row ry, re/im ri, column half h.  Rows no
-    // kernel reaches are zero: cleared once in both buffers and never loaded.
-    auto piece_dst = [&](int i) -> uint32_t {
-        const int p = i / (4 * N), r = i - p * 4 * N, ry = r >> 2, ri = (r >> 1) & 1, h = r & 1;
-        const int aa = ry / N2, b = ry - aa * N2, k = 2 * aa + ri;
-        return (uint32_t)(p * CS::A1P + (2 * b + h) * 128 + (k >> 3) * CS::LBO1 + (k & 7) * 16);
+    // Piece i = k kBlock + tid of a sample: pol p, row ry, re/im ri, column half h (i = ((p N + ry) 2
+    // + ri) 2 + h).  With kBlock a divisor of 4N, k fixes p and ry's multiple of 64 (PK, RYK below,
+    // compile-time) and the thread fixes ry mod 64 = r0, ri and h: every offset is a thread
+    // constant plus a compile-time one.  Rows no kernel reaches are zero: cleared once in both
+    // buffers and never loaded.
+    static_assert((4 * N) % kBlock == 0 && kBlock / 4 == 64 && N2 <= 64, "piece enumeration");
+    const int r0 = tid >> 2, ri0 = (tid >> 1) & 1, h0 = tid & 1;
+    const int a0 = r0 / N2, b0 = r0 - a0 * N2;
+    const uint32_t dst_t = (uint32_t)((2 * b0 + h0) * 128 + (2 * a0 + ri0) * 16);
+    const long long src_t = (long long)(2 * r0 + ri0) * N + x0 + 8 * h0;
+    auto piece_dst = [&](int k) -> uint32_t {      // k compile-time after unrolling
+        const int PK = (k * kBlock) / (4 * N), RYK = ((k * kBlock) % (4 * N)) >> 2, AK = RYK / N2;
+        return (uint32_t)(PK * CS::A1P + ((2 * AK) >> 3) * CS::LBO1 + ((2 * AK) & 7) * 16) + dst_t;
+    };
+    auto piece_src = [&](int k) -> long long {
+        const int PK = (k * kBlock) / (4 * N), RYK = ((k * kBlock) % (4 * N)) >> 2;
+        return (long long)(PK * N + RYK) * 2 * N + src_t;
     };
     uint32_t act = 0;
 #pragma unroll
     for (int k = 0; k < CS::ITER; ++k) {
-        const int i = tid + k * kBlock, ry = (i % (4 * N)) >> 2;
+        const int ry = (((k * kBlock) % (4 * N)) >> 2) + r0;
         if ((a.row_nz[ry >> 5] >> (ry & 31)) & 1u) {
             act |= 1u << k;
         } else {
-            const uint32_t d = piece_dst(i);
+            const uint32_t d = piece_dst(k);
             *reinterpret_cast<uint4 *>(sA1 + d) = make_uint4(0u, 0u, 0u, 0u);
             *reinterpret_cast<uint4 *>(sA1 + P * CS::A1P + d) = make_uint4(0u, 0u, 0u, 0u);
         }
@@ -116,16 +127,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_cols_dft(const ColDftArgs a) {
     const uint32_t tbase = *tslot;
 
     auto stage = [&](int tt, int buf) {
-        const __half *src = a.H + ((long long)tt * a.slab_t + (long long)cl * a.slab_c) * P * N * 2 * N + x0;
+        const __half *src = a.H + ((long long)tt * a.slab_t + (long long)cl * a.slab_c) * P * N * 2 * N;
         unsigned char *dst = sA1 + buf * P * CS::A1P;
 #pragma unroll
-        for (int k = 0; k < CS::ITER; ++k) {
-            if ((act >> k) & 1u) {
-                const int i = tid + k * kBlock;
-                const int p = i / (4 * N), r = i - p * 4 * N, ry = r >> 2, ri = (r >> 1) & 1, h = r & 1;
-                cp_async16(dst + piece_dst(i), src + ((long long)(p * N + ry) * 2 + ri) * N + 8 * h);
-            }
-        }
+        for (int k = 0; k < CS::ITER; ++k)
+            if ((act >> k) & 1u) cp_async16(dst + piece_dst(k), src + piece_src(k));
         cp_async_commit();
     };
     auto issue_s1 = [&](int buf) {
@@ -201,20 +207,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_cols_dft(const ColDftArgs a) {
         for (int d = 0; d < N2; ++d) acc[pq][d] = 0.f;
     auto epi2 = [&]() {
 #pragma unroll
-        for (int db = 0; db < N2 / 16; ++db) {
-            float ex[32];
-            tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(CS::D1 + j2 * C2 + 32 * db), ex);
+        for (int db = 0; db < N2 / 8; ++db) {         // 8 d per TMEM load of each pol
+            float ex[16];
+            tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(CS::D1 + j2 * C2 + 16 * db), ex);
             if constexpr (P == 1) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    acc[0][16 * db + i] = fmaf(ex[2 * i], ex[2 * i], fmaf(ex[2 * i + 1], ex[2 * i + 1], acc[0][16 * db + i]));
+                for (int i = 0; i < 8; ++i)
+                    acc[0][8 * db + i] = fmaf(ex[2 * i], ex[2 * i], fmaf(ex[2 * i + 1], ex[2 * i + 1], acc[0][8 * db + i]));
             } else {
-                float ey[32];
-                tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(CS::D1 + (CS::T2 + j2) * C2 + 32 * db), ey);
+                float ey[16];
+                tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(CS::D1 + (CS::T2 + j2) * C2 + 16 * db), ey);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
+                for (int i = 0; i < 8; ++i) {
                     const float xr = ex[2 * i], xi = ex[2 * i + 1], yr = ey[2 * i], yi = ey[2 * i + 1];
-                    const int d = 16 * db + i;
+                    const int d = 8 * db + i;
                     acc[0][d] = fmaf(xr, xr, fmaf(xi, xi, acc[0][d]));
                     acc[1][d] = fmaf(yr, yr, fmaf(yi, yi, acc[1][d]));
                     acc[2][d] = fmaf(xr, yr, fmaf(xi, yi, acc[2][d]));
@@ -337,13 +343,16 @@ __global__ void __launch_bounds__(kBlock) k_rows_dft(const RowDftArgs a) {
         tc::tmem_alloc(tslot, RD::TCOLS);
         tc::tmem_relinquish();
     }
-    auto piece = [&](int i, int &f, int &aa, int &ri, int &b8) {
-        b8 = i % (N2 / 8);
-        int r = i / (N2 / 8);
-        ri = r & 1;
-        r >>= 1;
-        aa = r & 15;
-        f = r >> 4;
+    // Piece i = k kBlock + tid = ((f 16 + aa) 2 + ri) (N2/8) + b8: with 32 (N2/8) a divisor of
+    // kBlock, k fixes f's high part (FK, compile-time) and the thread fixes (f mod FPK, aa, ri, b8).
+    constexpr int B8N = N2 / 8, FPK = kBlock / (32 * B8N);   // rows f per k step
+    static_assert(kBlock % (32 * B8N) == 0, "piece enumeration");
+    const int b8_0 = tid % B8N, ri_0 = (tid / B8N) & 1, aa_0 = (tid / (2 * B8N)) & 15, f_0 = tid / (32 * B8N);
+    auto piece = [&](int k, int &f, int &aa, int &ri, int &b8) {
+        f = k * FPK + f_0;
+        aa = aa_0;
+        ri = ri_0;
+        b8 = b8_0;
     };
     auto piece_dst = [&](int f, int aa, int ri, int b8) -> uint32_t {
         const int k = 2 * aa + ri;
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(kBlock) k_rows_dft(const RowDftArgs a) {
 #pragma unroll
     for (int k = 0; k < RD::ITER; ++k) {
         int f, aa, ri, b8;
-        piece(tid + k * kBlock, f, aa, ri, b8);
+        piece(k, f, aa, ri, b8);
         const int tx = (N2 * aa + 8 * b8) >> 3;
         if (a.active[ty * nty + tx]) {
             act |= 1u << k;
@@ -384,7 +393,7 @@ __global__ void __launch_bounds__(kBlock) k_rows_dft(const RowDftArgs a) {
         for (int k = 0; k < RD::ITER; ++k) {
             if ((act >> k) & 1u) {
                 int f, aa, ri, b8;
-                piece(tid + k * kBlock, f, aa, ri, b8);
+                piece(k, f, aa, ri, b8);
                 const int p = f / RS, ry = ry0 + (f - p * RS), tx = (N2 * aa + 8 * b8) >> 3;
                 const __half *src = a.G + ((((long long)cl * P + p) * nty + ty) * nty + tx) * tstride +
                                     (long long)tt * 128 + ((ry & 7) * 2 + ri) * 8;

@@ -41,11 +41,12 @@ constexpr int kGtChunkK = 2 * kGtChunkRows;              // contraction per chun
 constexpr int kGtStageBytes = 128 * kGtChunkK * 2;       // 128 samples x 32 k, FP16
 constexpr int kGtHalfBytes = kGtStageBytes / 2;          // one 64-sample half: 32 k-rows x 128 bytes
 constexpr long long kGtWaitCycles = 200000000LL;         // ~0.1 s at the SM clock
+constexpr int kGtBoxBytes = 32 * 128;                    // epilogue box: 32 samples x 64 halves, 128-byte swizzle
 
 template <int P>
 __global__ void __launch_bounds__(kGtThreads, 1)
     k_grid_tc(const GridTcArgs a, const __grid_constant__ CUtensorMap amap_re,
-              const __grid_constant__ CUtensorMap amap_im) {
+              const __grid_constant__ CUtensorMap amap_im, const __grid_constant__ CUtensorMap gmap) {
     constexpr int NT = 128 * P;                           // output columns (p, cy, re/im, cx)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int item = blockIdx.x;
@@ -66,7 +67,8 @@ __global__ void __launch_bounds__(kGtThreads, 1)
     const size_t bbytes = ((size_t)NT * a.kp_max * 2 + 1023) & ~(size_t)1023;
     unsigned char *sB = smem;                                  // NT x kp, K-major (resident)
     unsigned char *sA = sB + bbytes;                           // kGtStages x [128 x 32], 1024-aligned
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + kGtStages * kGtStageBytes);
+    unsigned char *sE = sA + kGtStages * kGtStageBytes;        // one epilogue box per warp, 1024-aligned
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sE + kGtEpiWarps * kGtBoxBytes);
     uint64_t *a_full = bars, *a_empty = bars + kGtStages, *d_full = bars + 2 * kGtStages,
              *d_empty = bars + 2 * kGtStages + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kGtStages + 4);
@@ -167,43 +169,58 @@ __global__ void __launch_bounds__(kGtThreads, 1)
     } else {
         // ---------------- epilogue warps 0-7: TMEM lanes 32 (w % 4) .. + 31 = samples; warp w / 4
         // drains half of the columns.  Column n = ((p 8 + cy) 2 + re/im) 8 + cx: every 8 columns are
-        // one 16-byte piece of a field row.
+        // one 16-byte piece (cy, re/im) of a sample's 256-byte row of the tile-major field
+        // [channel][pol][tile row][tile col][sample][cy][re/im][cx]; 8 pieces of 32 samples make one
+        // box (32 rows x 128 bytes, 128-byte swizzle) that one lane hands to the TMA unit.
         const int q4 = warp & 3, hc = warp >> 2;
+        const int nty = a.N >> 3;
+        unsigned char *box = sE + warp * kGtBoxBytes;
+        int nbox = 0;
         for (int i = 0; i < nitems; ++i) {
             const int b = i & 1;
             if (!tc::mbar_wait_abortable(&d_full[b], (uint32_t)((i >> 1) & 1), kGtWaitCycles, abort_flag)) break;
             tc::fence_after_sync();
-            const int cl = cb + i / ntb, t = (i % ntb) * 128 + q4 * 32 + lane;
+            const int cl = cb + i / ntb, t0w = (i % ntb) * 128 + q4 * 32;
             const uint32_t dcol = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * NT);
-            // tile-major field: [channel][pol][tile row][tile col][sample][cy][re/im][cx], 256 bytes per
-            // (pol, tile, sample), so a warp's 32 samples write 8 KB in one run
-            const int nty = a.N >> 3;
-            const long long tstride = (long long)a.Tb * 128;               // halves per (pol, tile)
-            __half *gs = a.G + (((long long)cl * P * nty + ty) * nty + tx) * tstride + (long long)t * 128;
-            constexpr int NLD = NT / 2 / 32;              // 32-column loads per warp
+            constexpr int NBX = NT / 2 / 64;              // boxes (64 columns each) per warp
 #pragma unroll 1
-            for (int l = 0; l < NLD; ++l) {
-                const int c0 = hc * (NT / 2) + 32 * l;
-                float v[32];
+            for (int bx = 0; bx < NBX; ++bx) {
+                const int c0 = hc * (NT / 2) + 64 * bx;   // first column: piece c0 / 8
+                float v[32], w[32];
                 tc::tmem_ld32(dcol + (uint32_t)c0, v);
-                if (l == NLD - 1) {                       // the item's last TMEM read: the accumulator is free
+                tc::tmem_ld32(dcol + (uint32_t)(c0 + 32), w);
+                if (bx == NBX - 1) {                      // the item's last TMEM read: the accumulator is free
                     tc::fence_before_sync();
                     tc::mbar_arrive(&d_empty[b]);
                 }
-                if (t < a.nt) {
+                uint4 pk[8];
 #pragma unroll
-                    for (int pc = 0; pc < 4; ++pc) {
-                        const int grp = (c0 >> 3) + pc;   // (p 8 + cy) 2 + re/im
-                        const int pr = grp >> 1, p = pr >> 3;
-                        __half2 h[4];
+                for (int pc = 0; pc < 8; ++pc) {
+                    const float *x = pc < 4 ? v + 8 * pc : w + 8 * (pc - 4);
+                    __half2 h[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) h[u] = __floats2half2_rn(v[8 * pc + 2 * u], v[8 * pc + 2 * u + 1]);
-                        __half *dst = gs + (long long)p * nty * nty * tstride + (grp & 15) * 8;   // (cy 2 + re/im) 8 halves
-                        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
-                    }
+                    for (int u = 0; u < 4; ++u) h[u] = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
+                    pk[pc] = *reinterpret_cast<const uint4 *>(h);
                 }
+                if (nbox > 0) {                           // the store that last read this box is done with it
+                    if (lane == 0) tc::bulk_wait_read<0>();
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int pc = 0; pc < 8; ++pc)
+                    *reinterpret_cast<uint4 *>(box + lane * 128 + ((pc ^ (lane & 7)) << 4)) = pk[pc];
+                tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    const int grp0 = c0 >> 3, p = grp0 >> 4;   // 16 pieces per pol
+                    const long long row = (((long long)(cl * P + p) * nty + ty) * nty + tx) * a.Tb + t0w;
+                    tc::tma_store_2d(&gmap, tc::smem_u32(box), (grp0 & 15) * 8, (int)row);
+                    tc::bulk_commit();
+                }
+                ++nbox;
             }
         }
+        if (lane == 0) tc::bulk_wait_all();
     }
     if (*abort_flag && tid == 0) atomicExch(a.err, tc::kErrWaitTimeout);
     tc::fence_before_sync();
@@ -234,7 +251,28 @@ size_t kmajor_byte(int n, int k, int K) {
 size_t gridtc_smem_bytes(int P, int kp_max) {
     const int NT = 128 * P;
     return 1024 + (((size_t)NT * kp_max * 2 + 1023) & ~(size_t)1023) + (size_t)kGtStages * kGtStageBytes +
-           (size_t)(2 * kGtStages + 4) * 8 + 16;
+           (size_t)kGtEpiWarps * kGtBoxBytes + (size_t)(2 * kGtStages + 4) * 8 + 16;
+}
+
+// Store map of the tile-major gridded field as rows of 128 halves (one sample of one (pol, tile)):
+// box 64 halves x 32 rows, 128-byte swizzle.
+cudaError_t encode_gridtc_store_map(CUtensorMap *map, void *G, long long rows) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const cuuint64_t dims[2] = {128, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {256};
+    const cuuint32_t box[2] = {64, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, G, dims, strides, box, estr,
+                                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // Tile tables of an array (host side, FP64 values rounded once to FP16 after the scale).
@@ -361,12 +399,12 @@ moff_status build_gridtc(int A, int K, int N, int P, bool jones, const double *p
     return MOFF_OK;
 }
 
-cudaError_t launch_grid_tc(const GridTcArgs &a, const CUtensorMap &are, const CUtensorMap &aim, int n_tiles,
-                           int cgroups, size_t smem, cudaStream_t st) {
+cudaError_t launch_grid_tc(const GridTcArgs &a, const CUtensorMap &are, const CUtensorMap &aim, const CUtensorMap &gmap,
+                           int n_tiles, int cgroups, size_t smem, cudaStream_t st) {
     auto k = a.P == 1 ? k_grid_tc<1> : k_grid_tc<2>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<dim3(n_tiles, cgroups), kGtThreads, smem, st>>>(a, are, aim);
+    k<<<dim3(n_tiles, cgroups), kGtThreads, smem, st>>>(a, are, aim, gmap);
     return cudaGetLastError();
 }
 

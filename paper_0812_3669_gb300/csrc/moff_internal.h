@@ -121,8 +121,10 @@ struct GridTc {
 moff_status build_gridtc(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, float scale,
                          GridTc *gt);
 size_t gridtc_smem_bytes(int P, int kp_max);
-cudaError_t launch_grid_tc(const GridTcArgs &a, const CUtensorMap &are, const CUtensorMap &aim, int n_tiles,
-                           int cgroups, size_t smem, cudaStream_t st);
+cudaError_t launch_grid_tc(const GridTcArgs &a, const CUtensorMap &are, const CUtensorMap &aim, const CUtensorMap &gmap,
+                           int n_tiles, int cgroups, size_t smem, cudaStream_t st);
+// Store map of the tile-major gridded field (rows of 128 halves; box 64 x 32, 128-byte swizzle).
+cudaError_t encode_gridtc_store_map(CUtensorMap *map, void *G, long long rows);
 cudaError_t launch_rows_dft(int N, int P, const RowDftArgs &a, cudaStream_t st);
 
 // Column transform + square-and-integrate (Eq. m6 steps 3-4, second axis).
