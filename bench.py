@@ -8,8 +8,8 @@ jitter; 512 x 256 cells, so x wraps the 512 grid), full pol with per-antenna
 a non-coplanar w-phase), 4096 channels, 512 x 512 grid, integrations of 4000
 samples accumulated in FP64 across blocks.  It runs on the FP16 tensor-core
 path (the factored-DFT route: FP32 gridding, both transform axes as tcgen05
-contractions).  One step = one block of 32 samples of every channel =
-131,072 channel-snapshots; its 8.6 GB of voltages are far larger than L2, so
+contractions).  One step = one block of 128 samples of every channel =
+524,288 channel-snapshots; its 34 GB of voltages are far larger than L2, so
 no flush is needed between steps.
 
 Named legs: the same array on the FP32 path; the 16384-antenna filled-aperture
@@ -45,15 +45,15 @@ UNIT = "channel-snapshots/s"
 # Dense workloads: (synth config, sizes, block of samples per step, integration length).
 DENSE = {
     "widefield": dict(cfg="config_widefield", n_ant=32768, n_pol=2, n_chan=4096, grid_n=512, ksize=9, jones=True,
-                      block=32, t_int=4000, seed=8123669 + 4,
+                      block=128, t_int=4000, seed=8123669 + 4,
                       name="wide-field 32768-antenna 256x128-lambda lattice (1 lambda pitch, 5% jitter), 9x9 Jones "
                            "kernels with w-phase, full pol, 4096 channels, 512x512 grid, XX/YY/XY, 4000-sample "
-                           "integrations accumulated in FP64 across blocks of 32 samples (one step = one block)"),
+                           "integrations accumulated in FP64 across blocks of 128 samples (one step = one block)"),
     "precision": dict(cfg="config_precision", n_ant=16384, n_pol=2, n_chan=1024, grid_n=512, ksize=7, jones=False,
-                      block=64, t_int=2000, seed=8123669 + 2,
+                      block=128, t_int=2000, seed=8123669 + 2,
                       name="filled aperture 16384 antennas on a 128x128-lambda lattice (5% jitter), dual pol, 7x7 "
                            "kernels, 1024 channels, 512x512 grid (zero-padded x2), 2000-sample integrations in "
-                           "blocks of 64 samples"),
+                           "blocks of 128 samples"),
 }
 # The F-stage workload (the round's former headline, now a named leg).
 WL = dict(n_ant=1024, n_pol=2, n_chan=1024, grid_n=128, ksize=7, ntaps=8, frames=1000)
@@ -129,12 +129,26 @@ def reached_rows(pos, N, K):
     return int(r.sum())
 
 
+def active_tiles(pos, N, K):
+    """8 x 8-cell tiles some kernel footprint reaches (the tensor-core gridding writes those)."""
+    import numpy as np
+    h = K // 2
+    anc = np.floor(np.asarray(pos) + 0.5).astype(int) % N
+    t = np.zeros((N // 8, N // 8), bool)
+    for dy in range(-h, h + 1):
+        for dx in range(-h, h + 1):
+            t[((anc[:, 1] + dy) % N) // 8, ((anc[:, 0] + dx) % N) // 8] = True
+    return int(t.sum())
+
+
 def dense_work(route, pos, taps, N, P, Tb):
     """Method's work per channel-snapshot of each kernel kind of a route:
     {kind: {"alu": FP32 flops, "tensor": tensor flops, "bytes": DRAM bytes}}.
 
     Gridding: 8 flops per nonzero kernel tap (complex multiply-add, Jones taps
-    counted per (p_out, p_in)) + 6 per voltage weighting.  Transforms: FP32 path
+    counted per (p_out, p_in)) + 6 per voltage weighting (on the tensor-core
+    gridding route the taps' flops are its tensor work, the padded tile products
+    it executes are not counted).  Transforms: FP32 path
     5 N log2 N per N-point transform (radix-2 count); tensor-core path the
     factored DFT's real products, 8 N (16 + N/16) per N-point transform.  Only
     reached grid rows carry a row transform.  Bytes: the 4-bit voltages, the FP16
@@ -147,6 +161,13 @@ def dense_work(route, pos, taps, N, P, Tb):
     nprod = 1 if P == 1 else 4
     acc_b = 2 * nprod * N * N * 8 / max(Tb, 1)
     sq = (16 if P == 2 else 4) * N * N
+    if route == "fp16_tcgrid":
+        fac = 8 * N * (16 + N // 16)
+        T = active_tiles(pos, N, int(np.asarray(taps).shape[-1]))
+        return {"volt_prep": {"alu": 0, "tensor": 0, "bytes": A * P + A * P * 4},
+                "grid_rows": {"alu": 0, "tensor": 8 * nnz, "bytes": A * P * 4 + T * 64 * P * 4},
+                "row_transform": {"alu": 0, "tensor": R * P * fac, "bytes": T * 64 * P * 4 + R * P * N * 4},
+                "cols_integrate": {"alu": sq, "tensor": N * P * fac, "bytes": R * P * N * 4 + acc_b}}
     if route == "fp16_dft":
         fac = 8 * N * (16 + N // 16)
         return {"grid_rows": {"alu": 8 * nnz + 6 * A * P, "tensor": R * P * fac, "bytes": A * P + R * P * N * 4},
@@ -482,9 +503,14 @@ KERNEL_SOURCES = {
     "grid_rows_dft": [("paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "struct ColShape"),
                       "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
     "cols_dft": ["paper_0812_3669_gb300/csrc/moff_dft_kernels.cu", "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
+    "rows_dft": ["paper_0812_3669_gb300/csrc/moff_dft_kernels.cu", "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
+    "grid_tc": ["paper_0812_3669_gb300/csrc/moff_gridtc.cu", "paper_0812_3669_gb300/csrc/moff_tc.cuh"],
+    "volt_prep": ["paper_0812_3669_gb300/csrc/moff_tc_kernels.cu"],
 }
 # kernel kind (moff_timing) -> its name in KERNEL_SOURCES, per route
-ROUTE_KERNELS = {"fp16_dft": {"grid_rows": "grid_rows_dft", "cols_integrate": "cols_dft"}}
+ROUTE_KERNELS = {"fp16_dft": {"grid_rows": "grid_rows_dft", "cols_integrate": "cols_dft"},
+                 "fp16_tcgrid": {"grid_rows": "grid_tc", "row_transform": "rows_dft", "cols_integrate": "cols_dft",
+                                 "volt_prep": "volt_prep"}}
 
 
 def traffic_for(kernel_key, src):
@@ -993,6 +1019,7 @@ def dense_leg(args, ctx, wl_name, steps, warmup, fp16=True, headline=False, keep
     pos, taps = cfg["pos"], cfg["taps"]
     gains = synth.device_gains(wl["seed"] + 11, C, A, P)
     codes = synth.device_codes(wl["seed"] + 1000 * ctx.rank, B, C, A, P)
+    torch.cuda.empty_cache()                  # the draws' temporaries: the plan allocates outside torch's cache
     t0 = time.perf_counter()
     pl = moff.Plan(pos, taps, N, C, P, jones=wl["jones"], fp16tc=fp16)
     setup_s = time.perf_counter() - t0
@@ -1014,21 +1041,25 @@ def dense_leg(args, ctx, wl_name, steps, warmup, fp16=True, headline=False, keep
         _, n = pl.read_image(out=img)
         img /= float(n)
     if headline and not args.no_e2e and args.e2e_steps > 0:
-        out["e2e"] = dense_e2e(args, ctx, pl, codes, C, P, N, B)
+        host = torch.empty(codes.shape, dtype=torch.uint8, pin_memory=True)
+        host.copy_(codes)
+        del codes                             # the end-to-end steps stage the block from host memory
+        torch.cuda.empty_cache()
+        out["e2e"] = dense_e2e(args, ctx, pl, host, C, P, N, B)
+        del host
+        codes = None
     pl.close()
-    del codes
+    del codes, gains
     torch.cuda.empty_cache()
     return out, img, (pos, taps)
 
 
-def dense_e2e(args, ctx, pl, codes, C, P, N, B):
+def dense_e2e(args, ctx, pl, host, C, P, N, B):
     """End to end through the C ABI with host buffers: every step copies its block
     of 4-bit voltages from pinned host memory (moff_submit with a host pointer
     stages it on the plan's copy stream); the integration's image is read back to
     pinned host memory once at the end (its bytes shared over the steps)."""
     torch = ctx.torch
-    host = torch.empty(codes.shape, dtype=torch.uint8, pin_memory=True)
-    host.copy_(codes)
     nq = 4 if P == 2 else 1
     out_h = torch.empty((C, nq, N, N), dtype=torch.float32, pin_memory=True)
     for _ in range(2):                          # warm both staging buffers and the read-back

@@ -66,3 +66,21 @@ def test_dense_work_model():
     w32 = bench.dense_work("fp32", pos, taps, 256, 1, Tb=64)
     assert w32["grid_rows"]["alu"] == 8 * 17 + 6 * 2 + 4 * 5 * 256 * 8
     assert w32["cols_integrate"]["bytes"] == 4 * 256 * 8 + 2 * 256 * 256 * 8 / 64
+
+
+def test_tcgrid_work_model():
+    """The tensor-core gridding route's kernels: taps' flops for the gridding, the
+    factored DFT for both transform axes, the FP16 field written once and read once
+    between each pair of kernels."""
+    import numpy as np
+    pos = np.array([[5.0, 10.0], [7.0, 20.0]])           # anchors (5, 10), (7, 20); 3x3 kernels
+    taps = np.ones((2, 1, 3, 3), dtype=complex)
+    taps[1] = 0                                          # the second antenna contributes no taps ...
+    # ... but still reaches cells: rows 9-11 x columns 4-6 (tile (1, 0)); rows 19-21 x columns 6-8
+    # (tiles (2, 0) and (2, 1))
+    assert bench.active_tiles(pos, 256, 3) == 3
+    w = bench.dense_work("fp16_tcgrid", pos, taps, 256, 1, Tb=128)
+    fac = 8 * 256 * 32
+    assert w["grid_rows"]["tensor"] == 8 * 9
+    assert w["row_transform"]["tensor"] == 6 * fac and w["cols_integrate"]["tensor"] == 256 * fac
+    assert w["row_transform"]["bytes"] == 3 * 64 * 4 + 6 * 256 * 4
