@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kGtEpiWarps = 8;
 constexpr int kGtThreads = (kGtEpiWarps + 2) * 32;
-constexpr int kGtStages = 4;
+constexpr int kGtMaxStages = 8;                          // A ring depth: as many as shared memory allows, <= 8
 constexpr int kGtChunkRows = 16;                         // plane rows per chunk
 constexpr int kGtChunkK = 2 * kGtChunkRows;              // contraction per chunk (re rows, im rows)
 constexpr int kGtStageBytes = 128 * kGtChunkK * 2;       // 128 samples x 32 k, FP16
@@ -66,26 +66,22 @@ __global__ void __launch_bounds__(kGtThreads, 1)
     unsigned char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const size_t bbytes = ((size_t)NT * a.kp_max * 2 + 1023) & ~(size_t)1023;
     unsigned char *sB = smem;                                  // NT x kp, K-major (resident)
-    unsigned char *sA = sB + bbytes;                           // kGtStages x [128 x 32], 1024-aligned
-    unsigned char *sE = sA + kGtStages * kGtStageBytes;        // one epilogue box per warp, 1024-aligned
+    const int ns = a.stages;
+    unsigned char *sA = sB + bbytes;                           // ns x [128 x 32], 1024-aligned
+    unsigned char *sE = sA + ns * kGtStageBytes;               // one epilogue box per warp, 1024-aligned
     uint64_t *bars = reinterpret_cast<uint64_t *>(sE + kGtEpiWarps * kGtBoxBytes);
-    uint64_t *a_full = bars, *a_empty = bars + kGtStages, *d_full = bars + 2 * kGtStages,
-             *d_empty = bars + 2 * kGtStages + 2;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kGtStages + 4);
+    uint64_t *a_full = bars, *a_empty = bars + ns, *d_full = bars + 2 * ns, *d_empty = bars + 2 * ns + 2,
+             *b_full = bars + 2 * ns + 4;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * ns + 5);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const uint32_t bbytes_item = (uint32_t)(NT * kp * 2);
 
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const unsigned char *>(a.bimg) +
-                                                           a.bimg_off[item]);
-        uint4 *dst = reinterpret_cast<uint4 *>(sB);
-        const int n16 = NT * kp * 2 / 16;
-        for (int i = tid; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
-    }
     if (tid == 0) {
-        for (int s = 0; s < kGtStages; ++s) {
+        for (int s = 0; s < ns; ++s) {
             tc::mbar_init(&a_full[s], 1);
             tc::mbar_init(&a_empty[s], 1);
         }
+        tc::mbar_init(b_full, 1);
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&d_full[b], 1);
             tc::mbar_init(&d_empty[b], kGtEpiWarps * 32);
@@ -103,16 +99,20 @@ __global__ void __launch_bounds__(kGtThreads, 1)
     const uint32_t tbase = *tslot;
 
     if (warp == kGtEpiWarps) {
-        // ---------------- producer (one lane): chunk g into stage g % kGtStages, four TMA boxes
-        // (re / im rows x two 64-sample halves) completing on a_full
+        // ---------------- producer (one lane): the tile's kernel matrix B by one bulk copy
+        // (completing on b_full), then chunk g into stage g % ns, four TMA boxes (re / im rows x
+        // two 64-sample halves) completing on a_full
         if (lane == 0) {
+            tc::mbar_arrive_expect_tx(b_full, bbytes_item);
+            tc::bulk_load(tc::smem_u32(sB), reinterpret_cast<const unsigned char *>(a.bimg) + a.bimg_off[item],
+                          bbytes_item, b_full);
             int g = 0;
             for (int i = 0; i < nitems && !*abort_flag; ++i) {
                 const int cl = cb + i / ntb, t0b = (i % ntb) * 128;
                 bool ok = true;
                 for (int ch = 0; ch < nchunk; ++ch, ++g) {
-                    const int st = g % kGtStages;
-                    if (!tc::mbar_wait_abortable(&a_empty[st], (uint32_t)(((g / kGtStages) & 1) ^ 1), kGtWaitCycles,
+                    const int st = g % ns;
+                    if (!tc::mbar_wait_abortable(&a_empty[st], (uint32_t)(((g / ns) & 1) ^ 1), kGtWaitCycles,
                                                  abort_flag)) {
                         ok = false;
                         break;
@@ -129,8 +129,9 @@ __global__ void __launch_bounds__(kGtThreads, 1)
                 }
                 if (!ok) break;
             }
-            for (int gg = g - kGtStages > 0 ? g - kGtStages : 0; gg < g; ++gg)
-                tc::mbar_wait_bounded(&a_full[gg % kGtStages], (uint32_t)((gg / kGtStages) & 1), kGtWaitCycles);
+            for (int gg = g - ns > 0 ? g - ns : 0; gg < g; ++gg)
+                tc::mbar_wait_bounded(&a_full[gg % ns], (uint32_t)((gg / ns) & 1), kGtWaitCycles);
+            tc::mbar_wait_bounded(b_full, 0, kGtWaitCycles);   // B has landed before the memory is released
         }
         __syncwarp();
     } else if (warp == kGtEpiWarps + 1) {
@@ -140,15 +141,15 @@ __global__ void __launch_bounds__(kGtThreads, 1)
             const uint32_t sb_sbo = (uint32_t)(kp / 8) * 128;
             const uint32_t sbb = tc::smem_u32(sB);
             int g = 0;
-            bool ok = true;
+            bool ok = tc::mbar_wait_abortable(b_full, 0, kGtWaitCycles, abort_flag);
             for (int i = 0; i < nitems && ok; ++i) {
                 const int b = i & 1;
                 ok = tc::mbar_wait_abortable(&d_empty[b], (uint32_t)(((i >> 1) & 1) ^ 1), kGtWaitCycles, abort_flag);
                 if (!ok) break;
                 const uint32_t d = tbase + (uint32_t)(b * NT);
                 for (int ch = 0; ch < nchunk; ++ch, ++g) {
-                    const int st = g % kGtStages;
-                    ok = tc::mbar_wait_abortable(&a_full[st], (uint32_t)((g / kGtStages) & 1), kGtWaitCycles,
+                    const int st = g % ns;
+                    ok = tc::mbar_wait_abortable(&a_full[st], (uint32_t)((g / ns) & 1), kGtWaitCycles,
                                                  abort_flag);
                     if (!ok) break;
                     tc::fence_after_sync();
@@ -248,10 +249,17 @@ size_t kmajor_byte(int n, int k, int K) {
 
 }  // namespace
 
-size_t gridtc_smem_bytes(int P, int kp_max) {
+size_t gridtc_smem_bytes(int P, int kp_max, int stages) {
     const int NT = 128 * P;
-    return 1024 + (((size_t)NT * kp_max * 2 + 1023) & ~(size_t)1023) + (size_t)kGtStages * kGtStageBytes +
-           (size_t)kGtEpiWarps * kGtBoxBytes + (size_t)(2 * kGtStages + 4) * 8 + 16;
+    return 1024 + (((size_t)NT * kp_max * 2 + 1023) & ~(size_t)1023) + (size_t)stages * kGtStageBytes +
+           (size_t)kGtEpiWarps * kGtBoxBytes + (size_t)(2 * stages + 5) * 8 + 16;
+}
+
+// A ring depth: the most stages (<= 8) that fit 227 KB beside B and the epilogue boxes; 0 if not even 4 fit.
+int gridtc_stages(int P, int kp_max) {
+    for (int s = kGtMaxStages; s >= 4; --s)
+        if (gridtc_smem_bytes(P, kp_max, s) <= 227 * 1024) return s;
+    return 0;
 }
 
 // Store map of the tile-major gridded field as rows of 128 halves (one sample of one (pol, tile)):
