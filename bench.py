@@ -502,8 +502,10 @@ KERNEL_SOURCES = {
     # the factored-DFT tensor-core route of the dense workloads
     "grid_rows_dft": [("paper_0812_3669_gb300/csrc/moff_image_kernels.cuh", "struct ColShape"),
                       "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
-    "cols_dft": ["paper_0812_3669_gb300/csrc/moff_dft_kernels.cu", "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
-    "rows_dft": ["paper_0812_3669_gb300/csrc/moff_dft_kernels.cu", "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
+    "cols_dft": [("paper_0812_3669_gb300/csrc/moff_dft_kernels.cu", "struct ColDftShape",
+                  "template <int N, int P>\nstruct RowDftShape"), "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
+    "rows_dft": [("paper_0812_3669_gb300/csrc/moff_dft_kernels.cu", "template <int N, int P>\nstruct RowDftShape",
+                  "template <int N, int P>\ncudaError_t launch_rows_dft_t"), "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
     "grid_tc": ["paper_0812_3669_gb300/csrc/moff_gridtc.cu", "paper_0812_3669_gb300/csrc/moff_tc.cuh"],
     "volt_prep": ["paper_0812_3669_gb300/csrc/moff_tc_kernels.cu"],
 }
@@ -513,9 +515,12 @@ ROUTE_KERNELS = {"fp16_dft": {"grid_rows": "grid_rows_dft", "cols_integrate": "c
                                  "volt_prep": "volt_prep"}}
 
 
-def traffic_for(kernel_key, src):
+def traffic_for(kernel_key, src, units_per_launch=None):
     """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
-    source is unchanged since the capture (else None)."""
+    source is unchanged since the capture (else None).  A record captured on a
+    smaller launch holds bytes per unit (channel-snapshot) and is scaled to
+    this launch's units; that holds where every byte the kernel moves grows
+    with the units it processes."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel_key)
@@ -523,6 +528,8 @@ def traffic_for(kernel_key, src):
         return None
     if not rec or rec.get("source_sha1") != source_sha1(src):
         return None
+    if "bytes_per_unit" in rec:
+        return rec["bytes_per_unit"] * units_per_launch if units_per_launch else None
     return rec.get("bytes_per_launch")
 
 
@@ -1029,6 +1036,12 @@ def dense_leg(args, ctx, wl_name, steps, warmup, fp16=True, headline=False, keep
     info, route, tun = pl.info(), pl.route(), pl.tuning()
     work = dense_work(route, pos, taps, N, P, info["time_chunk"])
     roofs = kernel_rooflines(kern, work, snaps, ctx.peaks)
+    for kind, r in roofs.items():             # DRAM bytes from the committed capture against the method's bytes
+        kname = ROUTE_KERNELS.get(route, {}).get(kind, kind)
+        units = snaps / max(r["launches"], 1)
+        t = traffic_for(kname + "@" + wl_name, KERNEL_SOURCES.get(kname, []), units)
+        r["traffic_bytes_per_launch"] = t
+        r["traffic_over_algorithmic"] = t / (work[kind]["bytes"] * units) if t else None
     out = {"value": job_rate(snaps, ctx.world, ms / 1000.0), "unit": UNIT, "ms_per_step": ms / steps,
            "steps": steps, "warmup": warmup, "route": route, "dtype": "f16 tensor-core, f32 accumulate" if fp16 else "f32",
            "samples_per_step": B, "channels": C, "plan_create_s": setup_s, "chunk": [info["time_chunk"], info["chan_chunk"]],
@@ -1110,9 +1123,9 @@ def run_ours(args):
     b = roofs[dom]["bound"]
     rd = roofs[dom][b]
     kname = ROUTE_KERNELS.get(head["route"], {}).get(dom, dom)
-    traffic = traffic_for(kname + "@" + args.workload, KERNEL_SOURCES.get(kname, []))
     work = dense_work(head["route"], pos, taps, wl["grid_n"], wl["n_pol"], head["chunk"][0])[dom]
     per_launch = head["steps"] * head["samples_per_step"] * head["channels"] / max(roofs[dom]["launches"], 1)
+    traffic = traffic_for(kname + "@" + args.workload, KERNEL_SOURCES.get(kname, []), per_launch)
     roofline = {"bound": b, "kernel": kname, "achieved": rd["achieved"], "peak": rd["peak"], "unit": rd["unit"],
                 "frac": rd["frac"], "peak_basis": rd["basis"], "traffic": traffic,
                 "work_per_launch": (work["tensor"] if b == "tensor" else work["alu"] if b == "alu" else work["bytes"])

@@ -312,6 +312,8 @@ def device_codes(seed: int, n_time: int, n_chan: int, n_ant: int, n_pol: int,
     g = torch.Generator(device="cuda")
     g.manual_seed(int(seed))
     out = torch.empty((n_time, n_chan, n_ant, n_pol), dtype=torch.uint8, device="cuda")
+    # at most ~1 GB of float temporaries per draw (the wide-field block is 268 M voltages per sample)
+    chunk = max(1, min(chunk, (1 << 28) // max(1, n_chan * n_ant * n_pol)))
     for t0 in range(0, n_time, chunk):
         n = min(chunk, n_time - t0)
         shape = (n, n_chan, n_ant, n_pol)

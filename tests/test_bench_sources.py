@@ -33,9 +33,25 @@ def test_recorded_captures_name_hashed_kernels():
     for name, r in rec.items():
         kernel = name.split("@")[0]
         assert kernel in bench.KERNEL_SOURCES, name
-        assert r["bytes_per_launch"] > 0 and len(r["source_sha1"]) == 40
+        assert r.get("bytes_per_launch", r.get("bytes_per_unit", 0)) > 0 and len(r["source_sha1"]) == 40
+        assert os.path.exists(os.path.join(ROOT, r["from"].split()[0])), r["from"]
         # a different region never matches the recorded hash
         assert bench.source_sha1(["include/moff.h"]) != r["source_sha1"]
+
+
+def test_traffic_scales_per_unit_records(tmp_path, monkeypatch):
+    """A record in bytes per unit gives bytes per launch for the launch's units;
+    a stale source hash gives nothing."""
+    rec = {"k@w": {"bytes_per_unit": 1000, "source_sha1": bench.source_sha1(["include/moff.h"]), "from": "x"},
+           "s@w": {"bytes_per_unit": 1000, "source_sha1": "0" * 40, "from": "x"}}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "include").mkdir()
+    (tmp_path / "include" / "moff.h").write_bytes(open(os.path.join(ROOT, "include", "moff.h"), "rb").read())
+    assert bench.traffic_for("k@w", ["include/moff.h"], 7680) == 7680000
+    assert bench.traffic_for("k@w", ["include/moff.h"]) is None
+    assert bench.traffic_for("s@w", ["include/moff.h"], 7680) is None
 
 
 def test_row_contraction_byte_model():
