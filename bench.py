@@ -84,7 +84,10 @@ def parse_args():
                     help="skip the legs of the method's extensions (feedback calibration, beams and autocorrelation "
                          "subtraction, channel-dependent positions and kernels, edge-padded oversampling)")
     ap.add_argument("--no-plain", action="store_true", help="skip the batching leg (graph + autotune vs one channel at a time)")
-    ap.add_argument("--serve-requests", type=int, default=32, help="requests per load point of the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests per load point of the serving leg (the full sweep uses 200)")
+    ap.add_argument("--only", default="", choices=["", "dualpol"],
+                    help="profiling case: run this leg alone and print its JSON (not a bench line)")
     ap.add_argument("--cpu-sample", default="", help=argparse.SUPPRESS)
     ap.add_argument("--frames", type=int, default=WL["frames"],
                     help="dual-pol leg: samples per step (smaller values give a profiling case, not a bench line)")
@@ -533,12 +536,19 @@ def traffic_for(kernel_key, src, units_per_launch=None):
     return rec.get("bytes_per_launch")
 
 
-def serving_leg(args, moff, synth, torch, fp16tc=False):
+SERVE_LOADS = (0.3, 0.5, 0.7, 0.85)
+
+
+def serving_leg(args, moff, synth, torch, fp16tc=False, images=None):
     """Request stream over sub-arrays of uneven size (MOFF_SERVED plans, one
     moff_server): first a closed burst to find the saturation rate, then Poisson
-    arrivals at fractions of it.  Reports p50/p99 block latency and throughput.
-    With fp16tc, each sub-array takes the FP16 tensor-core path where its density
-    allows (at most 128 antennas' kernel rows on a grid row) and FP32 otherwise."""
+    arrivals at fractions of it.  Reports p50/p99 block latency and throughput
+    per load point.  With fp16tc, each sub-array takes the FP16 tensor-core path
+    where its density allows (the row-spectrum contraction for sparse rows, the
+    tensor-core gridding and factored DFT for dense arrays on 256 and 512 grids)
+    and FP32 otherwise.  Both streams draw the same request order, so every plan
+    ends with the same blocks summed; with ``images`` (a list) each plan's image
+    divided by its sample count is appended, on the device."""
     import numpy as np
     mix = synth.config_serving()
     plans, blocks, prec = [], [], []
@@ -547,37 +557,39 @@ def serving_leg(args, moff, synth, torch, fp16tc=False):
         if fp16tc:
             try:
                 pl = moff.Plan(a["pos"], a["taps"], a["N"], a["C"], 2, served=True, fp16tc=True)
-                prec.append("fp16tc")
+                prec.append(pl.route())
             except moff.MoffError:
                 pl = None
         if pl is None:
             pl = moff.Plan(a["pos"], a["taps"], a["N"], a["C"], 2, served=True)
             prec.append("fp32")
-        pl.set_gains(a["gains"])
+        pl.set_gains(synth.device_gains(SEED + 600 + i, a["C"], a["A"], 2))
         plans.append(pl)
         blocks.append(synth.device_codes(SEED + 500 + i, a["T"], a["C"], a["A"], 2))
     torch.cuda.synchronize()
     units = [a["C"] * a["T"] for a in mix]
     rng = np.random.default_rng(SEED + 77)
-    srv = moff.Server(24 << 30, 4)
+    nreq = args.serve_requests
+    pool, slots = 32 << 30, 4
+    srv = moff.Server(pool, slots)
     try:
         for i in range(len(plans)):                       # warm every plan once
             srv.submit(plans[i], blocks[i])
-        srv.wait(0, 600000)
+        srv.wait(0, 1800000)
         srv.stats(reset=True)
         # saturation: everything at once
-        order = rng.integers(0, len(plans), size=args.serve_requests)
+        order = rng.integers(0, len(plans), size=nreq)
         t0 = time.perf_counter()
         for i in order:
             srv.submit(plans[i], blocks[i])
-        srv.wait(0, 600000)
+        srv.wait(0, 1800000)
         wall = time.perf_counter() - t0
         sat = srv.stats(reset=True)
         sat_req_s = len(order) / wall
         points = []
-        for load in (0.5, 0.9):
+        for load in SERVE_LOADS:
             rate = load * sat_req_s
-            order = rng.integers(0, len(plans), size=args.serve_requests)
+            order = rng.integers(0, len(plans), size=nreq)
             gaps = rng.exponential(1.0 / rate, size=len(order))
             t0 = time.perf_counter()
             due = t0
@@ -589,20 +601,27 @@ def serving_leg(args, moff, synth, torch, fp16tc=False):
                         break
                     time.sleep(min(due - now, 0.002))
                 srv.submit(plans[i], blocks[i])
-            srv.wait(0, 600000)
+            srv.wait(0, 1800000)
+            wall = time.perf_counter() - t0
             st = srv.stats(reset=True)
             points.append({"load": load, "offered_req_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                           "throughput": st["throughput"], "requests": st["completed"]})
+                           "throughput": st["throughput"], "requests": st["completed"], "wall_s": wall})
+        if images is not None:
+            for pl in plans:
+                img = torch.empty((pl.C, pl.n_prod, pl.N, pl.N), dtype=torch.float32, device="cuda")
+                _, n = pl.read_image(out=img)
+                images.append(img.div_(float(n)))
     finally:
         srv.close()
         for pl in plans:
             pl.close()
+        del blocks
+        torch.cuda.empty_cache()
     return {
-        "unit": UNIT, "precision": "fp16tc where the array allows, else fp32" if fp16tc else "fp32",
-        "slots": 4, "pool_bytes": 24 << 30,
-        "mix": [{"antennas": a["A"], "grid_n": a["N"], "channels": a["C"], "samples": a["T"], "path": p}
+        "unit": UNIT, "precision": "FP16 tensor-core route where the array allows, else fp32" if fp16tc else "fp32",
+        "slots": slots, "pool_bytes": pool, "requests_per_point": nreq,
+        "mix": [{"antennas": a["A"], "grid_n": a["N"], "channels": a["C"], "samples": a["T"], "route": p}
                 for a, p in zip(mix, prec)],
-        "mix_note": "request sizes scaled to channels in {64,128,256} and 100-300 samples so a sweep takes seconds",
         "saturation": {"req_per_s": sat_req_s, "throughput": sat["throughput"], "p50_ms": sat["p50_ms"],
                        "p99_ms": sat["p99_ms"], "requests": sat["completed"]},
         "points": points, "mean_units_per_request": float(np.mean(units)),
@@ -1114,6 +1133,11 @@ def run_ours(args):
         gpu_idx = int(vis.split(",")[local])
     ctx = Ctx(moff, synth, torch, np, world, rank, local, dist, device_peaks(torch), gpu_idx)
 
+    if args.only == "dualpol":
+        if rank == 0:
+            print(json.dumps({"only": "dualpol", "dualpol_fstage": dualpol_leg(args, ctx)}), flush=True)
+        return
+
     # ---------------------------------------------------------------- headline: the largest workload, FP16 tensor core
     wl = DENSE[args.workload]
     head, img16, (pos, taps) = dense_leg(args, ctx, args.workload, args.steps, args.warmup, fp16=True, headline=True,
@@ -1163,8 +1187,15 @@ def run_ours(args):
         dualpol = dualpol_leg(args, ctx)
     serving = None
     if not args.no_serving:
-        serving = serving_leg(args, moff, synth, torch)
-        serving["fp16tc_stream"] = serving_leg(args, moff, synth, torch, fp16tc=True)
+        im32, im16 = [], []
+        serving = serving_leg(args, moff, synth, torch, images=im32)
+        serving["fp16tc_stream"] = serving_leg(args, moff, synth, torch, fp16tc=True, images=im16)
+        # the two streams summed the same blocks per plan: FP16 routes against the FP32 path, max-normalised
+        serving["fp16tc_stream"]["max_norm_diff_vs_fp32"] = [image_diff(torch, a, b) for a, b in zip(im16, im32)]
+        serving["fp16tc_stream"]["saturation_speedup"] = (serving["fp16tc_stream"]["saturation"]["throughput"]
+                                                          / serving["saturation"]["throughput"])
+        del im32, im16
+        torch.cuda.empty_cache()
     batching = None
     if not args.no_plain:
         batching = batching_leg(args, moff, synth, torch)

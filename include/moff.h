@@ -175,8 +175,13 @@ moff_status moff_set_fstage(moff_plan *plan, int n_taps, const float *coeffs, fl
  *   volt    uint8 [n_time][C][A][P].
  *   n_time  samples in the block, >= 1.
  * With on_device = 0 the block is copied to the device before the call
- * returns.  With on_device = 1 the caller keeps the buffer alive and
- * unmodified until moff_sync or moff_read_image returns.
+ * returns; a block of 8 MB or more that spans several channel chunks is
+ * copied by channel segments (one 2D copy each, on the plan's copy stream),
+ * and each chunk's imaging waits only for its own segment, so the copies
+ * overlap the imaging (MOFF_STAGE_PIPELINE=0 copies it whole; graph replay
+ * always does).  The image is the same either way.  With on_device = 1 the
+ * caller keeps the buffer alive and unmodified until moff_sync or
+ * moff_read_image returns.
  */
 moff_status moff_submit(moff_plan *plan, const uint8_t *volt, int n_time, int on_device);
 

@@ -326,6 +326,9 @@ struct moff_plan {
     int beam_T = 0, beam_base = 0;     // beam_base: first sample of the block segment being imaged
     // pipelined host-ADC staging: one event per frame segment
     cudaEvent_t seg_ev[16] = {};
+    // pipelined host-voltage staging: while set, the chunk loops make the plan stream wait for
+    // seg_ev[(c0 / Cb) / chunk_seg] (the copy of that channel segment) before the chunk's launches
+    int chunk_seg = 0;
 
     // optional per-launch timing: (kind, start, stop)
     bool timing = false;
@@ -482,6 +485,54 @@ moff_status stage_done(moff_plan *pl, int i) {
     return wait_event(pl->ev_copied[i], -1);
 }
 
+// Channel chunk c0 of a block staged by channel segments: wait for its segment's copy.
+inline moff_status chunk_ready(moff_plan *pl, int c0) {
+    if (pl->chunk_seg > 0) {
+        const int c = c0 / pl->Cb;
+        if (c % pl->chunk_seg == 0) MOFF_CK(cudaStreamWaitEvent(pl->st, pl->seg_ev[c / pl->chunk_seg], 0));
+    }
+    return MOFF_OK;
+}
+
+// Host voltages [T][C][A][P] copied to staging slot i by channel segments (one cudaMemcpy2DAsync
+// per segment: its channels of every sample) on the copy stream, so imaging of the first
+// channel chunks starts while later ones are still in flight.  The launches and so the
+// image equal a device-input submit's.
+moff_status stage_in_by_channels(moff_plan *pl, const uint8_t *host, int n_time, const void **dev, int *slot) {
+    const int i = (int)(pl->nsub & 1);
+    const size_t cap = (size_t)pl->C * pl->A * pl->P, bytes = (size_t)n_time * cap;
+    if (pl->stage_bytes[i] < bytes) {
+        MOFF_CK(cudaEventSynchronize(pl->ev_consumed[i]));
+        pfree(pl, pl->d_stage[i]);
+        pl->dev_bytes -= pl->stage_bytes[i];
+        pl->d_stage[i] = nullptr;
+        pl->stage_bytes[i] = 0;
+        moff_status s = palloc(pl, &pl->d_stage[i], bytes);
+        if (s != MOFF_OK) return s;
+        pl->stage_bytes[i] = bytes;
+    }
+    for (cudaEvent_t &e : pl->seg_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return fail(MOFF_ECUDA, "event creation failed");
+    const int nseg_max = (int)(sizeof(pl->seg_ev) / sizeof(pl->seg_ev[0]));
+    const int nchunk = (pl->C + pl->Cb - 1) / pl->Cb;
+    const int per = (nchunk + nseg_max - 1) / nseg_max;       // channel chunks per segment
+    const size_t ap = (size_t)pl->A * pl->P;
+    uint8_t *dst = static_cast<uint8_t *>(pl->d_stage[i]);
+    MOFF_CK(cudaStreamWaitEvent(pl->cst, pl->ev_consumed[i], 0));
+    for (int k = 0, e = 0; k < nchunk; k += per, ++e) {
+        const size_t c0 = (size_t)k * pl->Cb, c1 = std::min<size_t>(pl->C, (size_t)(k + per) * pl->Cb);
+        MOFF_CK(cudaMemcpy2DAsync(dst + c0 * ap, cap, host + c0 * ap, cap, (c1 - c0) * ap, (size_t)n_time,
+                                  cudaMemcpyHostToDevice, pl->cst));
+        MOFF_CK(cudaEventRecord(pl->seg_ev[e], pl->cst));
+    }
+    MOFF_CK(cudaEventRecord(pl->ev_copied[i], pl->cst));
+    pl->chunk_seg = per;
+    *dev = dst;
+    *slot = i;
+    return MOFF_OK;
+}
+
 // Gridding-kernel arguments of a plan for channels [c0, c0+nc), samples [t0, t0+nt).
 GridArgs grid_args(const moff_plan *pl, const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc) {
     GridArgs g{};
@@ -579,6 +630,7 @@ moff_status run_feedback(moff_plan *pl, const uint8_t *volt, long long tstride, 
 moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
     const int AP = pl->A * pl->P;
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
+        if (moff_status w = chunk_ready(pl, c0); w != MOFF_OK) return w;
         const int nc = std::min(pl->Cb, pl->C - c0);
         for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
             const int nt = std::min(pl->Tb, n_time - t0);
@@ -698,6 +750,7 @@ moff_status launch_block(moff_plan *pl, int kind, const void *in, long long n, l
 moff_status run_image_dft(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
     const int cpl = pl->quads ? 4 : (pl->pairs ? 2 : 1);
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
+        if (moff_status w = chunk_ready(pl, c0); w != MOFF_OK) return w;
         const int nc = std::min(pl->Cb, pl->C - c0);
         for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
             const int nt = std::min(pl->Tb, n_time - t0);
@@ -738,6 +791,7 @@ moff_status run_image_dft(moff_plan *pl, const uint8_t *volt, int n_time, long l
 moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
     const int AP = pl->A * pl->P;
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
+        if (moff_status w = chunk_ready(pl, c0); w != MOFF_OK) return w;
         const int nc = std::min(pl->Cb, pl->C - c0);
         for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
             const int nt = std::min(pl->Tb, n_time - t0);
@@ -810,6 +864,7 @@ moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long 
     if (pl->dft) return run_image_dft(pl, volt, n_time, tstride);
     if (pl->tc) return run_image_tc(pl, volt, n_time, tstride);
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
+        if (moff_status w = chunk_ready(pl, c0); w != MOFF_OK) return w;
         const int nc = std::min(pl->Cb, pl->C - c0);
         for (int t0 = 0; t0 < n_time; t0 += pl->Tb) {
             const int nt = std::min(pl->Tb, n_time - t0);
@@ -2011,8 +2066,9 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     {
         // FP32 field (float2) on the FP32 path, FP16 (half2) on the tensor-core path
         const size_t per = (size_t)n_pol * grid_n * grid_n * (pl->tc ? 4 : 8);
-        // served plans borrow their scratch per block from a shared pool: keep it modest
-        long long budget = pl->served ? (2048LL << 20) : (32768LL << 20);
+        // served plans borrow their scratch per block from a shared pool: keep it modest (the tensor-core
+        // gridding route reads each tile's kernel matrix once per launch, so it wants more channels per chunk)
+        long long budget = pl->served ? (pl->gtc ? (8192LL << 20) : (2048LL << 20)) : (32768LL << 20);
         if (const char *e = getenv("MOFF_SCRATCH_MB")) budget = std::max(1LL, (long long)(atof(e) * 1048576.0));
         // channels split into equal chunks (no ragged last chunk)
         auto balance = [&](long long cb_max) {
@@ -2283,8 +2339,17 @@ moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_d
     } else {
         const void *dev = nullptr;
         int slot = 0;
-        if ((s = stage_in(pl, volt, bytes, &dev, &slot)) != MOFF_OK) return s;
-        if ((s = image(reinterpret_cast<const uint8_t *>(dev))) != MOFF_OK) return s;
+        // blocks of several channel chunks are copied by channel segments that overlap the imaging
+        // (not under graph replay, whose captured launches carry no per-segment waits)
+        static const bool pipeline = !(getenv("MOFF_STAGE_PIPELINE") && atoi(getenv("MOFF_STAGE_PIPELINE")) == 0);
+        const bool by_chan = pipeline && !pl->graphs && pl->Cb < pl->C && bytes >= ((size_t)8 << 20);
+        if ((s = by_chan ? stage_in_by_channels(pl, volt, n_time, &dev, &slot) : stage_in(pl, volt, bytes, &dev, &slot)) !=
+            MOFF_OK)
+            return s;
+        s = image(reinterpret_cast<const uint8_t *>(dev));
+        pl->chunk_seg = 0;
+        if (s != MOFF_OK) return s;
+        if (by_chan) MOFF_CK(cudaStreamWaitEvent(pl->st, pl->ev_copied[slot], 0));
         if ((s = stage_done(pl, slot)) != MOFF_OK) return s;
     }
     pl->n_samples += n_time;

@@ -279,13 +279,13 @@ def config_widefield(seed: int = SEED_BASE + 4, nx: int = 256, ny: int = 128, gr
 
 # --------------------------------------------------------------------------- device-side draws (large workloads)
 
-def config_serving(seed: int = SEED_BASE + 3, n_arrays: int = 8, chans=(64, 128, 256),
-                   t_range=(100, 300), ksize: int = 7):
+def config_serving(seed: int = SEED_BASE + 3, n_arrays: int = 8, chans=(64, 128, 256, 512, 1024),
+                   t_range=(100, 1000), ksize: int = 7):
     """Sub-arrays of uneven size for a request stream: A drawn from {256, 1024,
     4096, 16384} on a square 1 lambda lattice (ceil(sqrt A) per side, 5 % jitter)
     centred in a grid N drawn from {64, 128, 256, 512} with N >= 2 ceil(sqrt A)
-    cells, dual pol, 7x7 kernels; per array a channel count from ``chans`` and a
-    block length in ``t_range``."""
+    cells, dual pol, 7x7 kernels; per array a channel count from ``chans`` (64 to
+    1024) and a block length in ``t_range`` (100 to 1000 samples)."""
     rng = rng_for(seed)
     out = []
     for _ in range(n_arrays):

@@ -206,3 +206,54 @@ def test_served_tensor_core_plan_equals_unserved():
         img, n = ps.read_image()
     assert n == nr == 103
     assert np.array_equal(img, ref)
+
+
+def test_served_fp16_routes_mix_equals_alone_and_match_oracle():
+    """The FP16 stream of the serving pattern: a dense 48 x 48 lattice on the 256
+    grid (tensor-core gridding and factored DFT) and a sparse array (row-spectrum
+    contraction) served beside an FP32 plan.  Each image is bit-identical alone
+    and in the mix, and within the reduced-precision bar (3e-3) of the oracle."""
+    rng = np.random.default_rng(91)
+    side, N, K, C = 48, 256, 7, 3
+    dpos = synth.positions_lattice(rng, side, side, 1.0, 0.05, (N / 2 - side, N / 2 - side))
+    dtaps = c64(synth.taps_gaussian(rng, dpos, K, 1.2, n_pol=2))
+    dgains = c64(synth.gains_random(rng, C, dpos.shape[0], 2))
+    spos, staps, sgains = subarray(92, 300, 128, 7, 2, 4, 100)
+    fpos, ftaps, fgains = subarray(93, 200, 64, 5, 2, 2, 40)
+    cases = [(dpos, dtaps, dgains, N, C, True, "fp16_tcgrid", blocks(94, [37, 20], C, dpos.shape[0], 2)),
+             (spos, staps, sgains, 128, 4, True, "fp16_rowspec", blocks(95, [30, 11], 4, 300, 2)),
+             (fpos, ftaps, fgains, 64, 2, False, "fp32", blocks(96, [25, 16], 2, 200, 2))]
+
+    def make():
+        out = []
+        for pos, taps, gains, n, c, tc, route, _ in cases:
+            pl = moff.Plan(pos, taps, n, c, 2, served=True, fp16tc=tc)
+            assert pl.route() == route, pl.route()
+            pl.set_gains(gains)
+            out.append(pl)
+        return out
+
+    plans_a = make()
+    with moff.Server(8 << 30, 1) as srv:
+        for pl, case in zip(plans_a, cases):
+            for b in case[7]:
+                srv.submit(pl, b)
+            srv.wait(0, 120000)
+    alone = images(plans_a)
+    plans_m = make()
+    with moff.Server(8 << 30, 3) as srv:
+        for r in range(2):
+            for pl, case in zip(plans_m, cases):
+                srv.submit(pl, case[7][r])
+        srv.wait(0, 120000)
+    mix = images(plans_m)
+    for (ia, na), (im, nm), case in zip(alone, mix, cases):
+        assert na == nm == sum(b.shape[0] for b in case[7])
+        assert np.array_equal(ia, im), case[6]
+    for (img, _), (pos, taps, gains, n, _, tc, route, blks) in zip(mix, cases):
+        ref = oracle.moff_image(np.concatenate(blks), gains, pos, taps, n, 2)
+        err = oracle.max_norm_err(img, ref)
+        print(f"served {route}: max-normalised error {float(err.max()):.2e}")
+        assert err.max() <= (3e-3 if tc else TOL32)
+    for pl in plans_a + plans_m:
+        pl.close()
