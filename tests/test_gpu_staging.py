@@ -35,13 +35,14 @@ def run(pos, taps, N, C, P, gains, blocks, host, fp16tc=False):
 @pytest.mark.parametrize("fp16tc", [False, True])
 def test_host_block_by_channel_segments_equals_device_input(monkeypatch, fp16tc):
     rng = np.random.default_rng(501)
-    side, N, K, P, C = 32, 256, 5, 2, 48
+    side, N, K, P, C = 48, 256, 7, 2, 48
     pos = synth.positions_lattice(rng, side, side, 1.0, 0.05, (N / 2 - side, N / 2 - side))
     A = pos.shape[0]
     taps = synth.taps_gaussian(rng, pos, K, 1.2, n_pol=P).astype(np.complex64)
     gains = synth.gains_random(rng, C, A, P).astype(np.complex64)
-    # blocks of 9.4 MB and 1.9 MB (the second below the segmenting threshold); several channel chunks
+    # blocks of 22 MB and 4.4 MB, several channel chunks each
     blocks = [synth.device_codes(502, 100, C, A, P), synth.device_codes(503, 20, C, A, P)]
+    # (the second block still spans channel chunks: below 8 MB it is copied whole)
     monkeypatch.setenv("MOFF_SCRATCH_MB", "300" if fp16tc else "24")
     dev, nd, info = run(pos, taps, N, C, P, gains, blocks, host=False, fp16tc=fp16tc)
     assert info["chan_chunk"] < C, info
