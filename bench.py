@@ -55,7 +55,7 @@ DENSE = {
                            "kernels, 1024 channels, 512x512 grid (zero-padded x2), 2000-sample integrations in "
                            "blocks of 128 samples"),
 }
-# The F-stage workload (the round's former headline, now a named leg).
+# The dual-pol F-stage workload (a named leg of the bench line).
 WL = dict(n_ant=1024, n_pol=2, n_chan=1024, grid_n=128, ksize=7, ntaps=8, frames=1000)
 SEED = 8123669 + 1
 DUALPOL_NAME = ("dual-pol 1024-antenna hex core (1.5 lambda, 5% jitter), 8-bit ADC -> 8-tap x 2048 PFB -> 1024 "
@@ -371,8 +371,8 @@ def oracle_setup(wl_name, n_chan, n_time, seed):
     cfg = getattr(synth, wl["cfg"])(n_chan=n_chan)
     rng = np.random.default_rng(seed)
     shape = (n_time, n_chan, wl["n_ant"], wl["n_pol"])
-    re = np.clip(np.rint(rng.normal(0, 2, size=shape)), -7, 7).astype(int)
-    im = np.clip(np.rint(rng.normal(0, 2, size=shape)), -7, 7).astype(int)
+    re = np.clip(np.rint(2 * rng.standard_normal(size=shape, dtype=np.float32)), -7, 7).astype(np.int8)
+    im = np.clip(np.rint(2 * rng.standard_normal(size=shape, dtype=np.float32)), -7, 7).astype(np.int8)
     W = oracle.grid_matrix(cfg["pos"], cfg["taps"], wl["grid_n"], wl["n_pol"], jones=wl["jones"])
     return W, synth.pack_4bit(re, im), cfg["gains"]
 
@@ -407,11 +407,11 @@ def run_cpu_sample(wl_name):
     wl = DENSE[wl_name]
     N, P = wl["grid_n"], wl["n_pol"]
     cores = host_cores()
-    T1, C1, Tm = 32, 8, 64
-    W, codes, gains = oracle_setup(wl_name, max(C1, cores), T1, 8123669 + 77)
+    T1, C1, Tm = 64, 8, 256                  # about 10 s of one core, and of every core
+    W, codes, gains = oracle_setup(wl_name, max(C1, cores), max(T1, Tm), 8123669 + 77)
     oracle_channels(W, codes[:2, :1], gains[:1], N, P)                # warm
     t0 = time.perf_counter()
-    n1 = oracle_channels(W, codes[:, :C1], gains[:C1], N, P)
+    n1 = oracle_channels(W, codes[:T1, :C1], gains[:C1], N, P)
     dt1 = time.perf_counter() - t0
     ctx = mp.get_context("spawn")
     items = [(codes[:Tm, c:c + 1].copy(), gains[c:c + 1], N, P) for c in range(cores)]
