@@ -189,6 +189,18 @@ cudaError_t launch_cols(int N, int P, const ColArgs &a, cudaStream_t st, bool h1
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_persist(int N, int P, int cpl, bool wide, const PersistArgs &pa, size_t smem, int sms,
+                           cudaStream_t st) {
+    switch (N) {
+        case 32: return launch_persist_n32(P, cpl, wide, pa, smem, sms, st);
+        case 64: return launch_persist_n64(P, cpl, wide, pa, smem, sms, st);
+        case 128: return launch_persist_n128(P, cpl, wide, pa, smem, sms, st);
+        case 256: return launch_persist_n256(P, cpl, wide, pa, smem, sms, st);
+        case 512: return launch_persist_n512(P, cpl, wide, pa, smem, sms, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_to_f32(const double *acc, float *out, long long n, cudaStream_t st) {
     const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
     k_to_f32<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, st>>>(acc, out, n);

@@ -15,6 +15,7 @@
 #include <cuda_fp16.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "moff_dft.cuh"
@@ -40,33 +41,41 @@ size_t kmajor_at(int n, int k, int K) {
     return (size_t)(n >> 3) * (K >> 3) * 128 + (size_t)(k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
 }
 
-template <int N, int P>
+template <int N, int P, int W>
 struct ColDftShape {
     using S = DftShape<N>;
-    static constexpr int W = 16;                       // columns per CTA
+    static_assert(W == 8 || W == 16, "columns per CTA");
     static constexpr int N2 = S::N2;
-    static constexpr int M1 = W * N2;                  // stage-1 rows per pol: m = 16 b + x
+    static constexpr int H = W / 8;                    // 16-byte pieces per (pol, row, re/im) of the strip
+    static constexpr int M1 = W * N2;                  // stage-1 rows per pol: m = W b + x
     static constexpr int T1 = M1 / 128;
     static constexpr int LBO1 = (M1 / 8) * 128;        // stage-1 A: K-direction core-matrix stride
     static constexpr int A1P = M1 * S::K1 * 2;         // bytes of one pol's stage-1 A
-    static constexpr int M2 = 16 * W;                  // stage-2 rows per pol: m2 = 128 c_hi + 8 x + c_lo
+    static constexpr int M2 = 16 * W;                  // stage-2 rows per pol: m2 = 8 W c_hi + 8 x + c_lo
     static constexpr int T2 = M2 / 128;
     static constexpr int A2P = M2 * S::K2 * 2;         // bytes of one pol's stage-2 A (128-byte swizzled)
     static constexpr int D1 = P * T1 * S::C1;          // TMEM columns: stage-1 accumulators
     static constexpr int D2 = P * T2 * S::C2;          // then stage-2 accumulators
     static constexpr int TC_ = D1 + D2;
     static constexpr int TCOLS = TC_ <= 32 ? 32 : (TC_ <= 64 ? 64 : (TC_ <= 128 ? 128 : (TC_ <= 256 ? 256 : 512)));
-    static constexpr int NPIECE = P * N * 4;           // 16-byte pieces per sample: (p, ry, re/im, x half)
+    static constexpr int NPIECE = P * N * 2 * H;       // 16-byte pieces per sample: (p, ry, re/im, h)
     static constexpr int ITER = NPIECE / kBlock;
+    static constexpr int ROWS_K = kBlock / (2 * H);    // grid rows covered by one piece round of the block
+    // warp groups per stage-2 tile: with one tile (W = 8) the two groups split the d range
+    static constexpr int DSPLIT = 2 / T2;
+    static constexpr int ND = N2 / DSPLIT;             // d values per thread
+    static constexpr int MINB = W == 8 ? 2 : 1;        // CTAs per SM
     static constexpr size_t SMEM = 1024 + (size_t)P * A2P + 2 * (size_t)P * A1P + S::TAB_BYTES + 32;
-    static_assert(T2 == 2 && TC_ <= 512 && NPIECE % kBlock == 0 && ITER <= 32, "column-kernel shape");
+    static_assert(T2 >= 1 && T2 <= 2 && T1 >= 1 && TC_ * MINB <= 512 && NPIECE % kBlock == 0 && ITER <= 32 &&
+                      ND % 8 == 0 && (2 * H * N) % kBlock == 0 && ROWS_K % N2 == 0 && SMEM * MINB <= 225 * 1024,
+                  "column-kernel shape");
 };
 
-template <int N, int P>
-__global__ void __launch_bounds__(kBlock, 1) k_cols_dft(const ColDftArgs a) {
+template <int N, int P, int W>
+__global__ void __launch_bounds__(kBlock, ColDftShape<N, P, W>::MINB) k_cols_dft(const ColDftArgs a) {
     using S = DftShape<N>;
-    using CS = ColDftShape<N, P>;
-    constexpr int W = CS::W, N2 = S::N2, K2 = S::K2, C2 = S::C2;
+    using CS = ColDftShape<N, P, W>;
+    constexpr int N2 = S::N2, K2 = S::K2, C2 = S::C2, H = CS::H, ND = CS::ND;
     constexpr int NPROD = P == 1 ? 1 : 4;
     const int x0 = blockIdx.x * W, cl = blockIdx.y, c = a.c0 + cl;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3;
@@ -91,28 +100,32 @@ __global__ void __launch_bounds__(kBlock, 1) k_cols_dft(const ColDftArgs a) {
         tc::tmem_alloc(tslot, CS::TCOLS);
         tc::tmem_relinquish();
     }
-    // Piece i = k kBlock + tid of a sample: pol p, row ry, re/im ri, column half h (i = ((p N + ry) 2
-    // + ri) 2 + h).  With kBlock a divisor of 4N, k fixes p and ry's multiple of 64 (PK, RYK below,
-    // compile-time) and the thread fixes ry mod 64 = r0, ri and h: every offset is a thread
-    // constant plus a compile-time one.  Rows no kernel reaches are zero: cleared once in both
+    // Piece i = k kBlock + tid of a sample: pol p, row ry, re/im ri, column piece h (i = ((p N + ry) 2
+    // + ri) H + h).  With kBlock a divisor of 2 H N, k fixes p and ry's multiple of ROWS_K (PK, RYK
+    // below, compile-time) and the thread fixes ry mod ROWS_K = r0, ri and h: every offset is a thread
+    // constant plus a compile-time one.  In the stage-1 operand the piece is the 8 rows m = W b + 8 h
+    // + (0..7) at k = 2 a + ri (ry = N2 a + b).  Rows no kernel reaches are zero: cleared once in both
     // buffers and never loaded.
-    static_assert((4 * N) % kBlock == 0 && kBlock / 4 == 64 && N2 <= 64, "piece enumeration");
-    const int r0 = tid >> 2, ri0 = (tid >> 1) & 1, h0 = tid & 1;
-    const int a0 = r0 / N2, b0 = r0 - a0 * N2;
-    const uint32_t dst_t = (uint32_t)((2 * b0 + h0) * 128 + (2 * a0 + ri0) * 16);
+    const int h0 = tid % H, ri0 = (tid / H) & 1, r0 = tid / (2 * H);
+    const int a0 = r0 / N2, b0 = r0 - a0 * N2, kt = 2 * a0 + ri0;
+    // 2 a = 2 (RYK / N2) + 2 a0: the compile-time part is a multiple of 8 when ROWS_K is one of 4 N2,
+    // else (16 columns at N = 512) kt and the compile-time part share one core-matrix row group
+    constexpr bool KSPLIT8 = CS::ROWS_K % (4 * N2) == 0;
+    const uint32_t dst_t = (uint32_t)((H * b0 + h0) * 128) +
+                           (KSPLIT8 ? (uint32_t)((kt >> 3) * CS::LBO1 + (kt & 7) * 16) : (uint32_t)(kt * 16));
     const long long src_t = (long long)(2 * r0 + ri0) * N + x0 + 8 * h0;
     auto piece_dst = [&](int k) -> uint32_t {      // k compile-time after unrolling
-        const int PK = (k * kBlock) / (4 * N), RYK = ((k * kBlock) % (4 * N)) >> 2, AK = RYK / N2;
+        const int PK = (k * kBlock) / (2 * H * N), RYK = ((k * kBlock) % (2 * H * N)) / (2 * H), AK = RYK / N2;
         return (uint32_t)(PK * CS::A1P + ((2 * AK) >> 3) * CS::LBO1 + ((2 * AK) & 7) * 16) + dst_t;
     };
     auto piece_src = [&](int k) -> long long {
-        const int PK = (k * kBlock) / (4 * N), RYK = ((k * kBlock) % (4 * N)) >> 2;
+        const int PK = (k * kBlock) / (2 * H * N), RYK = ((k * kBlock) % (2 * H * N)) / (2 * H);
         return (long long)(PK * N + RYK) * 2 * N + src_t;
     };
     uint32_t act = 0;
 #pragma unroll
     for (int k = 0; k < CS::ITER; ++k) {
-        const int ry = (((k * kBlock) % (4 * N)) >> 2) + r0;
+        const int ry = (((k * kBlock) % (2 * H * N)) / (2 * H)) + r0;
         if ((a.row_nz[ry >> 5] >> (ry & 31)) & 1u) {
             act |= 1u << k;
         } else {
@@ -165,58 +178,63 @@ __global__ void __launch_bounds__(kBlock, 1) k_cols_dft(const ColDftArgs a) {
                                 tc::smem_desc(b0 + ks * 256, 128, SBOB), id2, ks > 0);
         tc::mma_commit(&mbar[1]);
     };
-    // Twiddle stage 1's result and write it as stage 2's A: thread (b, x) of tile (p, j)
-    // writes, for c = 8 ch .. 8 ch + 7, the re piece at k = b and the im piece at k = N2 + b.
+    // Twiddle stage 1's result and write it as stage 2's A: thread (b, x) of tile (p, j) writes, for
+    // c = 8 ch .. 8 ch + 7 (one TMEM load of 16 columns each), the re piece at k = b and the im piece
+    // at k = N2 + b of row group m2 = 8 W ch + 8 x.
     auto epi1 = [&]() {
         for (int idx = warp >> 2; idx < P * CS::T1; idx += kBlock / 128) {
             const int p = idx / CS::T1, j = idx - p * CS::T1;
-            const int m = 128 * j + 32 * q + lane, b = m >> 4, x = m & 15;
-            float v[32];
-            tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(idx * S::C1), v);
-            uint32_t re[8], im[8];
-#pragma unroll
-            for (int cc = 0; cc < 16; cc += 2) {
-                const float2 t0 = sTw[cc * N2 + b], t1 = sTw[(cc + 1) * N2 + b];
-                const float x0r = v[2 * cc] * t0.x - v[2 * cc + 1] * t0.y;
-                const float x0i = v[2 * cc] * t0.y + v[2 * cc + 1] * t0.x;
-                const float x1r = v[2 * cc + 2] * t1.x - v[2 * cc + 3] * t1.y;
-                const float x1i = v[2 * cc + 2] * t1.y + v[2 * cc + 3] * t1.x;
-                re[cc >> 1] = dftc::pack_hh(x0r, x1r);
-                im[cc >> 1] = dftc::pack_hh(x0i, x1i);
-            }
+            const int m = 128 * j + 32 * q + lane, b = m / W, x = m % W;
             unsigned char *a2 = sA2 + p * CS::A2P;
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {
-                const int m2 = ch * 128 + x * 8;
+                float v[16];
+                tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(idx * S::C1 + 16 * ch), v);
+                uint32_t re[4], im[4];
+#pragma unroll
+                for (int i = 0; i < 8; i += 2) {
+                    const int cc = 8 * ch + i;
+                    const float2 t0 = sTw[cc * N2 + b], t1 = sTw[(cc + 1) * N2 + b];
+                    const float x0r = v[2 * i] * t0.x - v[2 * i + 1] * t0.y;
+                    const float x0i = v[2 * i] * t0.y + v[2 * i + 1] * t0.x;
+                    const float x1r = v[2 * i + 2] * t1.x - v[2 * i + 3] * t1.y;
+                    const float x1i = v[2 * i + 2] * t1.y + v[2 * i + 3] * t1.x;
+                    re[i >> 1] = dftc::pack_hh(x0r, x1r);
+                    im[i >> 1] = dftc::pack_hh(x0i, x1i);
+                }
+                const int m2 = ch * 8 * W + x * 8;
                 const int hb = (m2 >> 6) * K2 * 128, cg = (m2 & 63) >> 3;
                 const int kr = b, ki = N2 + b;
                 *reinterpret_cast<uint4 *>(a2 + hb + kr * 128 + ((cg ^ (kr & 7)) << 4)) =
-                    make_uint4(re[4 * ch], re[4 * ch + 1], re[4 * ch + 2], re[4 * ch + 3]);
+                    make_uint4(re[0], re[1], re[2], re[3]);
                 *reinterpret_cast<uint4 *>(a2 + hb + ki * 128 + ((cg ^ (ki & 7)) << 4)) =
-                    make_uint4(im[4 * ch], im[4 * ch + 1], im[4 * ch + 2], im[4 * ch + 3]);
+                    make_uint4(im[0], im[1], im[2], im[3]);
             }
         }
     };
-    // Square and sum: warp (j2, q) holds pixels (ky = 8 j2 + c_lo + 16 d, kx = x0 + x) with
-    // 32 q + lane = 8 x + c_lo, for every d.
-    const int j2 = warp >> 2;
-    float acc[NPROD][N2];
+    // Square and sum: warp group g = warp / 4 takes stage-2 tile j2 (two tiles) or half the d range
+    // (one tile); lane quarter q's row l = 32 q + lane of the tile is m2 = 128 j2 + l = 8 W c_hi + 8 x
+    // + c_lo: pixels (ky = 8 c_hi + c_lo + 16 d, kx = x0 + x) for the group's d.
+    const int g = warp >> 2;
+    const int j2 = CS::T2 == 2 ? g : 0, dbase = CS::T2 == 2 ? 0 : g * ND;
+    float acc[NPROD][ND];
 #pragma unroll
     for (int pq = 0; pq < NPROD; ++pq)
 #pragma unroll
-        for (int d = 0; d < N2; ++d) acc[pq][d] = 0.f;
+        for (int d = 0; d < ND; ++d) acc[pq][d] = 0.f;
     auto epi2 = [&]() {
 #pragma unroll
-        for (int db = 0; db < N2 / 8; ++db) {         // 8 d per TMEM load of each pol
+        for (int db = 0; db < ND / 8; ++db) {         // 8 d per TMEM load of each pol
+            const uint32_t col = (uint32_t)(CS::D1 + j2 * C2 + 2 * dbase + 16 * db);
             float ex[16];
-            tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(CS::D1 + j2 * C2 + 16 * db), ex);
+            tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + col, ex);
             if constexpr (P == 1) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     acc[0][8 * db + i] = fmaf(ex[2 * i], ex[2 * i], fmaf(ex[2 * i + 1], ex[2 * i + 1], acc[0][8 * db + i]));
             } else {
                 float ey[16];
-                tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(CS::D1 + (CS::T2 + j2) * C2 + 16 * db), ey);
+                tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + col + (uint32_t)(CS::T2 * C2), ey);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const float xr = ex[2 * i], xi = ex[2 * i + 1], yr = ey[2 * i], yi = ey[2 * i + 1];
@@ -268,12 +286,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_cols_dft(const ColDftArgs a) {
         // undo the field's scale s_G / (16 N) (exact powers of two), squared, and fold into FP64
         const double un = 16.0 * (double)N / ((double)a.sy[c] * (double)a.s_t);
         const double sc2 = un * un;
-        const int l = 32 * q + lane, x = l >> 3, cy = 8 * j2 + (l & 7);
+        const int m2 = 128 * j2 + 32 * q + lane;
+        const int x = (m2 % (8 * W)) >> 3, cy = 8 * (m2 / (8 * W)) + (m2 & 7);
 #pragma unroll
         for (int pq = 0; pq < NPROD; ++pq) {
             double *dst = a.acc + ((long long)c * NPROD + pq) * N * N + x0 + x;
 #pragma unroll
-            for (int d = 0; d < N2; ++d) dst[(long long)(cy + 16 * d) * N] += (double)acc[pq][d] * sc2;
+            for (int d = 0; d < ND; ++d) dst[(long long)(cy + 16 * (dbase + d)) * N] += (double)acc[pq][d] * sc2;
         }
     } else if (tid == 0) {
         atomicExch(a.err, tc::kErrWaitTimeout);
@@ -523,14 +542,21 @@ cudaError_t launch_rows_dft_t(const RowDftArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int N, int P>
+template <int N, int P, int W>
 cudaError_t launch_cols_dft_t(const ColDftArgs &a, cudaStream_t st) {
-    auto k = k_cols_dft<N, P>;
-    const size_t smem = ColDftShape<N, P>::SMEM;
+    auto k = k_cols_dft<N, P, W>;
+    const size_t smem = ColDftShape<N, P, W>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<dim3(N / ColDftShape<N, P>::W, a.nc), kBlock, smem, st>>>(a);
+    k<<<dim3(N / W, a.nc), kBlock, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// Columns per CTA: 8 (two CTAs per SM, so one CTA's epilogue runs while the other waits on its
+// MMAs) unless MOFF_COLS_W=16 (one CTA per SM).
+int cols_dft_width() {
+    static const int w = (getenv("MOFF_COLS_W") && atoi(getenv("MOFF_COLS_W")) == 16) ? 16 : 8;
+    return w;
 }
 
 }  // namespace
@@ -576,14 +602,24 @@ std::vector<unsigned char> build_dft_table(int N) {
 }
 
 size_t cols_dft_smem_bytes(int N, int P) {
-    if (N == 512) return P == 1 ? ColDftShape<512, 1>::SMEM : ColDftShape<512, 2>::SMEM;
-    if (N == 256) return P == 1 ? ColDftShape<256, 1>::SMEM : ColDftShape<256, 2>::SMEM;
+    if (cols_dft_width() == 16) {
+        if (N == 512) return P == 1 ? ColDftShape<512, 1, 16>::SMEM : ColDftShape<512, 2, 16>::SMEM;
+        if (N == 256) return P == 1 ? ColDftShape<256, 1, 16>::SMEM : ColDftShape<256, 2, 16>::SMEM;
+    } else {
+        if (N == 512) return P == 1 ? ColDftShape<512, 1, 8>::SMEM : ColDftShape<512, 2, 8>::SMEM;
+        if (N == 256) return P == 1 ? ColDftShape<256, 1, 8>::SMEM : ColDftShape<256, 2, 8>::SMEM;
+    }
     return 0;
 }
 
 cudaError_t launch_cols_dft(int N, int P, const ColDftArgs &a, cudaStream_t st) {
-    if (N == 512) return P == 1 ? launch_cols_dft_t<512, 1>(a, st) : launch_cols_dft_t<512, 2>(a, st);
-    if (N == 256) return P == 1 ? launch_cols_dft_t<256, 1>(a, st) : launch_cols_dft_t<256, 2>(a, st);
+    if (cols_dft_width() == 16) {
+        if (N == 512) return P == 1 ? launch_cols_dft_t<512, 1, 16>(a, st) : launch_cols_dft_t<512, 2, 16>(a, st);
+        if (N == 256) return P == 1 ? launch_cols_dft_t<256, 1, 16>(a, st) : launch_cols_dft_t<256, 2, 16>(a, st);
+    } else {
+        if (N == 512) return P == 1 ? launch_cols_dft_t<512, 1, 8>(a, st) : launch_cols_dft_t<512, 2, 8>(a, st);
+        if (N == 256) return P == 1 ? launch_cols_dft_t<256, 1, 8>(a, st) : launch_cols_dft_t<256, 2, 8>(a, st);
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -126,8 +126,9 @@ static_assert(fft_radix(32, 0) == FftPlan<32>::R0 && fft_radix(32, 1) == FftPlan
 // block (f, e), (f, e + 1), (f + 1, e), (f + 1, e + 1), f even); each entry carries CPL taps.
 // DFT: the row transform runs as factored DFT contractions on the tensor cores
 // (moff_dft.cuh) and the field leaves as FP16 rows [re N][im N] (a.h16).
+// (s, cl): this CTA's stripe and channel of the launch; n_str: stripes per set (the grid's x extent).
 template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE, bool DFT = false>
-__device__ __forceinline__ void grid_rows(const GridArgs &a) {
+__device__ __forceinline__ void grid_rows(const GridArgs &a, const int s, const int cl, const int n_str) {
     constexpr bool PAIRS = CPL >= 2;
     using FP = FftPlan<N>;
     using TW = FftTw<N>;
@@ -137,14 +138,12 @@ __device__ __forceinline__ void grid_rows(const GridArgs &a) {
     constexpr int ROWS = GS::ROWS, PR = GS::PR, F = GS::F;
     constexpr int YPT = 2;                // voltages per thread whose bytes are prefetched
 
-    const int s = blockIdx.x;
-    const int cl = blockIdx.y;
     const int c = a.c0 + cl;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int nsl = a.n_slices;
     const int grp = a.chan_group ? a.chan_group[c] : 0;      // this channel's set of positions and kernels
-    const long long gs = (long long)grp * gridDim.x + s;     // stripe s of that set
+    const long long gs = (long long)grp * n_str + s;         // stripe s of that set
     const int *sao = a.st_ant_off + grp + gs;                // set g's offsets start at g (n_stripes + 1)
     const int ant0 = sao[0];
     const int nloc = sao[1] - ant0;
@@ -439,19 +438,19 @@ __device__ __forceinline__ void grid_rows(const GridArgs &a) {
 // explicit minimum of one CTA per SM lets it take about twice as many).
 template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE>
 __global__ void __launch_bounds__(kBlock) k_grid_rows(const GridArgs a) {
-    grid_rows<N, P, TB, STAGED, GRID_ONLY, CPL, WIDE>(a);
+    grid_rows<N, P, TB, STAGED, GRID_ONLY, CPL, WIDE>(a, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // Gridding with the row transform on the tensor cores (FP16 field out).
 template <int N, int P, int TB, int CPL>
 __global__ void __launch_bounds__(kBlock) k_grid_rows_dft(const GridArgs a) {
-    grid_rows<N, P, TB, false, false, CPL, false, true>(a);
+    grid_rows<N, P, TB, false, false, CPL, false, true>(a, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // Row transform in place: registers capped so that grid_min_blocks CTAs fit an SM.
 template <int N, int P, int TB, bool STAGED, bool GRID_ONLY, int CPL, bool WIDE>
 __global__ void __launch_bounds__(kBlock, grid_min_blocks<N, P, TB, CPL, WIDE>()) k_grid_rows_ip(const GridArgs a) {
-    grid_rows<N, P, TB, STAGED, GRID_ONLY, CPL, WIDE>(a);
+    grid_rows<N, P, TB, STAGED, GRID_ONLY, CPL, WIDE>(a, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 template <int N>
@@ -462,8 +461,9 @@ struct ColShape {
     static constexpr int NS = N / RL;                          // slots per column in the last pass
 };
 
+// (sx, cl): this CTA's column strip and channel of the launch.
 template <int N, int P, bool H16, bool TAPS>
-__global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
+__device__ __forceinline__ void cols_acc(const ColArgs &a, const int sx, const int cl) {
     using FP = FftPlan<N>;
     using TW = FftTw<N>;
     using CS = ColShape<N>;
@@ -475,8 +475,7 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
     constexpr int CHUNKS = TILE * EB / 16;          // 16-byte pieces per tile
     constexpr int ROWCH = W * EB / 16;              // pieces per tile row
 
-    const int kx0 = blockIdx.x * W;
-    const int cl = blockIdx.y;
+    const int kx0 = sx * W;
     const int c = a.c0 + cl;
     const int tid = threadIdx.x;
 
@@ -663,10 +662,146 @@ __global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
             const int ky = jL + r * CS::NS;
-            d[(long long)ky * N] += H16 ? (double)acc[q][r] * sc2 : (double)acc[q][r];
+            // read through L2: in a persistent launch another SM folded the previous chunk
+            d[(long long)ky * N] = __ldcg(d + (long long)ky * N) + (H16 ? (double)acc[q][r] * sc2 : (double)acc[q][r]);
         }
     }
 }
+
+template <int N, int P, bool H16, bool TAPS>
+__global__ void __launch_bounds__(kBlock) k_cols_acc(const ColArgs a) {
+    cols_acc<N, P, H16, TAPS>(a, blockIdx.x, blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batching pattern: every (Tb, Cb) chunk of a block in ONE persistent launch.  Each CTA pulls
+// work items from a device queue (an atomic counter over the item list, in chunk order: the
+// chunk's gridding + row-transform items, then its column items) until the queue is empty.
+// An item waits (one polling lane, bounded by a clock64 budget) for the items it depends on:
+//   row item (k, stripe, cl)   the column items of chunk k - 1 for channel slot cl (they read
+//                              the field scratch it overwrites);
+//   column item (k, strip, cl) the row items of chunk k for cl, and, when chunk k - 1 holds the
+//                              same channels, its column items for cl (both add to the same FP64
+//                              accumulators: chunks fold in order, so the sums equal the direct
+//                              launches' bit for bit).
+// Every dependency is on an earlier item of the queue, which a running CTA has claimed, so the
+// launch always progresses.  A wait that runs out of budget (or sees another CTA's failure)
+// records MOFF_ETIMEDOUT in the status word and the CTA leaves; no asynchronous copy is in
+// flight at any wait.
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// One lane: wait until *cnt >= need, within budget; false if it ran out or a CTA failed.
+__device__ __forceinline__ bool persist_wait(const int *cnt, int need, const PersistArgs &pa) {
+    const long long t0 = clock64();
+    while (ld_acquire_gpu(cnt) < need) {
+        if (ld_acquire_gpu(pa.status) != 0 || clock64() - t0 > pa.budget) return false;
+        __nanosleep(256);
+    }
+    return true;
+}
+
+// Item it of the queue: chunk k (item0[k] <= it < item0[k + 1]); within it, nc * n_stripes row
+// items (stripe fastest, as the direct launch's grid), then nc * n_strips column items.
+__device__ __forceinline__ int4 persist_item(const PersistArgs &pa, int it) {
+    int lo = 0, hi = pa.n_chunks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pa.item0[mid] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    const int r = it - pa.item0[lo], nr = pa.n_stripes * pa.chunks[lo].w;
+    if (r < nr) return make_int4(lo, 0, r % pa.n_stripes, r / pa.n_stripes);
+    const int rc = r - nr;
+    return make_int4(lo, 1, rc % pa.n_strips, rc / pa.n_strips);
+}
+
+template <int N, int P, int TB, int CPL, bool WIDE>
+__global__ void __launch_bounds__(kBlock) k_image_persist(const __grid_constant__ PersistArgs pa) {
+    __shared__ int4 s_w;
+    __shared__ int s_go;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            const int it = ld_acquire_gpu(pa.status) != 0 ? pa.n_items : atomicAdd(pa.next, 1);
+            int go = it < pa.n_items;
+            int4 w = make_int4(0, 0, 0, 0);
+            if (go) {
+                w = persist_item(pa, it);
+                const int k = w.x, cl = w.w;
+                if (w.y == 0) {
+                    if (k > 0) go = persist_wait(pa.cols_done + (k - 1) * pa.cb + cl, pa.n_strips, pa);
+                } else {
+                    go = persist_wait(pa.rows_done + k * pa.cb + cl, pa.n_stripes + pa.rows_extra, pa);
+                    if (go && k > 0 && pa.chunks[k - 1].z == pa.chunks[k].z)
+                        go = persist_wait(pa.cols_done + (k - 1) * pa.cb + cl, pa.n_strips, pa);
+                }
+                if (!go) atomicCAS(pa.status, 0, 1);
+            }
+            s_w = w;
+            s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const int4 w = s_w;
+        const int4 ch = pa.chunks[w.x];
+        if (w.y == 0) {
+            GridArgs g = pa.g;
+            g.t0 = ch.x;
+            g.nt = ch.y;
+            g.c0 = ch.z;
+            g.nc = ch.w;
+            grid_rows<N, P, TB, false, false, CPL, WIDE>(g, w.z, w.w, pa.n_stripes);
+        } else {
+            ColArgs ca = pa.ca;
+            ca.nt = ch.y;
+            ca.c0 = ch.z;
+            ca.nc = ch.w;
+            cols_acc<N, P, false, false>(ca, w.z, w.w);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd((w.y == 0 ? pa.rows_done : pa.cols_done) + w.x * pa.cb + w.w, 1);
+    }
+}
+
+template <int N, int P, int CPL, bool WIDE>
+cudaError_t launch_persist_t(const PersistArgs &pa, size_t smem, int sms, cudaStream_t st) {
+    auto k = k_image_persist<N, P, 4, CPL, WIDE>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBlock, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::max(1, std::min(pa.n_items, per_sm * sms));
+    k<<<grid, kBlock, smem, st>>>(pa);
+    return cudaGetLastError();
+}
+
+// The persistent launch runs the gridding shape with 4 samples per pass and kernel entries read
+// through L2; CPL and wide stripes as the plan chose them.
+template <int N, int P>
+cudaError_t launch_persist_p(int cpl, bool wide, const PersistArgs &pa, size_t smem, int sms, cudaStream_t st) {
+    if (cpl == 4) {
+        if constexpr (GridShape<N, P, 4, true>::ROWS % 2 == 0 && GridShape<N, P, 4, false>::ROWS % 2 == 0)
+            return wide ? launch_persist_t<N, P, 4, true>(pa, smem, sms, st) : launch_persist_t<N, P, 4, false>(pa, smem, sms, st);
+        return cudaErrorInvalidValue;
+    }
+    if (cpl == 2)
+        return wide ? launch_persist_t<N, P, 2, true>(pa, smem, sms, st) : launch_persist_t<N, P, 2, false>(pa, smem, sms, st);
+    return wide ? launch_persist_t<N, P, 1, true>(pa, smem, sms, st) : launch_persist_t<N, P, 1, false>(pa, smem, sms, st);
+}
+
+#define MOFF_DEFINE_PERSIST_N(NN)                                                                    \
+    cudaError_t launch_persist_n##NN(int P, int cpl, bool wide, const PersistArgs &pa, size_t smem, int sms, \
+                                     cudaStream_t st) {                                             \
+        return P == 1 ? launch_persist_p<NN, 1>(cpl, wide, pa, smem, sms, st)                       \
+                      : launch_persist_p<NN, 2>(cpl, wide, pa, smem, sms, st);                      \
+    }
 
 template <int N>
 size_t col_smem_bytes_t(int P, bool h16 = false) {

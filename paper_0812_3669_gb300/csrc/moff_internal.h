@@ -151,6 +151,25 @@ struct ColArgs {
     int beam_kx[kMaxBeams], beam_ky[kMaxBeams];
 };
 
+// Batching pattern: one persistent launch over every (Tb, Cb) chunk of a block (k_image_persist;
+// the work-item queue, the dependencies and the bounded waits are described there).
+constexpr int kPersistMaxChunks = 128;
+struct PersistArgs {
+    GridArgs g;              // chunk-independent gridding arguments (t0 / nt / c0 / nc set per chunk)
+    ColArgs ca;              // chunk-independent column arguments
+    int n_chunks, n_items;
+    int n_stripes, n_strips; // row items and column items per channel of a chunk
+    int cb;                  // channel slots per chunk (the counters' row length)
+    int rows_extra;          // row items a column item waits for beyond n_stripes (0; tests only)
+    int *next;               // queue head
+    int *rows_done;          // [chunk][cb] finished row items
+    int *cols_done;          // [chunk][cb] finished column items
+    int *status;             // 0, or nonzero once a wait ran out of time
+    long long budget;        // clock64 cycles per wait
+    int4 chunks[kPersistMaxChunks];       // {t0, nt, c0, nc}, in the direct launches' order
+    int item0[kPersistMaxChunks + 1];     // first item of each chunk
+};
+
 // FP16 tensor-core gridding + row transform: per (pol, grid row, kx tile) a
 // product of the row's segment voltages with the segments' row spectra.
 struct RowSpecArgs {
@@ -380,7 +399,9 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
 #define MOFF_DECLARE_N(NN)                                                                          \
     cudaError_t launch_grid_n##NN(int P, int TB, bool staged, bool grid_only, const GridArgs &a, int n_stripes, \
                                   size_t smem, cudaStream_t st);                                   \
-    cudaError_t launch_cols_n##NN(int P, const ColArgs &a, cudaStream_t st, bool h16);
+    cudaError_t launch_cols_n##NN(int P, const ColArgs &a, cudaStream_t st, bool h16);            \
+    cudaError_t launch_persist_n##NN(int P, int cpl, bool wide, const PersistArgs &pa, size_t smem, int sms, \
+                                     cudaStream_t st);
 MOFF_DECLARE_N(32)
 MOFF_DECLARE_N(64)
 MOFF_DECLARE_N(128)
