@@ -675,8 +675,27 @@ def batching_leg(args, moff, synth, torch):
     tune_s = time.perf_counter() - t0
     v_batched = timed(batched)
     binfo, tuned = batched.info(), batched.tuning()
+    img_b = torch.empty((Cs, 4, N, N), dtype=torch.float32, device="cuda")
+    batched.read_image(out=img_b, reset=True)
     batched.close()
+    # every chunk of the block in one persistent launch (work queue, bounded dependency waits),
+    # autotuned among the shapes it is built for, replayed as a graph
+    t0 = time.perf_counter()
+    pers = moff.Plan(cfg["pos"], cfg["taps"], N, Cs, P, autotune=True, graph=True, persist=True)
+    ptune_s = time.perf_counter() - t0
+    v_pers = timed(pers)
+    pinfo2, ptuned = pers.info(), pers.tuning()
+    img_p = torch.empty((Cs, 4, N, N), dtype=torch.float32, device="cuda")
+    pers.read_image(out=img_p, reset=True)
+    pers.close()
+    pdiff = image_diff(torch, img_p, img_b)
+    del img_b, img_p
     return {"unit": UNIT, "channels": Cs, "samples": F, "dtype": "f32",
+            "persistent_graph": {"value": v_pers, "time_batch": ptuned["time_batch"],
+                                 "cells_per_lane": ptuned["cells_per_lane"], "wide_rows": ptuned["wide_rows"],
+                                 "tune_source": ptuned["source"], "plan_create_s": ptune_s,
+                                 "chan_chunk": pinfo2["chan_chunk"], "time_chunk": pinfo2["time_chunk"],
+                                 "launches_per_block": 1, "max_norm_diff_vs_batched_direct": pdiff},
             "plain_one_channel": {"value": v_plain, "chan_chunk": pinfo["chan_chunk"],
                                   "time_chunk": pinfo["time_chunk"]},
             "batched_rule_direct": {"value": v_direct, "time_batch": rule["time_batch"], "staged": rule["staged"],

@@ -93,9 +93,24 @@ enum {
                                  this array at plan creation; results are cached per array and
                                  device in the process and, if the environment variable
                                  MOFF_TUNE_CACHE names a file, in that file.  FP32 path only. */
-    MOFF_GRAPH = 1u << 5      /* launch each block's kernel sequence as one CUDA graph: captured
+    MOFF_GRAPH = 1u << 5,     /* launch each block's kernel sequence as one CUDA graph: captured
                                  the first time a (input buffer, scratch, block length) is seen,
                                  replayed afterwards (8 kept per plan).  Not used while timing is on. */
+    MOFF_PERSIST = 1u << 6    /* batching pattern (no counterpart in the paper): every channel and
+                                 pol of a block in ONE persistent launch (k_image_persist) whose CTAs
+                                 pull work items -- the gridding + row-transform stripes and the
+                                 column strips of each (samples x channels) chunk -- from a device
+                                 queue; an item waits, on one polling lane bounded by a clock64
+                                 budget (about 1 s), for the items it depends on, so chunks overlap
+                                 while the FP64 sums still fold in chunk order: the image equals the
+                                 direct launches' bit for bit.  A wait that runs out records a status
+                                 that the next moff_sync / moff_read_image returns as
+                                 MOFF_ETIMEDOUT.  FP32 path of an unserved plan only (MOFF_EINVAL
+                                 with MOFF_PREC_FP16TC or MOFF_SERVED); the gridding shape is 4
+                                 samples per pass with entries through L2 (MOFF_AUTOTUNE picks among
+                                 those).  Blocks with feedback calibration, beams or autocorrelation
+                                 subtraction on run the direct launches.  With MOFF_GRAPH the
+                                 persistent launch is what the graph replays. */
 };
 
 /*
@@ -361,7 +376,8 @@ moff_status moff_set_timing(moff_plan *plan, int on);
  *      8 taps writes stream-major and reorders to [F][C][A][P]),
  *   5  feedback-calibration correlation (when a calibrator is set),
  *   6  autocorrelation sums (when switched on),
- *   7  (tensor-core gridding route only) the row transform of the gridded field.
+ *   7  (tensor-core gridding route only) the row transform of the gridded field,
+ *   8  (MOFF_PERSIST) the persistent launch (kinds 1 and 2 of every chunk).
  * On the tensor-core gridding route kind 1 is the cell-tile gridding alone and
  * kind 3 writes the voltage planes it reads.
  * Waits for the recorded work.  total_ms / launches may be NULL.  reset = 1

@@ -25,7 +25,7 @@ __all__ = [
     "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
     "moff_plan_info", "moff_plan_route", "moff_voltage_planes", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
-    "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "moff_plan_tuning",
+    "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "MOFF_PERSIST", "moff_plan_tuning",
     "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
     "moff_server_destroy", "moff_set_calibrator", "moff_read_feedback", "moff_feedback_gains",
     "moff_set_autocorr", "moff_read_image_cross", "moff_set_beams", "moff_read_beams", "moff_set_channel_groups",
@@ -43,9 +43,10 @@ MOFF_JONES = 1 << 2
 MOFF_SERVED = 1 << 3
 MOFF_AUTOTUNE = 1 << 4
 MOFF_GRAPH = 1 << 5
+MOFF_PERSIST = 1 << 6
 
 KERNEL_KINDS = {0: "pfb_fstage", 1: "grid_rows", 2: "cols_integrate", 3: "volt_prep", 4: "fstage_reorder",
-                5: "feedback_corr", 6: "autocorr", 7: "row_transform"}
+                5: "feedback_corr", 6: "autocorr", 7: "row_transform", 8: "persistent"}
 
 STATUS = {0: "MOFF_OK", -1: "MOFF_EINVAL", -2: "MOFF_ENOMEM", -3: "MOFF_ECUDA",
           -4: "MOFF_ESTATE", -5: "MOFF_ETIMEDOUT", -6: "MOFF_EBUSY"}
@@ -491,9 +492,10 @@ class Plan:
     """One array's imaging plan (owns a ``moff_plan``)."""
 
     def __init__(self, pos, taps, grid_n, n_chan, n_pol, jones=False, fstage=False, stream=None, fp16tc=False,
-                 served=False, autotune=False, graph=False):
+                 served=False, autotune=False, graph=False, persist=False):
         flags = (MOFF_JONES if jones else 0) | (MOFF_FSTAGE if fstage else 0) | (MOFF_PREC_FP16TC if fp16tc else 0)
         flags |= (MOFF_SERVED if served else 0) | (MOFF_AUTOTUNE if autotune else 0) | (MOFF_GRAPH if graph else 0)
+        flags |= MOFF_PERSIST if persist else 0
         if stream is None:
             try:
                 import torch

@@ -304,6 +304,13 @@ struct moff_plan {
     struct GraphEnt { int kind; const void *in, *scratch; long long n, stride; cudaGraphExec_t exec; unsigned long long used; };
     std::vector<GraphEnt> gcache;
     unsigned long long gclock = 0;
+    // MOFF_PERSIST: each block's chunks in one persistent launch (k_image_persist)
+    bool persist = false;
+    size_t persist_smem = 0;
+    int *d_pq = nullptr;              // queue head, then rows_done and cols_done [kPersistMaxChunks][Cb]
+    long long persist_budget = 0;     // clock64 cycles per wait
+    int persist_extra = 0;            // tests only: row items a column item waits for beyond the real ones
+    int sms = 152;
     // MOFF_AUTOTUNE: how the gridding shape was chosen (0 rule, 1 measured, 2 cache)
     int tune_source = 0;
     double tune_best_ms = 0.0;
@@ -461,7 +468,8 @@ moff_status check_device_err(moff_plan *pl) {
     MOFF_CK(cudaMemcpy(&h, pl->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h) {
         MOFF_CK(cudaMemset(pl->d_err, 0, sizeof(int)));
-        return fail(MOFF_ETIMEDOUT, "a tensor-core completion wait inside a kernel ran out of time");
+        return fail(MOFF_ETIMEDOUT, "a bounded wait inside a kernel ran out of time (tensor-core completion or "
+                                    "persistent work-queue dependency)");
     }
     return MOFF_OK;
 }
@@ -871,10 +879,58 @@ moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long l
     return MOFF_OK;
 }
 
+// Batching pattern: the block's (Tb, Cb) chunks, in the direct launches' order, as the work items
+// of one persistent launch (k_image_persist; up to kPersistMaxChunks chunks per launch).
+moff_status run_image_persist(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
+    std::vector<int4> chunks;
+    for (int c0 = 0; c0 < pl->C; c0 += pl->Cb)
+        for (int t0 = 0; t0 < n_time; t0 += pl->Tb)
+            chunks.push_back(make_int4(t0, std::min(pl->Tb, n_time - t0), c0, std::min(pl->Cb, pl->C - c0)));
+    const int cpl = pl->quads ? 4 : (pl->pairs ? 2 : 1);
+    const int n_strips = pl->N / col_width(pl->N);
+    for (size_t k0 = 0; k0 < chunks.size(); k0 += kPersistMaxChunks) {
+        const int nch = (int)std::min<size_t>(kPersistMaxChunks, chunks.size() - k0);
+        PersistArgs pa{};
+        pa.g = grid_args(pl, volt, tstride, 0, 0, 0, 0);
+        pa.ca.H = pl->d_H;
+        pa.ca.slab_t = pa.g.slab_t;
+        pa.ca.slab_c = pa.g.slab_c;
+        pa.ca.twp = pl->d_twp;
+        pa.ca.acc = pl->d_acc;
+        pa.ca.row_nz = pl->d_row_nz;
+        pa.n_chunks = nch;
+        pa.n_stripes = pl->n_stripes;
+        pa.n_strips = n_strips;
+        pa.cb = pl->Cb;
+        pa.rows_extra = pl->persist_extra;
+        pa.next = pl->d_pq;
+        pa.rows_done = pl->d_pq + 1;
+        pa.cols_done = pl->d_pq + 1 + (size_t)kPersistMaxChunks * pl->Cb;
+        pa.status = pl->d_err;
+        pa.budget = pl->persist_budget;
+        int items = 0;
+        for (int k = 0; k < nch; ++k) {
+            pa.chunks[k] = chunks[k0 + k];
+            pa.item0[k] = items;
+            items += (pl->n_stripes + n_strips) * pa.chunks[k].w;
+        }
+        pa.item0[nch] = items;
+        pa.n_items = items;
+        MOFF_CK(cudaMemsetAsync(pl->d_pq, 0, sizeof(int), pl->st));
+        MOFF_CK(cudaMemsetAsync(pa.rows_done, 0, (size_t)nch * pl->Cb * sizeof(int), pl->st));
+        MOFF_CK(cudaMemsetAsync(pa.cols_done, 0, (size_t)nch * pl->Cb * sizeof(int), pl->st));
+        TimedLaunch tp(pl, 8);
+        MOFF_CK(launch_persist(pl->N, pl->P, cpl, pl->wide, pa, pl->persist_smem, pl->sms, pl->st));
+        tp.done();
+    }
+    return MOFF_OK;
+}
+
 moff_status run_image(moff_plan *pl, const uint8_t *volt, int n_time, long long tstride) {
     if (pl->gtc) return run_image_gtc(pl, volt, n_time, tstride);
     if (pl->dft) return run_image_dft(pl, volt, n_time, tstride);
     if (pl->tc) return run_image_tc(pl, volt, n_time, tstride);
+    if (pl->persist && !pl->fb_on && !pl->auto_on && pl->n_beam == 0) return run_image_persist(pl, volt, n_time, tstride);
     for (int c0 = 0; c0 < pl->C; c0 += pl->Cb) {
         if (moff_status w = chunk_ready(pl, c0); w != MOFF_OK) return w;
         const int nc = std::min(pl->Cb, pl->C - c0);
@@ -1683,7 +1739,8 @@ std::string tune_key(const moff_plan *pl, const double *pos, const float *taps) 
     h = fnv1a(prop.name, strlen(prop.name), h);
     char buf[128];
     // the prefix changes with the gridding kernels, so picks timed on an older build are not reused
-    snprintf(buf, sizeof buf, "%s-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx", pl->dft ? "gdft1" : "grid6", pl->A, pl->K,
+    snprintf(buf, sizeof buf, "%s-A%d-K%d-N%d-P%d-J%d-T%d-C%d-sm%d-%016llx",
+             pl->dft ? "gdft1" : (pl->persist ? "gpst1" : "grid6"), pl->A, pl->K,
              pl->N, pl->P, (int)pl->jones, pl->Tb, std::min(pl->Cb, pl->C), prop.multiProcessorCount,
              (unsigned long long)h);
     return buf;
@@ -1753,6 +1810,8 @@ moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridC
             // cand 0-7: staged x pairs x wide; 8, 9: 2 x 2 blocks (entries through L2), without and with wide.
             // The tensor-core row transform: entries through L2, no wide stripes (cand 0, 2, 8).
             if (pl->dft && cand != 0 && cand != 2 && cand != 8) continue;
+            // the persistent launch is built for 4 samples per pass with entries through L2
+            if (pl->persist && (tb != 4 || (cand < 8 && (cand & 1)))) continue;
             const GridChoice ch = cand < 8 ? GridChoice{tb, (cand & 1) != 0, (cand & 2) != 0, (cand & 4) != 0, false}
                                            : GridChoice{tb, false, false, cand == 9, true};
             moff_plan tmp;
@@ -1972,8 +2031,11 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         return fail(MOFF_EINVAL, "ksize (%d) must be odd, in [1, 15] and <= grid_n", ksize);
     if (n_chan < 1) return fail(MOFF_EINVAL, "n_chan (%d) must be >= 1", n_chan);
     if (n_pol != 1 && n_pol != 2) return fail(MOFF_EINVAL, "n_pol (%d) must be 1 or 2", n_pol);
-    if (flags & ~(unsigned)(MOFF_FSTAGE | MOFF_JONES | MOFF_PREC_FP16TC | MOFF_SERVED | MOFF_AUTOTUNE | MOFF_GRAPH))
+    if (flags & ~(unsigned)(MOFF_FSTAGE | MOFF_JONES | MOFF_PREC_FP16TC | MOFF_SERVED | MOFF_AUTOTUNE | MOFF_GRAPH |
+                            MOFF_PERSIST))
         return fail(MOFF_EINVAL, "unknown flag bits 0x%x", flags);
+    if ((flags & MOFF_PERSIST) && (flags & (MOFF_PREC_FP16TC | MOFF_SERVED)))
+        return fail(MOFF_EINVAL, "MOFF_PERSIST runs the FP32 path of an unserved plan");
     if ((flags & MOFF_JONES) && n_pol != 2) return fail(MOFF_EINVAL, "MOFF_JONES requires n_pol = 2");
     if ((flags & MOFF_FSTAGE) && (!is_pow2(n_chan) || n_chan < 32 || n_chan > 2048))
         return fail(MOFF_EINVAL, "with MOFF_FSTAGE n_chan (%d) must be a power of two in [32, 2048]", n_chan);
@@ -1990,6 +2052,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     pl->fstage = (flags & MOFF_FSTAGE) != 0;
     pl->tc = (flags & MOFF_PREC_FP16TC) != 0;
     pl->served = (flags & MOFF_SERVED) != 0;
+    pl->persist = (flags & MOFF_PERSIST) != 0;
     // FP16 path at N = 256 / 512: the row-spectrum contraction where the array's rows are sparse
     // enough for it, else (or with MOFF_TC_DFT=1) the factored DFT contractions
     RowSpec rs_probe;
@@ -2175,6 +2238,31 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             if ((s = tune_grid(pl, pos, taps, &tuned)) != MOFF_OK) return bail(s);
         }
         if ((s = bin_plan(pl, pos, taps, pl->tune_source ? &tuned : nullptr)) != MOFF_OK) return bail(s);
+        if (pl->persist && (pl->tb != 4 || pl->staged)) {
+            GridChoice ch{4, false, pl->pairs, pl->wide, pl->quads};
+            if ((s = bin_plan(pl, pos, taps, &ch)) != MOFF_OK) return bail(s);
+        }
+    }
+    if (pl->persist) {
+        pl->persist_smem = std::max(pl->grid_smem, col_smem_bytes(grid_n, n_pol));
+        if (pl->persist_smem > 227 * 1024)
+            return bail(fail(MOFF_EINVAL, "MOFF_PERSIST: the persistent kernel needs %zu bytes of shared memory",
+                             pl->persist_smem));
+        cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, pl->device);
+        const size_t nq = 1 + 2 * (size_t)kPersistMaxChunks * pl->Cb;
+        if ((s = palloc(pl, &pl->d_pq, nq * sizeof(int))) != MOFF_OK) return bail(s);
+        if (!pl->d_err) {
+            if ((s = palloc(pl, &pl->d_err, 16)) != MOFF_OK) return bail(s);
+            if (cudaMemset(pl->d_err, 0, 16) != cudaSuccess) return bail(fail(MOFF_ECUDA, "memset failed"));
+        }
+        // about one second of SM clock per wait (MOFF_PERSIST_BUDGET_US shortens it); MOFF_PERSIST_EXTRA
+        // (tests) makes column items wait for row items that do not exist, so their waits run out
+        double us = 1e6;
+        if (const char *e = getenv("MOFF_PERSIST_BUDGET_US")) us = std::max(1.0, atof(e));
+        int clk_khz = 2070000;
+        cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, pl->device);
+        pl->persist_budget = (long long)(us * 1e-3 * (double)std::max(clk_khz, 100000));
+        if (const char *e = getenv("MOFF_PERSIST_EXTRA")) pl->persist_extra = std::max(0, atoi(e));
     }
     if (pl->tc && !pl->dft) {
         RowSpec rs;
@@ -2354,7 +2442,7 @@ moff_status moff_submit(moff_plan *pl, const uint8_t *volt, int n_time, int on_d
         // blocks of several channel chunks are copied by channel segments that overlap the imaging
         // (not under graph replay, whose captured launches carry no per-segment waits)
         static const bool pipeline = !(getenv("MOFF_STAGE_PIPELINE") && atoi(getenv("MOFF_STAGE_PIPELINE")) == 0);
-        const bool by_chan = pipeline && !pl->graphs && pl->Cb < pl->C && bytes >= ((size_t)8 << 20);
+        const bool by_chan = pipeline && !pl->graphs && !pl->persist && pl->Cb < pl->C && bytes >= ((size_t)8 << 20);
         if ((s = by_chan ? stage_in_by_channels(pl, volt, n_time, &dev, &slot) : stage_in(pl, volt, bytes, &dev, &slot)) !=
             MOFF_OK)
             return s;
@@ -2821,7 +2909,7 @@ moff_status moff_set_timing(moff_plan *pl, int on) {
 moff_status moff_timing(moff_plan *pl, int kind, double *total_ms, long long *launches, int reset) {
     moff_status s = check_plan(pl);
     if (s != MOFF_OK) return s;
-    if (kind < 0 || kind > 7) return fail(MOFF_EINVAL, "kind (%d) must be in [0, 7]", kind);
+    if (kind < 0 || kind > 8) return fail(MOFF_EINVAL, "kind (%d) must be in [0, 8]", kind);
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
     double tot = 0.0;
     long long n = 0;

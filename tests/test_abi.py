@@ -42,7 +42,9 @@ def test_argument_errors_without_gpu(L):
         (4, 3, 32, 1, 1, 4),        # Jones with one pol
         (4, 3, 32, 24, 1, 2),       # F-stage with non power-of-two channels
         (4, 3, 32, 1, 1, 1 << 9),   # unknown flag
-        (4, 3, 32, 1, 1, 1 << 6),   # unknown flag next to MOFF_GRAPH
+        (4, 3, 32, 1, 1, 1 << 7),   # unknown flag next to MOFF_PERSIST
+        (4, 3, 32, 1, 1, (1 << 6) | 1),   # MOFF_PERSIST with MOFF_PREC_FP16TC
+        (4, 3, 32, 1, 1, (1 << 6) | 8),   # MOFF_PERSIST with MOFF_SERVED
     ]
     for (A, K, N, C, P, fl) in bad:
         st = L.moff_plan_create(ctypes.byref(out), A, pos.ctypes.data, K, taps.ctypes.data, N, C, P, fl, None)
