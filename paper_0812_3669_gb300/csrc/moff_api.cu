@@ -276,7 +276,8 @@ struct moff_plan {
     // (power of two: the gridded field times sy[c] * dft_s_t stays within FP16), and the
     // gridding kernel's shared memory for a grid-only (FP32 transform) launch
     bool dft = false;
-    unsigned char *d_dft_tab = nullptr;
+    unsigned char *d_dft_tab = nullptr;     // rows (gridding kernel, row transform)
+    unsigned char *d_dft_tab_c = nullptr;   // the column kernel's image
     float dft_s_t = 1.f;
     size_t grid_smem_fft = 0;
     // ... with the gridding on the tensor cores too (cell tiles; MOFF_TC_GRID=0 keeps the FP32 gather):
@@ -795,7 +796,7 @@ moff_status run_image_dft(moff_plan *pl, const uint8_t *volt, int n_time, long l
             ca.row_nz = pl->d_row_nz;
             ca.sy = pl->d_sy;
             ca.s_t = pl->dft_s_t;
-            ca.dft_tab = pl->d_dft_tab;
+            ca.dft_tab = pl->d_dft_tab_c;
             ca.err = pl->d_err;
             TimedLaunch tc(pl, 2);
             MOFF_CK(launch_cols_dft(pl->N, pl->P, ca, pl->st));
@@ -868,7 +869,7 @@ moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long l
             ca.row_nz = pl->d_row_nz;
             ca.sy = pl->d_sy;
             ca.s_t = pl->dft_s_t;
-            ca.dft_tab = pl->d_dft_tab;
+            ca.dft_tab = pl->d_dft_tab_c;
             ca.err = pl->d_err;
             TimedLaunch tc(pl, 2);
             MOFF_CK(launch_cols_dft(pl->N, pl->P, ca, pl->st));
@@ -2196,9 +2197,11 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     if (pl->dft) {
         // factored-DFT tables, and the kernel scale: every cell's sum of |tap| over its contributions
         // (all output pols) times dft_s_t is at most 1, so |G| sy[c] dft_s_t <= 2^14
-        std::vector<unsigned char> tab = build_dft_table(grid_n);
+        std::vector<unsigned char> tab = build_dft_table(grid_n), tabc = build_dft_table(grid_n, true);
         if ((s = palloc(pl, &pl->d_dft_tab, tab.size())) != MOFF_OK) return bail(s);
-        if (cudaMemcpy(pl->d_dft_tab, tab.data(), tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        if ((s = palloc(pl, &pl->d_dft_tab_c, tabc.size())) != MOFF_OK) return bail(s);
+        if (cudaMemcpy(pl->d_dft_tab, tab.data(), tab.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(pl->d_dft_tab_c, tabc.data(), tabc.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(MOFF_ECUDA, "tensor-core DFT table upload failed"));
         if (!pl->gtc) pl->dft_s_t = dft_kernel_scale(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps);
         if ((s = palloc(pl, &pl->d_sy, (size_t)n_chan * 4)) != MOFF_OK) return bail(s);

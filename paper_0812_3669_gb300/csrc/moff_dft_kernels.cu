@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kBlock, ColDftShape<N, P, W>::MINB) k_cols_dft
     unsigned char *sA1 = sA2 + P * CS::A2P;                      // [2 buffers][P][A1P]
     unsigned char *sTab = sA1 + 2 * P * CS::A1P;
     const unsigned char *sB1 = sTab, *sB2 = sTab + S::B1_BYTES;
-    const float2 *sTw = reinterpret_cast<const float2 *>(sB2 + S::B2_BYTES);
+    const float4 *sTw = reinterpret_cast<const float4 *>(sB2 + S::B2_BYTES);   // [c pair][b]
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sTab + S::TAB_BYTES);   // [0] stage 1, [1] stage 2
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
 
@@ -179,8 +179,10 @@ __global__ void __launch_bounds__(kBlock, ColDftShape<N, P, W>::MINB) k_cols_dft
         tc::mma_commit(&mbar[1]);
     };
     // Twiddle stage 1's result and write it as stage 2's A: thread (b, x) of tile (p, j) writes, for
-    // c = 8 ch .. 8 ch + 7 (one TMEM load of 16 columns each), the re piece at k = b and the im piece
-    // at k = N2 + b of row group m2 = 8 W ch + 8 x.
+    // c = 8 ch .. 8 ch + 7 (one TMEM load of 16 columns each: real parts, then imaginary parts), the
+    // re piece at k = b and the im piece at k = N2 + b of row group m2 = 8 W ch + 8 x.  Outputs c and
+    // c + 1 go through packed FP32 arithmetic as a pair (t = (re w, -im w) / 16 of both):
+    //   re = Xr re w - Xi im w,   im = Xi re w + Xr im w.
     auto epi1 = [&]() {
         for (int idx = warp >> 2; idx < P * CS::T1; idx += kBlock / 128) {
             const int p = idx / CS::T1, j = idx - p * CS::T1;
@@ -192,15 +194,14 @@ __global__ void __launch_bounds__(kBlock, ColDftShape<N, P, W>::MINB) k_cols_dft
                 tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(idx * S::C1 + 16 * ch), v);
                 uint32_t re[4], im[4];
 #pragma unroll
-                for (int i = 0; i < 8; i += 2) {
-                    const int cc = 8 * ch + i;
-                    const float2 t0 = sTw[cc * N2 + b], t1 = sTw[(cc + 1) * N2 + b];
-                    const float x0r = v[2 * i] * t0.x - v[2 * i + 1] * t0.y;
-                    const float x0i = v[2 * i] * t0.y + v[2 * i + 1] * t0.x;
-                    const float x1r = v[2 * i + 2] * t1.x - v[2 * i + 3] * t1.y;
-                    const float x1i = v[2 * i + 2] * t1.y + v[2 * i + 3] * t1.x;
-                    re[i >> 1] = dftc::pack_hh(x0r, x1r);
-                    im[i >> 1] = dftc::pack_hh(x0i, x1i);
+                for (int i = 0; i < 4; ++i) {
+                    const float4 t = sTw[(4 * ch + i) * N2 + b];
+                    const float2 xr = make_float2(v[2 * i], v[2 * i + 1]), xi = make_float2(v[8 + 2 * i], v[9 + 2 * i]);
+                    const float2 wr = make_float2(t.x, t.y), nwi = make_float2(t.z, t.w);
+                    const float2 yr = dftc::fma2(xi, nwi, dftc::mul2(xr, wr));
+                    const float2 yi = dftc::sub2(dftc::mul2(xi, wr), dftc::mul2(xr, nwi));
+                    re[i] = dftc::pack_hh(yr.x, yr.y);
+                    im[i] = dftc::pack_hh(yi.x, yi.y);
                 }
                 const int m2 = ch * 8 * W + x * 8;
                 const int hb = (m2 >> 6) * K2 * 128, cg = (m2 & 63) >> 3;
@@ -217,32 +218,37 @@ __global__ void __launch_bounds__(kBlock, ColDftShape<N, P, W>::MINB) k_cols_dft
     // + c_lo: pixels (ky = 8 c_hi + c_lo + 16 d, kx = x0 + x) for the group's d.
     const int g = warp >> 2;
     const int j2 = CS::T2 == 2 ? g : 0, dbase = CS::T2 == 2 ? 0 : g * ND;
-    float acc[NPROD][ND];
+    // sums of d and d + 1 side by side (packed FP32)
+    float2 acc[NPROD][ND / 2];
 #pragma unroll
     for (int pq = 0; pq < NPROD; ++pq)
 #pragma unroll
-        for (int d = 0; d < ND; ++d) acc[pq][d] = 0.f;
+        for (int d = 0; d < ND / 2; ++d) acc[pq][d] = make_float2(0.f, 0.f);
     auto epi2 = [&]() {
 #pragma unroll
-        for (int db = 0; db < ND / 8; ++db) {         // 8 d per TMEM load of each pol
+        for (int db = 0; db < ND / 8; ++db) {         // 8 d per TMEM load of each pol: real parts, then imaginary
             const uint32_t col = (uint32_t)(CS::D1 + j2 * C2 + 2 * dbase + 16 * db);
             float ex[16];
             tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + col, ex);
             if constexpr (P == 1) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    acc[0][8 * db + i] = fmaf(ex[2 * i], ex[2 * i], fmaf(ex[2 * i + 1], ex[2 * i + 1], acc[0][8 * db + i]));
+                for (int i = 0; i < 4; ++i) {
+                    const float2 xr = make_float2(ex[2 * i], ex[2 * i + 1]), xi = make_float2(ex[8 + 2 * i], ex[9 + 2 * i]);
+                    float2 &s0 = acc[0][4 * db + i];
+                    s0 = dftc::fma2(xr, xr, dftc::fma2(xi, xi, s0));
+                }
             } else {
                 float ey[16];
                 tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + col + (uint32_t)(CS::T2 * C2), ey);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float xr = ex[2 * i], xi = ex[2 * i + 1], yr = ey[2 * i], yi = ey[2 * i + 1];
-                    const int d = 8 * db + i;
-                    acc[0][d] = fmaf(xr, xr, fmaf(xi, xi, acc[0][d]));
-                    acc[1][d] = fmaf(yr, yr, fmaf(yi, yi, acc[1][d]));
-                    acc[2][d] = fmaf(xr, yr, fmaf(xi, yi, acc[2][d]));
-                    acc[3][d] = fmaf(xi, yr, fmaf(-xr, yi, acc[3][d]));
+                for (int i = 0; i < 4; ++i) {
+                    const float2 xr = make_float2(ex[2 * i], ex[2 * i + 1]), xi = make_float2(ex[8 + 2 * i], ex[9 + 2 * i]);
+                    const float2 yr = make_float2(ey[2 * i], ey[2 * i + 1]), yi = make_float2(ey[8 + 2 * i], ey[9 + 2 * i]);
+                    const int dp = 4 * db + i;
+                    acc[0][dp] = dftc::fma2(xr, xr, dftc::fma2(xi, xi, acc[0][dp]));
+                    acc[1][dp] = dftc::fma2(yr, yr, dftc::fma2(yi, yi, acc[1][dp]));
+                    acc[2][dp] = dftc::fma2(xr, yr, dftc::fma2(xi, yi, acc[2][dp]));
+                    acc[3][dp] = dftc::sub2(dftc::fma2(xi, yr, acc[3][dp]), dftc::mul2(xr, yi));
                 }
             }
         }
@@ -292,7 +298,8 @@ __global__ void __launch_bounds__(kBlock, ColDftShape<N, P, W>::MINB) k_cols_dft
         for (int pq = 0; pq < NPROD; ++pq) {
             double *dst = a.acc + ((long long)c * NPROD + pq) * N * N + x0 + x;
 #pragma unroll
-            for (int d = 0; d < ND; ++d) dst[(long long)(cy + 16 * (dbase + d)) * N] += (double)acc[pq][d] * sc2;
+            for (int d = 0; d < ND; ++d)
+                dst[(long long)(cy + 16 * (dbase + d)) * N] += (double)((d & 1) ? acc[pq][d >> 1].y : acc[pq][d >> 1].x) * sc2;
         }
     } else if (tid == 0) {
         atomicExch(a.err, tc::kErrWaitTimeout);
@@ -564,39 +571,50 @@ int cols_dft_width() {
 // B1 [n = 2c + re/im][k = 2a + re/im] = the real form of exp(+2 pi i a c / 16);
 // B2 [n = 2d + re/im][k = re/im N2 + b] = that of exp(+2 pi i b d / N2) (both K-major
 // images); twiddles [c][b] = exp(+2 pi i b c / N) / 16.  All in FP64, then rounded once.
-std::vector<unsigned char> build_dft_table(int N) {
+// cols: the column kernel's image.  Output columns grouped by eight: n = 16 (c / 8) + 8 re/im
+// + c mod 8 (and the same for d), so one 16-column TMEM load returns the real parts of eight
+// outputs, then their imaginary parts, and neighbouring outputs pair up for packed FP32 arithmetic;
+// twiddles as float4 (re w_c, re w_{c+1}, -im w_c, -im w_{c+1}) / 16 per (c pair, b).
+std::vector<unsigned char> build_dft_table(int N, bool cols) {
     const int N2 = N / 16, K2 = 2 * N2;
     std::vector<unsigned char> img((size_t)dft_table_bytes(N), 0);
     auto put = [&](size_t off, double v) {
         const __half h = __float2half_rn((float)v);
         std::memcpy(img.data() + off, &h, 2);
     };
+    auto col = [&](int o, int ri) { return cols ? 16 * (o >> 3) + 8 * ri + (o & 7) : 2 * o + ri; };
     for (int cc = 0; cc < 16; ++cc)
         for (int aa = 0; aa < 16; ++aa) {
             double wc, ws;
             unit_root((long long)aa * cc, 16, &wc, &ws);
-            put(kmajor_at(2 * cc, 2 * aa, 32), wc);
-            put(kmajor_at(2 * cc, 2 * aa + 1, 32), -ws);
-            put(kmajor_at(2 * cc + 1, 2 * aa, 32), ws);
-            put(kmajor_at(2 * cc + 1, 2 * aa + 1, 32), wc);
+            put(kmajor_at(col(cc, 0), 2 * aa, 32), wc);
+            put(kmajor_at(col(cc, 0), 2 * aa + 1, 32), -ws);
+            put(kmajor_at(col(cc, 1), 2 * aa, 32), ws);
+            put(kmajor_at(col(cc, 1), 2 * aa + 1, 32), wc);
         }
     const size_t b2 = 2048;
     for (int d = 0; d < N2; ++d)
         for (int b = 0; b < N2; ++b) {
             double vc, vs;
             unit_root((long long)b * d, N2, &vc, &vs);
-            put(b2 + kmajor_at(2 * d, b, K2), vc);
-            put(b2 + kmajor_at(2 * d, N2 + b, K2), -vs);
-            put(b2 + kmajor_at(2 * d + 1, b, K2), vs);
-            put(b2 + kmajor_at(2 * d + 1, N2 + b, K2), vc);
+            put(b2 + kmajor_at(col(d, 0), b, K2), vc);
+            put(b2 + kmajor_at(col(d, 0), N2 + b, K2), -vs);
+            put(b2 + kmajor_at(col(d, 1), b, K2), vs);
+            put(b2 + kmajor_at(col(d, 1), N2 + b, K2), vc);
         }
     const size_t tw = b2 + (size_t)K2 * K2 * 2;
     for (int cc = 0; cc < 16; ++cc)
         for (int b = 0; b < N2; ++b) {
             double wc, ws;
             unit_root((long long)b * cc, N, &wc, &ws);
-            const float2 v = make_float2((float)(wc / 16.0), (float)(ws / 16.0));
-            std::memcpy(img.data() + tw + ((size_t)cc * N2 + b) * 8, &v, 8);
+            if (cols) {
+                float *q = reinterpret_cast<float *>(img.data() + tw + ((size_t)(cc >> 1) * N2 + b) * 16);
+                q[cc & 1] = (float)(wc / 16.0);
+                q[2 + (cc & 1)] = (float)(-ws / 16.0);
+            } else {
+                const float2 v = make_float2((float)(wc / 16.0), (float)(ws / 16.0));
+                std::memcpy(img.data() + tw + ((size_t)cc * N2 + b) * 8, &v, 8);
+            }
         }
     return img;
 }

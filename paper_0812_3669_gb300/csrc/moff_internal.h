@@ -340,7 +340,8 @@ size_t pfb_smem_bytes(int CN);
 // N-point transform (B1 | B2 | twiddles; built in FP64), the column kernel, and the
 // gridding kernel with the row transform on the tensor cores (TB, CPL as the plain one;
 // entries through L2, stripes of grid_fft_rows(N) rows).
-std::vector<unsigned char> build_dft_table(int N);
+// cols = true: the column kernel's image (outputs grouped by eight for packed FP32 epilogues).
+std::vector<unsigned char> build_dft_table(int N, bool cols = false);
 float dft_kernel_scale(int A, int K, int N, int P, bool jones, const double *pos, const float *taps);
 size_t cols_dft_smem_bytes(int N, int P);
 cudaError_t launch_cols_dft(int N, int P, const ColDftArgs &a, cudaStream_t st);
