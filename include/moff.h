@@ -354,6 +354,15 @@ moff_status moff_read_beams(moff_plan *plan, float *out, int *n_time, int timeou
  * 1); wide_rows = 1 if twice the usual number of grid rows is transformed per
  * pass (more gather work between barriers).
  */
+/*
+ * moff_plan_dft_tuning -- the dense FP16 routes' column kernel (any pointer may
+ * be NULL): cols_width = columns per CTA (8: two CTAs per SM; 16: one; 0 on
+ * other routes), source = 0 default (environment variable MOFF_COLS_W=16 picks
+ * 16), 1 measured by MOFF_AUTOTUNE at creation on one chunk of the plan's shape;
+ * ms_w8 / ms_w16 = the measured times per chunk (source 1).
+ */
+moff_status moff_plan_dft_tuning(const moff_plan *plan, int *cols_width, int *source, double *ms_w8, double *ms_w16);
+
 moff_status moff_plan_tuning(const moff_plan *plan, int *time_batch, int *staged, int *cells_per_lane,
                              int *source, double *best_ms, int *wide_rows);
 

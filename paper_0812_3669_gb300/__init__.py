@@ -25,7 +25,7 @@ __all__ = [
     "moff_plan_create", "moff_set_gains", "moff_set_fstage", "moff_submit", "moff_submit_adc",
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
     "moff_plan_info", "moff_plan_route", "moff_voltage_planes", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
-    "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "MOFF_PERSIST", "moff_plan_tuning",
+    "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "MOFF_PERSIST", "moff_plan_tuning", "moff_plan_dft_tuning",
     "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
     "moff_server_destroy", "moff_set_calibrator", "moff_read_feedback", "moff_feedback_gains",
     "moff_set_autocorr", "moff_read_image_cross", "moff_set_beams", "moff_read_beams", "moff_set_channel_groups",
@@ -97,6 +97,8 @@ _SIGS = {
     "moff_feedback_gains": [_vp, _vp, _i],
     "moff_plan_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)],
+    "moff_plan_dft_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)],
 }
 
 
@@ -284,6 +286,13 @@ def moff_plan_tuning(plan):
     return dict(time_batch=a.value, staged=b.value, cells_per_lane=p.value, cell_pairs=int(p.value == 2),
                 source=c.value, best_ms=d.value,
                 wide_rows=w.value)
+
+
+def moff_plan_dft_tuning(plan):
+    w, src = ctypes.c_int(), ctypes.c_int()
+    m8, m16 = ctypes.c_double(), ctypes.c_double()
+    _check(lib().moff_plan_dft_tuning(plan, ctypes.byref(w), ctypes.byref(src), ctypes.byref(m8), ctypes.byref(m16)))
+    return dict(cols_width=w.value, source=src.value, ms_w8=m8.value, ms_w16=m16.value)
 
 
 def moff_set_calibrator(plan, kx, ky):
@@ -569,6 +578,9 @@ class Plan:
 
     def tuning(self):
         return moff_plan_tuning(self.handle)
+
+    def dft_tuning(self):
+        return moff_plan_dft_tuning(self.handle)
 
     def set_calibrator(self, kx, ky):
         moff_set_calibrator(self.handle, kx, ky)

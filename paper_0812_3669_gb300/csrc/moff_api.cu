@@ -278,6 +278,9 @@ struct moff_plan {
     bool dft = false;
     unsigned char *d_dft_tab = nullptr;     // rows (gridding kernel, row transform)
     unsigned char *d_dft_tab_c = nullptr;   // the column kernel's image
+    int cols_w = 8;                         // columns per CTA of k_cols_dft
+    int cols_w_source = 0;                  // 0 default, 1 measured (MOFF_AUTOTUNE)
+    double cols_w_ms[2] = {0.0, 0.0};       // measured ms per chunk at W = 8, 16
     float dft_s_t = 1.f;
     size_t grid_smem_fft = 0;
     // ... with the gridding on the tensor cores too (cell tiles; MOFF_TC_GRID=0 keeps the FP32 gather):
@@ -799,7 +802,7 @@ moff_status run_image_dft(moff_plan *pl, const uint8_t *volt, int n_time, long l
             ca.dft_tab = pl->d_dft_tab_c;
             ca.err = pl->d_err;
             TimedLaunch tc(pl, 2);
-            MOFF_CK(launch_cols_dft(pl->N, pl->P, ca, pl->st));
+            MOFF_CK(launch_cols_dft(pl->N, pl->P, pl->cols_w, ca, pl->st));
             tc.done();
             MOFF_CK_S(run_feedback(pl, volt, tstride, t0, nt, c0, nc));
         }
@@ -872,7 +875,7 @@ moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long l
             ca.dft_tab = pl->d_dft_tab_c;
             ca.err = pl->d_err;
             TimedLaunch tc(pl, 2);
-            MOFF_CK(launch_cols_dft(pl->N, pl->P, ca, pl->st));
+            MOFF_CK(launch_cols_dft(pl->N, pl->P, pl->cols_w, ca, pl->st));
             tc.done();
             MOFF_CK_S(run_feedback(pl, volt, tstride, t0, nt, c0, nc));
         }
@@ -1747,6 +1750,50 @@ std::string tune_key(const moff_plan *pl, const double *pos, const float *taps) 
     return buf;
 }
 
+// MOFF_AUTOTUNE on the dense FP16 routes: the column kernel's width (8 or 16 columns per CTA)
+// timed on one chunk of the plan's own shape over a zeroed field (it adds zeros to the
+// accumulators, which are cleared afterwards anyway).
+moff_status tune_cols_width(moff_plan *pl) {
+    if (!pl->d_H || cols_dft_width_forced()) return MOFF_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(MOFF_ECUDA, "event creation failed");
+    }
+    ColDftArgs ca{};
+    ca.H = reinterpret_cast<const __half *>(pl->d_H);
+    ca.slab_t = 1;
+    ca.slab_c = pl->Tb;
+    ca.nt = pl->Tb;
+    ca.c0 = 0;
+    ca.nc = std::min(pl->Cb, pl->C);
+    ca.acc = pl->d_acc;
+    ca.row_nz = pl->d_row_nz;
+    ca.sy = pl->d_sy;
+    ca.s_t = pl->dft_s_t;
+    ca.dft_tab = pl->d_dft_tab_c;
+    ca.err = pl->d_err;
+    cudaError_t e = cudaMemsetAsync(pl->d_H, 0, pl->h_bytes, pl->st);
+    const int ws[2] = {8, 16};
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = launch_cols_dft(pl->N, pl->P, ws[i], ca, pl->st);                  // warm
+        if (e == cudaSuccess) e = cudaEventRecord(e0, pl->st);
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_cols_dft(pl->N, pl->P, ws[i], ca, pl->st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, pl->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        pl->cols_w_ms[i] = ms / 2.0;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_acc, 0, (size_t)pl->C * pl->nprod * pl->N * pl->N * 8, pl->st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(MOFF_ECUDA, "column-kernel tuning failed: %s", cudaGetErrorString(e));
+    pl->cols_w = pl->cols_w_ms[1] < pl->cols_w_ms[0] ? 16 : 8;
+    pl->cols_w_source = 1;
+    return check_device_err(pl);
+}
+
 moff_status tune_grid(moff_plan *pl, const double *pos, const float *taps, GridChoice *out) {
     const std::string key = tune_key(pl, pos, taps);
     const char *path = getenv("MOFF_TUNE_CACHE");
@@ -2245,6 +2292,10 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             GridChoice ch{4, false, pl->pairs, pl->wide, pl->quads};
             if ((s = bin_plan(pl, pos, taps, &ch)) != MOFF_OK) return bail(s);
         }
+    }
+    if (pl->dft) {   // the column kernel's width: the default, or timed (needs the plan's reached-row mask)
+        pl->cols_w = cols_dft_width();
+        if ((flags & MOFF_AUTOTUNE) && (s = tune_cols_width(pl)) != MOFF_OK) return bail(s);
     }
     if (pl->persist) {
         pl->persist_smem = std::max(pl->grid_smem, col_smem_bytes(grid_n, n_pol));
@@ -2897,6 +2948,16 @@ moff_status moff_plan_tuning(const moff_plan *pl, int *time_batch, int *staged, 
     if (source) *source = pl->tune_source;
     if (best_ms) *best_ms = pl->tune_best_ms;
     if (wide_rows) *wide_rows = pl->wide ? 1 : 0;
+    return MOFF_OK;
+}
+
+moff_status moff_plan_dft_tuning(const moff_plan *pl, int *cols_width, int *source, double *ms_w8, double *ms_w16) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (cols_width) *cols_width = pl->dft ? pl->cols_w : 0;
+    if (source) *source = pl->cols_w_source;
+    if (ms_w8) *ms_w8 = pl->cols_w_ms[0];
+    if (ms_w16) *ms_w16 = pl->cols_w_ms[1];
     return MOFF_OK;
 }
 

@@ -559,12 +559,7 @@ cudaError_t launch_cols_dft_t(const ColDftArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Columns per CTA: 8 (two CTAs per SM, so one CTA's epilogue runs while the other waits on its
-// MMAs) unless MOFF_COLS_W=16 (one CTA per SM).
-int cols_dft_width() {
-    static const int w = (getenv("MOFF_COLS_W") && atoi(getenv("MOFF_COLS_W")) == 16) ? 16 : 8;
-    return w;
-}
+
 
 }  // namespace
 
@@ -619,8 +614,13 @@ std::vector<unsigned char> build_dft_table(int N, bool cols) {
     return img;
 }
 
-size_t cols_dft_smem_bytes(int N, int P) {
-    if (cols_dft_width() == 16) {
+// Columns per CTA by default: 8 (two CTAs per SM, so one CTA's epilogue runs while the other
+// waits on its MMAs) unless MOFF_COLS_W=16 (one CTA per SM); MOFF_AUTOTUNE times both.
+int cols_dft_width() { return (getenv("MOFF_COLS_W") && atoi(getenv("MOFF_COLS_W")) == 16) ? 16 : 8; }
+bool cols_dft_width_forced() { return getenv("MOFF_COLS_W") != nullptr; }
+
+size_t cols_dft_smem_bytes(int N, int P, int W) {
+    if (W == 16) {
         if (N == 512) return P == 1 ? ColDftShape<512, 1, 16>::SMEM : ColDftShape<512, 2, 16>::SMEM;
         if (N == 256) return P == 1 ? ColDftShape<256, 1, 16>::SMEM : ColDftShape<256, 2, 16>::SMEM;
     } else {
@@ -630,8 +630,8 @@ size_t cols_dft_smem_bytes(int N, int P) {
     return 0;
 }
 
-cudaError_t launch_cols_dft(int N, int P, const ColDftArgs &a, cudaStream_t st) {
-    if (cols_dft_width() == 16) {
+cudaError_t launch_cols_dft(int N, int P, int W, const ColDftArgs &a, cudaStream_t st) {
+    if (W == 16) {
         if (N == 512) return P == 1 ? launch_cols_dft_t<512, 1, 16>(a, st) : launch_cols_dft_t<512, 2, 16>(a, st);
         if (N == 256) return P == 1 ? launch_cols_dft_t<256, 1, 16>(a, st) : launch_cols_dft_t<256, 2, 16>(a, st);
     } else {

@@ -343,8 +343,11 @@ size_t pfb_smem_bytes(int CN);
 // cols = true: the column kernel's image (outputs grouped by eight for packed FP32 epilogues).
 std::vector<unsigned char> build_dft_table(int N, bool cols = false);
 float dft_kernel_scale(int A, int K, int N, int P, bool jones, const double *pos, const float *taps);
-size_t cols_dft_smem_bytes(int N, int P);
-cudaError_t launch_cols_dft(int N, int P, const ColDftArgs &a, cudaStream_t st);
+// W = columns per CTA of the column kernel (8 or 16).
+size_t cols_dft_smem_bytes(int N, int P, int W);
+cudaError_t launch_cols_dft(int N, int P, int W, const ColDftArgs &a, cudaStream_t st);
+int cols_dft_width();            // the default W (MOFF_COLS_W=16 selects 16)
+bool cols_dft_width_forced();    // MOFF_COLS_W set: the autotuner keeps it
 cudaError_t launch_grid_dft(int N, int P, int TB, int CPL, const GridArgs &a, int n_stripes, size_t smem,
                             cudaStream_t st);
 cudaError_t launch_grid_dft_n256(int P, int TB, int CPL, const GridArgs &a, int n_stripes, size_t smem, cudaStream_t st);

@@ -149,3 +149,31 @@ def test_dft_route_autotuned_shape(monkeypatch):
         pl.submit(np.ascontiguousarray(codes))
         img, _ = pl.read_image()
     check(img, oracle.moff_image(codes, gains, pos, taps, 512, 2), "autotuned N=512")
+
+
+def test_autotuner_picks_the_column_kernel_width(monkeypatch):
+    """MOFF_AUTOTUNE times the column kernel at 8 and 16 columns per CTA on the plan's
+    chunk and keeps the faster; the image is within the tolerance either way, and the
+    two widths give the same image up to the order of FP32 sums (bit-identical here:
+    each pixel's sums run in the same order at both widths)."""
+    monkeypatch.setenv("MOFF_TC_DFT", "1")
+    monkeypatch.delenv("MOFF_COLS_W", raising=False)
+    pos, taps, codes, gains = case(790, 220, 256, 5, 2, C=3, T=20)
+    with moff.Plan(pos, taps, 256, 3, 2, fp16tc=True, autotune=True) as pl:
+        assert pl.route() in ROUTES
+        t = pl.dft_tuning()
+        assert t["source"] == 1 and t["cols_width"] in (8, 16) and t["ms_w8"] > 0 and t["ms_w16"] > 0, t
+        assert t["cols_width"] == (16 if t["ms_w16"] < t["ms_w8"] else 8)
+        pl.set_gains(gains)
+        pl.submit(np.ascontiguousarray(codes))
+        img, n = pl.read_image()
+    check(img, oracle.moff_image(codes, gains, pos, taps, 256, 2), f"autotuned column width {t['cols_width']}")
+    imgs = {}
+    for w in (8, 16):
+        monkeypatch.setenv("MOFF_COLS_W", str(w))
+        with moff.Plan(pos, taps, 256, 3, 2, fp16tc=True) as pl:
+            assert pl.dft_tuning()["cols_width"] == w
+            pl.set_gains(gains)
+            pl.submit(np.ascontiguousarray(codes))
+            imgs[w], _ = pl.read_image()
+    assert np.array_equal(imgs[8], imgs[16])
