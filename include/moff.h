@@ -434,7 +434,9 @@ moff_status moff_image_noalloc(int n_ant, const double *pos, int ksize, const fl
 
 /*
  * moff_voltage_planes -- diagnostic (the paper has no counterpart): the FP16
- * voltage planes the row-spectrum tensor-core route builds for one channel
+ * voltage planes the row-spectrum or the tensor-core gridding route builds for
+ * one channel (on the latter, rows copied for wrapping kernel windows must equal
+ * their originals: MOFF_ECUDA otherwise)
  * (Eq. m6 step 1: each 4-bit voltage decoded, times its gain, times the
  * channel's power-of-two scale, rounded to FP16), read back so the decoding can
  * be checked bit for bit.
@@ -443,8 +445,8 @@ moff_status moff_image_noalloc(int n_ant, const double *pos, int ksize, const fl
  *   out      host float32 complex [n_time][A][P][2]: the FP16 plane values,
  *            converted exactly, in voltage order.
  *   scale    the channel's power-of-two scale (may be NULL).
- * Synchronous.  MOFF_EINVAL unless the plan takes the row-spectrum route
- * (moff_plan_route = 1) and is not served.
+ * Synchronous.  MOFF_EINVAL unless the plan takes the row-spectrum or the
+ * tensor-core gridding route (moff_plan_route = 1 or 3) and is not served.
  */
 moff_status moff_voltage_planes(moff_plan *plan, const uint8_t *volt, int n_time, int on_device, int chan,
                                 float *out, float *scale);

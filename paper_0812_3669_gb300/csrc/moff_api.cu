@@ -2686,12 +2686,17 @@ moff_status moff_voltage_planes(moff_plan *pl, const uint8_t *volt, int n_time, 
                                 float *scale) {
     moff_status s = check_unserved(pl);
     if (s != MOFF_OK) return s;
-    if (!pl->tc || pl->dft)
-        return fail(MOFF_EINVAL, "voltage planes exist only on the row-spectrum tensor-core route");
+    if (!pl->tc || (pl->dft && !pl->gtc))
+        return fail(MOFF_EINVAL, "voltage planes exist only on the row-spectrum and tensor-core gridding routes");
     if (!volt || !out) return fail(MOFF_EINVAL, "volt and out must not be NULL");
     if (n_time < 1 || n_time > pl->Tb) return fail(MOFF_EINVAL, "n_time (%d) must be in [1, %d]", n_time, pl->Tb);
     if (chan < 0 || chan >= pl->C) return fail(MOFF_EINVAL, "chan (%d) out of range [0, %d)", chan, pl->C);
-    const int AP = pl->A * pl->P, APpad = AP + kRowSpecPad;
+    // row-spectrum route: one plane row per antenna-pol; tensor-core gridding route: raster order of
+    // the anchors plus copies of the rows whose kernel window wraps (every copy written out again)
+    const int AP = pl->A * pl->P;
+    const bool gt = pl->gtc;
+    const int APpad = gt ? pl->gt_rows : AP + kRowSpecPad, nrows = gt ? pl->gt_rows - kRowSpecPad : AP;
+    const int *dperm = gt ? pl->d_gt_perm : pl->d_rs_perm;
     const long long tstride = (long long)pl->C * AP;
     const uint8_t *src = volt;
     int slot = -1;
@@ -2700,22 +2705,26 @@ moff_status moff_voltage_planes(moff_plan *pl, const uint8_t *volt, int n_time, 
         if ((s = stage_in(pl, volt, (size_t)n_time * tstride, &dev, &slot)) != MOFF_OK) return s;
         src = reinterpret_cast<const uint8_t *>(dev);
     }
-    MOFF_CK(launch_volt_prep(src, tstride, 0, n_time, chan, 1, AP, APpad, pl->d_gains, pl->d_sy, pl->d_rs_perm, pl->Tb,
-                             pl->d_yre, pl->d_yim, pl->st));
+    MOFF_CK(launch_volt_prep(src, tstride, 0, n_time, chan, 1, AP, APpad, pl->d_gains, pl->d_sy, dperm, pl->Tb,
+                             pl->d_yre, pl->d_yim, pl->st, nrows));
     if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
-    std::vector<__half> re((size_t)AP * pl->Tb), im((size_t)AP * pl->Tb);
-    std::vector<int> perm(AP);
+    std::vector<__half> re((size_t)nrows * pl->Tb), im((size_t)nrows * pl->Tb);
+    std::vector<int> perm(nrows);
     float sy = 0.f;
     MOFF_CK(cudaMemcpyAsync(re.data(), pl->d_yre, re.size() * 2, cudaMemcpyDeviceToHost, pl->st));
     MOFF_CK(cudaMemcpyAsync(im.data(), pl->d_yim, im.size() * 2, cudaMemcpyDeviceToHost, pl->st));
-    MOFF_CK(cudaMemcpyAsync(perm.data(), pl->d_rs_perm, (size_t)AP * 4, cudaMemcpyDeviceToHost, pl->st));
+    MOFF_CK(cudaMemcpyAsync(perm.data(), dperm, (size_t)nrows * 4, cudaMemcpyDeviceToHost, pl->st));
     MOFF_CK(cudaMemcpyAsync(&sy, pl->d_sy + chan, 4, cudaMemcpyDeviceToHost, pl->st));
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
-    for (int v = 0; v < AP; ++v)
+    for (int v = 0; v < nrows; ++v)
         for (int t = 0; t < n_time; ++t) {
             const size_t o = ((size_t)t * AP + perm[v]) * 2;
-            out[o] = __half2float(re[(size_t)v * pl->Tb + t]);
-            out[o + 1] = __half2float(im[(size_t)v * pl->Tb + t]);
+            const float r = __half2float(re[(size_t)v * pl->Tb + t]), i = __half2float(im[(size_t)v * pl->Tb + t]);
+            if (gt && v > 0 && std::find(perm.begin(), perm.begin() + v, perm[v]) != perm.begin() + v &&
+                (out[o] != r || out[o + 1] != i))
+                return fail(MOFF_ECUDA, "a copied voltage-plane row differs from its original (row %d)", v);
+            out[o] = r;
+            out[o + 1] = i;
         }
     if (scale) *scale = sy;
     return MOFF_OK;

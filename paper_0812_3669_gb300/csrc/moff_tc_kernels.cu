@@ -138,29 +138,53 @@ __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ v
 }
 
 // Large arrays (a channel's voltage bytes of eight samples exceed the staging budget): one
-// thread per plane row and 32 samples.  Consecutive plane rows that hold consecutive
-// voltages read consecutive bytes of each sample; each thread writes its row's 32 samples as
-// four 16-byte pieces per plane.
+// thread per plane row and 32 samples; each thread writes its row's 32 samples as four
+// 16-byte pieces per plane.  A warp whose 32 plane rows hold 32 consecutive voltages (the
+// common case: antennas in raster order) reads each sample's 32 bytes as two or three aligned
+// 16-byte pieces into shared memory and picks its byte there; other warps read one byte per
+// sample and row.  vec_ok: 16-byte aligned voltage rows (tstride and A P multiples of 16).
 __global__ void __launch_bounds__(256) k_volt_prep_rows(const uint8_t *__restrict__ volt, long long tstride, int t0,
                                                         int nt, int c0, int AP, int APpad, int n_rows,
                                                         const float2 *__restrict__ gains, const float *__restrict__ sy,
-                                                        const int *__restrict__ perm, int Tpad,
+                                                        const int *__restrict__ perm, int Tpad, int vec_ok,
                                                         __half *__restrict__ yre, __half *__restrict__ yim) {
+    __shared__ __align__(16) unsigned char s_w[8][32][48];
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int tb = blockIdx.y * 32;
     const int cl = blockIdx.z, c = c0 + cl;
+    const bool have = v < n_rows;
+    const int sv = have ? perm[v] : 0;
+    const int sv0 = __shfl_sync(0xffffffffu, sv, 0);
+    const bool contig = vec_ok && __all_sync(0xffffffffu, have && sv == sv0 + lane);
+    uint32_t b[32];
+    if (contig) {
+        // bytes [row0, row0 + 32) of each sample: pieces [a0 + 16 k, a0 + 16 k + 16), k < npc, all inside the
+        // channel's A P bytes (c A P and A P are multiples of 16, sv0 + 32 <= A P)
+        const long long row0 = (long long)c * AP + sv0, a0 = row0 & ~15LL;
+        const int off = (int)(row0 - a0), npc = (off + 47) >> 4;
+        const uint8_t *base = volt + (long long)(t0 + tb) * tstride + a0;
+        for (int i = lane; i < 32 * npc; i += 32) {
+            const int t = i / npc, k = i - t * npc;
+            uint4 q = make_uint4(0u, 0u, 0u, 0u);
+            if (tb + t < nt) q = __ldg(reinterpret_cast<const uint4 *>(base + (long long)t * tstride + 16 * k));
+            *reinterpret_cast<uint4 *>(&s_w[wp][t][16 * k]) = q;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 32; ++t) b[t] = s_w[wp][t][off + lane];
+    } else {
+        const uint8_t *src = volt + (long long)(t0 + tb) * tstride + (long long)c * AP + sv;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) b[t] = have && tb + t < nt ? (uint32_t)__ldg(src + (long long)t * tstride) : 0u;
+    }
     if (v >= APpad) return;
     uint32_t re[16], im[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
-    if (v < n_rows) {
-        const int sv = perm[v];
+    if (have) {
         const float2 g = gains[(long long)c * AP + sv];
         const float s = sy[c];
-        const uint8_t *src = volt + (long long)(t0 + tb) * tstride + (long long)c * AP + sv;
-        uint32_t b[32];
-#pragma unroll
-        for (int t = 0; t < 32; ++t) b[t] = tb + t < nt ? (uint32_t)__ldg(src + (long long)t * tstride) : 0u;
 #pragma unroll
         for (int t = 0; t < 32; t += 2) {
             const float2 y0 = cmul(g, decode4_tc(b[t])), y1 = cmul(g, decode4_tc(b[t + 1]));
@@ -426,8 +450,9 @@ cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int
     const int rows = n_rows < 0 ? AP : n_rows;
     if (8 * APr > 96 * 1024 && Tpad % 32 == 0) {   // too large to stage 8 samples: one thread per plane row
         dim3 grid((APpad + 255) / 256, Tpad / 32, nc);
-        k_volt_prep_rows<<<grid, 256, 0, st>>>(volt, tstride, t0, nt, c0, AP, APpad, rows, gains, sy, perm, Tpad, yre,
-                                               yim);
+        const int vec_ok = tstride % 16 == 0 && AP % 16 == 0 && ((uintptr_t)volt & 15) == 0;
+        k_volt_prep_rows<<<grid, 256, 0, st>>>(volt, tstride, t0, nt, c0, AP, APpad, rows, gains, sy, perm, Tpad, vec_ok,
+                                               yre, yim);
         return cudaGetLastError();
     }
     int TT = 32;

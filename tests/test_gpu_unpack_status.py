@@ -135,3 +135,33 @@ def test_read_image_timeout_leaves_plan_unchanged():
     img, n = run(True)
     assert n == n_ref == 3 * T
     np.testing.assert_array_equal(img, ref)
+
+
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_tcgrid_voltage_planes_decode_exactly_for_large_arrays(shuffle):
+    """The plane kernel of large arrays (one thread per plane row) on the tensor-core gridding
+    route: warps whose rows hold consecutive voltages read them as aligned 16-byte pieces (a
+    lattice in index order), other warps byte by byte (the same lattice with its antennas
+    shuffled); rows copied for kernel windows that wrap the grid edge must equal their originals.
+    With unit gains every plane value is the decoded voltage times the channel's
+    power-of-two scale, exactly, in every sample, also where a 32-sample slice is ragged."""
+    rng = np.random.default_rng(404)
+    side, N, K, P, C, T = 80, 512, 5, 2, 2, 45
+    # the lattice straddles the grid's x edge, so kernel windows wrap and rows are copied
+    pos = synth.positions_lattice(rng, side, side, 1.0, 0.05, (N - side, N / 2 - side))
+    if shuffle:
+        pos = pos[rng.permutation(len(pos))]
+    A = len(pos)
+    taps = synth.taps_gaussian(rng, pos, K, 1.2, n_pol=P).astype(np.complex64)
+    re = rng.integers(-8, 8, size=(T, C, A, P))
+    im = rng.integers(-8, 8, size=(T, C, A, P))
+    volt = synth.pack_4bit(re, im)
+    with moff.Plan(pos, taps, N, C, P, fp16tc=True) as pl:
+        assert pl.route() == "fp16_tcgrid"
+        pl.set_gains(np.ones((C, A, P), dtype=np.complex64))
+        for chan in range(C):
+            planes, scale = pl.voltage_planes(volt, chan)
+            assert scale == 512.0
+            z = planes / scale
+            np.testing.assert_array_equal(z.real, re[:, chan])
+            np.testing.assert_array_equal(z.imag, im[:, chan])
