@@ -807,7 +807,7 @@ def dualpol_leg(args, ctx):
                 "peak_basis": f"FP32 FMA: {ctx.peaks['sms']} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (of derived peak)",
                 "flops_per_launch": flops[dom] / max(launches, 1),
                 "ms_per_launch": kern[dom]["ms_total"] / max(launches, 1),
-                "traffic": traffic_for(dom + "@dualpol1024", src)}
+                "traffic": traffic_for(dom + "@dualpol1024", src, snaps / max(launches, 1))}
     gpu_launches = sum(v["launches"] for v in kern.values())
     # DRAM traffic against the method's own bytes: the gridding kernel's algorithmic input is
     # the 4-bit voltages (the row-transformed field it writes is an intermediate); the column
@@ -817,7 +817,8 @@ def dualpol_leg(args, ctx):
            "cols_integrate": 2 * 4 * N * N * 8 * C / max(kern.get("cols_integrate", {}).get("launches", 1), 1)}
     for name in ("grid_rows", "cols_integrate"):
         if name in kern:
-            t = traffic_for(name + "@dualpol1024", KERNEL_SOURCES.get(name, []))
+            t = traffic_for(name + "@dualpol1024", KERNEL_SOURCES.get(name, []),
+                            snaps / max(kern[name]["launches"], 1))
             kern[name]["algorithmic_bytes_per_launch"] = alg[name]
             kern[name]["traffic_bytes_per_launch"] = t
             kern[name]["traffic_over_algorithmic"] = t / alg[name] if t else None
