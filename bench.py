@@ -812,9 +812,10 @@ def dualpol_leg(args, ctx):
     # DRAM traffic against the method's own bytes: the gridding kernel's algorithmic input is
     # the 4-bit voltages (the row-transformed field it writes is an intermediate); the column
     # kernel's is its share of the FP64 accumulators (read and written once per chunk)
+    # (every launch reads and writes the FP64 accumulators of its chunk's channels once)
     snaps_launch = snaps / max(launches, 1)
     alg = {"grid_rows": A * P * snaps_launch,
-           "cols_integrate": 2 * 4 * N * N * 8 * C / max(kern.get("cols_integrate", {}).get("launches", 1), 1)}
+           "cols_integrate": 2 * 4 * N * N * 8 * plan.info()["chan_chunk"]}
     for name in ("grid_rows", "cols_integrate"):
         if name in kern:
             t = traffic_for(name + "@dualpol1024", KERNEL_SOURCES.get(name, []),
