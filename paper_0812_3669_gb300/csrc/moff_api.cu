@@ -287,7 +287,7 @@ struct moff_plan {
     // tile tables, voltage planes in raster order of anchors (TMA maps of 16-row boxes), and the
     // FP16 gridded field (d_G, the row transform's input; the row-transformed field is d_H)
     bool gtc = false;
-    int gt_tiles = 0, gt_kp_max = 0, gt_cgroups = 1, gt_rows = 0, gt_stages = 4;   // gt_rows: plane rows per channel incl. padding
+    int gt_tiles = 0, gt_kp_max = 0, gt_cgroups = 1, gt_rows = 0, gt_stages = 4, gt_boxes = 1;   // gt_rows: plane rows per channel incl. padding
     size_t gt_smem = 0;
     int *d_gt_tile_cell = nullptr, *d_gt_kp = nullptr, *d_gt_chunk_off = nullptr, *d_gt_chunk_row = nullptr,
         *d_gt_perm = nullptr;
@@ -832,6 +832,7 @@ moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long l
             ga.AP = pl->gt_rows;
             ga.kp_max = pl->gt_kp_max;
             ga.stages = pl->gt_stages;
+            ga.boxes = pl->gt_boxes;
             ga.tile_cell = pl->d_gt_tile_cell;
             ga.kp = pl->d_gt_kp;
             ga.chunk_off = pl->d_gt_chunk_off;
@@ -2174,7 +2175,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             if ((s = build_gridtc(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps, pl->dft_s_t, &gtab)) != MOFF_OK)
                 return bail(s);
             // one CTA per SM: the tile's kernel matrix, the A ring and the barriers must fit shared memory
-            pl->gtc = !gtab.tile_cell.empty() && gridtc_stages(n_pol, gtab.kp_max) > 0;
+            pl->gtc = !gtab.tile_cell.empty() && gridtc_stages(n_pol, gtab.kp_max, 1) > 0;
             pl->gt_rows = gtab.n_rows + kRowSpecPad;
         }
     }
@@ -2255,8 +2256,13 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         if (pl->gtc) {
             pl->gt_tiles = (int)gtab.tile_cell.size();
             pl->gt_kp_max = gtab.kp_max;
-            pl->gt_stages = gridtc_stages(n_pol, gtab.kp_max);
-            pl->gt_smem = gridtc_smem_bytes(n_pol, gtab.kp_max, pl->gt_stages);
+            // one epilogue box per warp and the deepest A ring: on the wide-field array a second box
+            // per warp (4 stages instead of 8) measured 3.14 against 2.76 ms per launch
+            // (MOFF_GT_BOXES=2 selects it where it fits)
+            const char *gb = getenv("MOFF_GT_BOXES");
+            pl->gt_boxes = (gb && atoi(gb) == 2 && gridtc_stages(n_pol, gtab.kp_max, 2) > 0) ? 2 : 1;
+            pl->gt_stages = gridtc_stages(n_pol, gtab.kp_max, pl->gt_boxes);
+            pl->gt_smem = gridtc_smem_bytes(n_pol, gtab.kp_max, pl->gt_stages, pl->gt_boxes);
             // channel groups: about two CTAs' worth of tiles per SM over a launch
             int sms = 152;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);

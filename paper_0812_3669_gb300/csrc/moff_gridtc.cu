@@ -68,8 +68,8 @@ __global__ void __launch_bounds__(kGtThreads, 1)
     unsigned char *sB = smem;                                  // NT x kp, K-major (resident)
     const int ns = a.stages;
     unsigned char *sA = sB + bbytes;                           // ns x [128 x 32], 1024-aligned
-    unsigned char *sE = sA + ns * kGtStageBytes;               // one epilogue box per warp, 1024-aligned
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sE + kGtEpiWarps * kGtBoxBytes);
+    unsigned char *sE = sA + ns * kGtStageBytes;               // a.boxes epilogue boxes per warp, 1024-aligned
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sE + kGtEpiWarps * a.boxes * kGtBoxBytes);
     uint64_t *a_full = bars, *a_empty = bars + ns, *d_full = bars + 2 * ns, *d_empty = bars + 2 * ns + 2,
              *b_full = bars + 2 * ns + 4;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * ns + 5);
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kGtThreads, 1)
         // box (32 rows x 128 bytes, 128-byte swizzle) that one lane hands to the TMA unit.
         const int q4 = warp & 3, hc = warp >> 2;
         const int nty = a.N >> 3;
-        unsigned char *box = sE + warp * kGtBoxBytes;
+        unsigned char *boxes = sE + warp * a.boxes * kGtBoxBytes;
         int nbox = 0;
         for (int i = 0; i < nitems; ++i) {
             const int b = i & 1;
@@ -203,8 +203,12 @@ __global__ void __launch_bounds__(kGtThreads, 1)
                     for (int u = 0; u < 4; ++u) h[u] = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
                     pk[pc] = *reinterpret_cast<const uint4 *>(h);
                 }
-                if (nbox > 0) {                           // the store that last read this box is done with it
-                    if (lane == 0) tc::bulk_wait_read<0>();
+                unsigned char *box = boxes + (nbox % a.boxes) * kGtBoxBytes;
+                if (nbox >= a.boxes) {                    // the store that last read this box is done with it
+                    if (lane == 0) {
+                        if (a.boxes == 2) tc::bulk_wait_read<1>();
+                        else tc::bulk_wait_read<0>();
+                    }
                     __syncwarp();
                 }
 #pragma unroll
@@ -249,16 +253,16 @@ size_t kmajor_byte(int n, int k, int K) {
 
 }  // namespace
 
-size_t gridtc_smem_bytes(int P, int kp_max, int stages) {
+size_t gridtc_smem_bytes(int P, int kp_max, int stages, int boxes) {
     const int NT = 128 * P;
     return 1024 + (((size_t)NT * kp_max * 2 + 1023) & ~(size_t)1023) + (size_t)stages * kGtStageBytes +
-           (size_t)kGtEpiWarps * kGtBoxBytes + (size_t)(2 * stages + 5) * 8 + 16;
+           (size_t)kGtEpiWarps * boxes * kGtBoxBytes + (size_t)(2 * stages + 5) * 8 + 16;
 }
 
 // A ring depth: the most stages (<= 8) that fit 227 KB beside B and the epilogue boxes; 0 if not even 4 fit.
-int gridtc_stages(int P, int kp_max) {
+int gridtc_stages(int P, int kp_max, int boxes) {
     for (int s = kGtMaxStages; s >= 4; --s)
-        if (gridtc_smem_bytes(P, kp_max, s) <= 227 * 1024) return s;
+        if (gridtc_smem_bytes(P, kp_max, s, boxes) <= 227 * 1024) return s;
     return 0;
 }
 

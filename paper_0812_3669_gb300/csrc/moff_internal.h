@@ -99,6 +99,7 @@ struct RowDftArgs {
 struct GridTcArgs {
     int P, N, nt, nc, c0, AP, kp_max;   // AP: plane rows per channel (voltages + kRowSpecPad)
     int stages;                // depth of the A ring (gridtc_stages)
+    int boxes;                 // epilogue boxes per warp (1, or 2: a box is filled while the other is stored)
     const int *tile_cell;      // [tiles] (ty << 16) | tx: cells 8 ty .. 8 ty + 7, 8 tx .. 8 tx + 7
     const int *kp;             // [tiles] contraction length (32 per chunk of 16 plane rows)
     const int *chunk_off;      // [tiles + 1]
@@ -121,8 +122,8 @@ struct GridTc {
 };
 moff_status build_gridtc(int A, int K, int N, int P, bool jones, const double *pos, const float *taps, float scale,
                          GridTc *gt);
-size_t gridtc_smem_bytes(int P, int kp_max, int stages);
-int gridtc_stages(int P, int kp_max);
+size_t gridtc_smem_bytes(int P, int kp_max, int stages, int boxes);
+int gridtc_stages(int P, int kp_max, int boxes);
 cudaError_t launch_grid_tc(const GridTcArgs &a, const CUtensorMap &are, const CUtensorMap &aim, const CUtensorMap &gmap,
                            int n_tiles, int cgroups, size_t smem, cudaStream_t st);
 // Store map of the tile-major gridded field (rows of 128 halves; box 64 x 32, 128-byte swizzle).
