@@ -246,6 +246,23 @@ moff_status moff_read_image(moff_plan *plan, float *out, long long *n_samples, i
 /* moff_sync -- bounded wait for all work enqueued on the plan (MOFF_ETIMEDOUT on expiry). */
 moff_status moff_sync(moff_plan *plan, int timeout_ms);
 
+/*
+ * moff_export_accumulators / moff_import_accumulators -- checkpoint and resume
+ * an integration (no counterpart in the paper, whose time average Eq. m6 is a
+ * running sum): the FP64 image sums float64 [C][n_prod][N][N] and their sample
+ * count.  Export waits for the plan's work (bounded, as moff_read_image, and
+ * reports a failed in-kernel wait as MOFF_ETIMEDOUT) and copies them to out
+ * (host, or device with out_on_device = 1).  Import replaces the plan's sums and
+ * count with in (host: copied before the call returns; device: the caller keeps
+ * it until moff_sync), enqueued behind the plan's earlier work.  A plan of the
+ * same C, n_prod and N, on any route, continues the integration: its later
+ * blocks add to the imported sums exactly as they would have to its own.
+ * Feedback-calibration and autocorrelation sums are not included.
+ */
+moff_status moff_export_accumulators(moff_plan *plan, double *out, long long *n_samples, int out_on_device,
+                                     int timeout_ms);
+moff_status moff_import_accumulators(moff_plan *plan, const double *in, long long n_samples, int in_on_device);
+
 /* moff_reset -- zero the accumulators and the sample count (enqueued on the plan's stream). */
 moff_status moff_reset(moff_plan *plan);
 

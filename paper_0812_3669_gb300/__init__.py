@@ -26,6 +26,7 @@ __all__ = [
     "moff_channelise", "moff_grid_snapshot", "moff_read_image", "moff_sync", "moff_reset",
     "moff_plan_info", "moff_plan_route", "moff_voltage_planes", "moff_plan_destroy", "moff_last_error", "moff_set_timing", "moff_timing",
     "moff_image_noalloc", "moff_tc_selftest", "MOFF_SERVED", "MOFF_AUTOTUNE", "MOFF_GRAPH", "MOFF_PERSIST", "moff_plan_tuning", "moff_plan_dft_tuning",
+    "moff_export_accumulators", "moff_import_accumulators",
     "moff_server_create", "moff_server_submit", "moff_server_poll", "moff_server_wait", "moff_server_stats",
     "moff_server_destroy", "moff_set_calibrator", "moff_read_feedback", "moff_feedback_gains",
     "moff_set_autocorr", "moff_read_image_cross", "moff_set_beams", "moff_read_beams", "moff_set_channel_groups",
@@ -97,6 +98,8 @@ _SIGS = {
     "moff_feedback_gains": [_vp, _vp, _i],
     "moff_plan_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)],
+    "moff_export_accumulators": [_vp, _vp, ctypes.POINTER(_ll), _i, _i],
+    "moff_import_accumulators": [_vp, _vp, _ll, _i],
     "moff_plan_dft_tuning": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)],
 }
@@ -293,6 +296,20 @@ def moff_plan_dft_tuning(plan):
     m8, m16 = ctypes.c_double(), ctypes.c_double()
     _check(lib().moff_plan_dft_tuning(plan, ctypes.byref(w), ctypes.byref(src), ctypes.byref(m8), ctypes.byref(m16)))
     return dict(cols_width=w.value, source=src.value, ms_w8=m8.value, ms_w16=m16.value)
+
+
+def moff_export_accumulators(plan, out, timeout_ms=-1):
+    """The plan's FP64 image sums into ``out`` (host float64 array or CUDA tensor,
+    [C][n_prod][N][N]); returns the sample count."""
+    a, dev = _addr(out)
+    n = ctypes.c_longlong(0)
+    _check(lib().moff_export_accumulators(plan, a, ctypes.byref(n), dev, int(timeout_ms)))
+    return n.value
+
+
+def moff_import_accumulators(plan, src, n_samples):
+    a, dev = _addr(src)
+    _check(lib().moff_import_accumulators(plan, a, int(n_samples), dev))
 
 
 def moff_set_calibrator(plan, kx, ky):
@@ -581,6 +598,27 @@ class Plan:
 
     def dft_tuning(self):
         return moff_plan_dft_tuning(self.handle)
+
+    def _check_acc(self, buf):
+        n = self.C * self.n_prod * self.N * self.N
+        if _is_torch(buf):
+            import torch
+            ok = buf.dtype == torch.float64 and buf.numel() == n
+        else:
+            ok = isinstance(buf, np.ndarray) and buf.dtype == np.float64 and buf.size == n
+        if not ok:
+            raise ValueError(f"accumulators must be float64 with {n} elements ([C][n_prod][N][N])")
+
+    def export_accumulators(self, out=None, timeout_ms=-1):
+        """(float64 [C][n_prod][N][N] sums, sample count): a checkpoint of the integration."""
+        if out is None:
+            out = np.empty((self.C, self.n_prod, self.N, self.N), dtype=np.float64)
+        self._check_acc(out)
+        return out, moff_export_accumulators(self.handle, out, timeout_ms)
+
+    def import_accumulators(self, src, n_samples):
+        self._check_acc(src)
+        moff_import_accumulators(self.handle, src, n_samples)
 
     def set_calibrator(self, kx, ky):
         moff_set_calibrator(self.handle, kx, ky)

@@ -2410,6 +2410,16 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     pl->scratch_bytes = align_up(pl->h_bytes, 1024) + (pl->tc && !pl->dft ? 2 * align_up(pl->y_bytes, 1024) : 0) +
                         (pl->gtc ? align_up(pl->h_bytes, 1024) + 2 * align_up(pl->y_bytes, 1024) : 0);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(MOFF_ECUDA, "plan set-up failed"));
+    if (const char *lg = getenv("MOFF_LOG"); lg && atoi(lg) > 0) {   // the plan's decisions, one line on stderr
+        static const char *routes[4] = {"fp32", "fp16_rowspec", "fp16_dft", "fp16_tcgrid"};
+        const int route = pl->gtc ? 3 : (pl->dft ? 2 : (pl->tc ? 1 : 0));
+        fprintf(stderr,
+                "moff: plan A=%d K=%d N=%d C=%d P=%d route=%s chunk=%dx%d grid(tb=%d cells/lane=%d wide=%d staged=%d "
+                "source=%d) cols_w=%d persist=%d scratch=%.1f MB device=%.1f MB\n",
+                n_ant, ksize, grid_n, n_chan, n_pol, routes[route], pl->Tb, pl->Cb, pl->tb,
+                pl->quads ? 4 : (pl->pairs ? 2 : 1), (int)pl->wide, (int)pl->staged, pl->tune_source,
+                pl->dft ? pl->cols_w : 0, (int)pl->persist, pl->scratch_bytes / 1048576.0, pl->dev_bytes / 1048576.0);
+    }
     *out = pl;
     g_err.clear();
     return MOFF_OK;
@@ -2763,6 +2773,35 @@ moff_status moff_sync(moff_plan *pl, int timeout_ms) {
     if (s != MOFF_OK) return s;
     if ((s = sync_plan(pl, timeout_ms)) != MOFF_OK) return s;
     return check_device_err(pl);
+}
+
+moff_status moff_export_accumulators(moff_plan *pl, double *out, long long *n_samples, int out_on_device,
+                                     int timeout_ms) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!out) return fail(MOFF_EINVAL, "out is NULL");
+    if ((s = sync_plan(pl, timeout_ms)) != MOFF_OK) return s;
+    if ((s = check_device_err(pl)) != MOFF_OK) return s;
+    const size_t bytes = (size_t)pl->C * pl->nprod * pl->N * pl->N * 8;
+    MOFF_CK(cudaMemcpyAsync(out, pl->d_acc, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            pl->st));
+    if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    if (n_samples) *n_samples = pl->n_samples;
+    return MOFF_OK;
+}
+
+moff_status moff_import_accumulators(moff_plan *pl, const double *in, long long n_samples, int in_on_device) {
+    moff_status s = check_plan(pl);
+    if (s != MOFF_OK) return s;
+    if (!in) return fail(MOFF_EINVAL, "in is NULL");
+    if (n_samples < 0) return fail(MOFF_EINVAL, "n_samples (%lld) must be >= 0", n_samples);
+    const size_t bytes = (size_t)pl->C * pl->nprod * pl->N * pl->N * 8;
+    // enqueued behind the plan's work; a host source is read before the call returns
+    MOFF_CK(cudaMemcpyAsync(pl->d_acc, in, bytes, in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            pl->st));
+    if (!in_on_device && (s = sync_plan(pl, -1)) != MOFF_OK) return s;
+    pl->n_samples = n_samples;
+    return MOFF_OK;
 }
 
 moff_status moff_reset(moff_plan *pl) {
