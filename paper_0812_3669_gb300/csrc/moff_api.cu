@@ -2732,16 +2732,20 @@ moff_status moff_voltage_planes(moff_plan *pl, const uint8_t *volt, int n_time, 
     MOFF_CK(cudaMemcpyAsync(perm.data(), dperm, (size_t)nrows * 4, cudaMemcpyDeviceToHost, pl->st));
     MOFF_CK(cudaMemcpyAsync(&sy, pl->d_sy + chan, 4, cudaMemcpyDeviceToHost, pl->st));
     if ((s = sync_plan(pl, -1)) != MOFF_OK) return s;
-    for (int v = 0; v < nrows; ++v)
+    std::vector<char> seen(AP, 0);
+    for (int v = 0; v < nrows; ++v) {
+        if (perm[v] < 0 || perm[v] >= AP) return fail(MOFF_ECUDA, "voltage-plane row %d maps outside the array", v);
+        const bool copy = seen[perm[v]] != 0;    // a row copied for a wrapping kernel window: must equal its original
+        seen[perm[v]] = 1;
         for (int t = 0; t < n_time; ++t) {
             const size_t o = ((size_t)t * AP + perm[v]) * 2;
             const float r = __half2float(re[(size_t)v * pl->Tb + t]), i = __half2float(im[(size_t)v * pl->Tb + t]);
-            if (gt && v > 0 && std::find(perm.begin(), perm.begin() + v, perm[v]) != perm.begin() + v &&
-                (out[o] != r || out[o + 1] != i))
+            if (copy && (out[o] != r || out[o + 1] != i))
                 return fail(MOFF_ECUDA, "a copied voltage-plane row differs from its original (row %d)", v);
             out[o] = r;
             out[o + 1] = i;
         }
+    }
     if (scale) *scale = sy;
     return MOFF_OK;
 }
