@@ -137,68 +137,96 @@ __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ v
     }
 }
 
+// 16-byte asynchronous global -> shared copies for the plane kernel's staging ring.
+__device__ __forceinline__ void vp_cp16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void vp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most n (0..3) of this thread's copy groups are still in flight
+__device__ __forceinline__ void vp_wait(int n) {
+    if (n <= 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else if (n == 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+    else asm volatile("cp.async.wait_group 3;\n" ::: "memory");
+}
+
 // Large arrays (a channel's voltage bytes of eight samples exceed the staging budget): one
-// thread per plane row and 32 samples; each thread writes its row's 32 samples as four
-// 16-byte pieces per plane.  A warp whose 32 plane rows hold 32 consecutive voltages (the
-// common case: antennas in raster order) reads each sample's 32 bytes as two or three aligned
-// 16-byte pieces into shared memory and picks its byte there; other warps read one byte per
-// sample and row.  vec_ok: 16-byte aligned voltage rows (tstride and A P multiples of 16).
+// thread per plane row, all Tpad samples in passes of 32; each pass writes the row's 32 samples
+// as four 16-byte pieces per plane.  A warp whose 32 plane rows hold 32 consecutive voltages
+// (the common case: antennas in raster order) copies each sample's 32 bytes as two or three
+// aligned 16-byte pieces into a four-pass ring in shared memory (cp.async, up to three passes
+// ahead of the one it converts) and picks its byte there; other warps read one byte per sample
+// and row.  vec_ok: 16-byte aligned voltage rows (tstride and A P multiples of 16).
+constexpr int kVpRing = 4;
 __global__ void __launch_bounds__(256) k_volt_prep_rows(const uint8_t *__restrict__ volt, long long tstride, int t0,
                                                         int nt, int c0, int AP, int APpad, int n_rows,
                                                         const float2 *__restrict__ gains, const float *__restrict__ sy,
                                                         const int *__restrict__ perm, int Tpad, int vec_ok,
                                                         __half *__restrict__ yre, __half *__restrict__ yim) {
-    __shared__ __align__(16) unsigned char s_w[8][32][48];
+    __shared__ __align__(16) unsigned char s_w[kVpRing][8][32][48];
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int tb = blockIdx.y * 32;
-    const int cl = blockIdx.z, c = c0 + cl;
+    const int cl = blockIdx.y, c = c0 + cl;
     const bool have = v < n_rows;
     const int sv = have ? perm[v] : 0;
     const int sv0 = __shfl_sync(0xffffffffu, sv, 0);
     const bool contig = vec_ok && __all_sync(0xffffffffu, have && sv == sv0 + lane);
-    uint32_t b[32];
-    if (contig) {
-        // bytes [row0, row0 + 32) of each sample: pieces [a0 + 16 k, a0 + 16 k + 16), k < npc, all inside the
-        // channel's A P bytes (c A P and A P are multiples of 16, sv0 + 32 <= A P)
-        const long long row0 = (long long)c * AP + sv0, a0 = row0 & ~15LL;
-        const int off = (int)(row0 - a0), npc = (off + 47) >> 4;
-        const uint8_t *base = volt + (long long)(t0 + tb) * tstride + a0;
+    const int np = Tpad / 32;
+    // contiguous warps: bytes [row0, row0 + 32) of each sample are pieces [a0 + 16 k, a0 + 16 k + 16), k < npc,
+    // all inside the channel's A P bytes (c A P and A P are multiples of 16, sv0 + 32 <= A P)
+    const long long row0 = (long long)c * AP + sv0, a0 = row0 & ~15LL;
+    const int off = (int)(row0 - a0), npc = (off + 47) >> 4;
+    auto issue = [&](int p) {      // pass p's 32 samples into ring slot p mod 4 (zero past the block)
+        const uint8_t *base = volt + (long long)(t0 + 32 * p) * tstride + a0;
         for (int i = lane; i < 32 * npc; i += 32) {
             const int t = i / npc, k = i - t * npc;
-            uint4 q = make_uint4(0u, 0u, 0u, 0u);
-            if (tb + t < nt) q = __ldg(reinterpret_cast<const uint4 *>(base + (long long)t * tstride + 16 * k));
-            *reinterpret_cast<uint4 *>(&s_w[wp][t][16 * k]) = q;
+            unsigned char *d = &s_w[p % kVpRing][wp][t][16 * k];
+            if (32 * p + t < nt) vp_cp16(d, base + (long long)t * tstride + 16 * k);
+            else *reinterpret_cast<uint4 *>(d) = make_uint4(0u, 0u, 0u, 0u);
         }
-        __syncwarp();
+        vp_commit();
+    };
+    int issued = 0;
+    if (contig)
+        for (; issued < np && issued < kVpRing - 1; ++issued) issue(issued);
+    const float2 g = have ? gains[(long long)c * AP + sv] : make_float2(0.f, 0.f);
+    const float s = sy[c];
+    for (int p = 0; p < np; ++p) {
+        const int tb = 32 * p;
+        uint32_t b[32];
+        if (contig) {
+            if (issued < np) issue(issued++);
+            vp_wait(issued - 1 - p);                 // pass p's group has landed
+            __syncwarp();
 #pragma unroll
-        for (int t = 0; t < 32; ++t) b[t] = s_w[wp][t][off + lane];
-    } else {
-        const uint8_t *src = volt + (long long)(t0 + tb) * tstride + (long long)c * AP + sv;
+            for (int t = 0; t < 32; ++t) b[t] = s_w[p % kVpRing][wp][t][off + lane];
+            __syncwarp();                            // read by every lane before the slot is refilled
+        } else {
+            const uint8_t *src = volt + (long long)(t0 + tb) * tstride + (long long)c * AP + sv;
 #pragma unroll
-        for (int t = 0; t < 32; ++t) b[t] = have && tb + t < nt ? (uint32_t)__ldg(src + (long long)t * tstride) : 0u;
-    }
-    if (v >= APpad) return;
-    uint32_t re[16], im[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
-    if (have) {
-        const float2 g = gains[(long long)c * AP + sv];
-        const float s = sy[c];
-#pragma unroll
-        for (int t = 0; t < 32; t += 2) {
-            const float2 y0 = cmul(g, decode4_tc(b[t])), y1 = cmul(g, decode4_tc(b[t + 1]));
-            const __half2 hr = __floats2half2_rn(y0.x * s, y1.x * s), hi = __floats2half2_rn(y0.y * s, y1.y * s);
-            re[t >> 1] = *reinterpret_cast<const uint32_t *>(&hr);
-            im[t >> 1] = *reinterpret_cast<const uint32_t *>(&hi);
+            for (int t = 0; t < 32; ++t) b[t] = have && tb + t < nt ? (uint32_t)__ldg(src + (long long)t * tstride) : 0u;
         }
-    }
-    uint4 *ore = reinterpret_cast<uint4 *>(yre + ((long long)cl * APpad + v) * Tpad + tb);
-    uint4 *oim = reinterpret_cast<uint4 *>(yim + ((long long)cl * APpad + v) * Tpad + tb);
+        if (v >= APpad) continue;
+        uint32_t re[16], im[16];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        ore[k] = make_uint4(re[4 * k], re[4 * k + 1], re[4 * k + 2], re[4 * k + 3]);
-        oim[k] = make_uint4(im[4 * k], im[4 * k + 1], im[4 * k + 2], im[4 * k + 3]);
+        for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
+        if (have) {
+#pragma unroll
+            for (int t = 0; t < 32; t += 2) {
+                const float2 y0 = cmul(g, decode4_tc(b[t])), y1 = cmul(g, decode4_tc(b[t + 1]));
+                const __half2 hr = __floats2half2_rn(y0.x * s, y1.x * s), hi = __floats2half2_rn(y0.y * s, y1.y * s);
+                re[t >> 1] = *reinterpret_cast<const uint32_t *>(&hr);
+                im[t >> 1] = *reinterpret_cast<const uint32_t *>(&hi);
+            }
+        }
+        uint4 *ore = reinterpret_cast<uint4 *>(yre + ((long long)cl * APpad + v) * Tpad + tb);
+        uint4 *oim = reinterpret_cast<uint4 *>(yim + ((long long)cl * APpad + v) * Tpad + tb);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ore[k] = make_uint4(re[4 * k], re[4 * k + 1], re[4 * k + 2], re[4 * k + 3]);
+            oim[k] = make_uint4(im[4 * k], im[4 * k + 1], im[4 * k + 2], im[4 * k + 3]);
+        }
     }
 }
 
@@ -449,7 +477,7 @@ cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int
     const size_t APr = (size_t)((AP + 15) & ~15);
     const int rows = n_rows < 0 ? AP : n_rows;
     if (8 * APr > 96 * 1024 && Tpad % 32 == 0) {   // too large to stage 8 samples: one thread per plane row
-        dim3 grid((APpad + 255) / 256, Tpad / 32, nc);
+        dim3 grid((APpad + 255) / 256, nc);
         const int vec_ok = tstride % 16 == 0 && AP % 16 == 0 && ((uintptr_t)volt & 15) == 0;
         k_volt_prep_rows<<<grid, 256, 0, st>>>(volt, tstride, t0, nt, c0, AP, APpad, rows, gains, sy, perm, Tpad, vec_ok,
                                                yre, yim);
