@@ -263,6 +263,8 @@ struct moff_plan {
         *d_err = nullptr;
     long long *d_rs_bimg_off = nullptr;
     CUtensorMap a_map_re{}, a_map_im{};   // TMA maps of the voltage planes (d_yre, d_yim)
+    CUtensorMap vp_smap_re{}, vp_smap_im{};   // their store maps (row plane kernel)
+    bool vp_tma = true;                       // the row plane kernel stores by TMA boxes (MOFF_VP_TMA=0: directly)
     float *d_rs_row_sh = nullptr, *d_rs_row_inv = nullptr;
     CUtensorMap h_map;                 // tensor-core path: store map of the FP16 field
     int h_map_nt = 0;                  // its sample extent
@@ -660,7 +662,8 @@ moff_status run_image_tc(moff_plan *pl, const uint8_t *volt, int n_time, long lo
             const int nt = std::min(pl->Tb, n_time - t0);
             TimedLaunch tv(pl, 3);
             MOFF_CK(launch_volt_prep(volt, tstride, t0, nt, c0, nc, AP, AP + kRowSpecPad, pl->d_gains, pl->d_sy,
-                                     pl->d_rs_perm, pl->Tb, pl->d_yre, pl->d_yim, pl->st));
+                                     pl->d_rs_perm, pl->Tb, pl->d_yre, pl->d_yim, pl->st, -1,
+                                     pl->vp_tma ? &pl->vp_smap_re : nullptr, pl->vp_tma ? &pl->vp_smap_im : nullptr));
             tv.done();
             RowSpecArgs ra{};
             ra.P = pl->P;
@@ -821,7 +824,8 @@ moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long l
             const int nt = std::min(pl->Tb, n_time - t0);
             TimedLaunch tv(pl, 3);
             MOFF_CK(launch_volt_prep(volt, tstride, t0, nt, c0, nc, AP, pl->gt_rows, pl->d_gains, pl->d_sy,
-                                     pl->d_gt_perm, pl->Tb, pl->d_yre, pl->d_yim, pl->st, pl->gt_rows - kRowSpecPad));
+                                     pl->d_gt_perm, pl->Tb, pl->d_yre, pl->d_yim, pl->st, pl->gt_rows - kRowSpecPad,
+                                     pl->vp_tma ? &pl->vp_smap_re : nullptr, pl->vp_tma ? &pl->vp_smap_im : nullptr));
             tv.done();
             GridTcArgs ga{};
             ga.P = pl->P;
@@ -2028,7 +2032,9 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
         off += align_up(pl->y_bytes, 1024);
         const long long rows = (long long)pl->Cb * pl->gt_rows;
         if (encode_plane_map(&pl->gt_map_re, pl->d_yre, pl->Tb, rows, 16) != cudaSuccess ||
-            encode_plane_map(&pl->gt_map_im, pl->d_yim, pl->Tb, rows, 16) != cudaSuccess)
+            encode_plane_map(&pl->gt_map_im, pl->d_yim, pl->Tb, rows, 16) != cudaSuccess ||
+            encode_plane_store_map(&pl->vp_smap_re, pl->d_yre, pl->Tb, rows) != cudaSuccess ||
+            encode_plane_store_map(&pl->vp_smap_im, pl->d_yim, pl->Tb, rows) != cudaSuccess)
             return fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded");
         if (encode_gridtc_store_map(&pl->gt_map_g, pl->d_G, (long long)(pl->h_bytes / 256)) != cudaSuccess)
             return fail(MOFF_ECUDA, "tensor map of the gridded field could not be encoded");
@@ -2042,7 +2048,9 @@ moff_status plan_run_served(moff_plan *pl, void *scratch, const uint8_t *volt, i
             return fail(MOFF_ECUDA, "tensor map of the row-transformed field could not be encoded");
         const long long rows = (long long)pl->Cb * (pl->A * pl->P + kRowSpecPad);
         if (encode_plane_map(&pl->a_map_re, pl->d_yre, pl->Tb, rows) != cudaSuccess ||
-            encode_plane_map(&pl->a_map_im, pl->d_yim, pl->Tb, rows) != cudaSuccess)
+            encode_plane_map(&pl->a_map_im, pl->d_yim, pl->Tb, rows) != cudaSuccess ||
+            encode_plane_store_map(&pl->vp_smap_re, pl->d_yre, pl->Tb, rows) != cudaSuccess ||
+            encode_plane_store_map(&pl->vp_smap_im, pl->d_yim, pl->Tb, rows) != cudaSuccess)
             return fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded");
         pl->h_map_nt = pl->Tb;
     }
@@ -2138,6 +2146,7 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
     }
     if (cudaStreamCreateWithFlags(&pl->cst, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(MOFF_ECUDA, "copy stream creation failed"));
+    if (const char *e = getenv("MOFF_VP_TMA")) pl->vp_tma = atoi(e) != 0;
     for (int i = 0; i < 2; ++i) {
         if (cudaEventCreateWithFlags(&pl->ev_copied[i], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_consumed[i], cudaEventDisableTiming) != cudaSuccess)
@@ -2232,7 +2241,9 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
                 if ((s = palloc(pl, &pl->d_yim, pl->y_bytes)) != MOFF_OK) return bail(s);
                 const long long rows = (long long)pl->Cb * pl->gt_rows;
                 if (encode_plane_map(&pl->gt_map_re, pl->d_yre, pl->Tb, rows, 16) != cudaSuccess ||
-                    encode_plane_map(&pl->gt_map_im, pl->d_yim, pl->Tb, rows, 16) != cudaSuccess)
+                    encode_plane_map(&pl->gt_map_im, pl->d_yim, pl->Tb, rows, 16) != cudaSuccess ||
+                    encode_plane_store_map(&pl->vp_smap_re, pl->d_yre, pl->Tb, rows) != cudaSuccess ||
+                    encode_plane_store_map(&pl->vp_smap_im, pl->d_yim, pl->Tb, rows) != cudaSuccess)
                     return bail(fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded"));
                 if (encode_gridtc_store_map(&pl->gt_map_g, pl->d_G, (long long)(pl->h_bytes / 256)) != cudaSuccess)
                     return bail(fail(MOFF_ECUDA, "tensor map of the gridded field could not be encoded"));
@@ -2352,7 +2363,9 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             if ((s = palloc(pl, &pl->d_yim, ny * 2)) != MOFF_OK) return bail(s);
             const long long rows = (long long)pl->Cb * (n_ant * n_pol + kRowSpecPad);
             if (encode_plane_map(&pl->a_map_re, pl->d_yre, pl->Tb, rows) != cudaSuccess ||
-                encode_plane_map(&pl->a_map_im, pl->d_yim, pl->Tb, rows) != cudaSuccess)
+                encode_plane_map(&pl->a_map_im, pl->d_yim, pl->Tb, rows) != cudaSuccess ||
+                encode_plane_store_map(&pl->vp_smap_re, pl->d_yre, pl->Tb, rows) != cudaSuccess ||
+                encode_plane_store_map(&pl->vp_smap_im, pl->d_yim, pl->Tb, rows) != cudaSuccess)
                 return bail(fail(MOFF_ECUDA, "tensor maps of the voltage planes could not be encoded"));
         }
         if ((s = palloc(pl, &pl->d_sy, (size_t)n_chan * 4)) != MOFF_OK) return bail(s);
@@ -2722,7 +2735,8 @@ moff_status moff_voltage_planes(moff_plan *pl, const uint8_t *volt, int n_time, 
         src = reinterpret_cast<const uint8_t *>(dev);
     }
     MOFF_CK(launch_volt_prep(src, tstride, 0, n_time, chan, 1, AP, APpad, pl->d_gains, pl->d_sy, dperm, pl->Tb,
-                             pl->d_yre, pl->d_yim, pl->st, nrows));
+                             pl->d_yre, pl->d_yim, pl->st, nrows, pl->vp_tma ? &pl->vp_smap_re : nullptr,
+                             pl->vp_tma ? &pl->vp_smap_im : nullptr));
     if (slot >= 0 && (s = stage_done(pl, slot)) != MOFF_OK) return s;
     std::vector<__half> re((size_t)nrows * pl->Tb), im((size_t)nrows * pl->Tb);
     std::vector<int> perm(nrows);

@@ -376,7 +376,10 @@ constexpr int kRowSpecPad = 32;
 // Plane rows v < n_rows hold voltage perm[v]; rows n_rows .. APpad - 1 are zero (n_rows < 0: AP).
 cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc, int AP,
                              int APpad, const float2 *gains, const float *sy, const int *perm, int Tpad, __half *yre,
-                             __half *yim, cudaStream_t st, int n_rows = -1);
+                             __half *yim, cudaStream_t st, int n_rows = -1, const CUtensorMap *smap_re = nullptr,
+                             const CUtensorMap *smap_im = nullptr);
+// Store maps of the voltage planes for the row plane kernel (box 32 samples x 32 rows, 64-byte swizzle).
+cudaError_t encode_plane_store_map(CUtensorMap *map, void *plane, int Tpad, long long rows);
 cudaError_t launch_rowspec(int N, const RowSpecArgs &a, const CUtensorMap &hmap, const CUtensorMap &amap_re,
                            const CUtensorMap &amap_im, int cgroups, size_t smem, cudaStream_t st);
 // Tensor map of one FP16 voltage plane [rows][Tpad] (rows = Cb * A * P), box 64 samples x

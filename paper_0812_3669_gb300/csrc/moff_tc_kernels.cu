@@ -152,22 +152,34 @@ __device__ __forceinline__ void vp_wait(int n) {
 }
 
 // Large arrays (a channel's voltage bytes of eight samples exceed the staging budget): one
-// thread per plane row, all Tpad samples in passes of 32; each pass writes the row's 32 samples
-// as four 16-byte pieces per plane.  A warp whose 32 plane rows hold 32 consecutive voltages
-// (the common case: antennas in raster order) copies each sample's 32 bytes as two or three
-// aligned 16-byte pieces into a four-pass ring in shared memory (cp.async, up to three passes
-// ahead of the one it converts) and picks its byte there; other warps read one byte per sample
-// and row.  vec_ok: 16-byte aligned voltage rows (tstride and A P multiples of 16).
-constexpr int kVpRing = 4;
-__global__ void __launch_bounds__(256) k_volt_prep_rows(const uint8_t *__restrict__ volt, long long tstride, int t0,
+// thread per plane row, all Tpad samples in passes of 32.  A warp whose 32 plane rows hold 32
+// consecutive voltages (the common case: antennas in raster order) copies each sample's 32 bytes
+// as two or three aligned 16-byte pieces into a three-pass ring in shared memory (cp.async, up to
+// two passes ahead of the one it converts) and picks its byte there; other warps read one byte
+// per sample and row.  With store maps (use_tma) a warp whose 32 rows all lie inside the channel's
+// APpad rows writes each pass's 32 rows x 32 samples of each plane as one TMA box (64-byte
+// swizzle: piece k of row r at k ^ ((r >> 1) & 3)); other rows are stored directly as four
+// 16-byte pieces per plane.  vec_ok: 16-byte aligned voltage rows (tstride and A P multiples of 16).
+constexpr int kVpRing = 3;
+constexpr int kVpRingBytes = kVpRing * 8 * 32 * 48;
+constexpr int kVpBoxBytes = 2 * 32 * 64;                 // one warp's re and im boxes
+constexpr size_t kVpSmem = 1024 + kVpRingBytes + 8 * kVpBoxBytes;
+__global__ void __launch_bounds__(256, 3) k_volt_prep_rows(const uint8_t *__restrict__ volt, long long tstride, int t0,
                                                         int nt, int c0, int AP, int APpad, int n_rows,
                                                         const float2 *__restrict__ gains, const float *__restrict__ sy,
                                                         const int *__restrict__ perm, int Tpad, int vec_ok,
-                                                        __half *__restrict__ yre, __half *__restrict__ yim) {
-    __shared__ __align__(16) unsigned char s_w[kVpRing][8][32][48];
+                                                        __half *__restrict__ yre, __half *__restrict__ yim,
+                                                        const __grid_constant__ CUtensorMap smap_re,
+                                                        const __grid_constant__ CUtensorMap smap_im, int use_tma) {
+    extern __shared__ __align__(1024) unsigned char vp_smem[];
+    unsigned char *base_s = vp_smem + ((1024u - (tc::smem_u32(vp_smem) & 1023u)) & 1023u);
+    auto ring = [&](int slot, int wp, int t) { return base_s + ((slot * 8 + wp) * 32 + t) * 48; };
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int cl = blockIdx.y, c = c0 + cl;
+    const int v0 = v - lane;
+    const bool boxed = use_tma && v0 + 32 <= APpad;      // warp-uniform
+    unsigned char *bre = base_s + kVpRingBytes + wp * kVpBoxBytes, *bim = bre + kVpBoxBytes / 2;
     const bool have = v < n_rows;
     const int sv = have ? perm[v] : 0;
     const int sv0 = __shfl_sync(0xffffffffu, sv, 0);
@@ -177,12 +189,12 @@ __global__ void __launch_bounds__(256) k_volt_prep_rows(const uint8_t *__restric
     // all inside the channel's A P bytes (c A P and A P are multiples of 16, sv0 + 32 <= A P)
     const long long row0 = (long long)c * AP + sv0, a0 = row0 & ~15LL;
     const int off = (int)(row0 - a0), npc = (off + 47) >> 4;
-    auto issue = [&](int p) {      // pass p's 32 samples into ring slot p mod 4 (zero past the block)
-        const uint8_t *base = volt + (long long)(t0 + 32 * p) * tstride + a0;
+    auto issue = [&](int p) {      // pass p's 32 samples into ring slot p mod 3 (zero past the block)
+        const uint8_t *src = volt + (long long)(t0 + 32 * p) * tstride + a0;
         for (int i = lane; i < 32 * npc; i += 32) {
             const int t = i / npc, k = i - t * npc;
-            unsigned char *d = &s_w[p % kVpRing][wp][t][16 * k];
-            if (32 * p + t < nt) vp_cp16(d, base + (long long)t * tstride + 16 * k);
+            unsigned char *d = ring(p % kVpRing, wp, t) + 16 * k;
+            if (32 * p + t < nt) vp_cp16(d, src + (long long)t * tstride + 16 * k);
             else *reinterpret_cast<uint4 *>(d) = make_uint4(0u, 0u, 0u, 0u);
         }
         vp_commit();
@@ -200,14 +212,14 @@ __global__ void __launch_bounds__(256) k_volt_prep_rows(const uint8_t *__restric
             vp_wait(issued - 1 - p);                 // pass p's group has landed
             __syncwarp();
 #pragma unroll
-            for (int t = 0; t < 32; ++t) b[t] = s_w[p % kVpRing][wp][t][off + lane];
+            for (int t = 0; t < 32; ++t) b[t] = ring(p % kVpRing, wp, t)[off + lane];
             __syncwarp();                            // read by every lane before the slot is refilled
         } else {
             const uint8_t *src = volt + (long long)(t0 + tb) * tstride + (long long)c * AP + sv;
 #pragma unroll
             for (int t = 0; t < 32; ++t) b[t] = have && tb + t < nt ? (uint32_t)__ldg(src + (long long)t * tstride) : 0u;
         }
-        if (v >= APpad) continue;
+        if (!boxed && v >= APpad) continue;
         uint32_t re[16], im[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
@@ -220,6 +232,27 @@ __global__ void __launch_bounds__(256) k_volt_prep_rows(const uint8_t *__restric
                 im[t >> 1] = *reinterpret_cast<const uint32_t *>(&hi);
             }
         }
+        if (boxed) {
+            if (p > 0) {                             // the previous pass's stores have read the boxes
+                if (lane == 0) tc::bulk_wait_read<0>();
+                __syncwarp();
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int o = lane * 64 + ((k ^ ((lane >> 1) & 3)) << 4);
+                *reinterpret_cast<uint4 *>(bre + o) = make_uint4(re[4 * k], re[4 * k + 1], re[4 * k + 2], re[4 * k + 3]);
+                *reinterpret_cast<uint4 *>(bim + o) = make_uint4(im[4 * k], im[4 * k + 1], im[4 * k + 2], im[4 * k + 3]);
+            }
+            tc::fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                const int y = cl * APpad + v0;
+                tc::tma_store_2d(&smap_re, tc::smem_u32(bre), tb, y);
+                tc::tma_store_2d(&smap_im, tc::smem_u32(bim), tb, y);
+                tc::bulk_commit();
+            }
+            continue;
+        }
         uint4 *ore = reinterpret_cast<uint4 *>(yre + ((long long)cl * APpad + v) * Tpad + tb);
         uint4 *oim = reinterpret_cast<uint4 *>(yim + ((long long)cl * APpad + v) * Tpad + tb);
 #pragma unroll
@@ -228,6 +261,7 @@ __global__ void __launch_bounds__(256) k_volt_prep_rows(const uint8_t *__restric
             oim[k] = make_uint4(im[4 * k], im[4 * k + 1], im[4 * k + 2], im[4 * k + 3]);
         }
     }
+    if (boxed && lane == 0) tc::bulk_wait_all();
 }
 
 template <int N>
@@ -472,15 +506,21 @@ cudaError_t launch_gain_scale(const float2 *gains, int C, int AP, float *sy, cud
 
 cudaError_t launch_volt_prep(const uint8_t *volt, long long tstride, int t0, int nt, int c0, int nc, int AP,
                              int APpad, const float2 *gains, const float *sy, const int *perm, int Tpad, __half *yre,
-                             __half *yim, cudaStream_t st, int n_rows) {
+                             __half *yim, cudaStream_t st, int n_rows, const CUtensorMap *smap_re,
+                             const CUtensorMap *smap_im) {
     // samples per CTA: 32, or fewer (even, dividing Tpad) so the staged bytes stay within 96 KB
     const size_t APr = (size_t)((AP + 15) & ~15);
     const int rows = n_rows < 0 ? AP : n_rows;
     if (8 * APr > 96 * 1024 && Tpad % 32 == 0) {   // too large to stage 8 samples: one thread per plane row
         dim3 grid((APpad + 255) / 256, nc);
         const int vec_ok = tstride % 16 == 0 && AP % 16 == 0 && ((uintptr_t)volt & 15) == 0;
-        k_volt_prep_rows<<<grid, 256, 0, st>>>(volt, tstride, t0, nt, c0, AP, APpad, rows, gains, sy, perm, Tpad, vec_ok,
-                                               yre, yim);
+        const int use_tma = smap_re && smap_im ? 1 : 0;
+        CUtensorMap none{};
+        cudaError_t e = cudaFuncSetAttribute(k_volt_prep_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVpSmem);
+        if (e != cudaSuccess) return e;
+        k_volt_prep_rows<<<grid, 256, kVpSmem, st>>>(volt, tstride, t0, nt, c0, AP, APpad, rows, gains, sy, perm, Tpad,
+                                                     vec_ok, yre, yim, use_tma ? *smap_re : none,
+                                                     use_tma ? *smap_im : none, use_tma);
         return cudaGetLastError();
     }
     int TT = 32;
@@ -534,6 +574,27 @@ cudaError_t encode_plane_map(CUtensorMap *map, void *plane, int Tpad, long long 
                                                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Store map of the voltage planes for the row plane kernel: rows of Tpad halves, box 32 samples x
+// 32 rows, 64-byte swizzle.
+cudaError_t encode_plane_store_map(CUtensorMap *map, void *plane, int Tpad, long long rows) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const cuuint64_t dims[2] = {(cuuint64_t)Tpad, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Tpad * 2};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, plane, dims, strides, box,
+                                                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
