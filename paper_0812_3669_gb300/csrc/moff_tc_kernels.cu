@@ -30,9 +30,34 @@
 namespace moff {
 namespace {
 
-__device__ __forceinline__ float2 decode4_tc(uint32_t b) {
-    const int hi = (int)((b >> 4) & 15u), lo = (int)(b & 15u);
-    return make_float2((float)(hi - ((hi & 8) << 1)), (float)(lo - ((lo & 8) << 1)));
+// One weighted voltage y = (g s) x of a 4+4-bit code b (real part in the high nibble), with gs = g s
+// the gain times the channel's power-of-two scale.  A nibble u reads (u xor 8) - 8: (u xor 8) goes
+// into the low mantissa bits of 2^23, and one packed subtraction of 2^23 + 8 leaves the integer
+// exactly (no integer-to-float conversion); then re = gs.re x.re - gs.im x.im and im = gs.re x.im +
+// gs.im x.re, each one rounded product and one fused multiply-add, both parts in two packed
+// instructions.  Returns the pair as FP16 (round to nearest) for samples b0 (low half) and b1.
+__device__ __forceinline__ float2 weigh_tc(float2 gs, uint32_t b) {
+    const uint32_t bre = ((b >> 4) & 15u) ^ 0x4B000008u, bim = (b & 15u) ^ 0x4B000008u;
+    float2 x, p, y;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %4};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(x.x), "=f"(x.y)
+        : "r"(bre), "r"(bim), "f"(8388616.0f));
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(p.x), "=f"(p.y)
+        : "f"(-gs.y), "f"(gs.y), "f"(x.y), "f"(x.x));
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %2};\n\tmov.b64 rb, {%3, %4};\n\tmov.b64 rc, {%5, %6};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(y.x), "=f"(y.y)
+        : "f"(gs.x), "f"(x.x), "f"(x.y), "f"(p.x), "f"(p.y));
+    return y;
+}
+__device__ __forceinline__ void weigh2_tc(float2 gs, uint32_t b0, uint32_t b1, uint32_t &re, uint32_t &im) {
+    const float2 y0 = weigh_tc(gs, b0), y1 = weigh_tc(gs, b1);
+    const __half2 hr = __floats2half2_rn(y0.x, y1.x), hi = __floats2half2_rn(y0.y, y1.y);
+    re = *reinterpret_cast<const uint32_t *>(&hr);
+    im = *reinterpret_cast<const uint32_t *>(&hi);
 }
 
 // s_y[c] = 2^e with 16 * max|g_c| * 2^e in [2^13, 2^14): |y| <= |g| (|x_re| + |x_im|) <= 16 |g|.
@@ -102,17 +127,13 @@ __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ v
             uint4 re = make_uint4(0u, 0u, 0u, 0u), im = re;
             if (v < n_rows) {
                 const int sv = perm[v];
-                const float2 g = gains[(long long)c * AP + sv];
-                __half2 hr[4], hi[4];
+                const float2 g = gains[(long long)c * AP + sv], gs = make_float2(g.x * s, g.y * s);
+                uint32_t hr[4], hi[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float2 y0 = cmul(g, decode4_tc(s_v[(t8 + 2 * u) * APr + sv]));
-                    const float2 y1 = cmul(g, decode4_tc(s_v[(t8 + 2 * u + 1) * APr + sv]));
-                    hr[u] = __floats2half2_rn(y0.x * s, y1.x * s);
-                    hi[u] = __floats2half2_rn(y0.y * s, y1.y * s);
-                }
-                re = *reinterpret_cast<const uint4 *>(hr);
-                im = *reinterpret_cast<const uint4 *>(hi);
+                for (int u = 0; u < 4; ++u)
+                    weigh2_tc(gs, s_v[(t8 + 2 * u) * APr + sv], s_v[(t8 + 2 * u + 1) * APr + sv], hr[u], hi[u]);
+                re = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+                im = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             }
             const long long o = ((long long)cl * APpad + v) * Tpad + tb + t8;   // 16-byte aligned (Tpad % 8 == 0)
             *reinterpret_cast<uint4 *>(yre + o) = re;
@@ -123,17 +144,15 @@ __global__ void __launch_bounds__(256) k_volt_prep(const uint8_t *__restrict__ v
     const int np = TT / 2;
     for (int i = threadIdx.x; i < APpad * np; i += blockDim.x) {
         const int v = i / np, tp = 2 * (i - v * np), t = tb + tp;
-        __half2 re = __floats2half2_rn(0.f, 0.f), im = re;
+        uint32_t re = 0u, im = 0u;
         if (v < n_rows) {
             const int sv = perm[v];
             const float2 g = gains[(long long)c * AP + sv];
-            float2 y0 = cmul(g, decode4_tc(s_v[tp * APr + sv])), y1 = cmul(g, decode4_tc(s_v[(tp + 1) * APr + sv]));
-            re = __floats2half2_rn(y0.x * s, y1.x * s);
-            im = __floats2half2_rn(y0.y * s, y1.y * s);
+            weigh2_tc(make_float2(g.x * s, g.y * s), s_v[tp * APr + sv], s_v[(tp + 1) * APr + sv], re, im);
         }
         const long long o = ((long long)cl * APpad + v) * Tpad + t;   // t even, Tpad even: 4-byte aligned
-        *reinterpret_cast<__half2 *>(yre + o) = re;
-        *reinterpret_cast<__half2 *>(yim + o) = im;
+        *reinterpret_cast<uint32_t *>(yre + o) = re;
+        *reinterpret_cast<uint32_t *>(yim + o) = im;
     }
 }
 
@@ -203,7 +222,7 @@ __global__ void __launch_bounds__(256, 3) k_volt_prep_rows(const uint8_t *__rest
     if (contig)
         for (; issued < np && issued < kVpRing - 1; ++issued) issue(issued);
     const float2 g = have ? gains[(long long)c * AP + sv] : make_float2(0.f, 0.f);
-    const float s = sy[c];
+    const float2 gs = make_float2(g.x * sy[c], g.y * sy[c]);
     for (int p = 0; p < np; ++p) {
         const int tb = 32 * p;
         uint32_t b[32];
@@ -225,12 +244,7 @@ __global__ void __launch_bounds__(256, 3) k_volt_prep_rows(const uint8_t *__rest
         for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
         if (have) {
 #pragma unroll
-            for (int t = 0; t < 32; t += 2) {
-                const float2 y0 = cmul(g, decode4_tc(b[t])), y1 = cmul(g, decode4_tc(b[t + 1]));
-                const __half2 hr = __floats2half2_rn(y0.x * s, y1.x * s), hi = __floats2half2_rn(y0.y * s, y1.y * s);
-                re[t >> 1] = *reinterpret_cast<const uint32_t *>(&hr);
-                im[t >> 1] = *reinterpret_cast<const uint32_t *>(&hi);
-            }
+            for (int t = 0; t < 32; t += 2) weigh2_tc(gs, b[t], b[t + 1], re[t >> 1], im[t >> 1]);
         }
         if (boxed) {
             if (p > 0) {                             // the previous pass's stores have read the boxes
