@@ -108,6 +108,28 @@ def test_dft_route_dense_array_is_automatic(grid_kind):
     check(img, oracle.moff_image(codes, gains, pos, taps, N, P), f"{grid_kind} dense 48x48 lattice, N=256")
 
 
+def test_plane_store_paths_agree(monkeypatch):
+    """The row plane kernel's two store paths -- TMA boxes of 32 rows x 32 samples for warps whose rows
+    lie inside the channel's plane rows, 16-byte stores from registers otherwise (MOFF_VP_TMA=0: all
+    rows) -- write the same FP16 planes, so the images are bit-identical: a lattice large enough for the
+    row plane kernel, whose plane rows per channel are no multiple of 32 (the last warp of each
+    channel stores directly), ragged samples, three channels."""
+    monkeypatch.setenv("MOFF_TC_DFT", "1")
+    rng = np.random.default_rng(612)
+    side, N, K, P, C, T = 80, 256, 5, 2, 3, 45
+    pos = synth.positions_lattice(rng, side, side, 1.0, 0.05, (N / 2 - side, N / 2 - side))
+    A = len(pos)
+    taps = c64(synth.taps_gaussian(rng, pos, K, 1.2, n_pol=P))
+    gains = c64(synth.gains_random(rng, C, A, P))
+    codes = synth.pack_4bit(rng.integers(-8, 8, size=(T, C, A, P)), rng.integers(-8, 8, size=(T, C, A, P)))
+    monkeypatch.delenv("MOFF_VP_TMA", raising=False)
+    boxed = dft_image(pos, taps, N, C, P, codes, gains, route="fp16_tcgrid")
+    monkeypatch.setenv("MOFF_VP_TMA", "0")
+    direct = dft_image(pos, taps, N, C, P, codes, gains, route="fp16_tcgrid")
+    assert np.array_equal(boxed, direct)
+    check(boxed, oracle.moff_image(codes, gains, pos, taps, N, P), "plane store paths")
+
+
 def test_dft_route_deterministic_and_gain_rescale(monkeypatch, grid_kind):
     monkeypatch.setenv("MOFF_TC_DFT", "1")
     pos, taps, codes, gains = case(760, 120, 256, 5, 2, C=2, T=11)
