@@ -208,6 +208,37 @@ def test_served_tensor_core_plan_equals_unserved():
     assert np.array_equal(img, ref)
 
 
+def test_served_large_dense_array_equals_unserved():
+    """A served plan on the tensor-core gridding route for an array large enough for the row plane kernel
+    (6400 dual-pol antennas: 12 800 code bytes per channel-sample) borrows its planes from the pool per block,
+    with their load and store tensor maps encoded per block: its image equals the unserved plan's bit for
+    bit, over two blocks (one ragged), and is within the reduced-precision bar of the oracle."""
+    rng = np.random.default_rng(4242)
+    side, N, K, P, C = 80, 256, 5, 2, 2
+    pos = synth.positions_lattice(rng, side, side, 1.0, 0.05, (N / 2 - side, N / 2 - side))
+    A = len(pos)
+    taps = c64(synth.taps_gaussian(rng, pos, K, 1.2, n_pol=P))
+    gains = c64(synth.gains_random(rng, C, A, P))
+    blks = blocks(4243, [29, 11], C, A, P)
+    with moff.Plan(pos, taps, N, C, P, fp16tc=True) as pu:
+        assert pu.route() == "fp16_tcgrid"
+        pu.set_gains(gains)
+        for b in blks:
+            pu.submit(b)
+        ref, nr = pu.read_image()
+    with moff.Plan(pos, taps, N, C, P, fp16tc=True, served=True) as ps, moff.Server(8 << 30, 2) as srv:
+        ps.set_gains(gains)
+        for b in blks:
+            srv.submit(ps, b)
+        srv.wait(0, 120000)
+        img, n = ps.read_image()
+    assert n == nr == 40
+    assert np.array_equal(img, ref)
+    err = oracle.max_norm_err(img, oracle.moff_image(np.concatenate(blks), gains, pos, taps, N, P))
+    print(f"served large dense array: max-normalised error {float(err.max()):.2e}")
+    assert err.max() <= 3e-3
+
+
 def test_served_fp16_routes_mix_equals_alone_and_match_oracle():
     """The FP16 stream of the serving pattern: a dense 48 x 48 lattice on the 256
     grid (tensor-core gridding and factored DFT) and a sparse array (row-spectrum
