@@ -509,6 +509,8 @@ KERNEL_SOURCES = {
                   "template <int N, int P>\nstruct RowDftShape"), "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
     "rows_dft": [("paper_0812_3669_gb300/csrc/moff_dft_kernels.cu", "template <int N, int P>\nstruct RowDftShape",
                   "template <int N, int P>\ncudaError_t launch_rows_dft_t"), "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
+    "rows_dft8": [("paper_0812_3669_gb300/csrc/moff_dft_kernels.cu", "template <int P>\nstruct RowDft8Shape",
+                   "}  // namespace"), "paper_0812_3669_gb300/csrc/moff_dft.cuh"],
     "grid_tc": ["paper_0812_3669_gb300/csrc/moff_gridtc.cu", "paper_0812_3669_gb300/csrc/moff_tc.cuh"],
     "volt_prep": ["paper_0812_3669_gb300/csrc/moff_tc_kernels.cu"],
 }
@@ -516,6 +518,15 @@ KERNEL_SOURCES = {
 ROUTE_KERNELS = {"fp16_dft": {"grid_rows": "grid_rows_dft", "cols_integrate": "cols_dft"},
                  "fp16_tcgrid": {"grid_rows": "grid_tc", "row_transform": "rows_dft", "cols_integrate": "cols_dft",
                                  "volt_prep": "volt_prep"}}
+
+
+def route_kernel(route, kind, N):
+    """Name (in KERNEL_SOURCES) of the kernel behind a timing kind on a route: the tensor-core
+    gridding route's row transform is the 8 x 64 kernel on the 512 grid (unless MOFF_ROWS8=0)."""
+    k = ROUTE_KERNELS.get(route, {}).get(kind, kind)
+    if k == "rows_dft" and N == 512 and os.environ.get("MOFF_ROWS8", "1") != "0":
+        return "rows_dft8"
+    return k
 
 
 def traffic_for(kernel_key, src, units_per_launch=None):
@@ -1077,7 +1088,7 @@ def dense_leg(args, ctx, wl_name, steps, warmup, fp16=True, headline=False, keep
     work = dense_work(route, pos, taps, N, P, info["time_chunk"])
     roofs = kernel_rooflines(kern, work, snaps, ctx.peaks)
     for kind, r in roofs.items():             # DRAM bytes from the committed capture against the method's bytes
-        kname = ROUTE_KERNELS.get(route, {}).get(kind, kind)
+        kname = route_kernel(route, kind, N)
         units = snaps / max(r["launches"], 1)
         t = traffic_for(kname + "@" + wl_name, KERNEL_SOURCES.get(kname, []), units)
         r["traffic_bytes_per_launch"] = t
@@ -1167,7 +1178,7 @@ def run_ours(args):
     dom = max(roofs, key=lambda k: roofs[k]["ms_per_launch"] * roofs[k]["launches"])
     b = roofs[dom]["bound"]
     rd = roofs[dom][b]
-    kname = ROUTE_KERNELS.get(head["route"], {}).get(dom, dom)
+    kname = route_kernel(head["route"], dom, wl["grid_n"])
     work = dense_work(head["route"], pos, taps, wl["grid_n"], wl["n_pol"], head["chunk"][0])[dom]
     per_launch = head["steps"] * head["samples_per_step"] * head["channels"] / max(roofs[dom]["launches"], 1)
     traffic = traffic_for(kname + "@" + args.workload, KERNEL_SOURCES.get(kname, []), per_launch)

@@ -279,6 +279,8 @@ struct moff_plan {
     // gridding kernel's shared memory for a grid-only (FP32 transform) launch
     bool dft = false;
     unsigned char *d_dft_tab = nullptr;     // rows (gridding kernel, row transform)
+    unsigned char *d_dft_tab_r8 = nullptr;  // the 8 x 64 row transform's tables (N = 512)
+    bool rows8 = false;                     // row transform of the tensor-core gridding route as 8 x 64
     unsigned char *d_dft_tab_c = nullptr;   // the column kernel's image
     int cols_w = 8;                         // columns per CTA of k_cols_dft
     int cols_w_source = 0;                  // 0 default, 1 measured (MOFF_AUTOTUNE)
@@ -861,10 +863,10 @@ moff_status run_image_gtc(moff_plan *pl, const uint8_t *volt, int n_time, long l
             ra.nc = nc;
             ra.row_nz = pl->d_row_nz;
             ra.active = pl->d_gt_active;
-            ra.dft_tab = pl->d_dft_tab;
+            ra.dft_tab = pl->rows8 ? pl->d_dft_tab_r8 : pl->d_dft_tab;
             ra.err = pl->d_err;
             TimedLaunch tr(pl, 7);
-            MOFF_CK(launch_rows_dft(pl->N, pl->P, ra, pl->st));
+            MOFF_CK(pl->rows8 ? launch_rows_dft8(pl->P, ra, pl->st) : launch_rows_dft(pl->N, pl->P, ra, pl->st));
             tr.done();
             ColDftArgs ca{};
             ca.H = reinterpret_cast<const __half *>(pl->d_H);
@@ -2263,6 +2265,15 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
             cudaMemcpy(pl->d_dft_tab_c, tabc.data(), tabc.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(MOFF_ECUDA, "tensor-core DFT table upload failed"));
         if (!pl->gtc) pl->dft_s_t = dft_kernel_scale(n_ant, ksize, grid_n, n_pol, pl->jones, pos, taps);
+        // the 8 x 64 row transform on the 512 grid: 2.76 against 3.31 ms per wide-field launch for the
+        // 16 x 32 one (MOFF_ROWS8=0 keeps that)
+        if (const char *e = getenv("MOFF_ROWS8"); pl->gtc && grid_n == 512 && !(e && atoi(e) == 0)) {
+            std::vector<unsigned char> t8 = build_rows8_table();
+            if ((s = palloc(pl, &pl->d_dft_tab_r8, t8.size())) != MOFF_OK) return bail(s);
+            if (cudaMemcpy(pl->d_dft_tab_r8, t8.data(), t8.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(MOFF_ECUDA, "row-transform table upload failed"));
+            pl->rows8 = true;
+        }
         if ((s = palloc(pl, &pl->d_sy, (size_t)n_chan * 4)) != MOFF_OK) return bail(s);
         if (pl->gtc) {
             pl->gt_tiles = (int)gtab.tile_cell.size();

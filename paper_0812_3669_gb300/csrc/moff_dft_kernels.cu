@@ -560,6 +560,240 @@ cudaError_t launch_cols_dft_t(const ColDftArgs &a, cudaStream_t st) {
 }
 
 
+// ---------------------------------------------------------------------------------------------
+// Row transform for N = 512 as 8 x 64 with the second stage transposed.  With n = b + 64 a
+// (a < 8, b < 64): stage 1 is the 8-point DFT over a, [F 64 rows (f, b)] x [16 (a, re/im)] ->
+// 16 (re/im, c) columns per row; the twiddle exp(+2 pi i b c / 512) / 8 is formed from w_b =
+// exp(+2 pi i b / 512) by complex products in FP32 and applied there, the result rounded to FP16 into
+// the stage-2 operand Y'[(f, c)][(re/im, b)] (MN-major); stage 2 is the 64-point DFT over b as the
+// product D[(re/im, d)][(f, c)] = T[(re/im, d)][(re/im, b)] . Y', the DFT matrix T in real form the
+// K-major A operand.  T's four 64 x 64 blocks are C, -S / S, C (C, S the cosine and sine matrices),
+// kept once as [-S; C; S]: the real-input k-steps read rows C, S from the middle block on, the
+// imaginary-input ones -S, C from the top.  TMEM lane (re/im, d) then holds outputs k = c + 8 d,
+// c < 8, of every row f: eight consecutive outputs of one part, one 16-byte store per row, a warp's
+// 32 lanes (32 consecutive d) writing 512 contiguous bytes.  Output scale 1/8 x 1/64 = 1/512, as the
+// 16 x 32 kernel's.  72.5 KB of shared memory, 128 TMEM columns: three CTAs per SM.
+template <int P>
+struct RowDft8Shape {
+    static constexpr int N = 512, N1 = 8, N2 = 64;
+    static constexpr int RS = 8 / P, F = P * RS;          // 8 transform rows per stripe, f = p RS + rl
+    static constexpr int M1 = F * N2, T1 = M1 / 128;      // stage-1 rows (f, b): four tiles
+    static constexpr int K1 = 16, C1 = 16;                // (a, re/im) -> (re/im, c)
+    static constexpr int LBO1 = (M1 / 8) * 128;
+    static constexpr int A1B = M1 * K1 * 2;
+    static constexpr int NB = F * N1;                     // stage-2 N: (f, c)
+    static constexpr int K2 = 2 * N2;                     // stage-2 K: (re/im, b)
+    static constexpr int LBOB = (NB / 8) * 128;           // K-direction stride of the stage-2 B operand
+    static constexpr int BB = NB * K2 * 2;
+    static constexpr int B1_BYTES = C1 * K1 * 2;
+    static constexpr int TSBO = (N2 / 8) * 128;           // row-group stride of the [-S; C; S] image (K = 64)
+    static constexpr int T_BYTES = 3 * N2 * N2 * 2;
+    static constexpr int W_BYTES = N2 * 8;                // float2 w_b
+    static constexpr int TAB_BYTES = B1_BYTES + T_BYTES + W_BYTES;
+    static constexpr int D1 = T1 * C1;                    // TMEM: stage-1 accumulators, then NB stage-2 columns
+    static constexpr int TCOLS = 128;
+    static constexpr int NPIECE = F * N1 * 2 * (N2 / 8);  // 16-byte pieces per sample: (f, a, re/im, b8)
+    static constexpr int ITER = NPIECE / kBlock;
+    static constexpr size_t SMEM = 16 + 2 * (size_t)A1B + BB + TAB_BYTES + 32;
+    static_assert(D1 + NB <= TCOLS && NPIECE % kBlock == 0 && kBlock == 256 && T1 == 4 && TAB_BYTES % 16 == 0,
+                  "8 x 64 row-transform shape");
+};
+
+__device__ __forceinline__ float2 cmul8(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_rows_dft8(const RowDftArgs a) {
+    using RD = RowDft8Shape<P>;
+    constexpr int N = RD::N, N2 = RD::N2, RS = RD::RS;
+    const int s = blockIdx.x, cl = blockIdx.y;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3;
+    const int ry0 = s * RS;
+    {   // stripes no kernel reaches carry no field: nothing to transform or store
+        bool any = false;
+        for (int rl = 0; rl < RS; ++rl) any |= ((a.row_nz[(ry0 + rl) >> 5] >> ((ry0 + rl) & 31)) & 1u) != 0;
+        if (!any) return;
+    }
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *sA1 = smem;                                   // [2][A1B]
+    unsigned char *sB = sA1 + 2 * RD::A1B;                       // stage-2 B operand Y'
+    unsigned char *sTab = sB + RD::BB;
+    const unsigned char *sB1 = sTab, *sT = sTab + RD::B1_BYTES;
+    const float2 *sW = reinterpret_cast<const float2 *>(sT + RD::T_BYTES);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sTab + RD::TAB_BYTES);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+
+    dftc::load_table(sTab, a.dft_tab, RD::TAB_BYTES);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, RD::TCOLS);
+        tc::tmem_relinquish();
+    }
+    // Piece i = k kBlock + tid = ((f 8 + aa) 2 + ri) 8 + b8: the thread fixes (aa, ri, b8) and f mod 2,
+    // k fixes f's high part.  In the stage-1 operand the piece is the 8 rows m = 64 f + 8 b8 + (0..7)
+    // at k = 2 aa + ri; pieces of tiles no kernel reaches are zero, cleared once.
+    const int b8 = tid & 7, ri = (tid >> 3) & 1, aa = (tid >> 4) & 7, f0 = tid >> 7;
+    const int kk = 2 * aa + ri;
+    const uint32_t dst_t = (uint32_t)(b8 * 128 + (kk >> 3) * RD::LBO1 + (kk & 7) * 16);
+    const int ty = ry0 >> 3, nty = N / 8, tx = 8 * aa + b8;   // the stripe lies in one tile row
+    const bool active = a.active[ty * nty + tx] != 0;
+    if (!active) {
+#pragma unroll
+        for (int k = 0; k < RD::ITER; ++k) {
+            const uint32_t d = (uint32_t)((2 * k + f0) * 8 * 128) + dst_t;
+            *reinterpret_cast<uint4 *>(sA1 + d) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(sA1 + RD::A1B + d) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+    const float sc = 1.0f / (float)N2;
+
+    // output row f of sample tt: [re N][im N] halves
+    auto row_base = [&](int tt, int f) -> long long {
+        const int p = f / RS, rl = f - p * RS;
+        return (((long long)tt * a.slab_t + (long long)cl * a.slab_c) * P + p) * N * 2 * N +
+               (long long)(ry0 + rl) * 2 * N;
+    };
+    // input piece: the tile-major field, [channel][pol][tile row][tile col][sample][cy][re/im][cx]
+    const long long tstride = (long long)a.Tb * 128;
+    auto load = [&](int tt, int buf) {
+        if (active) {
+            unsigned char *dst = sA1 + buf * RD::A1B;
+#pragma unroll
+            for (int k = 0; k < RD::ITER; ++k) {
+                const int f = 2 * k + f0, p = f / RS, ry = ry0 + (f - p * RS);
+                const __half *src = a.G + ((((long long)cl * P + p) * nty + ty) * nty + tx) * tstride +
+                                    (long long)tt * 128 + ((ry & 7) * 2 + ri) * 8;
+                cp_async16(dst + (uint32_t)(f * 8 * 128) + dst_t, src);
+            }
+        }
+        cp_async_commit();
+    };
+    auto issue_s1 = [&](int buf) {
+        tc::fence_after_sync();
+        const uint32_t id1 = tc::idesc_f16(128, RD::C1, true, false);
+        const uint32_t a0 = tc::smem_u32(sA1 + buf * RD::A1B), b0 = tc::smem_u32(sB1);
+#pragma unroll
+        for (int j = 0; j < RD::T1; ++j)
+            tc::mma_f16(tbase + (uint32_t)(j * RD::C1), tc::smem_desc(a0 + j * 2048, RD::LBO1, 128),
+                        tc::smem_desc(b0, 128, (RD::K1 / 8) * 128), id1, false);
+        tc::mma_commit(&mbar[0]);
+    };
+    auto issue_s2 = [&]() {
+        tc::fence_after_sync();
+        const uint32_t id2 = tc::idesc_f16(128, RD::NB, false, true);
+        const uint32_t t0 = tc::smem_u32(sT), b0 = tc::smem_u32(sB);
+#pragma unroll
+        for (int ks = 0; ks < RD::K2 / 16; ++ks) {
+            // k-steps 0-3 (real parts of Y'): rows C, S from block 1; 4-7 (imaginary parts): -S, C from block 0
+            const uint32_t ta = t0 + (ks < 4 ? (uint32_t)(8 * RD::TSBO) : 0u) + (uint32_t)((ks & 3) * 256);
+            tc::mma_f16(tbase + (uint32_t)RD::D1, tc::smem_desc(ta, 128, RD::TSBO),
+                        tc::smem_desc(b0 + ks * 2 * RD::LBOB, RD::LBOB, 128), id2, ks > 0);
+        }
+        tc::mma_commit(&mbar[1]);
+    };
+    // twiddle, then the stage-2 operand: thread (f, b) writes the eight c of its row at k = b (re)
+    // and k = N2 + b (im) of n-group f
+    auto epi1 = [&]() {
+        for (int u = warp >> 2; u < RD::T1; u += kBlock / 128) {
+            const int m = 128 * u + 32 * q + lane, f = m / N2, b = m - f * N2;
+            float v[16];
+            tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(u * RD::C1), v);
+            float2 w[8];
+            w[0] = make_float2(1.f, 0.f);
+            w[1] = sW[b];
+            w[2] = cmul8(w[1], w[1]);
+            w[3] = cmul8(w[2], w[1]);
+            w[4] = cmul8(w[2], w[2]);
+            w[5] = cmul8(w[4], w[1]);
+            w[6] = cmul8(w[3], w[3]);
+            w[7] = cmul8(w[4], w[3]);
+            uint32_t re[4], im[4];
+#pragma unroll
+            for (int cc = 0; cc < 8; cc += 2) {
+                const float2 t0 = w[cc], t1 = w[cc + 1];
+                re[cc >> 1] = dftc::pack_hh((v[cc] * t0.x - v[8 + cc] * t0.y) * 0.125f,
+                                            (v[cc + 1] * t1.x - v[9 + cc] * t1.y) * 0.125f);
+                im[cc >> 1] = dftc::pack_hh((v[cc] * t0.y + v[8 + cc] * t0.x) * 0.125f,
+                                            (v[cc + 1] * t1.y + v[9 + cc] * t1.x) * 0.125f);
+            }
+            const int kr = b, ki = N2 + b;
+            *reinterpret_cast<uint4 *>(sB + f * 128 + (kr >> 3) * RD::LBOB + (kr & 7) * 16) =
+                make_uint4(re[0], re[1], re[2], re[3]);
+            *reinterpret_cast<uint4 *>(sB + f * 128 + (ki >> 3) * RD::LBOB + (ki & 7) * 16) =
+                make_uint4(im[0], im[1], im[2], im[3]);
+        }
+    };
+    // stage-2 accumulators -> FP16 (x 1/N2) rows: lane (re/im, d) of warp group g holds the eight c
+    // of rows f = 4 g .. 4 g + 3
+    auto epi2 = [&](int tt) {
+        const int g = warp >> 2, m2 = 32 * q + lane, part = m2 / N2, d = m2 - part * N2;
+        float v[32];
+        tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(RD::D1 + 32 * g), v);
+#pragma unroll
+        for (int fl = 0; fl < 4; ++fl) {
+            uint32_t h[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) h[u] = dftc::pack_hh(v[8 * fl + 2 * u] * sc, v[8 * fl + 2 * u + 1] * sc);
+            *reinterpret_cast<uint4 *>(a.H + row_base(tt, 4 * g + fl) + part * N + 8 * d) = make_uint4(h[0], h[1], h[2], h[3]);
+        }
+    };
+
+    bool ok = true;
+    if (a.nt > 0) load(0, 0);
+    for (int t = 0; t < a.nt; ++t) {
+        const int buf = t & 1;
+        cp_async_wait<0>();
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (tid == 0) issue_s1(buf);
+        if (t + 1 < a.nt) load(t + 1, buf ^ 1);
+        if (t > 0) {
+            ok &= tc::mbar_wait_bounded(&mbar[1], (uint32_t)((t - 1) & 1), dftc::kWaitCycles);
+            tc::fence_after_sync();
+            epi2(t - 1);
+        }
+        ok &= tc::mbar_wait_bounded(&mbar[0], (uint32_t)(t & 1), dftc::kWaitCycles);
+        tc::fence_after_sync();
+        epi1();
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (tid == 0) issue_s2();
+    }
+    if (ok && a.nt > 0) {
+        ok &= tc::mbar_wait_bounded(&mbar[1], (uint32_t)((a.nt - 1) & 1), dftc::kWaitCycles);
+        tc::fence_after_sync();
+        epi2(a.nt - 1);
+    }
+    cp_async_wait<0>();
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok);
+    tc::fence_after_sync();
+    if (!ok && tid == 0) atomicExch(a.err, tc::kErrWaitTimeout);
+    if (warp == 0) tc::tmem_dealloc(tbase, RD::TCOLS);
+}
+
+template <int P>
+cudaError_t launch_rows_dft8_t(const RowDftArgs &a, cudaStream_t st) {
+    auto k = k_rows_dft8<P>;
+    const size_t smem = RowDft8Shape<P>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(512 / RowDft8Shape<P>::RS, a.nc), kBlock, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 
 }  // namespace
 
@@ -612,6 +846,47 @@ std::vector<unsigned char> build_dft_table(int N, bool cols) {
             }
         }
     return img;
+}
+
+// Tables of the 8 x 64 row transform (N = 512), all in FP64 then rounded once: B1 [n = 8 re/im + c]
+// [k = 2 a + re/im] = the real form of exp(+2 pi i a c / 8) (K-major, 16 x 16); the stage-2 DFT
+// matrix's blocks [-S; C; S] (S, C [d][b] = sin, cos of 2 pi b d / 64; K-major, 192 rows x 64);
+// w_b = exp(+2 pi i b / 512) as float2.
+std::vector<unsigned char> build_rows8_table() {
+    constexpr int B1B = 16 * 16 * 2, TB = 3 * 64 * 64 * 2;
+    std::vector<unsigned char> img((size_t)B1B + TB + 64 * 8, 0);
+    auto put = [&](size_t off, double v) {
+        const __half h = __float2half_rn((float)v);
+        std::memcpy(img.data() + off, &h, 2);
+    };
+    for (int c = 0; c < 8; ++c)
+        for (int aa = 0; aa < 8; ++aa) {
+            double wc, ws;
+            unit_root((long long)aa * c, 8, &wc, &ws);
+            put(kmajor_at(c, 2 * aa, 16), wc);
+            put(kmajor_at(c, 2 * aa + 1, 16), -ws);
+            put(kmajor_at(8 + c, 2 * aa, 16), ws);
+            put(kmajor_at(8 + c, 2 * aa + 1, 16), wc);
+        }
+    for (int d = 0; d < 64; ++d)
+        for (int b = 0; b < 64; ++b) {
+            double vc, vs;
+            unit_root((long long)b * d, 64, &vc, &vs);
+            put(B1B + kmajor_at(d, b, 64), -vs);
+            put(B1B + kmajor_at(64 + d, b, 64), vc);
+            put(B1B + kmajor_at(128 + d, b, 64), vs);
+        }
+    for (int b = 0; b < 64; ++b) {
+        double wc, ws;
+        unit_root(b, 512, &wc, &ws);
+        const float2 v = make_float2((float)wc, (float)ws);
+        std::memcpy(img.data() + B1B + TB + (size_t)b * 8, &v, 8);
+    }
+    return img;
+}
+
+cudaError_t launch_rows_dft8(int P, const RowDftArgs &a, cudaStream_t st) {
+    return P == 1 ? launch_rows_dft8_t<1>(a, st) : launch_rows_dft8_t<2>(a, st);
 }
 
 // Columns per CTA by default: 8 (two CTAs per SM, so one CTA's epilogue runs while the other

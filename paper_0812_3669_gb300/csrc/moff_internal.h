@@ -129,6 +129,9 @@ cudaError_t launch_grid_tc(const GridTcArgs &a, const CUtensorMap &are, const CU
 // Store map of the tile-major gridded field (rows of 128 halves; box 64 x 32, 128-byte swizzle).
 cudaError_t encode_gridtc_store_map(CUtensorMap *map, void *G, long long rows);
 cudaError_t launch_rows_dft(int N, int P, const RowDftArgs &a, cudaStream_t st);
+// The N = 512 row transform as 8 x 64 with the second stage transposed (its own table image).
+cudaError_t launch_rows_dft8(int P, const RowDftArgs &a, cudaStream_t st);
+std::vector<unsigned char> build_rows8_table();
 
 // Column transform + square-and-integrate (Eq. m6 steps 3-4, second axis).
 struct ColArgs {

@@ -108,6 +108,22 @@ def test_dft_route_dense_array_is_automatic(grid_kind):
     check(img, oracle.moff_image(codes, gains, pos, taps, N, P), f"{grid_kind} dense 48x48 lattice, N=256")
 
 
+@pytest.mark.parametrize("rows8", ["1", "0"])
+@pytest.mark.parametrize("P,jones", [(1, False), (2, False), (2, True)])
+def test_row_transform_kernels_on_the_512_grid(monkeypatch, rows8, P, jones):
+    """Both row transforms of the tensor-core gridding route on the 512 grid -- 8 x 64 with the second
+    stage transposed (the default) and 16 x 32 (MOFF_ROWS8=0) -- against the oracle, both pol counts and
+    Jones kernels, ragged samples, channel chunks of one (several launches per block)."""
+    monkeypatch.setenv("MOFF_TC_DFT", "1")
+    monkeypatch.setenv("MOFF_ROWS8", rows8)
+    monkeypatch.setenv("MOFF_SCRATCH_MB", "200")
+    C, T, K, A = 2, 19, 5, 220
+    pos, taps, codes, gains = case(880 + P + 3 * int(jones), A, 512, K, P, C, T, jones=jones)
+    img = dft_image(pos, taps, 512, C, P, codes, gains, jones=jones, route="fp16_tcgrid")
+    check(img, oracle.moff_image(codes, gains, pos, taps, 512, P, jones=jones),
+          f"rows8={rows8} P={P} jones={jones}")
+
+
 def test_plane_store_paths_agree(monkeypatch):
     """The row plane kernel's two store paths -- TMA boxes of 32 rows x 32 samples for warps whose rows
     lie inside the channel's plane rows, 16-byte stores from registers otherwise (MOFF_VP_TMA=0: all
