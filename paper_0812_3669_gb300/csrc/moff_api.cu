@@ -2439,10 +2439,11 @@ moff_status moff_plan_create(moff_plan **out, int n_ant, const double *pos, int 
         const int route = pl->gtc ? 3 : (pl->dft ? 2 : (pl->tc ? 1 : 0));
         fprintf(stderr,
                 "moff: plan A=%d K=%d N=%d C=%d P=%d route=%s chunk=%dx%d grid(tb=%d cells/lane=%d wide=%d staged=%d "
-                "source=%d) cols_w=%d persist=%d scratch=%.1f MB device=%.1f MB\n",
+                "source=%d) cols_w=%d rows8=%d persist=%d scratch=%.1f MB device=%.1f MB\n",
                 n_ant, ksize, grid_n, n_chan, n_pol, routes[route], pl->Tb, pl->Cb, pl->tb,
                 pl->quads ? 4 : (pl->pairs ? 2 : 1), (int)pl->wide, (int)pl->staged, pl->tune_source,
-                pl->dft ? pl->cols_w : 0, (int)pl->persist, pl->scratch_bytes / 1048576.0, pl->dev_bytes / 1048576.0);
+                pl->dft ? pl->cols_w : 0, (int)pl->rows8, (int)pl->persist, pl->scratch_bytes / 1048576.0,
+                pl->dev_bytes / 1048576.0);
     }
     *out = pl;
     g_err.clear();
