@@ -572,7 +572,7 @@ cudaError_t launch_cols_dft_t(const ColDftArgs &a, cudaStream_t st) {
 // imaginary-input ones -S, C from the top.  TMEM lane (re/im, d) then holds outputs k = c + 8 d,
 // c < 8, of every row f: eight consecutive outputs of one part, one 16-byte store per row, a warp's
 // 32 lanes (32 consecutive d) writing 512 contiguous bytes.  Output scale 1/8 x 1/64 = 1/512, as the
-// 16 x 32 kernel's.  72.5 KB of shared memory, 128 TMEM columns: three CTAs per SM.
+// 16 x 32 kernel's.  73 KB of shared memory, 128 TMEM columns: three CTAs per SM.
 template <int P>
 struct RowDft8Shape {
     static constexpr int N = 512, N1 = 8, N2 = 64;
